@@ -1,0 +1,118 @@
+"""Block-structured matrices and Alg. 6 (single-pass randomized SVD for them), FP64.
+
+M = sum_j E_j kron M_j with 0/1 patterns E_j (p x q) and m x n blocks M_j
+(Sec. 4).  For the block Hankel matrix of Sec. 4.2, E_k (s x s) has ones where
+i + j - 1 = k, so block (i, j) (1-based) is H_{i+j-1}, k = 1..2s-1.
+
+The oracle forms M, Omega = Omega^(1) kr Omega^(2) and Psi = Psi^(1) kr Psi^(2)
+explicitly and multiplies; the structured identity of Eq. (4.1),
+M Omega = sum_j (E_j Omega^(1)) kr (M_j Omega^(2)), is what the CUDA path
+computes instead, and the tests pin the two against each other.
+
+Factor draws (Philox contract): Omega^(1) = factor 0, Omega^(2) = factor 1 on
+stream tag 0; Psi^(1) = factor 0, Psi^(2) = factor 1 on tag 1; draw id 0.
+"""
+
+from __future__ import annotations
+
+import numpy as np
+
+from . import philox
+from .linalg import householder_qr, jacobi_svd, lstsq_qr
+from .tensor import khatri_rao
+
+
+def block_hankel(blocks: np.ndarray) -> np.ndarray:
+    """Explicit (m s) x (n s) block Hankel matrix from blocks (m, n, 2s-1)."""
+    m, n, nb = blocks.shape
+    s = (nb + 1) // 2
+    if nb != 2 * s - 1:
+        raise ValueError("a block Hankel needs 2s-1 blocks")
+    h = np.zeros((m * s, n * s))
+    for i in range(s):
+        for j in range(s):
+            h[i * m:(i + 1) * m, j * n:(j + 1) * n] = blocks[:, :, i + j]
+    return h
+
+
+def hankel_pattern(s: int, k: int) -> np.ndarray:
+    """E_k in R^{s x s}: ones where i + j - 1 = k (1-based), zeros elsewhere."""
+    e = np.zeros((s, s))
+    for i in range(s):
+        j = k - 1 - i  # 0-based: i + j = k - 1
+        if 0 <= j < s:
+            e[i, j] = 1.0
+    return e
+
+
+def structured_sketch(blocks: np.ndarray, om1: np.ndarray, om2: np.ndarray,
+                      transpose: bool = False) -> np.ndarray:
+    """sum_k (E_k Omega^(1)) kr (H_k Omega^(2)) of Eq. (4.1).
+
+    With transpose=True: sum_k (E_k^T Psi^(1)) kr (H_k^T Psi^(2)), the row sketch
+    M^T Psi of Alg. 6.
+    """
+    m, n, nb = blocks.shape
+    s = (nb + 1) // 2
+    out = 0.0
+    for k in range(1, nb + 1):
+        e = hankel_pattern(s, k)
+        hk = blocks[:, :, k - 1]
+        if transpose:
+            e, hk = e.T, hk.T
+        out = out + khatri_rao(e @ om1, hk @ om2)
+    return out
+
+
+def sketch_factors(seed: int, s: int, m: int, n: int, ell_r: int, ell_l: int,
+                   omega_round=None):
+    """(Omega^(1) s x l_r, Omega^(2) n x l_r, Psi^(1) s x l_l, Psi^(2) m x l_l)."""
+    o1 = philox.gaussian_factor(seed, 0, 0, philox.TAG_OMEGA, s, ell_r)
+    o2 = philox.gaussian_factor(seed, 1, 0, philox.TAG_OMEGA, n, ell_r)
+    p1 = philox.gaussian_factor(seed, 0, 0, philox.TAG_PSI, s, ell_l)
+    p2 = philox.gaussian_factor(seed, 1, 0, philox.TAG_PSI, m, ell_l)
+    if omega_round == "f32":
+        o1, o2, p1, p2 = (philox.round_to_f32(a) for a in (o1, o2, p1, p2))
+    elif omega_round == "bf16":
+        o1, o2, p1, p2 = (philox.round_to_bf16(a) for a in (o1, o2, p1, p2))
+    return o1, o2, p1, p2
+
+
+def single_pass_svd(blocks: np.ndarray, r: int, ell_r: int, ell_l: int, seed: int,
+                    omega_round=None):
+    """Alg. 6 on the explicit block Hankel matrix.
+
+    1. Omega = Omega^(1) kr Omega^(2), Psi = Psi^(1) kr Psi^(2)
+    2. Y = M Omega, Z = M^T Psi
+    3. Y = Q R (Householder)
+    4. W = (Psi^T Q)^+ Z^T (least squares)
+    5. W = U_W Sigma V^T
+    6. U = Q U_W
+    7. return U[:, :r], Sigma[:r], V[:, :r]
+    Also returns the intermediates for tests.
+    """
+    m, n, nb = blocks.shape
+    s = (nb + 1) // 2
+    o1, o2, p1, p2 = sketch_factors(seed, s, m, n, ell_r, ell_l, omega_round)
+    h = block_hankel(blocks)
+    omega = khatri_rao(o1, o2)
+    psi = khatri_rao(p1, p2)
+    y = h @ omega
+    z = h.T @ psi
+    q, _ = householder_qr(y)
+    w = lstsq_qr(psi.T @ q, z.T)
+    uw, sig, vt = jacobi_svd(w)
+    u = q @ uw
+    return {"U": u[:, :r], "S": sig[:r], "V": vt[:r].T, "Y": y, "Z": z, "Q": q,
+            "W": w, "factors": (o1, o2, p1, p2), "H": h}
+
+
+def rng_count_block(m: int, n: int, p: int, q: int, ell_r: int, ell_l: int) -> int:
+    """Normals drawn by Alg. 6 with KRP sketches: (n+q) l_r + (m+p) l_l (Sec. 4.1)."""
+    return (n + q) * ell_r + (m + p) * ell_l
+
+
+def rng_count_block_gauss(m: int, n: int, p: int, q: int, ell_r: int,
+                          ell_l: int) -> int:
+    """Normals for the same algorithm with dense Gaussian sketches: nq l_r + mp l_l."""
+    return n * q * ell_r + m * p * ell_l

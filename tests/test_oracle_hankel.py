@@ -1,0 +1,99 @@
+"""Pins of the oracle's block-Hankel construction and Alg. 6 (Sec. 4).
+
+* The block Hankel matrix equals sum_k E_k kron H_k with the 0/1 patterns E_k
+  of Sec. 4.2, built from explicit Kronecker products.
+* Eq. (4.1): M (Omega1 kr Omega2) = sum_k (E_k Omega1) kr (H_k Omega2), and the
+  mirror identity for M^T (Psi1 kr Psi2).
+* Exact-rank input: the single-pass approximation reproduces H (the two-sided
+  sketch is exact when rank(M) <= l_r, Sec. 4.4) and its singular values match
+  LAPACK's.
+* Random-number counts: the shares printed in Sec. 4.2 (golden fixture).
+"""
+
+import math
+import os
+
+import numpy as np
+import pytest
+
+from oracle import hankel as HK
+from oracle import tensor as T
+from synth import HankelSpec, markov_parameters
+from synth.hankel import system_matrices
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def small_spec(order=6, m=3, n=2, s=9, seed=5):
+    return HankelSpec("t", order, m, n, s, 0.9, seed, r=order, ell_r=order + 4,
+                      ell_l=int(math.ceil(1.5 * (order + 4))))
+
+
+def test_block_hankel_is_sum_of_kronecker_patterns():
+    sp = small_spec()
+    blocks = markov_parameters(sp)
+    h = HK.block_hankel(blocks)
+    ref = sum(T.kron(HK.hankel_pattern(sp.s, k), blocks[:, :, k - 1])
+              for k in range(1, sp.nblocks + 1))
+    assert np.array_equal(h, ref)
+    # Hankel: block (i, j) depends on i + j only
+    assert np.array_equal(h[:sp.m, sp.n:2 * sp.n], h[sp.m:2 * sp.m, :sp.n])
+
+
+def test_markov_parameters_definition():
+    sp = small_spec()
+    a, b, c, eig = system_matrices(sp)
+    blocks = markov_parameters(sp)
+    np.testing.assert_allclose(blocks[:, :, 0], c @ b, rtol=1e-14)
+    np.testing.assert_allclose(blocks[:, :, 4], c @ np.linalg.matrix_power(a, 4) @ b,
+                               rtol=1e-12, atol=1e-14)
+    ev = np.linalg.eigvals(a)
+    assert np.max(np.abs(ev)) <= sp.radius + 1e-12
+    for e in eig:
+        assert np.min(np.abs(ev - e)) < 1e-10
+
+
+def test_structured_sketch_identity_eq_4_1():
+    sp = small_spec()
+    blocks = markov_parameters(sp)
+    h = HK.block_hankel(blocks)
+    rng = np.random.default_rng(1)
+    o1, o2 = rng.standard_normal((sp.s, 5)), rng.standard_normal((sp.n, 5))
+    p1, p2 = rng.standard_normal((sp.s, 7)), rng.standard_normal((sp.m, 7))
+    np.testing.assert_allclose(HK.structured_sketch(blocks, o1, o2),
+                               h @ T.khatri_rao(o1, o2), rtol=1e-12, atol=1e-13)
+    np.testing.assert_allclose(HK.structured_sketch(blocks, p1, p2, transpose=True),
+                               h.T @ T.khatri_rao(p1, p2), rtol=1e-12, atol=1e-13)
+
+
+def test_single_pass_exact_rank_recovery():
+    sp = small_spec(order=6, m=3, n=2, s=12, seed=9)
+    blocks = markov_parameters(sp)
+    res = HK.single_pass_svd(blocks, sp.r, sp.ell_r, sp.ell_l, seed=0)
+    h = res["H"]
+    approx = (res["U"] * res["S"]) @ res["V"].T
+    assert np.linalg.norm(h - approx) <= 1e-10 * np.linalg.norm(h)
+    s_ref = np.linalg.svd(h, compute_uv=False)[:sp.r]
+    np.testing.assert_allclose(res["S"], s_ref, rtol=1e-8)
+    assert np.linalg.norm(res["U"].T @ res["U"] - np.eye(sp.r)) < 1e-12
+    assert np.linalg.norm(res["V"].T @ res["V"] - np.eye(sp.r)) < 1e-12
+
+
+def test_rng_counts_against_printed_shares():
+    vals = {}
+    with open(os.path.join(GOLDEN, "era_rng_percentages.txt")) as f:
+        for line in f:
+            if line.strip() and not line.startswith("#"):
+                k, v = line.split()
+                vals[k] = float(v)
+    m, n, s = int(vals["m"]), int(vals["n"]), int(vals["s"])
+    ell_r = int(vals["r"] + vals["rho"])
+    ell_l = int(math.ceil(1.5 * ell_r))
+    krp = HK.rng_count_block(m, n, s, s, ell_r, ell_l)
+    gauss = HK.rng_count_block_gauss(m, n, s, s, ell_r, ell_l)
+    randera = n * s * ell_r
+    assert math.floor(1000 * krp / randera) / 10 == vals["pct_of_randera"]
+    assert math.floor(1000 * krp / gauss) / 10 == vals["pct_of_rgauss"]
+    # the oracle's actual draws have exactly that many entries
+    o1, o2, p1, p2 = HK.sketch_factors(0, s, m, n, 3, 4)
+    assert o1.size + o2.size + p1.size + p2.size == HK.rng_count_block(m, n, s, s, 3, 4)

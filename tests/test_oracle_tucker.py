@@ -1,0 +1,155 @@
+"""Pins of the oracle's Tucker algorithms (Alg. 4, 5, 7, 8, Sec. 5.1-5.2).
+
+* Exact recovery: a tensor of exact multilinear rank r <= l with no noise is
+  reproduced to <= 1e-12 relative (rank(V_r^T Omega) = r almost surely, the
+  premise of the deterministic bound used in Sec. 3.2).
+* Orthonormality of every Q_n.
+* Deterministic relations from the proofs of Thm. 5.1 and Thm. 5.2:
+  RHOSVD:  e^2 <= sum_i ||(I - Q_i Q_i^T) X_(i)||^2
+  RSTHOSVD: e^2 =  sum_i ||(I - Q_i Q_i^T) G^(i-1)_(i)||^2
+  both:    e^2 = ||X||^2 - ||G||^2 (X_hat is an orthogonal projection of X)
+* The deterministic range-finder bound of Eq. (3.5) per mode.
+* RNG counts against Table 1 and the counts in the text that follows it.
+* Truncation of the core equals an HOSVD (Alg. 4) of the rank-l approximation.
+"""
+
+import numpy as np
+import pytest
+
+from oracle import tucker as TK
+from oracle import tensor as T
+from synth import TuckerSpec, tucker_tensor
+
+
+def small_spec(dims=(12, 10, 9), core=(3, 2, 4), noise=0.0, seed=77, ell=6):
+    return TuckerSpec("t", dims, core, noise, None, seed, core, (ell,) * len(dims))
+
+
+@pytest.mark.parametrize("memo", [False, True])
+@pytest.mark.parametrize("dims,core", [((12, 10, 9), (3, 2, 4)),
+                                       ((7, 8, 6, 5), (2, 3, 2, 2))])
+def test_rhosvd_krp_exact_recovery(dims, core, memo):
+    x, _, _ = tucker_tensor(small_spec(dims, core))
+    res = TK.rhosvd_krp(x, [5] * len(dims), seed=3, memo=memo)
+    assert TK.rel_error(x, res["G"], res["Q"]) <= 1e-12
+    for q in res["Q"]:
+        assert np.linalg.norm(q.T @ q - np.eye(q.shape[1])) <= 1e-13
+    g2, q2 = TK.truncate_core(res["G"], res["Q"], core)
+    assert TK.rel_error(x, g2, q2) <= 1e-12
+    assert g2.shape == core
+
+
+@pytest.mark.parametrize("dims,core", [((12, 10, 9), (3, 2, 4)),
+                                       ((7, 8, 6, 5), (2, 3, 2, 2))])
+def test_rsthosvd_krp_exact_recovery(dims, core):
+    x, _, _ = tucker_tensor(small_spec(dims, core))
+    res = TK.rsthosvd_krp(x, [5] * len(dims), seed=4)
+    assert TK.rel_error(x, res["G"], res["Q"]) <= 1e-12
+    for q in res["Q"]:
+        assert np.linalg.norm(q.T @ q - np.eye(q.shape[1])) <= 1e-13
+
+
+def noisy(dims=(14, 12, 10), core=(4, 4, 4), noise=0.05, seed=5):
+    x, _, _ = tucker_tensor(small_spec(dims, core, noise, seed))
+    return x
+
+
+@pytest.mark.parametrize("memo", [False, True])
+def test_rhosvd_error_bounded_by_modewise_residuals(memo):
+    x = noisy()
+    res = TK.rhosvd_krp(x, [6, 6, 6], seed=1, memo=memo)
+    e2 = TK.rel_error(x, res["G"], res["Q"]) ** 2 * T.frob(x) ** 2
+    bound = sum(np.linalg.norm(T.unfold(x, i) - q @ (q.T @ T.unfold(x, i))) ** 2
+                for i, q in enumerate(res["Q"]))
+    assert e2 <= bound * (1 + 1e-12)
+    assert e2 == pytest.approx(T.frob(x) ** 2 - T.frob(res["G"]) ** 2, rel=1e-10)
+
+
+def test_rsthosvd_error_decomposition_is_exact():
+    x = noisy(dims=(11, 9, 8, 7), core=(3, 3, 3, 3), noise=0.1)
+    res = TK.rsthosvd_krp(x, [5, 4, 5, 4], seed=2)
+    e2 = TK.rel_error(x, res["G"], res["Q"]) ** 2 * T.frob(x) ** 2
+    terms = 0.0
+    for i, q in enumerate(res["Q"]):
+        gi = T.unfold(res["cores"][i], i)
+        terms += np.linalg.norm(gi - q @ (q.T @ gi)) ** 2
+    assert e2 == pytest.approx(terms, rel=1e-10)
+    assert e2 == pytest.approx(T.frob(x) ** 2 - T.frob(res["G"]) ** 2, rel=1e-10)
+
+
+def test_range_finder_deterministic_bound_per_mode():
+    x = noisy(dims=(16, 12, 10), core=(3, 3, 3), noise=0.2, seed=8)
+    ell, r = 6, 3
+    res = TK.rhosvd_krp(x, [ell] * 3, seed=9)
+    for i in range(3):
+        m = T.unfold(x, i)
+        kmat = T.krp_except(res["omega"][i], i)
+        q = res["Q"][i]
+        lhs = np.linalg.norm(m - q @ (q.T @ m)) ** 2
+        u, s, vt = np.linalg.svd(m, full_matrices=False)
+        v_r, v_p = vt[:r].T, vt[r:].T
+        s_p = np.diag(s[r:])
+        mid = s_p @ (v_p.T @ kmat) @ np.linalg.pinv(v_r.T @ kmat)
+        rhs = np.sum(s[r:] ** 2) + np.linalg.norm(mid) ** 2
+        assert lhs <= rhs * (1 + 1e-10)
+
+
+def test_rng_counts_match_table_1():
+    d, n, ell = 3, 9, 4
+    x = np.random.default_rng(0).standard_normal((n,) * d)
+    fresh = TK.rhosvd_krp(x, [ell] * d, seed=0)
+    drawn = sum(f.size for om in fresh["omega"] for f in om if f is not None)
+    assert drawn == d * (d - 1) * n * ell == TK.rng_count_rhosvd_krp((n,) * d, [ell] * d)
+    st = TK.rsthosvd_krp(x, [ell] * d, seed=0)
+    drawn = sum(f.size for om in st["omega"] for f in om if f is not None)
+    # text after Table 1: step i draws (d-i) n l + (i-1) l^2 entries (1-based i)
+    exact = sum((d - i) * n * ell + (i - 1) * ell * ell for i in range(1, d + 1))
+    assert drawn == exact == TK.rng_count_rsthosvd_krp((n,) * d, [ell] * d)
+    # memoized: one factor per mode (the table prints (d-1) n l; see DESIGN readings)
+    memo = TK.memo_factors(0, (n,) * d, ell)
+    assert sum(f.size for f in memo) == d * n * ell == TK.rng_count_memo((n,) * d, ell)
+
+
+def test_memo_uses_single_draw_and_prefix_columns():
+    x = noisy()
+    res = TK.rhosvd_krp(x, [6, 4, 5], seed=12, memo=True)
+    shared = TK.memo_factors(12, x.shape, 6)
+    for i, om in enumerate(res["omega"]):
+        for j, f in enumerate(om):
+            if j == i:
+                assert f is None
+            else:
+                assert np.array_equal(f, shared[j][:, :[6, 4, 5][i]])
+
+
+def test_hosvd_exact_and_quasi_optimal():
+    x, _, _ = tucker_tensor(small_spec((12, 10, 9), (3, 2, 4), seed=3))
+    g, q = TK.hosvd(x, (3, 2, 4))
+    assert TK.rel_error(x, g, q) <= 1e-13
+    xn = noisy(noise=0.3)
+    r = (3, 3, 3)
+    g, q = TK.hosvd(xn, r)
+    e = TK.rel_error(xn, g, q) * T.frob(xn)
+    tails = [np.sqrt(np.sum(np.linalg.svd(T.unfold(xn, i), compute_uv=False)[r[i]:] ** 2))
+             for i in range(3)]
+    assert max(tails) <= e * (1 + 1e-12)
+    assert e <= np.sqrt(sum(t * t for t in tails)) * (1 + 1e-12)
+    gs, qs = TK.sthosvd(xn, r)
+    assert max(tails) <= TK.rel_error(xn, gs, qs) * T.frob(xn) * (1 + 1e-12)
+
+
+def test_truncation_equals_hosvd_of_rank_l_approximation():
+    x = noisy(noise=0.2)
+    res = TK.rhosvd_krp(x, [7, 7, 7], seed=6, memo=True)
+    g2, q2 = TK.truncate_core(res["G"], res["Q"], (3, 3, 3))
+    xhat = TK.reconstruct(res["G"], res["Q"])
+    gh, qh = TK.hosvd(xhat, (3, 3, 3))
+    for a, b in zip(q2, qh):
+        np.testing.assert_allclose(a @ a.T, b @ b.T, atol=1e-10)
+    np.testing.assert_allclose(TK.reconstruct(g2, q2), TK.reconstruct(gh, qh), atol=1e-10)
+
+
+def test_omega_rounding_modes():
+    f = TK.memo_factors(0, (5, 6), 3, omega_round="bf16")
+    for a in f:
+        assert np.array_equal(a, a.astype(np.float32).astype(np.float64))

@@ -1,0 +1,360 @@
+"""Benchmark of the KRP randomized-Tucker hot path on one GB300 (or N replicas).
+
+A step is one pass of the whole path over one synthetic tensor, resident in HBM:
+factor generation (Philox), the all-mode KRP sketch by dimension tree (MEMO),
+FP64 QR of every sketch, the multi-TTM core, FP64 rank-r truncation and the
+FP64-accumulated residual ||X - X_hat|| / ||X|| -- i.e. krp_tucker_rhosvd with
+KRP_MEMO | KRP_TRUNCATE | KRP_RESIDUAL.
+
+Default workload: the 1024^3 FP32 tensor of multilinear rank 32 + 1e-4 noise,
+l = 48 (r = 32, oversampling 16), seed 0.  The BF16 tensor-core form is timed on
+the BF16 copy of the same tensor and reported beside it.
+
+Metric: algorithmic GB/s of the step (three passes over X: sketch, core,
+residual, N * bytes each), with TFLOP/s from the paper's leading-order flop
+counts and the step time.  Prints ONE JSON line.
+"""
+
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "KRP sketch GB/s & TFLOP/s, RHOSVD time: BF16 vs FP32 at stated rel. error"
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            return json.load(f), "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0,
+            "sm_max_mhz": 2070.0}, "fallback"
+
+
+def fp32_ffma_peak_tflops(sm_mhz: float, sms: int = 152) -> float:
+    # 128 FP32 lanes per SM, one FMA (2 flops) per lane per clock
+    return sms * 128 * 2 * sm_mhz * 1e6 / 1e12
+
+
+# ------------------------------------------------------------------- clocks --
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[4:8]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": float(max(smax)) if smax else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+# --------------------------------------------------------------- workload --
+def make_inputs(spec, device, want_bf16=True):
+    import torch
+    from synth.tucker import tucker_tensor_device
+    x64, _, _ = tucker_tensor_device(spec, device=device)
+    x32 = x64.to(torch.float32)
+    xbf = x64.to(torch.bfloat16) if want_bf16 else None
+    del x64
+    torch.cuda.empty_cache()
+    return x32, xbf
+
+
+def step_flops(spec):
+    n = spec.numel
+    ell = max(spec.ell)
+    d = spec.d
+    # Table 1 (MEMO): 4 N l for the dimension-tree sketch + the multi-TTM core
+    core = 0.0
+    size = float(n)
+    for i in range(d):
+        core += 2.0 * size * spec.ell[i]
+        size = size / spec.dims[i] * spec.ell[i]
+    sketch = 4.0 * n * ell
+    resid = 2.0 * n * spec.ranks[0]
+    qr = sum(4.0 * nn * l * l for nn, l in zip(spec.dims, spec.ell))
+    return sketch, core, resid, qr
+
+
+def run_ours(args, rank, world, local_rank):
+    import torch
+    import paper_2507_23207_gb300 as K
+    from synth import config_spec
+
+    dev = torch.device(f"cuda:{local_rank}")
+    torch.cuda.set_device(dev)
+    spec = config_spec(args.config)
+    peaks, peak_src = measured_peaks()
+    x32, xbf = make_inputs(spec, dev, want_bf16=not args.no_bf16)
+    forms = [("f32", x32)] + ([("bf16", xbf)] if xbf is not None else [])
+    ranks = list(spec.ranks)
+    p = spec.oversample
+    flags = K.KRP_MEMO | K.KRP_TRUNCATE | K.KRP_RESIDUAL
+    core = torch.empty(int(np.prod(ranks)), dtype=torch.float32, device=dev)
+    facs = [torch.empty(n * r, dtype=torch.float64, device=dev) for n, r in zip(spec.dims, ranks)]
+    stream = torch.cuda.current_stream(dev)
+    ctx = K.Context(local_rank, stream.cuda_stream)
+    sk, co, rs, qr = step_flops(spec)
+    results = {}
+    for form, x in forms:
+        def step(fl=flags):
+            return K.krp_tucker_rhosvd(ctx, x, spec.dims, ranks, p, spec.omega_seed, fl, core, facs)
+        for _ in range(args.warmup):
+            res = step()
+        # phase breakdown (separate, synchronising run)
+        ph = step(flags | K.KRP_TIMINGS)["times"]
+        torch.cuda.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
+        launches0 = ctx.launch_count()
+        clocks = ClockSampler(local_rank)
+        clocks.start()
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        for _ in range(args.steps):
+            res = step()
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        clk = clocks.stop()
+        ms = ev0.elapsed_time(ev1) / args.steps
+        launches = (ctx.launch_count() - launches0)
+        if world > 1:
+            t = torch.tensor([ms], device=dev)
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            ms = float(t.item())
+        results[form] = {"ms": ms, "res": res, "phases": ph, "clocks": clk,
+                         "launches": launches, "bytes_per_elem": x.element_size()}
+    # dominant-kernel roofline: the sketch of mode 1 alone (one MTTKRP launch)
+    kr = kernel_roofline(ctx, spec, x32, dev, stream, peaks, results["f32"]["clocks"], args)
+    # e2e through the C ABI with host buffers (pinned), FP32 form
+    e2e = e2e_run(ctx, spec, x32, args) if rank == 0 and not args.no_e2e else None
+    ctx.close()
+    return spec, results, kr, e2e, peaks, peak_src, (sk, co, rs, qr)
+
+
+def kernel_roofline(ctx, spec, x32, dev, stream, peaks, clk, args):
+    import torch
+    import paper_2507_23207_gb300 as K
+    ell = max(spec.ell)
+    om = [torch.empty((ell, n), dtype=torch.float32, device=dev) for n in spec.dims]
+    K.krp_gen_factors(ctx, 0, 0, 0, spec.dims, ell, om)
+    y = torch.empty((ell, spec.dims[0]), dtype=torch.float32, device=dev)
+    for _ in range(3):
+        K.krp_sketch_mode(ctx, x32, spec.dims, 0, om, ell, y)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    reps = max(3, args.steps)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(reps):
+        K.krp_sketch_mode(ctx, x32, spec.dims, 0, om, ell, y)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    flops = 2.0 * spec.numel * ell
+    mhz = (clk or {}).get("sm_max_mhz") or peaks.get("sm_max_mhz", 2070.0)
+    peak = fp32_ffma_peak_tflops(mhz)
+    ach = flops / (ms * 1e-3) / 1e12
+    return {"kernel": "mttkrp_first_kernel (FP32, mode-1 sketch)", "bound": "alu",
+            "achieved": round(ach, 3), "peak": round(peak, 3), "unit": "TFLOP/s",
+            "frac": round(ach / peak, 4), "traffic": None, "ms": round(ms, 4),
+            "gbs": round(spec.numel * 4 / (ms * 1e-3) / 1e9, 1),
+            "peak_note": f"FP32 FFMA peak = 152 SMs x 128 lanes x 2 flop x {mhz:.0f} MHz"}
+
+
+def e2e_run(ctx, spec, x32, args):
+    import torch
+    import paper_2507_23207_gb300 as K
+    host = torch.empty(x32.shape, dtype=torch.float32, pin_memory=True)
+    host.copy_(x32)
+    ranks = list(spec.ranks)
+    core = torch.empty(int(np.prod(ranks)), dtype=torch.float32, pin_memory=True)
+    facs = [torch.empty(n * r, dtype=torch.float64, pin_memory=True) for n, r in zip(spec.dims, ranks)]
+    flags = K.KRP_MEMO | K.KRP_TRUNCATE | K.KRP_RESIDUAL
+    K.krp_tucker_rhosvd(ctx, host, spec.dims, ranks, spec.oversample, spec.omega_seed, flags, core, facs)
+    torch.cuda.synchronize()
+    reps = max(1, min(args.steps, 5))
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        res = K.krp_tucker_rhosvd(ctx, host, spec.dims, ranks, spec.oversample, spec.omega_seed,
+                                  flags, core, facs)
+    torch.cuda.synchronize()
+    ms = (time.perf_counter() - t0) * 1e3 / reps
+    d2h = core.numel() * 4 + sum(f.numel() * 8 for f in facs) + 8
+    return {"ms": ms, "h2d": spec.numel * 4, "d2h": d2h, "resid": res["rel_residual"]}
+
+
+def cpu_baseline(spec, target_s=12.0):
+    """The FP64 oracle (RHOSVD-KRP-MEMO + truncation + explicit residual) on a
+    slab sample X[:, :, :k] of the same workload, timed on the host cores."""
+    from oracle import philox, tucker as TK
+    from synth.tucker import tucker_factors, expand_tucker
+    g0, us = tucker_factors(spec)
+    k = 2
+    best = None
+    while True:
+        us_k = list(us)
+        us_k[-1] = us[-1][:k]
+        xs = expand_tucker(g0, us_k)
+        xs = philox.round_to_f32(xs)
+        t0 = time.perf_counter()
+        ora = TK.rhosvd_krp(xs, list(spec.ell), spec.omega_seed, memo=True, omega_round="f32")
+        g2, q2 = TK.truncate_core(ora["G"], ora["Q"], list(spec.ranks))
+        TK.rel_error(xs, g2, q2)
+        dt = time.perf_counter() - t0
+        best = (k, dt, xs.size)
+        if dt > target_s / 4 or k >= spec.dims[-1]:
+            break
+        k = min(spec.dims[-1], k * 4)
+    k, dt, n = best
+    gbs = 3 * n * 4 / dt / 1e9
+    threads = os.cpu_count() or 1
+    return {"value": round(gbs, 4), "unit": "GB/s", "cores": threads, "kind": "oracle",
+            "sample": f"slab sample X[:, :, :{k}] of {spec.name} ({n} entries), one "
+                      f"RHOSVD-KRP-MEMO + truncation + explicit residual, {dt:.2f} s",
+            "seconds": round(dt, 3)}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--config", default="c2")
+    ap.add_argument("--no-bf16", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        from synth import config_spec
+        spec = config_spec(args.config)
+        vals = []
+        for _ in range(args.warmup):
+            cpu_baseline(spec, target_s=4.0)
+        for _ in range(max(1, args.steps)):
+            vals.append(cpu_baseline(spec, target_s=4.0))
+        v = float(np.median([c["value"] for c in vals]))
+        line = {"impl": "reference", "metric": METRIC, "value": round(v, 4), "unit": "GB/s",
+                "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+                "ms_per_step": round(1e3 * float(np.median([c["seconds"] for c in vals])), 2),
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+                "data": "synthetic", "config": {"workload": spec.name + " slab sample"},
+                "cpu_baseline": {k: vals[-1][k] for k in ("kind", "cores", "sample")} | {"value": round(v, 4)},
+                "e2e": {"value": round(v, 4), "unit": "GB/s", "h2d_bytes_per_step": 0,
+                        "d2h_bytes_per_step": 0}}
+        print(json.dumps(line))
+        return
+
+    if world > 1:
+        import torch
+        torch.distributed.init_process_group("nccl")
+    spec, results, kr, e2e, peaks, peak_src, (sk, co, rs, qr) = run_ours(args, rank, world, local_rank)
+    if rank != 0:
+        return
+    f32 = results["f32"]
+    n = spec.numel
+    bytes_step = 3.0 * n * 4
+    flops_step = sk + co + rs + qr
+    ms = f32["ms"]
+    value = world * bytes_step / (ms * 1e-3) / 1e9
+    cpu = None if args.no_cpu else cpu_baseline(spec)
+    line = {
+        "metric": METRIC, "value": round(value, 2), "unit": "GB/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 4),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": f"{spec.name}: {'x'.join(map(str, spec.dims))} FP32, multilinear rank "
+                   f"{spec.core[0]} + {spec.noise:g} noise, l={spec.ell[0]}, r={spec.ranks[0]}, "
+                   "RHOSVD-KRP-MEMO + FP64 QR + core + FP64 truncation + FP64 residual",
+                   "l2": "inputs larger than L2 (no flush)", "replicas": world},
+        "tflops": round(world * flops_step / (ms * 1e-3) / 1e12, 3),
+        "rhosvd_ms": round(ms, 3),
+        "rel_error": f32["res"]["rel_residual"],
+        "phases_ms": {k: round(v, 4) for k, v in f32["phases"].items()},
+        "clocks": f32["clocks"],
+        "gpu_launches": f32["launches"],
+        "roofline": kr,
+        "peaks_source": peak_src,
+    }
+    if "bf16" in results:
+        b = results["bf16"]
+        line["bf16_form"] = {
+            "ms_per_step": round(b["ms"], 4),
+            "value": round(world * 3.0 * n * 2 / (b["ms"] * 1e-3) / 1e9, 2), "unit": "GB/s",
+            "tflops": round(world * flops_step / (b["ms"] * 1e-3) / 1e12, 3),
+            "rel_error": b["res"]["rel_residual"],
+            "phases_ms": {k: round(v, 4) for k, v in b["phases"].items()},
+            "speedup_vs_f32": round(ms / b["ms"], 3)}
+    if e2e:
+        line["e2e"] = {"value": round(bytes_step / (e2e["ms"] * 1e-3) / 1e9, 2), "unit": "GB/s",
+                       "ms_per_step": round(e2e["ms"], 3), "h2d_bytes_per_step": e2e["h2d"],
+                       "d2h_bytes_per_step": e2e["d2h"]}
+    if cpu:
+        line["cpu_baseline"] = cpu
+    print(json.dumps(line))
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,249 @@
+/*
+ * krp.h -- C ABI of the GB300 (sm_103a) Khatri-Rao random projection library.
+ *
+ * What it computes (Saibaba, Verma, Ballard, "Improved Analysis of Khatri-Rao
+ * Random Projections and Applications"):
+ *   - the mode-n KRP sketch  Y_n = X_(n) (Omega_d kr ... kr Omega_{n+1} kr
+ *     Omega_{n-1} kr ... kr Omega_1)  of a dense d-way tensor, without forming
+ *     the Khatri-Rao product (Sec. 5.1, Alg. 7 MTTKRP step);
+ *   - all d sketches from one shared factor set by a dimension tree
+ *     (RHOSVD-KRP-MEMO, Sec. 5.1);
+ *   - randomized HOSVD / ST-HOSVD with KRP sketches (Alg. 7, Alg. 8): FP64
+ *     thin QR of every sketch, multi-TTM core G = X x_1 Q_1^T ... x_d Q_d^T,
+ *     optional FP64 rank-r truncation of the core and FP64 residual;
+ *   - the single-pass randomized SVD of a block Hankel matrix with KRP
+ *     sketches (Alg. 6, Eq. (4.1)).
+ *
+ * Conventions used by every entry point
+ *   Layout.  A d-way tensor X of dims (n_1..n_d) is dense and mode-1 fastest:
+ *     element (i_1..i_d), 0-based, sits at sum_j i_j * prod_{m<j} n_m.  (A
+ *     C-contiguous torch tensor of shape (n_d, ..., n_1) has this layout.)
+ *     Matrices (factors Omega_j, sketches Y_n, bases Q_n) are column-major with
+ *     leading dimension equal to their row count.
+ *   Memory.  Unless stated otherwise, data pointers are device pointers of the
+ *     context's device.  The caller allocates and owns inputs and outputs; the
+ *     context owns its workspace (grown on demand with cudaMalloc between
+ *     calls).  krp_tucker_* and krp_block_hankel_lowrank also accept host
+ *     pointers for X / blocks and for their outputs: they are detected with
+ *     cudaPointerGetAttributes and staged through the workspace.
+ *   Streams.  All work is enqueued on the context's stream (set at creation
+ *     or with krp_set_stream) and is asynchronous unless stated otherwise.
+ *   Errors.  Arguments are validated before any launch; on failure the call
+ *     returns a non-zero krp_status, launches nothing and records a message
+ *     readable with krp_last_error.  No entry point aborts or throws.
+ *   Threads.  A context may be used by one host thread at a time.
+ *   Precision.  KRP_F32 inputs use FP32 CUDA-core arithmetic (the plain form);
+ *     KRP_BF16 inputs run the contractions over X on tcgen05 tensor cores with
+ *     FP32 accumulation.  QR, truncation and residual are FP64.
+ */
+#ifndef KRP_H_
+#define KRP_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define KRP_ABI_VERSION 1
+#define KRP_MAXD 8
+
+typedef enum krp_status {
+  KRP_OK = 0,
+  KRP_EINVAL = 1,        /* invalid argument (shape, pointer, dtype, flag) */
+  KRP_ENOMEM = 2,        /* workspace allocation failed */
+  KRP_ECUDA = 3,         /* a CUDA runtime/driver call failed */
+  KRP_EUNSUPPORTED = 4,  /* valid request the library does not implement */
+  KRP_ETIMEOUT = 5,      /* a bounded device-side wait expired */
+  KRP_ENUMERIC = 6       /* NaN/Inf met in a FP64 stage */
+} krp_status;
+
+typedef enum krp_dtype {
+  KRP_F32 = 0,
+  KRP_BF16 = 1,
+  KRP_FP8_E4M3 = 2,  /* reserved */
+  KRP_F64 = 3
+} krp_dtype;
+
+/* Flags of krp_tucker_rhosvd / krp_tucker_sthosvd. */
+#define KRP_MEMO 0x1u     /* one shared factor set + dimension tree (MEMO variant) */
+#define KRP_TRUNCATE 0x2u /* truncate the rank-l result to ranks r_i */
+#define KRP_RESIDUAL 0x4u /* compute ||X - X_hat||_F / ||X||_F (extra pass over X) */
+#define KRP_TIMINGS 0x8u  /* fill krp_tucker_out.times (synchronises per phase) */
+
+/* Draw ids of the factor sets used by the Tucker pipelines (see
+ * krp_gen_factors): memoized set = 0, fresh set of mode i = 1 + i, ST-HOSVD
+ * step i = 64 + i.  Stream tags: 0 = Omega (right sketch), 1 = Psi (left). */
+#define KRP_DRAW_MEMO 0u
+#define KRP_DRAW_FRESH_BASE 1u
+#define KRP_DRAW_STHOSVD_BASE 64u
+#define KRP_TAG_OMEGA 0u
+#define KRP_TAG_PSI 1u
+
+typedef struct krp_ctx_s* krp_ctx;
+
+/* ---- context ------------------------------------------------------------ */
+
+/* Create a context on CUDA device `device` that enqueues on `cuda_stream`
+ * (a cudaStream_t; NULL = the legacy default stream).  Errors: KRP_EINVAL
+ * (null out, bad device), KRP_ECUDA. */
+krp_status krp_create(krp_ctx* out, int device, void* cuda_stream);
+
+/* Synchronise the context's stream, free its workspace and the context. */
+krp_status krp_destroy(krp_ctx ctx);
+
+/* Switch the stream later work is enqueued on. */
+krp_status krp_set_stream(krp_ctx ctx, void* cuda_stream);
+
+/* Message of the last failed call on `ctx` ("" if none).  Owned by ctx. */
+const char* krp_last_error(krp_ctx ctx);
+
+/* Static name of a status code. */
+const char* krp_status_string(krp_status s);
+
+/* KRP_ABI_VERSION of the loaded library. */
+int krp_abi_version(void);
+
+/* Number of kernels this context has launched so far (for launch counting). */
+uint64_t krp_launch_count(krp_ctx ctx);
+
+/* ---- a1: sketching factors (Def. of KRP, Sec. 2.5) ------------------------ */
+
+/* Draw i.i.d. N(0,1) factors Omega_j (rows[j] x ell, column-major) on the
+ * device from Philox4x32-10 (10 rounds, Salmon et al. SC'11) and Box-Muller:
+ *   key = (seed mod 2^32, seed >> 32); entry (i,k) has e = i + rows[j]*k and
+ *   counter (e >> 2, j, draw_id, tag); the 4 output words of a counter give
+ *   entries e&~3 .. e|3 as z0 = rho(w0)cos(2pi u(w1)), z1 = rho(w0)sin(..),
+ *   z2 = rho(w2)cos(2pi u(w3)), z3 = rho(w2)sin(..), u(w) = (w+0.5)/2^32,
+ *   rho(w) = sqrt(-2 ln u(w)), computed in FP64, then rounded to out_type
+ *   (KRP_F32: RN; KRP_BF16: RN to FP32 then RN-even to bfloat16; KRP_F64).
+ * omega[j] may be NULL to skip factor j.  Column k of a factor does not depend
+ * on ell (prefix-consistent).  Errors: KRP_EINVAL (d out of 1..KRP_MAXD,
+ * rows[j] < 1, ell < 1, bad dtype). */
+krp_status krp_gen_factors(krp_ctx ctx, uint64_t seed, uint32_t draw_id,
+                           uint32_t tag, int d, const int64_t* rows, int ell,
+                           krp_dtype out_type, void* const* omega);
+
+/* The raw Philox4x32-10 words for counters (first_block + b, c1, c2, c3),
+ * b = 0..nblocks-1, under the key of `seed`; out (device) receives 4*nblocks
+ * uint32 in counter order.  Used to check the stream bit-exactly. */
+krp_status krp_philox_words(krp_ctx ctx, uint64_t seed, uint32_t c1,
+                            uint32_t c2, uint32_t c3, uint64_t first_block,
+                            int64_t nblocks, uint32_t* out);
+
+/* ---- a2: one mode-n sketch (Alg. 7, MTTKRP step) -------------------------- */
+
+/* Y (dims[n] x ell, FP32, column-major) = X_(n) K_n with
+ * K_n = Omega_d kr ... kr Omega_{n+1} kr Omega_{n-1} kr ... kr Omega_1.
+ * X: xt = KRP_F32 or KRP_BF16; omega[j] (j != n) is dims[j] x ell of type
+ * omt (KRP_F32 for F32 X, KRP_BF16 for BF16 X); omega[n] is ignored.  n is
+ * 0-based.  d in 2..KRP_MAXD, 1 <= ell <= 256.  The product is never formed:
+ * the contraction runs over X once (two-stage: one factor by GEMM, the rest
+ * as Hadamard-weighted reductions).  Errors: KRP_EINVAL, KRP_ENOMEM, KRP_ECUDA. */
+krp_status krp_sketch_mode(krp_ctx ctx, const void* X, krp_dtype xt, int d,
+                           const int64_t* dims, int n,
+                           const void* const* omega, krp_dtype omt, int ell,
+                           float* Y);
+
+/* ---- a3: all d sketches with one factor set (RHOSVD-KRP-MEMO, Sec. 5.1) ---- */
+
+/* Y[n] (dims[n] x ell) for n = 0..d-1 from the shared factors omega[0..d-1],
+ * by a dimension tree that contracts the first mode once and reuses the
+ * partial result for every mode but the first (cost 4 N ell flops, Sec. 5.1).
+ * Arguments as in krp_sketch_mode. */
+krp_status krp_sketch_all_modes(krp_ctx ctx, const void* X, krp_dtype xt,
+                                int d, const int64_t* dims,
+                                const void* const* omega, krp_dtype omt,
+                                int ell, float* const* Y);
+
+/* ---- a4: FP64 thin QR (Alg. 1 step 3) ------------------------------------ */
+
+/* Householder QR of `count` FP32 matrices Y[b] (m[b] x l[b], column-major,
+ * m >= l) into Q[b] (FP64, m x l, column-major, diag(R) >= 0).  R[b] (l x l,
+ * FP64, column-major) may be NULL.  Errors: KRP_EINVAL (m < l, l > 256),
+ * KRP_ENUMERIC (non-finite input; reported after a stream synchronisation). */
+krp_status krp_qr(krp_ctx ctx, int count, const float* const* Y,
+                  const int64_t* m, const int* l, double* const* Q,
+                  double* const* R);
+
+/* ---- a5: multi-TTM core (Alg. 7 last step) ------------------------------- */
+
+/* G = X x_1 Q_1^T x_2 Q_2^T ... x_d Q_d^T, G of dims (cols[0..d-1]) FP32,
+ * mode-1 fastest.  Q[j] is FP64 dims[j] x cols[j] column-major. */
+krp_status krp_multi_ttm(krp_ctx ctx, const void* X, krp_dtype xt, int d,
+                         const int64_t* dims, const double* const* Q,
+                         const int* cols, float* G);
+
+/* ---- a6-a8: randomized Tucker pipelines (Alg. 7, Alg. 8) ------------------ */
+
+typedef struct krp_phase_times {
+  double rng_ms, sketch_ms, qr_ms, core_ms, truncate_ms, residual_ms, total_ms;
+} krp_phase_times;
+
+typedef struct krp_tucker_out {
+  /* in: output buffers sized for the output ranks (l_i = r_i + oversample,
+   * or r_i with KRP_TRUNCATE); device or host memory */
+  float* core;                   /* prod of output ranks, mode-1 fastest */
+  double* factors[KRP_MAXD];     /* n_i x rank_i, column-major */
+  /* out */
+  int d;
+  int64_t core_dims[KRP_MAXD];
+  double rel_residual;           /* with KRP_RESIDUAL, else -1 */
+  double x_norm;                 /* ||X||_F (with KRP_RESIDUAL, else -1) */
+  double core_norm;              /* ||G||_F */
+  krp_phase_times times;         /* with KRP_TIMINGS */
+} krp_tucker_out;
+
+/* RHOSVD-KRP (Alg. 7): per mode i a fresh factor set (draw 1+i) of sketch
+ * size l_i = ranks[i] + oversample, sketch Y_i, FP64 QR -> Q_i; then the core
+ * G = X x {Q_i^T}.  With KRP_MEMO one shared set (draw 0, l = max l_i) and
+ * the dimension tree (krp_sketch_all_modes).  KRP_TRUNCATE: rank-r_i
+ * truncation by an FP64 HOSVD of the core (U_i = leading r_i left singular
+ * vectors of G_(i), G <- G x {U_i^T}, Q_i <- Q_i U_i).  KRP_RESIDUAL: FP64
+ * ||X - X_hat||_F / ||X||_F by streaming reconstruction.  Needs l_i <= n_i.
+ * X is KRP_F32 or KRP_BF16 (then factors are drawn in BF16). */
+krp_status krp_tucker_rhosvd(krp_ctx ctx, const void* X, krp_dtype xt, int d,
+                             const int64_t* dims, const int* ranks,
+                             int oversample, uint64_t seed, unsigned flags,
+                             krp_tucker_out* out);
+
+/* RSTHOSVD-KRP (Alg. 8), modes in the order 1..d: step i sketches the current
+ * core with factors of draw 64+i (l_j x l_i for j < i, n_j x l_i for j > i),
+ * QR -> Q_i, G <- G x_i Q_i^T.  Flags as above except KRP_MEMO (ignored). */
+krp_status krp_tucker_sthosvd(krp_ctx ctx, const void* X, krp_dtype xt, int d,
+                              const int64_t* dims, const int* ranks,
+                              int oversample, uint64_t seed, unsigned flags,
+                              krp_tucker_out* out);
+
+/* ---- a9-a10: block Hankel single-pass low-rank approximation (Alg. 6) ------ */
+
+/* M is the (m s) x (n s) block Hankel matrix with block (i, j) = H_{i+j-1}
+ * (1-based), given as `blocks`: 2s-1 column-major m x n blocks stored one
+ * after another (FP32 or BF16).  With Omega = Omega1 kr Omega2 (s x l_r,
+ * n x l_r; tag 0) and Psi = Psi1 kr Psi2 (s x l_l, m x l_l; tag 1), draw 0:
+ *   Y = M Omega  = sum_k (E_k Omega1) kr (H_k Omega2)     (Eq. (4.1))
+ *   Z = M^T Psi  = sum_k (E_k^T Psi1) kr (H_k^T Psi2)
+ *   Y = QR;  W = (Psi^T Q)^+ Z^T;  W = U_W S V^T;  U = Q U_W;
+ * returns U (m s x r), S (r), V (n s x r), FP64 column-major (device or host).
+ * ell_l = 0 selects ceil(1.5 ell_r).  Needs r <= ell_r <= ell_l, ell_r <= m s,
+ * ell_l <= n s, ell_r <= 256, ell_l <= 256. */
+krp_status krp_block_hankel_lowrank(krp_ctx ctx, const void* blocks,
+                                    krp_dtype bt, int m, int n, int s, int r,
+                                    int ell_r, int ell_l, uint64_t seed,
+                                    double* U, double* S, double* V);
+
+/* The two sketches of Alg. 6 alone (device pointers): Y (m s x ell_r) and
+ * Z (n s x ell_l), FP32, from given factors (FP32 or BF16 like the blocks). */
+krp_status krp_block_hankel_sketch(krp_ctx ctx, const void* blocks,
+                                   krp_dtype bt, int m, int n, int s,
+                                   const void* omega1, const void* omega2,
+                                   int ell_r, const void* psi1,
+                                   const void* psi2, int ell_l, float* Y,
+                                   float* Z);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* KRP_H_ */

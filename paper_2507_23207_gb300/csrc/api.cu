@@ -1,0 +1,310 @@
+// C ABI edge: context management, argument validation, error translation, and
+// the primitive entry points (factors, Philox words, sketches, QR, multi-TTM).
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+
+#include "common.cuh"
+#include "pipeline.h"
+
+struct krp_ctx_s {
+  krp::Ctx c;
+};
+
+namespace krp {
+
+static thread_local Ctx* g_current = nullptr;
+
+Ctx* current() { return g_current; }
+cudaStream_t stream() { return g_current->stream; }
+
+void fail(krp_status s, const char* fmt, ...) {
+  char buf[1024];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  throw Error{s, std::string(buf)};
+}
+
+void note_launch(const char*) {
+  if (g_current) ++g_current->launches;
+}
+
+void check_launch(const char* name) {
+  note_launch(name);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) fail(KRP_ECUDA, "launch of %s failed: %s", name, cudaGetErrorString(e));
+}
+
+void ensure_workspace(Ctx* c, size_t bytes) {
+  bytes = (bytes + (size_t(1) << 20)) & ~((size_t(1) << 20) - 1);
+  c->ws.off = 0;
+  if (c->ws.cap >= bytes) return;
+  if (c->ws.base) {
+    KRP_CUDA_CHECK(cudaStreamSynchronize(c->stream));
+    KRP_CUDA_CHECK(cudaFree(c->ws.base));
+    c->ws.base = nullptr;
+    c->ws.cap = 0;
+  }
+  void* p = nullptr;
+  cudaError_t e = cudaMalloc(&p, bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    fail(KRP_ENOMEM, "workspace allocation of %zu bytes failed: %s", bytes, cudaGetErrorString(e));
+  }
+  c->ws.base = static_cast<char*>(p);
+  c->ws.cap = bytes;
+}
+
+bool is_device_ptr(const void* p) {
+  if (!p) return false;
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+size_t dtype_size(krp_dtype t) {
+  switch (t) {
+    case KRP_F32: return 4;
+    case KRP_BF16: return 2;
+    case KRP_F64: return 8;
+    case KRP_FP8_E4M3: return 1;
+  }
+  return 0;
+}
+
+int64_t checked_numel(int d, const int64_t* dims) {
+  KRP_REQUIRE(dims != nullptr, "dims is NULL");
+  int64_t n = 1;
+  for (int j = 0; j < d; ++j) {
+    KRP_REQUIRE(dims[j] >= 1, "dims[%d] = %lld must be >= 1", j, (long long)dims[j]);
+    KRP_REQUIRE(n <= (int64_t(1) << 62) / dims[j], "tensor too large");
+    n *= dims[j];
+  }
+  return n;
+}
+
+// Runs `body` with ctx as the current context and converts errors.
+template <class F>
+static krp_status guarded(krp_ctx ctx, F&& body) {
+  if (!ctx) return KRP_EINVAL;
+  Ctx* c = &ctx->c;
+  Ctx* prev = g_current;
+  g_current = c;
+  krp_status st = KRP_OK;
+  try {
+    int cur = -1;
+    if (cudaGetDevice(&cur) != cudaSuccess || cur != c->device) {
+      cudaGetLastError();
+      KRP_CUDA_CHECK(cudaSetDevice(c->device));
+    }
+    body();
+    c->last_error.clear();
+  } catch (const Error& e) {
+    c->last_error = e.msg;
+    st = e.status;
+  } catch (const std::bad_alloc&) {
+    c->last_error = "host allocation failed";
+    st = KRP_ENOMEM;
+  } catch (...) {
+    c->last_error = "unexpected internal error";
+    st = KRP_ECUDA;
+  }
+  g_current = prev;
+  return st;
+}
+
+}  // namespace krp
+
+using namespace krp;
+
+extern "C" {
+
+krp_status krp_create(krp_ctx* out, int device, void* cuda_stream) {
+  if (!out) return KRP_EINVAL;
+  *out = nullptr;
+  int n = 0;
+  if (cudaGetDeviceCount(&n) != cudaSuccess) {
+    cudaGetLastError();
+    return KRP_ECUDA;
+  }
+  if (device < 0 || device >= n) return KRP_EINVAL;
+  krp_ctx ctx = new (std::nothrow) krp_ctx_s();
+  if (!ctx) return KRP_ENOMEM;
+  ctx->c.device = device;
+  ctx->c.stream = static_cast<cudaStream_t>(cuda_stream);
+  krp_status st = guarded(ctx, [&] {
+    KRP_CUDA_CHECK(cudaDeviceGetAttribute(&ctx->c.num_sms, cudaDevAttrMultiProcessorCount, device));
+    void* p = nullptr;
+    KRP_CUDA_CHECK(cudaMalloc(&p, 256));
+    ctx->c.d_status = static_cast<int*>(p);
+    KRP_CUDA_CHECK(cudaMemset(ctx->c.d_status, 0, 256));
+  });
+  if (st != KRP_OK) {
+    delete ctx;
+    return st;
+  }
+  *out = ctx;
+  return KRP_OK;
+}
+
+krp_status krp_destroy(krp_ctx ctx) {
+  if (!ctx) return KRP_EINVAL;
+  krp_status st = guarded(ctx, [&] {
+    KRP_CUDA_CHECK(cudaStreamSynchronize(ctx->c.stream));
+    if (ctx->c.ws.base) KRP_CUDA_CHECK(cudaFree(ctx->c.ws.base));
+    if (ctx->c.d_status) KRP_CUDA_CHECK(cudaFree(ctx->c.d_status));
+    ctx->c.ws.base = nullptr;
+    ctx->c.d_status = nullptr;
+  });
+  delete ctx;
+  return st;
+}
+
+krp_status krp_set_stream(krp_ctx ctx, void* cuda_stream) {
+  return guarded(ctx, [&] { ctx->c.stream = static_cast<cudaStream_t>(cuda_stream); });
+}
+
+const char* krp_last_error(krp_ctx ctx) { return ctx ? ctx->c.last_error.c_str() : "null context"; }
+
+const char* krp_status_string(krp_status s) {
+  switch (s) {
+    case KRP_OK: return "KRP_OK";
+    case KRP_EINVAL: return "KRP_EINVAL";
+    case KRP_ENOMEM: return "KRP_ENOMEM";
+    case KRP_ECUDA: return "KRP_ECUDA";
+    case KRP_EUNSUPPORTED: return "KRP_EUNSUPPORTED";
+    case KRP_ETIMEOUT: return "KRP_ETIMEOUT";
+    case KRP_ENUMERIC: return "KRP_ENUMERIC";
+  }
+  return "KRP_UNKNOWN";
+}
+
+int krp_abi_version(void) { return KRP_ABI_VERSION; }
+
+uint64_t krp_launch_count(krp_ctx ctx) { return ctx ? ctx->c.launches : 0; }
+
+krp_status krp_gen_factors(krp_ctx ctx, uint64_t seed, uint32_t draw_id, uint32_t tag, int d,
+                           const int64_t* rows, int ell, krp_dtype out_type, void* const* omega) {
+  return guarded(ctx, [&] {
+    KRP_REQUIRE(d >= 1 && d <= KRP_MAXD, "d = %d out of range 1..%d", d, KRP_MAXD);
+    KRP_REQUIRE(rows && omega, "rows/omega is NULL");
+    KRP_REQUIRE(ell >= 1, "ell = %d must be >= 1", ell);
+    KRP_REQUIRE(out_type == KRP_F32 || out_type == KRP_BF16 || out_type == KRP_F64,
+                "unsupported factor dtype %d", (int)out_type);
+    FactorJob jobs[KRP_MAXD];
+    int nj = 0;
+    for (int j = 0; j < d; ++j) {
+      KRP_REQUIRE(rows[j] >= 1, "rows[%d] must be >= 1", j);
+      if (!omega[j]) continue;
+      jobs[nj++] = FactorJob{omega[j], rows[j], (rows[j] * ell + 3) / 4, (uint32_t)j};
+    }
+    launch_gen_factors(seed, draw_id, tag, ell, out_type, jobs, nj);
+  });
+}
+
+krp_status krp_philox_words(krp_ctx ctx, uint64_t seed, uint32_t c1, uint32_t c2, uint32_t c3,
+                            uint64_t first_block, int64_t nblocks, uint32_t* out) {
+  return guarded(ctx, [&] {
+    KRP_REQUIRE(nblocks >= 0, "nblocks < 0");
+    KRP_REQUIRE(nblocks == 0 || out, "out is NULL");
+    launch_philox_words(seed, c1, c2, c3, first_block, nblocks, out);
+  });
+}
+
+krp_status krp_sketch_mode(krp_ctx ctx, const void* X, krp_dtype xt, int d, const int64_t* dims,
+                           int n, const void* const* omega, krp_dtype omt, int ell, float* Y) {
+  return guarded(ctx, [&] {
+    SketchArgs a = validate_sketch(X, xt, d, dims, omega, omt, ell);
+    KRP_REQUIRE(n >= 0 && n < d, "mode n = %d out of range", n);
+    KRP_REQUIRE(Y, "Y is NULL");
+    ensure_workspace(current(), sketch_workspace_bytes(a, false));
+    sketch_one_mode(a, n, Y);
+  });
+}
+
+krp_status krp_sketch_all_modes(krp_ctx ctx, const void* X, krp_dtype xt, int d,
+                                const int64_t* dims, const void* const* omega, krp_dtype omt,
+                                int ell, float* const* Y) {
+  return guarded(ctx, [&] {
+    SketchArgs a = validate_sketch(X, xt, d, dims, omega, omt, ell);
+    KRP_REQUIRE(Y, "Y is NULL");
+    for (int j = 0; j < d; ++j) KRP_REQUIRE(Y[j], "Y[%d] is NULL", j);
+    ensure_workspace(current(), sketch_workspace_bytes(a, true));
+    sketch_all_modes(a, Y);
+  });
+}
+
+krp_status krp_qr(krp_ctx ctx, int count, const float* const* Y, const int64_t* m, const int* l,
+                  double* const* Q, double* const* R) {
+  return guarded(ctx, [&] {
+    KRP_REQUIRE(count >= 0 && count <= 4096, "count out of range");
+    if (count == 0) return;
+    KRP_REQUIRE(Y && m && l && Q, "NULL argument");
+    size_t bytes = ws_bytes(count, sizeof(QrJob));
+    for (int b = 0; b < count; ++b) {
+      KRP_REQUIRE(Y[b] && Q[b], "Y[%d]/Q[%d] is NULL", b, b);
+      KRP_REQUIRE(l[b] >= 1 && l[b] <= 256 && m[b] >= l[b], "QR %d: need m >= l, 1 <= l <= 256", b);
+      bytes += ws_bytes((size_t)m[b] * l[b], sizeof(double));
+    }
+    Ctx* c = current();
+    ensure_workspace(c, bytes);
+    std::vector<QrJob> jobs(count);
+    for (int b = 0; b < count; ++b)
+      jobs[b] = QrJob{Y[b], Q[b], R ? R[b] : nullptr, c->ws.take<double>((size_t)m[b] * l[b]),
+                      m[b], l[b]};
+    KRP_CUDA_CHECK(cudaMemsetAsync(c->d_status, 0, sizeof(int), c->stream));
+    qr_householder_f64(jobs.data(), count, c->d_status);
+    raise_device_status(c);
+  });
+}
+
+krp_status krp_multi_ttm(krp_ctx ctx, const void* X, krp_dtype xt, int d, const int64_t* dims,
+                         const double* const* Q, const int* cols, float* G) {
+  return guarded(ctx, [&] {
+    KRP_REQUIRE(d >= 1 && d <= KRP_MAXD, "d out of range");
+    checked_numel(d, dims);
+    KRP_REQUIRE(X && Q && cols && G, "NULL argument");
+    KRP_REQUIRE(xt == KRP_F32 || xt == KRP_BF16, "X dtype must be F32 or BF16");
+    for (int j = 0; j < d; ++j) {
+      KRP_REQUIRE(Q[j], "Q[%d] is NULL", j);
+      KRP_REQUIRE(cols[j] >= 1 && cols[j] <= 256, "cols[%d] out of range", j);
+    }
+    ensure_workspace(current(), multi_ttm_workspace_bytes(d, dims, cols, xt));
+    multi_ttm(X, xt, d, dims, Q, cols, G);
+  });
+}
+
+krp_status krp_tucker_rhosvd(krp_ctx ctx, const void* X, krp_dtype xt, int d, const int64_t* dims,
+                             const int* ranks, int oversample, uint64_t seed, unsigned flags,
+                             krp_tucker_out* out) {
+  return guarded(ctx, [&] { tucker_pipeline(false, X, xt, d, dims, ranks, oversample, seed, flags, out); });
+}
+
+krp_status krp_tucker_sthosvd(krp_ctx ctx, const void* X, krp_dtype xt, int d,
+                              const int64_t* dims, const int* ranks, int oversample,
+                              uint64_t seed, unsigned flags, krp_tucker_out* out) {
+  return guarded(ctx, [&] { tucker_pipeline(true, X, xt, d, dims, ranks, oversample, seed, flags, out); });
+}
+
+krp_status krp_block_hankel_lowrank(krp_ctx ctx, const void* blocks, krp_dtype bt, int m, int n,
+                                    int s, int r, int ell_r, int ell_l, uint64_t seed, double* U,
+                                    double* S, double* V) {
+  return guarded(ctx, [&] { hankel_pipeline(blocks, bt, m, n, s, r, ell_r, ell_l, seed, U, S, V); });
+}
+
+krp_status krp_block_hankel_sketch(krp_ctx ctx, const void* blocks, krp_dtype bt, int m, int n,
+                                   int s, const void* omega1, const void* omega2, int ell_r,
+                                   const void* psi1, const void* psi2, int ell_l, float* Y,
+                                   float* Z) {
+  return guarded(ctx, [&] {
+    hankel_sketch_only(blocks, bt, m, n, s, omega1, omega2, ell_r, psi1, psi2, ell_l, Y, Z);
+  });
+}
+
+}  // extern "C"

@@ -1,0 +1,636 @@
+// FP32 CUDA-core kernels of the plain form.
+//
+// Every contraction over the big tensor is one of two shapes, because the
+// library always works on the fastest (first) mode and rotates the new index
+// to the slowest position (Z(m1, rest) -> Z'(rest, l)):
+//   gemm_tn_f32:        out[s, k] = sum_i A[i, s] F[i, k]         (TTM, Sec. 2.1)
+//   mttkrp_first_f32:   Y[i, k]   = sum_s A[i, s] prod_j V_j[digit_j(s), k]
+//                       (mode-1 MTTKRP with the Khatri-Rao row generated on
+//                        the fly from the factors, Alg. 7 MTTKRP step)
+// plus the "diagonal" contractions that finish a dimension tree (Sec. 5.1,
+// memoization) and the streaming FP64-accumulated residual.
+#include <algorithm>
+
+#include "common.cuh"
+
+namespace krp {
+namespace {
+
+constexpr int TM = 128;  // rows of the output tile (s for gemm_tn, i for mttkrp)
+constexpr int TK = 32;   // contraction chunk
+constexpr int APITCH = TK + 4;
+
+__device__ __forceinline__ float comp(const float4& v, int c) {
+  return c == 0 ? v.x : (c == 1 ? v.y : (c == 2 ? v.z : v.w));
+}
+
+// ----------------------------------------------------------------------------
+// out[s + ldo*k] (=|+=) sum_{i<K} A[i + lda*s] * F[i + ldf*k]
+// CTA: 128 rows s x NP columns k; thread (g, h) owns rows s0+g+16j (j<8) and
+// columns k0+4h..4h+3.  A chunks are staged [s][i] (i contiguous, float4).
+template <int NP, bool VEC>
+__global__ void __launch_bounds__(NP * 4)
+    gemm_tn_kernel(const float* __restrict__ A, int64_t lda, int64_t S, int K,
+                   const float* __restrict__ F, int64_t ldf, int L, float* __restrict__ out,
+                   int64_t ldo, int accumulate) {
+  constexpr int NT = NP * 4;
+  constexpr int AV = (TM * TK / 4 + NT - 1) / NT;
+  constexpr int FV = TK * NP / NT;
+  __shared__ __align__(16) float As[2][TM][APITCH];
+  __shared__ __align__(16) float Fs[2][TK][NP];
+
+  const int tid = threadIdx.x, g = tid & 15, h = tid >> 4;
+  const int64_t s0 = (int64_t)blockIdx.x * TM;
+  const int k0 = blockIdx.y * NP;
+  float acc[8][4];
+#pragma unroll
+  for (int j = 0; j < 8; ++j)
+#pragma unroll
+    for (int c = 0; c < 4; ++c) acc[j][c] = 0.f;
+
+  float4 ra[AV];
+  float rf[FV];
+  const int nchunks = (K + TK - 1) / TK;
+
+  auto load = [&](int kc) {
+#pragma unroll
+    for (int v = 0; v < AV; ++v) {
+      const int q = tid + v * NT;
+      float4 val = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (q < TM * TK / 4) {
+        const int sl = q >> 3, c4 = q & 7;
+        const int64_t s = s0 + sl;
+        const int i = kc + 4 * c4;
+        if (s < S) {
+          const float* p = A + (int64_t)i + lda * s;
+          if (VEC) {
+            if (i < K) val = *reinterpret_cast<const float4*>(p);
+          } else {
+            if (i + 0 < K) val.x = p[0];
+            if (i + 1 < K) val.y = p[1];
+            if (i + 2 < K) val.z = p[2];
+            if (i + 3 < K) val.w = p[3];
+          }
+        }
+      }
+      ra[v] = val;
+    }
+#pragma unroll
+    for (int v = 0; v < FV; ++v) {
+      const int q = tid + v * NT;
+      const int i = q % TK, kk = q / TK;
+      float val = 0.f;
+      if (kc + i < K && k0 + kk < L) val = F[(int64_t)(kc + i) + ldf * (k0 + kk)];
+      rf[v] = val;
+    }
+  };
+  auto store = [&](int buf) {
+#pragma unroll
+    for (int v = 0; v < AV; ++v) {
+      const int q = tid + v * NT;
+      if (q < TM * TK / 4) {
+        const int sl = q >> 3, c4 = q & 7;
+        *reinterpret_cast<float4*>(&As[buf][sl][4 * c4]) = ra[v];
+      }
+    }
+#pragma unroll
+    for (int v = 0; v < FV; ++v) {
+      const int q = tid + v * NT;
+      Fs[buf][q % TK][q / TK] = rf[v];
+    }
+  };
+
+  load(0);
+  store(0);
+  __syncthreads();
+  for (int c = 0; c < nchunks; ++c) {
+    const int buf = c & 1;
+    if (c + 1 < nchunks) load((c + 1) * TK);
+#pragma unroll
+    for (int ii = 0; ii < TK; ii += 4) {
+      float4 a[8];
+#pragma unroll
+      for (int j = 0; j < 8; ++j) a[j] = *reinterpret_cast<const float4*>(&As[buf][g + 16 * j][ii]);
+#pragma unroll
+      for (int cc = 0; cc < 4; ++cc) {
+        const float4 f = *reinterpret_cast<const float4*>(&Fs[buf][ii + cc][4 * h]);
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+          const float av = comp(a[j], cc);
+          acc[j][0] = fmaf(av, f.x, acc[j][0]);
+          acc[j][1] = fmaf(av, f.y, acc[j][1]);
+          acc[j][2] = fmaf(av, f.z, acc[j][2]);
+          acc[j][3] = fmaf(av, f.w, acc[j][3]);
+        }
+      }
+    }
+    if (c + 1 < nchunks) store(buf ^ 1);
+    __syncthreads();
+  }
+#pragma unroll
+  for (int j = 0; j < 8; ++j) {
+    const int64_t s = s0 + g + 16 * j;
+    if (s >= S) continue;
+#pragma unroll
+    for (int cc = 0; cc < 4; ++cc) {
+      const int k = k0 + 4 * h + cc;
+      if (k < L) {
+        float* o = out + s + ldo * k;
+        *o = accumulate ? *o + acc[j][cc] : acc[j][cc];
+      }
+    }
+  }
+}
+
+template <int NP>
+void gemm_tn_launch(const float* A, int64_t lda, int64_t S, int K, const float* F, int64_t ldf,
+                    int L, float* out, int64_t ldo, bool accumulate) {
+  dim3 grid((unsigned)((S + TM - 1) / TM), (unsigned)((L + NP - 1) / NP));
+  const bool vec = (lda % 4 == 0) && (K % 4 == 0) && ((reinterpret_cast<uintptr_t>(A) & 15) == 0);
+  if (vec)
+    gemm_tn_kernel<NP, true><<<grid, NP * 4, 0, stream()>>>(A, lda, S, K, F, ldf, L, out, ldo,
+                                                            accumulate ? 1 : 0);
+  else
+    gemm_tn_kernel<NP, false><<<grid, NP * 4, 0, stream()>>>(A, lda, S, K, F, ldf, L, out, ldo,
+                                                             accumulate ? 1 : 0);
+  check_launch("gemm_tn_f32");
+}
+
+// ----------------------------------------------------------------------------
+// Y[i + n1*k] += sum_{s in split} A[i + n1*s] * W(s, k),
+// W(s, k) = prod_j V_j[digit_j(s) + radix_j * k]   (the Khatri-Rao row)
+struct RadixDev {
+  int n;
+  int64_t radix[KRP_MAXD];
+  const float* V[KRP_MAXD];
+};
+
+__device__ __forceinline__ float krp_weight(const RadixDev& R, int64_t s, int k) {
+  float w = 1.f;
+  for (int j = 0; j < R.n; ++j) {
+    const int64_t r = R.radix[j];
+    const int64_t dgt = s % r;
+    s /= r;
+    w *= R.V[j][dgt + r * k];
+  }
+  return w;
+}
+
+template <int NP, bool VEC>
+__global__ void __launch_bounds__(NP * 4)
+    mttkrp_first_kernel(const float* __restrict__ A, int64_t n1, int64_t S, const RadixDev R,
+                        int L, float* __restrict__ Y, int64_t s_per_split) {
+  constexpr int NT = NP * 4;
+  constexpr int AV = (TM * TK / 4 + NT - 1) / NT;
+  constexpr int WV = (TK * NP + NT - 1) / NT;
+  __shared__ __align__(16) float As[2][TK][TM];
+  __shared__ __align__(16) float Ws[2][TK][NP];
+
+  const int tid = threadIdx.x, g = tid & 15, h = tid >> 4;
+  const int64_t i0 = (int64_t)blockIdx.x * TM;
+  const int k0 = blockIdx.y * NP;
+  const int64_t sb = (int64_t)blockIdx.z * s_per_split;
+  const int64_t se = min(S, sb + s_per_split);
+  if (sb >= se) return;
+  float acc[8][4];
+#pragma unroll
+  for (int j = 0; j < 8; ++j)
+#pragma unroll
+    for (int c = 0; c < 4; ++c) acc[j][c] = 0.f;
+
+  float4 ra[AV];
+  float rw[WV];
+  const int64_t nchunks = (se - sb + TK - 1) / TK;
+
+  auto load = [&](int64_t sc) {
+#pragma unroll
+    for (int v = 0; v < AV; ++v) {
+      const int q = tid + v * NT;
+      float4 val = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (q < TM * TK / 4) {
+        const int sl = q >> 5, c4 = q & 31;
+        const int64_t s = sc + sl;
+        const int64_t i = i0 + 4 * c4;
+        if (s < se) {
+          const float* p = A + i + n1 * s;
+          if (VEC) {
+            if (i < n1) val = *reinterpret_cast<const float4*>(p);
+          } else {
+            if (i + 0 < n1) val.x = p[0];
+            if (i + 1 < n1) val.y = p[1];
+            if (i + 2 < n1) val.z = p[2];
+            if (i + 3 < n1) val.w = p[3];
+          }
+        }
+      }
+      ra[v] = val;
+    }
+#pragma unroll
+    for (int v = 0; v < WV; ++v) {
+      const int q = tid + v * NT;
+      float w = 0.f;
+      if (q < TK * NP) {
+        const int sl = q / NP, kk = q % NP;
+        const int64_t s = sc + sl;
+        if (s < se && k0 + kk < L) w = krp_weight(R, s, k0 + kk);
+      }
+      rw[v] = w;
+    }
+  };
+  auto store = [&](int buf) {
+#pragma unroll
+    for (int v = 0; v < AV; ++v) {
+      const int q = tid + v * NT;
+      if (q < TM * TK / 4) {
+        const int sl = q >> 5, c4 = q & 31;
+        *reinterpret_cast<float4*>(&As[buf][sl][4 * c4]) = ra[v];
+      }
+    }
+#pragma unroll
+    for (int v = 0; v < WV; ++v) {
+      const int q = tid + v * NT;
+      if (q < TK * NP) Ws[buf][q / NP][q % NP] = rw[v];
+    }
+  };
+
+  load(sb);
+  store(0);
+  __syncthreads();
+  for (int64_t c = 0; c < nchunks; ++c) {
+    const int buf = (int)(c & 1);
+    if (c + 1 < nchunks) load(sb + (c + 1) * TK);
+#pragma unroll 8
+    for (int sl = 0; sl < TK; ++sl) {
+      const float4 a0 = *reinterpret_cast<const float4*>(&As[buf][sl][4 * g]);
+      const float4 a1 = *reinterpret_cast<const float4*>(&As[buf][sl][64 + 4 * g]);
+      const float4 w = *reinterpret_cast<const float4*>(&Ws[buf][sl][4 * h]);
+      const float av[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        acc[j][0] = fmaf(av[j], w.x, acc[j][0]);
+        acc[j][1] = fmaf(av[j], w.y, acc[j][1]);
+        acc[j][2] = fmaf(av[j], w.z, acc[j][2]);
+        acc[j][3] = fmaf(av[j], w.w, acc[j][3]);
+      }
+    }
+    if (c + 1 < nchunks) store(buf ^ 1);
+    __syncthreads();
+  }
+#pragma unroll
+  for (int j = 0; j < 8; ++j) {
+    const int64_t i = i0 + (j < 4 ? 4 * g + j : 64 + 4 * g + (j - 4));
+    if (i >= n1) continue;
+#pragma unroll
+    for (int cc = 0; cc < 4; ++cc) {
+      const int k = k0 + 4 * h + cc;
+      if (k < L) atomicAdd(Y + i + n1 * k, acc[j][cc]);
+    }
+  }
+}
+
+template <int NP>
+void mttkrp_first_launch(const float* A, int64_t n1, int64_t S, const RadixDev& R, int L,
+                         float* Y) {
+  const int mt = (int)((n1 + TM - 1) / TM);
+  const int nt = (L + NP - 1) / NP;
+  const int want = 8 * current()->num_sms;  // several waves of CTAs over the SMs
+  int64_t splits = std::max<int64_t>(1, want / std::max(1, mt * nt));
+  int64_t per = (S + splits - 1) / splits;
+  per = std::max<int64_t>(per, 4 * TK);
+  per = (per + TK - 1) / TK * TK;
+  splits = (S + per - 1) / per;
+  dim3 grid(mt, nt, (unsigned)splits);
+  const bool vec = (n1 % 4 == 0) && ((reinterpret_cast<uintptr_t>(A) & 15) == 0);
+  if (vec)
+    mttkrp_first_kernel<NP, true><<<grid, NP * 4, 0, stream()>>>(A, n1, S, R, L, Y, per);
+  else
+    mttkrp_first_kernel<NP, false><<<grid, NP * 4, 0, stream()>>>(A, n1, S, R, L, Y, per);
+  check_launch("mttkrp_first_f32");
+}
+
+// ----------------------------------------------------------------------------
+// Diagonal contractions over an intermediate T (dims m_0..m_{D-1}, then the
+// sketch column k slowest with stride tk).
+struct DiagDev {
+  int D;
+  int64_t m[KRP_MAXD];
+  const float* V[KRP_MAXD];  // V_j: m_j x L, column-major; V[n] unused
+};
+
+// target n = 0: Y[i + m0*k] = sum_s T[i + m0*s + tk*k] * prod_{j>=1} V_j[digit, k]
+__global__ void diag_first_kernel(const float* __restrict__ T, const DiagDev P, int64_t tk,
+                                  int L, float* __restrict__ Y, int64_t s_per_split) {
+  __shared__ float wsh[256];
+  const int k = blockIdx.y;
+  const int64_t m0 = P.m[0];
+  int64_t S = 1;
+  for (int j = 1; j < P.D; ++j) S *= P.m[j];
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t sb = (int64_t)blockIdx.z * s_per_split;
+  const int64_t se = min(S, sb + s_per_split);
+  float acc = 0.f;
+  const float* Tk = T + tk * k;
+  for (int64_t sc = sb; sc < se; sc += 256) {
+    __syncthreads();
+    for (int q = threadIdx.x; q < 256; q += blockDim.x) {
+      int64_t s = sc + q;
+      float w = 0.f;
+      if (s < se) {
+        w = 1.f;
+        for (int j = 1; j < P.D; ++j) {
+          const int64_t r = P.m[j];
+          w *= P.V[j][(s % r) + r * k];
+          s /= r;
+        }
+      }
+      wsh[q] = w;
+    }
+    __syncthreads();
+    if (i < m0) {
+      const int lim = (int)((se - sc) < 256 ? (se - sc) : 256);
+      for (int q = 0; q < lim; ++q) acc = fmaf(Tk[i + m0 * (sc + q)], wsh[q], acc);
+    }
+  }
+  if (i < m0) atomicAdd(Y + i + m0 * k, acc);
+}
+
+// target n >= 1: one warp per row (i_n, s): sum over the P contiguous prefix
+// entries weighted by prod_{j<n} V_j, times prod_{j>n} V_j of s.
+__global__ void diag_mid_kernel(const float* __restrict__ T, const DiagDev P, int64_t tk, int n,
+                                int L, float* __restrict__ Y) {
+  const int k = blockIdx.y;
+  int64_t Pp = 1, Sfx = 1;
+  for (int j = 0; j < n; ++j) Pp *= P.m[j];
+  for (int j = n + 1; j < P.D; ++j) Sfx *= P.m[j];
+  const int64_t mn = P.m[n];
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const float* Tk = T + tk * k;
+  for (int64_t row = warp; row < mn * Sfx; row += nwarps) {
+    const int64_t in = row % mn, s = row / mn;
+    const float* base = Tk + Pp * row;  // = Pp*(in + mn*s)
+    float part = 0.f;
+    for (int64_t p = lane; p < Pp; p += 32) {
+      float w = 1.f;
+      int64_t q = p;
+      for (int j = 0; j < n; ++j) {
+        const int64_t r = P.m[j];
+        w *= P.V[j][(q % r) + r * k];
+        q /= r;
+      }
+      part = fmaf(base[p], w, part);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+    if (lane == 0) {
+      float w = 1.f;
+      int64_t q = s;
+      for (int j = n + 1; j < P.D; ++j) {
+        const int64_t r = P.m[j];
+        w *= P.V[j][(q % r) + r * k];
+        q /= r;
+      }
+      atomicAdd(Y + in + mn * k, part * w);
+    }
+  }
+}
+
+__global__ void cast_f64_f32_kernel(const double* __restrict__ s, float* __restrict__ d, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    d[i] = static_cast<float>(s[i]);
+}
+__global__ void cast_f32_f64_kernel(const float* __restrict__ s, double* __restrict__ d, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    d[i] = static_cast<double>(s[i]);
+}
+// dst (cols x rows, col-major) = src^T (src rows x cols col-major), as FP32
+__global__ void transpose_f64_f32_kernel(const double* __restrict__ s, int64_t rows, int64_t cols,
+                                         float* __restrict__ d) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < rows * cols;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = e % rows, c = e / rows;
+    d[c + cols * r] = static_cast<float>(s[e]);
+  }
+}
+// dst[r + rest*i] = src[i + m0*r]
+__global__ void rotate_kernel(const float* __restrict__ s, int64_t m0, int64_t rest,
+                              float* __restrict__ d) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < m0 * rest;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = e % m0, r = e / m0;
+    d[r + rest * i] = s[e];
+  }
+}
+
+int grid_for(int64_t n, int threads) {
+  int64_t g = (n + threads - 1) / threads;
+  return (int)std::max<int64_t>(1, std::min<int64_t>(g, 8192));
+}
+
+// ----------------------------------------------------------------------------
+// Residual: acc[0] += ||X - Q1 H||_F^2, acc[1] += ||X||_F^2 with X n1 x S
+// (FP32 or BF16), Q1 n1 x l, H l x S (column-major, FP32).  A 128 x 128 tile
+// of X_hat is formed in registers (thread tile 8 x 8), compared with X, and
+// squared differences are summed in FP32 per thread and in FP64 across threads.
+template <class XT>
+__device__ __forceinline__ float ldx(const XT* p);
+template <>
+__device__ __forceinline__ float ldx<float>(const float* p) { return *p; }
+template <>
+__device__ __forceinline__ float ldx<__nv_bfloat16>(const __nv_bfloat16* p) {
+  return __bfloat162float(*p);
+}
+
+template <class XT>
+__global__ void __launch_bounds__(256)
+    residual_kernel(const XT* __restrict__ X, int64_t n1, int64_t S,
+                    const float* __restrict__ Q1, int l, const float* __restrict__ H,
+                    double* __restrict__ acc) {
+  constexpr int KC = 16;
+  __shared__ __align__(16) float Qs[KC][TM];
+  __shared__ __align__(16) float Hs[KC][TM + 4];
+  __shared__ double red[2][8];
+  const int tid = threadIdx.x, gi = tid & 15, gs = tid >> 4;
+  const int64_t s0 = (int64_t)blockIdx.x * TM;
+  const int64_t i0 = (int64_t)blockIdx.y * TM;
+  float xh[8][8];
+#pragma unroll
+  for (int a = 0; a < 8; ++a)
+#pragma unroll
+    for (int b = 0; b < 8; ++b) xh[a][b] = 0.f;
+  for (int kc = 0; kc < l; kc += KC) {
+    __syncthreads();
+    for (int q = tid; q < KC * TM; q += 256) {
+      const int kk = q / TM, r = q % TM;
+      const int64_t i = i0 + r, s = s0 + r;
+      Qs[kk][r] = (kc + kk < l && i < n1) ? Q1[i + n1 * (kc + kk)] : 0.f;
+    }
+    for (int q = tid; q < KC * TM; q += 256) {
+      const int kk = q % KC, r = q / KC;
+      const int64_t s = s0 + r;
+      Hs[kk][r] = (kc + kk < l && s < S) ? H[(kc + kk) + (int64_t)l * s] : 0.f;
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (int kk = 0; kk < KC; ++kk) {
+      const float4 q0 = *reinterpret_cast<const float4*>(&Qs[kk][4 * gi]);
+      const float4 q1 = *reinterpret_cast<const float4*>(&Qs[kk][64 + 4 * gi]);
+      const float4 h0 = *reinterpret_cast<const float4*>(&Hs[kk][4 * gs]);
+      const float4 h1 = *reinterpret_cast<const float4*>(&Hs[kk][64 + 4 * gs]);
+      const float qa[8] = {q0.x, q0.y, q0.z, q0.w, q1.x, q1.y, q1.z, q1.w};
+      const float ha[8] = {h0.x, h0.y, h0.z, h0.w, h1.x, h1.y, h1.z, h1.w};
+#pragma unroll
+      for (int a = 0; a < 8; ++a)
+#pragma unroll
+        for (int b = 0; b < 8; ++b) xh[a][b] = fmaf(qa[a], ha[b], xh[a][b]);
+    }
+  }
+  float d2 = 0.f, x2 = 0.f;
+#pragma unroll
+  for (int b = 0; b < 8; ++b) {
+    const int64_t s = s0 + (b < 4 ? 4 * gs + b : 64 + 4 * gs + (b - 4));
+    if (s >= S) continue;
+#pragma unroll
+    for (int a = 0; a < 8; ++a) {
+      const int64_t i = i0 + (a < 4 ? 4 * gi + a : 64 + 4 * gi + (a - 4));
+      if (i >= n1) continue;
+      const float x = ldx<XT>(X + i + n1 * s);
+      const float df = x - xh[a][b];
+      d2 = fmaf(df, df, d2);
+      x2 = fmaf(x, x, x2);
+    }
+  }
+  double dd = d2, xx = x2;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    dd += __shfl_xor_sync(0xffffffffu, dd, o);
+    xx += __shfl_xor_sync(0xffffffffu, xx, o);
+  }
+  if ((tid & 31) == 0) {
+    red[0][tid >> 5] = dd;
+    red[1][tid >> 5] = xx;
+  }
+  __syncthreads();
+  if (tid == 0) {
+    double a = 0, b = 0;
+    for (int w = 0; w < 8; ++w) {
+      a += red[0][w];
+      b += red[1][w];
+    }
+    atomicAdd(acc, a);
+    atomicAdd(acc + 1, b);
+  }
+}
+
+}  // namespace
+
+void gemm_tn_f32(const float* A, int64_t lda, int64_t S, int K, const float* F, int64_t ldf,
+                 int L, float* out, int64_t ldo, bool accumulate) {
+  if (S <= 0 || L <= 0) return;
+  if (K <= 0) {
+    if (!accumulate)
+      for (int k = 0; k < L; ++k)
+        KRP_CUDA_CHECK(cudaMemsetAsync(out + ldo * k, 0, sizeof(float) * S, stream()));
+    return;
+  }
+  if (L <= 16)
+    gemm_tn_launch<16>(A, lda, S, K, F, ldf, L, out, ldo, accumulate);
+  else if (L <= 32)
+    gemm_tn_launch<32>(A, lda, S, K, F, ldf, L, out, ldo, accumulate);
+  else if (L <= 48)
+    gemm_tn_launch<48>(A, lda, S, K, F, ldf, L, out, ldo, accumulate);
+  else
+    gemm_tn_launch<64>(A, lda, S, K, F, ldf, L, out, ldo, accumulate);
+}
+
+void mttkrp_first_f32(const float* A, int64_t n1, int64_t S, const Radix& rest, int L, float* Y) {
+  KRP_CUDA_CHECK(cudaMemsetAsync(Y, 0, sizeof(float) * n1 * L, stream()));
+  if (S <= 0) return;
+  RadixDev R{};
+  R.n = rest.n;
+  for (int j = 0; j < rest.n; ++j) {
+    R.radix[j] = rest.radix[j];
+    R.V[j] = rest.V[j];
+  }
+  if (L <= 16)
+    mttkrp_first_launch<16>(A, n1, S, R, L, Y);
+  else if (L <= 32)
+    mttkrp_first_launch<32>(A, n1, S, R, L, Y);
+  else if (L <= 48)
+    mttkrp_first_launch<48>(A, n1, S, R, L, Y);
+  else
+    mttkrp_first_launch<64>(A, n1, S, R, L, Y);
+}
+
+void diag_contract_f32(const float* T, int D, const int64_t* m, int64_t tk, int n,
+                       const float* const* V, int L, float* Y) {
+  DiagDev P{};
+  P.D = D;
+  int64_t total = 1;
+  for (int j = 0; j < D; ++j) {
+    P.m[j] = m[j];
+    P.V[j] = V[j];
+    total *= m[j];
+  }
+  KRP_CUDA_CHECK(cudaMemsetAsync(Y, 0, sizeof(float) * m[n] * L, stream()));
+  if (total == 0) return;
+  if (n == 0) {
+    const int64_t S = total / m[0];
+    const int threads = 256;
+    const int bx = (int)((m[0] + threads - 1) / threads);
+    const int want = 4 * current()->num_sms;
+    int64_t splits = std::max<int64_t>(1, want / std::max(1, bx * L));
+    int64_t per = std::max<int64_t>(256, (S + splits - 1) / splits);
+    splits = (S + per - 1) / per;
+    dim3 grid(bx, L, (unsigned)splits);
+    diag_first_kernel<<<grid, threads, 0, stream()>>>(T, P, tk, L, Y, per);
+    check_launch("diag_first_f32");
+  } else {
+    int64_t nrows = m[n];
+    for (int j = n + 1; j < D; ++j) nrows *= m[j];
+    const int threads = 256;
+    const int64_t blocks = std::min<int64_t>((nrows * 32 + threads - 1) / threads, 2048);
+    dim3 grid((unsigned)std::max<int64_t>(1, blocks), L);
+    diag_mid_kernel<<<grid, threads, 0, stream()>>>(T, P, tk, n, L, Y);
+    check_launch("diag_mid_f32");
+  }
+}
+
+void cast_f64_to_f32(const double* src, float* dst, int64_t n) {
+  if (n <= 0) return;
+  cast_f64_f32_kernel<<<grid_for(n, 256), 256, 0, stream()>>>(src, dst, n);
+  check_launch("cast_f64_f32");
+}
+void cast_f32_to_f64(const float* src, double* dst, int64_t n) {
+  if (n <= 0) return;
+  cast_f32_f64_kernel<<<grid_for(n, 256), 256, 0, stream()>>>(src, dst, n);
+  check_launch("cast_f32_f64");
+}
+void transpose_f64_to_f32(const double* src, int64_t rows, int64_t cols, float* dst) {
+  if (rows * cols <= 0) return;
+  transpose_f64_f32_kernel<<<grid_for(rows * cols, 256), 256, 0, stream()>>>(src, rows, cols, dst);
+  check_launch("transpose_f64_f32");
+}
+void rotate_first_to_last_f32(const float* src, int64_t m0, int64_t rest, float* dst) {
+  if (m0 * rest <= 0) return;
+  rotate_kernel<<<grid_for(m0 * rest, 256), 256, 0, stream()>>>(src, m0, rest, dst);
+  check_launch("rotate_f32");
+}
+
+void residual_f32(const void* X, krp_dtype xt, int64_t n1, int64_t S, const float* Q1, int l,
+                  const float* H, double* acc) {
+  if (n1 <= 0 || S <= 0) return;
+  dim3 grid((unsigned)((S + TM - 1) / TM), (unsigned)((n1 + TM - 1) / TM));
+  if (xt == KRP_F32)
+    residual_kernel<float><<<grid, 256, 0, stream()>>>(static_cast<const float*>(X), n1, S, Q1,
+                                                       l, H, acc);
+  else
+    residual_kernel<__nv_bfloat16><<<grid, 256, 0, stream()>>>(
+        static_cast<const __nv_bfloat16*>(X), n1, S, Q1, l, H, acc);
+  check_launch("residual");
+}
+
+}  // namespace krp

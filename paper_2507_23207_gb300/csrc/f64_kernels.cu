@@ -1,0 +1,435 @@
+// FP64 stages: thin QR of every sketch (Alg. 1 step 3, used by Alg. 6-8), the
+// HOSVD of the small core used for rank truncation, and helpers.
+#include <algorithm>
+
+#include "common.cuh"
+
+namespace krp {
+namespace {
+
+constexpr int kQrThreads = 512;
+constexpr int kQrMaxL = 256;
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Householder QR of one m x l matrix per CTA.  Reflector j: x = A[j:, j],
+// alpha = -sign(x_0)||x||, v = x - alpha e_1 (stored over column j),
+// ||v||^2 = 2||x||(||x|| + |x_0|), A[j:, k] -= (2/||v||^2) v (v^T A[j:, k]) with
+// v^T A[j:, k] = x^T A[j:, k] - alpha A[j, k] (one fused reduction per step).
+// Q is formed by applying the reflectors in reverse order to [I; 0]; then the
+// signs are fixed so that diag(R) >= 0.
+__global__ void __launch_bounds__(kQrThreads) qr_kernel(const QrJob* __restrict__ jobs,
+                                                        int* status) {
+  const QrJob job = jobs[blockIdx.x];
+  const int64_t m = job.m;
+  const int l = job.l;
+  double* A = job.work;
+  __shared__ double w[kQrMaxL];
+  __shared__ double tau[kQrMaxL];
+  __shared__ double alph[kQrMaxL];
+  __shared__ int bad;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
+  if (tid == 0) bad = 0;
+  __syncthreads();
+  for (int64_t e = tid; e < m * l; e += blockDim.x) {
+    const double v = job.Y64 ? job.Y64[e] : (double)job.Y[e];
+    if (!isfinite(v)) bad = 1;
+    A[e] = v;
+  }
+  __syncthreads();
+  if (bad) {
+    if (tid == 0) atomicExch(status, (int)KRP_ENUMERIC);
+    return;
+  }
+  for (int j = 0; j < l; ++j) {
+    const double* aj = A + m * j;
+    for (int k = j + warp; k < l; k += nwarps) {
+      const double* ak = A + m * k;
+      double part = 0.0;
+      for (int64_t r = j + lane; r < m; r += 32) part = fma(aj[r], ak[r], part);
+      part = warp_sum(part);
+      if (lane == 0) w[k] = part;
+    }
+    __syncthreads();
+    if (tid == 0) {
+      const double normx = sqrt(w[j]);
+      const double x0 = A[j + m * j];
+      if (normx == 0.0) {
+        alph[j] = 0.0;
+        tau[j] = 0.0;
+        for (int k = j + 1; k < l; ++k) w[k] = 0.0;
+        A[j + m * j] = 0.0;
+      } else {
+        const double alpha = (x0 >= 0.0) ? -normx : normx;
+        const double vtv = 2.0 * normx * (normx + fabs(x0));
+        const double t = 2.0 / vtv;
+        alph[j] = alpha;
+        tau[j] = t;
+        for (int k = j + 1; k < l; ++k) w[k] = t * (w[k] - alpha * A[j + m * k]);
+        A[j + m * j] = x0 - alpha;  // v_0
+      }
+    }
+    __syncthreads();
+    const int64_t rows = m - j;
+    const int cols = l - j - 1;
+    for (int64_t e = tid; e < rows * cols; e += blockDim.x) {
+      const int64_t r = j + e % rows;
+      const int k = j + 1 + (int)(e / rows);
+      A[r + m * k] -= A[r + m * j] * w[k];
+    }
+    __syncthreads();
+  }
+  // R (upper triangle) before A's columns are reused
+  if (job.R) {
+    for (int e = tid; e < l * l; e += blockDim.x) {
+      const int r = e % l, c = e / l;
+      double v = 0.0;
+      if (r < c) v = A[r + m * c];
+      if (r == c) v = alph[r];
+      job.R[e] = v;
+    }
+  }
+  double* Q = job.Q;
+  for (int64_t e = tid; e < m * l; e += blockDim.x) {
+    const int64_t r = e % m;
+    const int64_t c = e / m;
+    Q[e] = (r == c) ? 1.0 : 0.0;
+  }
+  __syncthreads();
+  for (int j = l - 1; j >= 0; --j) {
+    const double* v = A + m * j;  // v_r for r >= j
+    for (int c = j + warp; c < l; c += nwarps) {
+      const double* qc = Q + m * c;
+      double part = 0.0;
+      for (int64_t r = j + lane; r < m; r += 32) part = fma(v[r], qc[r], part);
+      part = warp_sum(part);
+      if (lane == 0) w[c] = tau[j] * part;
+    }
+    __syncthreads();
+    const int64_t rows = m - j;
+    const int cols = l - j;
+    for (int64_t e = tid; e < rows * cols; e += blockDim.x) {
+      const int64_t r = j + e % rows;
+      const int c = j + (int)(e / rows);
+      Q[r + m * c] -= v[r] * w[c];
+    }
+    __syncthreads();
+  }
+  // diag(R) >= 0
+  for (int64_t e = tid; e < m * l; e += blockDim.x) {
+    const int c = (int)(e / m);
+    if (alph[c] < 0.0) Q[e] = -Q[e];
+  }
+  if (job.R) {
+    __syncthreads();
+    for (int e = tid; e < l * l; e += blockDim.x) {
+      const int r = e % l;
+      if (alph[r] < 0.0) job.R[e] = -job.R[e];
+    }
+  }
+}
+
+// S[a + l*b] += sum over the CTA's columns of G_(mode)[a, col] G_(mode)[b, col]
+__global__ void gram_kernel(const double* __restrict__ G, int64_t P, int64_t l, int64_t ncols,
+                            int64_t cols_per_cta, double* __restrict__ S) {
+  extern __shared__ double colbuf[];  // 32 columns x l
+  const int64_t c0 = (int64_t)blockIdx.x * cols_per_cta;
+  const int64_t c1 = min(ncols, c0 + cols_per_cta);
+  const int64_t pairs = l * l;
+  double acc[16];
+  for (int q = 0; q < 16; ++q) acc[q] = 0.0;
+  for (int64_t cc = c0; cc < c1; cc += 32) {
+    const int nc = (int)((c1 - cc) < 32 ? (c1 - cc) : 32);
+    __syncthreads();
+    for (int64_t e = threadIdx.x; e < nc * l; e += blockDim.x) {
+      const int64_t a = e % l, c = cc + e / l;
+      const int64_t p = c % P, s = c / P;
+      colbuf[e] = G[p + P * a + P * l * s];
+    }
+    __syncthreads();
+    for (int q = 0; q < 16; ++q) {
+      const int64_t pr = threadIdx.x + (int64_t)q * blockDim.x;
+      if (pr >= pairs) break;
+      const int64_t a = pr % l, b = pr / l;
+      double s = acc[q];
+      for (int c = 0; c < nc; ++c) s = fma(colbuf[a + l * c], colbuf[b + l * c], s);
+      acc[q] = s;
+    }
+  }
+  for (int q = 0; q < 16; ++q) {
+    const int64_t pr = threadIdx.x + (int64_t)q * blockDim.x;
+    if (pr >= pairs) break;
+    atomicAdd(S + pr, acc[q]);
+  }
+}
+
+constexpr int kEigMaxL = 64;
+
+struct EigJob {
+  const double* S;
+  double* U;
+  double* ev;  // sorted eigenvalues (l), may be null
+  int l, r;
+};
+
+// Cyclic Jacobi eigensolver for one symmetric l x l matrix per CTA (l <= 64),
+// parallel (round-robin) pair ordering: every round rotates l/2 disjoint
+// pairs, first updating columns (S J, V J) and then rows (J^T S).
+__global__ void __launch_bounds__(256) eig_kernel(const EigJob* __restrict__ jobs, int* status) {
+  const EigJob job = jobs[blockIdx.x];
+  const int l = job.l;
+  const int n = (l + 1) & ~1;  // padded to even for the tournament
+  extern __shared__ double eig_smem[];
+  double(*S)[kEigMaxL + 1] = reinterpret_cast<double(*)[kEigMaxL + 1]>(eig_smem);
+  double(*V)[kEigMaxL + 1] =
+      reinterpret_cast<double(*)[kEigMaxL + 1]>(eig_smem + kEigMaxL * (kEigMaxL + 1));
+  __shared__ double cs[kEigMaxL / 2], sn[kEigMaxL / 2];
+  __shared__ int pp[kEigMaxL / 2], qq[kEigMaxL / 2];
+  __shared__ int order[kEigMaxL];
+  __shared__ double offn, diagn;
+  __shared__ int ring[kEigMaxL];
+  const int tid = threadIdx.x;
+  for (int e = tid; e < n * n; e += blockDim.x) {
+    const int r = e % n, c = e / n;
+    S[r][c] = (r < l && c < l) ? job.S[r + l * c] : 0.0;
+    V[r][c] = (r == c) ? 1.0 : 0.0;
+  }
+  for (int i = tid; i < n; i += blockDim.x) ring[i] = i;
+  __syncthreads();
+  for (int sweep = 0; sweep < 40; ++sweep) {
+    if (tid == 0) {
+      double o = 0.0, dg = 0.0;
+      for (int r = 0; r < n; ++r)
+        for (int c = 0; c < n; ++c) {
+          if (r == c)
+            dg += S[r][c] * S[r][c];
+          else
+            o += S[r][c] * S[r][c];
+        }
+      offn = o;
+      diagn = dg;
+    }
+    __syncthreads();
+    if (!(offn > 1e-30 * diagn) || offn == 0.0) break;
+    for (int round = 0; round < n - 1; ++round) {
+      // pairs of this round: ring[i] with ring[n-1-i]
+      if (tid < n / 2) {
+        int p = ring[tid], q = ring[n - 1 - tid];
+        if (p > q) {
+          const int t = p;
+          p = q;
+          q = t;
+        }
+        pp[tid] = p;
+        qq[tid] = q;
+        const double apq = S[p][q];
+        double c = 1.0, s = 0.0;
+        if (apq != 0.0) {
+          const double app = S[p][p], aqq = S[q][q];
+          const double theta = (aqq - app) / (2.0 * apq);
+          const double t = (theta >= 0.0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(1.0 + theta * theta));
+          c = 1.0 / sqrt(1.0 + t * t);
+          s = t * c;
+        }
+        cs[tid] = c;
+        sn[tid] = s;
+      }
+      __syncthreads();
+      // columns: S <- S J, V <- V J   (J rotates columns p, q)
+      for (int e = tid; e < (n / 2) * n; e += blockDim.x) {
+        const int k = e % (n / 2), r = e / (n / 2);
+        const int p = pp[k], q = qq[k];
+        const double c = cs[k], s = sn[k];
+        const double sp = S[r][p], sq = S[r][q];
+        S[r][p] = c * sp - s * sq;
+        S[r][q] = s * sp + c * sq;
+        const double vp = V[r][p], vq = V[r][q];
+        V[r][p] = c * vp - s * vq;
+        V[r][q] = s * vp + c * vq;
+      }
+      __syncthreads();
+      // rows: S <- J^T S
+      for (int e = tid; e < (n / 2) * n; e += blockDim.x) {
+        const int k = e % (n / 2), col = e / (n / 2);
+        const int p = pp[k], q = qq[k];
+        const double c = cs[k], s = sn[k];
+        const double sp = S[p][col], sq = S[q][col];
+        S[p][col] = c * sp - s * sq;
+        S[q][col] = s * sp + c * sq;
+      }
+      __syncthreads();
+      if (tid == 0) {  // rotate the ring, keeping element 0 fixed
+        const int last = ring[n - 1];
+        for (int i = n - 1; i > 1; --i) ring[i] = ring[i - 1];
+        ring[1] = last;
+      }
+      __syncthreads();
+    }
+  }
+  if (tid == 0) {
+    for (int i = 0; i < l; ++i) order[i] = i;
+    for (int i = 1; i < l; ++i) {  // insertion sort, descending eigenvalue
+      const int key = order[i];
+      int j = i - 1;
+      while (j >= 0 && S[order[j]][order[j]] < S[key][key]) {
+        order[j + 1] = order[j];
+        --j;
+      }
+      order[j + 1] = key;
+    }
+    bool ok = true;
+    for (int i = 0; i < l; ++i) ok = ok && isfinite(S[i][i]);
+    if (!ok) atomicExch(status, (int)KRP_ENUMERIC);
+  }
+  __syncthreads();
+  for (int e = tid; e < l * job.r; e += blockDim.x) {
+    const int r = e % l, c = e / l;
+    job.U[e] = V[r][order[c]];
+  }
+  if (job.ev)
+    for (int i = tid; i < l; i += blockDim.x) job.ev[i] = S[order[i]][order[i]];
+}
+
+// out = G x_mode U^T: out[p + P*a + P*r*s] = sum_i G[p + P*i + P*n*s] U[i + n*a]
+__global__ void ttm_small_kernel(const double* __restrict__ G, int64_t P, int64_t n, int64_t Sfx,
+                                 const double* __restrict__ U, int r, double* __restrict__ out) {
+  const int64_t total = P * r * Sfx;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t p = e % P;
+    const int64_t a = (e / P) % r;
+    const int64_t s = e / (P * r);
+    double acc = 0.0;
+    const double* g = G + p + P * n * s;
+    for (int64_t i = 0; i < n; ++i) acc = fma(g[P * i], U[i + n * a], acc);
+    out[e] = acc;
+  }
+}
+
+__global__ void matmul_kernel(const double* __restrict__ A, const double* __restrict__ B,
+                              double* __restrict__ C, int64_t m, int k, int n) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < m * n;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = e % m, j = e / m;
+    double acc = 0.0;
+    for (int t = 0; t < k; ++t) acc = fma(A[i + m * t], B[t + (int64_t)k * j], acc);
+    C[e] = acc;
+  }
+}
+
+__global__ void sumsq_kernel(const double* __restrict__ x, int64_t n, double* out) {
+  double acc = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    acc = fma(x[i], x[i], acc);
+  acc = warp_sum(acc);
+  if ((threadIdx.x & 31) == 0) atomicAdd(out, acc);
+}
+
+__global__ void finite_kernel(const double* __restrict__ x, int64_t n, int* status) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    if (!isfinite(x[i])) atomicExch(status, (int)KRP_ENUMERIC);
+}
+
+int grid_for(int64_t n, int threads, int cap = 8192) {
+  int64_t g = (n + threads - 1) / threads;
+  return (int)std::max<int64_t>(1, std::min<int64_t>(g, cap));
+}
+
+}  // namespace
+
+void qr_householder_f64(const QrJob* jobs, int count, int* status) {
+  if (count <= 0) return;
+  for (int b = 0; b < count; ++b) {
+    KRP_REQUIRE(jobs[b].m >= jobs[b].l && jobs[b].l >= 1, "QR needs m >= l >= 1 (m=%lld l=%d)",
+                (long long)jobs[b].m, jobs[b].l);
+    KRP_REQUIRE(jobs[b].l <= kQrMaxL, "QR supports l <= %d", kQrMaxL);
+  }
+  Ctx* c = current();
+  QrJob* d_jobs = c->ws.take<QrJob>(count);
+  KRP_CUDA_CHECK(cudaMemcpyAsync(d_jobs, jobs, sizeof(QrJob) * count, cudaMemcpyHostToDevice,
+                                 stream()));
+  qr_kernel<<<count, kQrThreads, 0, stream()>>>(d_jobs, status);
+  check_launch("qr_householder_f64");
+}
+
+void gram_mode_f64(const double* G, int D, const int64_t* dims, int mode, double* S) {
+  int64_t P = 1, Sfx = 1;
+  for (int j = 0; j < mode; ++j) P *= dims[j];
+  for (int j = mode + 1; j < D; ++j) Sfx *= dims[j];
+  const int64_t l = dims[mode];
+  const int64_t ncols = P * Sfx;
+  KRP_REQUIRE(l <= kEigMaxL, "core truncation supports ranks l <= %d", kEigMaxL);
+  KRP_CUDA_CHECK(cudaMemsetAsync(S, 0, sizeof(double) * l * l, stream()));
+  const int threads = 256;
+  const int want = 2 * current()->num_sms;
+  int64_t per = std::max<int64_t>(32, (ncols + want - 1) / want);
+  const int blocks = (int)((ncols + per - 1) / per);
+  gram_kernel<<<blocks, threads, sizeof(double) * 32 * l, stream()>>>(G, P, l, ncols, per, S);
+  check_launch("gram_f64");
+}
+
+void sym_eig_top_f64(const double* const* S, const int* l, const int* r, double* const* U,
+                     int count, int* status, double* const* evals) {
+  if (count <= 0) return;
+  std::vector<EigJob> jobs(count);
+  for (int b = 0; b < count; ++b) {
+    KRP_REQUIRE(l[b] >= 1 && l[b] <= kEigMaxL && r[b] >= 1 && r[b] <= l[b],
+                "eigensolver needs 1 <= r <= l <= %d", kEigMaxL);
+    jobs[b] = EigJob{S[b], U[b], evals ? evals[b] : nullptr, l[b], r[b]};
+  }
+  EigJob* d_jobs = current()->ws.take<EigJob>(count);
+  KRP_CUDA_CHECK(cudaMemcpyAsync(d_jobs, jobs.data(), sizeof(EigJob) * count,
+                                 cudaMemcpyHostToDevice, stream()));
+  const size_t smem = 2 * sizeof(double) * kEigMaxL * (kEigMaxL + 1);
+  static bool attr_set = false;
+  if (!attr_set) {
+    KRP_CUDA_CHECK(cudaFuncSetAttribute(eig_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)smem));
+    attr_set = true;
+  }
+  eig_kernel<<<count, 256, smem, stream()>>>(d_jobs, status);
+  check_launch("jacobi_eig_f64");
+}
+
+void ttm_small_f64(const double* G, int D, const int64_t* dims, int mode, const double* U, int r,
+                   double* out) {
+  int64_t P = 1, Sfx = 1;
+  for (int j = 0; j < mode; ++j) P *= dims[j];
+  for (int j = mode + 1; j < D; ++j) Sfx *= dims[j];
+  const int64_t total = P * r * Sfx;
+  if (total <= 0) return;
+  ttm_small_kernel<<<grid_for(total, 256), 256, 0, stream()>>>(G, P, dims[mode], Sfx, U, r, out);
+  check_launch("ttm_small_f64");
+}
+
+void matmul_f64(const double* A, const double* B, double* C, int64_t m, int k, int n) {
+  if (m * n <= 0) return;
+  matmul_kernel<<<grid_for(m * n, 256), 256, 0, stream()>>>(A, B, C, m, k, n);
+  check_launch("matmul_f64");
+}
+
+double sum_squares_f64_sync(const double* x, int64_t n, double* scratch) {
+  KRP_CUDA_CHECK(cudaMemsetAsync(scratch, 0, sizeof(double), stream()));
+  if (n > 0) {
+    sumsq_kernel<<<grid_for(n, 256, 1024), 256, 0, stream()>>>(x, n, scratch);
+    check_launch("sumsq_f64");
+  }
+  double h = 0.0;
+  KRP_CUDA_CHECK(cudaMemcpyAsync(&h, scratch, sizeof(double), cudaMemcpyDeviceToHost, stream()));
+  KRP_CUDA_CHECK(cudaStreamSynchronize(stream()));
+  return h;
+}
+
+void check_finite_f64(const double* x, int64_t n, int* status) {
+  if (n <= 0) return;
+  finite_kernel<<<grid_for(n, 256, 1024), 256, 0, stream()>>>(x, n, status);
+  check_launch("finite_f64");
+}
+
+}  // namespace krp

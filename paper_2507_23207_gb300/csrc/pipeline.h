@@ -1,0 +1,69 @@
+// Internal: pipelines built from the kernels (not part of the C ABI).
+#pragma once
+
+#include "common.cuh"
+
+namespace krp {
+
+bool is_device_ptr(const void* p);
+size_t dtype_size(krp_dtype t);
+int64_t checked_numel(int d, const int64_t* dims);
+// Synchronise the stream, read and clear the device status word; fail on error.
+void raise_device_status(Ctx* c);
+
+struct SketchArgs {
+  const void* X;
+  krp_dtype xt;
+  int d;
+  int64_t dims[KRP_MAXD];
+  const void* omega[KRP_MAXD];
+  krp_dtype omt;
+  int ell;
+  int64_t N;
+};
+SketchArgs validate_sketch(const void* X, krp_dtype xt, int d, const int64_t* dims,
+                           const void* const* omega, krp_dtype omt, int ell);
+size_t sketch_workspace_bytes(const SketchArgs& a, bool all_modes);
+void sketch_one_mode(const SketchArgs& a, int n, float* Y);
+void sketch_all_modes(const SketchArgs& a, float* const* Y);
+
+size_t multi_ttm_workspace_bytes(int d, const int64_t* dims, const int* cols, krp_dtype xt);
+void multi_ttm(const void* X, krp_dtype xt, int d, const int64_t* dims, const double* const* Q,
+               const int* cols, float* G);
+
+void tucker_pipeline(bool sequential, const void* X, krp_dtype xt, int d, const int64_t* dims,
+                     const int* ranks, int oversample, uint64_t seed, unsigned flags,
+                     krp_tucker_out* out);
+
+void hankel_pipeline(const void* blocks, krp_dtype bt, int m, int n, int s, int r, int ell_r,
+                     int ell_l, uint64_t seed, double* U, double* S, double* V);
+void hankel_sketch_only(const void* blocks, krp_dtype bt, int m, int n, int s,
+                        const void* omega1, const void* omega2, int ell_r, const void* psi1,
+                        const void* psi2, int ell_l, float* Y, float* Z);
+
+// Contractions over the big tensor, dispatched on its element type:
+// FP32 -> CUDA-core kernels, BF16 -> tcgen05 tensor-core kernels.
+//   out[s + S*k] = sum_{i < n1} X[i + n1*s] F[i + n1*k],  S = N / n1
+// F is given in FP32 (Ff) and, for BF16 X, as a bf16 hi/lo pair (Fhi, Flo;
+// Flo may be null).
+void big_gemm_tn(const void* X, krp_dtype xt, int64_t n1, int64_t S, const float* Ff,
+                 const __nv_bfloat16* Fhi, const __nv_bfloat16* Flo, int L, float* out);
+//   Y[i + n1*k] = sum_s X[i + n1*s] prod_j V_j[digit_j(s), k] over the modes
+//   2..d (rest), with V_j FP32 (F32 X) or BF16 (BF16 X).
+void big_mttkrp_first(const void* X, krp_dtype xt, int64_t n1, int d_rest,
+                      const int64_t* rest_dims, const void* const* rest_V, int L, float* Y);
+
+// tcgen05 kernels (tc_kernels.cu)
+void tc_gemm_tn_bf16(const __nv_bfloat16* X, int64_t n1, int64_t S, const __nv_bfloat16* Fhi,
+                     const __nv_bfloat16* Flo, int L, float* out);
+// Y[i + n1*k] = sum_t w[t + T*k] sum_{i2} X[i + n1*(i2 + n2*t)] Om2[i2 + n2*k]
+void tc_mttkrp_first_bf16(const __nv_bfloat16* X, int64_t n1, int64_t n2, int64_t T,
+                          const __nv_bfloat16* Om2, const float* w, int L, float* Y);
+size_t tc_workspace_bytes(int64_t n1, int64_t S, int L);
+
+// weights w[t + T*k] = prod_j V_j[digit_j(t) + r_j*k] (bf16 or f32 factors)
+void krp_rows(const Radix& R, int64_t T, int L, bool bf16, float* w);
+void split_bf16_hilo(const double* src, int64_t n, __nv_bfloat16* hi, __nv_bfloat16* lo);
+void convert_bf16_to_f32(const __nv_bfloat16* src, float* dst, int64_t n);
+
+}  // namespace krp

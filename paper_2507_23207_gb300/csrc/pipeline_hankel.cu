@@ -1,0 +1,221 @@
+// Alg. 6: single-pass randomized SVD of a block Hankel matrix with KRP
+// sketches.  Sketches (a9) on CUDA cores in FP32; post-processing (a10) in FP64:
+//   Y = Q R (Householder);  P = Psi^T Q computed structurally,
+//   P[c, :] = sum_{i,a} Psi1[i, c] Psi2[a, c] Q[(i,a), :];
+//   W = P^+ Z^T by Householder least squares (P = Qp Rp, W = Rp^{-1} Qp^T Z^T);
+//   W = U_W S V^T through the eigen-decomposition of W W^T (Jacobi);
+//   U = Q U_W, V = W^T U_W S^{-1}.
+#include <cmath>
+
+#include "pipeline.h"
+
+namespace krp {
+namespace {
+
+template <class T>
+__device__ __forceinline__ double ldd(const T* p, int64_t i);
+template <>
+__device__ __forceinline__ double ldd<float>(const float* p, int64_t i) { return p[i]; }
+template <>
+__device__ __forceinline__ double ldd<__nv_bfloat16>(const __nv_bfloat16* p, int64_t i) {
+  return __bfloat162float(p[i]);
+}
+
+// P[c + ll*q] = sum_{i<s, a<m} psi1[i + s*c] psi2[a + m*c] Q[(a + m*i) + ms*q]
+template <class T>
+__global__ void psi_t_q_kernel(const T* __restrict__ psi1, const T* __restrict__ psi2, int s,
+                               int m, int ll, const double* __restrict__ Q, int lr,
+                               double* __restrict__ P) {
+  const int c = blockIdx.x, q = blockIdx.y;
+  const int64_t ms = (int64_t)m * s;
+  double acc = 0.0;
+  for (int64_t row = threadIdx.x; row < ms; row += blockDim.x) {
+    const int a = (int)(row % m), i = (int)(row / m);
+    acc = fma(ldd(psi1, i + (int64_t)s * c) * ldd(psi2, a + (int64_t)m * c), Q[row + ms * q], acc);
+  }
+  __shared__ double red[32];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+    P[c + (int64_t)ll * q] = t;
+  }
+}
+
+// W[q + lr*col] = (Rp^{-1} Qp^T Z^T)[q, col]; one thread per column col < ns.
+__global__ void ls_solve_kernel(const double* __restrict__ Qp, const double* __restrict__ Rp,
+                                const float* __restrict__ Z, int64_t ns, int ll, int lr,
+                                double* __restrict__ W) {
+  for (int64_t col = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; col < ns;
+       col += (int64_t)gridDim.x * blockDim.x) {
+    double* w = W + (int64_t)lr * col;
+    for (int q = 0; q < lr; ++q) {  // rhs = Qp^T z, z = Z[col, :]
+      double acc = 0.0;
+      for (int c = 0; c < ll; ++c) acc = fma(Qp[c + (int64_t)ll * q], (double)Z[col + ns * c], acc);
+      w[q] = acc;
+    }
+    for (int q = lr - 1; q >= 0; --q) {  // back substitution with Rp
+      double acc = w[q];
+      for (int t = q + 1; t < lr; ++t) acc -= Rp[q + (int64_t)lr * t] * w[t];
+      w[q] = acc / Rp[q + (int64_t)lr * q];
+    }
+  }
+}
+
+// V[col + ns*j] = sum_q W[q + lr*col] Uw[q + lr*j] / sigma_j ; S[j] = sigma_j
+__global__ void right_vectors_kernel(const double* __restrict__ W, int64_t ns, int lr,
+                                     const double* __restrict__ Uw, const double* __restrict__ ev,
+                                     int r, double* __restrict__ V, double* __restrict__ S) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < ns * r;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t col = e % ns;
+    const int j = (int)(e / ns);
+    const double sig = sqrt(fmax(ev[j], 0.0));
+    double acc = 0.0;
+    for (int q = 0; q < lr; ++q) acc = fma(W[q + (int64_t)lr * col], Uw[q + (int64_t)lr * j], acc);
+    V[e] = sig > 0.0 ? acc / sig : 0.0;
+    if (col == 0) S[j] = sig;
+  }
+}
+
+int grid_for(int64_t n) {
+  int64_t g = (n + 255) / 256;
+  return (int)(g < 1 ? 1 : (g > 8192 ? 8192 : g));
+}
+
+void validate_hankel(const void* blocks, krp_dtype bt, int m, int n, int s) {
+  KRP_REQUIRE(blocks, "blocks is NULL");
+  KRP_REQUIRE(bt == KRP_F32 || bt == KRP_BF16, "blocks dtype must be KRP_F32 or KRP_BF16");
+  KRP_REQUIRE(m >= 1 && n >= 1 && s >= 1, "m, n, s must be >= 1");
+  KRP_REQUIRE((int64_t)m * s <= (int64_t(1) << 31) && (int64_t)n * s <= (int64_t(1) << 31),
+              "block Hankel too large");
+}
+
+}  // namespace
+
+void hankel_sketch_only(const void* blocks, krp_dtype bt, int m, int n, int s, const void* omega1,
+                        const void* omega2, int ell_r, const void* psi1, const void* psi2,
+                        int ell_l, float* Y, float* Z) {
+  validate_hankel(blocks, bt, m, n, s);
+  KRP_REQUIRE(ell_r >= 1 && ell_l >= 0, "sketch sizes out of range");
+  const int nb = 2 * s - 1;
+  const int64_t zs = (int64_t)std::max(m, n) * std::max(ell_r, ell_l) * nb;
+  ensure_workspace(current(), ws_bytes(zs, 4) + (1 << 20));
+  float* Zs = current()->ws.take<float>(zs);
+  if (Y) {
+    KRP_REQUIRE(omega1 && omega2, "omega1/omega2 is NULL");
+    hankel_sketch(blocks, bt, m, n, s, omega1, omega2, ell_r, false, Y, Zs);
+  }
+  if (Z && ell_l > 0) {
+    KRP_REQUIRE(psi1 && psi2, "psi1/psi2 is NULL");
+    hankel_sketch(blocks, bt, m, n, s, psi1, psi2, ell_l, true, Z, Zs);
+  }
+}
+
+void hankel_pipeline(const void* blocks, krp_dtype bt, int m, int n, int s, int r, int ell_r,
+                     int ell_l, uint64_t seed, double* U, double* S, double* V) {
+  Ctx* c = current();
+  validate_hankel(blocks, bt, m, n, s);
+  if (ell_l == 0) ell_l = (int)std::ceil(1.5 * ell_r);
+  const int64_t ms = (int64_t)m * s, ns = (int64_t)n * s;
+  KRP_REQUIRE(r >= 1 && r <= ell_r && ell_r <= ell_l, "need 1 <= r <= ell_r <= ell_l");
+  KRP_REQUIRE(ell_r <= 64 && ell_l <= 256, "need ell_r <= 64 and ell_l <= 256");
+  KRP_REQUIRE(ell_r <= ms && ell_l <= ns && ell_r <= ell_l, "sketch sizes exceed the matrix");
+  KRP_REQUIRE(U && S && V, "U/S/V is NULL");
+  const int nb = 2 * s - 1;
+  const size_t eb = dtype_size(bt);
+  const bool b_dev = is_device_ptr(blocks);
+  size_t need = ws_bytes((size_t)m * n * nb, eb);
+  need += ws_bytes((size_t)std::max(m, n) * ell_l * nb, 4);
+  need += 2 * ws_bytes((size_t)s * ell_l, eb) + 2 * ws_bytes((size_t)std::max(m, n) * ell_l, eb);
+  need += ws_bytes((size_t)ms * ell_r, 4) + ws_bytes((size_t)ns * ell_l, 4);
+  need += 3 * ws_bytes((size_t)ms * ell_r, 8) + 4 * ws_bytes((size_t)ell_l * ell_r, 8);
+  need += ws_bytes((size_t)ell_r * ns, 8) + 4 * ws_bytes((size_t)ell_r * ell_r, 8);
+  need += ws_bytes((size_t)ms * r, 8) + ws_bytes((size_t)ns * r, 8) + ws_bytes(r, 8);
+  need += 1 << 20;
+  ensure_workspace(c, need);
+  Workspace& ws = c->ws;
+  KRP_CUDA_CHECK(cudaMemsetAsync(c->d_status, 0, sizeof(int), c->stream));
+
+  const void* Bd = blocks;
+  if (!b_dev) {
+    void* p = ws.take<char>((size_t)m * n * nb * eb);
+    KRP_CUDA_CHECK(cudaMemcpyAsync(p, blocks, (size_t)m * n * nb * eb, cudaMemcpyHostToDevice,
+                                   c->stream));
+    Bd = p;
+  }
+  float* Zs = ws.take<float>((size_t)std::max(m, n) * ell_l * nb);
+  void* o1 = ws.take<char>((size_t)s * ell_r * eb);
+  void* o2 = ws.take<char>((size_t)n * ell_r * eb);
+  void* p1 = ws.take<char>((size_t)s * ell_l * eb);
+  void* p2 = ws.take<char>((size_t)m * ell_l * eb);
+  FactorJob jo[2] = {{o1, s, ((int64_t)s * ell_r + 3) / 4, 0}, {o2, n, ((int64_t)n * ell_r + 3) / 4, 1}};
+  launch_gen_factors(seed, 0, KRP_TAG_OMEGA, ell_r, bt, jo, 2);
+  FactorJob jp[2] = {{p1, s, ((int64_t)s * ell_l + 3) / 4, 0}, {p2, m, ((int64_t)m * ell_l + 3) / 4, 1}};
+  launch_gen_factors(seed, 0, KRP_TAG_PSI, ell_l, bt, jp, 2);
+
+  float* Y = ws.take<float>((size_t)ms * ell_r);
+  float* Z = ws.take<float>((size_t)ns * ell_l);
+  hankel_sketch(Bd, bt, m, n, s, o1, o2, ell_r, false, Y, Zs);
+  hankel_sketch(Bd, bt, m, n, s, p1, p2, ell_l, true, Z, Zs);
+
+  // QR of Y
+  double* Q = ws.take<double>((size_t)ms * ell_r);
+  double* qw = ws.take<double>((size_t)ms * ell_r);
+  QrJob jy{Y, Q, nullptr, qw, ms, ell_r};
+  qr_householder_f64(&jy, 1, c->d_status);
+  // P = Psi^T Q (structured)
+  double* P = ws.take<double>((size_t)ell_l * ell_r);
+  dim3 g(ell_l, ell_r);
+  if (bt == KRP_F32)
+    psi_t_q_kernel<float><<<g, 256, 0, c->stream>>>(static_cast<const float*>(p1),
+                                                    static_cast<const float*>(p2), s, m, ell_l, Q,
+                                                    ell_r, P);
+  else
+    psi_t_q_kernel<__nv_bfloat16><<<g, 256, 0, c->stream>>>(
+        static_cast<const __nv_bfloat16*>(p1), static_cast<const __nv_bfloat16*>(p2), s, m,
+        ell_l, Q, ell_r, P);
+  check_launch("hankel_psi_t_q");
+  // least squares W = P^+ Z^T
+  double* Qp = ws.take<double>((size_t)ell_l * ell_r);
+  double* Rp = ws.take<double>((size_t)ell_r * ell_r);
+  double* pw = ws.take<double>((size_t)ell_l * ell_r);
+  QrJob jpq{nullptr, Qp, Rp, pw, ell_l, ell_r};
+  jpq.Y64 = P;
+  qr_householder_f64(&jpq, 1, c->d_status);
+  double* W = ws.take<double>((size_t)ell_r * ns);
+  ls_solve_kernel<<<grid_for(ns), 256, 0, c->stream>>>(Qp, Rp, Z, ns, ell_l, ell_r, W);
+  check_launch("hankel_ls_solve");
+  // SVD of W via W W^T
+  double* Wg = ws.take<double>((size_t)ell_r * ell_r);
+  const int64_t wd[2] = {ell_r, ns};
+  gram_mode_f64(W, 2, wd, 0, Wg);
+  double* Uw = ws.take<double>((size_t)ell_r * ell_r);
+  double* ev = ws.take<double>((size_t)ell_r);
+  const double* Sarr[1] = {Wg};
+  double* Uarr[1] = {Uw};
+  double* Earr[1] = {ev};
+  int lv[1] = {ell_r}, rv[1] = {ell_r};
+  sym_eig_top_f64(Sarr, lv, rv, Uarr, 1, c->d_status, Earr);
+  double* Ud = ws.take<double>((size_t)ms * r);
+  double* Vd = ws.take<double>((size_t)ns * r);
+  double* Sd = ws.take<double>((size_t)r);
+  matmul_f64(Q, Uw, Ud, ms, ell_r, r);
+  right_vectors_kernel<<<grid_for(ns * r), 256, 0, c->stream>>>(W, ns, ell_r, Uw, ev, r, Vd, Sd);
+  check_launch("hankel_right_vectors");
+  auto out = [&](double* dst, const double* src, size_t count) {
+    const bool dev = is_device_ptr(dst);
+    KRP_CUDA_CHECK(cudaMemcpyAsync(dst, src, count * sizeof(double),
+                                   dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                                   c->stream));
+  };
+  out(U, Ud, (size_t)ms * r);
+  out(V, Vd, (size_t)ns * r);
+  out(S, Sd, (size_t)r);
+  raise_device_status(c);
+}
+
+}  // namespace krp

@@ -1,0 +1,584 @@
+// Randomized Tucker pipelines over the kernels:
+//   RHOSVD-KRP (Alg. 7), its memoized dimension-tree variant (Sec. 5.1),
+//   RSTHOSVD-KRP (Alg. 8), the multi-TTM core, FP64 core truncation and the
+//   streaming FP64-accumulated residual.
+//
+// Layout trick used throughout: every contraction acts on the first (fastest)
+// mode of the current tensor and appends the new index as the slowest mode,
+// Z(m_1, rest) -> Z'(rest, l).  After d such steps the modes are back in their
+// natural order, so the core comes out as (l_1, ..., l_d), mode-1 fastest,
+// and no explicit unfolding/permutation of the big tensor is ever made.
+#include <algorithm>
+#include <cstring>
+
+#include "pipeline.h"
+
+namespace krp {
+namespace {
+
+__global__ void krp_rows_kernel(int n, const int64_t* radix_unused, int64_t r0, int64_t r1,
+                                int64_t r2, int64_t r3, int64_t r4, int64_t r5, int64_t r6,
+                                const void* v0, const void* v1, const void* v2, const void* v3,
+                                const void* v4, const void* v5, const void* v6, int bf16,
+                                int64_t T, int L, float* __restrict__ w) {
+  const int64_t rad[7] = {r0, r1, r2, r3, r4, r5, r6};
+  const void* V[7] = {v0, v1, v2, v3, v4, v5, v6};
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < T * L;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    int64_t t = e % T;
+    const int64_t k = e / T;
+    float acc = 1.f;
+    for (int j = 0; j < n; ++j) {
+      const int64_t dg = t % rad[j];
+      t /= rad[j];
+      const int64_t idx = dg + rad[j] * k;
+      acc *= bf16 ? __bfloat162float(static_cast<const __nv_bfloat16*>(V[j])[idx])
+                  : static_cast<const float*>(V[j])[idx];
+    }
+    w[e] = acc;
+  }
+}
+
+__global__ void split_hilo_kernel(const double* __restrict__ s, int64_t n,
+                                  __nv_bfloat16* __restrict__ hi, __nv_bfloat16* __restrict__ lo) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const float f = static_cast<float>(s[i]);
+    const __nv_bfloat16 h = __float2bfloat16_rn(f);
+    hi[i] = h;
+    if (lo) lo[i] = __float2bfloat16_rn(f - __bfloat162float(h));
+  }
+}
+
+__global__ void bf16_to_f32_kernel(const __nv_bfloat16* __restrict__ s, float* __restrict__ d,
+                                   int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    d[i] = __bfloat162float(s[i]);
+}
+
+int grid_of(int64_t n) { return (int)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, 8192)); }
+
+struct Timer {
+  bool on = false;
+  cudaEvent_t ev[64] = {};
+  int n = 0;
+  void start(bool enable) {
+    on = enable;
+    if (!on) return;
+    for (auto& e : ev) KRP_CUDA_CHECK(cudaEventCreate(&e));
+    mark();
+  }
+  void mark() {
+    if (on) KRP_CUDA_CHECK(cudaEventRecord(ev[n++], stream()));
+  }
+  float between(int a, int b) {
+    float ms = 0.f;
+    KRP_CUDA_CHECK(cudaEventElapsedTime(&ms, ev[a], ev[b]));
+    return ms;
+  }
+  ~Timer() {
+    if (on)
+      for (auto& e : ev) cudaEventDestroy(e);
+  }
+};
+
+}  // namespace
+
+void raise_device_status(Ctx* c) {
+  int h = 0;
+  KRP_CUDA_CHECK(cudaMemcpyAsync(&h, c->d_status, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  KRP_CUDA_CHECK(cudaStreamSynchronize(c->stream));
+  if (h != 0) {
+    KRP_CUDA_CHECK(cudaMemsetAsync(c->d_status, 0, sizeof(int), c->stream));
+    fail(static_cast<krp_status>(h), "device stage reported %s", krp_status_string((krp_status)h));
+  }
+}
+
+void krp_rows(const Radix& R, int64_t T, int L, bool bf16, float* w) {
+  if (T * L <= 0) return;
+  KRP_REQUIRE(R.n <= 7, "too many modes for krp_rows");
+  int64_t r[7] = {1, 1, 1, 1, 1, 1, 1};
+  const void* v[7] = {};
+  for (int j = 0; j < R.n; ++j) {
+    r[j] = R.radix[j];
+    v[j] = R.V[j];
+  }
+  krp_rows_kernel<<<grid_of(T * L), 256, 0, stream()>>>(R.n, nullptr, r[0], r[1], r[2], r[3], r[4],
+                                                        r[5], r[6], v[0], v[1], v[2], v[3], v[4],
+                                                        v[5], v[6], bf16 ? 1 : 0, T, L, w);
+  check_launch("krp_rows");
+}
+
+void split_bf16_hilo(const double* src, int64_t n, __nv_bfloat16* hi, __nv_bfloat16* lo) {
+  if (n <= 0) return;
+  split_hilo_kernel<<<grid_of(n), 256, 0, stream()>>>(src, n, hi, lo);
+  check_launch("split_bf16_hilo");
+}
+
+void convert_bf16_to_f32(const __nv_bfloat16* src, float* dst, int64_t n) {
+  if (n <= 0) return;
+  bf16_to_f32_kernel<<<grid_of(n), 256, 0, stream()>>>(src, dst, n);
+  check_launch("bf16_to_f32");
+}
+
+// ------------------------------------------------------------- dispatch ----
+void big_gemm_tn(const void* X, krp_dtype xt, int64_t n1, int64_t S, const float* Ff,
+                 const __nv_bfloat16* Fhi, const __nv_bfloat16* Flo, int L, float* out) {
+  if (xt == KRP_F32) {
+    gemm_tn_f32(static_cast<const float*>(X), n1, S, (int)n1, Ff, n1, L, out, S, false);
+  } else {
+    tc_gemm_tn_bf16(static_cast<const __nv_bfloat16*>(X), n1, S, Fhi, Flo, L, out);
+  }
+}
+
+void big_mttkrp_first(const void* X, krp_dtype xt, int64_t n1, int d_rest, const int64_t* rest_dims,
+                      const void* const* rest_V, int L, float* Y) {
+  int64_t S = 1;
+  for (int j = 0; j < d_rest; ++j) S *= rest_dims[j];
+  if (xt == KRP_F32) {
+    Radix R;
+    R.n = d_rest;
+    for (int j = 0; j < d_rest; ++j) {
+      R.radix[j] = rest_dims[j];
+      R.V[j] = static_cast<const float*>(rest_V[j]);
+    }
+    mttkrp_first_f32(static_cast<const float*>(X), n1, S, R, L, Y);
+  } else {
+    const int64_t n2 = d_rest >= 1 ? rest_dims[0] : 1;
+    const int64_t T = S / n2;
+    Radix R;
+    R.n = d_rest - 1;
+    for (int j = 1; j < d_rest; ++j) {
+      R.radix[j - 1] = rest_dims[j];
+      R.V[j - 1] = static_cast<const float*>(rest_V[j]);  // bf16 bits, typed as void below
+    }
+    float* w = current()->ws.take<float>((size_t)T * L);
+    krp_rows(R, T, L, true, w);
+    KRP_REQUIRE(d_rest >= 1, "BF16 sketch needs d >= 2");
+    tc_mttkrp_first_bf16(static_cast<const __nv_bfloat16*>(X), n1, n2, T,
+                         static_cast<const __nv_bfloat16*>(rest_V[0]), w, L, Y);
+  }
+}
+
+// ------------------------------------------------------------ sketches -----
+SketchArgs validate_sketch(const void* X, krp_dtype xt, int d, const int64_t* dims,
+                           const void* const* omega, krp_dtype omt, int ell) {
+  SketchArgs a{};
+  KRP_REQUIRE(d >= 2 && d <= KRP_MAXD, "d = %d out of range 2..%d", d, KRP_MAXD);
+  a.N = checked_numel(d, dims);
+  KRP_REQUIRE(X, "X is NULL");
+  KRP_REQUIRE(omega, "omega is NULL");
+  KRP_REQUIRE(ell >= 1 && ell <= 256, "ell = %d out of range 1..256", ell);
+  KRP_REQUIRE(xt == KRP_F32 || xt == KRP_BF16, "X dtype must be KRP_F32 or KRP_BF16");
+  KRP_REQUIRE(omt == xt, "factor dtype must equal the X dtype (F32 with F32, BF16 with BF16)");
+  a.X = X;
+  a.xt = xt;
+  a.d = d;
+  a.omt = omt;
+  a.ell = ell;
+  for (int j = 0; j < d; ++j) {
+    a.dims[j] = dims[j];
+    a.omega[j] = omega[j];
+  }
+  return a;
+}
+
+size_t sketch_workspace_bytes(const SketchArgs& a, bool) {
+  const int64_t n1 = a.dims[0];
+  size_t b = ws_bytes((size_t)(a.N / n1) * a.ell, 4);               // B
+  for (int j = 0; j < a.d; ++j) b += ws_bytes((size_t)a.dims[j] * a.ell, 4);  // f32 factors
+  b += ws_bytes((size_t)(a.N / n1) * a.ell, 4);                     // KRP rows (upper bound)
+  if (a.xt == KRP_BF16) b += tc_workspace_bytes(n1, a.N / n1, a.ell);
+  return b + (1 << 20);
+}
+
+static void f32_factor_views(const SketchArgs& a, const float** out) {
+  for (int j = 0; j < a.d; ++j) {
+    if (!a.omega[j]) {
+      out[j] = nullptr;
+      continue;
+    }
+    if (a.omt == KRP_F32) {
+      out[j] = static_cast<const float*>(a.omega[j]);
+    } else {
+      float* f = current()->ws.take<float>((size_t)a.dims[j] * a.ell);
+      convert_bf16_to_f32(static_cast<const __nv_bfloat16*>(a.omega[j]), f, a.dims[j] * a.ell);
+      out[j] = f;
+    }
+  }
+}
+
+void sketch_one_mode(const SketchArgs& a, int n, float* Y) {
+  for (int j = 0; j < a.d; ++j)
+    if (j != n) KRP_REQUIRE(a.omega[j], "omega[%d] is NULL", j);
+  const int64_t n1 = a.dims[0], S = a.N / n1;
+  if (n == 0) {
+    big_mttkrp_first(a.X, a.xt, n1, a.d - 1, a.dims + 1, a.omega + 1, a.ell, Y);
+    return;
+  }
+  const float* f32v[KRP_MAXD];
+  f32_factor_views(a, f32v);
+  float* B = current()->ws.take<float>((size_t)S * a.ell);
+  big_gemm_tn(a.X, a.xt, n1, S, f32v[0], static_cast<const __nv_bfloat16*>(a.omega[0]), nullptr,
+              a.ell, B);
+  diag_contract_f32(B, a.d - 1, a.dims + 1, S, n - 1, f32v + 1, a.ell, Y);
+}
+
+void sketch_all_modes(const SketchArgs& a, float* const* Y) {
+  for (int j = 0; j < a.d; ++j) KRP_REQUIRE(a.omega[j], "omega[%d] is NULL", j);
+  const int64_t n1 = a.dims[0], S = a.N / n1;
+  const float* f32v[KRP_MAXD];
+  f32_factor_views(a, f32v);
+  big_mttkrp_first(a.X, a.xt, n1, a.d - 1, a.dims + 1, a.omega + 1, a.ell, Y[0]);
+  float* B = current()->ws.take<float>((size_t)S * a.ell);
+  big_gemm_tn(a.X, a.xt, n1, S, f32v[0], static_cast<const __nv_bfloat16*>(a.omega[0]), nullptr,
+              a.ell, B);
+  for (int n = 1; n < a.d; ++n) diag_contract_f32(B, a.d - 1, a.dims + 1, S, n - 1, f32v + 1, a.ell, Y[n]);
+}
+
+// ----------------------------------------------------------- multi-TTM -----
+size_t multi_ttm_workspace_bytes(int d, const int64_t* dims, const int* cols, krp_dtype xt) {
+  const int64_t N = checked_numel(d, dims);
+  size_t big = (size_t)(N / dims[0]) * cols[0];
+  size_t b = 2 * ws_bytes(big, 4);
+  for (int j = 0; j < d; ++j) b += ws_bytes((size_t)dims[j] * cols[j], 4 + 2 + 2);
+  if (xt == KRP_BF16) b += tc_workspace_bytes(dims[0], N / dims[0], 2 * cols[0]);
+  return b + (1 << 20);
+}
+
+void multi_ttm(const void* X, krp_dtype xt, int d, const int64_t* dims, const double* const* Q,
+               const int* cols, float* G) {
+  Ctx* c = current();
+  const int64_t N = checked_numel(d, dims);
+  const int64_t n1 = dims[0];
+  float* Qf[KRP_MAXD];
+  __nv_bfloat16 *Qh = nullptr, *Ql = nullptr;
+  for (int j = 0; j < d; ++j) {
+    Qf[j] = c->ws.take<float>((size_t)dims[j] * cols[j]);
+    cast_f64_to_f32(Q[j], Qf[j], dims[j] * cols[j]);
+  }
+  if (xt == KRP_BF16) {
+    Qh = c->ws.take<__nv_bfloat16>((size_t)n1 * cols[0]);
+    Ql = c->ws.take<__nv_bfloat16>((size_t)n1 * cols[0]);
+    split_bf16_hilo(Q[0], n1 * cols[0], Qh, Ql);
+  }
+  const size_t big = (size_t)(N / n1) * cols[0];
+  float* buf[2] = {c->ws.take<float>(big), c->ws.take<float>(big)};
+  int64_t size = N;
+  float* cur = (d == 1) ? G : buf[0];
+  big_gemm_tn(X, xt, n1, N / n1, Qf[0], Qh, Ql, cols[0], cur);
+  size = (N / n1) * cols[0];
+  for (int j = 1; j < d; ++j) {
+    float* nxt = (j == d - 1) ? G : buf[j & 1];
+    const int64_t S = size / dims[j];
+    gemm_tn_f32(cur, dims[j], S, (int)dims[j], Qf[j], dims[j], cols[j], nxt, S, false);
+    size = S * cols[j];
+    cur = nxt;
+  }
+}
+
+// ------------------------------------------------------------ pipeline -----
+void tucker_pipeline(bool sequential, const void* X, krp_dtype xt, int d, const int64_t* dims,
+                     const int* ranks, int oversample, uint64_t seed, unsigned flags,
+                     krp_tucker_out* out) {
+  Ctx* c = current();
+  KRP_REQUIRE(d >= 2 && d <= KRP_MAXD, "d = %d out of range 2..%d", d, KRP_MAXD);
+  const int64_t N = checked_numel(d, dims);
+  KRP_REQUIRE(X && ranks && out, "NULL argument");
+  KRP_REQUIRE(xt == KRP_F32 || xt == KRP_BF16, "X dtype must be KRP_F32 or KRP_BF16");
+  KRP_REQUIRE(oversample >= 0, "oversample must be >= 0");
+  KRP_REQUIRE((flags & ~0xFu) == 0, "unknown flag bits 0x%x", flags);
+  const bool memo = (flags & KRP_MEMO) && !sequential;
+  const bool trunc = flags & KRP_TRUNCATE;
+  const bool resid = flags & KRP_RESIDUAL;
+  int ell[KRP_MAXD], oc[KRP_MAXD];
+  int ellmax = 0;
+  for (int i = 0; i < d; ++i) {
+    KRP_REQUIRE(ranks[i] >= 1, "ranks[%d] must be >= 1", i);
+    ell[i] = ranks[i] + oversample;
+    KRP_REQUIRE(ell[i] <= dims[i], "l_%d = %d exceeds n_%d = %lld", i, ell[i], i, (long long)dims[i]);
+    KRP_REQUIRE(ell[i] <= (trunc ? 64 : 256), "l_%d = %d too large", i, ell[i]);
+    oc[i] = trunc ? ranks[i] : ell[i];
+    ellmax = std::max(ellmax, ell[i]);
+    KRP_REQUIRE(out->factors[i], "out->factors[%d] is NULL", i);
+  }
+  KRP_REQUIRE(out->core, "out->core is NULL");
+  const size_t xb = dtype_size(xt);
+
+  // ---------------- workspace plan (upper bound; take() checks overflow)
+  const bool x_dev = is_device_ptr(X);
+  int64_t maxS = 0;
+  for (int i = 0; i < d; ++i) maxS = std::max<int64_t>(maxS, N / dims[i]);
+  const size_t big = (size_t)(N / dims[0]) * ellmax;
+  size_t need = 5 * ws_bytes(big, 4);
+  need += ws_bytes((size_t)maxS * ellmax, 4);  // KRP rows for the BF16 mode-1 sketch
+  if (!x_dev) need += ws_bytes((size_t)N, xb);
+  int64_t core_l = 1;
+  for (int i = 0; i < d; ++i) {
+    need += (size_t)d * ws_bytes((size_t)dims[i] * ellmax, 4 + 4);  // factors (both types)
+    need += ws_bytes((size_t)dims[i] * ellmax, 4);                  // Y_i
+    need += 3 * ws_bytes((size_t)dims[i] * ellmax, 8);              // Q_i, QR work, Q_i U_i
+    need += ws_bytes((size_t)dims[i] * ellmax, 4 + 2 + 2 + 4);      // Q casts
+    need += ws_bytes((size_t)ellmax * ellmax, 8) * 2;
+    core_l *= ell[i];
+  }
+  need += 4 * ws_bytes((size_t)core_l, 8) + 2 * ws_bytes((size_t)core_l, 4);
+  if (xt == KRP_BF16) need += tc_workspace_bytes(dims[0], N / dims[0], 2 * ellmax);
+  need += 4 << 20;
+  ensure_workspace(c, need);
+  Workspace& ws = c->ws;
+
+  Timer tm;
+  tm.start(flags & KRP_TIMINGS);  // event 0
+  KRP_CUDA_CHECK(cudaMemsetAsync(c->d_status, 0, sizeof(int), c->stream));
+
+  const void* Xd = X;
+  if (!x_dev) {
+    void* p = ws.take<char>((size_t)N * xb);
+    KRP_CUDA_CHECK(cudaMemcpyAsync(p, X, (size_t)N * xb, cudaMemcpyHostToDevice, c->stream));
+    Xd = p;
+  }
+
+  // ---------------- factors (a1) and sketches (a2/a3), QR (a4), core (a5/a6)
+  float* Y[KRP_MAXD];
+  double* Q[KRP_MAXD];
+  for (int i = 0; i < d; ++i) {
+    Y[i] = ws.take<float>((size_t)dims[i] * ellmax);
+    Q[i] = ws.take<double>((size_t)dims[i] * ell[i]);
+  }
+  float* G = ws.take<float>((size_t)core_l);
+  double* qr_work[KRP_MAXD];
+  for (int i = 0; i < d; ++i) qr_work[i] = ws.take<double>((size_t)dims[i] * ell[i]);
+  auto run_qr = [&](int i0, int cnt) {
+    std::vector<QrJob> jobs(cnt);
+    for (int b = 0; b < cnt; ++b) {
+      const int i = i0 + b;
+      jobs[b] = QrJob{Y[i], Q[i], nullptr, qr_work[i], dims[i], ell[i]};
+    }
+    qr_householder_f64(jobs.data(), cnt, c->d_status);
+  };
+  const krp_dtype ft = xt;  // factor dtype for contractions over X
+  const size_t fb = dtype_size(ft);
+
+  if (!sequential) {
+    void* fac[KRP_MAXD][KRP_MAXD] = {};
+    if (memo) {
+      for (int j = 0; j < d; ++j) fac[0][j] = ws.take<char>((size_t)dims[j] * ellmax * fb);
+      FactorJob jobs[KRP_MAXD];
+      for (int j = 0; j < d; ++j) jobs[j] = FactorJob{fac[0][j], dims[j], (dims[j] * ellmax + 3) / 4, (uint32_t)j};
+      launch_gen_factors(seed, KRP_DRAW_MEMO, KRP_TAG_OMEGA, ellmax, ft, jobs, d);
+    } else {
+      for (int i = 0; i < d; ++i) {
+        FactorJob jobs[KRP_MAXD];
+        int nj = 0;
+        for (int j = 0; j < d; ++j) {
+          if (j == i) continue;
+          fac[i][j] = ws.take<char>((size_t)dims[j] * ell[i] * fb);
+          jobs[nj++] = FactorJob{fac[i][j], dims[j], (dims[j] * ell[i] + 3) / 4, (uint32_t)j};
+        }
+        launch_gen_factors(seed, KRP_DRAW_FRESH_BASE + i, KRP_TAG_OMEGA, ell[i], ft, jobs, nj);
+      }
+    }
+    tm.mark();  // 1
+    if (memo) {
+      SketchArgs a{};
+      a.X = Xd; a.xt = xt; a.d = d; a.omt = ft; a.ell = ellmax; a.N = N;
+      for (int j = 0; j < d; ++j) { a.dims[j] = dims[j]; a.omega[j] = fac[0][j]; }
+      sketch_all_modes(a, Y);
+    } else {
+      for (int i = 0; i < d; ++i) {
+        SketchArgs a{};
+        a.X = Xd; a.xt = xt; a.d = d; a.omt = ft; a.ell = ell[i]; a.N = N;
+        for (int j = 0; j < d; ++j) { a.dims[j] = dims[j]; a.omega[j] = fac[i][j]; }
+        sketch_one_mode(a, i, Y[i]);
+      }
+    }
+    tm.mark();  // 2
+    run_qr(0, d);
+    tm.mark();  // 3
+    multi_ttm(Xd, xt, d, dims, Q, ell, G);
+    tm.mark();  // 4
+  } else {
+    // Alg. 8: G <- X; for i: sketch G_(i), QR, G <- G x_i Q_i^T  (rotated layout)
+    const void* cur = Xd;
+    krp_dtype ct = xt;
+    int64_t size = N;
+    int order[KRP_MAXD];       // rotated mode order of `cur`
+    int64_t cdims[KRP_MAXD];   // its sides
+    for (int j = 0; j < d; ++j) { order[j] = j; cdims[j] = dims[j]; }
+    float* pp[2] = {ws.take<float>(big), ws.take<float>(big)};
+    for (int i = 0; i < d; ++i) {
+      const int64_t ni = dims[i];
+      const krp_dtype sft = ct;  // factors in the dtype of the tensor sketched
+      const size_t sfb = dtype_size(sft);
+      void* fac[KRP_MAXD] = {};
+      FactorJob jobs[KRP_MAXD];
+      int nj = 0;
+      for (int j = 0; j < d; ++j) {
+        if (j == i) continue;
+        const int64_t rows = (j < i) ? ell[j] : dims[j];
+        fac[j] = ws.take<char>((size_t)rows * ell[i] * sfb);
+        jobs[nj++] = FactorJob{fac[j], rows, (rows * ell[i] + 3) / 4, (uint32_t)j};
+      }
+      launch_gen_factors(seed, KRP_DRAW_STHOSVD_BASE + i, KRP_TAG_OMEGA, ell[i], sft, jobs, nj);
+      tm.mark();
+      // rest of the rotated order: order[1..d-1]
+      int64_t rdims[KRP_MAXD];
+      const void* rV[KRP_MAXD];
+      for (int q = 1; q < d; ++q) {
+        rdims[q - 1] = cdims[q];
+        rV[q - 1] = fac[order[q]];
+      }
+      big_mttkrp_first(cur, ct, ni, d - 1, rdims, rV, ell[i], Y[i]);
+      tm.mark();
+      run_qr(i, 1);
+      tm.mark();
+      // G <- G x_i Q_i^T
+      float* Qf = ws.take<float>((size_t)ni * ell[i]);
+      cast_f64_to_f32(Q[i], Qf, ni * ell[i]);
+      __nv_bfloat16 *Qh = nullptr, *Ql = nullptr;
+      if (ct == KRP_BF16) {
+        Qh = ws.take<__nv_bfloat16>((size_t)ni * ell[i]);
+        Ql = ws.take<__nv_bfloat16>((size_t)ni * ell[i]);
+        split_bf16_hilo(Q[i], ni * ell[i], Qh, Ql);
+      }
+      float* nxt = (i == d - 1) ? G : pp[i & 1];
+      big_gemm_tn(cur, ct, ni, size / ni, Qf, Qh, Ql, ell[i], nxt);
+      size = size / ni * ell[i];
+      for (int q = 0; q < d - 1; ++q) { order[q] = order[q + 1]; cdims[q] = cdims[q + 1]; }
+      order[d - 1] = i;
+      cdims[d - 1] = ell[i];
+      cur = nxt;
+      ct = KRP_F32;
+      tm.mark();
+    }
+  }
+
+  // ---------------- truncation (a7): HOSVD of the core in FP64
+  float* Gout = G;
+  double* Qout[KRP_MAXD];
+  for (int i = 0; i < d; ++i) Qout[i] = Q[i];
+  int64_t cdim[KRP_MAXD];
+  for (int i = 0; i < d; ++i) cdim[i] = ell[i];
+  const int tmark_trunc0 = tm.n;
+  if (trunc) {
+    double* G64 = ws.take<double>((size_t)core_l);
+    double* G64b = ws.take<double>((size_t)core_l);
+    cast_f32_to_f64(G, G64, core_l);
+    double* Sg[KRP_MAXD];
+    double* U[KRP_MAXD];
+    int lv[KRP_MAXD], rv[KRP_MAXD];
+    for (int i = 0; i < d; ++i) {
+      Sg[i] = ws.take<double>((size_t)ell[i] * ell[i]);
+      U[i] = ws.take<double>((size_t)ell[i] * ranks[i]);
+      lv[i] = ell[i];
+      rv[i] = ranks[i];
+      gram_mode_f64(G64, d, cdim, i, Sg[i]);
+    }
+    sym_eig_top_f64(Sg, lv, rv, U, d, c->d_status);
+    double* src = G64;
+    double* dst = G64b;
+    for (int i = 0; i < d; ++i) {
+      ttm_small_f64(src, d, cdim, i, U[i], ranks[i], dst);
+      cdim[i] = ranks[i];
+      std::swap(src, dst);
+      Qout[i] = ws.take<double>((size_t)dims[i] * ranks[i]);
+      matmul_f64(Q[i], U[i], Qout[i], dims[i], ell[i], ranks[i]);
+    }
+    int64_t rl = 1;
+    for (int i = 0; i < d; ++i) rl *= ranks[i];
+    Gout = ws.take<float>((size_t)rl);
+    cast_f64_to_f32(src, Gout, rl);
+  }
+  tm.mark();
+  int64_t out_l = 1;
+  for (int i = 0; i < d; ++i) out_l *= cdim[i];
+
+  // ---------------- residual (a8): ||X - G x {Q}||_F, FP64 accumulation
+  double resid_val = -1.0, xnorm = -1.0;
+  double* acc = ws.take<double>(4);
+  if (resid) {
+    float* QTf[KRP_MAXD];
+    for (int i = 1; i < d; ++i) {
+      QTf[i] = ws.take<float>((size_t)dims[i] * cdim[i]);
+      transpose_f64_to_f32(Qout[i], dims[i], cdim[i], QTf[i]);
+    }
+    float* Q1f = ws.take<float>((size_t)dims[0] * cdim[0]);
+    cast_f64_to_f32(Qout[0], Q1f, dims[0] * cdim[0]);
+    const size_t hbig = (size_t)(N / dims[0]) * cdim[0];
+    float* hb[2] = {ws.take<float>(hbig), ws.take<float>(hbig)};
+    // rotate G (c1, c2..cd) -> (c2..cd, c1), then expand modes 2..d
+    rotate_first_to_last_f32(Gout, cdim[0], out_l / cdim[0], hb[0]);
+    float* curh = hb[0];
+    int64_t size = out_l;
+    for (int j = 1; j < d; ++j) {
+      float* nx = hb[j & 1];
+      if (nx == curh) nx = hb[(j + 1) & 1];
+      const int64_t S = size / cdim[j];
+      gemm_tn_f32(curh, cdim[j], S, (int)cdim[j], QTf[j], cdim[j], (int)dims[j], nx, S, false);
+      size = S * dims[j];
+      curh = nx;
+    }
+    KRP_CUDA_CHECK(cudaMemsetAsync(acc, 0, 2 * sizeof(double), c->stream));
+    residual_f32(Xd, xt, dims[0], N / dims[0], Q1f, (int)cdim[0], curh, acc);
+  }
+  tm.mark();
+
+  // ---------------- outputs
+  const bool core_dev = is_device_ptr(out->core);
+  KRP_CUDA_CHECK(cudaMemcpyAsync(out->core, Gout, sizeof(float) * out_l,
+                                 core_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                                 c->stream));
+  for (int i = 0; i < d; ++i) {
+    const bool fdev = is_device_ptr(out->factors[i]);
+    KRP_CUDA_CHECK(cudaMemcpyAsync(out->factors[i], Qout[i], sizeof(double) * dims[i] * cdim[i],
+                                   fdev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                                   c->stream));
+  }
+  double* gsq = ws.take<double>(1);
+  // ||G||_F in FP64 from the FP32 core
+  double* g64 = ws.take<double>((size_t)out_l);
+  cast_f32_to_f64(Gout, g64, out_l);
+  const double gn2 = sum_squares_f64_sync(g64, out_l, gsq);  // synchronises the stream
+  double hacc[2] = {0, 0};
+  if (resid) {
+    KRP_CUDA_CHECK(cudaMemcpy(hacc, acc, 2 * sizeof(double), cudaMemcpyDeviceToHost));
+    xnorm = std::sqrt(hacc[1]);
+    resid_val = hacc[1] > 0 ? std::sqrt(hacc[0] / hacc[1]) : 0.0;
+  }
+  tm.mark();
+  raise_device_status(c);
+
+  out->d = d;
+  for (int i = 0; i < d; ++i) out->core_dims[i] = cdim[i];
+  out->rel_residual = resid_val;
+  out->x_norm = xnorm;
+  out->core_norm = std::sqrt(gn2);
+  std::memset(&out->times, 0, sizeof(out->times));
+  if (tm.on) {
+    KRP_CUDA_CHECK(cudaEventSynchronize(tm.ev[tm.n - 1]));
+    krp_phase_times& T = out->times;
+    const int last = tm.n - 1;
+    if (!sequential) {
+      T.rng_ms = tm.between(0, 1);
+      T.sketch_ms = tm.between(1, 2);
+      T.qr_ms = tm.between(2, 3);
+      T.core_ms = tm.between(3, 4);
+    } else {
+      // per step: [gen, sketch, qr, ttm] marks after event 0
+      for (int i = 0; i < d; ++i) {
+        const int b = 4 * i;
+        T.rng_ms += tm.between(b, b + 1);
+        T.sketch_ms += tm.between(b + 1, b + 2);
+        T.qr_ms += tm.between(b + 2, b + 3);
+        T.core_ms += tm.between(b + 3, b + 4);
+      }
+    }
+    T.truncate_ms = tm.between(tmark_trunc0 - 1, tmark_trunc0);
+    T.residual_ms = tm.between(tmark_trunc0, tmark_trunc0 + 1);
+    T.total_ms = tm.between(0, last);
+  }
+}
+
+}  // namespace krp

@@ -1,0 +1,290 @@
+"""Thin ctypes binding of libkrp (include/krp.h): argument marshalling only.
+
+Every function has the name of the C entry point it calls.  Tensors are torch
+tensors (device memory of the context's GPU) or, where the C ABI allows host
+memory, CPU torch tensors / numpy arrays.  Element types map as
+torch.float32 -> KRP_F32, torch.bfloat16 -> KRP_BF16, torch.float64 -> KRP_F64.
+No computation happens here; a missing or unloadable library raises
+immediately (there is no fallback path).
+"""
+
+from __future__ import annotations
+
+import ctypes as C
+import os
+from typing import Optional, Sequence
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libkrp.so")
+
+KRP_OK, KRP_EINVAL, KRP_ENOMEM, KRP_ECUDA, KRP_EUNSUPPORTED, KRP_ETIMEOUT, KRP_ENUMERIC = range(7)
+KRP_F32, KRP_BF16, KRP_FP8_E4M3, KRP_F64 = 0, 1, 2, 3
+KRP_MEMO, KRP_TRUNCATE, KRP_RESIDUAL, KRP_TIMINGS = 0x1, 0x2, 0x4, 0x8
+KRP_MAXD = 8
+KRP_DRAW_MEMO, KRP_DRAW_FRESH_BASE, KRP_DRAW_STHOSVD_BASE = 0, 1, 64
+KRP_TAG_OMEGA, KRP_TAG_PSI = 0, 1
+
+EXPORTED = [
+    "krp_create", "krp_destroy", "krp_set_stream", "krp_last_error", "krp_status_string",
+    "krp_abi_version", "krp_launch_count", "krp_gen_factors", "krp_philox_words",
+    "krp_sketch_mode", "krp_sketch_all_modes", "krp_qr", "krp_multi_ttm",
+    "krp_tucker_rhosvd", "krp_tucker_sthosvd", "krp_block_hankel_lowrank",
+    "krp_block_hankel_sketch",
+]
+
+
+class KrpError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{_status_name(status)}: {msg}")
+        self.status = status
+
+
+class PhaseTimes(C.Structure):
+    _fields_ = [(n, C.c_double) for n in
+                ("rng_ms", "sketch_ms", "qr_ms", "core_ms", "truncate_ms", "residual_ms",
+                 "total_ms")]
+
+
+class TuckerOut(C.Structure):
+    _fields_ = [
+        ("core", C.c_void_p),
+        ("factors", C.c_void_p * KRP_MAXD),
+        ("d", C.c_int),
+        ("core_dims", C.c_int64 * KRP_MAXD),
+        ("rel_residual", C.c_double),
+        ("x_norm", C.c_double),
+        ("core_norm", C.c_double),
+        ("times", PhaseTimes),
+    ]
+
+
+_lib = None
+
+
+def load_library(path: Optional[str] = None):
+    """Load libkrp.so (raises OSError if it has not been built)."""
+    global _lib
+    if _lib is not None and path is None:
+        return _lib
+    p = path or LIB_PATH
+    if not os.path.exists(p):
+        raise OSError(f"libkrp not built: {p} is missing (run __graft_entry__.build())")
+    lib = C.CDLL(p)
+    vp, i64p = C.c_void_p, C.POINTER(C.c_int64)
+    sig = {
+        "krp_create": (C.c_int, [C.POINTER(vp), C.c_int, vp]),
+        "krp_destroy": (C.c_int, [vp]),
+        "krp_set_stream": (C.c_int, [vp, vp]),
+        "krp_last_error": (C.c_char_p, [vp]),
+        "krp_status_string": (C.c_char_p, [C.c_int]),
+        "krp_abi_version": (C.c_int, []),
+        "krp_launch_count": (C.c_uint64, [vp]),
+        "krp_gen_factors": (C.c_int, [vp, C.c_uint64, C.c_uint32, C.c_uint32, C.c_int, i64p,
+                                      C.c_int, C.c_int, C.POINTER(vp)]),
+        "krp_philox_words": (C.c_int, [vp, C.c_uint64, C.c_uint32, C.c_uint32, C.c_uint32,
+                                       C.c_uint64, C.c_int64, vp]),
+        "krp_sketch_mode": (C.c_int, [vp, vp, C.c_int, C.c_int, i64p, C.c_int, C.POINTER(vp),
+                                      C.c_int, C.c_int, vp]),
+        "krp_sketch_all_modes": (C.c_int, [vp, vp, C.c_int, C.c_int, i64p, C.POINTER(vp),
+                                           C.c_int, C.c_int, C.POINTER(vp)]),
+        "krp_qr": (C.c_int, [vp, C.c_int, C.POINTER(vp), i64p, C.POINTER(C.c_int),
+                             C.POINTER(vp), C.POINTER(vp)]),
+        "krp_multi_ttm": (C.c_int, [vp, vp, C.c_int, C.c_int, i64p, C.POINTER(vp),
+                                    C.POINTER(C.c_int), vp]),
+        "krp_tucker_rhosvd": (C.c_int, [vp, vp, C.c_int, C.c_int, i64p, C.POINTER(C.c_int),
+                                        C.c_int, C.c_uint64, C.c_uint, C.POINTER(TuckerOut)]),
+        "krp_tucker_sthosvd": (C.c_int, [vp, vp, C.c_int, C.c_int, i64p, C.POINTER(C.c_int),
+                                         C.c_int, C.c_uint64, C.c_uint, C.POINTER(TuckerOut)]),
+        "krp_block_hankel_lowrank": (C.c_int, [vp, vp, C.c_int, C.c_int, C.c_int, C.c_int,
+                                               C.c_int, C.c_int, C.c_int, C.c_uint64, vp, vp,
+                                               vp]),
+        "krp_block_hankel_sketch": (C.c_int, [vp, vp, C.c_int, C.c_int, C.c_int, C.c_int, vp,
+                                              vp, C.c_int, vp, vp, C.c_int, vp, vp]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    if path is None:
+        _lib = lib
+    return lib
+
+
+def _status_name(s: int) -> str:
+    names = ["KRP_OK", "KRP_EINVAL", "KRP_ENOMEM", "KRP_ECUDA", "KRP_EUNSUPPORTED",
+             "KRP_ETIMEOUT", "KRP_ENUMERIC"]
+    return names[s] if 0 <= s < len(names) else f"status {s}"
+
+
+# ---------------------------------------------------------------- marshalling --
+
+def _dtype_code(t) -> int:
+    import torch
+    if isinstance(t, np.ndarray):
+        m = {np.dtype(np.float32): KRP_F32, np.dtype(np.float64): KRP_F64}
+        return m[t.dtype]
+    m = {torch.float32: KRP_F32, torch.bfloat16: KRP_BF16, torch.float64: KRP_F64}
+    if t.dtype not in m:
+        raise TypeError(f"unsupported dtype {t.dtype}")
+    return m[t.dtype]
+
+
+def _ptr(t) -> Optional[int]:
+    if t is None:
+        return None
+    if isinstance(t, np.ndarray):
+        if not (t.flags["C_CONTIGUOUS"] or t.flags["F_CONTIGUOUS"]):
+            raise ValueError("array must be contiguous")
+        return t.ctypes.data
+    if not t.is_contiguous():
+        raise ValueError("tensor must be contiguous")
+    return t.data_ptr()
+
+
+def _i64(vals) -> C.Array:
+    return (C.c_int64 * len(vals))(*[int(v) for v in vals])
+
+
+def _i32(vals) -> C.Array:
+    return (C.c_int * len(vals))(*[int(v) for v in vals])
+
+
+def _ptrs(ts) -> C.Array:
+    return (C.c_void_p * len(ts))(*[_ptr(t) for t in ts])
+
+
+def _current_stream(device: int) -> int:
+    import torch
+    return torch.cuda.current_stream(device).cuda_stream
+
+
+class Context:
+    """Owns a krp_ctx (workspace + stream binding) on one CUDA device."""
+
+    def __init__(self, device: int = 0, stream: Optional[int] = None):
+        self.lib = load_library()
+        self.device = device
+        h = C.c_void_p()
+        s = _current_stream(device) if stream is None else stream
+        st = self.lib.krp_create(C.byref(h), device, C.c_void_p(s))
+        if st != KRP_OK:
+            raise KrpError(st, "krp_create failed")
+        self.handle = h
+
+    def check(self, st: int):
+        if st != KRP_OK:
+            raise KrpError(st, self.last_error())
+
+    def last_error(self) -> str:
+        return self.lib.krp_last_error(self.handle).decode()
+
+    def set_stream(self, stream: int):
+        self.check(self.lib.krp_set_stream(self.handle, C.c_void_p(stream)))
+
+    def launch_count(self) -> int:
+        return int(self.lib.krp_launch_count(self.handle))
+
+    def close(self):
+        if getattr(self, "handle", None):
+            self.lib.krp_destroy(self.handle)
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+# ---------------------------------------------------------------- entry points --
+
+def krp_abi_version() -> int:
+    return int(load_library().krp_abi_version())
+
+
+def krp_gen_factors(ctx: Context, seed: int, draw_id: int, tag: int, rows: Sequence[int],
+                    ell: int, omega: Sequence):
+    """Fill each non-None tensor omega[j] (rows[j] x ell, column-major) with N(0,1)."""
+    t = next(o for o in omega if o is not None)
+    ctx.check(ctx.lib.krp_gen_factors(ctx.handle, seed, draw_id, tag, len(rows), _i64(rows), ell,
+                                      _dtype_code(t), _ptrs(omega)))
+
+
+def krp_philox_words(ctx: Context, seed: int, c1: int, c2: int, c3: int, first_block: int,
+                     nblocks: int, out):
+    ctx.check(ctx.lib.krp_philox_words(ctx.handle, seed, c1, c2, c3, first_block, nblocks,
+                                       _ptr(out)))
+
+
+def krp_sketch_mode(ctx: Context, X, dims: Sequence[int], n: int, omega: Sequence, ell: int, Y):
+    om_t = next(o for o in omega if o is not None)
+    ctx.check(ctx.lib.krp_sketch_mode(ctx.handle, _ptr(X), _dtype_code(X), len(dims), _i64(dims),
+                                      n, _ptrs(omega), _dtype_code(om_t), ell, _ptr(Y)))
+
+
+def krp_sketch_all_modes(ctx: Context, X, dims: Sequence[int], omega: Sequence, ell: int,
+                         Ys: Sequence):
+    ctx.check(ctx.lib.krp_sketch_all_modes(ctx.handle, _ptr(X), _dtype_code(X), len(dims),
+                                           _i64(dims), _ptrs(omega), _dtype_code(omega[0]), ell,
+                                           _ptrs(Ys)))
+
+
+def krp_qr(ctx: Context, Ys: Sequence, ms: Sequence[int], ls: Sequence[int], Qs: Sequence,
+           Rs: Optional[Sequence] = None):
+    ctx.check(ctx.lib.krp_qr(ctx.handle, len(Ys), _ptrs(Ys), _i64(ms), _i32(ls), _ptrs(Qs),
+                             _ptrs(Rs) if Rs is not None else None))
+
+
+def krp_multi_ttm(ctx: Context, X, dims: Sequence[int], Qs: Sequence, cols: Sequence[int], G):
+    ctx.check(ctx.lib.krp_multi_ttm(ctx.handle, _ptr(X), _dtype_code(X), len(dims), _i64(dims),
+                                    _ptrs(Qs), _i32(cols), _ptr(G)))
+
+
+def _tucker(fn, ctx, X, dims, ranks, oversample, seed, flags, core, factors):
+    out = TuckerOut()
+    out.core = _ptr(core)
+    for i, f in enumerate(factors):
+        out.factors[i] = _ptr(f)
+    ctx.check(fn(ctx.handle, _ptr(X), _dtype_code(X), len(dims), _i64(dims), _i32(ranks),
+                 oversample, seed, flags, C.byref(out)))
+    t = out.times
+    return {
+        "core_dims": [int(out.core_dims[i]) for i in range(out.d)],
+        "rel_residual": out.rel_residual,
+        "x_norm": out.x_norm,
+        "core_norm": out.core_norm,
+        "times": {k: getattr(t, k) for k, _ in PhaseTimes._fields_},
+    }
+
+
+def krp_tucker_rhosvd(ctx: Context, X, dims, ranks, oversample, seed, flags, core, factors):
+    """RHOSVD-KRP (Alg. 7); core/factors are preallocated outputs."""
+    return _tucker(ctx.lib.krp_tucker_rhosvd, ctx, X, dims, ranks, oversample, seed, flags, core,
+                   factors)
+
+
+def krp_tucker_sthosvd(ctx: Context, X, dims, ranks, oversample, seed, flags, core, factors):
+    """RSTHOSVD-KRP (Alg. 8); core/factors are preallocated outputs."""
+    return _tucker(ctx.lib.krp_tucker_sthosvd, ctx, X, dims, ranks, oversample, seed, flags,
+                   core, factors)
+
+
+def krp_block_hankel_lowrank(ctx: Context, blocks, m, n, s, r, ell_r, ell_l, seed, U, S, V):
+    ctx.check(ctx.lib.krp_block_hankel_lowrank(ctx.handle, _ptr(blocks), _dtype_code(blocks), m,
+                                               n, s, r, ell_r, ell_l, seed, _ptr(U), _ptr(S),
+                                               _ptr(V)))
+
+
+def krp_block_hankel_sketch(ctx: Context, blocks, m, n, s, omega1, omega2, ell_r, psi1, psi2,
+                            ell_l, Y, Z):
+    ctx.check(ctx.lib.krp_block_hankel_sketch(ctx.handle, _ptr(blocks), _dtype_code(blocks), m,
+                                              n, s, _ptr(omega1), _ptr(omega2), ell_r, _ptr(psi1),
+                                              _ptr(psi2), ell_l, _ptr(Y), _ptr(Z)))

@@ -1,0 +1,148 @@
+"""a6-a8 parity: RHOSVD-KRP (fresh, memoized), RSTHOSVD-KRP, truncation, residual.
+
+Compared quantities (basis-invariant, FP32 bound 1e-5):
+  P2  ||X_hat_gpu - X_hat_oracle||_F / ||X||_F
+  P3  |e_gpu - e_oracle| with e = ||X - X_hat||_F / ||X||_F
+  P4  after truncation, the rank-r projectors Q_r Q_r^T of every mode
+plus orthonormality of every returned factor (FP64 QR).  The oracle runs the
+same algorithm on the same FP32-rounded X with its own FP32-rounded factors.
+"""
+
+import numpy as np
+import pytest
+
+from tests.gpu_util import require_gpu, dev, tensor_to_dev, rel
+from oracle import philox, tucker as TK
+from synth import TuckerSpec, tucker_tensor, config_spec
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    require_gpu()
+    import paper_2507_23207_gb300 as K
+    c = K.Context(0)
+    yield c
+    c.close()
+
+
+def run_gpu(ctx, x32, spec_dims, ranks, p, seed, flags, sequential=False, host=False):
+    import torch
+    import paper_2507_23207_gb300 as K
+    trunc = bool(flags & K.KRP_TRUNCATE)
+    oc = [r if trunc else r + p for r in ranks]
+    if host:
+        from synth import to_torch_layout
+        xd = to_torch_layout(np.asfortranarray(x32)).to(torch.float32)
+        core = torch.empty(int(np.prod(oc)), dtype=torch.float32)
+        facs = [torch.empty(n * c, dtype=torch.float64) for n, c in zip(spec_dims, oc)]
+    else:
+        xd = tensor_to_dev(x32, torch.float32)
+        core = torch.empty(int(np.prod(oc)), dtype=torch.float32, device=dev())
+        facs = [torch.empty(n * c, dtype=torch.float64, device=dev()) for n, c in zip(spec_dims, oc)]
+    fn = K.krp_tucker_sthosvd if sequential else K.krp_tucker_rhosvd
+    res = fn(ctx, xd, spec_dims, ranks, p, seed, flags, core, facs)
+    torch.cuda.synchronize()
+    g = core.cpu().numpy().reshape(oc[::-1]).T.astype(np.float64)
+    qs = [f.cpu().numpy().reshape(c, n).T for f, n, c in zip(facs, spec_dims, oc)]
+    return g, qs, res
+
+
+def oracle_run(x32, ells, seed, memo, sequential):
+    if sequential:
+        # step 0 sketches the FP32 X with FP32 factors; later steps sketch FP32 cores
+        return TK.rsthosvd_krp(x32, ells, seed, omega_round="f32")
+    return TK.rhosvd_krp(x32, ells, seed, memo=memo, omega_round="f32")
+
+
+SPECS = [
+    TuckerSpec("c1", (64, 64, 64), (5, 5, 5), 1e-6, None, 1001, (5, 5, 5), (10, 10, 10)),
+    TuckerSpec("ragged", (37, 29, 23), (3, 4, 5), 1e-3, None, 17, (3, 4, 5), (6, 7, 8)),
+    TuckerSpec("d4", (12, 10, 9, 8), (3, 3, 2, 3), 1e-2, None, 23, (3, 3, 2, 3), (5, 5, 4, 5)),
+    TuckerSpec("tall", (300, 20, 10), (6, 5, 4), 1e-4, None, 29, (6, 5, 4), (10, 9, 8)),
+]
+
+
+@pytest.mark.parametrize("spec", SPECS, ids=[s.name for s in SPECS])
+@pytest.mark.parametrize("variant", ["fresh", "memo", "sthosvd"])
+def test_tucker_parity(ctx, spec, variant):
+    import paper_2507_23207_gb300 as K
+    x, _, _ = tucker_tensor(spec)
+    x32 = philox.round_to_f32(x)
+    p = spec.oversample
+    ells = [r + p for r in spec.ranks]
+    memo = variant == "memo"
+    seq = variant == "sthosvd"
+    flags = (K.KRP_MEMO if memo else 0) | K.KRP_RESIDUAL
+    g, qs, res = run_gpu(ctx, x32, spec.dims, spec.ranks, p, spec.omega_seed, flags, seq)
+    ora = oracle_run(x32, ells, spec.omega_seed, memo, seq)
+    for q in qs:
+        assert np.linalg.norm(q.T @ q - np.eye(q.shape[1])) <= 1e-12
+    nx = np.linalg.norm(x32)
+    xh = TK.reconstruct(g, qs)
+    xh_o = TK.reconstruct(ora["G"], ora["Q"])
+    assert np.linalg.norm(xh - xh_o) / nx <= 1e-5
+    e_o = TK.rel_error(x32, ora["G"], ora["Q"])
+    assert abs(res["rel_residual"] - e_o) <= 1e-5
+    assert abs(res["x_norm"] - nx) <= 1e-6 * nx
+    # truncated variant
+    flags_t = flags | K.KRP_TRUNCATE
+    g2, q2, res2 = run_gpu(ctx, x32, spec.dims, spec.ranks, p, spec.omega_seed, flags_t, seq)
+    g2o, q2o = TK.truncate_core(ora["G"], ora["Q"], spec.ranks)
+    for a, b in zip(q2, q2o):
+        assert np.linalg.norm(a @ a.T - b @ b.T) / np.sqrt(a.shape[1]) <= 1e-5
+    assert np.linalg.norm(TK.reconstruct(g2, q2) - TK.reconstruct(g2o, q2o)) / nx <= 1e-5
+    assert abs(res2["rel_residual"] - TK.rel_error(x32, g2o, q2o)) <= 1e-5
+    assert list(res2["core_dims"]) == list(spec.ranks)
+
+
+def test_exact_recovery_fp32(ctx):
+    import paper_2507_23207_gb300 as K
+    spec = TuckerSpec("exact", (40, 36, 30), (4, 3, 5), 0.0, None, 31, (4, 3, 5), (7, 6, 8))
+    x, _, _ = tucker_tensor(spec)
+    x32 = philox.round_to_f32(x)
+    for flags in (K.KRP_MEMO | K.KRP_RESIDUAL, K.KRP_RESIDUAL | K.KRP_TRUNCATE):
+        g, qs, res = run_gpu(ctx, x32, spec.dims, spec.ranks, spec.oversample, 0, flags)
+        # FP32 arithmetic floor: the error of an exact-rank input is ~FP32 epsilon
+        assert res["rel_residual"] <= 1e-5
+
+
+def test_host_pointers_match_device_pointers(ctx):
+    import paper_2507_23207_gb300 as K
+    spec = SPECS[1]
+    x, _, _ = tucker_tensor(spec)
+    x32 = philox.round_to_f32(x)
+    flags = K.KRP_MEMO | K.KRP_TRUNCATE | K.KRP_RESIDUAL
+    gd, qd, rd = run_gpu(ctx, x32, spec.dims, spec.ranks, spec.oversample, 0, flags)
+    gh, qh, rh = run_gpu(ctx, x32, spec.dims, spec.ranks, spec.oversample, 0, flags, host=True)
+    assert np.array_equal(gd, gh)
+    for a, b in zip(qd, qh):
+        assert np.array_equal(a, b)
+    assert rd["rel_residual"] == rh["rel_residual"]
+
+
+def test_timings_reported(ctx):
+    import paper_2507_23207_gb300 as K
+    spec = SPECS[0]
+    x, _, _ = tucker_tensor(spec)
+    x32 = philox.round_to_f32(x)
+    for seq in (False, True):
+        _, _, res = run_gpu(ctx, x32, spec.dims, spec.ranks, spec.oversample, 0,
+                            K.KRP_MEMO | K.KRP_TIMINGS | K.KRP_TRUNCATE | K.KRP_RESIDUAL, seq)
+        t = res["times"]
+        assert t["total_ms"] > 0 and t["sketch_ms"] > 0 and t["qr_ms"] > 0 and t["core_ms"] > 0
+        assert t["total_ms"] >= t["sketch_ms"]
+
+
+def test_tucker_invalid_arguments(ctx):
+    import torch
+    import paper_2507_23207_gb300 as K
+    x32 = np.zeros((8, 8, 8), dtype=np.float64, order="F")
+    with pytest.raises(K.KrpError) as e:  # l = 9 > n = 8
+        run_gpu(ctx, x32, (8, 8, 8), (5, 5, 5), 4, 0, 0)
+    assert e.value.status == K.KRP_EINVAL
+    with pytest.raises(K.KrpError):
+        run_gpu(ctx, x32, (8, 8, 8), (0, 2, 2), 1, 0, 0)
+    with pytest.raises(K.KrpError):
+        run_gpu(ctx, x32, (8, 8, 8), (2, 2, 2), 1, 0, 0x100)

@@ -165,17 +165,6 @@ struct RadixDev {
   const float* V[KRP_MAXD];
 };
 
-__device__ __forceinline__ float krp_weight(const RadixDev& R, int64_t s, int k) {
-  float w = 1.f;
-  for (int j = 0; j < R.n; ++j) {
-    const int64_t r = R.radix[j];
-    const int64_t dgt = s % r;
-    s /= r;
-    w *= R.V[j][dgt + r * k];
-  }
-  return w;
-}
-
 template <int NP, bool VEC>
 __global__ void __launch_bounds__(NP * 4)
     mttkrp_first_kernel(const float* __restrict__ A, int64_t n1, int64_t S, const RadixDev R,
@@ -185,6 +174,8 @@ __global__ void __launch_bounds__(NP * 4)
   constexpr int WV = (TK * NP + NT - 1) / NT;
   __shared__ __align__(16) float As[2][TK][TM];
   __shared__ __align__(16) float Ws[2][TK][NP];
+  // mixed-radix digits of the chunk's TK rows, decoded once per chunk
+  __shared__ int dig[2][TK][KRP_MAXD];
 
   const int tid = threadIdx.x, g = tid & 15, h = tid >> 4;
   const int64_t i0 = (int64_t)blockIdx.x * TM;
@@ -225,6 +216,7 @@ __global__ void __launch_bounds__(NP * 4)
       }
       ra[v] = val;
     }
+    const int db = (int)(((sc - sb) / TK) & 1);
 #pragma unroll
     for (int v = 0; v < WV; ++v) {
       const int q = tid + v * NT;
@@ -232,9 +224,24 @@ __global__ void __launch_bounds__(NP * 4)
       if (q < TK * NP) {
         const int sl = q / NP, kk = q % NP;
         const int64_t s = sc + sl;
-        if (s < se && k0 + kk < L) w = krp_weight(R, s, k0 + kk);
+        const int k = k0 + kk;
+        if (s < se && k < L) {
+          w = 1.f;
+          for (int j = 0; j < R.n; ++j) w *= R.V[j][dig[db][sl][j] + R.radix[j] * k];
+        }
       }
       rw[v] = w;
+    }
+  };
+  // digits of rows s = sc + sl of one chunk (first TK threads)
+  auto decode = [&](int64_t sc, int buf) {
+    if (tid < TK) {
+      int64_t s = sc + tid;
+      for (int j = 0; j < R.n; ++j) {
+        const int64_t r = R.radix[j];
+        dig[buf][tid][j] = (int)(s % r);
+        s /= r;
+      }
     }
   };
   auto store = [&](int buf) {
@@ -253,6 +260,9 @@ __global__ void __launch_bounds__(NP * 4)
     }
   };
 
+  decode(sb, 0);
+  if (nchunks > 1) decode(sb + TK, 1);
+  __syncthreads();
   load(sb);
   store(0);
   __syncthreads();
@@ -274,6 +284,7 @@ __global__ void __launch_bounds__(NP * 4)
       }
     }
     if (c + 1 < nchunks) store(buf ^ 1);
+    if (c + 2 < nchunks) decode(sb + (c + 2) * TK, buf);
     __syncthreads();
   }
 #pragma unroll
@@ -444,6 +455,23 @@ __device__ __forceinline__ float ldx<__nv_bfloat16>(const __nv_bfloat16* p) {
   return __bfloat162float(*p);
 }
 
+// four consecutive elements (16-byte / 8-byte aligned)
+template <class XT>
+__device__ __forceinline__ void ld4(const XT* p, float* v);
+template <>
+__device__ __forceinline__ void ld4<float>(const float* p, float* v) {
+  const float4 q = *reinterpret_cast<const float4*>(p);
+  v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
+}
+template <>
+__device__ __forceinline__ void ld4<__nv_bfloat16>(const __nv_bfloat16* p, float* v) {
+  const uint2 q = *reinterpret_cast<const uint2*>(p);
+  v[0] = __uint_as_float(q.x << 16);
+  v[1] = __uint_as_float(q.x & 0xFFFF0000u);
+  v[2] = __uint_as_float(q.y << 16);
+  v[3] = __uint_as_float(q.y & 0xFFFF0000u);
+}
+
 template <class XT>
 __global__ void __launch_bounds__(256)
     residual_kernel(const XT* __restrict__ X, int64_t n1, int64_t S,
@@ -489,18 +517,28 @@ __global__ void __launch_bounds__(256)
     }
   }
   float d2 = 0.f, x2 = 0.f;
+  const bool vec = (n1 % 4) == 0;
 #pragma unroll
   for (int b = 0; b < 8; ++b) {
     const int64_t s = s0 + (b < 4 ? 4 * gs + b : 64 + 4 * gs + (b - 4));
     if (s >= S) continue;
 #pragma unroll
-    for (int a = 0; a < 8; ++a) {
-      const int64_t i = i0 + (a < 4 ? 4 * gi + a : 64 + 4 * gi + (a - 4));
-      if (i >= n1) continue;
-      const float x = ldx<XT>(X + i + n1 * s);
-      const float df = x - xh[a][b];
-      d2 = fmaf(df, df, d2);
-      x2 = fmaf(x, x, x2);
+    for (int half = 0; half < 2; ++half) {
+      const int64_t ib = i0 + half * 64 + 4 * gi;
+      float xv[4];
+      if (vec && ib + 3 < n1) {
+        ld4<XT>(X + ib + n1 * s, xv);
+      } else {
+#pragma unroll
+        for (int a = 0; a < 4; ++a) xv[a] = (ib + a < n1) ? ldx<XT>(X + ib + a + n1 * s) : 0.f;
+      }
+#pragma unroll
+      for (int a = 0; a < 4; ++a) {
+        if (ib + a >= n1) continue;
+        const float df = xv[a] - xh[half * 4 + a][b];
+        d2 = fmaf(df, df, d2);
+        x2 = fmaf(xv[a], xv[a], x2);
+      }
     }
   }
   double dd = d2, xx = x2;

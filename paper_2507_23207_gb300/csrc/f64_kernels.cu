@@ -200,21 +200,32 @@ __global__ void __launch_bounds__(256) eig_kernel(const EigJob* __restrict__ job
   }
   for (int i = tid; i < n; i += blockDim.x) ring[i] = i;
   __syncthreads();
-  for (int sweep = 0; sweep < 40; ++sweep) {
+  for (int sweep = 0; sweep < 30; ++sweep) {
     if (tid == 0) {
-      double o = 0.0, dg = 0.0;
-      for (int r = 0; r < n; ++r)
-        for (int c = 0; c < n; ++c) {
-          if (r == c)
-            dg += S[r][c] * S[r][c];
-          else
-            o += S[r][c] * S[r][c];
-        }
-      offn = o;
-      diagn = dg;
+      offn = 0.0;
+      diagn = 0.0;
     }
     __syncthreads();
-    if (!(offn > 1e-30 * diagn) || offn == 0.0) break;
+    {
+      double o = 0.0, dg = 0.0;
+      for (int e = tid; e < n * n; e += blockDim.x) {
+        const int r = e % n, c = e / n;
+        const double v = S[r][c] * S[r][c];
+        if (r == c)
+          dg += v;
+        else
+          o += v;
+      }
+      o = warp_sum(o);
+      dg = warp_sum(dg);
+      if ((tid & 31) == 0) {
+        atomicAdd(&offn, o);
+        atomicAdd(&diagn, dg);
+      }
+    }
+    __syncthreads();
+    // converged once the off-diagonal norm is below 1e-13 of the diagonal's
+    if (!(offn > 1e-26 * diagn) || offn == 0.0) break;
     for (int round = 0; round < n - 1; ++round) {
       // pairs of this round: ring[i] with ring[n-1-i]
       if (tid < n / 2) {
@@ -228,7 +239,7 @@ __global__ void __launch_bounds__(256) eig_kernel(const EigJob* __restrict__ job
         qq[tid] = q;
         const double apq = S[p][q];
         double c = 1.0, s = 0.0;
-        if (apq != 0.0) {
+        if (fabs(apq) > 1e-16 * sqrt(fabs(S[p][p] * S[q][q]))) {
           const double app = S[p][p], aqq = S[q][q];
           const double theta = (aqq - app) / (2.0 * apq);
           const double t = (theta >= 0.0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(1.0 + theta * theta));
@@ -336,6 +347,176 @@ __global__ void finite_kernel(const double* __restrict__ x, int64_t n, int* stat
     if (!isfinite(x[i])) atomicExch(status, (int)KRP_ENUMERIC);
 }
 
+// ---------------------------------------------------------------------------
+// Shifted CholeskyQR3 in FP64 (Fukaya, Kannan, Nakatsukasa, Zhang, Yamamoto,
+// SIAM J. Sci. Comput. 2020): three passes of  G = W^T W (+ s I on the first),
+// G = R^T R (Cholesky), W <- W R^{-1}.  The thin QR it returns is the unique one
+// with diag(R) > 0 whenever Y has full column rank (then it equals the
+// Householder result), and the first-pass shift keeps it defined for rank-
+// deficient sketches.  All three kinds of step spread over many SMs.
+constexpr int kCqrMaxL = 64;
+constexpr int kCqrRows = 32;  // rows per CTA in the Gram / solve kernels
+
+struct CqrJob {
+  const float* Y;      // FP32 input (pass 1) or null
+  const double* Y64;   // FP64 input (pass 1) or null
+  double* W;           // m x l FP64 working matrix (passes 2, 3 read it)
+  double* Q;           // final output
+  double* G;           // l x l Gram accumulator
+  double* Rk;          // 3 x l x l upper factors of the passes
+  double* R;           // optional product R3 R2 R1
+  int* zero;           // set when the input is exactly zero
+  int64_t m;
+  int l;
+};
+
+template <bool FROM_INPUT>
+__global__ void __launch_bounds__(256) cqr_gram_kernel(const CqrJob* __restrict__ jobs, int* status) {
+  const CqrJob job = jobs[blockIdx.y];
+  const int64_t r0 = (int64_t)blockIdx.x * kCqrRows;
+  if (r0 >= job.m) return;
+  const int l = job.l;
+  const int rows = (int)((job.m - r0) < kCqrRows ? (job.m - r0) : kCqrRows);
+  __shared__ double blk[kCqrRows][kCqrMaxL + 1];
+  __shared__ int bad;
+  if (threadIdx.x == 0) bad = 0;
+  __syncthreads();
+  for (int e = threadIdx.x; e < rows * l; e += blockDim.x) {
+    const int r = e % rows, c = e / rows;
+    const int64_t idx = r0 + r + job.m * c;
+    double v;
+    if (FROM_INPUT)
+      v = job.Y64 ? job.Y64[idx] : (double)job.Y[idx];
+    else
+      v = job.W[idx];
+    if (!isfinite(v)) bad = 1;
+    blk[r][c] = v;
+  }
+  __syncthreads();
+  if (bad) {
+    if (threadIdx.x == 0) atomicExch(status, (int)KRP_ENUMERIC);
+    return;
+  }
+  // upper triangle (a <= b) of the partial Gram
+  const int pairs = l * (l + 1) / 2;
+  for (int p = threadIdx.x; p < pairs; p += blockDim.x) {
+    int a = 0, rem = p;
+    while (rem >= l - a) {
+      rem -= l - a;
+      ++a;
+    }
+    const int b = a + rem;
+    double s = 0.0;
+    for (int r = 0; r < rows; ++r) s = fma(blk[r][a], blk[r][b], s);
+    atomicAdd(job.G + a + l * b, s);
+  }
+}
+
+// Cholesky G (+ shift) = R^T R of one l x l matrix per CTA; R stored in Rk[pass].
+__global__ void __launch_bounds__(256) cqr_chol_kernel(const CqrJob* __restrict__ jobs, int pass) {
+  const CqrJob job = jobs[blockIdx.x];
+  const int l = job.l;
+  __shared__ double A[kCqrMaxL][kCqrMaxL + 1];
+  __shared__ double piv;
+  __shared__ int zero_input;
+  for (int e = threadIdx.x; e < l * l; e += blockDim.x) {
+    const int a = e % l, b = e / l;
+    A[a][b] = (a <= b) ? job.G[a + l * b] : job.G[b + l * a];
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double tr = 0.0;
+    for (int j = 0; j < l; ++j) tr += A[j][j];
+    zero_input = !(tr > 0.0);
+    if (pass == 0) *job.zero = zero_input;
+    if (pass == 0 && !zero_input) {
+      // s = 11 (m l + l (l + 1)) u ||Y||^2 with ||Y||_F^2 >= ||Y||_2^2
+      const double s = 11.0 * ((double)job.m * l + (double)l * (l + 1)) * 0x1p-53 * tr;
+      for (int j = 0; j < l; ++j) A[j][j] += s;
+    }
+  }
+  __syncthreads();
+  double* R = job.Rk + (size_t)pass * l * l;
+  for (int j = 0; j < l; ++j) {
+    if (threadIdx.x == 0) {
+      double d = A[j][j];
+      // a non-positive pivot (zero input or rounding) gets a unit pivot: the
+      // column is then orthonormalised by the next passes
+      piv = (d > 0.0 && !zero_input) ? sqrt(d) : 1.0;
+    }
+    __syncthreads();
+    const double dj = piv;
+    for (int i = threadIdx.x; i < l; i += blockDim.x) {
+      const double v = (i >= j) ? A[j][i] / dj : 0.0;
+      R[j + l * i] = (i == j) ? dj : v;
+      if (i > j) A[j][i] = v;
+    }
+    __syncthreads();
+    const int rem = l - j - 1;
+    for (int e = threadIdx.x; e < rem * rem; e += blockDim.x) {
+      const int a = j + 1 + e % rem, b = j + 1 + e / rem;
+      if (a <= b) A[a][b] -= A[j][a] * A[j][b];
+    }
+    __syncthreads();
+  }
+  // zero the lower triangle of R
+  for (int e = threadIdx.x; e < l * l; e += blockDim.x) {
+    const int a = e % l, b = e / l;
+    if (a > b) R[a + l * b] = 0.0;
+  }
+  if (job.R && pass == 2) {
+    __syncthreads();
+    // R = R3 R2 R1 (upper triangular products)
+    const double* R1 = job.Rk;
+    const double* R2 = job.Rk + (size_t)l * l;
+    const double* R3 = job.Rk + 2 * (size_t)l * l;
+    for (int e = threadIdx.x; e < l * l; e += blockDim.x) {
+      const int a = e % l, b = e / l;
+      double acc = 0.0;
+      for (int k = a; k <= b; ++k) {
+        double t = 0.0;
+        for (int q = k; q <= b; ++q) t = fma(R2[k + l * q], R1[q + l * b], t);
+        acc = fma(R3[a + l * k], t, acc);
+      }
+      job.R[e] = (a <= b) ? acc : 0.0;
+    }
+  }
+}
+
+// W_out[r, :] = W_in[r, :] R^{-1}, one row per thread (forward substitution).
+template <bool FROM_INPUT, bool TO_Q>
+__global__ void __launch_bounds__(kCqrRows) cqr_solve_kernel(const CqrJob* __restrict__ jobs,
+                                                             int pass) {
+  const CqrJob job = jobs[blockIdx.y];
+  const int l = job.l;
+  const int64_t r = (int64_t)blockIdx.x * kCqrRows + threadIdx.x;
+  __shared__ double R[kCqrMaxL][kCqrMaxL + 1];
+  const double* Rg = job.Rk + (size_t)pass * l * l;
+  for (int e = threadIdx.x; e < l * l; e += blockDim.x) R[e % l][e / l] = Rg[e];
+  __syncthreads();
+  if (r >= job.m) return;
+  double x[kCqrMaxL];
+#pragma unroll
+  for (int j = 0; j < kCqrMaxL; ++j) {
+    if (j < l) {
+      const int64_t idx = r + job.m * j;
+      double v;
+      if (FROM_INPUT)
+        v = job.Y64 ? job.Y64[idx] : (double)job.Y[idx];
+      else
+        v = job.W[idx];
+#pragma unroll
+      for (int k = 0; k < j; ++k) v = fma(-x[k], R[k][j], v);
+      x[j] = v / R[j][j];
+    }
+  }
+  double* out = TO_Q ? job.Q : job.W;
+  const bool zero = TO_Q && *job.zero;  // Q of a zero matrix: [I; 0]
+#pragma unroll
+  for (int j = 0; j < kCqrMaxL; ++j)
+    if (j < l) out[r + job.m * j] = zero ? (r == j ? 1.0 : 0.0) : x[j];
+}
+
 int grid_for(int64_t n, int threads, int cap = 8192) {
   int64_t g = (n + threads - 1) / threads;
   return (int)std::max<int64_t>(1, std::min<int64_t>(g, cap));
@@ -351,11 +532,63 @@ void qr_householder_f64(const QrJob* jobs, int count, int* status) {
     KRP_REQUIRE(jobs[b].l <= kQrMaxL, "QR supports l <= %d", kQrMaxL);
   }
   Ctx* c = current();
-  QrJob* d_jobs = c->ws.take<QrJob>(count);
-  KRP_CUDA_CHECK(cudaMemcpyAsync(d_jobs, jobs, sizeof(QrJob) * count, cudaMemcpyHostToDevice,
-                                 stream()));
-  qr_kernel<<<count, kQrThreads, 0, stream()>>>(d_jobs, status);
-  check_launch("qr_householder_f64");
+  // narrow sketches (l <= 64): shifted CholeskyQR3 over many SMs; wider ones:
+  // one-CTA Householder
+  std::vector<QrJob> hh;
+  std::vector<CqrJob> cq;
+  int64_t maxm = 0;
+  for (int b = 0; b < count; ++b) {
+    const QrJob& j = jobs[b];
+    if (j.l > kCqrMaxL) {
+      hh.push_back(j);
+      continue;
+    }
+    CqrJob q{};
+    q.Y = j.Y;
+    q.Y64 = j.Y64;
+    q.W = j.work;
+    q.Q = j.Q;
+    q.R = j.R;
+    q.m = j.m;
+    q.l = j.l;
+    q.G = c->ws.take<double>((size_t)j.l * j.l);
+    q.Rk = c->ws.take<double>((size_t)3 * j.l * j.l);
+    q.zero = c->ws.take<int>(1);
+    cq.push_back(q);
+    maxm = std::max<int64_t>(maxm, j.m);
+  }
+  if (!hh.empty()) {
+    QrJob* d_jobs = c->ws.take<QrJob>(hh.size());
+    KRP_CUDA_CHECK(cudaMemcpyAsync(d_jobs, hh.data(), sizeof(QrJob) * hh.size(),
+                                   cudaMemcpyHostToDevice, stream()));
+    qr_kernel<<<(int)hh.size(), kQrThreads, 0, stream()>>>(d_jobs, status);
+    check_launch("qr_householder_f64");
+  }
+  if (!cq.empty()) {
+    const int nq = (int)cq.size();
+    CqrJob* d_cq = c->ws.take<CqrJob>(nq);
+    KRP_CUDA_CHECK(cudaMemcpyAsync(d_cq, cq.data(), sizeof(CqrJob) * nq, cudaMemcpyHostToDevice,
+                                   stream()));
+    const dim3 g((unsigned)((maxm + kCqrRows - 1) / kCqrRows), (unsigned)nq);
+    for (int pass = 0; pass < 3; ++pass) {
+      for (const CqrJob& q : cq)
+        KRP_CUDA_CHECK(cudaMemsetAsync(q.G, 0, sizeof(double) * q.l * q.l, stream()));
+      if (pass == 0)
+        cqr_gram_kernel<true><<<g, 256, 0, stream()>>>(d_cq, status);
+      else
+        cqr_gram_kernel<false><<<g, 256, 0, stream()>>>(d_cq, status);
+      check_launch("cholqr_gram_f64");
+      cqr_chol_kernel<<<nq, 256, 0, stream()>>>(d_cq, pass);
+      check_launch("cholqr_chol_f64");
+      if (pass == 0)
+        cqr_solve_kernel<true, false><<<g, kCqrRows, 0, stream()>>>(d_cq, pass);
+      else if (pass == 1)
+        cqr_solve_kernel<false, false><<<g, kCqrRows, 0, stream()>>>(d_cq, pass);
+      else
+        cqr_solve_kernel<false, true><<<g, kCqrRows, 0, stream()>>>(d_cq, pass);
+      check_launch("cholqr_solve_f64");
+    }
+  }
 }
 
 void gram_mode_f64(const double* G, int D, const int64_t* dims, int mode, double* S) {

@@ -1,20 +1,665 @@
-// BF16 tensor-core (tcgen05) kernels: placeholder until the sm_103a kernels land.
+// BF16 tensor-core contractions over the big tensor on sm_103a: tcgen05.mma
+// (kind::f16, BF16 operands, FP32 accumulators in TMEM) fed by TMA
+// (cp.async.bulk.tensor, 128-byte swizzle) through an mbarrier pipeline.
+//
+//   tc_gemm_tn_bf16:       out[s, k] = sum_i X[i, s] F[i, k]
+//       (TTM of the fastest mode, Sec. 2.1; A = X is K-major: i contiguous)
+//   tc_mttkrp_first_bf16:  Y[i, k] = sum_t w[t, k] sum_{i2} X[i, i2, t] Om2[i2, k]
+//       (mode-1 MTTKRP, Alg. 7: the contraction against one factor is the MMA,
+//        A = X is MN-major: i contiguous; the remaining Khatri-Rao factors enter
+//        as the per-slab weights w[t, :] applied to the TMEM result)
+//
+// Both kernels are persistent (one CTA per SM) and warp-specialised:
+//   warp 0: TMA producer (one elected lane), warp 1: TMEM allocator + MMA
+//   issuer (one elected lane), warps 2-5: epilogue (TMEM -> registers -> HBM).
+// Accumulators are double-buffered in TMEM so the epilogue of one tile
+// overlaps the MMAs of the next.  Every mbarrier wait is bounded (1 s of
+// %globaltimer); on expiry the kernel raises KRP_ETIMEOUT in the status word,
+// drains its own TMA loads and MMAs (bounded again), frees TMEM and returns.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+#include <algorithm>
+#include <mutex>
+
 #include "pipeline.h"
 
 namespace krp {
+namespace {
 
-bool tc_available() { return false; }
+constexpr uint64_t kWaitNs = 1000000000ull;  // 1 s per wait
+constexpr int kThreads = 192;                // 6 warps
+constexpr int kBM = 128;                     // rows per tile (TMEM lanes)
+constexpr int kBK = 64;                      // K elements per stage (128 B of BF16)
 
-size_t tc_workspace_bytes(int64_t, int64_t, int) { return 0; }
-
-void tc_gemm_tn_bf16(const __nv_bfloat16*, int64_t, int64_t, const __nv_bfloat16*,
-                     const __nv_bfloat16*, int, float*) {
-  fail(KRP_EUNSUPPORTED, "BF16 tensor-core contraction not built yet");
+// ------------------------------------------------------------ PTX helpers ---
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ uint64_t gtime() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+__device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Bounded wait for the phase with the given parity; false on timeout/abort.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort_flag) {
+  if (mbar_try(bar, parity)) return true;
+  const uint64_t t0 = gtime();
+  for (;;) {
+    if (mbar_try(bar, parity)) return true;
+    if (*abort_flag) return false;
+    if (gtime() - t0 > kWaitNs) return false;
+  }
+}
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, uint32_t bar,
+                                            int c0, int c1) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%3, %4}], [%2];" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(bar), "r"(c0), "r"(c1)
+      : "memory");
+}
+__device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap* map, uint32_t bar,
+                                            int c0, int c1, int c2) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%3, %4, %5}], [%2];" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(bar), "r"(c0), "r"(c1), "r"(c2)
+      : "memory");
+}
+__device__ __forceinline__ void tmem_alloc(uint32_t dst_smem, uint32_t ncols) {
+  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(dst_smem),
+               "r"(ncols)
+               : "memory");
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols)
+               : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void mma_bf16(uint32_t dtmem, uint64_t adesc, uint64_t bdesc,
+                                         uint32_t idesc, uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(dtmem),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+__device__ __forceinline__ void mma_commit(uint32_t bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                   bar)
+               : "memory");
+}
+// 32 lanes x 16 consecutive 32-bit columns per warp.
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+      "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+        "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
-void tc_mttkrp_first_bf16(const __nv_bfloat16*, int64_t, int64_t, int64_t, const __nv_bfloat16*,
-                          const float*, int, float*) {
-  fail(KRP_EUNSUPPORTED, "BF16 tensor-core MTTKRP not built yet");
+// Shared-memory matrix descriptor, 128-byte swizzle (sm_100 layout):
+// start>>4 [0,14), leading-byte-offset>>4 [16,30), stride-byte-offset>>4
+// [32,46), version 1 at [46,48), layout SWIZZLE_128B (=2) at [61,64).
+__device__ __forceinline__ uint64_t sdesc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+  uint64_t d = 0;
+  d |= static_cast<uint64_t>((addr & 0x3FFFFu) >> 4);
+  d |= static_cast<uint64_t>((lbo >> 4) & 0x3FFFu) << 16;
+  d |= static_cast<uint64_t>((sbo >> 4) & 0x3FFFu) << 32;
+  d |= static_cast<uint64_t>(1) << 46;
+  d |= static_cast<uint64_t>(2) << 61;
+  return d;
+}
+// Instruction descriptor of kind::f16: D FP32, A/B BF16, M x N, majorness.
+__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N, bool a_mn, bool b_mn) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((a_mn ? 1u : 0u) << 15) | ((b_mn ? 1u : 0u) << 16) |
+         (static_cast<uint32_t>(N >> 3) << 17) | (static_cast<uint32_t>(M >> 4) << 24);
+}
+
+struct Bars {
+  uint64_t full[8];
+  uint64_t empty[8];
+  uint64_t tfull[2];
+  uint64_t tempty[2];
+  uint64_t drain;
+  uint32_t tmem_base;
+  int abort_flag;
+  int issued;    // TMA loads issued (producer)
+  int consumed;  // stages consumed by the MMA warp
+};
+
+__device__ __forceinline__ void raise_timeout(Bars* b, int* status) {
+  b->abort_flag = 1;
+  atomicExch(status, static_cast<int>(KRP_ETIMEOUT));
+}
+
+// Producer-side drain after an abort: wait (bounded) for every TMA load that
+// was issued but not consumed, so no copy lands in shared memory after exit.
+template <int NS>
+__device__ void drain_loads(Bars* b) {
+  int dummy = 0;
+  for (int j = b->consumed; j < b->issued; ++j) {
+    const int st = j % NS;
+    const uint32_t ph = (j / NS) & 1;
+    mbar_wait(smem_u32(&b->full[st]), ph, reinterpret_cast<volatile int*>(&dummy));
+  }
+}
+
+// ----------------------------------------------------------------------------
+// out[s + S*k] = sum_i X[i + n1*s] F[i, k] (+ lo part at column Lp + k)
+// A tile: 128 rows (s) x 64 K (i), box of mapA = {64, 128}.  B: mapB over the
+// combined factor buffer (K = n1p contiguous, rows = N columns of F).
+template <int N, int NS>
+__global__ void __launch_bounds__(kThreads, 1)
+    tc_gemm_tn_kernel(const __grid_constant__ CUtensorMap mapA,
+                      const __grid_constant__ CUtensorMap mapB, int64_t S, int kchunks, int L,
+                      int Lp, int has_lo, float* __restrict__ out, int* status) {
+  constexpr uint32_t kABytes = kBM * kBK * 2;  // 16 KB
+  constexpr uint32_t kBBytes = N * kBK * 2;
+  constexpr uint32_t kStage = kABytes + kBBytes;
+  constexpr uint32_t kTmemCols = (2 * N <= 32) ? 32 : (2 * N <= 64) ? 64 : (2 * N <= 128) ? 128 : (2 * N <= 256) ? 256 : 512;
+  constexpr uint32_t kIdesc = idesc_bf16(kBM, N, false, false);
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  Bars* bars = reinterpret_cast<Bars*>(smem + NS * kStage);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t tiles = (S + kBM - 1) / kBM;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < NS; ++s) {
+      mbar_init(smem_u32(&bars->full[s]), 1);
+      mbar_init(smem_u32(&bars->empty[s]), 1);
+    }
+    for (int a = 0; a < 2; ++a) {
+      mbar_init(smem_u32(&bars->tfull[a]), 1);
+      mbar_init(smem_u32(&bars->tempty[a]), 4);
+    }
+    mbar_init(smem_u32(&bars->drain), 1);
+    bars->abort_flag = 0;
+    bars->issued = 0;
+    bars->consumed = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  if (warp == 1) tmem_alloc(smem_u32(&bars->tmem_base), kTmemCols);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = bars->tmem_base;
+  volatile int* abort_flag = &bars->abort_flag;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      int it = 0;
+      for (int64_t tile = blockIdx.x; tile < tiles && !*abort_flag; tile += gridDim.x) {
+        for (int kc = 0; kc < kchunks; ++kc, ++it) {
+          const int st = it % NS;
+          const uint32_t ph = (it / NS) & 1;
+          if (!mbar_wait(smem_u32(&bars->empty[st]), ph ^ 1, abort_flag)) {
+            raise_timeout(bars, status);
+            break;
+          }
+          const uint32_t a = smem_u32(smem + st * kStage);
+          const uint32_t fb = smem_u32(&bars->full[st]);
+          mbar_expect_tx(fb, kStage);
+          tma_load_2d(a, &mapA, fb, kc * kBK, static_cast<int>(tile * kBM));
+          tma_load_2d(a + kABytes, &mapB, fb, kc * kBK, 0);
+          bars->issued = it + 1;
+        }
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      int it = 0, tl = 0;
+      for (int64_t tile = blockIdx.x; tile < tiles && !*abort_flag; tile += gridDim.x, ++tl) {
+        const int acc = tl & 1;
+        const uint32_t aph = (tl >> 1) & 1;
+        if (!mbar_wait(smem_u32(&bars->tempty[acc]), aph ^ 1, abort_flag)) {
+          raise_timeout(bars, status);
+          break;
+        }
+        tc_fence_after();
+        const uint32_t dt = tmem + acc * N;
+        bool ok = true;
+        for (int kc = 0; kc < kchunks; ++kc, ++it) {
+          const int st = it % NS;
+          const uint32_t ph = (it / NS) & 1;
+          if (!mbar_wait(smem_u32(&bars->full[st]), ph, abort_flag)) {
+            raise_timeout(bars, status);
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const uint32_t a = smem_u32(smem + st * kStage);
+          const uint32_t b = a + kABytes;
+#pragma unroll
+          for (int k = 0; k < kBK / 16; ++k)
+            mma_bf16(dt, sdesc(a + 32 * k, 16, 1024), sdesc(b + 32 * k, 16, 1024), kIdesc,
+                     (kc | k) != 0);
+          mma_commit(smem_u32(&bars->empty[st]));
+          bars->consumed = it + 1;
+        }
+        if (!ok) break;
+        mma_commit(smem_u32(&bars->tfull[acc]));
+      }
+      // all MMAs issued by this thread have completed once this commit fires
+      mma_commit(smem_u32(&bars->drain));
+      int dummy = 0;
+      mbar_wait(smem_u32(&bars->drain), 0, reinterpret_cast<volatile int*>(&dummy));
+    }
+  } else {
+    const int q = warp & 3;  // TMEM lane quarter of this warp
+    int tl = 0;
+    for (int64_t tile = blockIdx.x; tile < tiles; tile += gridDim.x, ++tl) {
+      const int acc = tl & 1;
+      const uint32_t ph = (tl >> 1) & 1;
+      if (!mbar_wait(smem_u32(&bars->tfull[acc]), ph, abort_flag)) {
+        if (lane == 0) raise_timeout(bars, status);
+        break;
+      }
+      tc_fence_after();
+      const int row = q * 32 + lane;
+      const int64_t s = tile * kBM + row;
+      const uint32_t base = tmem + (static_cast<uint32_t>(q * 32) << 16) + acc * N;
+      for (int c0 = 0; c0 < Lp; c0 += 16) {
+        float v[16];
+        tmem_ld16(base + c0, v);
+        if (has_lo) {
+          float w[16];
+          tmem_ld16(base + Lp + c0, w);
+#pragma unroll
+          for (int j = 0; j < 16; ++j) v[j] += w[j];
+        }
+        if (s < S) {
+#pragma unroll
+          for (int j = 0; j < 16; ++j)
+            if (c0 + j < L) out[s + S * (c0 + j)] = v[j];
+        }
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(smem_u32(&bars->tempty[acc]));
+    }
+  }
+  __syncthreads();
+  if (warp == 0 && lane == 0 && bars->abort_flag) drain_loads<NS>(bars);
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    tmem_dealloc(tmem, kTmemCols);
+  }
+}
+
+// ----------------------------------------------------------------------------
+// Y[i + n1*k] += sum_{t in range} w[t + T*k] * D_t[i, k],
+// D_t[i, k] = sum_{i2} X[i, i2, t] Om2[i2, k]   (MN-major A, two 64-row boxes)
+template <int N, int NS>
+__global__ void __launch_bounds__(kThreads, 1)
+    tc_mttkrp_kernel(const __grid_constant__ CUtensorMap mapX,
+                     const __grid_constant__ CUtensorMap mapB, int64_t n1, int64_t T, int kchunks,
+                     int mblocks, int64_t t_per_cta, const float* __restrict__ w, int L,
+                     float* __restrict__ Y, int* status) {
+  constexpr uint32_t kBox = 64 * kBK * 2;  // 64 (i) x 64 (i2) BF16 = 8 KB
+  constexpr uint32_t kABytes = 2 * kBox;
+  constexpr uint32_t kBBytes = N * kBK * 2;
+  constexpr uint32_t kStage = kABytes + kBBytes;
+  constexpr uint32_t kTmemCols = (2 * N <= 32) ? 32 : (2 * N <= 64) ? 64 : (2 * N <= 128) ? 128 : (2 * N <= 256) ? 256 : 512;
+  constexpr uint32_t kIdesc = idesc_bf16(kBM, N, true, false);
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  Bars* bars = reinterpret_cast<Bars*>(smem + NS * kStage);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int mb = blockIdx.x % mblocks;
+  const int64_t t0 = static_cast<int64_t>(blockIdx.x / mblocks) * t_per_cta;
+  const int64_t t1 = min(T, t0 + t_per_cta);
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < NS; ++s) {
+      mbar_init(smem_u32(&bars->full[s]), 1);
+      mbar_init(smem_u32(&bars->empty[s]), 1);
+    }
+    for (int a = 0; a < 2; ++a) {
+      mbar_init(smem_u32(&bars->tfull[a]), 1);
+      mbar_init(smem_u32(&bars->tempty[a]), 4);
+    }
+    mbar_init(smem_u32(&bars->drain), 1);
+    bars->abort_flag = 0;
+    bars->issued = 0;
+    bars->consumed = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  if (warp == 1) tmem_alloc(smem_u32(&bars->tmem_base), kTmemCols);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = bars->tmem_base;
+  volatile int* abort_flag = &bars->abort_flag;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      int it = 0;
+      for (int64_t t = t0; t < t1 && !*abort_flag; ++t) {
+        for (int kc = 0; kc < kchunks; ++kc, ++it) {
+          const int st = it % NS;
+          const uint32_t ph = (it / NS) & 1;
+          if (!mbar_wait(smem_u32(&bars->empty[st]), ph ^ 1, abort_flag)) {
+            raise_timeout(bars, status);
+            break;
+          }
+          const uint32_t a = smem_u32(smem + st * kStage);
+          const uint32_t fb = smem_u32(&bars->full[st]);
+          mbar_expect_tx(fb, kStage);
+          tma_load_3d(a, &mapX, fb, mb * kBM, kc * kBK, static_cast<int>(t));
+          tma_load_3d(a + kBox, &mapX, fb, mb * kBM + 64, kc * kBK, static_cast<int>(t));
+          tma_load_2d(a + kABytes, &mapB, fb, kc * kBK, 0);
+          bars->issued = it + 1;
+        }
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      int it = 0, tl = 0;
+      for (int64_t t = t0; t < t1 && !*abort_flag; ++t, ++tl) {
+        const int acc = tl & 1;
+        const uint32_t aph = (tl >> 1) & 1;
+        if (!mbar_wait(smem_u32(&bars->tempty[acc]), aph ^ 1, abort_flag)) {
+          raise_timeout(bars, status);
+          break;
+        }
+        tc_fence_after();
+        const uint32_t dt = tmem + acc * N;
+        bool ok = true;
+        for (int kc = 0; kc < kchunks; ++kc, ++it) {
+          const int st = it % NS;
+          const uint32_t ph = (it / NS) & 1;
+          if (!mbar_wait(smem_u32(&bars->full[st]), ph, abort_flag)) {
+            raise_timeout(bars, status);
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const uint32_t a = smem_u32(smem + st * kStage);
+          const uint32_t b = a + kABytes;
+          // A (MN-major): 8-row K groups 1024 B apart, the two 64-wide M atoms
+          // kBox apart; each MMA (K = 16) spans two K groups.
+#pragma unroll
+          for (int k = 0; k < kBK / 16; ++k)
+            mma_bf16(dt, sdesc(a + 2048 * k, kBox, 1024), sdesc(b + 32 * k, 16, 1024), kIdesc,
+                     (kc | k) != 0);
+          mma_commit(smem_u32(&bars->empty[st]));
+          bars->consumed = it + 1;
+        }
+        if (!ok) break;
+        mma_commit(smem_u32(&bars->tfull[acc]));
+      }
+      mma_commit(smem_u32(&bars->drain));
+      int dummy = 0;
+      mbar_wait(smem_u32(&bars->drain), 0, reinterpret_cast<volatile int*>(&dummy));
+    }
+  } else {
+    const int q = warp & 3;
+    const int row = q * 32 + lane;
+    const int64_t i = static_cast<int64_t>(mb) * kBM + row;
+    float accum[N];
+#pragma unroll
+    for (int k = 0; k < N; ++k) accum[k] = 0.f;
+    int tl = 0;
+    for (int64_t t = t0; t < t1; ++t, ++tl) {
+      const int acc = tl & 1;
+      const uint32_t ph = (tl >> 1) & 1;
+      if (!mbar_wait(smem_u32(&bars->tfull[acc]), ph, abort_flag)) {
+        if (lane == 0) raise_timeout(bars, status);
+        break;
+      }
+      tc_fence_after();
+      const uint32_t base = tmem + (static_cast<uint32_t>(q * 32) << 16) + acc * N;
+#pragma unroll
+      for (int c0 = 0; c0 < N; c0 += 16) {
+        float v[16];
+        tmem_ld16(base + c0, v);
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+          const int k = c0 + j;
+          const float wk = (k < L) ? __ldg(w + t + T * k) : 0.f;
+          accum[k] = fmaf(wk, v[j], accum[k]);
+        }
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(smem_u32(&bars->tempty[acc]));
+    }
+    if (i < n1) {
+#pragma unroll
+      for (int k = 0; k < N; ++k)
+        if (k < L) atomicAdd(Y + i + n1 * k, accum[k]);
+    }
+  }
+  __syncthreads();
+  if (warp == 0 && lane == 0 && bars->abort_flag) drain_loads<NS>(bars);
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    tmem_dealloc(tmem, kTmemCols);
+  }
+}
+
+// combined factor buffer Fc[r * n1p + i], r < N: hi rows 0..L-1, lo rows
+// Lp..Lp+L-1, zeros elsewhere and for i >= n1.
+__global__ void pack_factor_kernel(const __nv_bfloat16* __restrict__ hi,
+                                   const __nv_bfloat16* __restrict__ lo, int64_t n1, int64_t n1p,
+                                   int L, int Lp, int N, __nv_bfloat16* __restrict__ out) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n1p * N;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = e % n1p;
+    const int r = static_cast<int>(e / n1p);
+    __nv_bfloat16 v = __float2bfloat16_rn(0.f);
+    if (i < n1) {
+      if (r < L)
+        v = hi[i + n1 * r];
+      else if (lo && r >= Lp && r - Lp < L)
+        v = lo[i + n1 * (r - Lp)];
+    }
+    out[e] = v;
+  }
+}
+
+// ------------------------------------------------------------- host side ----
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPoint("cuTensorMapEncodeTiled", &p, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    cudaGetLastError();
+  });
+  if (!fn) fail(KRP_ECUDA, "cuTensorMapEncodeTiled is unavailable");
+  return fn;
+}
+
+CUtensorMap make_map(const void* base, int rank, const uint64_t* dims, const uint64_t* strides_bytes,
+                     const uint32_t* box) {
+  CUtensorMap m;
+  uint32_t estr[3] = {1, 1, 1};
+  const CUresult r = encode_fn()(&m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, rank, const_cast<void*>(base),
+                                 dims, strides_bytes, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                                 CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                                 CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) fail(KRP_ECUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
+  return m;
+}
+
+int round_up(int64_t v, int64_t m) { return static_cast<int>((v + m - 1) / m * m); }
+
+template <class K>
+void set_smem(K kernel, size_t bytes) {
+  KRP_CUDA_CHECK(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      static_cast<int>(bytes)));
+}
+
+template <int N>
+void launch_gemm_tn(const CUtensorMap& ma, const CUtensorMap& mb, int64_t S, int kchunks, int L,
+                    int Lp, int has_lo, float* out) {
+  constexpr int NS = (N <= 64) ? 8 : (N <= 128 ? 6 : 4);
+  const size_t smem = 1024 + NS * (size_t)(kBM * kBK * 2 + N * kBK * 2) + sizeof(Bars) + 64;
+  set_smem(tc_gemm_tn_kernel<N, NS>, smem);
+  const int64_t tiles = (S + kBM - 1) / kBM;
+  const int grid = static_cast<int>(std::min<int64_t>(tiles, current()->num_sms));
+  tc_gemm_tn_kernel<N, NS><<<grid, kThreads, smem, stream()>>>(ma, mb, S, kchunks, L, Lp, has_lo, out,
+                                                               current()->d_status);
+  check_launch("tc_gemm_tn_bf16");
+}
+
+template <int N>
+void launch_mttkrp(const CUtensorMap& mx, const CUtensorMap& mb, int64_t n1, int64_t T, int kchunks,
+                   const float* w, int L, float* Y) {
+  constexpr int NS = (N <= 64) ? 8 : 6;
+  const size_t smem = 1024 + NS * (size_t)(2 * 64 * kBK * 2 + N * kBK * 2) + sizeof(Bars) + 64;
+  set_smem(tc_mttkrp_kernel<N, NS>, smem);
+  const int mblocks = static_cast<int>((n1 + kBM - 1) / kBM);
+  const int sms = current()->num_sms;
+  int64_t chunks = std::max<int64_t>(1, sms / mblocks);
+  chunks = std::min<int64_t>(chunks, T);
+  const int64_t per = (T + chunks - 1) / chunks;
+  chunks = (T + per - 1) / per;
+  const int grid = static_cast<int>(mblocks * chunks);
+  tc_mttkrp_kernel<N, NS><<<grid, kThreads, smem, stream()>>>(mx, mb, n1, T, kchunks, mblocks, per,
+                                                              w, L, Y, current()->d_status);
+  check_launch("tc_mttkrp_bf16");
+}
+
+}  // namespace
+
+bool tc_available() { return true; }
+
+size_t tc_workspace_bytes(int64_t n1, int64_t S, int L) {
+  (void)S;
+  const int64_t n1p = (n1 + 63) / 64 * 64;
+  const int64_t Lp = (L + 15) / 16 * 16;
+  return ws_bytes((size_t)n1p * 2 * Lp, 2) + ws_bytes((size_t)(n1p + 64) * Lp * 2, 2) + (1 << 16);
+}
+
+void tc_gemm_tn_bf16(const __nv_bfloat16* X, int64_t n1, int64_t S, const __nv_bfloat16* Fhi,
+                     const __nv_bfloat16* Flo, int L, float* out) {
+  KRP_REQUIRE(n1 % 8 == 0, "BF16 tensor-core path needs n_1 %% 8 == 0 (n_1 = %lld)", (long long)n1);
+  KRP_REQUIRE((reinterpret_cast<uintptr_t>(X) & 15) == 0, "X must be 16-byte aligned");
+  KRP_REQUIRE(S < (int64_t(1) << 31), "too many rows for the TMA coordinates");
+  const int Lp = round_up(L, 16);
+  const int N = Flo ? 2 * Lp : Lp;
+  KRP_REQUIRE(N <= 256, "sketch width too large for one MMA (L = %d)", L);
+  const int64_t n1p = round_up(n1, 64);
+  Ctx* c = current();
+  __nv_bfloat16* Fc = c->ws.take<__nv_bfloat16>((size_t)n1p * N);
+  const int64_t tot = n1p * N;
+  pack_factor_kernel<<<(int)std::min<int64_t>((tot + 255) / 256, 4096), 256, 0, stream()>>>(
+      Fhi, Flo, n1, n1p, L, Lp, N, Fc);
+  check_launch("pack_factor");
+  const uint64_t adims[2] = {(uint64_t)n1, (uint64_t)S};
+  const uint64_t astr[1] = {(uint64_t)n1 * 2};
+  const uint32_t abox[2] = {kBK, kBM};
+  const CUtensorMap ma = make_map(X, 2, adims, astr, abox);
+  const uint64_t bdims[2] = {(uint64_t)n1p, (uint64_t)N};
+  const uint64_t bstr[1] = {(uint64_t)n1p * 2};
+  const uint32_t bbox[2] = {kBK, (uint32_t)N};
+  const CUtensorMap mb = make_map(Fc, 2, bdims, bstr, bbox);
+  const int kchunks = static_cast<int>((n1 + kBK - 1) / kBK);
+  const int has_lo = Flo ? 1 : 0;
+  switch (N) {
+    case 16: launch_gemm_tn<16>(ma, mb, S, kchunks, L, Lp, has_lo, out); break;
+    case 32: launch_gemm_tn<32>(ma, mb, S, kchunks, L, Lp, has_lo, out); break;
+    case 48: launch_gemm_tn<48>(ma, mb, S, kchunks, L, Lp, has_lo, out); break;
+    case 64: launch_gemm_tn<64>(ma, mb, S, kchunks, L, Lp, has_lo, out); break;
+    case 96: launch_gemm_tn<96>(ma, mb, S, kchunks, L, Lp, has_lo, out); break;
+    case 128: launch_gemm_tn<128>(ma, mb, S, kchunks, L, Lp, has_lo, out); break;
+    case 160: launch_gemm_tn<160>(ma, mb, S, kchunks, L, Lp, has_lo, out); break;
+    case 192: launch_gemm_tn<192>(ma, mb, S, kchunks, L, Lp, has_lo, out); break;
+    case 224: launch_gemm_tn<224>(ma, mb, S, kchunks, L, Lp, has_lo, out); break;
+    case 256: launch_gemm_tn<256>(ma, mb, S, kchunks, L, Lp, has_lo, out); break;
+    default:
+      if (N == 80) launch_gemm_tn<80>(ma, mb, S, kchunks, L, Lp, has_lo, out);
+      else if (N == 112) launch_gemm_tn<112>(ma, mb, S, kchunks, L, Lp, has_lo, out);
+      else if (N == 144) launch_gemm_tn<144>(ma, mb, S, kchunks, L, Lp, has_lo, out);
+      else if (N == 176) launch_gemm_tn<176>(ma, mb, S, kchunks, L, Lp, has_lo, out);
+      else if (N == 208) launch_gemm_tn<208>(ma, mb, S, kchunks, L, Lp, has_lo, out);
+      else if (N == 240) launch_gemm_tn<240>(ma, mb, S, kchunks, L, Lp, has_lo, out);
+      else fail(KRP_EUNSUPPORTED, "unsupported MMA width %d", N);
+  }
+}
+
+void tc_mttkrp_first_bf16(const __nv_bfloat16* X, int64_t n1, int64_t n2, int64_t T,
+                          const __nv_bfloat16* Om2, const float* w, int L, float* Y) {
+  KRP_REQUIRE(n1 % 8 == 0, "BF16 tensor-core path needs n_1 %% 8 == 0 (n_1 = %lld)", (long long)n1);
+  KRP_REQUIRE((reinterpret_cast<uintptr_t>(X) & 15) == 0, "X must be 16-byte aligned");
+  KRP_REQUIRE(T < (int64_t(1) << 31) && n2 < (int64_t(1) << 31), "tensor too large for TMA");
+  const int Lp = round_up(L, 16);
+  KRP_REQUIRE(Lp <= 128, "sketch width too large (L = %d)", L);
+  const int64_t n2p = round_up(n2, 64);
+  Ctx* c = current();
+  __nv_bfloat16* Bc = c->ws.take<__nv_bfloat16>((size_t)n2p * Lp);
+  const int64_t tot = n2p * Lp;
+  pack_factor_kernel<<<(int)std::min<int64_t>((tot + 255) / 256, 4096), 256, 0, stream()>>>(
+      Om2, nullptr, n2, n2p, L, Lp, Lp, Bc);
+  check_launch("pack_factor");
+  KRP_CUDA_CHECK(cudaMemsetAsync(Y, 0, sizeof(float) * n1 * L, stream()));
+  const uint64_t xdims[3] = {(uint64_t)n1, (uint64_t)n2, (uint64_t)T};
+  const uint64_t xstr[2] = {(uint64_t)n1 * 2, (uint64_t)n1 * n2 * 2};
+  const uint32_t xbox[3] = {64, kBK, 1};
+  const CUtensorMap mx = make_map(X, 3, xdims, xstr, xbox);
+  const uint64_t bdims[2] = {(uint64_t)n2p, (uint64_t)Lp};
+  const uint64_t bstr[1] = {(uint64_t)n2p * 2};
+  const uint32_t bbox[2] = {kBK, (uint32_t)Lp};
+  const CUtensorMap mb = make_map(Bc, 2, bdims, bstr, bbox);
+  const int kchunks = static_cast<int>((n2 + kBK - 1) / kBK);
+  switch (Lp) {
+    case 16: launch_mttkrp<16>(mx, mb, n1, T, kchunks, w, L, Y); break;
+    case 32: launch_mttkrp<32>(mx, mb, n1, T, kchunks, w, L, Y); break;
+    case 48: launch_mttkrp<48>(mx, mb, n1, T, kchunks, w, L, Y); break;
+    case 64: launch_mttkrp<64>(mx, mb, n1, T, kchunks, w, L, Y); break;
+    case 80: launch_mttkrp<80>(mx, mb, n1, T, kchunks, w, L, Y); break;
+    case 96: launch_mttkrp<96>(mx, mb, n1, T, kchunks, w, L, Y); break;
+    case 112: launch_mttkrp<112>(mx, mb, n1, T, kchunks, w, L, Y); break;
+    case 128: launch_mttkrp<128>(mx, mb, n1, T, kchunks, w, L, Y); break;
+    default: fail(KRP_EUNSUPPORTED, "unsupported sketch width %d", L);
+  }
 }
 
 }  // namespace krp

@@ -1,0 +1,143 @@
+"""BF16 tensor-core (tcgen05) path: parity against the oracle on BF16-rounded data.
+
+The oracle sees exactly the BF16 values the GPU streams (X and factors rounded
+RN-even from FP32), so products are exact on both sides and only FP32
+accumulation differs: sketches keep the 1e-5 bound.  The core uses Q_1 split
+into a BF16 hi/lo pair (|Q - hi - lo| <= 2^-17 |Q|), so the core and the
+reconstruction get a bound derived from that split: 3e-5 (core, relative) and
+5e-5 (reconstruction relative to ||X||).
+"""
+
+import numpy as np
+import pytest
+
+from tests.gpu_util import (require_gpu, dev, mat_to_dev, mat_from_dev, empty_mat,
+                            tensor_to_dev, tensor_from_dev, rel)
+from oracle import linalg as L, philox, tensor as T, tucker as TK
+from synth import TuckerSpec, tucker_tensor
+
+pytestmark = pytest.mark.gpu
+
+CASES = [((64, 48, 40), 5), ((128, 72, 33), 16), ((200, 200, 7), 30), ((256, 64, 16, 3), 12),
+         ((1024, 64, 5), 48), ((136, 40, 30), 64), ((8, 9, 10), 3), ((520, 130, 9), 20)]
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    require_gpu()
+    import paper_2507_23207_gb300 as K
+    c = K.Context(0)
+    yield c
+    c.close()
+
+
+def bf16_case(dims, ell, seed=1):
+    rng = np.random.default_rng(seed + sum(dims) + ell)
+    x = philox.round_to_bf16(np.asfortranarray(rng.standard_normal(dims)))
+    om = [philox.round_to_bf16(philox.gaussian_factor(9, j, 0, 0, n, ell))
+          for j, n in enumerate(dims)]
+    return x, om
+
+
+@pytest.mark.parametrize("dims,ell", CASES)
+def test_bf16_sketch_mode(ctx, dims, ell):
+    import torch
+    import paper_2507_23207_gb300 as K
+    x, om = bf16_case(dims, ell)
+    xd = tensor_to_dev(x, torch.bfloat16)
+    omd = [mat_to_dev(o, torch.bfloat16) for o in om]
+    for n in range(len(dims)):
+        y = empty_mat(dims[n], ell, torch.float32)
+        K.krp_sketch_mode(ctx, xd, dims, n, omd, ell, y)
+        torch.cuda.synchronize()
+        assert rel(mat_from_dev(y, dims[n], ell), T.mttkrp(x, om, n)) <= 1e-5, (dims, n)
+
+
+@pytest.mark.parametrize("dims,ell", CASES)
+def test_bf16_sketch_all_modes(ctx, dims, ell):
+    import torch
+    import paper_2507_23207_gb300 as K
+    x, om = bf16_case(dims, ell, seed=2)
+    xd = tensor_to_dev(x, torch.bfloat16)
+    omd = [mat_to_dev(o, torch.bfloat16) for o in om]
+    ys = [empty_mat(n, ell, torch.float32) for n in dims]
+    K.krp_sketch_all_modes(ctx, xd, dims, omd, ell, ys)
+    torch.cuda.synchronize()
+    for n in range(len(dims)):
+        assert rel(mat_from_dev(ys[n], dims[n], ell), T.mttkrp(x, om, n)) <= 1e-5, (dims, n)
+
+
+@pytest.mark.parametrize("dims,cols", [((64, 48, 40), (8, 6, 5)), ((1024, 64, 5), (48, 20, 5)),
+                                       ((200, 40, 30, 7), (30, 10, 9, 7)), ((16, 16, 16), (16, 16, 16))])
+def test_bf16_multi_ttm(ctx, dims, cols):
+    import torch
+    import paper_2507_23207_gb300 as K
+    rng = np.random.default_rng(5)
+    x = philox.round_to_bf16(np.asfortranarray(rng.standard_normal(dims)))
+    qs = [L.householder_qr(rng.standard_normal((n, c)))[0] for n, c in zip(dims, cols)]
+    g = torch.empty(int(np.prod(cols)), dtype=torch.float32, device=dev())
+    K.krp_multi_ttm(ctx, tensor_to_dev(x, torch.bfloat16), dims, [mat_to_dev(q, torch.float64) for q in qs],
+                    cols, g)
+    torch.cuda.synchronize()
+    assert rel(tensor_from_dev(g, cols), T.multi_ttm(x, [q.T for q in qs])) <= 3e-5
+
+
+SPECS = [TuckerSpec("b1", (64, 48, 40), (4, 4, 4), 1e-3, None, 41, (4, 4, 4), (8, 8, 8)),
+         TuckerSpec("b2", (128, 40, 24, 16), (3, 3, 3, 3), 1e-2, None, 43, (3, 3, 3, 3), (6, 6, 6, 6))]
+
+
+@pytest.mark.parametrize("spec", SPECS, ids=[s.name for s in SPECS])
+@pytest.mark.parametrize("variant", ["fresh", "memo", "sthosvd"])
+def test_bf16_tucker(ctx, spec, variant):
+    import torch
+    import paper_2507_23207_gb300 as K
+    x, _, _ = tucker_tensor(spec)
+    xb = philox.round_to_bf16(x)
+    p = spec.oversample
+    ells = [r + p for r in spec.ranks]
+    memo, seq = variant == "memo", variant == "sthosvd"
+    flags = (K.KRP_MEMO if memo else 0) | K.KRP_RESIDUAL
+    core = torch.empty(int(np.prod(ells)), dtype=torch.float32, device=dev())
+    facs = [torch.empty(n * l, dtype=torch.float64, device=dev()) for n, l in zip(spec.dims, ells)]
+    fn = K.krp_tucker_sthosvd if seq else K.krp_tucker_rhosvd
+    res = fn(ctx, tensor_to_dev(xb, torch.bfloat16), spec.dims, spec.ranks, p, 0, flags, core, facs)
+    torch.cuda.synchronize()
+    g = core.cpu().numpy().reshape(ells[::-1]).T.astype(np.float64)
+    qs = [f.cpu().numpy().reshape(l, n).T for f, n, l in zip(facs, spec.dims, ells)]
+    if seq:
+        # step 1 sketches the BF16 X with BF16 factors; later steps FP32 cores
+        ora = _sthosvd_bf16_first(xb, ells)
+    else:
+        ora = TK.rhosvd_krp(xb, ells, 0, memo=memo, omega_round="bf16")
+    nx = np.linalg.norm(xb)
+    for q in qs:
+        assert np.linalg.norm(q.T @ q - np.eye(q.shape[1])) <= 1e-12
+    d2 = np.linalg.norm(TK.reconstruct(g, qs) - TK.reconstruct(ora["G"], ora["Q"])) / nx
+    assert d2 <= 5e-5
+    assert abs(res["rel_residual"] - TK.rel_error(xb, ora["G"], ora["Q"])) <= 5e-5
+
+
+def _sthosvd_bf16_first(x, ells):
+    """Alg. 8 with the step-1 factors rounded to BF16 and later ones to FP32."""
+    g = x
+    qs, cores = [], [x]
+    for i in range(x.ndim):
+        om = TK.sthosvd_factors(0, g.shape, i, ells[i], omega_round="bf16" if i == 0 else "f32")
+        y = T.mttkrp(g, om, i)
+        q, _ = L.householder_qr(y)
+        g = T.ttm(g, q.T, i)
+        qs.append(q)
+        cores.append(g)
+    return {"G": g, "Q": qs}
+
+
+def test_bf16_requires_aligned_first_mode(ctx):
+    import torch
+    import paper_2507_23207_gb300 as K
+    dims, ell = (37, 8, 8), 4
+    x, om = bf16_case(dims, ell)
+    y = empty_mat(37, ell, torch.float32)
+    with pytest.raises(K.KrpError) as e:
+        K.krp_sketch_mode(ctx, tensor_to_dev(x, torch.bfloat16), dims, 0,
+                          [mat_to_dev(o, torch.bfloat16) for o in om], ell, y)
+    assert e.value.status == K.KRP_EINVAL

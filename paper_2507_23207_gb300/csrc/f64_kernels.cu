@@ -365,14 +365,33 @@ struct CqrJob {
   double* G;           // l x l Gram accumulator
   double* Rk;          // 3 x l x l upper factors of the passes
   double* R;           // optional product R3 R2 R1
-  int* zero;           // set when the input is exactly zero
+  unsigned long long* defmask;  // columns refilled in the current pass (bit j)
   int64_t m;
   int l;
 };
 
+// Deterministic pseudo-random entry used to refill a column whose pivot
+// collapsed (exactly dependent or zero column): the next pass orthonormalises
+// it against the others, completing the basis as Householder QR would.
+__device__ __forceinline__ double refill_value(int64_t r, int j) {
+  uint32_t h = static_cast<uint32_t>(r) * 0x9E3779B1u ^ static_cast<uint32_t>(j) * 0x85EBCA77u;
+  h ^= h >> 15;
+  h *= 0x2C1B3C6Du;
+  h ^= h >> 12;
+  h *= 0x297A2D39u;
+  h ^= h >> 15;
+  return (static_cast<double>(h) + 0.5) * 0x1p-32 - 0.5;
+}
+
+// Up to kCqrMaxBatch problems passed to the kernels by value.
+constexpr int kCqrMaxBatch = 8;
+struct CqrBatch {
+  CqrJob job[kCqrMaxBatch];
+};
+
 template <bool FROM_INPUT>
-__global__ void __launch_bounds__(256) cqr_gram_kernel(const CqrJob* __restrict__ jobs, int* status) {
-  const CqrJob job = jobs[blockIdx.y];
+__global__ void __launch_bounds__(256) cqr_gram_kernel(const CqrBatch jobs, int* status) {
+  const CqrJob job = jobs.job[blockIdx.y];
   const int64_t r0 = (int64_t)blockIdx.x * kCqrRows;
   if (r0 >= job.m) return;
   const int l = job.l;
@@ -413,41 +432,51 @@ __global__ void __launch_bounds__(256) cqr_gram_kernel(const CqrJob* __restrict_
 }
 
 // Cholesky G (+ shift) = R^T R of one l x l matrix per CTA; R stored in Rk[pass].
-__global__ void __launch_bounds__(256) cqr_chol_kernel(const CqrJob* __restrict__ jobs, int pass) {
-  const CqrJob job = jobs[blockIdx.x];
+__global__ void __launch_bounds__(256) cqr_chol_kernel(const CqrBatch jobs, int pass) {
+  const CqrJob job = jobs.job[blockIdx.x];
   const int l = job.l;
   __shared__ double A[kCqrMaxL][kCqrMaxL + 1];
-  __shared__ double piv;
-  __shared__ int zero_input;
+  __shared__ double diag0[kCqrMaxL];
+  __shared__ double piv, tol;
+  __shared__ int refill;
+  __shared__ unsigned long long mask;
   for (int e = threadIdx.x; e < l * l; e += blockDim.x) {
     const int a = e % l, b = e / l;
     A[a][b] = (a <= b) ? job.G[a + l * b] : job.G[b + l * a];
   }
   __syncthreads();
   if (threadIdx.x == 0) {
-    double tr = 0.0;
-    for (int j = 0; j < l; ++j) tr += A[j][j];
-    zero_input = !(tr > 0.0);
-    if (pass == 0) *job.zero = zero_input;
-    if (pass == 0 && !zero_input) {
+    double tr = 0.0, dmax = 0.0;
+    for (int j = 0; j < l; ++j) {
+      diag0[j] = A[j][j];
+      tr += A[j][j];
+      dmax = fmax(dmax, A[j][j]);
+    }
+    if (pass == 0) {
       // s = 11 (m l + l (l + 1)) u ||Y||^2 with ||Y||_F^2 >= ||Y||_2^2
       const double s = 11.0 * ((double)job.m * l + (double)l * (l + 1)) * 0x1p-53 * tr;
       for (int j = 0; j < l; ++j) A[j][j] += s;
     }
+    // pass 0: only exactly zero columns are refilled (the shift handles the
+    // rest); later passes: pivots lost to cancellation
+    tol = (pass == 0) ? 0.0 : 64.0 * l * 0x1p-53 * dmax;
+    mask = 0ull;
   }
   __syncthreads();
   double* R = job.Rk + (size_t)pass * l * l;
   for (int j = 0; j < l; ++j) {
     if (threadIdx.x == 0) {
-      double d = A[j][j];
-      // a non-positive pivot (zero input or rounding) gets a unit pivot: the
-      // column is then orthonormalised by the next passes
-      piv = (d > 0.0 && !zero_input) ? sqrt(d) : 1.0;
+      const double d = A[j][j];
+      const bool deficient = (pass == 0) ? !(diag0[j] > 0.0) : !(d > tol);
+      refill = deficient;
+      piv = deficient ? 1.0 : sqrt(d);
+      if (deficient) mask |= 1ull << j;
     }
     __syncthreads();
     const double dj = piv;
+    const bool rf = refill;
     for (int i = threadIdx.x; i < l; i += blockDim.x) {
-      const double v = (i >= j) ? A[j][i] / dj : 0.0;
+      const double v = (i > j && !rf) ? A[j][i] / dj : 0.0;
       R[j + l * i] = (i == j) ? dj : v;
       if (i > j) A[j][i] = v;
     }
@@ -464,6 +493,7 @@ __global__ void __launch_bounds__(256) cqr_chol_kernel(const CqrJob* __restrict_
     const int a = e % l, b = e / l;
     if (a > b) R[a + l * b] = 0.0;
   }
+  if (threadIdx.x == 0) *job.defmask = mask;
   if (job.R && pass == 2) {
     __syncthreads();
     // R = R3 R2 R1 (upper triangular products)
@@ -485,9 +515,9 @@ __global__ void __launch_bounds__(256) cqr_chol_kernel(const CqrJob* __restrict_
 
 // W_out[r, :] = W_in[r, :] R^{-1}, one row per thread (forward substitution).
 template <bool FROM_INPUT, bool TO_Q>
-__global__ void __launch_bounds__(kCqrRows) cqr_solve_kernel(const CqrJob* __restrict__ jobs,
+__global__ void __launch_bounds__(kCqrRows) cqr_solve_kernel(const CqrBatch jobs,
                                                              int pass) {
-  const CqrJob job = jobs[blockIdx.y];
+  const CqrJob job = jobs.job[blockIdx.y];
   const int l = job.l;
   const int64_t r = (int64_t)blockIdx.x * kCqrRows + threadIdx.x;
   __shared__ double R[kCqrMaxL][kCqrMaxL + 1];
@@ -495,6 +525,7 @@ __global__ void __launch_bounds__(kCqrRows) cqr_solve_kernel(const CqrJob* __res
   for (int e = threadIdx.x; e < l * l; e += blockDim.x) R[e % l][e / l] = Rg[e];
   __syncthreads();
   if (r >= job.m) return;
+  const unsigned long long refill = *job.defmask;
   double x[kCqrMaxL];
 #pragma unroll
   for (int j = 0; j < kCqrMaxL; ++j) {
@@ -507,14 +538,13 @@ __global__ void __launch_bounds__(kCqrRows) cqr_solve_kernel(const CqrJob* __res
         v = job.W[idx];
 #pragma unroll
       for (int k = 0; k < j; ++k) v = fma(-x[k], R[k][j], v);
-      x[j] = v / R[j][j];
+      x[j] = ((refill >> j) & 1ull) ? refill_value(r, j) : v / R[j][j];
     }
   }
   double* out = TO_Q ? job.Q : job.W;
-  const bool zero = TO_Q && *job.zero;  // Q of a zero matrix: [I; 0]
 #pragma unroll
   for (int j = 0; j < kCqrMaxL; ++j)
-    if (j < l) out[r + job.m * j] = zero ? (r == j ? 1.0 : 0.0) : x[j];
+    if (j < l) out[r + job.m * j] = x[j];
 }
 
 int grid_for(int64_t n, int threads, int cap = 8192) {
@@ -523,6 +553,8 @@ int grid_for(int64_t n, int threads, int cap = 8192) {
 }
 
 }  // namespace
+
+void cholqr3_launch(const CqrBatch& batch, int nq, int64_t maxm, int* status);
 
 void qr_householder_f64(const QrJob* jobs, int count, int* status) {
   if (count <= 0) return;
@@ -553,7 +585,7 @@ void qr_householder_f64(const QrJob* jobs, int count, int* status) {
     q.l = j.l;
     q.G = c->ws.take<double>((size_t)j.l * j.l);
     q.Rk = c->ws.take<double>((size_t)3 * j.l * j.l);
-    q.zero = c->ws.take<int>(1);
+    q.defmask = c->ws.take<unsigned long long>(1);
     cq.push_back(q);
     maxm = std::max<int64_t>(maxm, j.m);
   }
@@ -564,30 +596,39 @@ void qr_householder_f64(const QrJob* jobs, int count, int* status) {
     qr_kernel<<<(int)hh.size(), kQrThreads, 0, stream()>>>(d_jobs, status);
     check_launch("qr_householder_f64");
   }
-  if (!cq.empty()) {
-    const int nq = (int)cq.size();
-    CqrJob* d_cq = c->ws.take<CqrJob>(nq);
-    KRP_CUDA_CHECK(cudaMemcpyAsync(d_cq, cq.data(), sizeof(CqrJob) * nq, cudaMemcpyHostToDevice,
-                                   stream()));
-    const dim3 g((unsigned)((maxm + kCqrRows - 1) / kCqrRows), (unsigned)nq);
-    for (int pass = 0; pass < 3; ++pass) {
-      for (const CqrJob& q : cq)
-        KRP_CUDA_CHECK(cudaMemsetAsync(q.G, 0, sizeof(double) * q.l * q.l, stream()));
-      if (pass == 0)
-        cqr_gram_kernel<true><<<g, 256, 0, stream()>>>(d_cq, status);
-      else
-        cqr_gram_kernel<false><<<g, 256, 0, stream()>>>(d_cq, status);
-      check_launch("cholqr_gram_f64");
-      cqr_chol_kernel<<<nq, 256, 0, stream()>>>(d_cq, pass);
-      check_launch("cholqr_chol_f64");
-      if (pass == 0)
-        cqr_solve_kernel<true, false><<<g, kCqrRows, 0, stream()>>>(d_cq, pass);
-      else if (pass == 1)
-        cqr_solve_kernel<false, false><<<g, kCqrRows, 0, stream()>>>(d_cq, pass);
-      else
-        cqr_solve_kernel<false, true><<<g, kCqrRows, 0, stream()>>>(d_cq, pass);
-      check_launch("cholqr_solve_f64");
+  for (size_t b0 = 0; b0 < cq.size(); b0 += kCqrMaxBatch) {
+    const int nq = (int)std::min<size_t>(kCqrMaxBatch, cq.size() - b0);
+    CqrBatch batch{};
+    int64_t bm = 0;
+    for (int q = 0; q < nq; ++q) {
+      batch.job[q] = cq[b0 + q];
+      bm = std::max<int64_t>(bm, cq[b0 + q].m);
     }
+    cholqr3_launch(batch, nq, bm, status);
+  }
+  (void)maxm;
+}
+
+void cholqr3_launch(const CqrBatch& batch, int nq, int64_t maxm, int* status) {
+  const dim3 g((unsigned)((maxm + kCqrRows - 1) / kCqrRows), (unsigned)nq);
+  for (int pass = 0; pass < 3; ++pass) {
+    for (int q = 0; q < nq; ++q)
+      KRP_CUDA_CHECK(cudaMemsetAsync(batch.job[q].G, 0, sizeof(double) * batch.job[q].l * batch.job[q].l,
+                                     stream()));
+    if (pass == 0)
+      cqr_gram_kernel<true><<<g, 256, 0, stream()>>>(batch, status);
+    else
+      cqr_gram_kernel<false><<<g, 256, 0, stream()>>>(batch, status);
+    check_launch("cholqr_gram_f64");
+    cqr_chol_kernel<<<nq, 256, 0, stream()>>>(batch, pass);
+    check_launch("cholqr_chol_f64");
+    if (pass == 0)
+      cqr_solve_kernel<true, false><<<g, kCqrRows, 0, stream()>>>(batch, pass);
+    else if (pass == 1)
+      cqr_solve_kernel<false, false><<<g, kCqrRows, 0, stream()>>>(batch, pass);
+    else
+      cqr_solve_kernel<false, true><<<g, kCqrRows, 0, stream()>>>(batch, pass);
+    check_launch("cholqr_solve_f64");
   }
 }
 

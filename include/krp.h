@@ -167,6 +167,31 @@ krp_status krp_qr(krp_ctx ctx, int count, const float* const* Y,
                   const int64_t* m, const int* l, double* const* Q,
                   double* const* R);
 
+/* The same FP64 thin QR as krp_qr, for one FP32 matrix, without allocating any
+ * device memory.  The paper has no counterpart: this is a service for callers
+ * that may not call cudaMalloc while they run -- code inside a framework whose
+ * caching allocator owns the device memory, loops that cannot afford the
+ * device-wide synchronisation of cudaMalloc/cudaFree, programs that reserve
+ * their memory budget up front.  It needs no context: it runs on the calling
+ * thread's current device and enqueues on `cuda_stream` (a cudaStream_t, NULL
+ * = legacy default stream); Y (m x l), Q (m x l) and the optional R (l x l)
+ * are device pointers, column-major.
+ * Scratch: one fixed __device__ array of KRP_QR_NOALLOC_MAX_DOUBLES doubles
+ * (4 MiB) built into the library, resident on every GPU that loads it until
+ * the process exits.  A call needs m*l + 4*l*l + 2 of those doubles; larger
+ * requests, l outside 1..64, m < l and NULL Y/Q return KRP_EINVAL before any
+ * launch.  The first call on each device looks the array's device address up
+ * (cudaGetSymbolAddress) and caches it; make that first call before any
+ * stream capture.  All calls share the array and it keeps the last call's
+ * contents (the accumulators a call needs zeroed are cleared by the call), so
+ * calls whose work can overlap on the GPU -- on different streams, or from
+ * different threads -- race and must be serialised by the caller.  The call
+ * is asynchronous and does not check the input for NaN/Inf (use krp_qr for
+ * that); CUDA launch failures return KRP_ECUDA. */
+#define KRP_QR_NOALLOC_MAX_DOUBLES 524288
+krp_status krp_qr_noalloc(const float* Y, int64_t m, int l, double* Q,
+                          double* R, void* cuda_stream);
+
 /* ---- a5: multi-TTM core (Alg. 7 last step) ------------------------------- */
 
 /* G = X x_1 Q_1^T x_2 Q_2^T ... x_d Q_d^T, G of dims (cols[0..d-1]) FP32,

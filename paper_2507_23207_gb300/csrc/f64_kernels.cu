@@ -556,6 +556,46 @@ int grid_for(int64_t n, int threads, int cap = 8192) {
 
 void cholqr3_launch(const CqrBatch& batch, int nq, int64_t maxm, int* status);
 
+// Shifted CholeskyQR3 of one m x l FP32 matrix on an explicit stream, with
+// every scratch buffer taken from `scratch` (m*l + 4*l*l + 2 doubles): the
+// working matrix, the Gram accumulator, the three pass factors, the refill
+// mask and a status word.  Allocates nothing and copies nothing from the host.
+cudaError_t cholqr3_single_on_stream(const float* Y, int64_t m, int l, double* Q, double* R,
+                                     double* scratch, cudaStream_t st) {
+  CqrBatch batch{};
+  CqrJob& q = batch.job[0];
+  q.Y = Y;
+  q.Y64 = nullptr;
+  q.Q = Q;
+  q.R = R;
+  q.m = m;
+  q.l = l;
+  q.W = scratch;
+  q.G = scratch + (size_t)m * l;
+  q.Rk = q.G + (size_t)l * l;
+  q.defmask = reinterpret_cast<unsigned long long*>(q.Rk + (size_t)3 * l * l);
+  int* status = reinterpret_cast<int*>(q.Rk + (size_t)3 * l * l + 1);
+  const dim3 g((unsigned)((m + kCqrRows - 1) / kCqrRows), 1u);
+  for (int pass = 0; pass < 3; ++pass) {
+    cudaError_t e = cudaMemsetAsync(q.G, 0, sizeof(double) * l * l, st);
+    if (e != cudaSuccess) return e;
+    if (pass == 0)
+      cqr_gram_kernel<true><<<g, 256, 0, st>>>(batch, status);
+    else
+      cqr_gram_kernel<false><<<g, 256, 0, st>>>(batch, status);
+    cqr_chol_kernel<<<1, 256, 0, st>>>(batch, pass);
+    if (pass == 0)
+      cqr_solve_kernel<true, false><<<g, kCqrRows, 0, st>>>(batch, pass);
+    else if (pass == 1)
+      cqr_solve_kernel<false, false><<<g, kCqrRows, 0, st>>>(batch, pass);
+    else
+      cqr_solve_kernel<false, true><<<g, kCqrRows, 0, st>>>(batch, pass);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
 void qr_householder_f64(const QrJob* jobs, int count, int* status) {
   if (count <= 0) return;
   for (int b = 0; b < count; ++b) {

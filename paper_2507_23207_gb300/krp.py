@@ -29,7 +29,7 @@ KRP_TAG_OMEGA, KRP_TAG_PSI = 0, 1
 EXPORTED = [
     "krp_create", "krp_destroy", "krp_set_stream", "krp_last_error", "krp_status_string",
     "krp_abi_version", "krp_launch_count", "krp_gen_factors", "krp_philox_words",
-    "krp_sketch_mode", "krp_sketch_all_modes", "krp_qr", "krp_multi_ttm",
+    "krp_sketch_mode", "krp_sketch_all_modes", "krp_qr", "krp_qr_noalloc", "krp_multi_ttm",
     "krp_tucker_rhosvd", "krp_tucker_sthosvd", "krp_block_hankel_lowrank",
     "krp_block_hankel_sketch",
 ]
@@ -91,6 +91,7 @@ def load_library(path: Optional[str] = None):
                                            C.c_int, C.c_int, C.POINTER(vp)]),
         "krp_qr": (C.c_int, [vp, C.c_int, C.POINTER(vp), i64p, C.POINTER(C.c_int),
                              C.POINTER(vp), C.POINTER(vp)]),
+        "krp_qr_noalloc": (C.c_int, [vp, C.c_int64, C.c_int, vp, vp, vp]),
         "krp_multi_ttm": (C.c_int, [vp, vp, C.c_int, C.c_int, i64p, C.POINTER(vp),
                                     C.POINTER(C.c_int), vp]),
         "krp_tucker_rhosvd": (C.c_int, [vp, vp, C.c_int, C.c_int, i64p, C.POINTER(C.c_int),
@@ -241,6 +242,23 @@ def krp_qr(ctx: Context, Ys: Sequence, ms: Sequence[int], ls: Sequence[int], Qs:
            Rs: Optional[Sequence] = None):
     ctx.check(ctx.lib.krp_qr(ctx.handle, len(Ys), _ptrs(Ys), _i64(ms), _i32(ls), _ptrs(Qs),
                              _ptrs(Rs) if Rs is not None else None))
+
+
+KRP_QR_NOALLOC_MAX_DOUBLES = 524288
+
+
+def krp_qr_noalloc(Y, m: int, l: int, Q, R=None, stream: Optional[int] = None) -> int:
+    """Thin QR of one FP32 matrix without device allocation (no context).
+
+    For callers that may not allocate while running; the library keeps one
+    fixed 4 MiB scratch array per GPU for it, shared by all calls (overlapping
+    calls race).  Returns the krp_status code (0 = KRP_OK).
+    """
+    lib = load_library()
+    if stream is None:
+        import torch
+        stream = torch.cuda.current_stream().cuda_stream
+    return int(lib.krp_qr_noalloc(_ptr(Y), m, l, _ptr(Q), _ptr(R), C.c_void_p(stream)))
 
 
 def krp_multi_ttm(ctx: Context, X, dims: Sequence[int], Qs: Sequence, cols: Sequence[int], G):

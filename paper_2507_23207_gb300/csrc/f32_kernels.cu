@@ -24,20 +24,41 @@ __device__ __forceinline__ float comp(const float4& v, int c) {
   return c == 0 ? v.x : (c == 1 ? v.y : (c == 2 ? v.z : v.w));
 }
 
+// ---- cp.async helpers --------------------------------------------------------
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem, bool pred) {
+  const unsigned s = static_cast<unsigned>(__cvta_generic_to_shared(smem));
+  const int n = pred ? 16 : 0;  // src-size 0 zero-fills the 16 bytes
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(s), "l"(gmem), "r"(n)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async4(void* smem, const void* gmem, bool pred) {
+  const unsigned s = static_cast<unsigned>(__cvta_generic_to_shared(smem));
+  const int n = pred ? 4 : 0;
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(s), "l"(gmem), "r"(n)
+               : "memory");
+}
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
 // ----------------------------------------------------------------------------
 // out[s + ldo*k] (=|+=) sum_{i<K} A[i + lda*s] * F[i + ldf*k]
 // CTA: 128 rows s x NP columns k; thread (g, h) owns rows s0+g+16j (j<8) and
-// columns k0+4h..4h+3.  A chunks are staged [s][i] (i contiguous, float4).
+// columns k0+4h..4h+3.  Two-stage cp.async ring: A chunk staged [s][i], F chunk
+// staged [k][i] (both i contiguous, rows padded to 36 floats).
+constexpr int kGemmStages = 2;
+
 template <int NP, bool VEC>
-__global__ void __launch_bounds__(NP * 4)
+__global__ void __launch_bounds__(NP * 4, (NP <= 48) ? 3 : 2)
     gemm_tn_kernel(const float* __restrict__ A, int64_t lda, int64_t S, int K,
                    const float* __restrict__ F, int64_t ldf, int L, float* __restrict__ out,
                    int64_t ldo, int accumulate) {
   constexpr int NT = NP * 4;
-  constexpr int AV = (TM * TK / 4 + NT - 1) / NT;
-  constexpr int FV = TK * NP / NT;
-  __shared__ __align__(16) float As[2][TM][APITCH];
-  __shared__ __align__(16) float Fs[2][TK][NP];
+  extern __shared__ __align__(16) float gsm[];
+  float(*As)[TM][APITCH] = reinterpret_cast<float(*)[TM][APITCH]>(gsm);
+  float(*Fs)[NP][APITCH] = reinterpret_cast<float(*)[NP][APITCH]>(gsm + kGemmStages * TM * APITCH);
 
   const int tid = threadIdx.x, g = tid & 15, h = tid >> 4;
   const int64_t s0 = (int64_t)blockIdx.x * TM;
@@ -47,85 +68,73 @@ __global__ void __launch_bounds__(NP * 4)
   for (int j = 0; j < 8; ++j)
 #pragma unroll
     for (int c = 0; c < 4; ++c) acc[j][c] = 0.f;
-
-  float4 ra[AV];
-  float rf[FV];
   const int nchunks = (K + TK - 1) / TK;
 
-  auto load = [&](int kc) {
-#pragma unroll
-    for (int v = 0; v < AV; ++v) {
-      const int q = tid + v * NT;
-      float4 val = make_float4(0.f, 0.f, 0.f, 0.f);
-      if (q < TM * TK / 4) {
+  auto issue = [&](int chunk, int stage) {
+    const int kc = chunk * TK;
+    if (VEC) {
+      for (int q = tid; q < TM * (TK / 4); q += NT) {
         const int sl = q >> 3, c4 = q & 7;
         const int64_t s = s0 + sl;
         const int i = kc + 4 * c4;
-        if (s < S) {
-          const float* p = A + (int64_t)i + lda * s;
-          if (VEC) {
-            if (i < K) val = *reinterpret_cast<const float4*>(p);
-          } else {
-            if (i + 0 < K) val.x = p[0];
-            if (i + 1 < K) val.y = p[1];
-            if (i + 2 < K) val.z = p[2];
-            if (i + 3 < K) val.w = p[3];
-          }
-        }
+        const bool ok = (s < S) && (i < K);
+        cp_async16(&As[stage][sl][4 * c4], ok ? (const void*)(A + i + lda * s) : (const void*)A, ok);
       }
-      ra[v] = val;
-    }
-#pragma unroll
-    for (int v = 0; v < FV; ++v) {
-      const int q = tid + v * NT;
-      const int i = q % TK, kk = q / TK;
-      float val = 0.f;
-      if (kc + i < K && k0 + kk < L) val = F[(int64_t)(kc + i) + ldf * (k0 + kk)];
-      rf[v] = val;
-    }
-  };
-  auto store = [&](int buf) {
-#pragma unroll
-    for (int v = 0; v < AV; ++v) {
-      const int q = tid + v * NT;
-      if (q < TM * TK / 4) {
-        const int sl = q >> 3, c4 = q & 7;
-        *reinterpret_cast<float4*>(&As[buf][sl][4 * c4]) = ra[v];
+      for (int q = tid; q < NP * (TK / 4); q += NT) {
+        const int kk = q >> 3, c4 = q & 7;
+        const int i = kc + 4 * c4;
+        const bool ok = (k0 + kk < L) && (i < K);
+        cp_async16(&Fs[stage][kk][4 * c4], ok ? (const void*)(F + i + ldf * (k0 + kk)) : (const void*)F, ok);
+      }
+    } else {
+      for (int q = tid; q < TM * TK; q += NT) {
+        const int sl = q >> 5, ii = q & 31;
+        const int64_t s = s0 + sl;
+        const int i = kc + ii;
+        const bool ok = (s < S) && (i < K);
+        cp_async4(&As[stage][sl][ii], ok ? (const void*)(A + i + lda * s) : (const void*)A, ok);
+      }
+      for (int q = tid; q < NP * TK; q += NT) {
+        const int kk = q >> 5, ii = q & 31;
+        const int i = kc + ii;
+        const bool ok = (k0 + kk < L) && (i < K);
+        cp_async4(&Fs[stage][kk][ii], ok ? (const void*)(F + i + ldf * (k0 + kk)) : (const void*)F, ok);
       }
     }
-#pragma unroll
-    for (int v = 0; v < FV; ++v) {
-      const int q = tid + v * NT;
-      Fs[buf][q % TK][q / TK] = rf[v];
-    }
+    cp_commit();
   };
 
-  load(0);
-  store(0);
-  __syncthreads();
+  issue(0, 0);
   for (int c = 0; c < nchunks; ++c) {
-    const int buf = c & 1;
-    if (c + 1 < nchunks) load((c + 1) * TK);
+    const int st = c % kGemmStages;
+    if (c + 1 < nchunks) {
+      issue(c + 1, (c + 1) % kGemmStages);
+      cp_wait<1>();
+    } else {
+      cp_wait<0>();
+    }
+    __syncthreads();
 #pragma unroll
     for (int ii = 0; ii < TK; ii += 4) {
       float4 a[8];
 #pragma unroll
-      for (int j = 0; j < 8; ++j) a[j] = *reinterpret_cast<const float4*>(&As[buf][g + 16 * j][ii]);
+      for (int j = 0; j < 8; ++j) a[j] = *reinterpret_cast<const float4*>(&As[st][g + 16 * j][ii]);
+      float4 f[4];
 #pragma unroll
-      for (int cc = 0; cc < 4; ++cc) {
-        const float4 f = *reinterpret_cast<const float4*>(&Fs[buf][ii + cc][4 * h]);
+      for (int cc = 0; cc < 4; ++cc) f[cc] = *reinterpret_cast<const float4*>(&Fs[st][4 * h + cc][ii]);
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
 #pragma unroll
         for (int j = 0; j < 8; ++j) {
-          const float av = comp(a[j], cc);
-          acc[j][0] = fmaf(av, f.x, acc[j][0]);
-          acc[j][1] = fmaf(av, f.y, acc[j][1]);
-          acc[j][2] = fmaf(av, f.z, acc[j][2]);
-          acc[j][3] = fmaf(av, f.w, acc[j][3]);
+          const float av = comp(a[j], q);
+          acc[j][0] = fmaf(av, comp(f[0], q), acc[j][0]);
+          acc[j][1] = fmaf(av, comp(f[1], q), acc[j][1]);
+          acc[j][2] = fmaf(av, comp(f[2], q), acc[j][2]);
+          acc[j][3] = fmaf(av, comp(f[3], q), acc[j][3]);
         }
       }
     }
-    if (c + 1 < nchunks) store(buf ^ 1);
-    __syncthreads();
+    __syncthreads();  // stage st is refilled by the next-but-one issue
   }
 #pragma unroll
   for (int j = 0; j < 8; ++j) {
@@ -142,40 +151,59 @@ __global__ void __launch_bounds__(NP * 4)
   }
 }
 
+template <class Kern>
+void set_dyn_smem(Kern k, size_t bytes) {
+  if (bytes > 48 * 1024)
+    KRP_CUDA_CHECK(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+}
+
 template <int NP>
 void gemm_tn_launch(const float* A, int64_t lda, int64_t S, int K, const float* F, int64_t ldf,
                     int L, float* out, int64_t ldo, bool accumulate) {
   dim3 grid((unsigned)((S + TM - 1) / TM), (unsigned)((L + NP - 1) / NP));
-  const bool vec = (lda % 4 == 0) && (K % 4 == 0) && ((reinterpret_cast<uintptr_t>(A) & 15) == 0);
-  if (vec)
-    gemm_tn_kernel<NP, true><<<grid, NP * 4, 0, stream()>>>(A, lda, S, K, F, ldf, L, out, ldo,
-                                                            accumulate ? 1 : 0);
-  else
-    gemm_tn_kernel<NP, false><<<grid, NP * 4, 0, stream()>>>(A, lda, S, K, F, ldf, L, out, ldo,
-                                                             accumulate ? 1 : 0);
+  const bool vec = (lda % 4 == 0) && (ldf % 4 == 0) && (K % 4 == 0) &&
+                   ((reinterpret_cast<uintptr_t>(A) & 15) == 0) &&
+                   ((reinterpret_cast<uintptr_t>(F) & 15) == 0);
+  const size_t smem = sizeof(float) * kGemmStages * (TM + NP) * APITCH;
+  if (vec) {
+    set_dyn_smem(gemm_tn_kernel<NP, true>, smem);
+    gemm_tn_kernel<NP, true><<<grid, NP * 4, smem, stream()>>>(A, lda, S, K, F, ldf, L, out, ldo,
+                                                               accumulate ? 1 : 0);
+  } else {
+    set_dyn_smem(gemm_tn_kernel<NP, false>, smem);
+    gemm_tn_kernel<NP, false><<<grid, NP * 4, smem, stream()>>>(A, lda, S, K, F, ldf, L, out, ldo,
+                                                                accumulate ? 1 : 0);
+  }
   check_launch("gemm_tn_f32");
 }
 
 // ----------------------------------------------------------------------------
 // Y[i + n1*k] += sum_{s in split} A[i + n1*s] * W(s, k),
 // W(s, k) = prod_j V_j[digit_j(s) + radix_j * k]   (the Khatri-Rao row)
+// Three-stage cp.async ring for A (staged [s][i]); the Khatri-Rao rows of the
+// next chunk are gathered into registers while the current chunk is
+// multiplied, and written to shared memory afterwards.
 struct RadixDev {
   int n;
   int64_t radix[KRP_MAXD];
   const float* V[KRP_MAXD];
 };
 
-template <int NP, bool VEC>
-__global__ void __launch_bounds__(NP * 4)
+constexpr int kMttStages = 3;
+
+// DR: upper bound on the number of Khatri-Rao factors of a row (R.n <= DR),
+// so that the gathered factor values take DR registers per row value.
+template <int NP, bool VEC, int DR>
+__global__ void __launch_bounds__(NP * 4, (NP <= 48) ? 3 : 2)
     mttkrp_first_kernel(const float* __restrict__ A, int64_t n1, int64_t S, const RadixDev R,
                         int L, float* __restrict__ Y, int64_t s_per_split) {
   constexpr int NT = NP * 4;
-  constexpr int AV = (TM * TK / 4 + NT - 1) / NT;
-  constexpr int WV = (TK * NP + NT - 1) / NT;
-  __shared__ __align__(16) float As[2][TK][TM];
-  __shared__ __align__(16) float Ws[2][TK][NP];
-  // mixed-radix digits of the chunk's TK rows, decoded once per chunk
-  __shared__ int dig[2][TK][KRP_MAXD];
+  constexpr int WV = (TK * NP + NT - 1) / NT;  // = 8
+  extern __shared__ __align__(16) float msm[];
+  float(*As)[TK][TM] = reinterpret_cast<float(*)[TK][TM]>(msm);
+  float(*Ws)[TK][NP] = reinterpret_cast<float(*)[TK][NP]>(msm + kMttStages * TK * TM);
+  int(*dig)[TK][KRP_MAXD] =
+      reinterpret_cast<int(*)[TK][KRP_MAXD]>(msm + kMttStages * TK * TM + 2 * TK * NP);
 
   const int tid = threadIdx.x, g = tid & 15, h = tid >> 4;
   const int64_t i0 = (int64_t)blockIdx.x * TM;
@@ -188,92 +216,89 @@ __global__ void __launch_bounds__(NP * 4)
   for (int j = 0; j < 8; ++j)
 #pragma unroll
     for (int c = 0; c < 4; ++c) acc[j][c] = 0.f;
-
-  float4 ra[AV];
-  float rw[WV];
   const int64_t nchunks = (se - sb + TK - 1) / TK;
 
-  auto load = [&](int64_t sc) {
-#pragma unroll
-    for (int v = 0; v < AV; ++v) {
-      const int q = tid + v * NT;
-      float4 val = make_float4(0.f, 0.f, 0.f, 0.f);
-      if (q < TM * TK / 4) {
-        const int sl = q >> 5, c4 = q & 31;
-        const int64_t s = sc + sl;
-        const int64_t i = i0 + 4 * c4;
-        if (s < se) {
-          const float* p = A + i + n1 * s;
-          if (VEC) {
-            if (i < n1) val = *reinterpret_cast<const float4*>(p);
-          } else {
-            if (i + 0 < n1) val.x = p[0];
-            if (i + 1 < n1) val.y = p[1];
-            if (i + 2 < n1) val.z = p[2];
-            if (i + 3 < n1) val.w = p[3];
-          }
+  auto issue = [&](int64_t chunk) {
+    if (chunk < nchunks) {
+      const int st = (int)(chunk % kMttStages);
+      const int64_t sc = sb + chunk * TK;
+      if (VEC) {
+        for (int q = tid; q < TK * (TM / 4); q += NT) {
+          const int sl = q >> 5, c4 = q & 31;
+          const int64_t s = sc + sl, i = i0 + 4 * c4;
+          const bool ok = (s < se) && (i < n1);
+          cp_async16(&As[st][sl][4 * c4], ok ? (const void*)(A + i + n1 * s) : (const void*)A, ok);
+        }
+      } else {
+        for (int q = tid; q < TK * TM; q += NT) {
+          const int sl = q >> 7, ii = q & 127;
+          const int64_t s = sc + sl, i = i0 + ii;
+          const bool ok = (s < se) && (i < n1);
+          cp_async4(&As[st][sl][ii], ok ? (const void*)(A + i + n1 * s) : (const void*)A, ok);
         }
       }
-      ra[v] = val;
     }
-    const int db = (int)(((sc - sb) / TK) & 1);
-#pragma unroll
-    for (int v = 0; v < WV; ++v) {
-      const int q = tid + v * NT;
-      float w = 0.f;
-      if (q < TK * NP) {
-        const int sl = q / NP, kk = q % NP;
-        const int64_t s = sc + sl;
-        const int k = k0 + kk;
-        if (s < se && k < L) {
-          w = 1.f;
-          for (int j = 0; j < R.n; ++j) w *= R.V[j][dig[db][sl][j] + R.radix[j] * k];
-        }
-      }
-      rw[v] = w;
-    }
+    cp_commit();  // always one group per call (possibly empty)
   };
-  // digits of rows s = sc + sl of one chunk (first TK threads)
-  auto decode = [&](int64_t sc, int buf) {
-    if (tid < TK) {
-      int64_t s = sc + tid;
+  auto decode = [&](int64_t chunk) {
+    if (tid < TK && chunk < nchunks) {
+      int64_t s = sb + chunk * TK + tid;
       for (int j = 0; j < R.n; ++j) {
         const int64_t r = R.radix[j];
-        dig[buf][tid][j] = (int)(s % r);
+        dig[chunk & 1][tid][j] = (int)(s % r);
         s /= r;
       }
     }
   };
-  auto store = [&](int buf) {
-#pragma unroll
-    for (int v = 0; v < AV; ++v) {
-      const int q = tid + v * NT;
-      if (q < TM * TK / 4) {
-        const int sl = q >> 5, c4 = q & 31;
-        *reinterpret_cast<float4*>(&As[buf][sl][4 * c4]) = ra[v];
-      }
-    }
+  // factor values of the Khatri-Rao rows of `chunk`, gathered into registers
+  float fv[WV][DR];
+  auto gather = [&](int64_t chunk) {
+    const int64_t sc = sb + chunk * TK;
 #pragma unroll
     for (int v = 0; v < WV; ++v) {
       const int q = tid + v * NT;
-      if (q < TK * NP) Ws[buf][q / NP][q % NP] = rw[v];
+      const int sl = q / NP, kk = q % NP;
+      const bool ok = (chunk < nchunks) && (q < TK * NP) && (sc + sl < se) && (k0 + kk < L);
+#pragma unroll
+      for (int j = 0; j < DR; ++j)
+        fv[v][j] = (ok && j < R.n) ? R.V[j][dig[chunk & 1][sl][j] + R.radix[j] * (k0 + kk)] : 0.f;
+    }
+  };
+  auto scatter = [&](int64_t chunk) {
+#pragma unroll
+    for (int v = 0; v < WV; ++v) {
+      const int q = tid + v * NT;
+      if (q < TK * NP) {
+        float w = (R.n > 0) ? fv[v][0] : 1.f;
+#pragma unroll
+        for (int j = 1; j < DR; ++j)
+          if (j < R.n) w *= fv[v][j];
+        const int sl = q / NP;
+        const bool ok = (chunk < nchunks) && (sb + chunk * TK + sl < se) && (k0 + q % NP < L);
+        Ws[chunk & 1][sl][q % NP] = ok ? w : 0.f;
+      }
     }
   };
 
-  decode(sb, 0);
-  if (nchunks > 1) decode(sb + TK, 1);
+  issue(0);
+  issue(1);
+  decode(0);
+  decode(1);
   __syncthreads();
-  load(sb);
-  store(0);
-  __syncthreads();
+  gather(0);
+  scatter(0);
   for (int64_t c = 0; c < nchunks; ++c) {
-    const int buf = (int)(c & 1);
-    if (c + 1 < nchunks) load(sb + (c + 1) * TK);
+    cp_wait<1>();  // chunk c has landed (chunk c+1 may be in flight)
+    __syncthreads();
+    issue(c + 2);
+    gather(c + 1);  // global loads overlap the multiply below
+    const int st = (int)(c % kMttStages);
+    const int wb = (int)(c & 1);
 #pragma unroll 8
     for (int sl = 0; sl < TK; ++sl) {
-      const float4 a0 = *reinterpret_cast<const float4*>(&As[buf][sl][4 * g]);
-      const float4 a1 = *reinterpret_cast<const float4*>(&As[buf][sl][64 + 4 * g]);
-      const float4 w = *reinterpret_cast<const float4*>(&Ws[buf][sl][4 * h]);
+      const float4 a0 = *reinterpret_cast<const float4*>(&As[st][sl][4 * g]);
+      const float4 a1 = *reinterpret_cast<const float4*>(&As[st][sl][64 + 4 * g]);
+      const float4 w = *reinterpret_cast<const float4*>(&Ws[wb][sl][4 * h]);
       const float av[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
 #pragma unroll
       for (int j = 0; j < 8; ++j) {
@@ -283,9 +308,9 @@ __global__ void __launch_bounds__(NP * 4)
         acc[j][3] = fmaf(av[j], w.w, acc[j][3]);
       }
     }
-    if (c + 1 < nchunks) store(buf ^ 1);
-    if (c + 2 < nchunks) decode(sb + (c + 2) * TK, buf);
+    scatter(c + 1);  // Ws[(c+1)&1] was last read in the previous iteration
     __syncthreads();
+    decode(c + 2);   // dig[c&1] was last read by gather(c) in the previous iteration
   }
 #pragma unroll
   for (int j = 0; j < 8; ++j) {
@@ -304,7 +329,7 @@ void mttkrp_first_launch(const float* A, int64_t n1, int64_t S, const RadixDev& 
                          float* Y) {
   const int mt = (int)((n1 + TM - 1) / TM);
   const int nt = (L + NP - 1) / NP;
-  const int want = 8 * current()->num_sms;  // several waves of CTAs over the SMs
+  const int want = 6 * current()->num_sms;  // two waves of three CTAs per SM
   int64_t splits = std::max<int64_t>(1, want / std::max(1, mt * nt));
   int64_t per = (S + splits - 1) / splits;
   per = std::max<int64_t>(per, 4 * TK);
@@ -312,10 +337,20 @@ void mttkrp_first_launch(const float* A, int64_t n1, int64_t S, const RadixDev& 
   splits = (S + per - 1) / per;
   dim3 grid(mt, nt, (unsigned)splits);
   const bool vec = (n1 % 4 == 0) && ((reinterpret_cast<uintptr_t>(A) & 15) == 0);
-  if (vec)
-    mttkrp_first_kernel<NP, true><<<grid, NP * 4, 0, stream()>>>(A, n1, S, R, L, Y, per);
-  else
-    mttkrp_first_kernel<NP, false><<<grid, NP * 4, 0, stream()>>>(A, n1, S, R, L, Y, per);
+  const size_t smem = sizeof(float) * (kMttStages * TK * TM + 2 * TK * NP) + sizeof(int) * 2 * TK * KRP_MAXD;
+  auto go = [&](auto kern) {
+    set_dyn_smem(kern, smem);
+    kern<<<grid, NP * 4, smem, stream()>>>(A, n1, S, R, L, Y, per);
+  };
+  if (vec) {
+    if (R.n <= 1) go(mttkrp_first_kernel<NP, true, 1>);
+    else if (R.n == 2) go(mttkrp_first_kernel<NP, true, 2>);
+    else if (R.n == 3) go(mttkrp_first_kernel<NP, true, 3>);
+    else go(mttkrp_first_kernel<NP, true, KRP_MAXD - 1>);
+  } else {
+    if (R.n <= 2) go(mttkrp_first_kernel<NP, false, 2>);
+    else go(mttkrp_first_kernel<NP, false, KRP_MAXD - 1>);
+  }
   check_launch("mttkrp_first_f32");
 }
 

@@ -176,41 +176,32 @@ struct EigJob {
   int l, r;
 };
 
-// Cyclic Jacobi eigensolver for one symmetric l x l matrix per CTA (l <= 64),
-// parallel (round-robin) pair ordering: every round rotates l/2 disjoint
-// pairs, first updating columns (S J, V J) and then rows (J^T S).
-__global__ void __launch_bounds__(256) eig_kernel(const EigJob* __restrict__ jobs, int* status) {
-  const EigJob job = jobs[blockIdx.x];
-  const int l = job.l;
-  const int n = (l + 1) & ~1;  // padded to even for the tournament
-  extern __shared__ double eig_smem[];
-  double(*S)[kEigMaxL + 1] = reinterpret_cast<double(*)[kEigMaxL + 1]>(eig_smem);
-  double(*V)[kEigMaxL + 1] =
-      reinterpret_cast<double(*)[kEigMaxL + 1]>(eig_smem + kEigMaxL * (kEigMaxL + 1));
-  __shared__ double cs[kEigMaxL / 2], sn[kEigMaxL / 2];
-  __shared__ int pp[kEigMaxL / 2], qq[kEigMaxL / 2];
-  __shared__ int order[kEigMaxL];
-  __shared__ double offn, diagn;
-  __shared__ int ring[kEigMaxL];
+// Symmetric eigensolver for one l x l FP64 matrix per CTA (l <= 64): cyclic
+// Jacobi with the parallel (round-robin) pair ordering, where every round
+// rotates l/2 disjoint pairs, updating columns (S J, V J) and then rows (J^T S).
+// GB300 issues FP32 at ~58x the FP64 rate, so the sweeps that only need to
+// bring the matrix close to diagonal run in FP32; the FP32 basis is then made
+// orthonormal in FP64 (modified Gram-Schmidt), S' = V0^T S V0 is formed in
+// FP64, and the last sweeps run in FP64 on S' while rotating V0 itself, so the
+// returned eigenvectors are orthonormal and accurate to FP64 rounding.
+constexpr int kEP = kEigMaxL + 1;  // padded row pitch
+
+template <class T>
+__device__ void jacobi_sweeps(T (*S)[kEP], T (*V)[kEP], int n, int max_sweeps, double tol,
+                              T* cs, T* sn, int* pp, int* qq, int* ring, double* red) {
   const int tid = threadIdx.x;
-  for (int e = tid; e < n * n; e += blockDim.x) {
-    const int r = e % n, c = e / n;
-    S[r][c] = (r < l && c < l) ? job.S[r + l * c] : 0.0;
-    V[r][c] = (r == c) ? 1.0 : 0.0;
-  }
-  for (int i = tid; i < n; i += blockDim.x) ring[i] = i;
-  __syncthreads();
-  for (int sweep = 0; sweep < 30; ++sweep) {
+  for (int sweep = 0; sweep < max_sweeps; ++sweep) {
     if (tid == 0) {
-      offn = 0.0;
-      diagn = 0.0;
+      red[0] = 0.0;
+      red[1] = 0.0;
     }
+    for (int i = tid; i < n; i += blockDim.x) ring[i] = i;
     __syncthreads();
     {
       double o = 0.0, dg = 0.0;
       for (int e = tid; e < n * n; e += blockDim.x) {
         const int r = e % n, c = e / n;
-        const double v = S[r][c] * S[r][c];
+        const double v = (double)S[r][c] * (double)S[r][c];
         if (r == c)
           dg += v;
         else
@@ -219,15 +210,13 @@ __global__ void __launch_bounds__(256) eig_kernel(const EigJob* __restrict__ job
       o = warp_sum(o);
       dg = warp_sum(dg);
       if ((tid & 31) == 0) {
-        atomicAdd(&offn, o);
-        atomicAdd(&diagn, dg);
+        atomicAdd(&red[0], o);
+        atomicAdd(&red[1], dg);
       }
     }
     __syncthreads();
-    // converged once the off-diagonal norm is below 1e-13 of the diagonal's
-    if (!(offn > 1e-26 * diagn) || offn == 0.0) break;
+    if (!(red[0] > tol * red[1]) || red[0] == 0.0) break;
     for (int round = 0; round < n - 1; ++round) {
-      // pairs of this round: ring[i] with ring[n-1-i]
       if (tid < n / 2) {
         int p = ring[tid], q = ring[n - 1 - tid];
         if (p > q) {
@@ -237,38 +226,37 @@ __global__ void __launch_bounds__(256) eig_kernel(const EigJob* __restrict__ job
         }
         pp[tid] = p;
         qq[tid] = q;
-        const double apq = S[p][q];
-        double c = 1.0, s = 0.0;
-        if (fabs(apq) > 1e-16 * sqrt(fabs(S[p][p] * S[q][q]))) {
-          const double app = S[p][p], aqq = S[q][q];
-          const double theta = (aqq - app) / (2.0 * apq);
-          const double t = (theta >= 0.0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(1.0 + theta * theta));
-          c = 1.0 / sqrt(1.0 + t * t);
+        const T apq = S[p][q];
+        T c = T(1), s = T(0);
+        const T app = S[p][p], aqq = S[q][q];
+        const T thr = (sizeof(T) == 8 ? T(1e-16) : T(1e-8)) * sqrt(fabs(app * aqq));
+        if (fabs(apq) > thr) {
+          const T theta = (aqq - app) / (T(2) * apq);
+          const T t = (theta >= T(0) ? T(1) : T(-1)) / (fabs(theta) + sqrt(T(1) + theta * theta));
+          c = T(1) / sqrt(T(1) + t * t);
           s = t * c;
         }
         cs[tid] = c;
         sn[tid] = s;
       }
       __syncthreads();
-      // columns: S <- S J, V <- V J   (J rotates columns p, q)
       for (int e = tid; e < (n / 2) * n; e += blockDim.x) {
         const int k = e % (n / 2), r = e / (n / 2);
         const int p = pp[k], q = qq[k];
-        const double c = cs[k], s = sn[k];
-        const double sp = S[r][p], sq = S[r][q];
+        const T c = cs[k], s = sn[k];
+        const T sp = S[r][p], sq = S[r][q];
         S[r][p] = c * sp - s * sq;
         S[r][q] = s * sp + c * sq;
-        const double vp = V[r][p], vq = V[r][q];
+        const T vp = V[r][p], vq = V[r][q];
         V[r][p] = c * vp - s * vq;
         V[r][q] = s * vp + c * vq;
       }
       __syncthreads();
-      // rows: S <- J^T S
       for (int e = tid; e < (n / 2) * n; e += blockDim.x) {
         const int k = e % (n / 2), col = e / (n / 2);
         const int p = pp[k], q = qq[k];
-        const double c = cs[k], s = sn[k];
-        const double sp = S[p][col], sq = S[q][col];
+        const T c = cs[k], s = sn[k];
+        const T sp = S[p][col], sq = S[q][col];
         S[p][col] = c * sp - s * sq;
         S[q][col] = s * sp + c * sq;
       }
@@ -281,6 +269,90 @@ __global__ void __launch_bounds__(256) eig_kernel(const EigJob* __restrict__ job
       __syncthreads();
     }
   }
+}
+
+constexpr int kEigThreads = 1024;  // many warps to hide FP64 and shared-memory latency
+
+__global__ void __launch_bounds__(kEigThreads) eig_kernel(const EigJob* __restrict__ jobs, int* status) {
+  const EigJob job = jobs[blockIdx.x];
+  const int l = job.l;
+  const int n = (l + 1) & ~1;  // padded to even for the tournament
+  extern __shared__ double eig_smem[];
+  double(*S)[kEP] = reinterpret_cast<double(*)[kEP]>(eig_smem);
+  double(*V)[kEP] = reinterpret_cast<double(*)[kEP]>(eig_smem + kEigMaxL * kEP);
+  double(*Tm)[kEP] = reinterpret_cast<double(*)[kEP]>(eig_smem + 2 * kEigMaxL * kEP);
+  float(*S32)[kEP] = reinterpret_cast<float(*)[kEP]>(eig_smem + 3 * kEigMaxL * kEP);
+  float(*V32)[kEP] = reinterpret_cast<float(*)[kEP]>(eig_smem + 3 * kEigMaxL * kEP) + kEigMaxL;
+  __shared__ double cs[kEigMaxL / 2], sn[kEigMaxL / 2];
+  __shared__ float cs32[kEigMaxL / 2], sn32[kEigMaxL / 2];
+  __shared__ int pp[kEigMaxL / 2], qq[kEigMaxL / 2];
+  __shared__ int order[kEigMaxL];
+  __shared__ int ring[kEigMaxL];
+  __shared__ double red[2];
+  __shared__ double colnorm;
+  const int tid = threadIdx.x;
+  for (int e = tid; e < n * n; e += blockDim.x) {
+    const int r = e % n, c = e / n;
+    const double v = (r < l && c < l) ? job.S[r + l * c] : 0.0;
+    S[r][c] = v;
+    S32[r][c] = (float)v;
+    V32[r][c] = (r == c) ? 1.f : 0.f;
+  }
+  __syncthreads();
+  // phase 1 (FP32): most of the sweeps
+  jacobi_sweeps<float>(S32, V32, n, 20, 1e-12, cs32, sn32, pp, qq, ring, red);
+  // phase 2 (FP64): V0 = orthonormalised V32 (modified Gram-Schmidt on columns)
+  for (int e = tid; e < n * n; e += blockDim.x) {
+    const int r = e % n, c = e / n;
+    V[r][c] = (double)V32[r][c];
+  }
+  __syncthreads();
+  for (int j = 0; j < n; ++j) {
+    if (tid < 32) {
+      double s = 0.0;
+      for (int r = tid; r < n; r += 32) s = fma(V[r][j], V[r][j], s);
+      s = warp_sum(s);
+      if (tid == 0) colnorm = sqrt(s);
+    }
+    __syncthreads();
+    const double inv = colnorm > 0.0 ? 1.0 / colnorm : 0.0;
+    for (int r = tid; r < n; r += blockDim.x) V[r][j] *= inv;
+    __syncthreads();
+    // project column j out of the later columns: one warp per column
+    for (int k = j + 1 + (tid >> 5); k < n; k += (blockDim.x >> 5)) {
+      double d = 0.0;
+      for (int r = (tid & 31); r < n; r += 32) d = fma(V[r][j], V[r][k], d);
+      d = warp_sum(d);
+      for (int r = (tid & 31); r < n; r += 32) V[r][k] = fma(-d, V[r][j], V[r][k]);
+    }
+    __syncthreads();
+  }
+  // S' = V0^T S V0 (FP64): Tm = S V0, then S = V0^T Tm, symmetrised
+  for (int e = tid; e < n * n; e += blockDim.x) {
+    const int r = e % n, c = e / n;
+    double a = 0.0;
+    for (int k = 0; k < n; ++k) a = fma(S[r][k], V[k][c], a);
+    Tm[r][c] = a;
+  }
+  __syncthreads();
+  for (int e = tid; e < n * n; e += blockDim.x) {
+    const int r = e % n, c = e / n;
+    double a = 0.0;
+    for (int k = 0; k < n; ++k) a = fma(V[k][r], Tm[k][c], a);
+    S[r][c] = a;
+  }
+  __syncthreads();
+  for (int e = tid; e < n * n; e += blockDim.x) {
+    const int r = e % n, c = e / n;
+    if (r < c) {
+      const double m = 0.5 * (S[r][c] + S[c][r]);
+      S[r][c] = m;
+      S[c][r] = m;
+    }
+  }
+  __syncthreads();
+  // phase 3 (FP64): finish on the nearly diagonal S', rotating V0 itself
+  jacobi_sweeps<double>(S, V, n, 12, 1e-26, cs, sn, pp, qq, ring, red);
   if (tid == 0) {
     for (int i = 0; i < l; ++i) order[i] = i;
     for (int i = 1; i < l; ++i) {  // insertion sort, descending eigenvalue
@@ -700,14 +772,14 @@ void sym_eig_top_f64(const double* const* S, const int* l, const int* r, double*
   EigJob* d_jobs = current()->ws.take<EigJob>(count);
   KRP_CUDA_CHECK(cudaMemcpyAsync(d_jobs, jobs.data(), sizeof(EigJob) * count,
                                  cudaMemcpyHostToDevice, stream()));
-  const size_t smem = 2 * sizeof(double) * kEigMaxL * (kEigMaxL + 1);
+  const size_t smem = 4 * sizeof(double) * kEigMaxL * (kEigMaxL + 1);
   static bool attr_set = false;
   if (!attr_set) {
     KRP_CUDA_CHECK(cudaFuncSetAttribute(eig_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                         (int)smem));
     attr_set = true;
   }
-  eig_kernel<<<count, 256, smem, stream()>>>(d_jobs, status);
+  eig_kernel<<<count, kEigThreads, smem, stream()>>>(d_jobs, status);
   check_launch("jacobi_eig_f64");
 }
 

@@ -60,6 +60,12 @@ void tc_gemm_tn_bf16(const __nv_bfloat16* X, int64_t n1, int64_t S, const __nv_b
 void tc_mttkrp_first_bf16(const __nv_bfloat16* X, int64_t n1, int64_t n2, int64_t T,
                           const __nv_bfloat16* Om2, const float* w, int L, float* Y);
 size_t tc_workspace_bytes(int64_t n1, int64_t S, int L);
+// acc[0] += ||X - Q1 H||^2, acc[1] += ||X||^2 for BF16 X (n1 x S), Q1 FP64
+// n1 x c, H FP32 c x S, on tensor cores (c <= 64, n1 % 8 == 0)
+bool tc_residual_supported(int64_t n1, int c);
+size_t tc_residual_workspace_bytes(int64_t n1, int64_t S);
+void tc_residual_bf16(const __nv_bfloat16* X, int64_t n1, int64_t S, const double* Q1, int c,
+                      const float* H, double* acc);
 
 // weights w[t + T*k] = prod_j V_j[digit_j(t) + r_j*k] (bf16 or f32 factors)
 void krp_rows(const Radix& R, int64_t T, int L, bool bf16, float* w);

@@ -325,6 +325,7 @@ void tucker_pipeline(bool sequential, const void* X, krp_dtype xt, int d, const 
   }
   need += 4 * ws_bytes((size_t)core_l, 8) + 2 * ws_bytes((size_t)core_l, 4);
   if (xt == KRP_BF16) need += tc_workspace_bytes(dims[0], N / dims[0], 2 * ellmax);
+  if (xt == KRP_BF16 && resid) need += tc_residual_workspace_bytes(dims[0], N / dims[0]);
   need += 4 << 20;
   ensure_workspace(c, need);
   Workspace& ws = c->ws;
@@ -521,7 +522,11 @@ void tucker_pipeline(bool sequential, const void* X, krp_dtype xt, int d, const 
       curh = nx;
     }
     KRP_CUDA_CHECK(cudaMemsetAsync(acc, 0, 2 * sizeof(double), c->stream));
-    residual_f32(Xd, xt, dims[0], N / dims[0], Q1f, (int)cdim[0], curh, acc);
+    if (xt == KRP_BF16 && tc_residual_supported(dims[0], (int)cdim[0]))
+      tc_residual_bf16(static_cast<const __nv_bfloat16*>(Xd), dims[0], N / dims[0], Qout[0],
+                       (int)cdim[0], curh, acc);
+    else
+      residual_f32(Xd, xt, dims[0], N / dims[0], Q1f, (int)cdim[0], curh, acc);
   }
   tm.mark();
 

@@ -479,6 +479,195 @@ __global__ void __launch_bounds__(kThreads, 1)
   }
 }
 
+// ----------------------------------------------------------------------------
+// Residual of the BF16 form: acc[0] += ||X - Q1 H||_F^2, acc[1] += ||X||_F^2,
+// X n1 x S (BF16), Q1 n1 x c (K-major rows, BF16 hi/lo), H c x S (K-major rows
+// per s, BF16 hi/lo), c <= 64 padded to 64.  Tile = 128 rows i x 128 columns
+// s; X_hat = Qh Hh + Qh Hl + Ql Hh accumulates in TMEM (the dropped Ql Hl term
+// is below 2^-16 relative), and the epilogue compares it with the X tile that
+// TMA placed in the same pipeline stage.  A stage is released when both the
+// MMAs (tcgen05.commit) and the four epilogue warps are done with it.
+constexpr int kResN = 128;
+
+__global__ void __launch_bounds__(kThreads, 1)
+    tc_residual_kernel(const __grid_constant__ CUtensorMap mapX,
+                       const __grid_constant__ CUtensorMap mapQ,
+                       const __grid_constant__ CUtensorMap mapH, int64_t n1, int64_t S,
+                       int mblocks, double* __restrict__ acc, int* status) {
+  constexpr int NS = 2;
+  constexpr uint32_t kOp = 128 * 128;       // one 128-row x 64-element BF16 operand tile
+  constexpr uint32_t kXBox = 64 * kResN * 2;  // 64 (i) x 128 (s) BF16 = 16 KB
+  constexpr uint32_t kStage = 4 * kOp + 2 * kXBox;  // Qh Ql Hh Hl + two X boxes = 96 KB
+  constexpr uint32_t kTmemCols = 256;
+  constexpr uint32_t kIdesc = idesc_bf16(kBM, kResN, false, false);
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  Bars* bars = reinterpret_cast<Bars*>(smem + NS * kStage);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t sblocks = (S + kResN - 1) / kResN;
+  const int64_t tiles = sblocks * mblocks;  // tile = (sb, mb), mb fastest
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < NS; ++s) {
+      mbar_init(smem_u32(&bars->full[s]), 1);
+      mbar_init(smem_u32(&bars->empty[s]), 1 + 4);  // MMA commit + four epilogue warps
+    }
+    for (int a = 0; a < 2; ++a) {
+      mbar_init(smem_u32(&bars->tfull[a]), 1);
+      mbar_init(smem_u32(&bars->tempty[a]), 4);
+    }
+    mbar_init(smem_u32(&bars->drain), 1);
+    bars->abort_flag = 0;
+    bars->issued = 0;
+    bars->consumed = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  if (warp == 1) tmem_alloc(smem_u32(&bars->tmem_base), kTmemCols);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = bars->tmem_base;
+  volatile int* abort_flag = &bars->abort_flag;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      int it = 0;
+      for (int64_t tile = blockIdx.x; tile < tiles && !*abort_flag; tile += gridDim.x, ++it) {
+        const int st = it % NS;
+        const uint32_t ph = (it / NS) & 1;
+        if (!mbar_wait(smem_u32(&bars->empty[st]), ph ^ 1, abort_flag)) {
+          raise_timeout(bars, status);
+          break;
+        }
+        const int mb = static_cast<int>(tile % mblocks);
+        const int sb = static_cast<int>(tile / mblocks);
+        const uint32_t a = smem_u32(smem + st * kStage);
+        const uint32_t fb = smem_u32(&bars->full[st]);
+        mbar_expect_tx(fb, kStage);
+        tma_load_2d(a + 0 * kOp, &mapQ, fb, 0, mb * kBM);            // Qh
+        tma_load_2d(a + 1 * kOp, &mapQ, fb, 64, mb * kBM);           // Ql
+        tma_load_2d(a + 2 * kOp, &mapH, fb, 0, sb * kResN);          // Hh
+        tma_load_2d(a + 3 * kOp, &mapH, fb, 64, sb * kResN);         // Hl
+        tma_load_2d(a + 4 * kOp, &mapX, fb, mb * kBM, sb * kResN);   // X, i 0..63
+        tma_load_2d(a + 4 * kOp + kXBox, &mapX, fb, mb * kBM + 64, sb * kResN);  // i 64..127
+        bars->issued = it + 1;
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      int it = 0;
+      for (int64_t tile = blockIdx.x; tile < tiles && !*abort_flag; tile += gridDim.x, ++it) {
+        const int st = it % NS;
+        const uint32_t ph = (it / NS) & 1;
+        const int accb = it & 1;
+        const uint32_t aph = (it >> 1) & 1;
+        if (!mbar_wait(smem_u32(&bars->tempty[accb]), aph ^ 1, abort_flag) ||
+            !mbar_wait(smem_u32(&bars->full[st]), ph, abort_flag)) {
+          raise_timeout(bars, status);
+          break;
+        }
+        tc_fence_after();
+        const uint32_t a = smem_u32(smem + st * kStage);
+        const uint32_t dt = tmem + accb * kResN;
+        const uint32_t qh = a, ql = a + kOp, hh = a + 2 * kOp, hl = a + 3 * kOp;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          mma_bf16(dt, sdesc(qh + 32 * k, 16, 1024), sdesc(hh + 32 * k, 16, 1024), kIdesc, k != 0);
+          mma_bf16(dt, sdesc(qh + 32 * k, 16, 1024), sdesc(hl + 32 * k, 16, 1024), kIdesc, 1);
+          mma_bf16(dt, sdesc(ql + 32 * k, 16, 1024), sdesc(hh + 32 * k, 16, 1024), kIdesc, 1);
+        }
+        mma_commit(smem_u32(&bars->empty[st]));
+        mma_commit(smem_u32(&bars->tfull[accb]));
+        bars->consumed = it + 1;
+      }
+      mma_commit(smem_u32(&bars->drain));
+      int dummy = 0;
+      mbar_wait(smem_u32(&bars->drain), 0, reinterpret_cast<volatile int*>(&dummy));
+    }
+  } else {
+    const int q = warp & 3;
+    const int row = q * 32 + lane;  // i within the tile
+    double dsum = 0.0, xsum = 0.0;
+    int it = 0;
+    for (int64_t tile = blockIdx.x; tile < tiles; tile += gridDim.x, ++it) {
+      const int st = it % NS;
+      const uint32_t ph = (it / NS) & 1;
+      const int accb = it & 1;
+      const uint32_t aph = (it >> 1) & 1;
+      if (!mbar_wait(smem_u32(&bars->tfull[accb]), aph, abort_flag)) {
+        if (lane == 0) raise_timeout(bars, status);
+        break;
+      }
+      (void)ph;
+      tc_fence_after();
+      // X tile: box (row / 64), smem row s holds 64 i values (128 B), 16-byte
+      // chunks swizzled by (s mod 8)
+      const uint8_t* xb = smem + st * kStage + 4 * kOp + (row >> 6) * kXBox;
+      const int ii = row & 63;
+      const uint32_t base = tmem + (static_cast<uint32_t>(q * 32) << 16) + accb * kResN;
+      float d2 = 0.f, x2 = 0.f;
+#pragma unroll 1
+      for (int c0 = 0; c0 < kResN; c0 += 16) {
+        float v[16];
+        tmem_ld16(base + c0, v);
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+          const int s = c0 + j;
+          const int chunk = (ii >> 3) ^ (s & 7);
+          const __nv_bfloat16 xv =
+              *reinterpret_cast<const __nv_bfloat16*>(xb + s * 128 + chunk * 16 + (ii & 7) * 2);
+          const float x = __bfloat162float(xv);
+          const float df = x - v[j];
+          d2 = fmaf(df, df, d2);
+          x2 = fmaf(x, x, x2);
+        }
+      }
+      dsum += d2;
+      xsum += x2;
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) {
+        mbar_arrive(smem_u32(&bars->tempty[accb]));
+        mbar_arrive(smem_u32(&bars->empty[st]));
+      }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      dsum += __shfl_xor_sync(0xffffffffu, dsum, o);
+      xsum += __shfl_xor_sync(0xffffffffu, xsum, o);
+    }
+    if (lane == 0) {
+      atomicAdd(acc, dsum);
+      atomicAdd(acc + 1, xsum);
+    }
+  }
+  __syncthreads();
+  if (warp == 0 && lane == 0 && bars->abort_flag) drain_loads<NS>(bars);
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    tmem_dealloc(tmem, kTmemCols);
+  }
+}
+
+// rows of a K-major hi/lo pair: out[r * 128 + k] = hi(v), out[r * 128 + 64 + k]
+// = lo(v) for k < c (zero for c <= k < 64), v = src[k * ld_k + r * ld_r]
+template <class T>
+__global__ void pack_rows_hilo_kernel(const T* __restrict__ src, int64_t rows, int c, int64_t ld_k,
+                                      int64_t ld_r, __nv_bfloat16* __restrict__ out) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < rows * 64;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int k = static_cast<int>(e & 63);
+    const int64_t r = e >> 6;
+    float v = 0.f;
+    if (k < c) v = static_cast<float>(src[k * ld_k + r * ld_r]);
+    const __nv_bfloat16 h = __float2bfloat16_rn(v);
+    out[r * 128 + k] = h;
+    out[r * 128 + 64 + k] = __float2bfloat16_rn(v - __bfloat162float(h));
+  }
+}
+
 // combined factor buffer Fc[r * n1p + i], r < N: hi rows 0..L-1, lo rows
 // Lp..Lp+L-1, zeros elsewhere and for i >= n1.
 __global__ void pack_factor_kernel(const __nv_bfloat16* __restrict__ hi,
@@ -623,6 +812,47 @@ void tc_gemm_tn_bf16(const __nv_bfloat16* X, int64_t n1, int64_t S, const __nv_b
       else if (N == 240) launch_gemm_tn<240>(ma, mb, S, kchunks, L, Lp, has_lo, out);
       else fail(KRP_EUNSUPPORTED, "unsupported MMA width %d", N);
   }
+}
+
+size_t tc_residual_workspace_bytes(int64_t n1, int64_t S) {
+  return ws_bytes((size_t)S * 128, 2) + ws_bytes((size_t)n1 * 128, 2) + (1 << 16);
+}
+
+bool tc_residual_supported(int64_t n1, int c) { return n1 % 8 == 0 && c >= 1 && c <= 64; }
+
+void tc_residual_bf16(const __nv_bfloat16* X, int64_t n1, int64_t S, const double* Q1, int c,
+                      const float* H, double* acc) {
+  KRP_REQUIRE(tc_residual_supported(n1, c), "tensor-core residual needs n_1 %% 8 == 0 and c <= 64");
+  KRP_REQUIRE((reinterpret_cast<uintptr_t>(X) & 15) == 0, "X must be 16-byte aligned");
+  KRP_REQUIRE(S < (int64_t(1) << 31) && n1 < (int64_t(1) << 31), "tensor too large for TMA");
+  Ctx* ctx = current();
+  __nv_bfloat16* Qp = ctx->ws.take<__nv_bfloat16>((size_t)n1 * 128);
+  __nv_bfloat16* Hp = ctx->ws.take<__nv_bfloat16>((size_t)S * 128);
+  pack_rows_hilo_kernel<double><<<(int)std::min<int64_t>((n1 * 64 + 255) / 256, 4096), 256, 0, stream()>>>(
+      Q1, n1, c, n1, 1, Qp);
+  check_launch("pack_rows_hilo");
+  pack_rows_hilo_kernel<float><<<(int)std::min<int64_t>((S * 64 + 255) / 256, 8192), 256, 0, stream()>>>(
+      H, S, c, 1, c, Hp);
+  check_launch("pack_rows_hilo");
+  const uint64_t xd[2] = {(uint64_t)n1, (uint64_t)S};
+  const uint64_t xs[1] = {(uint64_t)n1 * 2};
+  const uint32_t xbox[2] = {64, kResN};
+  const CUtensorMap mx = make_map(X, 2, xd, xs, xbox);
+  const uint64_t qd[2] = {128, (uint64_t)n1};
+  const uint64_t qs[1] = {256};
+  const uint32_t qbox[2] = {64, kBM};
+  const CUtensorMap mq = make_map(Qp, 2, qd, qs, qbox);
+  const uint64_t hd[2] = {128, (uint64_t)S};
+  const uint32_t hbox[2] = {64, kResN};
+  const CUtensorMap mh = make_map(Hp, 2, hd, qs, hbox);
+  const int mblocks = static_cast<int>((n1 + kBM - 1) / kBM);
+  const int64_t tiles = ((S + kResN - 1) / kResN) * mblocks;
+  const size_t smem = 1024 + 2 * (size_t)(4 * 128 * 128 + 2 * 64 * kResN * 2) + sizeof(Bars) + 64;
+  set_smem(tc_residual_kernel, smem);
+  const int grid = static_cast<int>(std::min<int64_t>(tiles, ctx->num_sms));
+  tc_residual_kernel<<<grid, kThreads, smem, stream()>>>(mx, mq, mh, n1, S, mblocks, acc,
+                                                        ctx->d_status);
+  check_launch("tc_residual_bf16");
 }
 
 void tc_mttkrp_first_bf16(const __nv_bfloat16* X, int64_t n1, int64_t n2, int64_t T,

@@ -176,49 +176,68 @@ struct EigJob {
   int l, r;
 };
 
-// Symmetric eigensolver for one l x l FP64 matrix per CTA (l <= 64): cyclic
-// Jacobi with the parallel (round-robin) pair ordering, where every round
-// rotates l/2 disjoint pairs, updating columns (S J, V J) and then rows (J^T S).
-// GB300 issues FP32 at ~58x the FP64 rate, so the sweeps that only need to
-// bring the matrix close to diagonal run in FP32; the FP32 basis is then made
-// orthonormal in FP64 (modified Gram-Schmidt), S' = V0^T S V0 is formed in
-// FP64, and the last sweeps run in FP64 on S' while rotating V0 itself, so the
-// returned eigenvectors are orthonormal and accurate to FP64 rounding.
+// Symmetric eigensolver for one l x l FP64 matrix per CTA (l <= 64), in two
+// stages.  GB300 issues FP32 at ~58x its FP64 rate, so
+//  1. cyclic Jacobi runs in FP32 on the matrix scaled by a power of two, with
+//     the parallel (round-robin) pair ordering: each round rotates n/2
+//     disjoint pairs (p_k, q_k).  The two-sided update S <- J^T S J of a round
+//     maps every 2 x 2 block {p_i, q_i} x {p_j, q_j} onto itself, so each
+//     thread updates whole blocks in place and a round needs two barriers;
+//  2. the FP32 eigenvectors are refined in FP64 by the iteration of Ogita and
+//     Aishima (Japan J. Indust. Appl. Math. 35, 2018), which uses only matrix
+//     products: with R = I - X^T X and S = X^T A X, lambda_i = s_ii / (1 - r_ii),
+//     E_ij = (s_ij + lambda_j r_ij) / (lambda_j - lambda_i) for eigenvalues
+//     further apart than delta = 2 (||S - diag(lambda)|| + ||A|| ||R||), else
+//     E_ij = r_ij / 2, and X <- X + X E.  It converges quadratically, so two
+//     steps take the FP32 start (error ~1e-7) to FP64 rounding; within a
+//     cluster narrower than delta it only restores orthonormality.
 constexpr int kEP = kEigMaxL + 1;  // padded row pitch
+constexpr int kEigThreads = 256;
+constexpr int kEigRefine = 2;
+constexpr int kEigSweeps32 = 15;
 
-template <class T>
-__device__ void jacobi_sweeps(T (*S)[kEP], T (*V)[kEP], int n, int max_sweeps, double tol,
-                              T* cs, T* sn, int* pp, int* qq, int* ring, double* red) {
-  const int tid = threadIdx.x;
-  for (int sweep = 0; sweep < max_sweeps; ++sweep) {
-    if (tid == 0) {
-      red[0] = 0.0;
-      red[1] = 0.0;
+__device__ __forceinline__ float warp_max(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+
+// Block-wide sum of one value per thread (all threads call it).
+__device__ double block_sum(double v, double* red) {
+  const int tid = threadIdx.x, nw = blockDim.x >> 5;
+  v = warp_sum(v);
+  __syncthreads();
+  if ((tid & 31) == 0) red[tid >> 5] = v;
+  __syncthreads();
+  double s = 0.0;
+  for (int w = 0; w < nw; ++w) s += red[w];
+  return s;
+}
+
+__device__ void jacobi32(float (*S)[kEP], float (*V)[kEP], int n, float* cs, float* sn, int* pp,
+                         int* qq, double* red) {
+  const int tid = threadIdx.x, P = n / 2;
+  for (int sweep = 0; sweep < kEigSweeps32; ++sweep) {
+    double o = 0.0, dg = 0.0;
+    for (int e = tid; e < n * n; e += blockDim.x) {
+      const int r = e % n, c = e / n;
+      const double v = (double)S[r][c] * (double)S[r][c];
+      if (r == c)
+        dg += v;
+      else
+        o += v;
     }
-    for (int i = tid; i < n; i += blockDim.x) ring[i] = i;
-    __syncthreads();
-    {
-      double o = 0.0, dg = 0.0;
-      for (int e = tid; e < n * n; e += blockDim.x) {
-        const int r = e % n, c = e / n;
-        const double v = (double)S[r][c] * (double)S[r][c];
-        if (r == c)
-          dg += v;
-        else
-          o += v;
-      }
-      o = warp_sum(o);
-      dg = warp_sum(dg);
-      if ((tid & 31) == 0) {
-        atomicAdd(&red[0], o);
-        atomicAdd(&red[1], dg);
-      }
-    }
-    __syncthreads();
-    if (!(red[0] > tol * red[1]) || red[0] == 0.0) break;
+    const double off = block_sum(o, red);
+    const double dia = block_sum(dg, red + 8);
+    // off-diagonal norm at 1e-6 of the diagonal's: the FP64 stage does the rest
+    if (!(off > 1e-12 * dia) || off == 0.0) break;
     for (int round = 0; round < n - 1; ++round) {
-      if (tid < n / 2) {
-        int p = ring[tid], q = ring[n - 1 - tid];
+      if (tid < P) {
+        // round-robin tournament: position 0 holds player 0, position k >= 1
+        // holds player ((k - 1 + round) mod (n - 1)) + 1; pairs (k, n-1-k)
+        const int k2 = n - 1 - tid;
+        int p = (tid == 0) ? 0 : ((tid - 1 + round) % (n - 1)) + 1;
+        int q = ((k2 - 1 + round) % (n - 1)) + 1;
         if (p > q) {
           const int t = p;
           p = q;
@@ -226,155 +245,178 @@ __device__ void jacobi_sweeps(T (*S)[kEP], T (*V)[kEP], int n, int max_sweeps, d
         }
         pp[tid] = p;
         qq[tid] = q;
-        const T apq = S[p][q];
-        T c = T(1), s = T(0);
-        const T app = S[p][p], aqq = S[q][q];
-        const T thr = (sizeof(T) == 8 ? T(1e-16) : T(1e-8)) * sqrt(fabs(app * aqq));
-        if (fabs(apq) > thr) {
-          const T theta = (aqq - app) / (T(2) * apq);
-          const T t = (theta >= T(0) ? T(1) : T(-1)) / (fabs(theta) + sqrt(T(1) + theta * theta));
-          c = T(1) / sqrt(T(1) + t * t);
+        const float apq = S[p][q], app = S[p][p], aqq = S[q][q];
+        float c = 1.f, s = 0.f;
+        if (fabsf(apq) > 1e-8f * sqrtf(fabsf(app * aqq))) {
+          const float theta = (aqq - app) / (2.f * apq);
+          const float t = (theta >= 0.f ? 1.f : -1.f) / (fabsf(theta) + sqrtf(1.f + theta * theta));
+          c = 1.f / sqrtf(1.f + t * t);
           s = t * c;
         }
         cs[tid] = c;
         sn[tid] = s;
       }
       __syncthreads();
-      for (int e = tid; e < (n / 2) * n; e += blockDim.x) {
-        const int k = e % (n / 2), r = e / (n / 2);
-        const int p = pp[k], q = qq[k];
-        const T c = cs[k], s = sn[k];
-        const T sp = S[r][p], sq = S[r][q];
-        S[r][p] = c * sp - s * sq;
-        S[r][q] = s * sp + c * sq;
-        const T vp = V[r][p], vq = V[r][q];
-        V[r][p] = c * vp - s * vq;
-        V[r][q] = s * vp + c * vq;
-      }
-      __syncthreads();
-      for (int e = tid; e < (n / 2) * n; e += blockDim.x) {
-        const int k = e % (n / 2), col = e / (n / 2);
-        const int p = pp[k], q = qq[k];
-        const T c = cs[k], s = sn[k];
-        const T sp = S[p][col], sq = S[q][col];
-        S[p][col] = c * sp - s * sq;
-        S[q][col] = s * sp + c * sq;
-      }
-      __syncthreads();
-      if (tid == 0) {  // rotate the ring, keeping element 0 fixed
-        const int last = ring[n - 1];
-        for (int i = n - 1; i > 1; --i) ring[i] = ring[i - 1];
-        ring[1] = last;
+      for (int b = tid; b < P * P + n * P; b += blockDim.x) {
+        if (b < P * P) {
+          const int i = b % P, j = b / P;
+          const int pi = pp[i], qi = qq[i], pj = pp[j], qj = qq[j];
+          const float ci = cs[i], si = sn[i], cj = cs[j], sj = sn[j];
+          const float a = S[pi][pj], bq = S[pi][qj], cq = S[qi][pj], d = S[qi][qj];
+          // columns (p_j, q_j), then rows (p_i, q_i)
+          const float a1 = cj * a - sj * bq, b1 = sj * a + cj * bq;
+          const float c1 = cj * cq - sj * d, d1 = sj * cq + cj * d;
+          float a2 = ci * a1 - si * c1, c2 = si * a1 + ci * c1;
+          float b2 = ci * b1 - si * d1, d2 = si * b1 + ci * d1;
+          if (i == j && si != 0.f) {  // the rotated pair's coupling is zero by construction
+            b2 = 0.f;
+            c2 = 0.f;
+          }
+          S[pi][pj] = a2;
+          S[pi][qj] = b2;
+          S[qi][pj] = c2;
+          S[qi][qj] = d2;
+        } else {
+          const int e = b - P * P;
+          const int k = e % P, r = e / P;
+          const int p = pp[k], q = qq[k];
+          const float c = cs[k], s = sn[k];
+          const float vp = V[r][p], vq = V[r][q];
+          V[r][p] = c * vp - s * vq;
+          V[r][q] = s * vp + c * vq;
+        }
       }
       __syncthreads();
     }
   }
 }
 
-constexpr int kEigThreads = 1024;  // many warps to hide FP64 and shared-memory latency
+// C = op(A) B for l x l matrices in shared memory (op = transpose if TA);
+// with SYM only the upper triangle is computed and mirrored.
+template <bool TA, bool SYM>
+__device__ void smem_gemm(const double (*A)[kEP], const double (*B)[kEP], double (*C)[kEP], int l) {
+  for (int e = threadIdx.x; e < l * l; e += blockDim.x) {
+    const int i = e % l, j = e / l;
+    if (SYM && i > j) continue;
+    double acc = 0.0;
+    for (int k = 0; k < l; ++k) acc = fma(TA ? A[k][i] : A[i][k], B[k][j], acc);
+    C[i][j] = acc;
+    if (SYM) C[j][i] = acc;
+  }
+}
 
 __global__ void __launch_bounds__(kEigThreads) eig_kernel(const EigJob* __restrict__ jobs, int* status) {
   const EigJob job = jobs[blockIdx.x];
   const int l = job.l;
   const int n = (l + 1) & ~1;  // padded to even for the tournament
   extern __shared__ double eig_smem[];
-  double(*S)[kEP] = reinterpret_cast<double(*)[kEP]>(eig_smem);
-  double(*V)[kEP] = reinterpret_cast<double(*)[kEP]>(eig_smem + kEigMaxL * kEP);
-  double(*Tm)[kEP] = reinterpret_cast<double(*)[kEP]>(eig_smem + 2 * kEigMaxL * kEP);
-  float(*S32)[kEP] = reinterpret_cast<float(*)[kEP]>(eig_smem + 3 * kEigMaxL * kEP);
-  float(*V32)[kEP] = reinterpret_cast<float(*)[kEP]>(eig_smem + 3 * kEigMaxL * kEP) + kEigMaxL;
-  __shared__ double cs[kEigMaxL / 2], sn[kEigMaxL / 2];
+  constexpr int kMat = kEigMaxL * kEP;
+  double(*A)[kEP] = reinterpret_cast<double(*)[kEP]>(eig_smem);
+  double(*X)[kEP] = reinterpret_cast<double(*)[kEP]>(eig_smem + kMat);
+  double(*T)[kEP] = reinterpret_cast<double(*)[kEP]>(eig_smem + 2 * kMat);
+  double(*Sm)[kEP] = reinterpret_cast<double(*)[kEP]>(eig_smem + 3 * kMat);
+  double(*Rm)[kEP] = reinterpret_cast<double(*)[kEP]>(eig_smem + 4 * kMat);
+  // the FP32 stage lives in T's storage
+  float(*S32)[kEP] = reinterpret_cast<float(*)[kEP]>(eig_smem + 2 * kMat);
+  float(*V32)[kEP] = reinterpret_cast<float(*)[kEP]>(eig_smem + 2 * kMat) + kEigMaxL;
   __shared__ float cs32[kEigMaxL / 2], sn32[kEigMaxL / 2];
   __shared__ int pp[kEigMaxL / 2], qq[kEigMaxL / 2];
   __shared__ int order[kEigMaxL];
-  __shared__ int ring[kEigMaxL];
-  __shared__ double red[2];
-  __shared__ double colnorm;
+  __shared__ double lam[kEigMaxL];
+  __shared__ double red[16];
+  __shared__ float redf[8];
   const int tid = threadIdx.x;
+
+  // scale by a power of two (exact) so that max |a_ij| is in [0.5, 1)
+  float amax = 0.f;
+  for (int e = tid; e < l * l; e += blockDim.x) amax = fmaxf(amax, (float)fabs(job.S[e]));
+  amax = warp_max(amax);
+  if ((tid & 31) == 0) redf[tid >> 5] = amax;
+  __syncthreads();
+  amax = 0.f;
+  for (int w = 0; w < (int)(blockDim.x >> 5); ++w) amax = fmaxf(amax, redf[w]);
+  int ex = 0;
+  if (amax > 0.f && isfinite(amax)) frexpf(amax, &ex);
+  const double scale = ldexp(1.0, -ex);
+  bool finite_in = true;
   for (int e = tid; e < n * n; e += blockDim.x) {
     const int r = e % n, c = e / n;
-    const double v = (r < l && c < l) ? job.S[r + l * c] : 0.0;
-    S[r][c] = v;
+    const double v = (r < l && c < l) ? job.S[r + l * c] * scale : 0.0;
+    finite_in = finite_in && isfinite(v);
+    A[r][c] = v;
     S32[r][c] = (float)v;
     V32[r][c] = (r == c) ? 1.f : 0.f;
   }
-  __syncthreads();
-  // phase 1 (FP32): most of the sweeps
-  jacobi_sweeps<float>(S32, V32, n, 20, 1e-12, cs32, sn32, pp, qq, ring, red);
-  // phase 2 (FP64): V0 = orthonormalised V32 (modified Gram-Schmidt on columns)
-  for (int e = tid; e < n * n; e += blockDim.x) {
-    const int r = e % n, c = e / n;
-    V[r][c] = (double)V32[r][c];
+  if (!__syncthreads_and(finite_in)) {
+    if (tid == 0) atomicExch(status, (int)KRP_ENUMERIC);
+    return;
+  }
+  jacobi32(S32, V32, n, cs32, sn32, pp, qq, red);
+  for (int e = tid; e < l * l; e += blockDim.x) {
+    const int r = e % l, c = e / l;
+    X[r][c] = (double)V32[r][c];
   }
   __syncthreads();
-  for (int j = 0; j < n; ++j) {
-    if (tid < 32) {
-      double s = 0.0;
-      for (int r = tid; r < n; r += 32) s = fma(V[r][j], V[r][j], s);
-      s = warp_sum(s);
-      if (tid == 0) colnorm = sqrt(s);
+  double a2 = 0.0;
+  for (int e = tid; e < l * l; e += blockDim.x) a2 = fma(A[e % l][e / l], A[e % l][e / l], a2);
+  const double anorm = sqrt(block_sum(a2, red));
+  for (int it = 0; it < kEigRefine; ++it) {
+    smem_gemm<false, false>(A, X, T, l);  // T = A X
+    __syncthreads();
+    smem_gemm<true, true>(X, T, Sm, l);  // S = X^T A X
+    smem_gemm<true, true>(X, X, Rm, l);  // X^T X (turned into R below)
+    __syncthreads();
+    double soff = 0.0, r2 = 0.0;
+    for (int e = tid; e < l * l; e += blockDim.x) {
+      const int i = e % l, j = e / l;
+      const double rij = (i == j ? 1.0 : 0.0) - Rm[i][j];
+      r2 = fma(rij, rij, r2);
+      if (i != j) soff = fma(Sm[i][j], Sm[i][j], soff);
+    }
+    for (int i = tid; i < l; i += blockDim.x) lam[i] = Sm[i][i] / Rm[i][i];  // 1 - r_ii = (X^T X)_ii
+    const double sn = block_sum(soff, red);  // diag(S) - lambda is second order: left out
+    const double rn = block_sum(r2, red + 8);
+    const double delta = 2.0 * (sqrt(sn) + anorm * sqrt(rn));
+    // E (into T): built from the symmetric S and R, read before any write
+    for (int e = tid; e < l * l; e += blockDim.x) {
+      const int i = e % l, j = e / l;
+      const double rij = (i == j ? 1.0 : 0.0) - Rm[i][j];
+      double eij = 0.5 * rij;
+      const double gap = lam[j] - lam[i];
+      if (i != j && fabs(gap) > delta) eij = (Sm[i][j] + lam[j] * rij) / gap;
+      T[i][j] = eij;
     }
     __syncthreads();
-    const double inv = colnorm > 0.0 ? 1.0 / colnorm : 0.0;
-    for (int r = tid; r < n; r += blockDim.x) V[r][j] *= inv;
+    smem_gemm<false, false>(X, T, Sm, l);  // X E
     __syncthreads();
-    // project column j out of the later columns: one warp per column
-    for (int k = j + 1 + (tid >> 5); k < n; k += (blockDim.x >> 5)) {
-      double d = 0.0;
-      for (int r = (tid & 31); r < n; r += 32) d = fma(V[r][j], V[r][k], d);
-      d = warp_sum(d);
-      for (int r = (tid & 31); r < n; r += 32) V[r][k] = fma(-d, V[r][j], V[r][k]);
+    for (int e = tid; e < l * l; e += blockDim.x) {
+      const int i = e % l, j = e / l;
+      X[i][j] += Sm[i][j];
     }
     __syncthreads();
   }
-  // S' = V0^T S V0 (FP64): Tm = S V0, then S = V0^T Tm, symmetrised
-  for (int e = tid; e < n * n; e += blockDim.x) {
-    const int r = e % n, c = e / n;
-    double a = 0.0;
-    for (int k = 0; k < n; ++k) a = fma(S[r][k], V[k][c], a);
-    Tm[r][c] = a;
-  }
-  __syncthreads();
-  for (int e = tid; e < n * n; e += blockDim.x) {
-    const int r = e % n, c = e / n;
-    double a = 0.0;
-    for (int k = 0; k < n; ++k) a = fma(V[k][r], Tm[k][c], a);
-    S[r][c] = a;
-  }
-  __syncthreads();
-  for (int e = tid; e < n * n; e += blockDim.x) {
-    const int r = e % n, c = e / n;
-    if (r < c) {
-      const double m = 0.5 * (S[r][c] + S[c][r]);
-      S[r][c] = m;
-      S[c][r] = m;
-    }
-  }
-  __syncthreads();
-  // phase 3 (FP64): finish on the nearly diagonal S', rotating V0 itself
-  jacobi_sweeps<double>(S, V, n, 12, 1e-26, cs, sn, pp, qq, ring, red);
   if (tid == 0) {
     for (int i = 0; i < l; ++i) order[i] = i;
     for (int i = 1; i < l; ++i) {  // insertion sort, descending eigenvalue
       const int key = order[i];
       int j = i - 1;
-      while (j >= 0 && S[order[j]][order[j]] < S[key][key]) {
+      while (j >= 0 && lam[order[j]] < lam[key]) {
         order[j + 1] = order[j];
         --j;
       }
       order[j + 1] = key;
     }
     bool ok = true;
-    for (int i = 0; i < l; ++i) ok = ok && isfinite(S[i][i]);
+    for (int i = 0; i < l; ++i) ok = ok && isfinite(lam[i]);
     if (!ok) atomicExch(status, (int)KRP_ENUMERIC);
   }
   __syncthreads();
   for (int e = tid; e < l * job.r; e += blockDim.x) {
     const int r = e % l, c = e / l;
-    job.U[e] = V[r][order[c]];
+    job.U[e] = X[r][order[c]];
   }
   if (job.ev)
-    for (int i = tid; i < l; i += blockDim.x) job.ev[i] = S[order[i]][order[i]];
+    for (int i = tid; i < l; i += blockDim.x) job.ev[i] = lam[order[i]] / scale;
 }
 
 // out = G x_mode U^T: out[p + P*a + P*r*s] = sum_i G[p + P*i + P*n*s] U[i + n*a]
@@ -772,7 +814,7 @@ void sym_eig_top_f64(const double* const* S, const int* l, const int* r, double*
   EigJob* d_jobs = current()->ws.take<EigJob>(count);
   KRP_CUDA_CHECK(cudaMemcpyAsync(d_jobs, jobs.data(), sizeof(EigJob) * count,
                                  cudaMemcpyHostToDevice, stream()));
-  const size_t smem = 4 * sizeof(double) * kEigMaxL * (kEigMaxL + 1);
+  const size_t smem = 5 * sizeof(double) * kEigMaxL * kEP;
   static bool attr_set = false;
   if (!attr_set) {
     KRP_CUDA_CHECK(cudaFuncSetAttribute(eig_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,

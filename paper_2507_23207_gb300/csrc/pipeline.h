@@ -62,6 +62,13 @@ void tc_mttkrp_first_bf16(const __nv_bfloat16* X, int64_t n1, int64_t n2, int64_
 size_t tc_workspace_bytes(int64_t n1, int64_t S, int L);
 // acc[0] += ||X - Q1 H||^2, acc[1] += ||X||^2 for BF16 X (n1 x S), Q1 FP64
 // n1 x c, H FP32 c x S, on tensor cores (c <= 64, n1 % 8 == 0)
+// One pass over BF16 X (n1, n2, T) for the dimension tree: Y1 (n1 x L),
+// Y2 (n2 x L) and C (T x L, the contraction of modes 1 and 2 weighted by the
+// factors); w is the T x L table of Khatri-Rao weights of modes 3..d.
+bool tc_tree_supported(int64_t n1, int L);
+void tc_tree_bf16(const __nv_bfloat16* X, int64_t n1, int64_t n2, int64_t T,
+                  const __nv_bfloat16* Om1, const __nv_bfloat16* Om2, const float* w, int L,
+                  float* Y1, float* Y2, float* C);
 bool tc_residual_supported(int64_t n1, int c);
 size_t tc_residual_workspace_bytes(int64_t n1, int64_t S);
 void tc_residual_bf16(const __nv_bfloat16* X, int64_t n1, int64_t S, const double* Q1, int c,

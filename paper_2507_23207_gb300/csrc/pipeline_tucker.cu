@@ -230,6 +230,25 @@ void sketch_all_modes(const SketchArgs& a, float* const* Y) {
   const int64_t n1 = a.dims[0], S = a.N / n1;
   const float* f32v[KRP_MAXD];
   f32_factor_views(a, f32v);
+  if (a.xt == KRP_BF16 && tc_tree_supported(n1, a.ell)) {
+    // one pass over X for every mode (fused dimension tree on tensor cores)
+    const int64_t n2 = a.dims[1], T = S / n2;
+    Radix R;
+    R.n = a.d - 2;
+    for (int j = 2; j < a.d; ++j) {
+      R.radix[j - 2] = a.dims[j];
+      R.V[j - 2] = static_cast<const float*>(a.omega[j]);  // bf16 bits
+    }
+    float* w = current()->ws.take<float>((size_t)T * a.ell);
+    krp_rows(R, T, a.ell, true, w);
+    float* C = (a.d == 3) ? Y[2] : current()->ws.take<float>((size_t)T * a.ell);
+    tc_tree_bf16(static_cast<const __nv_bfloat16*>(a.X), n1, n2, T,
+                 static_cast<const __nv_bfloat16*>(a.omega[0]),
+                 static_cast<const __nv_bfloat16*>(a.omega[1]), w, a.ell, Y[0], Y[1], C);
+    for (int n = 2; n < a.d && a.d > 3; ++n)
+      diag_contract_f32(C, a.d - 2, a.dims + 2, T, n - 2, f32v + 2, a.ell, Y[n]);
+    return;
+  }
   big_mttkrp_first(a.X, a.xt, n1, a.d - 1, a.dims + 1, a.omega + 1, a.ell, Y[0]);
   float* B = current()->ws.take<float>((size_t)S * a.ell);
   big_gemm_tn(a.X, a.xt, n1, S, f32v[0], static_cast<const __nv_bfloat16*>(a.omega[0]), nullptr,

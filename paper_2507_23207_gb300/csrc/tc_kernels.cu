@@ -480,6 +480,262 @@ __global__ void __launch_bounds__(kThreads, 1)
 }
 
 // ----------------------------------------------------------------------------
+// Dimension tree in one pass over X (Sec. 5.1, memoization): X viewed as
+// (n1, n2, T), T = prod_{j>=3} n_j, w[t, k] = prod_{j>=3} Omega_j[i_j(t), k].
+// A CTA owns one 128-row block b of i2 and a range of slabs t; every stage
+// holds X[128 i1, 128 i2, t] (two 64-wide TMA boxes) and is read twice by the
+// tensor core:
+//   MMA1 (K-major, rows i2, K = i1):  D1[i2, k] = sum_i1 X Omega1      (per t)
+//   MMA2 (MN-major, M = i1, K = i2):  D2[i1, k] += sum_i2 X B2_t,
+//        B2_t[i2, k] = Omega2[i2, k] w[t, k] as a BF16 hi/lo pair written to
+//        shared memory by a producer warpgroup (D2 accumulates over all t).
+// Epilogue per t: Y2[i2, k] += D1 w[t, k] (registers across t) and
+// C[t, k] += sum_i2 Omega2[i2, k] D1[i2, k]; at the end D2 -> Y1.
+// For d = 3, C is Y3 itself.
+struct TreeArgs {
+  const float* w;            // T x L
+  const __nv_bfloat16* om2;  // n2 x L (column-major)
+  float* Y1;                 // n1 x L
+  float* Y2;                 // n2 x L
+  float* C;                  // T x L
+  int64_t n1, n2, T, t_per_cta;
+  int L, nb, kchunks;        // kchunks = ceil(n1 / 128)
+};
+
+template <int N>
+__global__ void __launch_bounds__(320, 1)
+    tc_tree_kernel(const __grid_constant__ CUtensorMap mapX,
+                   const __grid_constant__ CUtensorMap mapF, const TreeArgs P, int* status) {
+  constexpr int NS = 3;
+  constexpr uint32_t kXBox = 64 * 128 * 2;            // 64 i1 x 128 i2
+  constexpr uint32_t kFBox = N * 128;                 // N rows (k) x 64 i1
+  constexpr uint32_t kStage = 2 * kXBox + 2 * kFBox;
+  constexpr uint32_t kB2Atom = N * 128;               // N rows (k) x 64 i2
+  constexpr uint32_t kB2Buf = 4 * kB2Atom;            // hi (2 atoms) + lo (2 atoms)
+  constexpr uint32_t kIdesc1 = idesc_bf16(kBM, N, false, false);
+  constexpr uint32_t kIdesc2 = idesc_bf16(kBM, N, true, false);
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  uint8_t* b2 = smem + NS * kStage;
+  Bars* bars = reinterpret_cast<Bars*>(b2 + 2 * kB2Buf);
+  __shared__ uint64_t b2full[2], b2empty[2];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int b = blockIdx.x % P.nb;
+  const int64_t t0 = static_cast<int64_t>(blockIdx.x / P.nb) * P.t_per_cta;
+  const int64_t t1 = min(P.T, t0 + P.t_per_cta);
+  const int kch = P.kchunks;
+  const uint32_t tmem_cols = 512;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < NS; ++s) {
+      mbar_init(smem_u32(&bars->full[s]), 1);
+      mbar_init(smem_u32(&bars->empty[s]), 1);
+    }
+    for (int a = 0; a < 2; ++a) {
+      mbar_init(smem_u32(&bars->tfull[a]), 1);
+      mbar_init(smem_u32(&bars->tempty[a]), 4);
+      mbar_init(smem_u32(&b2full[a]), 4);
+      mbar_init(smem_u32(&b2empty[a]), 1);
+    }
+    mbar_init(smem_u32(&bars->drain), 1);
+    bars->abort_flag = 0;
+    bars->issued = 0;
+    bars->consumed = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  if (warp == 1) tmem_alloc(smem_u32(&bars->tmem_base), tmem_cols);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = bars->tmem_base;  // D1 buffers at 0 and N; D2 chunk c at (2 + c) N
+  volatile int* abort_flag = &bars->abort_flag;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      int it = 0;
+      for (int64_t t = t0; t < t1 && !*abort_flag; ++t) {
+        for (int c = 0; c < kch; ++c, ++it) {
+          const int st = it % NS;
+          const uint32_t ph = (it / NS) & 1;
+          if (!mbar_wait(smem_u32(&bars->empty[st]), ph ^ 1, abort_flag)) {
+            raise_timeout(bars, status);
+            break;
+          }
+          const uint32_t a = smem_u32(smem + st * kStage);
+          const uint32_t fb = smem_u32(&bars->full[st]);
+          mbar_expect_tx(fb, kStage);
+          tma_load_3d(a, &mapX, fb, c * 128, b * 128, static_cast<int>(t));
+          tma_load_3d(a + kXBox, &mapX, fb, c * 128 + 64, b * 128, static_cast<int>(t));
+          tma_load_2d(a + 2 * kXBox, &mapF, fb, c * 128, 0);
+          tma_load_2d(a + 2 * kXBox + kFBox, &mapF, fb, c * 128 + 64, 0);
+          bars->issued = it + 1;
+        }
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      int it = 0, tl = 0;
+      for (int64_t t = t0; t < t1 && !*abort_flag; ++t, ++tl) {
+        const int acc = tl & 1;
+        const uint32_t aph = (tl >> 1) & 1;
+        if (!mbar_wait(smem_u32(&bars->tempty[acc]), aph ^ 1, abort_flag) ||
+            !mbar_wait(smem_u32(&b2full[acc]), aph, abort_flag)) {
+          raise_timeout(bars, status);
+          break;
+        }
+        tc_fence_after();
+        const uint32_t d1 = tmem + acc * N;
+        const uint32_t b2b = smem_u32(b2 + acc * kB2Buf);
+        bool ok = true;
+        for (int c = 0; c < kch; ++c, ++it) {
+          const int st = it % NS;
+          const uint32_t ph = (it / NS) & 1;
+          if (!mbar_wait(smem_u32(&bars->full[st]), ph, abort_flag)) {
+            raise_timeout(bars, status);
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const uint32_t a = smem_u32(smem + st * kStage);
+          const uint32_t f = a + 2 * kXBox;
+          // MMA1: rows i2, K = i1 (two 64-wide boxes, 4 K-steps each)
+#pragma unroll
+          for (int h = 0; h < 2; ++h)
+#pragma unroll
+            for (int k = 0; k < 4; ++k)
+              mma_bf16(d1, sdesc(a + h * kXBox + 32 * k, 16, 1024),
+                       sdesc(f + h * kFBox + 32 * k, 16, 1024), kIdesc1, (c | h | k) != 0);
+          // MMA2: M = i1 (the two boxes kXBox apart), K = i2 (128 rows, 8 K-steps),
+          // B = B2_t hi then lo (two 64-wide K atoms each)
+          const uint32_t d2 = tmem + (2 + c) * N;
+#pragma unroll
+          for (int k = 0; k < 8; ++k) {
+            const uint32_t adesc_lo = a + 2048 * k;
+            const uint32_t batom = (k >> 2) * kB2Atom + 32 * (k & 3);
+            mma_bf16(d2, sdesc(adesc_lo, kXBox, 1024), sdesc(b2b + batom, 16, 1024), kIdesc2,
+                     (tl != 0 || k != 0) ? 1u : 0u);
+            mma_bf16(d2, sdesc(adesc_lo, kXBox, 1024), sdesc(b2b + 2 * kB2Atom + batom, 16, 1024),
+                     kIdesc2, 1u);
+          }
+          mma_commit(smem_u32(&bars->empty[st]));
+          bars->consumed = it + 1;
+        }
+        if (!ok) break;
+        mma_commit(smem_u32(&bars->tfull[acc]));
+        mma_commit(smem_u32(&b2empty[acc]));
+      }
+      mma_commit(smem_u32(&bars->drain));
+      int dummy = 0;
+      mbar_wait(smem_u32(&bars->drain), 0, reinterpret_cast<volatile int*>(&dummy));
+    }
+  } else if (warp >= 6) {
+    // B2 producer warpgroup: B2_t[i2, k] = Omega2[i2, k] w[t, k] in the K-major
+    // 128-byte swizzled layout (rows k, 64 i2 per atom), as BF16 hi and lo.
+    const int tid = threadIdx.x - 192;  // 0..127, one i2 row each
+    const int64_t i2 = static_cast<int64_t>(b) * 128 + tid;
+    float om[N];
+#pragma unroll
+    for (int k = 0; k < N; ++k)
+      om[k] = (k < P.L && i2 < P.n2) ? __bfloat162float(P.om2[i2 + P.n2 * k]) : 0.f;
+    int tl = 0;
+    for (int64_t t = t0; t < t1; ++t, ++tl) {
+      const int buf = tl & 1;
+      const uint32_t ph = (tl >> 1) & 1;
+      if (!mbar_wait(smem_u32(&b2empty[buf]), ph ^ 1, abort_flag)) {
+        if (lane == 0) raise_timeout(bars, status);
+        break;
+      }
+      uint8_t* base = b2 + buf * kB2Buf + (tid >> 6) * kB2Atom;
+      const int col = tid & 63;
+#pragma unroll
+      for (int k = 0; k < N; ++k) {
+        const float v = (k < P.L) ? om[k] * __ldg(P.w + t + P.T * k) : 0.f;
+        const __nv_bfloat16 hi = __float2bfloat16_rn(v);
+        const __nv_bfloat16 lo = __float2bfloat16_rn(v - __bfloat162float(hi));
+        const uint32_t off = k * 128 + ((((col >> 3) ^ (k & 7)) << 4)) + (col & 7) * 2;
+        *reinterpret_cast<__nv_bfloat16*>(base + off) = hi;
+        *reinterpret_cast<__nv_bfloat16*>(base + 2 * kB2Atom + off) = lo;
+      }
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      __syncwarp();
+      if (lane == 0) mbar_arrive(smem_u32(&b2full[buf]));
+    }
+  } else {
+    const int q = warp & 3;
+    const int row = q * 32 + lane;  // i2 within the block
+    const int64_t i2 = static_cast<int64_t>(b) * 128 + row;
+    const bool valid = i2 < P.n2;
+    float y2[N];
+    float o2[N];
+#pragma unroll
+    for (int k = 0; k < N; ++k) {
+      y2[k] = 0.f;
+      o2[k] = (valid && k < P.L) ? __bfloat162float(P.om2[i2 + P.n2 * k]) : 0.f;
+    }
+    int tl = 0;
+    for (int64_t t = t0; t < t1; ++t, ++tl) {
+      const int acc = tl & 1;
+      const uint32_t ph = (tl >> 1) & 1;
+      if (!mbar_wait(smem_u32(&bars->tfull[acc]), ph, abort_flag)) {
+        if (lane == 0) raise_timeout(bars, status);
+        break;
+      }
+      tc_fence_after();
+      const uint32_t base = tmem + (static_cast<uint32_t>(q * 32) << 16) + acc * N;
+#pragma unroll
+      for (int c0 = 0; c0 < N; c0 += 16) {
+        float v[16];
+        tmem_ld16(base + c0, v);
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+          const int k = c0 + j;
+          const float wk = (k < P.L) ? __ldg(P.w + t + P.T * k) : 0.f;
+          y2[k] = fmaf(v[j], wk, y2[k]);
+          float cp = v[j] * o2[k];
+#pragma unroll
+          for (int o = 16; o > 0; o >>= 1) cp += __shfl_xor_sync(0xffffffffu, cp, o);
+          // each warp adds its 32-row partial of C[t, k] (no cross-warp barrier)
+          if (lane == 0 && k < P.L) atomicAdd(P.C + t + P.T * k, cp);
+        }
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(smem_u32(&bars->tempty[acc]));
+    }
+    if (valid) {
+#pragma unroll
+      for (int k = 0; k < N; ++k)
+        if (k < P.L) atomicAdd(P.Y2 + i2 + P.n2 * k, y2[k]);
+    }
+    // D2 (all MMAs are complete once the last tfull has been observed)
+    if (t1 > t0) {
+      tc_fence_after();
+      for (int c = 0; c < kch; ++c) {
+        const int64_t i1 = static_cast<int64_t>(c) * 128 + row;
+        const uint32_t base = tmem + (static_cast<uint32_t>(q * 32) << 16) + (2 + c) * N;
+#pragma unroll
+        for (int c0 = 0; c0 < N; c0 += 16) {
+          float v[16];
+          tmem_ld16(base + c0, v);
+          if (i1 < P.n1)
+#pragma unroll
+            for (int j = 0; j < 16; ++j)
+              if (c0 + j < P.L) atomicAdd(P.Y1 + i1 + P.n1 * (c0 + j), v[j]);
+        }
+      }
+    }
+  }
+  __syncthreads();
+  if (warp == 0 && lane == 0 && bars->abort_flag) drain_loads<NS>(bars);
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    tmem_dealloc(tmem, tmem_cols);
+  }
+}
+
+// ----------------------------------------------------------------------------
 // Residual of the BF16 form: acc[0] += ||X - Q1 H||_F^2, acc[1] += ||X||_F^2,
 // X n1 x S (BF16), Q1 n1 x c (K-major rows, BF16 hi/lo), H c x S (K-major rows
 // per s, BF16 hi/lo), c <= 64 padded to 64.  Tile = 128 rows i x 128 columns
@@ -812,6 +1068,68 @@ void tc_gemm_tn_bf16(const __nv_bfloat16* X, int64_t n1, int64_t S, const __nv_b
       else if (N == 240) launch_gemm_tn<240>(ma, mb, S, kchunks, L, Lp, has_lo, out);
       else fail(KRP_EUNSUPPORTED, "unsupported MMA width %d", N);
   }
+}
+
+bool tc_tree_supported(int64_t n1, int L) {
+  const int N = round_up(L, 16);
+  const int64_t kch = (n1 + 127) / 128;
+  return n1 % 8 == 0 && N <= 64 && (2 + kch) * N <= 512;
+}
+
+void tc_tree_bf16(const __nv_bfloat16* X, int64_t n1, int64_t n2, int64_t T,
+                  const __nv_bfloat16* Om1, const __nv_bfloat16* Om2, const float* w, int L,
+                  float* Y1, float* Y2, float* C) {
+  KRP_REQUIRE(tc_tree_supported(n1, L), "fused tree needs n_1 %% 8 == 0, l <= 64 and TMEM room");
+  KRP_REQUIRE((reinterpret_cast<uintptr_t>(X) & 15) == 0, "X must be 16-byte aligned");
+  KRP_REQUIRE(T < (int64_t(1) << 31) && n2 < (int64_t(1) << 31), "tensor too large for TMA");
+  const int N = round_up(L, 16);
+  const int64_t n1p = round_up(n1, 128);
+  Ctx* ctx = current();
+  __nv_bfloat16* Fc = ctx->ws.take<__nv_bfloat16>((size_t)n1p * N);
+  pack_factor_kernel<<<(int)std::min<int64_t>((n1p * N + 255) / 256, 4096), 256, 0, stream()>>>(
+      Om1, nullptr, n1, n1p, L, N, N, Fc);
+  check_launch("pack_factor");
+  KRP_CUDA_CHECK(cudaMemsetAsync(Y1, 0, sizeof(float) * n1 * L, stream()));
+  KRP_CUDA_CHECK(cudaMemsetAsync(Y2, 0, sizeof(float) * n2 * L, stream()));
+  KRP_CUDA_CHECK(cudaMemsetAsync(C, 0, sizeof(float) * T * L, stream()));
+  const uint64_t xd[3] = {(uint64_t)n1, (uint64_t)n2, (uint64_t)T};
+  const uint64_t xs[2] = {(uint64_t)n1 * 2, (uint64_t)n1 * n2 * 2};
+  const uint32_t xbox[3] = {64, 128, 1};
+  const CUtensorMap mx = make_map(X, 3, xd, xs, xbox);
+  const uint64_t fd[2] = {(uint64_t)n1p, (uint64_t)N};
+  const uint64_t fs[1] = {(uint64_t)n1p * 2};
+  const uint32_t fbox[2] = {64, (uint32_t)N};
+  const CUtensorMap mf = make_map(Fc, 2, fd, fs, fbox);
+  TreeArgs P{};
+  P.w = w;
+  P.om2 = Om2;
+  P.Y1 = Y1;
+  P.Y2 = Y2;
+  P.C = C;
+  P.n1 = n1;
+  P.n2 = n2;
+  P.T = T;
+  P.L = L;
+  P.nb = static_cast<int>((n2 + 127) / 128);
+  P.kchunks = static_cast<int>((n1 + 127) / 128);
+  int64_t chunks = std::max<int64_t>(1, ctx->num_sms / P.nb);
+  chunks = std::min<int64_t>(chunks, T);
+  P.t_per_cta = (T + chunks - 1) / chunks;
+  chunks = (T + P.t_per_cta - 1) / P.t_per_cta;
+  const int grid = static_cast<int>(P.nb * chunks);
+  auto go = [&](auto kern, size_t stage) {
+    const size_t smem = 1024 + 3 * stage + 2 * (4 * (size_t)N * 128) + sizeof(Bars) + 64;
+    set_smem(kern, smem);
+    kern<<<grid, 320, smem, stream()>>>(mx, mf, P, ctx->d_status);
+  };
+  switch (N) {
+    case 16: go(tc_tree_kernel<16>, 2 * 16384 + 2 * 16 * 128); break;
+    case 32: go(tc_tree_kernel<32>, 2 * 16384 + 2 * 32 * 128); break;
+    case 48: go(tc_tree_kernel<48>, 2 * 16384 + 2 * 48 * 128); break;
+    case 64: go(tc_tree_kernel<64>, 2 * 16384 + 2 * 64 * 128); break;
+    default: fail(KRP_EUNSUPPORTED, "fused tree width %d", N);
+  }
+  check_launch("tc_tree_bf16");
 }
 
 size_t tc_residual_workspace_bytes(int64_t n1, int64_t S) {

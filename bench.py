@@ -210,7 +210,7 @@ def kernel_roofline(ctx, spec, x32, dev, stream, peaks, clk, args):
     mhz = (clk or {}).get("sm_max_mhz") or peaks.get("sm_max_mhz", 2070.0)
     peak = fp32_ffma_peak_tflops(mhz)
     ach = flops / (ms * 1e-3) / 1e12
-    return {"kernel": "mttkrp_first_kernel (FP32, mode-1 sketch)", "bound": "alu",
+    return {"kernel": "krp_slab_mttkrp_kernel (FP32, mode-1 KRP sketch)", "bound": "alu",
             "achieved": round(ach, 3), "peak": round(peak, 3), "unit": "TFLOP/s",
             "frac": round(ach / peak, 4), "traffic": None, "ms": round(ms, 4),
             "gbs": round(spec.numel * 4 / (ms * 1e-3) / 1e9, 1),

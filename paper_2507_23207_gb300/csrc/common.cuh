@@ -105,6 +105,9 @@ void gemm_tn_f32(const float* A, int64_t lda, int64_t S, int K, const float* F,
 // Y[i + n1*k] = sum_s A[i + n1*s] * prod_j V_j[digit_j(s), k]   (Y zeroed here)
 void mttkrp_first_f32(const float* A, int64_t n1, int64_t S, const Radix& rest,
                       int L, float* Y);
+// workspace mttkrp_first_f32 may take (S = product of the other sides,
+// n2max = largest side of the second mode)
+size_t mttkrp_first_f32_workspace_bytes(int64_t S, int64_t n2max);
 // Diagonal contraction of T (dims m_0..m_{D-1}, then k slowest, stride tk):
 // Y[i_n + m_n*k] = sum_{others} T[...,k] prod_{j != n} V_j[i_j, k]  (Y zeroed)
 void diag_contract_f32(const float* T, int D, const int64_t* m, int64_t tk,

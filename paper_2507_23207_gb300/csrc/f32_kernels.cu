@@ -507,7 +507,11 @@ __device__ __forceinline__ void ld4<__nv_bfloat16>(const __nv_bfloat16* p, float
   v[3] = __uint_as_float(q.y & 0xFFFF0000u);
 }
 
-template <class XT>
+// PRE: the CTA's 128 x 128 tile of X is copied into shared memory with
+// cp.async as the CTA starts, so that its HBM latency overlaps the
+// reconstruction product (needs n1 to be a multiple of 16 bytes' worth of
+// elements and a 16-byte aligned X).
+template <class XT, bool PRE>
 __global__ void __launch_bounds__(256)
     residual_kernel(const XT* __restrict__ X, int64_t n1, int64_t S,
                     const float* __restrict__ Q1, int l, const float* __restrict__ H,
@@ -516,9 +520,22 @@ __global__ void __launch_bounds__(256)
   __shared__ __align__(16) float Qs[KC][TM];
   __shared__ __align__(16) float Hs[KC][TM + 4];
   __shared__ double red[2][8];
+  extern __shared__ __align__(16) unsigned char rxs[];
+  XT(*Xs)[TM] = reinterpret_cast<XT(*)[TM]>(rxs);  // [s][i]
   const int tid = threadIdx.x, gi = tid & 15, gs = tid >> 4;
   const int64_t s0 = (int64_t)blockIdx.x * TM;
   const int64_t i0 = (int64_t)blockIdx.y * TM;
+  if (PRE) {
+    constexpr int E = 16 / sizeof(XT);  // elements per 16-byte copy
+    constexpr int CPR = TM / E;         // copies per s row of the tile
+    for (int q = tid; q < TM * CPR; q += 256) {
+      const int sl = q / CPR, c = q % CPR;
+      const int64_t s = s0 + sl, i = i0 + c * E;
+      const bool ok = (s < S) && (i < n1);  // n1 % E == 0: a copy is all in or all out
+      cp_async16(&Xs[sl][c * E], ok ? (const void*)(X + i + n1 * s) : (const void*)X, ok);
+    }
+    cp_commit();
+  }
   float xh[8][8];
 #pragma unroll
   for (int a = 0; a < 8; ++a)
@@ -551,17 +568,24 @@ __global__ void __launch_bounds__(256)
         for (int b = 0; b < 8; ++b) xh[a][b] = fmaf(qa[a], ha[b], xh[a][b]);
     }
   }
+  if (PRE) {
+    cp_wait<0>();
+    __syncthreads();
+  }
   float d2 = 0.f, x2 = 0.f;
   const bool vec = (n1 % 4) == 0;
 #pragma unroll
   for (int b = 0; b < 8; ++b) {
-    const int64_t s = s0 + (b < 4 ? 4 * gs + b : 64 + 4 * gs + (b - 4));
+    const int sl = b < 4 ? 4 * gs + b : 64 + 4 * gs + (b - 4);
+    const int64_t s = s0 + sl;
     if (s >= S) continue;
 #pragma unroll
     for (int half = 0; half < 2; ++half) {
       const int64_t ib = i0 + half * 64 + 4 * gi;
       float xv[4];
-      if (vec && ib + 3 < n1) {
+      if (PRE) {
+        ld4<XT>(&Xs[sl][half * 64 + 4 * gi], xv);
+      } else if (vec && ib + 3 < n1) {
         ld4<XT>(X + ib + n1 * s, xv);
       } else {
 #pragma unroll
@@ -598,7 +622,313 @@ __global__ void __launch_bounds__(256)
   }
 }
 
+
+// ----------------------------------------------------------------------------
+// Tiled TTM with 128-row tiles (the main FP32 contraction):
+//   out[s + ldo*k] (=|+=) sum_i A[i + lda*s] F[i + ldf*k]
+// Thread (g = tid >> 3, h = tid & 7) owns rows g + (BMS/8) j (j < 8) and the
+// strided columns h + 8 c (c < NP/8), so that both operand reads below are
+// conflict-free 16-byte shared-memory loads.  Chunks of GK contraction indices
+// are staged [s][i] and [k][i] (pitch GP floats) by an NS-stage cp.async ring
+// with one block barrier per chunk.  Each copy slot of a thread is fixed, so
+// its global address is computed once and advanced by GK per chunk.
+constexpr int GK = 16, GP = 20;
+template <int NP, int BMS, int NS, int MINB>
+__global__ void __launch_bounds__(BMS, MINB)
+    gemm_tn_tile_kernel(const float* __restrict__ A, int64_t lda, int64_t S, int K,
+                        const float* __restrict__ F, int64_t ldf, int L, float* __restrict__ out,
+                        int64_t ldo, int accumulate) {
+  constexpr int NT = BMS, RG = BMS / 8, CPT = NP / 8;
+  extern __shared__ __align__(16) float gts[];
+  float(*As)[BMS][GP] = reinterpret_cast<float(*)[BMS][GP]>(gts);
+  float(*Fs)[NP][GP] = reinterpret_cast<float(*)[NP][GP]>(gts + NS * BMS * GP);
+  const int tid = threadIdx.x, g = tid >> 3, h = tid & 7;
+  const int64_t s0 = (int64_t)blockIdx.x * BMS;
+  const int k0 = blockIdx.y * NP;
+  float acc[8][CPT];
+#pragma unroll
+  for (int j = 0; j < 8; ++j)
+#pragma unroll
+    for (int c = 0; c < CPT; ++c) acc[j][c] = 0.f;
+  const int nchunks = (K + GK - 1) / GK;
+  constexpr int AV = BMS * (GK / 4) / NT;
+  constexpr int FV = (NP * (GK / 4) + NT - 1) / NT;
+  const float* pa[AV];
+  bool oka[AV];
+#pragma unroll
+  for (int v = 0; v < AV; ++v) {
+    const int q = tid + NT * v;
+    const int64_t s = s0 + (q >> 2);
+    oka[v] = s < S;
+    pa[v] = A + 4 * (q & 3) + lda * (oka[v] ? s : 0);
+  }
+  const float* pf[FV];
+  bool okf[FV];
+#pragma unroll
+  for (int v = 0; v < FV; ++v) {
+    const int q = tid + NT * v;
+    okf[v] = (q < NP * (GK / 4)) && (k0 + (q >> 2) < L);
+    pf[v] = F + 4 * (q & 3) + ldf * (okf[v] ? (k0 + (q >> 2)) : 0);
+  }
+  auto issue = [&](int chunk) {
+    if (chunk < nchunks) {
+      const int stage = chunk % NS;
+      const int kc = chunk * GK;
+#pragma unroll
+      for (int v = 0; v < AV; ++v) {
+        const int q = tid + NT * v;
+        const bool ok = oka[v] && (kc + 4 * (q & 3) < K);
+        cp_async16(&As[stage][q >> 2][4 * (q & 3)], ok ? (const void*)(pa[v] + kc) : (const void*)A, ok);
+      }
+#pragma unroll
+      for (int v = 0; v < FV; ++v) {
+        const int q = tid + NT * v;
+        if (q < NP * (GK / 4)) {
+          const bool ok = okf[v] && (kc + 4 * (q & 3) < K);
+          cp_async16(&Fs[stage][q >> 2][4 * (q & 3)], ok ? (const void*)(pf[v] + kc) : (const void*)F, ok);
+        }
+      }
+    }
+    cp_commit();  // one group per call, possibly empty
+  };
+#pragma unroll
+  for (int p = 0; p < NS - 1; ++p) issue(p);
+  for (int c = 0; c < nchunks; ++c) {
+    cp_wait<NS - 2>();  // chunk c has landed
+    __syncthreads();    // ... for every thread; stage (c-1) % NS is free again
+    issue(c + NS - 1);
+    const int st = c % NS;
+#pragma unroll
+    for (int ii = 0; ii < GK; ii += 4) {
+      float4 f[CPT];
+#pragma unroll
+      for (int cc = 0; cc < CPT; ++cc) f[cc] = *reinterpret_cast<const float4*>(&Fs[st][h + 8 * cc][ii]);
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        const float4 a = *reinterpret_cast<const float4*>(&As[st][g + RG * j][ii]);
+#pragma unroll
+        for (int cc = 0; cc < CPT; ++cc) {
+          float v = acc[j][cc];
+          v = fmaf(a.x, f[cc].x, v);
+          v = fmaf(a.y, f[cc].y, v);
+          v = fmaf(a.z, f[cc].z, v);
+          v = fmaf(a.w, f[cc].w, v);
+          acc[j][cc] = v;
+        }
+      }
+    }
+  }
+#pragma unroll
+  for (int j = 0; j < 8; ++j) {
+    const int64_t s = s0 + g + RG * j;
+    if (s >= S) continue;
+#pragma unroll
+    for (int cc = 0; cc < CPT; ++cc) {
+      const int k = k0 + h + 8 * cc;
+      if (k < L) {
+        float* o = out + s + ldo * k;
+        *o = accumulate ? *o + acc[j][cc] : acc[j][cc];
+      }
+    }
+  }
+}
+
+// ----------------------------------------------------------------------------
+// Two-stage partial-Khatri-Rao MTTKRP of the first mode (Alg. 7 MTTKRP step
+// without forming the KRP):
+//   Y[i + n1*k] += sum_t wT[t*NP + k] sum_{i2 < n2} X[i + n1*(i2 + n2*t)] O2T[i2*NP + k]
+// Stage one is a GEMM of each slab X(:, :, t) (n1 x n2) with the mode-2
+// factor; stage two weights it by the Khatri-Rao row w_t of modes 3..d and
+// sums over t.  The weight is folded into the B operand as it is staged
+// (B_t = O2 diag(w_t), 4 columns per thread with 16-byte loads), so the
+// accumulators hold Y directly.  CTA: BM rows i x NP columns, BM threads;
+// thread (g = tid >> 3, h = tid & 7) owns rows 4g..4g+3, BM/2+4g..BM/2+4g+3 and
+// columns h*CPT..h*CPT+CPT-1.  A moves through an NS-stage cp.async ring, B is
+// loaded one chunk ahead into registers and stored after the multiply; one
+// block barrier per chunk.  Chunks are numbered c = t * cps + b (the b-th block
+// of BK rows of slab t); CTA (x, z) takes rows x and chunks [z per, (z+1) per).
+constexpr int MBM = 256, MBK = 16, MNS = 4;
+template <int NP>
+__global__ void __launch_bounds__(MBM, 2)
+    krp_slab_mttkrp_kernel(const float* __restrict__ X, int64_t n1, int64_t n2, int64_t T,
+                           const float* __restrict__ O2T, const float* __restrict__ wT,
+                           float* __restrict__ Y, int L, int64_t per) {
+  constexpr int BM = MBM, BK = MBK, NS = MNS, NT = MBM, CPT = NP / 8;
+  static_assert(CPT % 2 == 0, "columns per thread must be even");
+  extern __shared__ __align__(16) float kss[];
+  float(*As)[BK][BM] = reinterpret_cast<float(*)[BK][BM]>(kss);
+  float(*Bs)[BK][NP] = reinterpret_cast<float(*)[BK][NP]>(kss + NS * BK * BM);
+  const int tid = threadIdx.x, g = tid >> 3, h = tid & 7;
+  const int64_t i0 = (int64_t)blockIdx.x * BM;
+  const int64_t cps = (n2 + BK - 1) / BK;
+  const int64_t total = T * cps;
+  const int64_t cb = (int64_t)blockIdx.y * per;
+  const int64_t ce = min(total, cb + per);
+  if (cb >= ce) return;
+  float acc[8][CPT];
+#pragma unroll
+  for (int r = 0; r < 8; ++r)
+#pragma unroll
+    for (int c = 0; c < CPT; ++c) acc[r][c] = 0.f;
+  // slab / row-block positions of the next A chunk to issue and of the next
+  // B chunk to load, advanced one chunk at a time
+  int64_t tA = cb / cps, rA = (cb % cps) * BK, tB = tA, rB = rA;
+  auto advance = [&](int64_t& t, int64_t& r) {
+    r += BK;
+    if (r >= n2) {
+      r = 0;
+      ++t;
+    }
+  };
+  constexpr int RPV = NT / (BM / 4);  // chunk rows covered per copy round
+  const int arow = tid / (BM / 4), ac4 = tid % (BM / 4);
+  const bool a_in = (i0 + 4 * ac4) < n1;
+  auto issueA = [&](int64_t c) {
+    if (c < ce) {
+      const int st = (int)((c - cb) % NS);
+      const float* src = X + i0 + 4 * ac4 + n1 * (rA + arow + n2 * tA);
+#pragma unroll
+      for (int v = 0; v < BK / RPV; ++v) {
+        const int r = arow + RPV * v;
+        const bool ok = a_in && (rA + r < n2);
+        cp_async16(&As[st][r][4 * ac4], ok ? (const void*)(src + n1 * RPV * v) : (const void*)X, ok);
+      }
+      advance(tA, rA);
+    }
+    cp_commit();
+  };
+  constexpr int QPR = NP / 4;
+  static_assert(BK * QPR <= NT, "one quad of B per thread");
+  const int brow = tid / QPR, bq = tid % QPR;
+  const bool b_act = tid < BK * QPR;
+  float4 bv;
+  auto loadB = [&](int64_t c) {
+    bv = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (b_act && c < ce && rB + brow < n2) {
+      const float4 o = __ldg(reinterpret_cast<const float4*>(O2T + (rB + brow) * NP) + bq);
+      const float4 w = __ldg(reinterpret_cast<const float4*>(wT + tB * NP) + bq);
+      bv = make_float4(o.x * w.x, o.y * w.y, o.z * w.z, o.w * w.w);
+    }
+    if (c < ce) advance(tB, rB);
+  };
+  auto storeB = [&](int64_t c) {
+    if (b_act) *reinterpret_cast<float4*>(&Bs[(int)((c - cb) & 1)][brow][4 * bq]) = bv;
+  };
+#pragma unroll
+  for (int p = 0; p < NS - 1; ++p) issueA(cb + p);
+  loadB(cb);
+  storeB(cb);
+  for (int64_t c = cb; c < ce; ++c) {
+    cp_wait<NS - 2>();  // chunk c of A has landed
+    __syncthreads();    // ... for all threads; B[c] stored; stage (c-1) % NS free
+    issueA(c + NS - 1);
+    loadB(c + 1);       // global loads overlap the multiply below
+    const int st = (int)((c - cb) % NS), buf = (int)((c - cb) & 1);
+#pragma unroll
+    for (int k = 0; k < BK; ++k) {
+      const float4 a0 = *reinterpret_cast<const float4*>(&As[st][k][4 * g]);
+      const float4 a1 = *reinterpret_cast<const float4*>(&As[st][k][BM / 2 + 4 * g]);
+      const float av[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+      float bb[CPT];
+#pragma unroll
+      for (int m = 0; m < CPT / 2; ++m) {
+        const float2 b = *reinterpret_cast<const float2*>(&Bs[buf][k][h * CPT + 2 * m]);
+        bb[2 * m] = b.x;
+        bb[2 * m + 1] = b.y;
+      }
+#pragma unroll
+      for (int r = 0; r < 8; ++r)
+#pragma unroll
+        for (int c2 = 0; c2 < CPT; ++c2) acc[r][c2] = fmaf(av[r], bb[c2], acc[r][c2]);
+    }
+    storeB(c + 1);  // buffer (c+1) & 1 was last read in iteration c-1
+  }
+#pragma unroll
+  for (int r = 0; r < 8; ++r) {
+    const int64_t ib = i0 + (r < 4 ? 4 * g + r : BM / 2 + 4 * g + (r - 4));
+#pragma unroll
+    for (int c2 = 0; c2 < CPT; ++c2) {
+      const int k = h * CPT + c2;
+      if (k < L && ib < n1) atomicAdd(Y + ib + n1 * k, acc[r][c2]);
+    }
+  }
+}
+
+// OT[i*NP + k] = O[i + n*k] for k < L, 0 for L <= k < NP
+__global__ void pad_transpose_kernel(const float* __restrict__ O, int64_t n, int L, int NP,
+                                     float* __restrict__ OT) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n * NP;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = e / NP;
+    const int k = (int)(e % NP);
+    OT[e] = k < L ? O[i + n * k] : 0.f;
+  }
+}
+
+// wT[t*NP + k] = prod_j V_j[digit_j(t) + radix_j*k] (k < L; 0 for L <= k < NP),
+// digits of t in mixed radix with the first listed mode fastest; 1 if no modes
+__global__ void krp_weights_padded_kernel(const RadixDev R, int64_t T, int L, int NP,
+                                          float* __restrict__ wT) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < T * NP;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t t = e / NP;
+    const int k = (int)(e % NP);
+    float w = 0.f;
+    if (k < L) {
+      w = 1.f;
+      int64_t s = t;
+      for (int j = 0; j < R.n; ++j) {
+        const int64_t r = R.radix[j];
+        w *= R.V[j][s % r + r * k];
+        s /= r;
+      }
+    }
+    wT[e] = w;
+  }
+}
+
 }  // namespace
+
+namespace {
+template <int NP, int MINB>
+void gemm_tn_tile_launch(const float* A, int64_t lda, int64_t S, int K, const float* F, int64_t ldf,
+                         int L, float* out, int64_t ldo, bool accumulate) {
+  constexpr int BMS = 128, NS = 4;
+  dim3 grid((unsigned)((S + BMS - 1) / BMS), (unsigned)((L + NP - 1) / NP));
+  const size_t smem = sizeof(float) * NS * (BMS + NP) * GP;
+  set_dyn_smem(gemm_tn_tile_kernel<NP, BMS, NS, MINB>, smem);
+  gemm_tn_tile_kernel<NP, BMS, NS, MINB><<<grid, BMS, smem, stream()>>>(A, lda, S, K, F, ldf, L, out,
+                                                                        ldo, accumulate ? 1 : 0);
+  check_launch("gemm_tn_f32");
+}
+
+template <int NP>
+void krp_slab_mttkrp_launch(const float* X, int64_t n1, int64_t n2, int64_t T, const float* O2,
+                            const RadixDev& W, int L, float* Y) {
+  float* O2T = current()->ws.take<float>((size_t)n2 * NP);
+  float* wT = current()->ws.take<float>((size_t)T * NP);
+  pad_transpose_kernel<<<grid_for(n2 * NP, 256), 256, 0, stream()>>>(O2, n2, L, NP, O2T);
+  check_launch("pad_transpose");
+  krp_weights_padded_kernel<<<grid_for(T * NP, 256), 256, 0, stream()>>>(W, T, L, NP, wT);
+  check_launch("krp_weights_padded");
+  const int mt = (int)((n1 + MBM - 1) / MBM);
+  const int64_t cps = (n2 + MBK - 1) / MBK;
+  const int64_t total = T * cps;
+  const int64_t want = std::max<int64_t>(1, (int64_t)2 * current()->num_sms / mt);
+  const int64_t per = (total + want - 1) / want;
+  const int64_t splits = (total + per - 1) / per;
+  const size_t smem = sizeof(float) * (MNS * MBK * MBM + 2 * MBK * NP);
+  set_dyn_smem(krp_slab_mttkrp_kernel<NP>, smem);
+  krp_slab_mttkrp_kernel<NP><<<dim3(mt, (unsigned)splits), MBM, smem, stream()>>>(
+      X, n1, n2, T, O2T, wT, Y, L, per);
+  check_launch("krp_slab_mttkrp_f32");
+}
+}  // namespace
+
+size_t mttkrp_first_f32_workspace_bytes(int64_t S, int64_t n2max) {
+  // padded mode-2 factor (n2 x 64) and Khatri-Rao weights (S / n2 x 64, n2 >= 16)
+  return ws_bytes((size_t)n2max * 64, 4) + ws_bytes((size_t)(S / 16 + 1) * 64, 4);
+}
 
 void gemm_tn_f32(const float* A, int64_t lda, int64_t S, int K, const float* F, int64_t ldf,
                  int L, float* out, int64_t ldo, bool accumulate) {
@@ -607,6 +937,20 @@ void gemm_tn_f32(const float* A, int64_t lda, int64_t S, int K, const float* F, 
     if (!accumulate)
       for (int k = 0; k < L; ++k)
         KRP_CUDA_CHECK(cudaMemsetAsync(out + ldo * k, 0, sizeof(float) * S, stream()));
+    return;
+  }
+  const bool vec = (lda % 4 == 0) && (ldf % 4 == 0) && (K % 4 == 0) &&
+                   ((reinterpret_cast<uintptr_t>(A) & 15) == 0) &&
+                   ((reinterpret_cast<uintptr_t>(F) & 15) == 0);
+  if (vec) {
+    if (L <= 16)
+      gemm_tn_tile_launch<16, 4>(A, lda, S, K, F, ldf, L, out, ldo, accumulate);
+    else if (L <= 32)
+      gemm_tn_tile_launch<32, 4>(A, lda, S, K, F, ldf, L, out, ldo, accumulate);
+    else if (L <= 48)
+      gemm_tn_tile_launch<48, 4>(A, lda, S, K, F, ldf, L, out, ldo, accumulate);
+    else
+      gemm_tn_tile_launch<64, 2>(A, lda, S, K, F, ldf, L, out, ldo, accumulate);
     return;
   }
   if (L <= 16)
@@ -627,6 +971,28 @@ void mttkrp_first_f32(const float* A, int64_t n1, int64_t S, const Radix& rest, 
   for (int j = 0; j < rest.n; ++j) {
     R.radix[j] = rest.radix[j];
     R.V[j] = rest.V[j];
+  }
+  // two-stage slab kernel: needs 16-byte rows of X, slabs of >= 16 rows and
+  // at most 64 sketch columns (one column tile)
+  if (L <= 64 && rest.n >= 1 && rest.radix[0] >= MBK && n1 % 4 == 0 &&
+      (reinterpret_cast<uintptr_t>(A) & 15) == 0) {
+    const int64_t n2 = rest.radix[0];
+    RadixDev W{};
+    W.n = rest.n - 1;
+    for (int j = 1; j < rest.n; ++j) {
+      W.radix[j - 1] = rest.radix[j];
+      W.V[j - 1] = rest.V[j];
+    }
+    const int64_t T = S / n2;
+    if (L <= 16)
+      krp_slab_mttkrp_launch<16>(A, n1, n2, T, rest.V[0], W, L, Y);
+    else if (L <= 32)
+      krp_slab_mttkrp_launch<32>(A, n1, n2, T, rest.V[0], W, L, Y);
+    else if (L <= 48)
+      krp_slab_mttkrp_launch<48>(A, n1, n2, T, rest.V[0], W, L, Y);
+    else
+      krp_slab_mttkrp_launch<64>(A, n1, n2, T, rest.V[0], W, L, Y);
+    return;
   }
   if (L <= 16)
     mttkrp_first_launch<16>(A, n1, S, R, L, Y);
@@ -697,12 +1063,26 @@ void residual_f32(const void* X, krp_dtype xt, int64_t n1, int64_t S, const floa
                   const float* H, double* acc) {
   if (n1 <= 0 || S <= 0) return;
   dim3 grid((unsigned)((S + TM - 1) / TM), (unsigned)((n1 + TM - 1) / TM));
-  if (xt == KRP_F32)
-    residual_kernel<float><<<grid, 256, 0, stream()>>>(static_cast<const float*>(X), n1, S, Q1,
-                                                       l, H, acc);
-  else
-    residual_kernel<__nv_bfloat16><<<grid, 256, 0, stream()>>>(
-        static_cast<const __nv_bfloat16*>(X), n1, S, Q1, l, H, acc);
+  const bool aligned = (reinterpret_cast<uintptr_t>(X) & 15) == 0;
+  if (xt == KRP_F32) {
+    const float* Xf = static_cast<const float*>(X);
+    if (aligned && n1 % 4 == 0) {
+      const size_t smem = sizeof(float) * TM * TM;
+      set_dyn_smem(residual_kernel<float, true>, smem);
+      residual_kernel<float, true><<<grid, 256, smem, stream()>>>(Xf, n1, S, Q1, l, H, acc);
+    } else {
+      residual_kernel<float, false><<<grid, 256, 0, stream()>>>(Xf, n1, S, Q1, l, H, acc);
+    }
+  } else {
+    const __nv_bfloat16* Xb = static_cast<const __nv_bfloat16*>(X);
+    if (aligned && n1 % 8 == 0) {
+      const size_t smem = sizeof(__nv_bfloat16) * TM * TM;
+      set_dyn_smem(residual_kernel<__nv_bfloat16, true>, smem);
+      residual_kernel<__nv_bfloat16, true><<<grid, 256, smem, stream()>>>(Xb, n1, S, Q1, l, H, acc);
+    } else {
+      residual_kernel<__nv_bfloat16, false><<<grid, 256, 0, stream()>>>(Xb, n1, S, Q1, l, H, acc);
+    }
+  }
   check_launch("residual");
 }
 

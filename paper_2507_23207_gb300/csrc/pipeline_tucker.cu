@@ -189,6 +189,9 @@ size_t sketch_workspace_bytes(const SketchArgs& a, bool) {
   size_t b = ws_bytes((size_t)(a.N / n1) * a.ell, 4);               // B
   for (int j = 0; j < a.d; ++j) b += ws_bytes((size_t)a.dims[j] * a.ell, 4);  // f32 factors
   b += ws_bytes((size_t)(a.N / n1) * a.ell, 4);                     // KRP rows (upper bound)
+  int64_t dmax = 1;
+  for (int j = 0; j < a.d; ++j) dmax = std::max<int64_t>(dmax, a.dims[j]);
+  b += mttkrp_first_f32_workspace_bytes(a.N / std::max<int64_t>(1, a.dims[0]), dmax);
   if (a.xt == KRP_BF16) b += tc_workspace_bytes(n1, a.N / n1, a.ell);
   return b + (1 << 20);
 }
@@ -332,6 +335,11 @@ void tucker_pipeline(bool sequential, const void* X, krp_dtype xt, int d, const 
   const size_t big = (size_t)(N / dims[0]) * ellmax;
   size_t need = 5 * ws_bytes(big, 4);
   need += ws_bytes((size_t)maxS * ellmax, 4);  // KRP rows for the BF16 mode-1 sketch
+  {
+    int64_t dmax = 1;
+    for (int i = 0; i < d; ++i) dmax = std::max<int64_t>(dmax, dims[i]);
+    need += mttkrp_first_f32_workspace_bytes(maxS, dmax);  // FP32 slab-MTTKRP operands
+  }
   if (!x_dev) need += ws_bytes((size_t)N, xb);
   int64_t core_l = 1;
   for (int i = 0; i < d; ++i) {

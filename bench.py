@@ -183,8 +183,120 @@ def run_ours(args, rank, world, local_rank):
     kr = kernel_roofline(ctx, spec, x32, dev, stream, peaks, results["f32"]["clocks"], args)
     # e2e through the C ABI with host buffers (pinned), FP32 form
     e2e = e2e_run(ctx, spec, x32, args) if rank == 0 and not args.no_e2e else None
+    extra = {}
+    if not args.no_extra and not args.dims and args.config == "c2":
+        extra["sthosvd_1024cubed"] = sthosvd_run(ctx, spec, forms, dev, stream, args)
+        del forms, x, x32, xbf
+        torch.cuda.empty_cache()
+        extra["tucker_200pow4"] = c3_run(ctx, dev, stream, args)
+        extra["block_hankel_1024"] = c4_run(ctx, dev, stream, args)
     ctx.close()
-    return spec, results, kr, e2e, peaks, peak_src, (sk, co, rs, qr)
+    return spec, results, kr, e2e, peaks, peak_src, (sk, co, rs, qr), extra
+
+
+def _timed(stream, step, reps, warm):
+    import torch
+    for _ in range(warm):
+        res = step()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(reps):
+        res = step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / reps, res
+
+
+def _golden():
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "tests", "golden",
+                        "fullsize_c3_c4.json")
+    with open(path) as f:
+        return json.load(f)
+
+
+def sthosvd_run(ctx, spec, forms, dev, stream, args):
+    """RSTHOSVD-KRP (Alg. 8) + truncation + residual on the same 1024^3 tensors."""
+    import torch
+    import paper_2507_23207_gb300 as K
+    ranks = list(spec.ranks)
+    core = torch.empty(int(np.prod(ranks)), dtype=torch.float32, device=dev)
+    facs = [torch.empty(n * r, dtype=torch.float64, device=dev) for n, r in zip(spec.dims, ranks)]
+    flags = K.KRP_TRUNCATE | K.KRP_RESIDUAL
+    out = {}
+    for form, x in forms:
+        ms, res = _timed(stream, lambda: K.krp_tucker_sthosvd(
+            ctx, x, spec.dims, ranks, spec.oversample, spec.omega_seed, flags, core, facs),
+            reps=max(3, min(args.steps, 5)), warm=2)
+        out[form] = {"ms": round(ms, 3), "rel_error": res["rel_residual"],
+                     "gbs": round(3.0 * spec.numel * x.element_size() / (ms * 1e-3) / 1e9, 1)}
+    out["note"] = "steps: sketch+TTM of mode 1 on X, then the shrinking core; residual pass on X"
+    return out
+
+
+def c3_run(ctx, dev, stream, args):
+    """200^4 decaying-core workload, RHOSVD-KRP-MEMO l=30 -> rank 20, both forms,
+    next to the FP64 oracle's errors (stored by tests/golden/make_fullsize.py)."""
+    import torch
+    import paper_2507_23207_gb300 as K
+    from synth import config_spec
+    from synth.tucker import tucker_tensor_device
+    spec = config_spec("c3")
+    x64, _, _ = tucker_tensor_device(spec, device=dev)
+    xs = {"f32": x64.to(torch.float32), "bf16": x64.to(torch.bfloat16)}
+    del x64
+    torch.cuda.empty_cache()
+    ranks = list(spec.ranks)
+    core = torch.empty(int(np.prod(ranks)), dtype=torch.float32, device=dev)
+    facs = [torch.empty(n * r, dtype=torch.float64, device=dev) for n, r in zip(spec.dims, ranks)]
+    flags = K.KRP_MEMO | K.KRP_TRUNCATE | K.KRP_RESIDUAL
+    gold = _golden()["c3"]
+    out = {"workload": "200x200x200x200, core 40^4 N(0,1)*0.8^(i+j+k+l), no noise, "
+                       "RHOSVD-KRP-MEMO l=30 -> rank 20 + FP64 residual",
+           "hosvd_rel_error": gold["hosvd_rel_error"]}
+    for form, x in xs.items():
+        ms, res = _timed(stream, lambda: K.krp_tucker_rhosvd(
+            ctx, x, spec.dims, ranks, spec.oversample, spec.omega_seed, flags, core, facs),
+            reps=max(3, min(args.steps, 5)), warm=2)
+        out[form] = {"ms": round(ms, 3), "rel_error": res["rel_residual"],
+                     "oracle_rel_error": gold[f"rhosvd_memo_truncated_rel_error_{form}"],
+                     "gbs": round(3.0 * spec.numel * x.element_size() / (ms * 1e-3) / 1e9, 1)}
+    out["bf16_error_over_f32"] = round(out["bf16"]["rel_error"] / out["f32"]["rel_error"], 5)
+    out["bf16_speedup"] = round(out["f32"]["ms"] / out["bf16"]["ms"], 3)
+    del xs
+    torch.cuda.empty_cache()
+    return out
+
+
+def c4_run(ctx, dev, stream, args):
+    """1024 x 1024 block Hankel (state order 40), Alg. 6 with l_r=50, l_l=75,
+    r=40, both forms; singular values against the stored FP64 oracle's."""
+    import torch
+    import paper_2507_23207_gb300 as K
+    from synth import hankel_config_spec, markov_parameters
+    spec = hankel_config_spec("c4")
+    b = markov_parameters(spec)
+    flat = np.concatenate([np.asfortranarray(b[:, :, k]).ravel(order="F") for k in range(b.shape[2])])
+    t32 = torch.from_numpy(flat).to(torch.float32)
+    blocks = {"f32": t32.to(dev), "bf16": t32.to(torch.bfloat16).to(dev)}
+    ms_, ns_, r = spec.m * spec.s, spec.n * spec.s, spec.r
+    U = torch.empty((r, ms_), dtype=torch.float64, device=dev)
+    V = torch.empty((r, ns_), dtype=torch.float64, device=dev)
+    S = torch.empty(r, dtype=torch.float64, device=dev)
+    gold = _golden()["c4"]
+    out = {"workload": "1024x1024 block Hankel, 128x128 blocks of 8x8, state order 40, "
+                       "Alg. 6 l_r=50 l_l=75 r=40"}
+    for form, bl in blocks.items():
+        ms, _ = _timed(stream, lambda: K.krp_block_hankel_lowrank(
+            ctx, bl, spec.m, spec.n, spec.s, r, spec.ell_r, spec.ell_l, spec.omega_seed, U, S, V),
+            reps=10, warm=3)
+        sg = S.cpu().numpy()
+        so = np.asarray(gold[f"sigma_{form}"])
+        out[form] = {"ms": round(ms, 4),
+                     "sigma_max_abs_diff_over_sigma1": float(np.max(np.abs(sg - so)) / so[0]),
+                     "oracle_rel_error_vs_input": gold[f"rel_error_vs_input_{form}"]}
+    return out
 
 
 def kernel_roofline(ctx, spec, x32, dev, stream, peaks, clk, args):
@@ -292,6 +404,8 @@ def main():
     ap.add_argument("--no-bf16", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-extra", action="store_true",
+                    help="skip the STHOSVD, 200^4 and block-Hankel measurements")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -321,7 +435,8 @@ def main():
     if world > 1:
         import torch
         torch.distributed.init_process_group("nccl")
-    spec, results, kr, e2e, peaks, peak_src, (sk, co, rs, qr) = run_ours(args, rank, world, local_rank)
+    spec, results, kr, e2e, peaks, peak_src, (sk, co, rs, qr), extra = run_ours(args, rank, world,
+                                                                                local_rank)
     if rank != 0:
         return
     f32 = results["f32"]
@@ -369,6 +484,7 @@ def main():
                        "d2h_bytes_per_step": e2e["d2h"]}
     if cpu:
         line["cpu_baseline"] = cpu
+    line.update(extra)
     print(json.dumps(line))
 
 

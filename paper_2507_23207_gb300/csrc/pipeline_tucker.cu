@@ -419,7 +419,12 @@ void tucker_pipeline(bool sequential, const void* X, krp_dtype xt, int d, const 
         SketchArgs a{};
         a.X = Xd; a.xt = xt; a.d = d; a.omt = ft; a.ell = ell[i]; a.N = N;
         for (int j = 0; j < d; ++j) { a.dims[j] = dims[j]; a.omega[j] = fac[i][j]; }
+        // the sketch's temporaries are dead once Y_i is written: rewind the
+        // arena so the d sketches reuse the same space (stream order keeps
+        // the next sketch's writes after this one's reads)
+        const size_t mark = ws.off;
         sketch_one_mode(a, i, Y[i]);
+        ws.off = mark;
       }
     }
     tm.mark();  // 2

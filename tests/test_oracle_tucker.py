@@ -18,6 +18,7 @@ import pytest
 
 from oracle import tucker as TK
 from oracle import tensor as T
+from oracle import philox
 from synth import TuckerSpec, tucker_tensor
 
 
@@ -153,3 +154,21 @@ def test_omega_rounding_modes():
     f = TK.memo_factors(0, (5, 6), 3, omega_round="bf16")
     for a in f:
         assert np.array_equal(a, a.astype(np.float32).astype(np.float64))
+
+
+def test_bf16_quantisation_degrades_decaying_core():
+    """BF16 rounding of X (relative error q ~ 1.7e-3) acts as noise that the
+    sketch amplifies: on a decaying core (0.8^(i+j+k)) truncated to rank 20
+    from l = 30 the oracle's error grows by well over 5%, so a 1.05x accuracy
+    criterion cannot hold for BF16 storage of such a tensor (the reading
+    recorded for the 200^4 workload)."""
+    spec = TuckerSpec("q", (120, 120, 120), (40, 40, 40), 0.0, 0.8, 1003, (20, 20, 20),
+                      (30, 30, 30))
+    x, _, _ = tucker_tensor(spec)
+    xb = philox.round_to_bf16(x)
+    errs = []
+    for xx in (x, xb):
+        o = TK.rhosvd_krp(xx, [30] * 3, 0, memo=True, omega_round="f32")
+        g2, q2 = TK.truncate_core(o["G"], o["Q"], [20] * 3)
+        errs.append(TK.rel_error(x, g2, q2))
+    assert errs[1] > 1.05 * errs[0]

@@ -267,6 +267,42 @@ krp_status krp_block_hankel_sketch(krp_ctx ctx, const void* blocks,
                                    const void* psi2, int ell_l, float* Y,
                                    float* Z);
 
+/* ---- a11: batches of small uneven 3-way tensors -------------------------- */
+
+/* One tensor of a batch (all device pointers). */
+typedef struct krp_tucker_item {
+  const void* X;          /* in: n1 x n2 x n3, mode-1 fastest, the batch dtype */
+  int64_t dims[3];        /* in: 1 <= n_i <= 256 */
+  int ranks[3];           /* in: r_i; l_i = r_i + oversample <= min(32, n_i) */
+  uint64_t seed;          /* in: Philox key of this tensor's factor set */
+  float* core;            /* in: output, prod of output ranks, mode-1 fastest */
+  double* factors[3];     /* in: outputs, n_i x rank_i column-major FP64 */
+  double rel_residual;    /* out: with KRP_RESIDUAL, else -1 */
+} krp_tucker_item;
+
+/* RHOSVD-KRP-MEMO (Alg. 7 with one factor set per tensor, draw 0 of key
+ * `seed`, i.e. exactly what krp_tucker_rhosvd with KRP_MEMO computes for that
+ * tensor alone) of `count` 3-way tensors of different shapes and ranks, each
+ * phase one launch over the whole batch (persistent kernels over work tiles of
+ * mode-3 slabs; QR and eigenproblems as job arrays).  Flags: KRP_TRUNCATE,
+ * KRP_RESIDUAL (KRP_MEMO implied).  The first call with a given set of
+ * descriptors (pointers, shapes, ranks, seeds, flags) allocates the batch's
+ * scratch, picks the work-tile size by timing, and records the phase
+ * sequence as a CUDA graph; later calls with identical descriptors replay
+ * the graph.  The call synchronises the stream and fills rel_residual.  The
+ * plan and its scratch stay with the context until a call with other
+ * descriptors or krp_destroy.  The paper describes single tensors only; the
+ * batched form has no counterpart there.  Errors: KRP_EINVAL (shapes, ranks,
+ * host pointers, dtype), KRP_ENOMEM, KRP_ECUDA, KRP_ENUMERIC. */
+krp_status krp_tucker_rhosvd_batched(krp_ctx ctx, krp_dtype xt, int count,
+                                     krp_tucker_item* items, int oversample,
+                                     unsigned flags);
+
+/* Work-tile choice of the context's current batch plan (slabs per tile,
+ * number of tiles, persistent grid size); KRP_EINVAL if there is none. */
+krp_status krp_tucker_batch_plan_info(krp_ctx ctx, int* slabs_per_tile,
+                                      int* tiles, int* grid);
+
 #ifdef __cplusplus
 }
 #endif

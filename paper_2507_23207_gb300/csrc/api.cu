@@ -157,6 +157,8 @@ krp_status krp_destroy(krp_ctx ctx) {
   if (!ctx) return KRP_EINVAL;
   krp_status st = guarded(ctx, [&] {
     KRP_CUDA_CHECK(cudaStreamSynchronize(ctx->c.stream));
+    if (ctx->c.batch_plan) ctx->c.batch_plan_free(ctx->c.batch_plan);
+    ctx->c.batch_plan = nullptr;
     if (ctx->c.ws.base) KRP_CUDA_CHECK(cudaFree(ctx->c.ws.base));
     if (ctx->c.d_status) KRP_CUDA_CHECK(cudaFree(ctx->c.d_status));
     ctx->c.ws.base = nullptr;
@@ -290,6 +292,17 @@ krp_status krp_tucker_sthosvd(krp_ctx ctx, const void* X, krp_dtype xt, int d,
                               const int64_t* dims, const int* ranks, int oversample,
                               uint64_t seed, unsigned flags, krp_tucker_out* out) {
   return guarded(ctx, [&] { tucker_pipeline(true, X, xt, d, dims, ranks, oversample, seed, flags, out); });
+}
+
+krp_status krp_tucker_rhosvd_batched(krp_ctx ctx, krp_dtype xt, int count, krp_tucker_item* items,
+                                     int oversample, unsigned flags) {
+  return guarded(ctx, [&] { tucker_batched(xt, count, items, oversample, flags); });
+}
+
+krp_status krp_tucker_batch_plan_info(krp_ctx ctx, int* slabs_per_tile, int* tiles, int* grid) {
+  return guarded(ctx, [&] {
+    KRP_REQUIRE(tucker_batched_plan_info(slabs_per_tile, tiles, grid), "no batch plan");
+  });
 }
 
 krp_status krp_block_hankel_lowrank(krp_ctx ctx, const void* blocks, krp_dtype bt, int m, int n,

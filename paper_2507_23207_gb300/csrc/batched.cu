@@ -1,0 +1,965 @@
+// a11: many small, uneven 3-way tensors in one launch per phase.
+//
+// RHOSVD-KRP-MEMO (Alg. 7 with one factor set, Sec. 5.1) of every tensor of a
+// batch.  Each phase is one kernel launch over the whole batch:
+//   factors     one Philox launch over all (tensor, mode) factors
+//   sketch      persistent kernel over (tensor, slab range) work tiles: for a
+//               mode-3 slab X_t (n1 x n2) it forms A_t = X_t Om2 and
+//               B_t = X_t^T Om1 and accumulates Y1 += A_t diag(Om3[t,:]),
+//               Y2 += B_t diag(Om3[t,:]), Y3[t,:] = colsum(Om1 * A_t): all
+//               three mode sketches from one pass over X (the dimension tree
+//               of Sec. 5.1, 4 N l flops)
+//   QR          one CTA per (tensor, mode), FP64 Householder
+//   core        persistent kernel over the same tiles: C_t = Q1^T X_t Q2,
+//               then G(:,:,c) = sum_t C_t Q3[t,c] in a per-tensor kernel
+//   truncation  FP64 Gram matrices of the core unfoldings, the eigensolver
+//               on all 3 x count of them, then G x {U_i^T}, Q_i U_i
+//   residual    persistent kernel: ||X_t - Q1 (sum_c G(:,:,c) Q3[t,c]) Q2^T||^2
+//               with FP64 sums per tensor
+// The tiles are sorted by work (largest first) and handed out by an atomic
+// counter.  The slabs-per-tile granularity is picked once per batch by timing
+// the sketch phase for a few candidates.  The whole sequence is captured in a
+// CUDA graph when the batch is first seen; a repeated call with the same
+// descriptors replays the graph.  Products run on CUDA cores in FP32 with
+// FP32 accumulation (the slabs are too small and too unevenly shaped for
+// 128-row tensor-core tiles); X may be FP32 or BF16.
+#include <algorithm>
+#include <cstring>
+#include <memory>
+#include <vector>
+
+#include "common.cuh"
+#include "pipeline.h"
+
+namespace krp {
+namespace {
+
+constexpr int kBT = 256;              // threads of the slab kernels
+constexpr int kMaxSide = 256;         // n_i
+constexpr int kMaxEll = 32;           // l_i
+constexpr int kJB = 32;               // slab columns per staged chunk
+constexpr int kRPT = kMaxSide / 32;   // rows per thread in the row mappings
+
+struct TbItem {
+  const void* X;
+  int n[3];
+  int l[3];
+  int lm;            // memo factor width: max l_i
+  int r[3];          // output sizes (r_i with truncation, l_i without)
+  float* om[3];      // n_i x lm
+  float* Y[3];       // n_i x lm
+  double* Q[3];      // n_i x l_i
+  float* C;          // n3 slab cores, l1 x l2 each
+  float* G;          // l1 l2 l3
+  double* T1;        // r1 l2 l3 (truncation scratch)
+  double* T2;        // r1 r2 l3
+  double* S[3];      // l_i x l_i
+  double* U[3];      // l_i x r_i
+  float* core_out;   // r1 r2 r3
+  double* fac_out[3];
+  double* acc;       // ||X - X_hat||^2, ||X||^2
+};
+
+struct TbTile {
+  int item, t0, t1, pad;
+};
+
+template <class XT>
+__device__ __forceinline__ float ldx(const XT* p, int64_t i);
+template <>
+__device__ __forceinline__ float ldx<float>(const float* p, int64_t i) { return p[i]; }
+template <>
+__device__ __forceinline__ float ldx<__nv_bfloat16>(const __nv_bfloat16* p, int64_t i) {
+  return __bfloat162float(p[i]);
+}
+
+// Stage columns j0 .. j0+kJB-1 of slab t (rows 0..fill-1, zero outside the
+// slab) into Xs[jl][i], pitch `pitch`; warp w copies rows jl = w, w+8, ...
+template <class XT>
+__device__ void stage_chunk(const XT* X, int n1, int n2, int t, int j0, int fill, float* Xs,
+                            int pitch) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int jl = warp; jl < kJB; jl += kBT / 32) {
+    const int j = j0 + jl;
+    const bool jok = j < n2;
+    const int64_t base = (int64_t)n1 * (j + (int64_t)n2 * t);
+    for (int i = lane; i < fill; i += 32) Xs[jl * pitch + i] = (jok && i < n1) ? ldx(X, base + i) : 0.f;
+  }
+}
+
+__device__ int next_tile(int* counter, int* s_tile) {
+  __syncthreads();  // everyone is done with the previous tile's shared memory
+  if (threadIdx.x == 0) *s_tile = atomicAdd(counter, 1);
+  __syncthreads();
+  return *s_tile;
+}
+
+// ---------------------------------------------------------------- sketch ----
+// Shared memory (floats): Xs[kJB][pitch], O1s[n1max4][Lp], O2s[n2max][Lp],
+// Y2p[n2max][Lp], o3s[Lp], y3s[Lp].
+template <class XT>
+__global__ void __launch_bounds__(kBT, 2)
+    batch_sketch_kernel(const TbItem* __restrict__ items, const TbTile* __restrict__ tiles,
+                        int ntiles, int* counter, int pitch, int Lp, int n1max4, int n2max) {
+  extern __shared__ __align__(16) float bsm[];
+  float* Xs = bsm;
+  float* O1s = Xs + kJB * pitch;
+  float* O2s = O1s + n1max4 * Lp;
+  float* Y2p = O2s + n2max * Lp;
+  float* o3s = Y2p + n2max * Lp;
+  float* y3s = o3s + Lp;
+  __shared__ int s_tile;
+  const int tid = threadIdx.x, ig = tid >> 3, kg = tid & 7;
+  for (;;) {
+    const int ti = next_tile(counter, &s_tile);
+    if (ti >= ntiles) break;
+    const TbTile tile = tiles[ti];
+    const TbItem& it = items[tile.item];
+    const int n1 = it.n[0], n2 = it.n[1], n3 = it.n[2], lm = it.lm;
+    const int n1p4 = (n1 + 3) & ~3;
+    const int rpt = (n1 + 31) >> 5;
+    const XT* X = static_cast<const XT*>(it.X);
+    for (int e = tid; e < n1p4 * Lp; e += kBT) {
+      const int i = e / Lp, k = e % Lp;
+      O1s[e] = (i < n1 && k < lm) ? it.om[0][i + (int64_t)n1 * k] : 0.f;
+    }
+    for (int e = tid; e < n2 * Lp; e += kBT) {
+      const int j = e / Lp, k = e % Lp;
+      O2s[e] = k < lm ? it.om[1][j + (int64_t)n2 * k] : 0.f;
+      Y2p[e] = 0.f;
+    }
+    float y1[kRPT][4];
+#pragma unroll
+    for (int u = 0; u < kRPT; ++u)
+#pragma unroll
+      for (int c = 0; c < 4; ++c) y1[u][c] = 0.f;
+    const bool kact = 4 * kg < Lp;
+    for (int t = tile.t0; t < tile.t1; ++t) {
+      if (tid < Lp) {
+        o3s[tid] = tid < lm ? it.om[2][t + (int64_t)n3 * tid] : 0.f;
+        y3s[tid] = 0.f;
+      }
+      float a[kRPT][4];
+#pragma unroll
+      for (int u = 0; u < kRPT; ++u)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) a[u][c] = 0.f;
+      for (int j0 = 0; j0 < n2; j0 += kJB) {
+        __syncthreads();  // previous chunk consumed
+        stage_chunk<XT>(X, n1, n2, t, j0, 32 * rpt, Xs, pitch);
+        __syncthreads();
+        const int jn = min(kJB, n2 - j0);
+        if (kact) {
+          // A_t rows ig + 32u, columns 4kg..4kg+3
+          for (int jl = 0; jl < jn; ++jl) {
+            const float4 w = *reinterpret_cast<const float4*>(&O2s[(j0 + jl) * Lp + 4 * kg]);
+#pragma unroll
+            for (int u = 0; u < kRPT; ++u) {
+              if (u < rpt) {
+                const float x = Xs[jl * pitch + ig + 32 * u];
+                a[u][0] = fmaf(x, w.x, a[u][0]);
+                a[u][1] = fmaf(x, w.y, a[u][1]);
+                a[u][2] = fmaf(x, w.z, a[u][2]);
+                a[u][3] = fmaf(x, w.w, a[u][3]);
+              }
+            }
+          }
+          // B_t row j0 + ig (ig doubles as the chunk column here)
+          if (ig < jn) {
+            float b0 = 0.f, b1 = 0.f, b2 = 0.f, b3 = 0.f;
+            for (int i = 0; i < n1p4; i += 4) {
+              const float4 x = *reinterpret_cast<const float4*>(&Xs[ig * pitch + i]);
+              const float xv[4] = {x.x, x.y, x.z, x.w};
+#pragma unroll
+              for (int q = 0; q < 4; ++q) {
+                const float4 w = *reinterpret_cast<const float4*>(&O1s[(i + q) * Lp + 4 * kg]);
+                b0 = fmaf(xv[q], w.x, b0);
+                b1 = fmaf(xv[q], w.y, b1);
+                b2 = fmaf(xv[q], w.z, b2);
+                b3 = fmaf(xv[q], w.w, b3);
+              }
+            }
+            float* yp = &Y2p[(j0 + ig) * Lp + 4 * kg];
+            yp[0] = fmaf(b0, o3s[4 * kg + 0], yp[0]);
+            yp[1] = fmaf(b1, o3s[4 * kg + 1], yp[1]);
+            yp[2] = fmaf(b2, o3s[4 * kg + 2], yp[2]);
+            yp[3] = fmaf(b3, o3s[4 * kg + 3], yp[3]);
+          }
+        }
+      }
+      // slab t done: Y1 partial and Y3[t, :]
+      float p[4] = {0.f, 0.f, 0.f, 0.f};
+      if (kact) {
+#pragma unroll
+        for (int u = 0; u < kRPT; ++u) {
+          if (u < rpt) {
+            const int i = ig + 32 * u;
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+              y1[u][c] = fmaf(a[u][c], o3s[4 * kg + c], y1[u][c]);
+              if (i < n1) p[c] = fmaf(O1s[i * Lp + 4 * kg + c], a[u][c], p[c]);
+            }
+          }
+        }
+      }
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        p[c] += __shfl_xor_sync(0xffffffffu, p[c], 8);
+        p[c] += __shfl_xor_sync(0xffffffffu, p[c], 16);
+      }
+      if ((tid & 31) < 8 && kact) {
+#pragma unroll
+        for (int c = 0; c < 4; ++c) atomicAdd(&y3s[4 * kg + c], p[c]);
+      }
+      __syncthreads();
+      if (tid < lm) it.Y[2][t + (int64_t)n3 * tid] = y3s[tid];
+    }
+    if (kact) {
+#pragma unroll
+      for (int u = 0; u < kRPT; ++u) {
+        const int i = ig + 32 * u;
+        if (u < rpt && i < n1) {
+#pragma unroll
+          for (int c = 0; c < 4; ++c) {
+            const int k = 4 * kg + c;
+            if (k < lm) atomicAdd(&it.Y[0][i + (int64_t)n1 * k], y1[u][c]);
+          }
+        }
+      }
+    }
+    __syncthreads();
+    for (int e = tid; e < n2 * Lp; e += kBT) {
+      const int j = e / Lp, k = e % Lp;
+      if (k < lm) atomicAdd(&it.Y[1][j + (int64_t)n2 * k], Y2p[e]);
+    }
+  }
+}
+
+// ------------------------------------------------------------------ core ----
+// C_t = Q1^T X_t Q2 (l1 x l2) for every slab of the tile.  Shared memory
+// (floats): Xs[kJB][pitch], Q1s[n1max4][Lp], Q2s[n2max][Lp], Ts[kJB][Lp].
+template <class XT>
+__global__ void __launch_bounds__(kBT, 2)
+    batch_core_kernel(const TbItem* __restrict__ items, const TbTile* __restrict__ tiles,
+                      int ntiles, int* counter, int pitch, int Lp, int n1max4, int n2max) {
+  extern __shared__ __align__(16) float bsm[];
+  float* Xs = bsm;
+  float* Q1s = Xs + kJB * pitch;
+  float* Q2s = Q1s + n1max4 * Lp;
+  float* Ts = Q2s + n2max * Lp;
+  __shared__ int s_tile;
+  const int tid = threadIdx.x, hi = tid >> 3, kg = tid & 7;
+  for (;;) {
+    const int ti = next_tile(counter, &s_tile);
+    if (ti >= ntiles) break;
+    const TbTile tile = tiles[ti];
+    const TbItem& it = items[tile.item];
+    const int n1 = it.n[0], n2 = it.n[1], l1 = it.l[0], l2 = it.l[1];
+    const int n1p4 = (n1 + 3) & ~3;
+    const int rpt = (n1 + 31) >> 5;
+    const XT* X = static_cast<const XT*>(it.X);
+    for (int e = tid; e < n1p4 * Lp; e += kBT) {
+      const int i = e / Lp, a = e % Lp;
+      Q1s[e] = (i < n1 && a < l1) ? (float)it.Q[0][i + (int64_t)n1 * a] : 0.f;
+    }
+    for (int e = tid; e < n2 * Lp; e += kBT) {
+      const int j = e / Lp, b = e % Lp;
+      Q2s[e] = b < l2 ? (float)it.Q[1][j + (int64_t)n2 * b] : 0.f;
+    }
+    const bool kact = 4 * kg < Lp;
+    for (int t = tile.t0; t < tile.t1; ++t) {
+      // thread (a = hi, b = 4kg..4kg+3) of C_t
+      float cacc[4] = {0.f, 0.f, 0.f, 0.f};
+      for (int j0 = 0; j0 < n2; j0 += kJB) {
+        __syncthreads();
+        stage_chunk<XT>(X, n1, n2, t, j0, 32 * rpt, Xs, pitch);
+        __syncthreads();
+        const int jn = min(kJB, n2 - j0);
+        // Ts[jl][a] = sum_i Xs[jl][i] Q1s[i][a]: thread (jl = hi, a = 4kg..)
+        if (kact) {
+          float t0 = 0.f, t1 = 0.f, t2 = 0.f, t3 = 0.f;
+          if (hi < jn) {
+            for (int i = 0; i < n1p4; i += 4) {
+              const float4 x = *reinterpret_cast<const float4*>(&Xs[hi * pitch + i]);
+              const float xv[4] = {x.x, x.y, x.z, x.w};
+#pragma unroll
+              for (int q = 0; q < 4; ++q) {
+                const float4 w = *reinterpret_cast<const float4*>(&Q1s[(i + q) * Lp + 4 * kg]);
+                t0 = fmaf(xv[q], w.x, t0);
+                t1 = fmaf(xv[q], w.y, t1);
+                t2 = fmaf(xv[q], w.z, t2);
+                t3 = fmaf(xv[q], w.w, t3);
+              }
+            }
+          }
+          *reinterpret_cast<float4*>(&Ts[hi * Lp + 4 * kg]) = make_float4(t0, t1, t2, t3);
+        }
+        __syncthreads();
+        if (kact && hi < Lp) {
+          for (int jl = 0; jl < jn; ++jl) {
+            const float ta = Ts[jl * Lp + hi];
+            const float4 w = *reinterpret_cast<const float4*>(&Q2s[(j0 + jl) * Lp + 4 * kg]);
+            cacc[0] = fmaf(ta, w.x, cacc[0]);
+            cacc[1] = fmaf(ta, w.y, cacc[1]);
+            cacc[2] = fmaf(ta, w.z, cacc[2]);
+            cacc[3] = fmaf(ta, w.w, cacc[3]);
+          }
+        }
+      }
+      if (kact && hi < l1) {
+        float* Ct = it.C + (int64_t)t * l1 * l2;
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+          const int b = 4 * kg + c;
+          if (b < l2) Ct[hi + l1 * b] = cacc[c];
+        }
+      }
+    }
+  }
+}
+
+// G[ab + l1 l2 c] = sum_t C_t[ab] Q3[t, c]; one CTA per tensor
+__global__ void batch_core_finish_kernel(const TbItem* __restrict__ items) {
+  const TbItem& it = items[blockIdx.x];
+  const int l12 = it.l[0] * it.l[1], l3 = it.l[2], n3 = it.n[2];
+  for (int e = threadIdx.x; e < l12 * l3; e += blockDim.x) {
+    const int ab = e % l12, c = e / l12;
+    const double* q3 = it.Q[2] + (int64_t)n3 * c;
+    float acc = 0.f;
+    for (int t = 0; t < n3; ++t) acc = fmaf(it.C[(int64_t)t * l12 + ab], (float)q3[t], acc);
+    it.G[e] = acc;
+  }
+}
+
+// ------------------------------------------------------------ truncation ----
+// Gram of unfolding `mode` of the FP32 core, FP64 accumulation; grid (count, 3)
+__global__ void batch_gram_kernel(const TbItem* __restrict__ items) {
+  extern __shared__ float gsh[];
+  const TbItem& it = items[blockIdx.x];
+  const int mode = blockIdx.y;
+  const int l0 = it.l[0], l1 = it.l[1], l2 = it.l[2];
+  const int L = l0 * l1 * l2;
+  for (int e = threadIdx.x; e < L; e += blockDim.x) gsh[e] = it.G[e];
+  __syncthreads();
+  const int lmode = it.l[mode];
+  const int ncol = L / lmode;
+  // element (x0, x1, x2) at x0 + l0 x1 + l0 l1 x2; the unfolding's column
+  // index runs over the other two in order
+  const int stride = mode == 0 ? 1 : (mode == 1 ? l0 : l0 * l1);
+  const int la = mode == 0 ? l1 : l0;             // first other side
+  const int sa = mode == 0 ? l0 : 1;              // its stride
+  const int sb = mode == 2 ? l0 : l0 * l1;        // second other side's stride
+  for (int pq = threadIdx.x; pq < lmode * lmode; pq += blockDim.x) {
+    const int p = pq % lmode, q = pq / lmode;
+    if (p > q) continue;
+    double s = 0.0;
+    for (int col = 0; col < ncol; ++col) {
+      const int off = (col % la) * sa + (col / la) * sb;
+      s = fma((double)gsh[off + p * stride], (double)gsh[off + q * stride], s);
+    }
+    it.S[mode][p + lmode * q] = s;
+    it.S[mode][q + lmode * p] = s;
+  }
+}
+
+// Truncated core and factors (one CTA per tensor): G' = G x_1 U1^T x_2 U2^T
+// x_3 U3^T in FP64 through two global scratch tensors, Q_i U_i; without
+// truncation the core and factors are copied out.
+__global__ void batch_trunc_apply_kernel(const TbItem* __restrict__ items, int trunc) {
+  const TbItem& it = items[blockIdx.x];
+  const int l0 = it.l[0], l1 = it.l[1], l2 = it.l[2];
+  const int r0 = it.r[0], r1 = it.r[1], r2 = it.r[2];
+  const int tid = threadIdx.x, nt = blockDim.x;
+  if (!trunc) {
+    for (int e = tid; e < l0 * l1 * l2; e += nt) it.core_out[e] = it.G[e];
+    for (int m = 0; m < 3; ++m)
+      for (int e = tid; e < it.n[m] * it.l[m]; e += nt) it.fac_out[m][e] = it.Q[m][e];
+    return;
+  }
+  // T1[a', x1, x2] = sum_a U0[a, a'] G[a, x1, x2]
+  for (int e = tid; e < r0 * l1 * l2; e += nt) {
+    const int ap = e % r0, rest = e / r0;
+    double s = 0.0;
+    for (int a = 0; a < l0; ++a) s = fma(it.U[0][a + l0 * ap], (double)it.G[a + l0 * rest], s);
+    it.T1[e] = s;
+  }
+  __syncthreads();
+  // T2[a', b', x2] = sum_b U1[b, b'] T1[a', b, x2]
+  for (int e = tid; e < r0 * r1 * l2; e += nt) {
+    const int ap = e % r0, bp = (e / r0) % r1, c = e / (r0 * r1);
+    double s = 0.0;
+    for (int b = 0; b < l1; ++b) s = fma(it.U[1][b + l1 * bp], it.T1[ap + r0 * (b + l1 * c)], s);
+    it.T2[e] = s;
+  }
+  __syncthreads();
+  for (int e = tid; e < r0 * r1 * r2; e += nt) {
+    const int ab = e % (r0 * r1), cp = e / (r0 * r1);
+    double s = 0.0;
+    for (int c = 0; c < l2; ++c) s = fma(it.U[2][c + l2 * cp], it.T2[ab + r0 * r1 * c], s);
+    it.core_out[e] = (float)s;
+  }
+  for (int m = 0; m < 3; ++m) {
+    const int n = it.n[m], l = it.l[m], r = it.r[m];
+    for (int e = tid; e < n * r; e += nt) {
+      const int i = e % n, k = e / n;
+      double s = 0.0;
+      for (int a = 0; a < l; ++a) s = fma(it.Q[m][i + (int64_t)n * a], it.U[m][a + l * k], s);
+      it.fac_out[m][e] = s;
+    }
+  }
+}
+
+// -------------------------------------------------------------- residual ----
+// ||X_t - F1 M_t F2^T||^2 with M_t = sum_c Gt(:,:,c) F3[t,c].  Shared memory
+// (floats): Xs[kJB][pitch], F1s[n1max][Rp], F2s[Rp][n2max], Ms[Rp][Rp],
+// Ps[Rp][n1max].
+template <class XT>
+__global__ void __launch_bounds__(kBT, 2)
+    batch_resid_kernel(const TbItem* __restrict__ items, const TbTile* __restrict__ tiles,
+                       int ntiles, int* counter, int pitch, int Rp, int n1max, int n2max) {
+  extern __shared__ __align__(16) float bsm[];
+  float* Xs = bsm;
+  float* F1s = Xs + kJB * pitch;
+  float* F2s = F1s + n1max * Rp;
+  float* Ms = F2s + Rp * n2max;
+  float* Ps = Ms + Rp * Rp;
+  __shared__ int s_tile;
+  __shared__ double red[2][kBT / 32];
+  const int tid = threadIdx.x, ig = tid >> 3, jq = tid & 7;
+  for (;;) {
+    const int ti = next_tile(counter, &s_tile);
+    if (ti >= ntiles) break;
+    const TbTile tile = tiles[ti];
+    const TbItem& it = items[tile.item];
+    const int n1 = it.n[0], n2 = it.n[1], n3 = it.n[2];
+    const int r0 = it.r[0], r1 = it.r[1], r2 = it.r[2];
+    const int n1p4 = (n1 + 3) & ~3;
+    const int rpt = (n1 + 31) >> 5;
+    const XT* X = static_cast<const XT*>(it.X);
+    for (int e = tid; e < n1 * r0; e += kBT) {
+      const int i = e % n1, a = e / n1;
+      F1s[i * Rp + a] = (float)it.fac_out[0][e];
+    }
+    for (int e = tid; e < n2 * r1; e += kBT) {
+      const int j = e % n2, b = e / n2;
+      F2s[b * n2max + j] = (float)it.fac_out[1][e];
+    }
+    double dd = 0.0, xx = 0.0;
+    for (int t = tile.t0; t < tile.t1; ++t) {
+      __syncthreads();
+      for (int e = tid; e < r0 * r1; e += kBT) {
+        float s = 0.f;
+        for (int c = 0; c < r2; ++c)
+          s = fmaf(it.core_out[e + r0 * r1 * c], (float)it.fac_out[2][t + (int64_t)n3 * c], s);
+        Ms[e] = s;  // Ms[a + r0 b]
+      }
+      __syncthreads();
+      for (int e = tid; e < n1 * r1; e += kBT) {
+        const int i = e % n1, b = e / n1;
+        float s = 0.f;
+        for (int a = 0; a < r0; ++a) s = fmaf(F1s[i * Rp + a], Ms[a + r0 * b], s);
+        Ps[b * n1max + i] = s;
+      }
+      float d2 = 0.f, x2 = 0.f;
+      for (int j0 = 0; j0 < n2; j0 += kJB) {
+        __syncthreads();
+        stage_chunk<XT>(X, n1, n2, t, j0, 32 * rpt, Xs, pitch);
+        __syncthreads();
+#pragma unroll
+        for (int w = 0; w < kJB / 8; ++w) {
+          const int jl = jq + 8 * w, j = j0 + jl;
+          if (j >= n2) continue;
+#pragma unroll
+          for (int u = 0; u < kRPT; ++u) {
+            const int i = ig + 32 * u;
+            if (u < rpt && i < n1) {
+              float xh = 0.f;
+              for (int b = 0; b < r1; ++b) xh = fmaf(Ps[b * n1max + i], F2s[b * n2max + j], xh);
+              const float xv = Xs[jl * pitch + i];
+              const float df = xv - xh;
+              d2 = fmaf(df, df, d2);
+              x2 = fmaf(xv, xv, x2);
+            }
+          }
+        }
+      }
+      dd += d2;
+      xx += x2;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      dd += __shfl_xor_sync(0xffffffffu, dd, o);
+      xx += __shfl_xor_sync(0xffffffffu, xx, o);
+    }
+    if ((tid & 31) == 0) {
+      red[0][tid >> 5] = dd;
+      red[1][tid >> 5] = xx;
+    }
+    __syncthreads();
+    if (tid == 0) {
+      double a = 0.0, b = 0.0;
+      for (int w = 0; w < kBT / 32; ++w) {
+        a += red[0][w];
+        b += red[1][w];
+      }
+      atomicAdd(it.acc, a);
+      atomicAdd(it.acc + 1, b);
+    }
+  }
+}
+
+__global__ void batch_resid_finish_kernel(const TbItem* __restrict__ items, int count,
+                                          double* __restrict__ rel) {
+  for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < count; b += gridDim.x * blockDim.x) {
+    const double* a = items[b].acc;
+    rel[b] = a[1] > 0.0 ? sqrt(a[0] / a[1]) : 0.0;
+  }
+}
+
+// ------------------------------------------------------------------ plan ----
+template <class T>
+T* carve(char*& p, size_t count) {
+  T* r = reinterpret_cast<T*>(p);
+  p += (count * sizeof(T) + 255) & ~size_t(255);
+  return r;
+}
+
+struct TbPlan {
+  // signature
+  krp_dtype xt{};
+  int count = 0, oversample = 0;
+  unsigned flags = 0;
+  std::vector<krp_tucker_item> sig;
+  // device state
+  char* arena = nullptr;
+  TbItem* d_items = nullptr;
+  TbTile* d_tiles = nullptr;
+  int ntiles = 0;
+  int* d_counters = nullptr;  // 3
+  BatchFactorJob* d_fjobs = nullptr;
+  int64_t* d_fstart = nullptr;
+  int64_t fblocks = 0;
+  QrJob* d_qjobs = nullptr;
+  EigJob* d_ejobs = nullptr;
+  double* d_rel = nullptr;
+  double* h_rel = nullptr;  // pinned
+  float* y_begin = nullptr;
+  size_t y_bytes = 0;
+  double* acc_begin = nullptr;
+  int pitch = 0, Lp = 0, Rp = 0, n1max = 0, n1max4 = 0, n2max = 0, lmax = 0;
+  size_t sm_sketch = 0, sm_core = 0, sm_resid = 0, sm_gram = 0;
+  int grid_persist = 0;
+  int slabs_per_tile = 0;
+  std::vector<TbItem> h_items;
+  cudaGraphExec_t exec = nullptr;
+  int kernels_per_run = 0;
+  // the graph is captured and replayed on a stream of the plan (the caller's
+  // stream may be the legacy default stream, which cannot be captured),
+  // ordered after and before the caller's work with two events
+  cudaStream_t cs = nullptr;
+  cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+
+  ~TbPlan() {
+    if (exec) cudaGraphExecDestroy(exec);
+    if (ev_in) cudaEventDestroy(ev_in);
+    if (ev_out) cudaEventDestroy(ev_out);
+    if (cs) cudaStreamDestroy(cs);
+    if (arena) cudaFree(arena);
+    if (h_rel) cudaFreeHost(h_rel);
+  }
+};
+
+bool same_signature(const TbPlan& p, krp_dtype xt, int count, const krp_tucker_item* items,
+                    int oversample, unsigned flags) {
+  if (p.xt != xt || p.count != count || p.oversample != oversample || p.flags != flags) return false;
+  for (int b = 0; b < count; ++b) {
+    const krp_tucker_item& a = p.sig[b];
+    const krp_tucker_item& c = items[b];
+    if (a.X != c.X || a.seed != c.seed || a.core != c.core) return false;
+    for (int m = 0; m < 3; ++m)
+      if (a.dims[m] != c.dims[m] || a.ranks[m] != c.ranks[m] || a.factors[m] != c.factors[m])
+        return false;
+  }
+  return true;
+}
+
+void build_tiles(const std::vector<TbItem>& items, int spt, std::vector<TbTile>& tiles) {
+  tiles.clear();
+  for (int b = 0; b < (int)items.size(); ++b) {
+    const int n3 = items[b].n[2];
+    for (int t0 = 0; t0 < n3; t0 += spt) tiles.push_back(TbTile{b, t0, std::min(n3, t0 + spt), 0});
+  }
+  // largest work first: n1 * n2 * slabs
+  std::stable_sort(tiles.begin(), tiles.end(), [&](const TbTile& a, const TbTile& c) {
+    const int64_t wa = (int64_t)items[a.item].n[0] * items[a.item].n[1] * (a.t1 - a.t0);
+    const int64_t wc = (int64_t)items[c.item].n[0] * items[c.item].n[1] * (c.t1 - c.t0);
+    return wa > wc;
+  });
+}
+
+void launch_sketch(const TbPlan& P) {
+  if (P.xt == KRP_F32)
+    batch_sketch_kernel<float><<<P.grid_persist, kBT, P.sm_sketch, stream()>>>(
+        P.d_items, P.d_tiles, P.ntiles, P.d_counters + 0, P.pitch, P.Lp, P.n1max4, P.n2max);
+  else
+    batch_sketch_kernel<__nv_bfloat16><<<P.grid_persist, kBT, P.sm_sketch, stream()>>>(
+        P.d_items, P.d_tiles, P.ntiles, P.d_counters + 0, P.pitch, P.Lp, P.n1max4, P.n2max);
+  check_launch("batch_sketch");
+}
+
+// The whole batch, enqueued on the context stream (captured once into a graph).
+void enqueue_all(TbPlan& P, int* status) {
+  const bool trunc = P.flags & KRP_TRUNCATE;
+  const bool resid = P.flags & KRP_RESIDUAL;
+  int nk = 0;
+  KRP_CUDA_CHECK(cudaMemsetAsync(P.d_counters, 0, 3 * sizeof(int), stream()));
+  KRP_CUDA_CHECK(cudaMemsetAsync(P.y_begin, 0, P.y_bytes, stream()));
+  KRP_CUDA_CHECK(cudaMemsetAsync(P.acc_begin, 0, sizeof(double) * 2 * P.count, stream()));
+  launch_gen_factors_batch(P.d_fjobs, P.d_fstart, 3 * P.count, P.fblocks);
+  ++nk;
+  launch_sketch(P);
+  ++nk;
+  qr_householder_launch(P.d_qjobs, 3 * P.count, status);
+  ++nk;
+  if (P.xt == KRP_F32)
+    batch_core_kernel<float><<<P.grid_persist, kBT, P.sm_core, stream()>>>(
+        P.d_items, P.d_tiles, P.ntiles, P.d_counters + 1, P.pitch, P.Lp, P.n1max4, P.n2max);
+  else
+    batch_core_kernel<__nv_bfloat16><<<P.grid_persist, kBT, P.sm_core, stream()>>>(
+        P.d_items, P.d_tiles, P.ntiles, P.d_counters + 1, P.pitch, P.Lp, P.n1max4, P.n2max);
+  check_launch("batch_core");
+  batch_core_finish_kernel<<<P.count, 256, 0, stream()>>>(P.d_items);
+  check_launch("batch_core_finish");
+  nk += 2;
+  if (trunc) {
+    batch_gram_kernel<<<dim3(P.count, 3), 256, P.sm_gram, stream()>>>(P.d_items);
+    check_launch("batch_gram");
+    eig_launch(P.d_ejobs, 3 * P.count, P.lmax, status);
+    nk += 2;
+  }
+  batch_trunc_apply_kernel<<<P.count, 256, 0, stream()>>>(P.d_items, trunc ? 1 : 0);
+  check_launch("batch_trunc_apply");
+  ++nk;
+  if (resid) {
+    if (P.xt == KRP_F32)
+      batch_resid_kernel<float><<<P.grid_persist, kBT, P.sm_resid, stream()>>>(
+          P.d_items, P.d_tiles, P.ntiles, P.d_counters + 2, P.pitch, P.Rp, P.n1max, P.n2max);
+    else
+      batch_resid_kernel<__nv_bfloat16><<<P.grid_persist, kBT, P.sm_resid, stream()>>>(
+          P.d_items, P.d_tiles, P.ntiles, P.d_counters + 2, P.pitch, P.Rp, P.n1max, P.n2max);
+    check_launch("batch_resid");
+    batch_resid_finish_kernel<<<(P.count + 255) / 256, 256, 0, stream()>>>(P.d_items, P.count,
+                                                                          P.d_rel);
+    check_launch("batch_resid_finish");
+    nk += 2;
+    KRP_CUDA_CHECK(cudaMemcpyAsync(P.h_rel, P.d_rel, sizeof(double) * P.count,
+                                   cudaMemcpyDeviceToHost, stream()));
+  }
+  P.kernels_per_run = nk;
+}
+
+template <class K>
+void allow_smem(K k, size_t bytes) {
+  KRP_CUDA_CHECK(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+}
+
+std::unique_ptr<TbPlan> build_plan(Ctx* c, krp_dtype xt, int count, const krp_tucker_item* items,
+                                   int oversample, unsigned flags) {
+  auto P = std::make_unique<TbPlan>();
+  P->xt = xt;
+  P->count = count;
+  P->oversample = oversample;
+  P->flags = flags;
+  P->sig.assign(items, items + count);
+  const bool trunc = flags & KRP_TRUNCATE;
+  // sizes
+  size_t bytes = 0;
+  auto add = [&](size_t n, size_t e) { bytes += (n * e + 255) & ~size_t(255); };
+  std::vector<int> lm(count);
+  for (int b = 0; b < count; ++b) {
+    const krp_tucker_item& it = items[b];
+    int l[3], r[3];
+    int lmx = 0;
+    for (int m = 0; m < 3; ++m) {
+      l[m] = it.ranks[m] + oversample;
+      r[m] = trunc ? it.ranks[m] : l[m];
+      lmx = std::max(lmx, l[m]);
+    }
+    lm[b] = lmx;
+    for (int m = 0; m < 3; ++m) {
+      add((size_t)it.dims[m] * lmx, 4);       // om
+      add((size_t)it.dims[m] * lmx, 4);       // Y (added separately below too)
+      add((size_t)it.dims[m] * l[m], 8);      // Q
+      add((size_t)it.dims[m] * l[m], 8);      // QR work
+      add((size_t)l[m] * l[m], 8);            // S
+      add((size_t)l[m] * r[m], 8);            // U
+    }
+    add((size_t)it.dims[2] * l[0] * l[1], 4);       // C
+    add((size_t)l[0] * l[1] * l[2], 4);             // G
+    add((size_t)r[0] * l[1] * l[2], 8);             // T1
+    add((size_t)r[0] * r[1] * l[2], 8);             // T2
+  }
+  add((size_t)2 * count, 8);  // acc
+  add((size_t)count, sizeof(TbItem));
+  add((size_t)3 * count, sizeof(BatchFactorJob));
+  add((size_t)3 * count + 1, 8);
+  add((size_t)3 * count, sizeof(QrJob));
+  add((size_t)3 * count, sizeof(EigJob));
+  add((size_t)count, 8);  // rel
+  add(3, 4);              // counters
+  int64_t total_slabs = 0;
+  for (int b = 0; b < count; ++b) total_slabs += items[b].dims[2];
+  add((size_t)total_slabs, sizeof(TbTile));
+  KRP_CUDA_CHECK(cudaStreamCreateWithFlags(&P->cs, cudaStreamNonBlocking));
+  KRP_CUDA_CHECK(cudaEventCreateWithFlags(&P->ev_in, cudaEventDisableTiming));
+  KRP_CUDA_CHECK(cudaEventCreateWithFlags(&P->ev_out, cudaEventDisableTiming));
+  KRP_CUDA_CHECK(cudaMalloc(&P->arena, bytes));
+  KRP_CUDA_CHECK(cudaMallocHost(&P->h_rel, sizeof(double) * count));
+  char* p = P->arena;
+  // Y arrays first and contiguous (one memset per run), then the rest
+  P->h_items.resize(count);
+  char* y0 = p;
+  for (int b = 0; b < count; ++b)
+    for (int m = 0; m < 3; ++m)
+      P->h_items[b].Y[m] = carve<float>(p, (size_t)items[b].dims[m] * lm[b]);
+  P->y_begin = reinterpret_cast<float*>(y0);
+  P->y_bytes = (size_t)(p - y0);
+  P->acc_begin = carve<double>(p, (size_t)2 * count);
+  std::vector<BatchFactorJob> fj;
+  std::vector<int64_t> fstart(1, 0);
+  std::vector<QrJob> qj;
+  std::vector<EigJob> ej;
+  P->n1max = P->n2max = P->lmax = 0;
+  int rmax = 0;
+  for (int b = 0; b < count; ++b) {
+    const krp_tucker_item& src = items[b];
+    TbItem& it = P->h_items[b];
+    it.X = src.X;
+    it.lm = lm[b];
+    for (int m = 0; m < 3; ++m) {
+      it.n[m] = (int)src.dims[m];
+      it.l[m] = src.ranks[m] + oversample;
+      it.r[m] = trunc ? src.ranks[m] : it.l[m];
+      it.om[m] = carve<float>(p, (size_t)it.n[m] * it.lm);
+      it.Q[m] = carve<double>(p, (size_t)it.n[m] * it.l[m]);
+      double* work = carve<double>(p, (size_t)it.n[m] * it.l[m]);
+      it.S[m] = carve<double>(p, (size_t)it.l[m] * it.l[m]);
+      it.U[m] = carve<double>(p, (size_t)it.l[m] * it.r[m]);
+      it.fac_out[m] = src.factors[m];
+      BatchFactorJob f{};
+      f.ptr = it.om[m];
+      f.rows = it.n[m];
+      f.seed = src.seed;
+      f.factor = (uint32_t)m;
+      f.draw = KRP_DRAW_MEMO;
+      f.tag = KRP_TAG_OMEGA;
+      f.ell = it.lm;
+      f.bf16_round = xt == KRP_BF16 ? 1 : 0;
+      fj.push_back(f);
+      fstart.push_back(fstart.back() + ((int64_t)it.n[m] * it.lm + 3) / 4);
+      QrJob q{};
+      q.Y = it.Y[m];
+      q.Q = it.Q[m];
+      q.R = nullptr;
+      q.work = work;
+      q.m = it.n[m];
+      q.l = it.l[m];
+      qj.push_back(q);
+      ej.push_back(EigJob{it.S[m], it.U[m], nullptr, it.l[m], it.r[m]});
+      P->lmax = std::max(P->lmax, it.l[m]);
+      rmax = std::max(rmax, it.r[m]);
+    }
+    it.C = carve<float>(p, (size_t)it.n[2] * it.l[0] * it.l[1]);
+    it.G = carve<float>(p, (size_t)it.l[0] * it.l[1] * it.l[2]);
+    it.T1 = carve<double>(p, (size_t)it.r[0] * it.l[1] * it.l[2]);
+    it.T2 = carve<double>(p, (size_t)it.r[0] * it.r[1] * it.l[2]);
+    it.core_out = src.core;
+    it.acc = P->acc_begin + 2 * b;
+    P->n1max = std::max(P->n1max, it.n[0]);
+    P->n2max = std::max(P->n2max, it.n[1]);
+  }
+  P->d_items = carve<TbItem>(p, count);
+  P->d_fjobs = carve<BatchFactorJob>(p, (size_t)3 * count);
+  P->d_fstart = carve<int64_t>(p, (size_t)3 * count + 1);
+  P->d_qjobs = carve<QrJob>(p, (size_t)3 * count);
+  P->d_ejobs = carve<EigJob>(p, (size_t)3 * count);
+  P->d_rel = carve<double>(p, count);
+  P->d_counters = carve<int>(p, 3);
+  P->d_tiles = carve<TbTile>(p, (size_t)total_slabs);
+  KRP_REQUIRE((size_t)(p - P->arena) <= bytes, "batch plan arena overflow");
+  P->fblocks = fstart.back();
+  cudaStream_t s = c->stream;
+  KRP_CUDA_CHECK(cudaMemcpyAsync(P->d_items, P->h_items.data(), sizeof(TbItem) * count,
+                                 cudaMemcpyHostToDevice, s));
+  KRP_CUDA_CHECK(cudaMemcpyAsync(P->d_fjobs, fj.data(), sizeof(BatchFactorJob) * fj.size(),
+                                 cudaMemcpyHostToDevice, s));
+  KRP_CUDA_CHECK(cudaMemcpyAsync(P->d_fstart, fstart.data(), sizeof(int64_t) * fstart.size(),
+                                 cudaMemcpyHostToDevice, s));
+  KRP_CUDA_CHECK(cudaMemcpyAsync(P->d_qjobs, qj.data(), sizeof(QrJob) * qj.size(),
+                                 cudaMemcpyHostToDevice, s));
+  KRP_CUDA_CHECK(cudaMemcpyAsync(P->d_ejobs, ej.data(), sizeof(EigJob) * ej.size(),
+                                 cudaMemcpyHostToDevice, s));
+  // shared-memory shapes
+  P->n1max4 = (P->n1max + 3) & ~3;
+  P->pitch = ((P->n1max4 + 31) & ~31) + 4;
+  P->Lp = (P->lmax + 3) & ~3;
+  P->Rp = std::max(1, rmax);
+  P->sm_sketch = sizeof(float) * ((size_t)kJB * P->pitch + (size_t)P->n1max4 * P->Lp +
+                                  2 * (size_t)P->n2max * P->Lp + 2 * P->Lp);
+  P->sm_core = sizeof(float) * ((size_t)kJB * P->pitch + (size_t)P->n1max4 * P->Lp +
+                                (size_t)P->n2max * P->Lp + (size_t)kJB * P->Lp);
+  P->sm_resid = sizeof(float) * ((size_t)kJB * P->pitch + (size_t)P->n1max * P->Rp +
+                                 (size_t)P->Rp * P->n2max + (size_t)P->Rp * P->Rp +
+                                 (size_t)P->Rp * P->n1max);
+  P->sm_gram = sizeof(float) * (size_t)P->lmax * P->lmax * P->lmax;
+  allow_smem(batch_sketch_kernel<float>, P->sm_sketch);
+  allow_smem(batch_sketch_kernel<__nv_bfloat16>, P->sm_sketch);
+  allow_smem(batch_core_kernel<float>, P->sm_core);
+  allow_smem(batch_core_kernel<__nv_bfloat16>, P->sm_core);
+  allow_smem(batch_resid_kernel<float>, P->sm_resid);
+  allow_smem(batch_resid_kernel<__nv_bfloat16>, P->sm_resid);
+  allow_smem(batch_gram_kernel, P->sm_gram);
+  int occ = 1;
+  KRP_CUDA_CHECK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+      &occ, batch_sketch_kernel<float>, kBT, P->sm_sketch));
+  P->grid_persist = std::max(1, occ) * c->num_sms;
+  return P;
+}
+
+// Slabs per work tile: time the sketch phase for a few granularities.
+void autotune(TbPlan& P) {
+  const int cand[] = {1, 2, 4, 8};
+  std::vector<TbTile> tiles;
+  float best_ms = 1e30f;
+  int best = 1;
+  cudaEvent_t e0, e1;
+  KRP_CUDA_CHECK(cudaEventCreate(&e0));
+  KRP_CUDA_CHECK(cudaEventCreate(&e1));
+  // factors for the sketch
+  launch_gen_factors_batch(P.d_fjobs, P.d_fstart, 3 * P.count, P.fblocks);
+  for (int spt : cand) {
+    build_tiles(P.h_items, spt, tiles);
+    P.ntiles = (int)tiles.size();
+    KRP_CUDA_CHECK(cudaMemcpyAsync(P.d_tiles, tiles.data(), sizeof(TbTile) * tiles.size(),
+                                   cudaMemcpyHostToDevice, stream()));
+    float ms_sum = 0.f;
+    for (int rep = 0; rep < 2; ++rep) {
+      KRP_CUDA_CHECK(cudaMemsetAsync(P.d_counters, 0, 3 * sizeof(int), stream()));
+      KRP_CUDA_CHECK(cudaMemsetAsync(P.y_begin, 0, P.y_bytes, stream()));
+      KRP_CUDA_CHECK(cudaEventRecord(e0, stream()));
+      launch_sketch(P);
+      KRP_CUDA_CHECK(cudaEventRecord(e1, stream()));
+      KRP_CUDA_CHECK(cudaEventSynchronize(e1));
+      float ms = 0.f;
+      KRP_CUDA_CHECK(cudaEventElapsedTime(&ms, e0, e1));
+      if (rep) ms_sum += ms;
+    }
+    if (ms_sum < best_ms) {
+      best_ms = ms_sum;
+      best = spt;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  P.slabs_per_tile = best;
+  build_tiles(P.h_items, best, tiles);
+  P.ntiles = (int)tiles.size();
+  KRP_CUDA_CHECK(cudaMemcpyAsync(P.d_tiles, tiles.data(), sizeof(TbTile) * tiles.size(),
+                                 cudaMemcpyHostToDevice, stream()));
+  KRP_CUDA_CHECK(cudaStreamSynchronize(stream()));
+}
+
+// Temporarily direct the context's launches to another stream.
+struct StreamSwap {
+  Ctx* c;
+  cudaStream_t saved;
+  StreamSwap(Ctx* ctx, cudaStream_t s) : c(ctx), saved(ctx->stream) { c->stream = s; }
+  ~StreamSwap() { c->stream = saved; }
+};
+
+void capture(TbPlan& P, Ctx* c) {
+  cudaGraph_t g = nullptr;
+  const uint64_t launches = c->launches;  // captured kernels do not run here
+  StreamSwap sw(c, P.cs);
+  KRP_CUDA_CHECK(cudaStreamBeginCapture(P.cs, cudaStreamCaptureModeRelaxed));
+  try {
+    enqueue_all(P, c->d_status);
+  } catch (...) {
+    cudaStreamEndCapture(P.cs, &g);
+    if (g) cudaGraphDestroy(g);
+    throw;
+  }
+  KRP_CUDA_CHECK(cudaStreamEndCapture(P.cs, &g));
+  c->launches = launches;
+  const cudaError_t e = cudaGraphInstantiate(&P.exec, g, 0);
+  cudaGraphDestroy(g);
+  KRP_CUDA_CHECK(e);
+}
+
+void plan_free(void* p) { delete static_cast<TbPlan*>(p); }
+
+}  // namespace
+
+void tucker_batched(krp_dtype xt, int count, krp_tucker_item* items, int oversample,
+                    unsigned flags) {
+  Ctx* c = current();
+  KRP_REQUIRE(count >= 1, "count must be >= 1");
+  KRP_REQUIRE(items, "items is NULL");
+  KRP_REQUIRE(xt == KRP_F32 || xt == KRP_BF16, "X dtype must be KRP_F32 or KRP_BF16");
+  KRP_REQUIRE(oversample >= 0, "oversample must be >= 0");
+  KRP_REQUIRE(!(flags & ~(unsigned)(KRP_MEMO | KRP_TRUNCATE | KRP_RESIDUAL)),
+              "batched flags: KRP_MEMO, KRP_TRUNCATE, KRP_RESIDUAL");
+  for (int b = 0; b < count; ++b) {
+    const krp_tucker_item& it = items[b];
+    KRP_REQUIRE(it.X && is_device_ptr(it.X), "item %d: X must be a device pointer", b);
+    KRP_REQUIRE(it.core && is_device_ptr(it.core), "item %d: core must be a device pointer", b);
+    for (int m = 0; m < 3; ++m) {
+      KRP_REQUIRE(it.dims[m] >= 1 && it.dims[m] <= kMaxSide, "item %d: n_%d = %lld out of 1..%d",
+                  b, m, (long long)it.dims[m], kMaxSide);
+      const int l = it.ranks[m] + oversample;
+      KRP_REQUIRE(it.ranks[m] >= 1 && l <= kMaxEll && l <= it.dims[m],
+                  "item %d: l_%d = %d must be <= min(%d, n_%d)", b, m, l, kMaxEll, m);
+      KRP_REQUIRE(it.factors[m] && is_device_ptr(it.factors[m]),
+                  "item %d: factors[%d] must be a device pointer", b, m);
+    }
+    if (xt == KRP_BF16)
+      KRP_REQUIRE((reinterpret_cast<uintptr_t>(it.X) & 1) == 0, "item %d: X misaligned", b);
+  }
+  flags |= KRP_MEMO;  // the batched path draws one factor set per tensor
+  TbPlan* P = static_cast<TbPlan*>(c->batch_plan);
+  if (!P || !same_signature(*P, xt, count, items, oversample, flags)) {
+    if (c->batch_plan) c->batch_plan_free(c->batch_plan);
+    c->batch_plan = nullptr;
+    std::unique_ptr<TbPlan> np = build_plan(c, xt, count, items, oversample, flags);
+    autotune(*np);
+    // one eager run (validates the sequence), then the graph
+    enqueue_all(*np, c->d_status);
+    KRP_CUDA_CHECK(cudaStreamSynchronize(c->stream));
+    raise_device_status(c);
+    capture(*np, c);
+    P = np.release();
+    c->batch_plan = P;
+    c->batch_plan_free = plan_free;
+  }
+  KRP_CUDA_CHECK(cudaEventRecord(P->ev_in, c->stream));
+  KRP_CUDA_CHECK(cudaStreamWaitEvent(P->cs, P->ev_in, 0));
+  KRP_CUDA_CHECK(cudaGraphLaunch(P->exec, P->cs));
+  KRP_CUDA_CHECK(cudaEventRecord(P->ev_out, P->cs));
+  KRP_CUDA_CHECK(cudaStreamWaitEvent(c->stream, P->ev_out, 0));
+  c->launches += P->kernels_per_run;
+  KRP_CUDA_CHECK(cudaStreamSynchronize(P->cs));
+  raise_device_status(c);
+  for (int b = 0; b < count; ++b)
+    items[b].rel_residual = (flags & KRP_RESIDUAL) ? P->h_rel[b] : -1.0;
+}
+
+int tucker_batched_plan_info(int* slabs_per_tile, int* tiles, int* grid) {
+  TbPlan* P = static_cast<TbPlan*>(current()->batch_plan);
+  if (!P) return 0;
+  if (slabs_per_tile) *slabs_per_tile = P->slabs_per_tile;
+  if (tiles) *tiles = P->ntiles;
+  if (grid) *grid = P->grid_persist;
+  return 1;
+}
+
+}  // namespace krp

@@ -70,6 +70,8 @@ struct Ctx {
   uint64_t launches = 0;
   int num_sms = 0;
   int* d_status = nullptr;  // device status word for bounded waits / numerics
+  void* batch_plan = nullptr;              // cached batched-Tucker plan (batched.cu)
+  void (*batch_plan_free)(void*) = nullptr;
 };
 
 Ctx* current();           // context of the API call in progress (thread-local)
@@ -86,6 +88,19 @@ struct FactorJob {
 };
 void launch_gen_factors(uint64_t seed, uint32_t draw, uint32_t tag, int ell,
                         krp_dtype type, const FactorJob* jobs, int njobs);
+// One factor of a batch: its own key (seed), counter words (factor, draw,
+// tag) as above, rows x ell FP32 column-major output.
+struct BatchFactorJob {
+  float* ptr;
+  int64_t rows;
+  uint64_t seed;
+  uint32_t factor, draw, tag;
+  int ell;
+  int bf16_round;
+};
+// d_start: njobs+1 prefix sums of ceil(rows*ell/4) (device memory)
+void launch_gen_factors_batch(const BatchFactorJob* d_jobs, const int64_t* d_start, int njobs,
+                              int64_t total_blocks);
 void launch_philox_words(uint64_t seed, uint32_t c1, uint32_t c2, uint32_t c3,
                          uint64_t first_block, int64_t nblocks, uint32_t* out);
 
@@ -137,6 +152,19 @@ void qr_householder_f64(const QrJob* jobs, int count, int* status);
 void gram_mode_f64(const double* G, int D, const int64_t* dims, int mode, double* S);
 // eigenvectors of symmetric S (l x l), sorted by eigenvalue descending; U gets
 // the first r columns (l x r column-major)
+// One symmetric eigenproblem (l x l FP64, l <= 64): the r leading
+// eigenvectors into U (l x r, column-major) and, if ev is set, all l
+// eigenvalues in descending order.
+struct EigJob {
+  const double* S;
+  double* U;
+  double* ev;
+  int l, r;
+};
+// Launchers over job arrays already in device memory (no host copies, so
+// they can be captured in a CUDA graph); maxl bounds every job's l.
+void eig_launch(const EigJob* d_jobs, int count, int maxl, int* status);
+void qr_householder_launch(const QrJob* d_jobs, int count, int* status);
 void sym_eig_top_f64(const double* const* S, const int* l, const int* r,
                      double* const* U, int count, int* status,
                      double* const* evals = nullptr);

@@ -169,12 +169,6 @@ __global__ void gram_kernel(const double* __restrict__ G, int64_t P, int64_t l, 
 
 constexpr int kEigMaxL = 64;
 
-struct EigJob {
-  const double* S;
-  double* U;
-  double* ev;  // sorted eigenvalues (l), may be null
-  int l, r;
-};
 
 // Symmetric eigensolver for one l x l FP64 matrix per CTA (l <= 64), in two
 // stages.  GB300 issues FP32 at ~58x its FP64 rate, so
@@ -191,7 +185,6 @@ struct EigJob {
 //     E_ij = r_ij / 2, and X <- X + X E.  It converges quadratically, so two
 //     steps take the FP32 start (error ~1e-7) to FP64 rounding; within a
 //     cluster narrower than delta it only restores orthonormality.
-constexpr int kEP = kEigMaxL + 1;  // padded row pitch
 constexpr int kEigThreads = 256;
 constexpr int kEigRefine = 2;
 constexpr int kEigSweeps32 = 15;
@@ -214,7 +207,8 @@ __device__ double block_sum(double v, double* red) {
   return s;
 }
 
-__device__ void jacobi32(float (*S)[kEP], float (*V)[kEP], int n, float* cs, float* sn, int* pp,
+template <int EP>  // row pitch of the padded matrices
+__device__ void jacobi32(float (*S)[EP], float (*V)[EP], int n, float* cs, float* sn, int* pp,
                          int* qq, double* red) {
   const int tid = threadIdx.x, P = n / 2;
   for (int sweep = 0; sweep < kEigSweeps32; ++sweep) {
@@ -293,8 +287,8 @@ __device__ void jacobi32(float (*S)[kEP], float (*V)[kEP], int n, float* cs, flo
 
 // C = op(A) B for l x l matrices in shared memory (op = transpose if TA);
 // with SYM only the upper triangle is computed and mirrored.
-template <bool TA, bool SYM>
-__device__ void smem_gemm(const double (*A)[kEP], const double (*B)[kEP], double (*C)[kEP], int l) {
+template <bool TA, bool SYM, int EP>
+__device__ void smem_gemm(const double (*A)[EP], const double (*B)[EP], double (*C)[EP], int l) {
   for (int e = threadIdx.x; e < l * l; e += blockDim.x) {
     const int i = e % l, j = e / l;
     if (SYM && i > j) continue;
@@ -305,12 +299,15 @@ __device__ void smem_gemm(const double (*A)[kEP], const double (*B)[kEP], double
   }
 }
 
+// ML: largest l the instance handles (shared memory 5 * 8 * ML * (ML+1) bytes)
+template <int ML>
 __global__ void __launch_bounds__(kEigThreads) eig_kernel(const EigJob* __restrict__ jobs, int* status) {
+  constexpr int kEP = ML + 1;  // padded row pitch
   const EigJob job = jobs[blockIdx.x];
   const int l = job.l;
   const int n = (l + 1) & ~1;  // padded to even for the tournament
   extern __shared__ double eig_smem[];
-  constexpr int kMat = kEigMaxL * kEP;
+  constexpr int kMat = ML * kEP;
   double(*A)[kEP] = reinterpret_cast<double(*)[kEP]>(eig_smem);
   double(*X)[kEP] = reinterpret_cast<double(*)[kEP]>(eig_smem + kMat);
   double(*T)[kEP] = reinterpret_cast<double(*)[kEP]>(eig_smem + 2 * kMat);
@@ -318,11 +315,11 @@ __global__ void __launch_bounds__(kEigThreads) eig_kernel(const EigJob* __restri
   double(*Rm)[kEP] = reinterpret_cast<double(*)[kEP]>(eig_smem + 4 * kMat);
   // the FP32 stage lives in T's storage
   float(*S32)[kEP] = reinterpret_cast<float(*)[kEP]>(eig_smem + 2 * kMat);
-  float(*V32)[kEP] = reinterpret_cast<float(*)[kEP]>(eig_smem + 2 * kMat) + kEigMaxL;
-  __shared__ float cs32[kEigMaxL / 2], sn32[kEigMaxL / 2];
-  __shared__ int pp[kEigMaxL / 2], qq[kEigMaxL / 2];
-  __shared__ int order[kEigMaxL];
-  __shared__ double lam[kEigMaxL];
+  float(*V32)[kEP] = reinterpret_cast<float(*)[kEP]>(eig_smem + 2 * kMat) + ML;
+  __shared__ float cs32[ML / 2], sn32[ML / 2];
+  __shared__ int pp[ML / 2], qq[ML / 2];
+  __shared__ int order[ML];
+  __shared__ double lam[ML];
   __shared__ double red[16];
   __shared__ float redf[8];
   const int tid = threadIdx.x;
@@ -351,7 +348,7 @@ __global__ void __launch_bounds__(kEigThreads) eig_kernel(const EigJob* __restri
     if (tid == 0) atomicExch(status, (int)KRP_ENUMERIC);
     return;
   }
-  jacobi32(S32, V32, n, cs32, sn32, pp, qq, red);
+  jacobi32<kEP>(S32, V32, n, cs32, sn32, pp, qq, red);
   for (int e = tid; e < l * l; e += blockDim.x) {
     const int r = e % l, c = e / l;
     X[r][c] = (double)V32[r][c];
@@ -361,10 +358,10 @@ __global__ void __launch_bounds__(kEigThreads) eig_kernel(const EigJob* __restri
   for (int e = tid; e < l * l; e += blockDim.x) a2 = fma(A[e % l][e / l], A[e % l][e / l], a2);
   const double anorm = sqrt(block_sum(a2, red));
   for (int it = 0; it < kEigRefine; ++it) {
-    smem_gemm<false, false>(A, X, T, l);  // T = A X
+    smem_gemm<false, false, kEP>(A, X, T, l);  // T = A X
     __syncthreads();
-    smem_gemm<true, true>(X, T, Sm, l);  // S = X^T A X
-    smem_gemm<true, true>(X, X, Rm, l);  // X^T X (turned into R below)
+    smem_gemm<true, true, kEP>(X, T, Sm, l);  // S = X^T A X
+    smem_gemm<true, true, kEP>(X, X, Rm, l);  // X^T X (turned into R below)
     __syncthreads();
     double soff = 0.0, r2 = 0.0;
     for (int e = tid; e < l * l; e += blockDim.x) {
@@ -387,7 +384,7 @@ __global__ void __launch_bounds__(kEigThreads) eig_kernel(const EigJob* __restri
       T[i][j] = eij;
     }
     __syncthreads();
-    smem_gemm<false, false>(X, T, Sm, l);  // X E
+    smem_gemm<false, false, kEP>(X, T, Sm, l);  // X E
     __syncthreads();
     for (int e = tid; e < l * l; e += blockDim.x) {
       const int i = e % l, j = e / l;
@@ -802,6 +799,29 @@ void gram_mode_f64(const double* G, int D, const int64_t* dims, int mode, double
   check_launch("gram_f64");
 }
 
+void eig_launch(const EigJob* d_jobs, int count, int maxl, int* status) {
+  if (count <= 0) return;
+  KRP_REQUIRE(maxl >= 1 && maxl <= kEigMaxL, "eigensolver needs l <= %d", kEigMaxL);
+  if (maxl <= 32) {
+    const size_t smem = 5 * sizeof(double) * 32 * 33;
+    KRP_CUDA_CHECK(cudaFuncSetAttribute(eig_kernel<32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)smem));
+    eig_kernel<32><<<count, kEigThreads, smem, stream()>>>(d_jobs, status);
+  } else {
+    const size_t smem = 5 * sizeof(double) * kEigMaxL * (kEigMaxL + 1);
+    KRP_CUDA_CHECK(cudaFuncSetAttribute(eig_kernel<kEigMaxL>,
+                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    eig_kernel<kEigMaxL><<<count, kEigThreads, smem, stream()>>>(d_jobs, status);
+  }
+  check_launch("jacobi_eig_f64");
+}
+
+void qr_householder_launch(const QrJob* d_jobs, int count, int* status) {
+  if (count <= 0) return;
+  qr_kernel<<<count, kQrThreads, 0, stream()>>>(d_jobs, status);
+  check_launch("qr_householder_f64");
+}
+
 void sym_eig_top_f64(const double* const* S, const int* l, const int* r, double* const* U,
                      int count, int* status, double* const* evals) {
   if (count <= 0) return;
@@ -814,15 +834,7 @@ void sym_eig_top_f64(const double* const* S, const int* l, const int* r, double*
   EigJob* d_jobs = current()->ws.take<EigJob>(count);
   KRP_CUDA_CHECK(cudaMemcpyAsync(d_jobs, jobs.data(), sizeof(EigJob) * count,
                                  cudaMemcpyHostToDevice, stream()));
-  const size_t smem = 5 * sizeof(double) * kEigMaxL * kEP;
-  static bool attr_set = false;
-  if (!attr_set) {
-    KRP_CUDA_CHECK(cudaFuncSetAttribute(eig_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                        (int)smem));
-    attr_set = true;
-  }
-  eig_kernel<<<count, kEigThreads, smem, stream()>>>(d_jobs, status);
-  check_launch("jacobi_eig_f64");
+  eig_launch(d_jobs, count, kEigMaxL, status);
 }
 
 void ttm_small_f64(const double* G, int D, const int64_t* dims, int mode, const double* U, int r,

@@ -84,6 +84,43 @@ __global__ void gen_factors_kernel(const GenParams P) {
   }
 }
 
+// Many factors with their own keys: job j covers blocks [start[j], start[j+1])
+// of the flattened launch; values are stored as FP32 (bf16_round: rounded to
+// BF16 first, the values a BF16 factor would hold).
+__global__ void gen_factors_batch_kernel(const BatchFactorJob* __restrict__ jobs,
+                                         const int64_t* __restrict__ start, int njobs) {
+  const int64_t total = start[njobs];
+  for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < total;
+       g += (int64_t)gridDim.x * blockDim.x) {
+    int lo = 0, hi = njobs - 1;  // last job with start <= g
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (start[mid] <= g) lo = mid; else hi = mid - 1;
+    }
+    const BatchFactorJob& job = jobs[lo];
+    const int64_t b = g - start[lo];
+    const uint4 w = philox10(make_uint4(static_cast<uint32_t>(b), job.factor, job.draw, job.tag),
+                             static_cast<uint32_t>(job.seed & 0xFFFFFFFFu),
+                             static_cast<uint32_t>(job.seed >> 32));
+    const int64_t n = job.rows * job.ell;
+    const double ra = sqrt(-2.0 * log(uopen(w.x)));
+    const double rb = sqrt(-2.0 * log(uopen(w.z)));
+    double sa, ca, sb, cb;
+    sincospi(2.0 * uopen(w.y), &sa, &ca);
+    sincospi(2.0 * uopen(w.w), &sb, &cb);
+    const double z[4] = {ra * ca, ra * sa, rb * cb, rb * sb};
+#pragma unroll
+    for (int l = 0; l < 4; ++l) {
+      const int64_t e = 4 * b + l;
+      if (e < n) {
+        float v = static_cast<float>(z[l]);
+        if (job.bf16_round) v = __bfloat162float(__float2bfloat16_rn(v));
+        job.ptr[e] = v;
+      }
+    }
+  }
+}
+
 __global__ void philox_words_kernel(uint32_t k0, uint32_t k1, uint32_t c1, uint32_t c2,
                                     uint32_t c3, uint64_t first, int64_t n, uint32_t* out) {
   for (int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; b < n;
@@ -123,6 +160,16 @@ void launch_gen_factors(uint64_t seed, uint32_t draw, uint32_t tag, int ell, krp
     default: fail(KRP_EINVAL, "unsupported factor dtype %d", (int)type);
   }
   check_launch("gen_factors");
+}
+
+void launch_gen_factors_batch(const BatchFactorJob* d_jobs, const int64_t* d_start, int njobs,
+                              int64_t total_blocks) {
+  if (njobs <= 0 || total_blocks <= 0) return;
+  const int threads = 256;
+  const int64_t want = (total_blocks + threads - 1) / threads;
+  const int grid = static_cast<int>(want < 4096 ? want : 4096);
+  gen_factors_batch_kernel<<<grid, threads, 0, stream()>>>(d_jobs, d_start, njobs);
+  check_launch("gen_factors_batch");
 }
 
 void launch_philox_words(uint64_t seed, uint32_t c1, uint32_t c2, uint32_t c3, uint64_t first,

@@ -35,6 +35,10 @@ void tucker_pipeline(bool sequential, const void* X, krp_dtype xt, int d, const 
                      const int* ranks, int oversample, uint64_t seed, unsigned flags,
                      krp_tucker_out* out);
 
+void tucker_batched(krp_dtype xt, int count, krp_tucker_item* items, int oversample,
+                    unsigned flags);
+int tucker_batched_plan_info(int* slabs_per_tile, int* tiles, int* grid);
+
 void hankel_pipeline(const void* blocks, krp_dtype bt, int m, int n, int s, int r, int ell_r,
                      int ell_l, uint64_t seed, double* U, double* S, double* V);
 void hankel_sketch_only(const void* blocks, krp_dtype bt, int m, int n, int s,

@@ -31,7 +31,7 @@ EXPORTED = [
     "krp_abi_version", "krp_launch_count", "krp_gen_factors", "krp_philox_words",
     "krp_sketch_mode", "krp_sketch_all_modes", "krp_qr", "krp_qr_noalloc", "krp_multi_ttm",
     "krp_tucker_rhosvd", "krp_tucker_sthosvd", "krp_block_hankel_lowrank",
-    "krp_block_hankel_sketch",
+    "krp_block_hankel_sketch", "krp_tucker_rhosvd_batched", "krp_tucker_batch_plan_info",
 ]
 
 
@@ -57,6 +57,18 @@ class TuckerOut(C.Structure):
         ("x_norm", C.c_double),
         ("core_norm", C.c_double),
         ("times", PhaseTimes),
+    ]
+
+
+class TuckerItem(C.Structure):
+    _fields_ = [
+        ("X", C.c_void_p),
+        ("dims", C.c_int64 * 3),
+        ("ranks", C.c_int * 3),
+        ("seed", C.c_uint64),
+        ("core", C.c_void_p),
+        ("factors", C.c_void_p * 3),
+        ("rel_residual", C.c_double),
     ]
 
 
@@ -103,6 +115,10 @@ def load_library(path: Optional[str] = None):
                                                vp]),
         "krp_block_hankel_sketch": (C.c_int, [vp, vp, C.c_int, C.c_int, C.c_int, C.c_int, vp,
                                               vp, C.c_int, vp, vp, C.c_int, vp, vp]),
+        "krp_tucker_rhosvd_batched": (C.c_int, [vp, C.c_int, C.c_int, C.POINTER(TuckerItem),
+                                                C.c_int, C.c_uint]),
+        "krp_tucker_batch_plan_info": (C.c_int, [vp, C.POINTER(C.c_int), C.POINTER(C.c_int),
+                                                 C.POINTER(C.c_int)]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -306,3 +322,34 @@ def krp_block_hankel_sketch(ctx: Context, blocks, m, n, s, omega1, omega2, ell_r
     ctx.check(ctx.lib.krp_block_hankel_sketch(ctx.handle, _ptr(blocks), _dtype_code(blocks), m,
                                               n, s, _ptr(omega1), _ptr(omega2), ell_r, _ptr(psi1),
                                               _ptr(psi2), ell_l, _ptr(Y), _ptr(Z)))
+
+
+def make_tucker_items(xs, dims, ranks, seeds, cores, factors):
+    """Array of krp_tucker_item from per-tensor lists (kept by the caller so
+    that a repeated call can pass the same descriptors)."""
+    n = len(xs)
+    arr = (TuckerItem * n)()
+    for b in range(n):
+        it = arr[b]
+        it.X = _ptr(xs[b])
+        for m in range(3):
+            it.dims[m] = int(dims[b][m])
+            it.ranks[m] = int(ranks[b][m])
+            it.factors[m] = _ptr(factors[b][m])
+        it.seed = int(seeds[b])
+        it.core = _ptr(cores[b])
+        it.rel_residual = 0.0
+    return arr
+
+
+def krp_tucker_rhosvd_batched(ctx: Context, xt: int, items, oversample: int, flags: int):
+    """Batched RHOSVD-KRP-MEMO of 3-way tensors; fills items[b].rel_residual."""
+    ctx.check(ctx.lib.krp_tucker_rhosvd_batched(ctx.handle, int(xt), len(items), items,
+                                                int(oversample), int(flags)))
+    return [items[b].rel_residual for b in range(len(items))]
+
+
+def krp_tucker_batch_plan_info(ctx: Context):
+    a, b, c = C.c_int(0), C.c_int(0), C.c_int(0)
+    ctx.check(ctx.lib.krp_tucker_batch_plan_info(ctx.handle, C.byref(a), C.byref(b), C.byref(c)))
+    return {"slabs_per_tile": a.value, "tiles": b.value, "grid": c.value}

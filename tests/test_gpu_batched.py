@@ -1,0 +1,136 @@
+"""a11: the batched uneven Tucker path against the FP64 oracle, per tensor.
+
+Each tensor b of a batch is RHOSVD-KRP-MEMO with its own Philox key seed_b, so
+the oracle's rhosvd_krp(X_b, l, seed_b, memo=True) (+ truncation) is the
+reference: FP32 form within 1e-5 (reconstruction relative to ||X_b||); error
+values within 1e-5 relative plus 1e-6: the factors enter the reconstruction
+in FP32, Q~_i = Q_i + E_i with ||E_i||_F ~ 2^-24 sqrt(l_i), so the residual
+differs from the residual R of the exact projection by first-order terms
+<R, E_i Q_i^T X_(i)> (one per mode; the core's own rounding only acts at
+second order since R is orthogonal to the projection's range).  Each shifts
+the relative error value by at most about 2^-24 sqrt(l) <= 3.4e-7 for
+l <= 32, so three modes give the 1e-6 absolute term.  BF16 form (X and factors rounded to BF16, FP32 arithmetic
+on CUDA cores): the same bounds on the BF16-rounded data.  Also: a repeated call
+replays the captured graph with identical results, and new descriptors build
+a new plan.
+"""
+
+import numpy as np
+import pytest
+
+from tests.gpu_util import require_gpu, dev, tensor_to_dev
+from oracle import philox, tucker as TK
+from synth import TuckerSpec, tucker_tensor
+
+pytestmark = pytest.mark.gpu
+
+P = 4
+SHAPES = [((40, 33, 27), (3, 4, 2)), ((5, 7, 9), (1, 2, 2)), ((64, 16, 48), (6, 5, 8)),
+          ((31, 90, 12), (4, 4, 4)), ((96, 40, 70), (8, 3, 6)), ((17, 17, 17), (2, 2, 3)),
+          ((128, 50, 33), (12, 9, 16)), ((8, 200, 24), (4, 16, 10))]
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    require_gpu()
+    import paper_2507_23207_gb300 as K
+    c = K.Context(0)
+    yield c
+    c.close()
+
+
+def _batch(dtype, flags_trunc, shapes=SHAPES, seed0=500):
+    import torch
+    xs, hosts, dims, ranks, seeds, cores, facs = [], [], [], [], [], [], []
+    for b, (d, r) in enumerate(shapes):
+        spec = TuckerSpec(f"t{b}", d, tuple(min(n, rr + 2) for n, rr in zip(d, r)), 1e-3, None,
+                          77 + b, r, tuple(rr + P for rr in r))
+        x, _, _ = tucker_tensor(spec)
+        x = philox.round_to_bf16(x) if dtype == torch.bfloat16 else philox.round_to_f32(x)
+        hosts.append(x)
+        xs.append(tensor_to_dev(x, dtype))
+        dims.append(d)
+        ranks.append(r)
+        seeds.append(seed0 + b)
+        out = r if flags_trunc else tuple(rr + P for rr in r)
+        cores.append(torch.empty(int(np.prod(out)), dtype=torch.float32, device=dev()))
+        facs.append([torch.empty(n * o, dtype=torch.float64, device=dev()) for n, o in zip(d, out)])
+    return xs, hosts, dims, ranks, seeds, cores, facs
+
+
+def _check(hosts, ranks, seeds, cores, facs, rels, trunc, omega_round, tol):
+    for b, x in enumerate(hosts):
+        ells = [r + P for r in ranks[b]]
+        ora = TK.rhosvd_krp(x, ells, seeds[b], memo=True, omega_round=omega_round)
+        g, qs = ora["G"], ora["Q"]
+        if trunc:
+            g, qs = TK.truncate_core(g, qs, list(ranks[b]))
+        out = list(ranks[b]) if trunc else ells
+        gg = cores[b].cpu().numpy().astype(np.float64).reshape(out[::-1]).T
+        qq = [f.cpu().numpy().reshape(o, n).T for f, n, o in zip(facs[b], x.shape, out)]
+        nx = np.linalg.norm(x)
+        d = np.linalg.norm(TK.reconstruct(gg, qq) - TK.reconstruct(g, qs)) / nx
+        assert d <= tol, (b, x.shape, d)
+        e_ora = TK.rel_error(x, g, qs)
+        assert abs(rels[b] - e_ora) <= tol * e_ora + 1e-6, (b, rels[b], e_ora)
+        for q in qq:
+            assert np.linalg.norm(q.T @ q - np.eye(q.shape[1])) <= 1e-10
+
+
+@pytest.mark.parametrize("form", ["f32", "bf16"])
+@pytest.mark.parametrize("trunc", [True, False])
+def test_batched_matches_oracle(ctx, form, trunc):
+    import torch
+    import paper_2507_23207_gb300 as K
+    dtype = torch.float32 if form == "f32" else torch.bfloat16
+    xs, hosts, dims, ranks, seeds, cores, facs = _batch(dtype, trunc)
+    items = K.make_tucker_items(xs, dims, ranks, seeds, cores, facs)
+    flags = (K.KRP_TRUNCATE if trunc else 0) | K.KRP_RESIDUAL
+    rels = K.krp_tucker_rhosvd_batched(ctx, K.KRP_F32 if form == "f32" else K.KRP_BF16, items, P,
+                                       flags)
+    torch.cuda.synchronize()
+    _check(hosts, ranks, seeds, cores, facs, rels, trunc, form, 1e-5)
+
+
+def test_batched_graph_replay_and_rebuild(ctx):
+    import torch
+    import paper_2507_23207_gb300 as K
+    xs, hosts, dims, ranks, seeds, cores, facs = _batch(torch.float32, True)
+    items = K.make_tucker_items(xs, dims, ranks, seeds, cores, facs)
+    flags = K.KRP_TRUNCATE | K.KRP_RESIDUAL
+    r1 = K.krp_tucker_rhosvd_batched(ctx, K.KRP_F32, items, P, flags)
+    info = K.krp_tucker_batch_plan_info(ctx)
+    assert info["slabs_per_tile"] in (1, 2, 4, 8) and info["tiles"] >= len(SHAPES)
+    def recon(b):
+        out = list(ranks[b])
+        g = cores[b].cpu().numpy().astype(np.float64).reshape(out[::-1]).T
+        qs = [f.cpu().numpy().reshape(o, n).T for f, n, o in zip(facs[b], dims[b], out)]
+        return TK.reconstruct(g, qs)
+
+    x1 = [recon(b) for b in range(len(SHAPES))]
+    for c in cores:
+        c.zero_()
+    r2 = K.krp_tucker_rhosvd_batched(ctx, K.KRP_F32, items, P, flags)
+    assert K.krp_tucker_batch_plan_info(ctx) == info
+    # the replay recomputes everything (cores were cleared); atomics may sum in
+    # another order, so compare basis-invariant results
+    for b in range(len(SHAPES)):
+        assert np.linalg.norm(recon(b) - x1[b]) <= 1e-5 * np.linalg.norm(hosts[b])
+    assert np.allclose(r1, r2, rtol=1e-4)
+    # other seeds: a new plan, results follow the oracle for the new seeds
+    seeds2 = [s + 1000 for s in seeds]
+    items2 = K.make_tucker_items(xs, dims, ranks, seeds2, cores, facs)
+    rels = K.krp_tucker_rhosvd_batched(ctx, K.KRP_F32, items2, P, flags)
+    _check(hosts, ranks, seeds2, cores, facs, rels, True, "f32", 1e-5)
+
+
+def test_batched_rejects_bad_descriptors(ctx):
+    import torch
+    import paper_2507_23207_gb300 as K
+    xs, hosts, dims, ranks, seeds, cores, facs = _batch(torch.float32, True, SHAPES[:2])
+    bad = [list(r) for r in ranks]
+    bad[1][0] = dims[1][0]  # l = r + P > n
+    items = K.make_tucker_items(xs, dims, bad, seeds, cores, facs)
+    with pytest.raises(K.KrpError) as e:
+        K.krp_tucker_rhosvd_batched(ctx, K.KRP_F32, items, P, K.KRP_TRUNCATE)
+    assert e.value.status == K.KRP_EINVAL

@@ -190,6 +190,7 @@ def run_ours(args, rank, world, local_rank):
         torch.cuda.empty_cache()
         extra["tucker_200pow4"] = c3_run(ctx, dev, stream, args)
         extra["block_hankel_1024"] = c4_run(ctx, dev, stream, args)
+        extra["batched_512_tucker"] = batch_run(ctx, dev, stream, args)
     ctx.close()
     return spec, results, kr, e2e, peaks, peak_src, (sk, co, rs, qr), extra
 
@@ -265,6 +266,65 @@ def c3_run(ctx, dev, stream, args):
     out["bf16_error_over_f32"] = round(out["bf16"]["rel_error"] / out["f32"]["rel_error"], 5)
     out["bf16_speedup"] = round(out["f32"]["ms"] / out["bf16"]["ms"], 3)
     del xs
+    torch.cuda.empty_cache()
+    return out
+
+
+def batch_run(ctx, dev, stream, args):
+    """512 uneven 3-way tensors (sides 32..192, ranks 4..16, l = r + 8):
+    the batched path (one launch per phase, graph replay) in BF16 and FP32,
+    against a loop of single-tensor FP32 calls."""
+    import torch
+    import paper_2507_23207_gb300 as K
+    from synth import batch_tucker_specs
+    from synth.tucker import tucker_tensor_device
+    specs = batch_tucker_specs()
+    x32, xbf = [], []
+    for sp in specs:
+        x64, _, _ = tucker_tensor_device(sp, device=dev)
+        x32.append(x64.to(torch.float32))
+        xbf.append(x64.to(torch.bfloat16))
+        del x64
+    torch.cuda.empty_cache()
+    dims = [sp.dims for sp in specs]
+    ranks = [sp.ranks for sp in specs]
+    seeds = [sp.omega_seed for sp in specs]
+    cores = [torch.empty(int(np.prod(sp.ranks)), dtype=torch.float32, device=dev) for sp in specs]
+    facs = [[torch.empty(n * r, dtype=torch.float64, device=dev) for n, r in zip(sp.dims, sp.ranks)]
+            for sp in specs]
+    flags = K.KRP_MEMO | K.KRP_TRUNCATE | K.KRP_RESIDUAL
+    nelem = sum(sp.numel for sp in specs)
+    out = {"workload": f"{len(specs)} tensors, sides U(32..192), ranks U(4..16), noise 1e-5, "
+                       "l = r + 8, RHOSVD-KRP-MEMO + truncation + residual",
+           "elements": nelem}
+    reps = max(3, min(args.steps, 10))
+    for form, xs, xt in (("f32", x32, K.KRP_F32), ("bf16", xbf, K.KRP_BF16)):
+        items = K.make_tucker_items(xs, dims, ranks, seeds, cores, facs)
+        t0 = time.perf_counter()
+        rels = K.krp_tucker_rhosvd_batched(ctx, xt, items, 8, flags)  # plan, autotune, capture
+        plan_s = time.perf_counter() - t0
+        ms, rels = _timed(stream, lambda: K.krp_tucker_rhosvd_batched(ctx, xt, items, 8, flags),
+                          reps=reps, warm=2)
+        info = K.krp_tucker_batch_plan_info(ctx)
+        esz = xs[0].element_size()
+        out[form] = {"ms": round(ms, 3), "tensors_per_s": round(len(specs) / (ms * 1e-3), 1),
+                     "gbs": round(3.0 * nelem * esz / (ms * 1e-3) / 1e9, 1),
+                     "rel_error_mean": float(np.mean(rels)), "rel_error_max": float(np.max(rels)),
+                     "plan_s": round(plan_s, 3), "plan": info}
+    # baseline: a loop of single-tensor FP32 calls
+    def loop():
+        res = []
+        for b, sp in enumerate(specs):
+            r = K.krp_tucker_rhosvd(ctx, x32[b], sp.dims, list(sp.ranks), 8, sp.omega_seed, flags,
+                                    cores[b], facs[b])
+            res.append(r["rel_residual"])
+        return res
+    ms_loop, rl = _timed(stream, loop, reps=1, warm=1)
+    out["loop_f32_single_calls"] = {"ms": round(ms_loop, 3), "rel_error_mean": float(np.mean(rl)),
+                                    "rel_error_max": float(np.max(rl))}
+    out["speedup_bf16_batched_vs_loop"] = round(ms_loop / out["bf16"]["ms"], 2)
+    out["speedup_f32_batched_vs_loop"] = round(ms_loop / out["f32"]["ms"], 2)
+    del x32, xbf
     torch.cuda.empty_cache()
     return out
 

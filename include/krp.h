@@ -298,6 +298,28 @@ krp_status krp_tucker_rhosvd_batched(krp_ctx ctx, krp_dtype xt, int count,
                                      krp_tucker_item* items, int oversample,
                                      unsigned flags);
 
+/* One block Hankel matrix of a batch (device pointers), as for
+ * krp_block_hankel_lowrank: 2s-1 column-major m x n blocks, target rank r,
+ * sketch sizes ell_r, ell_l (0 = ceil(1.5 ell_r)), Philox key seed. */
+typedef struct krp_hankel_item {
+  const void* blocks;
+  int m, n, s, r, ell_r, ell_l;
+  uint64_t seed;
+  double* U;              /* out: m s x r */
+  double* S;              /* out: r */
+  double* V;              /* out: n s x r */
+} krp_hankel_item;
+
+/* Alg. 6 for `count` block Hankel matrices of different sizes, each phase one
+ * launch over the batch; item b computes what krp_block_hankel_lowrank
+ * computes for it alone.  As for krp_tucker_rhosvd_batched, the first call
+ * with given descriptors builds a plan and records a CUDA graph that later
+ * identical calls replay (ell_l = 0 is replaced in the descriptor by its
+ * value).  Needs ell_r <= 64.  Synchronises the stream.  The paper describes
+ * single matrices only; the batched form has no counterpart there. */
+krp_status krp_block_hankel_batched(krp_ctx ctx, krp_dtype bt, int count,
+                                    krp_hankel_item* items);
+
 /* Work-tile choice of the context's current batch plan (slabs per tile,
  * number of tiles, persistent grid size); KRP_EINVAL if there is none. */
 krp_status krp_tucker_batch_plan_info(krp_ctx ctx, int* slabs_per_tile,

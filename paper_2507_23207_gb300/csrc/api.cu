@@ -159,6 +159,8 @@ krp_status krp_destroy(krp_ctx ctx) {
     KRP_CUDA_CHECK(cudaStreamSynchronize(ctx->c.stream));
     if (ctx->c.batch_plan) ctx->c.batch_plan_free(ctx->c.batch_plan);
     ctx->c.batch_plan = nullptr;
+    if (ctx->c.hankel_plan) ctx->c.hankel_plan_free(ctx->c.hankel_plan);
+    ctx->c.hankel_plan = nullptr;
     if (ctx->c.ws.base) KRP_CUDA_CHECK(cudaFree(ctx->c.ws.base));
     if (ctx->c.d_status) KRP_CUDA_CHECK(cudaFree(ctx->c.d_status));
     ctx->c.ws.base = nullptr;
@@ -297,6 +299,10 @@ krp_status krp_tucker_sthosvd(krp_ctx ctx, const void* X, krp_dtype xt, int d,
 krp_status krp_tucker_rhosvd_batched(krp_ctx ctx, krp_dtype xt, int count, krp_tucker_item* items,
                                      int oversample, unsigned flags) {
   return guarded(ctx, [&] { tucker_batched(xt, count, items, oversample, flags); });
+}
+
+krp_status krp_block_hankel_batched(krp_ctx ctx, krp_dtype bt, int count, krp_hankel_item* items) {
+  return guarded(ctx, [&] { hankel_batched(bt, count, items); });
 }
 
 krp_status krp_tucker_batch_plan_info(krp_ctx ctx, int* slabs_per_tile, int* tiles, int* grid) {

@@ -24,6 +24,7 @@
 // FP32 accumulation (the slabs are too small and too unevenly shaped for
 // 128-row tensor-core tiles); X may be FP32 or BF16.
 #include <algorithm>
+#include <cmath>
 #include <cstring>
 #include <memory>
 #include <vector>
@@ -58,6 +59,7 @@ struct TbItem {
   float* core_out;   // r1 r2 r3
   double* fac_out[3];
   double* acc;       // ||X - X_hat||^2, ||X||^2
+  float* M;          // n3 x (r1 r2): the slab matrices of the residual
 };
 
 struct TbTile {
@@ -73,18 +75,68 @@ __device__ __forceinline__ float ldx<__nv_bfloat16>(const __nv_bfloat16* p, int6
   return __bfloat162float(p[i]);
 }
 
-// Stage columns j0 .. j0+kJB-1 of slab t (rows 0..fill-1, zero outside the
-// slab) into Xs[jl][i], pitch `pitch`; warp w copies rows jl = w, w+8, ...
-template <class XT>
-__device__ void stage_chunk(const XT* X, int n1, int n2, int t, int j0, int fill, float* Xs,
-                            int pitch) {
+// A chunk of columns j0 .. j0+kJB-1 of slab t, moved through registers so
+// that all of a thread's loads are in flight together (and the next chunk's
+// while the current one is multiplied): warp w holds rows jl = w + 8p of the
+// chunk, lane l holds entries i = l + 32u (u < R = ceil(n1 / 32)); zero
+// outside the slab.
+template <int R>
+struct ChunkRegs {
+  float v[kJB / 8][R];
+};
+
+template <class XT, int R>
+__device__ __forceinline__ void chunk_load(ChunkRegs<R>& r, const XT* X, int n1, int n2, int t,
+                                           int j0) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  for (int jl = warp; jl < kJB; jl += kBT / 32) {
-    const int j = j0 + jl;
+#pragma unroll
+  for (int p = 0; p < kJB / 8; ++p) {
+    const int j = j0 + warp + 8 * p;
     const bool jok = j < n2;
     const int64_t base = (int64_t)n1 * (j + (int64_t)n2 * t);
-    for (int i = lane; i < fill; i += 32) Xs[jl * pitch + i] = (jok && i < n1) ? ldx(X, base + i) : 0.f;
+#pragma unroll
+    for (int u = 0; u < R; ++u) {
+      const int i = lane + 32 * u;
+      r.v[p][u] = (jok && i < n1) ? ldx(X, base + i) : 0.f;
+    }
   }
+}
+
+template <int R>
+__device__ __forceinline__ void chunk_store(const ChunkRegs<R>& r, float* Xs, int pitch) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+#pragma unroll
+  for (int p = 0; p < kJB / 8; ++p)
+#pragma unroll
+    for (int u = 0; u < R; ++u) Xs[(warp + 8 * p) * pitch + lane + 32 * u] = r.v[p][u];
+}
+
+// sum_i Xs[row][i] W[i][4kg..4kg+3] over i < n1p8, with two partial sums per
+// output (even and odd groups of four i) for instruction-level parallelism;
+// W rows n1..n1p8-1 and Xs entries beyond n1 are zero.
+__device__ __forceinline__ float4 row_dot4(const float* Xrow, const float* W, int Lp, int kg,
+                                           int n1p8) {
+  float e0 = 0.f, e1 = 0.f, e2 = 0.f, e3 = 0.f, o0 = 0.f, o1 = 0.f, o2 = 0.f, o3 = 0.f;
+  for (int i = 0; i < n1p8; i += 8) {
+    const float4 xa = *reinterpret_cast<const float4*>(&Xrow[i]);
+    const float4 xb = *reinterpret_cast<const float4*>(&Xrow[i + 4]);
+    const float xva[4] = {xa.x, xa.y, xa.z, xa.w};
+    const float xvb[4] = {xb.x, xb.y, xb.z, xb.w};
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const float4 wa = *reinterpret_cast<const float4*>(&W[(i + q) * Lp + 4 * kg]);
+      const float4 wb = *reinterpret_cast<const float4*>(&W[(i + 4 + q) * Lp + 4 * kg]);
+      e0 = fmaf(xva[q], wa.x, e0);
+      e1 = fmaf(xva[q], wa.y, e1);
+      e2 = fmaf(xva[q], wa.z, e2);
+      e3 = fmaf(xva[q], wa.w, e3);
+      o0 = fmaf(xvb[q], wb.x, o0);
+      o1 = fmaf(xvb[q], wb.y, o1);
+      o2 = fmaf(xvb[q], wb.z, o2);
+      o3 = fmaf(xvb[q], wb.w, o3);
+    }
+  }
+  return make_float4(e0 + o0, e1 + o1, e2 + o2, e3 + o3);
 }
 
 __device__ int next_tile(int* counter, int* s_tile) {
@@ -95,110 +147,92 @@ __device__ int next_tile(int* counter, int* s_tile) {
 }
 
 // ---------------------------------------------------------------- sketch ----
-// Shared memory (floats): Xs[kJB][pitch], O1s[n1max4][Lp], O2s[n2max][Lp],
+// Shared memory (floats): Xs[kJB][pitch], O1s[n1max8][Lp], O2s[n2max][Lp],
 // Y2p[n2max][Lp], o3s[Lp], y3s[Lp].
-template <class XT>
-__global__ void __launch_bounds__(kBT, 2)
-    batch_sketch_kernel(const TbItem* __restrict__ items, const TbTile* __restrict__ tiles,
-                        int ntiles, int* counter, int pitch, int Lp, int n1max4, int n2max) {
-  extern __shared__ __align__(16) float bsm[];
-  float* Xs = bsm;
-  float* O1s = Xs + kJB * pitch;
-  float* O2s = O1s + n1max4 * Lp;
-  float* Y2p = O2s + n2max * Lp;
-  float* o3s = Y2p + n2max * Lp;
-  float* y3s = o3s + Lp;
-  __shared__ int s_tile;
+struct SketchSmem {
+  float *Xs, *O1s, *O2s, *Y2p, *o3s, *y3s;
+  int pitch, Lp;
+};
+
+template <class XT, int R>
+__device__ void sketch_tile(const TbItem& it, const TbTile& tile, const SketchSmem& S) {
   const int tid = threadIdx.x, ig = tid >> 3, kg = tid & 7;
-  for (;;) {
-    const int ti = next_tile(counter, &s_tile);
-    if (ti >= ntiles) break;
-    const TbTile tile = tiles[ti];
-    const TbItem& it = items[tile.item];
-    const int n1 = it.n[0], n2 = it.n[1], n3 = it.n[2], lm = it.lm;
-    const int n1p4 = (n1 + 3) & ~3;
-    const int rpt = (n1 + 31) >> 5;
-    const XT* X = static_cast<const XT*>(it.X);
-    for (int e = tid; e < n1p4 * Lp; e += kBT) {
-      const int i = e / Lp, k = e % Lp;
-      O1s[e] = (i < n1 && k < lm) ? it.om[0][i + (int64_t)n1 * k] : 0.f;
-    }
-    for (int e = tid; e < n2 * Lp; e += kBT) {
-      const int j = e / Lp, k = e % Lp;
-      O2s[e] = k < lm ? it.om[1][j + (int64_t)n2 * k] : 0.f;
-      Y2p[e] = 0.f;
-    }
-    float y1[kRPT][4];
+  const int n1 = it.n[0], n2 = it.n[1], n3 = it.n[2], lm = it.lm;
+  const int pitch = S.pitch, Lp = S.Lp;
+  const int n1p8 = (n1 + 7) & ~7;
+  const XT* X = static_cast<const XT*>(it.X);
+  // factors are column-major: consecutive threads read consecutive rows
+  for (int e = tid; e < n1p8 * Lp; e += kBT) {
+    const int i = e % n1p8, k = e / n1p8;
+    S.O1s[i * Lp + k] = (i < n1 && k < lm) ? it.om[0][i + (int64_t)n1 * k] : 0.f;
+  }
+  for (int e = tid; e < n2 * Lp; e += kBT) {
+    const int j = e % n2, k = e / n2;
+    S.O2s[j * Lp + k] = k < lm ? it.om[1][j + (int64_t)n2 * k] : 0.f;
+    S.Y2p[j * Lp + k] = 0.f;
+  }
+  float y1[R][4];
 #pragma unroll
-    for (int u = 0; u < kRPT; ++u)
+  for (int u = 0; u < R; ++u)
 #pragma unroll
-      for (int c = 0; c < 4; ++c) y1[u][c] = 0.f;
-    const bool kact = 4 * kg < Lp;
-    for (int t = tile.t0; t < tile.t1; ++t) {
+    for (int c = 0; c < 4; ++c) y1[u][c] = 0.f;
+  const bool kact = 4 * kg < Lp;
+  const int nch = (n2 + kJB - 1) / kJB;
+  const int nq = (tile.t1 - tile.t0) * nch;
+  ChunkRegs<R> cr;
+  chunk_load<XT, R>(cr, X, n1, n2, tile.t0, 0);
+  float a[R][4];
+  for (int q = 0; q < nq; ++q) {
+    const int t = tile.t0 + q / nch, ch = q % nch, j0 = ch * kJB;
+    __syncthreads();  // previous chunk and slab epilogue consumed
+    if (ch == 0) {
       if (tid < Lp) {
-        o3s[tid] = tid < lm ? it.om[2][t + (int64_t)n3 * tid] : 0.f;
-        y3s[tid] = 0.f;
+        S.o3s[tid] = tid < lm ? it.om[2][t + (int64_t)n3 * tid] : 0.f;
+        S.y3s[tid] = 0.f;
       }
-      float a[kRPT][4];
 #pragma unroll
-      for (int u = 0; u < kRPT; ++u)
+      for (int u = 0; u < R; ++u)
 #pragma unroll
         for (int c = 0; c < 4; ++c) a[u][c] = 0.f;
-      for (int j0 = 0; j0 < n2; j0 += kJB) {
-        __syncthreads();  // previous chunk consumed
-        stage_chunk<XT>(X, n1, n2, t, j0, 32 * rpt, Xs, pitch);
-        __syncthreads();
-        const int jn = min(kJB, n2 - j0);
-        if (kact) {
-          // A_t rows ig + 32u, columns 4kg..4kg+3
-          for (int jl = 0; jl < jn; ++jl) {
-            const float4 w = *reinterpret_cast<const float4*>(&O2s[(j0 + jl) * Lp + 4 * kg]);
+    }
+    chunk_store<R>(cr, S.Xs, pitch);
+    __syncthreads();
+    if (q + 1 < nq) chunk_load<XT, R>(cr, X, n1, n2, tile.t0 + (q + 1) / nch, ((q + 1) % nch) * kJB);
+    const int jn = min(kJB, n2 - j0);
+    if (kact) {
+      // A_t rows ig + 32u, columns 4kg..4kg+3
+      for (int jl = 0; jl < jn; ++jl) {
+        const float4 w = *reinterpret_cast<const float4*>(&S.O2s[(j0 + jl) * Lp + 4 * kg]);
 #pragma unroll
-            for (int u = 0; u < kRPT; ++u) {
-              if (u < rpt) {
-                const float x = Xs[jl * pitch + ig + 32 * u];
-                a[u][0] = fmaf(x, w.x, a[u][0]);
-                a[u][1] = fmaf(x, w.y, a[u][1]);
-                a[u][2] = fmaf(x, w.z, a[u][2]);
-                a[u][3] = fmaf(x, w.w, a[u][3]);
-              }
-            }
-          }
-          // B_t row j0 + ig (ig doubles as the chunk column here)
-          if (ig < jn) {
-            float b0 = 0.f, b1 = 0.f, b2 = 0.f, b3 = 0.f;
-            for (int i = 0; i < n1p4; i += 4) {
-              const float4 x = *reinterpret_cast<const float4*>(&Xs[ig * pitch + i]);
-              const float xv[4] = {x.x, x.y, x.z, x.w};
-#pragma unroll
-              for (int q = 0; q < 4; ++q) {
-                const float4 w = *reinterpret_cast<const float4*>(&O1s[(i + q) * Lp + 4 * kg]);
-                b0 = fmaf(xv[q], w.x, b0);
-                b1 = fmaf(xv[q], w.y, b1);
-                b2 = fmaf(xv[q], w.z, b2);
-                b3 = fmaf(xv[q], w.w, b3);
-              }
-            }
-            float* yp = &Y2p[(j0 + ig) * Lp + 4 * kg];
-            yp[0] = fmaf(b0, o3s[4 * kg + 0], yp[0]);
-            yp[1] = fmaf(b1, o3s[4 * kg + 1], yp[1]);
-            yp[2] = fmaf(b2, o3s[4 * kg + 2], yp[2]);
-            yp[3] = fmaf(b3, o3s[4 * kg + 3], yp[3]);
-          }
+        for (int u = 0; u < R; ++u) {
+          const float x = S.Xs[jl * pitch + ig + 32 * u];
+          a[u][0] = fmaf(x, w.x, a[u][0]);
+          a[u][1] = fmaf(x, w.y, a[u][1]);
+          a[u][2] = fmaf(x, w.z, a[u][2]);
+          a[u][3] = fmaf(x, w.w, a[u][3]);
         }
       }
+      // B_t row j0 + ig (ig doubles as the chunk column here)
+      if (ig < jn) {
+        const float4 bb = row_dot4(&S.Xs[ig * pitch], S.O1s, Lp, kg, n1p8);
+        float* yp = &S.Y2p[(j0 + ig) * Lp + 4 * kg];
+        yp[0] = fmaf(bb.x, S.o3s[4 * kg + 0], yp[0]);
+        yp[1] = fmaf(bb.y, S.o3s[4 * kg + 1], yp[1]);
+        yp[2] = fmaf(bb.z, S.o3s[4 * kg + 2], yp[2]);
+        yp[3] = fmaf(bb.w, S.o3s[4 * kg + 3], yp[3]);
+      }
+    }
+    if (ch == nch - 1) {
       // slab t done: Y1 partial and Y3[t, :]
       float p[4] = {0.f, 0.f, 0.f, 0.f};
       if (kact) {
 #pragma unroll
-        for (int u = 0; u < kRPT; ++u) {
-          if (u < rpt) {
-            const int i = ig + 32 * u;
+        for (int u = 0; u < R; ++u) {
+          const int i = ig + 32 * u;
 #pragma unroll
-            for (int c = 0; c < 4; ++c) {
-              y1[u][c] = fmaf(a[u][c], o3s[4 * kg + c], y1[u][c]);
-              if (i < n1) p[c] = fmaf(O1s[i * Lp + 4 * kg + c], a[u][c], p[c]);
-            }
+          for (int c = 0; c < 4; ++c) {
+            y1[u][c] = fmaf(a[u][c], S.o3s[4 * kg + c], y1[u][c]);
+            if (i < n1) p[c] = fmaf(S.O1s[i * Lp + 4 * kg + c], a[u][c], p[c]);
           }
         }
       }
@@ -209,111 +243,152 @@ __global__ void __launch_bounds__(kBT, 2)
       }
       if ((tid & 31) < 8 && kact) {
 #pragma unroll
-        for (int c = 0; c < 4; ++c) atomicAdd(&y3s[4 * kg + c], p[c]);
+        for (int c = 0; c < 4; ++c) atomicAdd(&S.y3s[4 * kg + c], p[c]);
       }
       __syncthreads();
-      if (tid < lm) it.Y[2][t + (int64_t)n3 * tid] = y3s[tid];
+      if (tid < lm) it.Y[2][t + (int64_t)n3 * tid] = S.y3s[tid];
     }
-    if (kact) {
+  }
+  // flush the tile's partial Y2 and Y1 with row-contiguous (coalesced) atomics;
+  // Y1 goes through shared memory (the Xs staging area, free by now)
+  __syncthreads();
+  for (int e = tid; e < n2 * lm; e += kBT) {
+    const int j = e % n2, k = e / n2;
+    atomicAdd(&it.Y[1][j + (int64_t)n2 * k], S.Y2p[j * Lp + k]);
+  }
+  float* Y1p = S.Xs;  // [k][i], n1 x Lp <= kJB * pitch floats
+  if (kact) {
 #pragma unroll
-      for (int u = 0; u < kRPT; ++u) {
-        const int i = ig + 32 * u;
-        if (u < rpt && i < n1) {
+    for (int u = 0; u < R; ++u) {
+      const int i = ig + 32 * u;
+      if (i < n1) {
 #pragma unroll
-          for (int c = 0; c < 4; ++c) {
-            const int k = 4 * kg + c;
-            if (k < lm) atomicAdd(&it.Y[0][i + (int64_t)n1 * k], y1[u][c]);
-          }
-        }
+        for (int c = 0; c < 4; ++c) Y1p[(4 * kg + c) * n1 + i] = y1[u][c];
       }
     }
-    __syncthreads();
-    for (int e = tid; e < n2 * Lp; e += kBT) {
-      const int j = e / Lp, k = e % Lp;
-      if (k < lm) atomicAdd(&it.Y[1][j + (int64_t)n2 * k], Y2p[e]);
+  }
+  __syncthreads();
+  for (int e = tid; e < n1 * lm; e += kBT) atomicAdd(&it.Y[0][e], Y1p[e]);
+}
+
+template <class XT>
+__global__ void __launch_bounds__(kBT, 2)
+    batch_sketch_kernel(const TbItem* __restrict__ items, const TbTile* __restrict__ tiles,
+                        int ntiles, int* counter, int pitch, int Lp, int n1max8, int n2max) {
+  extern __shared__ __align__(16) float bsm[];
+  SketchSmem S;
+  S.Xs = bsm;
+  S.O1s = S.Xs + kJB * pitch;
+  S.O2s = S.O1s + n1max8 * Lp;
+  S.Y2p = S.O2s + n2max * Lp;
+  S.o3s = S.Y2p + n2max * Lp;
+  S.y3s = S.o3s + Lp;
+  S.pitch = pitch;
+  S.Lp = Lp;
+  __shared__ int s_tile;
+  for (;;) {
+    const int ti = next_tile(counter, &s_tile);
+    if (ti >= ntiles) break;
+    const TbTile tile = tiles[ti];
+    const TbItem& it = items[tile.item];
+    switch ((it.n[0] + 31) >> 5) {  // uniform over the CTA
+      case 1: sketch_tile<XT, 1>(it, tile, S); break;
+      case 2: sketch_tile<XT, 2>(it, tile, S); break;
+      case 3: sketch_tile<XT, 3>(it, tile, S); break;
+      case 4: sketch_tile<XT, 4>(it, tile, S); break;
+      case 5: sketch_tile<XT, 5>(it, tile, S); break;
+      case 6: sketch_tile<XT, 6>(it, tile, S); break;
+      case 7: sketch_tile<XT, 7>(it, tile, S); break;
+      default: sketch_tile<XT, 8>(it, tile, S); break;
     }
   }
 }
 
 // ------------------------------------------------------------------ core ----
 // C_t = Q1^T X_t Q2 (l1 x l2) for every slab of the tile.  Shared memory
-// (floats): Xs[kJB][pitch], Q1s[n1max4][Lp], Q2s[n2max][Lp], Ts[kJB][Lp].
+// (floats): Xs[kJB][pitch], Q1s[n1max8][Lp], Q2s[n2max][Lp], Ts[kJB][Lp].
+template <class XT, int R>
+__device__ void core_tile(const TbItem& it, const TbTile& tile, float* Xs, float* Q1s, float* Q2s,
+                          float* Ts, int pitch, int Lp) {
+  const int tid = threadIdx.x, hi = tid >> 3, kg = tid & 7;
+  const int n1 = it.n[0], n2 = it.n[1], l1 = it.l[0], l2 = it.l[1];
+  const int n1p8 = (n1 + 7) & ~7;
+  const XT* X = static_cast<const XT*>(it.X);
+  for (int e = tid; e < n1p8 * Lp; e += kBT) {
+    const int i = e % n1p8, a = e / n1p8;
+    Q1s[i * Lp + a] = (i < n1 && a < l1) ? (float)it.Q[0][i + (int64_t)n1 * a] : 0.f;
+  }
+  for (int e = tid; e < n2 * Lp; e += kBT) {
+    const int j = e % n2, b = e / n2;
+    Q2s[j * Lp + b] = b < l2 ? (float)it.Q[1][j + (int64_t)n2 * b] : 0.f;
+  }
+  const bool kact = 4 * kg < Lp;
+  const int nch = (n2 + kJB - 1) / kJB;
+  const int nq = (tile.t1 - tile.t0) * nch;
+  ChunkRegs<R> cr;
+  chunk_load<XT, R>(cr, X, n1, n2, tile.t0, 0);
+  // thread (a = hi, b = 4kg..4kg+3) of C_t
+  float cacc[4];
+  for (int q = 0; q < nq; ++q) {
+    const int t = tile.t0 + q / nch, ch = q % nch, j0 = ch * kJB;
+    if (ch == 0) cacc[0] = cacc[1] = cacc[2] = cacc[3] = 0.f;
+    __syncthreads();
+    chunk_store<R>(cr, Xs, pitch);
+    __syncthreads();
+    if (q + 1 < nq) chunk_load<XT, R>(cr, X, n1, n2, tile.t0 + (q + 1) / nch, ((q + 1) % nch) * kJB);
+    const int jn = min(kJB, n2 - j0);
+    // Ts[jl][a] = sum_i Xs[jl][i] Q1s[i][a]: thread (jl = hi, a = 4kg..)
+    if (kact) {
+      const float4 tv = hi < jn ? row_dot4(&Xs[hi * pitch], Q1s, Lp, kg, n1p8)
+                                : make_float4(0.f, 0.f, 0.f, 0.f);
+      *reinterpret_cast<float4*>(&Ts[hi * Lp + 4 * kg]) = tv;
+    }
+    __syncthreads();
+    if (kact && hi < Lp) {
+      for (int jl = 0; jl < jn; ++jl) {
+        const float ta = Ts[jl * Lp + hi];
+        const float4 w = *reinterpret_cast<const float4*>(&Q2s[(j0 + jl) * Lp + 4 * kg]);
+        cacc[0] = fmaf(ta, w.x, cacc[0]);
+        cacc[1] = fmaf(ta, w.y, cacc[1]);
+        cacc[2] = fmaf(ta, w.z, cacc[2]);
+        cacc[3] = fmaf(ta, w.w, cacc[3]);
+      }
+    }
+    if (ch == nch - 1 && kact && hi < l1) {
+      float* Ct = it.C + (int64_t)t * l1 * l2;
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        const int b = 4 * kg + c;
+        if (b < l2) Ct[hi + l1 * b] = cacc[c];
+      }
+    }
+  }
+}
+
 template <class XT>
 __global__ void __launch_bounds__(kBT, 2)
     batch_core_kernel(const TbItem* __restrict__ items, const TbTile* __restrict__ tiles,
-                      int ntiles, int* counter, int pitch, int Lp, int n1max4, int n2max) {
+                      int ntiles, int* counter, int pitch, int Lp, int n1max8, int n2max) {
   extern __shared__ __align__(16) float bsm[];
   float* Xs = bsm;
   float* Q1s = Xs + kJB * pitch;
-  float* Q2s = Q1s + n1max4 * Lp;
+  float* Q2s = Q1s + n1max8 * Lp;
   float* Ts = Q2s + n2max * Lp;
   __shared__ int s_tile;
-  const int tid = threadIdx.x, hi = tid >> 3, kg = tid & 7;
   for (;;) {
     const int ti = next_tile(counter, &s_tile);
     if (ti >= ntiles) break;
     const TbTile tile = tiles[ti];
     const TbItem& it = items[tile.item];
-    const int n1 = it.n[0], n2 = it.n[1], l1 = it.l[0], l2 = it.l[1];
-    const int n1p4 = (n1 + 3) & ~3;
-    const int rpt = (n1 + 31) >> 5;
-    const XT* X = static_cast<const XT*>(it.X);
-    for (int e = tid; e < n1p4 * Lp; e += kBT) {
-      const int i = e / Lp, a = e % Lp;
-      Q1s[e] = (i < n1 && a < l1) ? (float)it.Q[0][i + (int64_t)n1 * a] : 0.f;
-    }
-    for (int e = tid; e < n2 * Lp; e += kBT) {
-      const int j = e / Lp, b = e % Lp;
-      Q2s[e] = b < l2 ? (float)it.Q[1][j + (int64_t)n2 * b] : 0.f;
-    }
-    const bool kact = 4 * kg < Lp;
-    for (int t = tile.t0; t < tile.t1; ++t) {
-      // thread (a = hi, b = 4kg..4kg+3) of C_t
-      float cacc[4] = {0.f, 0.f, 0.f, 0.f};
-      for (int j0 = 0; j0 < n2; j0 += kJB) {
-        __syncthreads();
-        stage_chunk<XT>(X, n1, n2, t, j0, 32 * rpt, Xs, pitch);
-        __syncthreads();
-        const int jn = min(kJB, n2 - j0);
-        // Ts[jl][a] = sum_i Xs[jl][i] Q1s[i][a]: thread (jl = hi, a = 4kg..)
-        if (kact) {
-          float t0 = 0.f, t1 = 0.f, t2 = 0.f, t3 = 0.f;
-          if (hi < jn) {
-            for (int i = 0; i < n1p4; i += 4) {
-              const float4 x = *reinterpret_cast<const float4*>(&Xs[hi * pitch + i]);
-              const float xv[4] = {x.x, x.y, x.z, x.w};
-#pragma unroll
-              for (int q = 0; q < 4; ++q) {
-                const float4 w = *reinterpret_cast<const float4*>(&Q1s[(i + q) * Lp + 4 * kg]);
-                t0 = fmaf(xv[q], w.x, t0);
-                t1 = fmaf(xv[q], w.y, t1);
-                t2 = fmaf(xv[q], w.z, t2);
-                t3 = fmaf(xv[q], w.w, t3);
-              }
-            }
-          }
-          *reinterpret_cast<float4*>(&Ts[hi * Lp + 4 * kg]) = make_float4(t0, t1, t2, t3);
-        }
-        __syncthreads();
-        if (kact && hi < Lp) {
-          for (int jl = 0; jl < jn; ++jl) {
-            const float ta = Ts[jl * Lp + hi];
-            const float4 w = *reinterpret_cast<const float4*>(&Q2s[(j0 + jl) * Lp + 4 * kg]);
-            cacc[0] = fmaf(ta, w.x, cacc[0]);
-            cacc[1] = fmaf(ta, w.y, cacc[1]);
-            cacc[2] = fmaf(ta, w.z, cacc[2]);
-            cacc[3] = fmaf(ta, w.w, cacc[3]);
-          }
-        }
-      }
-      if (kact && hi < l1) {
-        float* Ct = it.C + (int64_t)t * l1 * l2;
-#pragma unroll
-        for (int c = 0; c < 4; ++c) {
-          const int b = 4 * kg + c;
-          if (b < l2) Ct[hi + l1 * b] = cacc[c];
-        }
-      }
+    switch ((it.n[0] + 31) >> 5) {
+      case 1: core_tile<XT, 1>(it, tile, Xs, Q1s, Q2s, Ts, pitch, Lp); break;
+      case 2: core_tile<XT, 2>(it, tile, Xs, Q1s, Q2s, Ts, pitch, Lp); break;
+      case 3: core_tile<XT, 3>(it, tile, Xs, Q1s, Q2s, Ts, pitch, Lp); break;
+      case 4: core_tile<XT, 4>(it, tile, Xs, Q1s, Q2s, Ts, pitch, Lp); break;
+      case 5: core_tile<XT, 5>(it, tile, Xs, Q1s, Q2s, Ts, pitch, Lp); break;
+      case 6: core_tile<XT, 6>(it, tile, Xs, Q1s, Q2s, Ts, pitch, Lp); break;
+      case 7: core_tile<XT, 7>(it, tile, Xs, Q1s, Q2s, Ts, pitch, Lp); break;
+      default: core_tile<XT, 8>(it, tile, Xs, Q1s, Q2s, Ts, pitch, Lp); break;
     }
   }
 }
@@ -410,81 +485,139 @@ __global__ void batch_trunc_apply_kernel(const TbItem* __restrict__ items, int t
 }
 
 // -------------------------------------------------------------- residual ----
-// ||X_t - F1 M_t F2^T||^2 with M_t = sum_c Gt(:,:,c) F3[t,c].  Shared memory
-// (floats): Xs[kJB][pitch], F1s[n1max][Rp], F2s[Rp][n2max], Ms[Rp][Rp],
-// Ps[Rp][n1max].
+// M_t[a + r0 b] = sum_c Gt[a + r0 b + r0 r1 c] F3[t, c] for every slab t of a
+// tensor (one CTA per tensor), so the residual kernel reads each M_t as one
+// contiguous block.
+__global__ void batch_resid_prep_kernel(const TbItem* __restrict__ items) {
+  const TbItem& it = items[blockIdx.x];
+  const int r01 = it.r[0] * it.r[1], r2 = it.r[2], n3 = it.n[2];
+  for (int e = threadIdx.x; e < n3 * r01; e += blockDim.x) {
+    const int t = e / r01, ab = e % r01;
+    float s = 0.f;
+    for (int c = 0; c < r2; ++c)
+      s = fmaf(it.core_out[ab + r01 * c], (float)it.fac_out[2][t + (int64_t)n3 * c], s);
+    it.M[e] = s;
+  }
+}
+
+// ||X_t - F1 M_t F2^T||^2.  Shared memory (floats): Xs[kJB][pitch],
+// F1s[n1max][Rp], F2s[Rp][n2max], Ms[Rp * Rp], Ps[Rp][n1max].
+struct ResidSmem {
+  float *Xs, *F1s, *F2s, *Ms, *Ps;
+  int pitch, Rp, n1max, n2max;
+};
+
+template <class XT, int R>
+__device__ void resid_tile(const TbItem& it, const TbTile& tile, const ResidSmem& S, double& dd,
+                           double& xx) {
+  const int tid = threadIdx.x, ig = tid >> 3, jq = tid & 7;
+  const int n1 = it.n[0], n2 = it.n[1];
+  const int r0 = it.r[0], r1 = it.r[1];
+  const int pitch = S.pitch, Rp = S.Rp, n1max = S.n1max, n2max = S.n2max;
+  const XT* X = static_cast<const XT*>(it.X);
+  for (int e = tid; e < n1 * r0; e += kBT) {
+    const int i = e % n1, a = e / n1;
+    S.F1s[i * Rp + a] = (float)it.fac_out[0][e];
+  }
+  for (int e = tid; e < n2 * r1; e += kBT) {
+    const int j = e % n2, b = e / n2;
+    S.F2s[b * n2max + j] = (float)it.fac_out[1][e];
+  }
+  const int nch = (n2 + kJB - 1) / kJB;
+  const int nq = (tile.t1 - tile.t0) * nch;
+  ChunkRegs<R> cr;
+  chunk_load<XT, R>(cr, X, n1, n2, tile.t0, 0);
+  float d2 = 0.f, x2 = 0.f;
+  for (int q = 0; q < nq; ++q) {
+    const int t = tile.t0 + q / nch, ch = q % nch, j0 = ch * kJB;
+    __syncthreads();
+    if (ch == 0) {
+      const float* Mt = it.M + (int64_t)t * r0 * r1;
+      for (int e = tid; e < r0 * r1; e += kBT) S.Ms[e] = Mt[e];
+      __syncthreads();
+      for (int e = tid; e < n1 * r1; e += kBT) {
+        const int i = e % n1, b = e / n1;
+        float sm = 0.f;
+        for (int a = 0; a < r0; ++a) sm = fmaf(S.F1s[i * Rp + a], S.Ms[a + r0 * b], sm);
+        S.Ps[b * n1max + i] = sm;
+      }
+    }
+    chunk_store<R>(cr, S.Xs, pitch);
+    __syncthreads();
+    if (q + 1 < nq) chunk_load<XT, R>(cr, X, n1, n2, tile.t0 + (q + 1) / nch, ((q + 1) % nch) * kJB);
+    // X_hat rows ig + 32u, columns j0 + jq + 8w: register tile R x 4
+    float xh[R][kJB / 8];
+#pragma unroll
+    for (int u = 0; u < R; ++u)
+#pragma unroll
+      for (int w = 0; w < kJB / 8; ++w) xh[u][w] = 0.f;
+    for (int b = 0; b < r1; ++b) {
+      float pv[R], fv[kJB / 8];
+#pragma unroll
+      for (int u = 0; u < R; ++u) pv[u] = S.Ps[b * n1max + min(ig + 32 * u, n1max - 1)];
+#pragma unroll
+      for (int w = 0; w < kJB / 8; ++w) fv[w] = S.F2s[b * n2max + min(j0 + jq + 8 * w, n2max - 1)];
+#pragma unroll
+      for (int u = 0; u < R; ++u)
+#pragma unroll
+        for (int w = 0; w < kJB / 8; ++w) xh[u][w] = fmaf(pv[u], fv[w], xh[u][w]);
+    }
+#pragma unroll
+    for (int w = 0; w < kJB / 8; ++w) {
+      const int jl = jq + 8 * w;
+      if (j0 + jl >= n2) continue;
+#pragma unroll
+      for (int u = 0; u < R; ++u) {
+        const int i = ig + 32 * u;
+        if (i < n1) {
+          const float xv = S.Xs[jl * pitch + i];
+          const float df = xv - xh[u][w];
+          d2 = fmaf(df, df, d2);
+          x2 = fmaf(xv, xv, x2);
+        }
+      }
+    }
+    if (ch == nch - 1) {
+      dd += d2;
+      xx += x2;
+      d2 = x2 = 0.f;
+    }
+  }
+}
+
 template <class XT>
 __global__ void __launch_bounds__(kBT, 2)
     batch_resid_kernel(const TbItem* __restrict__ items, const TbTile* __restrict__ tiles,
                        int ntiles, int* counter, int pitch, int Rp, int n1max, int n2max) {
   extern __shared__ __align__(16) float bsm[];
-  float* Xs = bsm;
-  float* F1s = Xs + kJB * pitch;
-  float* F2s = F1s + n1max * Rp;
-  float* Ms = F2s + Rp * n2max;
-  float* Ps = Ms + Rp * Rp;
+  ResidSmem S;
+  S.Xs = bsm;
+  S.F1s = S.Xs + kJB * pitch;
+  S.F2s = S.F1s + n1max * Rp;
+  S.Ms = S.F2s + Rp * n2max;
+  S.Ps = S.Ms + Rp * Rp;
+  S.pitch = pitch;
+  S.Rp = Rp;
+  S.n1max = n1max;
+  S.n2max = n2max;
   __shared__ int s_tile;
   __shared__ double red[2][kBT / 32];
-  const int tid = threadIdx.x, ig = tid >> 3, jq = tid & 7;
+  const int tid = threadIdx.x;
   for (;;) {
     const int ti = next_tile(counter, &s_tile);
     if (ti >= ntiles) break;
     const TbTile tile = tiles[ti];
     const TbItem& it = items[tile.item];
-    const int n1 = it.n[0], n2 = it.n[1], n3 = it.n[2];
-    const int r0 = it.r[0], r1 = it.r[1], r2 = it.r[2];
-    const int n1p4 = (n1 + 3) & ~3;
-    const int rpt = (n1 + 31) >> 5;
-    const XT* X = static_cast<const XT*>(it.X);
-    for (int e = tid; e < n1 * r0; e += kBT) {
-      const int i = e % n1, a = e / n1;
-      F1s[i * Rp + a] = (float)it.fac_out[0][e];
-    }
-    for (int e = tid; e < n2 * r1; e += kBT) {
-      const int j = e % n2, b = e / n2;
-      F2s[b * n2max + j] = (float)it.fac_out[1][e];
-    }
     double dd = 0.0, xx = 0.0;
-    for (int t = tile.t0; t < tile.t1; ++t) {
-      __syncthreads();
-      for (int e = tid; e < r0 * r1; e += kBT) {
-        float s = 0.f;
-        for (int c = 0; c < r2; ++c)
-          s = fmaf(it.core_out[e + r0 * r1 * c], (float)it.fac_out[2][t + (int64_t)n3 * c], s);
-        Ms[e] = s;  // Ms[a + r0 b]
-      }
-      __syncthreads();
-      for (int e = tid; e < n1 * r1; e += kBT) {
-        const int i = e % n1, b = e / n1;
-        float s = 0.f;
-        for (int a = 0; a < r0; ++a) s = fmaf(F1s[i * Rp + a], Ms[a + r0 * b], s);
-        Ps[b * n1max + i] = s;
-      }
-      float d2 = 0.f, x2 = 0.f;
-      for (int j0 = 0; j0 < n2; j0 += kJB) {
-        __syncthreads();
-        stage_chunk<XT>(X, n1, n2, t, j0, 32 * rpt, Xs, pitch);
-        __syncthreads();
-#pragma unroll
-        for (int w = 0; w < kJB / 8; ++w) {
-          const int jl = jq + 8 * w, j = j0 + jl;
-          if (j >= n2) continue;
-#pragma unroll
-          for (int u = 0; u < kRPT; ++u) {
-            const int i = ig + 32 * u;
-            if (u < rpt && i < n1) {
-              float xh = 0.f;
-              for (int b = 0; b < r1; ++b) xh = fmaf(Ps[b * n1max + i], F2s[b * n2max + j], xh);
-              const float xv = Xs[jl * pitch + i];
-              const float df = xv - xh;
-              d2 = fmaf(df, df, d2);
-              x2 = fmaf(xv, xv, x2);
-            }
-          }
-        }
-      }
-      dd += d2;
-      xx += x2;
+    switch ((it.n[0] + 31) >> 5) {
+      case 1: resid_tile<XT, 1>(it, tile, S, dd, xx); break;
+      case 2: resid_tile<XT, 2>(it, tile, S, dd, xx); break;
+      case 3: resid_tile<XT, 3>(it, tile, S, dd, xx); break;
+      case 4: resid_tile<XT, 4>(it, tile, S, dd, xx); break;
+      case 5: resid_tile<XT, 5>(it, tile, S, dd, xx); break;
+      case 6: resid_tile<XT, 6>(it, tile, S, dd, xx); break;
+      case 7: resid_tile<XT, 7>(it, tile, S, dd, xx); break;
+      default: resid_tile<XT, 8>(it, tile, S, dd, xx); break;
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
@@ -546,7 +679,7 @@ struct TbPlan {
   float* y_begin = nullptr;
   size_t y_bytes = 0;
   double* acc_begin = nullptr;
-  int pitch = 0, Lp = 0, Rp = 0, n1max = 0, n1max4 = 0, n2max = 0, lmax = 0;
+  int pitch = 0, Lp = 0, Rp = 0, n1max = 0, n1max8 = 0, n2max = 0, lmax = 0;
   size_t sm_sketch = 0, sm_core = 0, sm_resid = 0, sm_gram = 0;
   int grid_persist = 0;
   int slabs_per_tile = 0;
@@ -600,10 +733,10 @@ void build_tiles(const std::vector<TbItem>& items, int spt, std::vector<TbTile>&
 void launch_sketch(const TbPlan& P) {
   if (P.xt == KRP_F32)
     batch_sketch_kernel<float><<<P.grid_persist, kBT, P.sm_sketch, stream()>>>(
-        P.d_items, P.d_tiles, P.ntiles, P.d_counters + 0, P.pitch, P.Lp, P.n1max4, P.n2max);
+        P.d_items, P.d_tiles, P.ntiles, P.d_counters + 0, P.pitch, P.Lp, P.n1max8, P.n2max);
   else
     batch_sketch_kernel<__nv_bfloat16><<<P.grid_persist, kBT, P.sm_sketch, stream()>>>(
-        P.d_items, P.d_tiles, P.ntiles, P.d_counters + 0, P.pitch, P.Lp, P.n1max4, P.n2max);
+        P.d_items, P.d_tiles, P.ntiles, P.d_counters + 0, P.pitch, P.Lp, P.n1max8, P.n2max);
   check_launch("batch_sketch");
 }
 
@@ -623,10 +756,10 @@ void enqueue_all(TbPlan& P, int* status) {
   ++nk;
   if (P.xt == KRP_F32)
     batch_core_kernel<float><<<P.grid_persist, kBT, P.sm_core, stream()>>>(
-        P.d_items, P.d_tiles, P.ntiles, P.d_counters + 1, P.pitch, P.Lp, P.n1max4, P.n2max);
+        P.d_items, P.d_tiles, P.ntiles, P.d_counters + 1, P.pitch, P.Lp, P.n1max8, P.n2max);
   else
     batch_core_kernel<__nv_bfloat16><<<P.grid_persist, kBT, P.sm_core, stream()>>>(
-        P.d_items, P.d_tiles, P.ntiles, P.d_counters + 1, P.pitch, P.Lp, P.n1max4, P.n2max);
+        P.d_items, P.d_tiles, P.ntiles, P.d_counters + 1, P.pitch, P.Lp, P.n1max8, P.n2max);
   check_launch("batch_core");
   batch_core_finish_kernel<<<P.count, 256, 0, stream()>>>(P.d_items);
   check_launch("batch_core_finish");
@@ -641,6 +774,9 @@ void enqueue_all(TbPlan& P, int* status) {
   check_launch("batch_trunc_apply");
   ++nk;
   if (resid) {
+    batch_resid_prep_kernel<<<P.count, 256, 0, stream()>>>(P.d_items);
+    check_launch("batch_resid_prep");
+    ++nk;
     if (P.xt == KRP_F32)
       batch_resid_kernel<float><<<P.grid_persist, kBT, P.sm_resid, stream()>>>(
           P.d_items, P.d_tiles, P.ntiles, P.d_counters + 2, P.pitch, P.Rp, P.n1max, P.n2max);
@@ -698,6 +834,7 @@ std::unique_ptr<TbPlan> build_plan(Ctx* c, krp_dtype xt, int count, const krp_tu
     add((size_t)l[0] * l[1] * l[2], 4);             // G
     add((size_t)r[0] * l[1] * l[2], 8);             // T1
     add((size_t)r[0] * r[1] * l[2], 8);             // T2
+    add((size_t)it.dims[2] * r[0] * r[1], 4);       // M
   }
   add((size_t)2 * count, 8);  // acc
   add((size_t)count, sizeof(TbItem));
@@ -773,6 +910,7 @@ std::unique_ptr<TbPlan> build_plan(Ctx* c, krp_dtype xt, int count, const krp_tu
     it.G = carve<float>(p, (size_t)it.l[0] * it.l[1] * it.l[2]);
     it.T1 = carve<double>(p, (size_t)it.r[0] * it.l[1] * it.l[2]);
     it.T2 = carve<double>(p, (size_t)it.r[0] * it.r[1] * it.l[2]);
+    it.M = carve<float>(p, (size_t)it.n[2] * it.r[0] * it.r[1]);
     it.core_out = src.core;
     it.acc = P->acc_begin + 2 * b;
     P->n1max = std::max(P->n1max, it.n[0]);
@@ -800,13 +938,13 @@ std::unique_ptr<TbPlan> build_plan(Ctx* c, krp_dtype xt, int count, const krp_tu
   KRP_CUDA_CHECK(cudaMemcpyAsync(P->d_ejobs, ej.data(), sizeof(EigJob) * ej.size(),
                                  cudaMemcpyHostToDevice, s));
   // shared-memory shapes
-  P->n1max4 = (P->n1max + 3) & ~3;
-  P->pitch = ((P->n1max4 + 31) & ~31) + 4;
+  P->n1max8 = (P->n1max + 7) & ~7;
+  P->pitch = ((P->n1max + 31) & ~31) + 4;
   P->Lp = (P->lmax + 3) & ~3;
   P->Rp = std::max(1, rmax);
-  P->sm_sketch = sizeof(float) * ((size_t)kJB * P->pitch + (size_t)P->n1max4 * P->Lp +
+  P->sm_sketch = sizeof(float) * ((size_t)kJB * P->pitch + (size_t)P->n1max8 * P->Lp +
                                   2 * (size_t)P->n2max * P->Lp + 2 * P->Lp);
-  P->sm_core = sizeof(float) * ((size_t)kJB * P->pitch + (size_t)P->n1max4 * P->Lp +
+  P->sm_core = sizeof(float) * ((size_t)kJB * P->pitch + (size_t)P->n1max8 * P->Lp +
                                 (size_t)P->n2max * P->Lp + (size_t)kJB * P->Lp);
   P->sm_resid = sizeof(float) * ((size_t)kJB * P->pitch + (size_t)P->n1max * P->Rp +
                                  (size_t)P->Rp * P->n2max + (size_t)P->Rp * P->Rp +
@@ -898,6 +1036,350 @@ void capture(TbPlan& P, Ctx* c) {
 
 void plan_free(void* p) { delete static_cast<TbPlan*>(p); }
 
+// ======================================================= block Hankel ======
+// Alg. 6 for many block Hankel matrices, one launch per phase over the batch
+// (same arithmetic as the single-matrix pipeline: structured sketches in
+// FP32, FP64 Householder QR, structured Psi^T Q, least squares, Gram + FP64
+// eigensolver, output vectors).
+struct HbItem {
+  const void* blocks;  // 2s-1 column-major m x n blocks
+  int m, n, s, r, lr, ll;
+  float* o1;           // s x lr   (tag Omega, factor 0)
+  float* o2;           // n x lr   (tag Omega, factor 1)
+  float* p1;           // s x ll   (tag Psi, factor 0)
+  float* p2;           // m x ll   (tag Psi, factor 1)
+  float* Zy;           // (2s-1) blocks of m x lr:  H_k Omega2
+  float* Zz;           // (2s-1) blocks of n x ll:  H_k^T Psi2
+  float* Y;            // ms x lr
+  float* Z;            // ns x ll
+  double* Q;           // ms x lr
+  double* P;           // ll x lr
+  double* Qp;          // ll x lr
+  double* Rp;          // lr x lr
+  double* W;           // lr x ns
+  double* Sg;          // lr x lr
+  double* Uw;          // lr x lr
+  double* ev;          // lr
+  double* U;           // out: ms x r
+  double* S;           // out: r
+  double* V;           // out: ns x r
+};
+
+template <class BT>
+__device__ __forceinline__ float ldb(const BT* p, int64_t i);
+template <>
+__device__ __forceinline__ float ldb<float>(const float* p, int64_t i) { return p[i]; }
+template <>
+__device__ __forceinline__ float ldb<__nv_bfloat16>(const __nv_bfloat16* p, int64_t i) {
+  return __bfloat162float(p[i]);
+}
+
+// Z-blocks of both sketches: grid (x: element chunks, y: item, z: 0 = Y, 1 = Z)
+//   Zy[a + m (c + lr k)] = sum_b H_k[a, b] Omega2[b, c]
+//   Zz[b + n (c + ll k)] = sum_a H_k[a, b] Psi2[a, c]
+template <class BT>
+__global__ void hb_blockmul_kernel(const HbItem* __restrict__ items) {
+  const HbItem& it = items[blockIdx.y];
+  const bool tz = blockIdx.z == 1;
+  const int m = it.m, n = it.n, nb = 2 * it.s - 1;
+  const int mo = tz ? n : m, ki = tz ? m : n, ell = tz ? it.ll : it.lr;
+  const float* F2 = tz ? it.p2 : it.o2;
+  float* Zs = tz ? it.Zz : it.Zy;
+  const BT* B = static_cast<const BT*>(it.blocks);
+  const int64_t total = (int64_t)mo * ell * nb;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int a = (int)(e % mo);
+    const int c = (int)((e / mo) % ell);
+    const int k = (int)(e / ((int64_t)mo * ell));
+    const BT* H = B + (int64_t)m * n * k;
+    float acc = 0.f;
+    for (int b = 0; b < ki; ++b) {
+      const float h = tz ? ldb(H, b + (int64_t)m * a) : ldb(H, a + (int64_t)m * b);
+      acc = fmaf(h, F2[b + (int64_t)ki * c], acc);
+    }
+    Zs[e] = acc;
+  }
+}
+
+// Y[(a + mo i) + mo s c] = sum_{j<s} F1[j + s c] Zs[a + mo (c + ell (i + j))]
+__global__ void hb_corr_kernel(const HbItem* __restrict__ items) {
+  const HbItem& it = items[blockIdx.y];
+  const bool tz = blockIdx.z == 1;
+  const int s = it.s, mo = tz ? it.n : it.m, ell = tz ? it.ll : it.lr;
+  const float* F1 = tz ? it.p1 : it.o1;
+  const float* Zs = tz ? it.Zz : it.Zy;
+  float* out = tz ? it.Z : it.Y;
+  const int64_t total = (int64_t)mo * s * ell;
+  const int64_t zstride = (int64_t)mo * ell;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int a = (int)(e % mo);
+    const int i = (int)((e / mo) % s);
+    const int c = (int)(e / ((int64_t)mo * s));
+    const float* z = Zs + a + (int64_t)mo * c;
+    float acc = 0.f;
+    for (int j = 0; j < s; ++j) acc = fmaf(F1[j + (int64_t)s * c], z[zstride * (i + j)], acc);
+    out[e] = acc;
+  }
+}
+
+// P[c + ll q] = sum_{i, a} Psi1[i, c] Psi2[a, c] Q[(a + m i) + ms q]; grid (ll_max, count)
+__global__ void hb_psitq_kernel(const HbItem* __restrict__ items) {
+  const HbItem& it = items[blockIdx.y];
+  const int c = blockIdx.x;
+  if (c >= it.ll) return;
+  const int m = it.m, s = it.s, lr = it.lr;
+  const int64_t ms = (int64_t)m * s;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  for (int q = warp; q < lr; q += nw) {
+    double acc = 0.0;
+    for (int64_t row = lane; row < ms; row += 32) {
+      const int a = (int)(row % m), i = (int)(row / m);
+      const double w = (double)it.p1[i + (int64_t)s * c] * (double)it.p2[a + (int64_t)m * c];
+      acc = fma(w, it.Q[row + ms * q], acc);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (lane == 0) it.P[c + (int64_t)it.ll * q] = acc;
+  }
+}
+
+// W[q + lr col] = (Rp^{-1} Qp^T Z^T)[q, col]: grid (x: column chunks, y: item)
+__global__ void hb_ls_kernel(const HbItem* __restrict__ items) {
+  const HbItem& it = items[blockIdx.y];
+  const int ll = it.ll, lr = it.lr;
+  const int64_t ns = (int64_t)it.n * it.s;
+  for (int64_t col = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; col < ns;
+       col += (int64_t)gridDim.x * blockDim.x) {
+    double* w = it.W + (int64_t)lr * col;
+    for (int q = 0; q < lr; ++q) {
+      double acc = 0.0;
+      for (int c = 0; c < ll; ++c) acc = fma(it.Qp[c + (int64_t)ll * q], (double)it.Z[col + ns * c], acc);
+      w[q] = acc;
+    }
+    for (int q = lr - 1; q >= 0; --q) {
+      double acc = w[q];
+      for (int t = q + 1; t < lr; ++t) acc -= it.Rp[q + (int64_t)lr * t] * w[t];
+      w[q] = acc / it.Rp[q + (int64_t)lr * q];
+    }
+  }
+}
+
+// Sg = W W^T (lr x lr, FP64); one CTA per item
+__global__ void hb_gram_kernel(const HbItem* __restrict__ items) {
+  const HbItem& it = items[blockIdx.x];
+  const int lr = it.lr;
+  const int64_t ns = (int64_t)it.n * it.s;
+  for (int pq = threadIdx.x; pq < lr * lr; pq += blockDim.x) {
+    const int p = pq % lr, q = pq / lr;
+    if (p > q) continue;
+    double acc = 0.0;
+    for (int64_t col = 0; col < ns; ++col)
+      acc = fma(it.W[p + (int64_t)lr * col], it.W[q + (int64_t)lr * col], acc);
+    it.Sg[p + lr * q] = acc;
+    it.Sg[q + lr * p] = acc;
+  }
+}
+
+// U = Q Uw[:, :r], V = W^T Uw[:, :r] / sigma, S = sigma; grid (x: chunks, y: item)
+__global__ void hb_out_kernel(const HbItem* __restrict__ items) {
+  const HbItem& it = items[blockIdx.y];
+  const int lr = it.lr, r = it.r;
+  const int64_t ms = (int64_t)it.m * it.s, ns = (int64_t)it.n * it.s;
+  const int64_t nu = ms * r, total = nu + ns * r;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    if (e < nu) {
+      const int64_t row = e % ms;
+      const int j = (int)(e / ms);
+      double acc = 0.0;
+      for (int q = 0; q < lr; ++q) acc = fma(it.Q[row + ms * q], it.Uw[q + (int64_t)lr * j], acc);
+      it.U[e] = acc;
+    } else {
+      const int64_t f = e - nu;
+      const int64_t col = f % ns;
+      const int j = (int)(f / ns);
+      const double sig = sqrt(fmax(it.ev[j], 0.0));
+      double acc = 0.0;
+      for (int q = 0; q < lr; ++q) acc = fma(it.W[q + (int64_t)lr * col], it.Uw[q + (int64_t)lr * j], acc);
+      it.V[f] = sig > 0.0 ? acc / sig : 0.0;
+      if (col == 0) it.S[j] = sig;
+    }
+  }
+}
+
+struct HbPlan {
+  krp_dtype bt{};
+  int count = 0;
+  std::vector<krp_hankel_item> sig;
+  char* arena = nullptr;
+  HbItem* d_items = nullptr;
+  BatchFactorJob* d_fjobs = nullptr;
+  int64_t* d_fstart = nullptr;
+  int64_t fblocks = 0;
+  QrJob* d_qy = nullptr;
+  QrJob* d_qp = nullptr;
+  EigJob* d_ej = nullptr;
+  int gx_blockmul = 1, gx_corr = 1, gx_ls = 1, gx_out = 1, llmax = 1, lrmax = 1;
+  int kernels_per_run = 0;
+  cudaGraphExec_t exec = nullptr;
+  cudaStream_t cs = nullptr;
+  cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+  ~HbPlan() {
+    if (exec) cudaGraphExecDestroy(exec);
+    if (ev_in) cudaEventDestroy(ev_in);
+    if (ev_out) cudaEventDestroy(ev_out);
+    if (cs) cudaStreamDestroy(cs);
+    if (arena) cudaFree(arena);
+  }
+};
+
+bool hb_same(const HbPlan& p, krp_dtype bt, int count, const krp_hankel_item* items) {
+  if (p.bt != bt || p.count != count) return false;
+  return std::memcmp(p.sig.data(), items, sizeof(krp_hankel_item) * count) == 0;
+}
+
+int chunks_for(int64_t n) { return (int)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, 1024)); }
+
+void hb_enqueue(HbPlan& P, int* status) {
+  int nk = 0;
+  launch_gen_factors_batch(P.d_fjobs, P.d_fstart, 4 * P.count, P.fblocks);
+  ++nk;
+  if (P.bt == KRP_F32)
+    hb_blockmul_kernel<float><<<dim3(P.gx_blockmul, P.count, 2), 256, 0, stream()>>>(P.d_items);
+  else
+    hb_blockmul_kernel<__nv_bfloat16><<<dim3(P.gx_blockmul, P.count, 2), 256, 0, stream()>>>(
+        P.d_items);
+  check_launch("hb_blockmul");
+  hb_corr_kernel<<<dim3(P.gx_corr, P.count, 2), 256, 0, stream()>>>(P.d_items);
+  check_launch("hb_corr");
+  qr_householder_launch(P.d_qy, P.count, status);
+  hb_psitq_kernel<<<dim3(P.llmax, P.count), 256, 0, stream()>>>(P.d_items);
+  check_launch("hb_psitq");
+  qr_householder_launch(P.d_qp, P.count, status);
+  hb_ls_kernel<<<dim3(P.gx_ls, P.count), 256, 0, stream()>>>(P.d_items);
+  check_launch("hb_ls");
+  hb_gram_kernel<<<P.count, 256, 0, stream()>>>(P.d_items);
+  check_launch("hb_gram");
+  eig_launch(P.d_ej, P.count, P.lrmax, status);
+  hb_out_kernel<<<dim3(P.gx_out, P.count), 256, 0, stream()>>>(P.d_items);
+  check_launch("hb_out");
+  nk += 9;
+  P.kernels_per_run = nk;
+}
+
+std::unique_ptr<HbPlan> hb_build(Ctx* c, krp_dtype bt, int count, const krp_hankel_item* items) {
+  auto P = std::make_unique<HbPlan>();
+  P->bt = bt;
+  P->count = count;
+  P->sig.assign(items, items + count);
+  size_t bytes = 0;
+  auto add = [&](size_t n, size_t e) { bytes += (n * e + 255) & ~size_t(255); };
+  for (int b = 0; b < count; ++b) {
+    const krp_hankel_item& h = items[b];
+    const size_t ms = (size_t)h.m * h.s, ns = (size_t)h.n * h.s, nb = 2 * (size_t)h.s - 1;
+    const size_t lr = h.ell_r, ll = h.ell_l;
+    add((size_t)h.s * lr, 4); add((size_t)h.n * lr, 4); add((size_t)h.s * ll, 4); add((size_t)h.m * ll, 4);
+    add(nb * h.m * lr, 4); add(nb * h.n * ll, 4);
+    add(ms * lr, 4); add(ns * ll, 4);
+    add(ms * lr, 8); add(ms * lr, 8);          // Q, QR work
+    add(ll * lr, 8); add(ll * lr, 8); add(ll * lr, 8); add(lr * lr, 8);  // P, Qp, QR work, Rp
+    add(lr * ns, 8); add(lr * lr, 8); add(lr * lr, 8); add(lr, 8);        // W, Sg, Uw, ev
+  }
+  add(count, sizeof(HbItem));
+  add((size_t)4 * count, sizeof(BatchFactorJob));
+  add((size_t)4 * count + 1, 8);
+  add(count, sizeof(QrJob));
+  add(count, sizeof(QrJob));
+  add(count, sizeof(EigJob));
+  KRP_CUDA_CHECK(cudaStreamCreateWithFlags(&P->cs, cudaStreamNonBlocking));
+  KRP_CUDA_CHECK(cudaEventCreateWithFlags(&P->ev_in, cudaEventDisableTiming));
+  KRP_CUDA_CHECK(cudaEventCreateWithFlags(&P->ev_out, cudaEventDisableTiming));
+  KRP_CUDA_CHECK(cudaMalloc(&P->arena, bytes));
+  char* p = P->arena;
+  std::vector<HbItem> hi(count);
+  std::vector<BatchFactorJob> fj;
+  std::vector<int64_t> fstart(1, 0);
+  std::vector<QrJob> qy, qp;
+  std::vector<EigJob> ej;
+  int64_t maxbm = 1, maxcorr = 1, maxns = 1, maxout = 1;
+  for (int b = 0; b < count; ++b) {
+    const krp_hankel_item& h = items[b];
+    HbItem& it = hi[b];
+    it.blocks = h.blocks;
+    it.m = h.m; it.n = h.n; it.s = h.s; it.r = h.r; it.lr = h.ell_r; it.ll = h.ell_l;
+    const int64_t ms = (int64_t)h.m * h.s, ns = (int64_t)h.n * h.s, nb = 2 * (int64_t)h.s - 1;
+    it.o1 = carve<float>(p, (size_t)h.s * it.lr);
+    it.o2 = carve<float>(p, (size_t)h.n * it.lr);
+    it.p1 = carve<float>(p, (size_t)h.s * it.ll);
+    it.p2 = carve<float>(p, (size_t)h.m * it.ll);
+    it.Zy = carve<float>(p, (size_t)nb * h.m * it.lr);
+    it.Zz = carve<float>(p, (size_t)nb * h.n * it.ll);
+    it.Y = carve<float>(p, (size_t)ms * it.lr);
+    it.Z = carve<float>(p, (size_t)ns * it.ll);
+    it.Q = carve<double>(p, (size_t)ms * it.lr);
+    double* qwork = carve<double>(p, (size_t)ms * it.lr);
+    it.P = carve<double>(p, (size_t)it.ll * it.lr);
+    it.Qp = carve<double>(p, (size_t)it.ll * it.lr);
+    double* pwork = carve<double>(p, (size_t)it.ll * it.lr);
+    it.Rp = carve<double>(p, (size_t)it.lr * it.lr);
+    it.W = carve<double>(p, (size_t)it.lr * ns);
+    it.Sg = carve<double>(p, (size_t)it.lr * it.lr);
+    it.Uw = carve<double>(p, (size_t)it.lr * it.lr);
+    it.ev = carve<double>(p, (size_t)it.lr);
+    it.U = h.U; it.S = h.S; it.V = h.V;
+    // factors: Omega1 (s x lr, factor 0), Omega2 (n x lr, factor 1) with tag
+    // Omega; Psi1 (s x ll), Psi2 (m x ll) with tag Psi; draw 0, key = seed
+    struct F { float* ptr; int64_t rows; uint32_t factor, tag; int ell; };
+    const F fs[4] = {{it.o1, h.s, 0, KRP_TAG_OMEGA, it.lr}, {it.o2, h.n, 1, KRP_TAG_OMEGA, it.lr},
+                     {it.p1, h.s, 0, KRP_TAG_PSI, it.ll}, {it.p2, h.m, 1, KRP_TAG_PSI, it.ll}};
+    for (const F& f : fs) {
+      BatchFactorJob j{};
+      j.ptr = f.ptr; j.rows = f.rows; j.seed = h.seed; j.factor = f.factor; j.draw = 0;
+      j.tag = f.tag; j.ell = f.ell; j.bf16_round = bt == KRP_BF16 ? 1 : 0;
+      fj.push_back(j);
+      fstart.push_back(fstart.back() + (f.rows * f.ell + 3) / 4);
+    }
+    QrJob a{};
+    a.Y = it.Y; a.Q = it.Q; a.R = nullptr; a.work = qwork; a.m = ms; a.l = it.lr;
+    qy.push_back(a);
+    QrJob pq{};
+    pq.Y = nullptr; pq.Y64 = it.P; pq.Q = it.Qp; pq.R = it.Rp; pq.work = pwork; pq.m = it.ll; pq.l = it.lr;
+    qp.push_back(pq);
+    ej.push_back(EigJob{it.Sg, it.Uw, it.ev, it.lr, it.lr});
+    maxbm = std::max<int64_t>(maxbm, std::max<int64_t>(nb * h.m * it.lr, nb * h.n * it.ll));
+    maxcorr = std::max<int64_t>(maxcorr, std::max<int64_t>(ms * it.lr, ns * it.ll));
+    maxns = std::max<int64_t>(maxns, ns);
+    maxout = std::max<int64_t>(maxout, (ms + ns) * h.r);
+    P->llmax = std::max(P->llmax, it.ll);
+    P->lrmax = std::max(P->lrmax, it.lr);
+  }
+  P->d_items = carve<HbItem>(p, count);
+  P->d_fjobs = carve<BatchFactorJob>(p, (size_t)4 * count);
+  P->d_fstart = carve<int64_t>(p, (size_t)4 * count + 1);
+  P->d_qy = carve<QrJob>(p, count);
+  P->d_qp = carve<QrJob>(p, count);
+  P->d_ej = carve<EigJob>(p, count);
+  KRP_REQUIRE((size_t)(p - P->arena) <= bytes, "Hankel batch arena overflow");
+  P->fblocks = fstart.back();
+  P->gx_blockmul = chunks_for(maxbm);
+  P->gx_corr = chunks_for(maxcorr);
+  P->gx_ls = chunks_for(maxns);
+  P->gx_out = chunks_for(maxout);
+  cudaStream_t s = c->stream;
+  KRP_CUDA_CHECK(cudaMemcpyAsync(P->d_items, hi.data(), sizeof(HbItem) * count, cudaMemcpyHostToDevice, s));
+  KRP_CUDA_CHECK(cudaMemcpyAsync(P->d_fjobs, fj.data(), sizeof(BatchFactorJob) * fj.size(), cudaMemcpyHostToDevice, s));
+  KRP_CUDA_CHECK(cudaMemcpyAsync(P->d_fstart, fstart.data(), sizeof(int64_t) * fstart.size(), cudaMemcpyHostToDevice, s));
+  KRP_CUDA_CHECK(cudaMemcpyAsync(P->d_qy, qy.data(), sizeof(QrJob) * count, cudaMemcpyHostToDevice, s));
+  KRP_CUDA_CHECK(cudaMemcpyAsync(P->d_qp, qp.data(), sizeof(QrJob) * count, cudaMemcpyHostToDevice, s));
+  KRP_CUDA_CHECK(cudaMemcpyAsync(P->d_ej, ej.data(), sizeof(EigJob) * count, cudaMemcpyHostToDevice, s));
+  KRP_CUDA_CHECK(cudaStreamSynchronize(s));
+  return P;
+}
+
+void hb_plan_free(void* p) { delete static_cast<HbPlan*>(p); }
+
 }  // namespace
 
 void tucker_batched(krp_dtype xt, int count, krp_tucker_item* items, int oversample,
@@ -960,6 +1442,63 @@ int tucker_batched_plan_info(int* slabs_per_tile, int* tiles, int* grid) {
   if (tiles) *tiles = P->ntiles;
   if (grid) *grid = P->grid_persist;
   return 1;
+}
+
+void hankel_batched(krp_dtype bt, int count, krp_hankel_item* items) {
+  Ctx* c = current();
+  KRP_REQUIRE(count >= 1, "count must be >= 1");
+  KRP_REQUIRE(items, "items is NULL");
+  KRP_REQUIRE(bt == KRP_F32 || bt == KRP_BF16, "blocks dtype must be KRP_F32 or KRP_BF16");
+  for (int b = 0; b < count; ++b) {
+    krp_hankel_item& h = items[b];
+    if (h.ell_l == 0) h.ell_l = (int)std::ceil(1.5 * h.ell_r);
+    KRP_REQUIRE(h.blocks && is_device_ptr(h.blocks), "item %d: blocks must be a device pointer", b);
+    KRP_REQUIRE(h.m >= 1 && h.n >= 1 && h.s >= 1, "item %d: m, n, s must be >= 1", b);
+    KRP_REQUIRE(h.r >= 1 && h.r <= h.ell_r && h.ell_r <= h.ell_l && h.ell_r <= 64 &&
+                    h.ell_l <= 256,
+                "item %d: need 1 <= r <= ell_r <= ell_l, ell_r <= 64, ell_l <= 256", b);
+    KRP_REQUIRE((int64_t)h.ell_r <= (int64_t)h.m * h.s && (int64_t)h.ell_l <= (int64_t)h.n * h.s,
+                "item %d: sketch sizes exceed the matrix", b);
+    KRP_REQUIRE(h.U && h.S && h.V && is_device_ptr(h.U) && is_device_ptr(h.S) && is_device_ptr(h.V),
+                "item %d: U, S, V must be device pointers", b);
+  }
+  HbPlan* P = static_cast<HbPlan*>(c->hankel_plan);
+  if (!P || !hb_same(*P, bt, count, items)) {
+    if (c->hankel_plan) c->hankel_plan_free(c->hankel_plan);
+    c->hankel_plan = nullptr;
+    std::unique_ptr<HbPlan> np = hb_build(c, bt, count, items);
+    KRP_CUDA_CHECK(cudaMemsetAsync(c->d_status, 0, sizeof(int), c->stream));
+    hb_enqueue(*np, c->d_status);  // eager run: validates the sequence
+    raise_device_status(c);
+    cudaGraph_t g = nullptr;
+    const uint64_t launches = c->launches;
+    {
+      StreamSwap sw(c, np->cs);
+      KRP_CUDA_CHECK(cudaStreamBeginCapture(np->cs, cudaStreamCaptureModeRelaxed));
+      try {
+        hb_enqueue(*np, c->d_status);
+      } catch (...) {
+        cudaStreamEndCapture(np->cs, &g);
+        if (g) cudaGraphDestroy(g);
+        throw;
+      }
+      KRP_CUDA_CHECK(cudaStreamEndCapture(np->cs, &g));
+    }
+    c->launches = launches;
+    const cudaError_t e = cudaGraphInstantiate(&np->exec, g, 0);
+    cudaGraphDestroy(g);
+    KRP_CUDA_CHECK(e);
+    P = np.release();
+    c->hankel_plan = P;
+    c->hankel_plan_free = hb_plan_free;
+  }
+  KRP_CUDA_CHECK(cudaEventRecord(P->ev_in, c->stream));
+  KRP_CUDA_CHECK(cudaStreamWaitEvent(P->cs, P->ev_in, 0));
+  KRP_CUDA_CHECK(cudaGraphLaunch(P->exec, P->cs));
+  KRP_CUDA_CHECK(cudaEventRecord(P->ev_out, P->cs));
+  KRP_CUDA_CHECK(cudaStreamWaitEvent(c->stream, P->ev_out, 0));
+  c->launches += P->kernels_per_run;
+  raise_device_status(c);
 }
 
 }  // namespace krp

@@ -72,6 +72,8 @@ struct Ctx {
   int* d_status = nullptr;  // device status word for bounded waits / numerics
   void* batch_plan = nullptr;              // cached batched-Tucker plan (batched.cu)
   void (*batch_plan_free)(void*) = nullptr;
+  void* hankel_plan = nullptr;             // cached batched block-Hankel plan
+  void (*hankel_plan_free)(void*) = nullptr;
 };
 
 Ctx* current();           // context of the API call in progress (thread-local)

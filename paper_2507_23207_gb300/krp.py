@@ -32,6 +32,7 @@ EXPORTED = [
     "krp_sketch_mode", "krp_sketch_all_modes", "krp_qr", "krp_qr_noalloc", "krp_multi_ttm",
     "krp_tucker_rhosvd", "krp_tucker_sthosvd", "krp_block_hankel_lowrank",
     "krp_block_hankel_sketch", "krp_tucker_rhosvd_batched", "krp_tucker_batch_plan_info",
+    "krp_block_hankel_batched",
 ]
 
 
@@ -69,6 +70,16 @@ class TuckerItem(C.Structure):
         ("core", C.c_void_p),
         ("factors", C.c_void_p * 3),
         ("rel_residual", C.c_double),
+    ]
+
+
+class HankelItem(C.Structure):
+    _fields_ = [
+        ("blocks", C.c_void_p),
+        ("m", C.c_int), ("n", C.c_int), ("s", C.c_int), ("r", C.c_int),
+        ("ell_r", C.c_int), ("ell_l", C.c_int),
+        ("seed", C.c_uint64),
+        ("U", C.c_void_p), ("S", C.c_void_p), ("V", C.c_void_p),
     ]
 
 
@@ -119,6 +130,7 @@ def load_library(path: Optional[str] = None):
                                                 C.c_int, C.c_uint]),
         "krp_tucker_batch_plan_info": (C.c_int, [vp, C.POINTER(C.c_int), C.POINTER(C.c_int),
                                                  C.POINTER(C.c_int)]),
+        "krp_block_hankel_batched": (C.c_int, [vp, C.c_int, C.c_int, C.POINTER(HankelItem)]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -353,3 +365,21 @@ def krp_tucker_batch_plan_info(ctx: Context):
     a, b, c = C.c_int(0), C.c_int(0), C.c_int(0)
     ctx.check(ctx.lib.krp_tucker_batch_plan_info(ctx.handle, C.byref(a), C.byref(b), C.byref(c)))
     return {"slabs_per_tile": a.value, "tiles": b.value, "grid": c.value}
+
+
+def make_hankel_items(blocks, shapes, seeds, Us, Ss, Vs):
+    """Array of krp_hankel_item; shapes[b] = (m, n, s, r, ell_r, ell_l)."""
+    n = len(blocks)
+    arr = (HankelItem * n)()
+    for b in range(n):
+        it = arr[b]
+        it.blocks = _ptr(blocks[b])
+        it.m, it.n, it.s, it.r, it.ell_r, it.ell_l = (int(v) for v in shapes[b])
+        it.seed = int(seeds[b])
+        it.U, it.S, it.V = _ptr(Us[b]), _ptr(Ss[b]), _ptr(Vs[b])
+    return arr
+
+
+def krp_block_hankel_batched(ctx: Context, bt: int, items):
+    """Batched Alg. 6 over block Hankel matrices (outputs in the items' U, S, V)."""
+    ctx.check(ctx.lib.krp_block_hankel_batched(ctx.handle, int(bt), len(items), items))

@@ -134,3 +134,54 @@ def test_batched_rejects_bad_descriptors(ctx):
     with pytest.raises(K.KrpError) as e:
         K.krp_tucker_rhosvd_batched(ctx, K.KRP_F32, items, P, K.KRP_TRUNCATE)
     assert e.value.status == K.KRP_EINVAL
+
+
+HSPECS = [(6, 3, 2, 9, 6, 10, 15), (10, 5, 3, 17, 10, 13, 20), (12, 8, 8, 40, 12, 20, 30),
+          (8, 4, 4, 33, 8, 16, 24), (20, 6, 6, 64, 20, 28, 42)]
+
+
+def _hankel_batch(dtype):
+    import torch
+    from synth import HankelSpec, markov_parameters
+    blocks, hosts, shapes, seeds, Us, Ss, Vs = [], [], [], [], [], [], []
+    for b, (order, m, n, s, r, lr, ll) in enumerate(HSPECS):
+        spec = HankelSpec(f"h{b}", order, m, n, s, 0.9, 300 + b, r, lr, ll)
+        bl = markov_parameters(spec)
+        bl = philox.round_to_bf16(bl) if dtype == torch.bfloat16 else philox.round_to_f32(bl)
+        hosts.append(bl)
+        flat = np.concatenate([np.asfortranarray(bl[:, :, k]).ravel(order="F")
+                               for k in range(bl.shape[2])])
+        blocks.append(torch.from_numpy(flat).to(dtype).to(dev()))
+        shapes.append((m, n, s, r, lr, ll))
+        seeds.append(40 + b)
+        Us.append(torch.empty((r, m * s), dtype=torch.float64, device=dev()))
+        Vs.append(torch.empty((r, n * s), dtype=torch.float64, device=dev()))
+        Ss.append(torch.empty(r, dtype=torch.float64, device=dev()))
+    return blocks, hosts, shapes, seeds, Us, Ss, Vs
+
+
+@pytest.mark.parametrize("form", ["f32", "bf16"])
+def test_batched_hankel_matches_oracle(ctx, form):
+    """Every matrix of the batch against the oracle's Alg. 6 with the same key:
+    singular values (relative to sigma_1) and U S V^T (relative to ||H||)."""
+    import torch
+    import paper_2507_23207_gb300 as K
+    from oracle import hankel as HK
+    dtype = torch.float32 if form == "f32" else torch.bfloat16
+    blocks, hosts, shapes, seeds, Us, Ss, Vs = _hankel_batch(dtype)
+    items = K.make_hankel_items(blocks, shapes, seeds, Us, Ss, Vs)
+    for rep in range(2):  # first call builds and captures, second replays
+        for u in Us:
+            u.zero_()
+        K.krp_block_hankel_batched(ctx, K.KRP_F32 if form == "f32" else K.KRP_BF16, items)
+        torch.cuda.synchronize()
+        for b, bl in enumerate(hosts):
+            m, n, s, r, lr, ll = shapes[b]
+            ora = HK.single_pass_svd(bl, r, lr, ll, seeds[b], omega_round=form)
+            ug = Us[b].cpu().numpy().T
+            vg = Vs[b].cpu().numpy().T
+            sg = Ss[b].cpu().numpy()
+            assert np.max(np.abs(sg - ora["S"])) <= 1e-5 * ora["S"][0], (b, rep)
+            ag = (ug * sg) @ vg.T
+            ao = (ora["U"] * ora["S"]) @ ora["V"].T
+            assert np.linalg.norm(ag - ao) <= 1e-5 * np.linalg.norm(ora["H"]), (b, rep)

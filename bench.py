@@ -140,6 +140,11 @@ def run_ours(args, rank, world, local_rank):
     peaks, peak_src = measured_peaks()
     x32, xbf = make_inputs(spec, dev, want_bf16=not args.no_bf16)
     forms = [("f32", x32)] + ([("bf16", xbf)] if xbf is not None else [])
+    if xbf is not None:
+        ctx0 = K.Context(local_rank, torch.cuda.current_stream(dev).cuda_stream)
+        forms.append(("bf16x2", K.krp_split_bf16x2(ctx0, x32)))
+        torch.cuda.synchronize()
+        ctx0.close()
     ranks = list(spec.ranks)
     p = spec.oversample
     flags = K.KRP_MEMO | K.KRP_TRUNCATE | K.KRP_RESIDUAL
@@ -178,7 +183,8 @@ def run_ours(args, rank, world, local_rank):
             torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
             ms = float(t.item())
         results[form] = {"ms": ms, "res": res, "phases": ph, "clocks": clk,
-                         "launches": launches, "bytes_per_elem": x.element_size()}
+                         "launches": launches,
+                         "bytes_per_elem": 4 if form == "bf16x2" else x.element_size()}
     # dominant-kernel roofline: the sketch of mode 1 alone (one MTTKRP launch)
     kr = kernel_roofline(ctx, spec, x32, dev, stream, peaks, results["f32"]["clocks"], args)
     # e2e through the C ABI with host buffers (pinned), FP32 form
@@ -191,6 +197,7 @@ def run_ours(args, rank, world, local_rank):
         extra["tucker_200pow4"] = c3_run(ctx, dev, stream, args)
         extra["block_hankel_1024"] = c4_run(ctx, dev, stream, args)
         extra["batched_512_tucker"] = batch_run(ctx, dev, stream, args)
+        extra["batched_64_hankel"] = hankel_batch_run(ctx, dev, stream, args)
     ctx.close()
     return spec, results, kr, e2e, peaks, peak_src, (sk, co, rs, qr), extra
 
@@ -248,6 +255,7 @@ def c3_run(ctx, dev, stream, args):
     xs = {"f32": x64.to(torch.float32), "bf16": x64.to(torch.bfloat16)}
     del x64
     torch.cuda.empty_cache()
+    xs["bf16x2"] = K.krp_split_bf16x2(ctx, xs["f32"])
     ranks = list(spec.ranks)
     core = torch.empty(int(np.prod(ranks)), dtype=torch.float32, device=dev)
     facs = [torch.empty(n * r, dtype=torch.float64, device=dev) for n, r in zip(spec.dims, ranks)]
@@ -260,11 +268,15 @@ def c3_run(ctx, dev, stream, args):
         ms, res = _timed(stream, lambda: K.krp_tucker_rhosvd(
             ctx, x, spec.dims, ranks, spec.oversample, spec.omega_seed, flags, core, facs),
             reps=max(3, min(args.steps, 5)), warm=2)
+        esz = 4 if form == "bf16x2" else x.element_size()
+        okey = "f32" if form == "f32" else "bf16"  # BF16 factors for both BF16 forms
         out[form] = {"ms": round(ms, 3), "rel_error": res["rel_residual"],
-                     "oracle_rel_error": gold[f"rhosvd_memo_truncated_rel_error_{form}"],
-                     "gbs": round(3.0 * spec.numel * x.element_size() / (ms * 1e-3) / 1e9, 1)}
+                     "oracle_rel_error": gold[f"rhosvd_memo_truncated_rel_error_{okey}"],
+                     "gbs": round(3.0 * spec.numel * esz / (ms * 1e-3) / 1e9, 1)}
     out["bf16_error_over_f32"] = round(out["bf16"]["rel_error"] / out["f32"]["rel_error"], 5)
     out["bf16_speedup"] = round(out["f32"]["ms"] / out["bf16"]["ms"], 3)
+    out["bf16x2_error_over_f32"] = round(out["bf16x2"]["rel_error"] / out["f32"]["rel_error"], 5)
+    out["bf16x2_speedup"] = round(out["f32"]["ms"] / out["bf16x2"]["ms"], 3)
     del xs
     torch.cuda.empty_cache()
     return out
@@ -326,6 +338,42 @@ def batch_run(ctx, dev, stream, args):
     out["speedup_f32_batched_vs_loop"] = round(ms_loop / out["f32"]["ms"], 2)
     del x32, xbf
     torch.cuda.empty_cache()
+    return out
+
+
+def hankel_batch_run(ctx, dev, stream, args):
+    """64 block Hankel matrices (state order 8..32, blocks 4x4..8x8, 32..128
+    block rows, r = order, l_r = r + 8): the batched path against a loop of
+    single-matrix calls, both forms."""
+    import torch
+    import paper_2507_23207_gb300 as K
+    from synth import batch_hankel_specs, markov_parameters
+    specs = batch_hankel_specs()
+    host = []
+    for sp in specs:
+        b = markov_parameters(sp)
+        host.append(np.concatenate([np.asfortranarray(b[:, :, k]).ravel(order="F")
+                                    for k in range(b.shape[2])]))
+    shapes = [(sp.m, sp.n, sp.s, sp.r, sp.ell_r, sp.ell_l) for sp in specs]
+    seeds = [sp.omega_seed for sp in specs]
+    Us = [torch.empty((sp.r, sp.m * sp.s), dtype=torch.float64, device=dev) for sp in specs]
+    Vs = [torch.empty((sp.r, sp.n * sp.s), dtype=torch.float64, device=dev) for sp in specs]
+    Ss = [torch.empty(sp.r, dtype=torch.float64, device=dev) for sp in specs]
+    out = {"workload": f"{len(specs)} block Hankel matrices, order U(8..32), m = n U(4..8), "
+                       "s U(32..128), r = order, l_r = r + 8, l_l = 1.5 l_r"}
+    reps = max(3, min(args.steps, 10))
+    for form, dt, bt in (("f32", torch.float32, K.KRP_F32), ("bf16", torch.bfloat16, K.KRP_BF16)):
+        blocks = [torch.from_numpy(h).to(torch.float32).to(dt).to(dev) for h in host]
+        items = K.make_hankel_items(blocks, shapes, seeds, Us, Ss, Vs)
+        K.krp_block_hankel_batched(ctx, bt, items)
+        ms, _ = _timed(stream, lambda: K.krp_block_hankel_batched(ctx, bt, items), reps=reps, warm=2)
+        def loop():
+            for b, sp in enumerate(specs):
+                K.krp_block_hankel_lowrank(ctx, blocks[b], sp.m, sp.n, sp.s, sp.r, sp.ell_r,
+                                           sp.ell_l, sp.omega_seed, Us[b], Ss[b], Vs[b])
+        ms_loop, _ = _timed(stream, loop, reps=1, warm=1)
+        out[form] = {"batched_ms": round(ms, 3), "loop_ms": round(ms_loop, 3),
+                     "speedup": round(ms_loop / ms, 2)}
     return out
 
 
@@ -536,6 +584,16 @@ def main():
             "value": round(world * 3.0 * n * 2 / (b["ms"] * 1e-3) / 1e9, 2), "unit": "GB/s",
             "tflops": round(world * flops_step / (b["ms"] * 1e-3) / 1e12, 3),
             "rel_error": b["res"]["rel_residual"],
+            "phases_ms": {k: round(v, 4) for k, v in b["phases"].items()},
+            "speedup_vs_f32": round(ms / b["ms"], 3)}
+    if "bf16x2" in results:
+        b = results["bf16x2"]
+        line["bf16x2_form"] = {
+            "note": "X as a BF16 hi/lo pair on tensor cores (4 B per element)",
+            "ms_per_step": round(b["ms"], 4),
+            "value": round(world * 3.0 * n * 4 / (b["ms"] * 1e-3) / 1e9, 2), "unit": "GB/s",
+            "rel_error": b["res"]["rel_residual"],
+            "error_over_f32": round(b["res"]["rel_residual"] / f32["res"]["rel_residual"], 5),
             "phases_ms": {k: round(v, 4) for k, v in b["phases"].items()},
             "speedup_vs_f32": round(ms / b["ms"], 3)}
     if e2e:

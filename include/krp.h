@@ -63,7 +63,12 @@ typedef enum krp_dtype {
   KRP_F32 = 0,
   KRP_BF16 = 1,
   KRP_FP8_E4M3 = 2,  /* reserved */
-  KRP_F64 = 3
+  KRP_F64 = 3,
+  /* X as a BF16 hi/lo pair: 2N BF16 values, the hi plane (N) then the lo
+   * plane (N), X ~ hi + lo with |X - hi - lo| <= 2^-17 |X| (krp_split_bf16x2
+   * builds it from FP32).  Contractions over X run on tensor cores with both
+   * planes (FP32 accuracy of X at 4 bytes per element); factors are BF16. */
+  KRP_BF16X2 = 4
 } krp_dtype;
 
 /* Flags of krp_tucker_rhosvd / krp_tucker_sthosvd. */
@@ -191,6 +196,12 @@ krp_status krp_qr(krp_ctx ctx, int count, const float* const* Y,
 #define KRP_QR_NOALLOC_MAX_DOUBLES 524288
 krp_status krp_qr_noalloc(const float* Y, int64_t m, int l, double* Q,
                           double* R, void* cuda_stream);
+
+/* hi[e] = bf16_rn(X[e]), lo[e] = bf16_rn(X[e] - hi[e]) for e < n; out holds
+ * 2n BF16 values (hi plane then lo plane), the KRP_BF16X2 layout.  X and out
+ * are device pointers (out 16-byte aligned).  The paper streams X in one
+ * precision; this split form is not in it. */
+krp_status krp_split_bf16x2(krp_ctx ctx, const float* X, int64_t n, void* out);
 
 /* ---- a5: multi-TTM core (Alg. 7 last step) ------------------------------- */
 

@@ -74,6 +74,7 @@ size_t dtype_size(krp_dtype t) {
     case KRP_BF16: return 2;
     case KRP_F64: return 8;
     case KRP_FP8_E4M3: return 1;
+    case KRP_BF16X2: return 4;
   }
   return 0;
 }
@@ -274,7 +275,8 @@ krp_status krp_multi_ttm(krp_ctx ctx, const void* X, krp_dtype xt, int d, const 
     KRP_REQUIRE(d >= 1 && d <= KRP_MAXD, "d out of range");
     checked_numel(d, dims);
     KRP_REQUIRE(X && Q && cols && G, "NULL argument");
-    KRP_REQUIRE(xt == KRP_F32 || xt == KRP_BF16, "X dtype must be F32 or BF16");
+    KRP_REQUIRE(xt == KRP_F32 || xt == KRP_BF16 || xt == KRP_BF16X2,
+                "X dtype must be F32, BF16 or BF16X2");
     for (int j = 0; j < d; ++j) {
       KRP_REQUIRE(Q[j], "Q[%d] is NULL", j);
       KRP_REQUIRE(cols[j] >= 1 && cols[j] <= 256, "cols[%d] out of range", j);
@@ -294,6 +296,15 @@ krp_status krp_tucker_sthosvd(krp_ctx ctx, const void* X, krp_dtype xt, int d,
                               const int64_t* dims, const int* ranks, int oversample,
                               uint64_t seed, unsigned flags, krp_tucker_out* out) {
   return guarded(ctx, [&] { tucker_pipeline(true, X, xt, d, dims, ranks, oversample, seed, flags, out); });
+}
+
+krp_status krp_split_bf16x2(krp_ctx ctx, const float* X, int64_t n, void* out) {
+  return guarded(ctx, [&] {
+    KRP_REQUIRE(X && out && n >= 0, "bad arguments");
+    KRP_REQUIRE(is_device_ptr(X) && is_device_ptr(out), "X and out must be device pointers");
+    KRP_REQUIRE((reinterpret_cast<uintptr_t>(out) & 15) == 0, "out must be 16-byte aligned");
+    split_f32_bf16x2(X, n, static_cast<__nv_bfloat16*>(out));
+  });
 }
 
 krp_status krp_tucker_rhosvd_batched(krp_ctx ctx, krp_dtype xt, int count, krp_tucker_item* items,

@@ -59,11 +59,14 @@ void big_mttkrp_first(const void* X, krp_dtype xt, int64_t n1, int d_rest,
                       const int64_t* rest_dims, const void* const* rest_V, int L, float* Y);
 
 // tcgen05 kernels (tc_kernels.cu)
+// Xlo (optional): lo plane of X given as a BF16 hi/lo pair (X ~ X + Xlo)
 void tc_gemm_tn_bf16(const __nv_bfloat16* X, int64_t n1, int64_t S, const __nv_bfloat16* Fhi,
-                     const __nv_bfloat16* Flo, int L, float* out);
+                     const __nv_bfloat16* Flo, int L, float* out,
+                     const __nv_bfloat16* Xlo = nullptr);
 // Y[i + n1*k] = sum_t w[t + T*k] sum_{i2} X[i + n1*(i2 + n2*t)] Om2[i2 + n2*k]
 void tc_mttkrp_first_bf16(const __nv_bfloat16* X, int64_t n1, int64_t n2, int64_t T,
-                          const __nv_bfloat16* Om2, const float* w, int L, float* Y);
+                          const __nv_bfloat16* Om2, const float* w, int L, float* Y,
+                          const __nv_bfloat16* Xlo = nullptr);
 size_t tc_workspace_bytes(int64_t n1, int64_t S, int L);
 // acc[0] += ||X - Q1 H||^2, acc[1] += ||X||^2 for BF16 X (n1 x S), Q1 FP64
 // n1 x c, H FP32 c x S, on tensor cores (c <= 64, n1 % 8 == 0)
@@ -77,11 +80,13 @@ void tc_tree_bf16(const __nv_bfloat16* X, int64_t n1, int64_t n2, int64_t T,
 bool tc_residual_supported(int64_t n1, int c);
 size_t tc_residual_workspace_bytes(int64_t n1, int64_t S);
 void tc_residual_bf16(const __nv_bfloat16* X, int64_t n1, int64_t S, const double* Q1, int c,
-                      const float* H, double* acc);
+                      const float* H, double* acc, const __nv_bfloat16* Xlo = nullptr);
 
 // weights w[t + T*k] = prod_j V_j[digit_j(t) + r_j*k] (bf16 or f32 factors)
 void krp_rows(const Radix& R, int64_t T, int L, bool bf16, float* w);
 void split_bf16_hilo(const double* src, int64_t n, __nv_bfloat16* hi, __nv_bfloat16* lo);
 void convert_bf16_to_f32(const __nv_bfloat16* src, float* dst, int64_t n);
+// out[e] = bf16(x), out[n + e] = bf16(x - bf16(x))
+void split_f32_bf16x2(const float* X, int64_t n, __nv_bfloat16* out);
 
 }  // namespace krp

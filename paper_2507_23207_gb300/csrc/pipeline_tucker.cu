@@ -50,6 +50,16 @@ __global__ void split_hilo_kernel(const double* __restrict__ s, int64_t n,
   }
 }
 
+__global__ void split_x2_kernel(const float* __restrict__ X, int64_t n, __nv_bfloat16* __restrict__ out) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const float x = X[e];
+    const __nv_bfloat16 h = __float2bfloat16_rn(x);
+    out[e] = h;
+    out[n + e] = __float2bfloat16_rn(x - __bfloat162float(h));
+  }
+}
+
 __global__ void bf16_to_f32_kernel(const __nv_bfloat16* __restrict__ s, float* __restrict__ d,
                                    int64_t n) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
@@ -116,6 +126,12 @@ void split_bf16_hilo(const double* src, int64_t n, __nv_bfloat16* hi, __nv_bfloa
   check_launch("split_bf16_hilo");
 }
 
+void split_f32_bf16x2(const float* X, int64_t n, __nv_bfloat16* out) {
+  if (n <= 0) return;
+  split_x2_kernel<<<grid_of(n), 256, 0, stream()>>>(X, n, out);
+  check_launch("split_bf16x2");
+}
+
 void convert_bf16_to_f32(const __nv_bfloat16* src, float* dst, int64_t n) {
   if (n <= 0) return;
   bf16_to_f32_kernel<<<grid_of(n), 256, 0, stream()>>>(src, dst, n);
@@ -123,12 +139,19 @@ void convert_bf16_to_f32(const __nv_bfloat16* src, float* dst, int64_t n) {
 }
 
 // ------------------------------------------------------------- dispatch ----
+// BF16 hi/lo input: the lo plane follows the hi plane (N elements later)
+static const __nv_bfloat16* lo_plane(const void* X, krp_dtype xt, int64_t N) {
+  return xt == KRP_BF16X2 ? static_cast<const __nv_bfloat16*>(X) + N : nullptr;
+}
+static bool bf16_family(krp_dtype t) { return t == KRP_BF16 || t == KRP_BF16X2; }
+
 void big_gemm_tn(const void* X, krp_dtype xt, int64_t n1, int64_t S, const float* Ff,
                  const __nv_bfloat16* Fhi, const __nv_bfloat16* Flo, int L, float* out) {
   if (xt == KRP_F32) {
     gemm_tn_f32(static_cast<const float*>(X), n1, S, (int)n1, Ff, n1, L, out, S, false);
   } else {
-    tc_gemm_tn_bf16(static_cast<const __nv_bfloat16*>(X), n1, S, Fhi, Flo, L, out);
+    tc_gemm_tn_bf16(static_cast<const __nv_bfloat16*>(X), n1, S, Fhi, Flo, L, out,
+                    lo_plane(X, xt, n1 * S));
   }
 }
 
@@ -157,7 +180,8 @@ void big_mttkrp_first(const void* X, krp_dtype xt, int64_t n1, int d_rest, const
     krp_rows(R, T, L, true, w);
     KRP_REQUIRE(d_rest >= 1, "BF16 sketch needs d >= 2");
     tc_mttkrp_first_bf16(static_cast<const __nv_bfloat16*>(X), n1, n2, T,
-                         static_cast<const __nv_bfloat16*>(rest_V[0]), w, L, Y);
+                         static_cast<const __nv_bfloat16*>(rest_V[0]), w, L, Y,
+                         lo_plane(X, xt, n1 * S));
   }
 }
 
@@ -170,8 +194,9 @@ SketchArgs validate_sketch(const void* X, krp_dtype xt, int d, const int64_t* di
   KRP_REQUIRE(X, "X is NULL");
   KRP_REQUIRE(omega, "omega is NULL");
   KRP_REQUIRE(ell >= 1 && ell <= 256, "ell = %d out of range 1..256", ell);
-  KRP_REQUIRE(xt == KRP_F32 || xt == KRP_BF16, "X dtype must be KRP_F32 or KRP_BF16");
-  KRP_REQUIRE(omt == xt, "factor dtype must equal the X dtype (F32 with F32, BF16 with BF16)");
+  KRP_REQUIRE(xt == KRP_F32 || bf16_family(xt), "X dtype must be KRP_F32, KRP_BF16 or KRP_BF16X2");
+  KRP_REQUIRE(omt == (xt == KRP_BF16X2 ? KRP_BF16 : xt),
+              "factor dtype must match X (F32 with F32, BF16 with BF16 or BF16X2)");
   a.X = X;
   a.xt = xt;
   a.d = d;
@@ -192,7 +217,7 @@ size_t sketch_workspace_bytes(const SketchArgs& a, bool) {
   int64_t dmax = 1;
   for (int j = 0; j < a.d; ++j) dmax = std::max<int64_t>(dmax, a.dims[j]);
   b += mttkrp_first_f32_workspace_bytes(a.N / std::max<int64_t>(1, a.dims[0]), dmax);
-  if (a.xt == KRP_BF16) b += tc_workspace_bytes(n1, a.N / n1, a.ell);
+  if (bf16_family(a.xt)) b += tc_workspace_bytes(n1, a.N / n1, a.ell);
   return b + (1 << 20);
 }
 
@@ -265,7 +290,7 @@ size_t multi_ttm_workspace_bytes(int d, const int64_t* dims, const int* cols, kr
   size_t big = (size_t)(N / dims[0]) * cols[0];
   size_t b = 2 * ws_bytes(big, 4);
   for (int j = 0; j < d; ++j) b += ws_bytes((size_t)dims[j] * cols[j], 4 + 2 + 2);
-  if (xt == KRP_BF16) b += tc_workspace_bytes(dims[0], N / dims[0], 2 * cols[0]);
+  if (bf16_family(xt)) b += tc_workspace_bytes(dims[0], N / dims[0], 2 * cols[0]);
   return b + (1 << 20);
 }
 
@@ -280,7 +305,7 @@ void multi_ttm(const void* X, krp_dtype xt, int d, const int64_t* dims, const do
     Qf[j] = c->ws.take<float>((size_t)dims[j] * cols[j]);
     cast_f64_to_f32(Q[j], Qf[j], dims[j] * cols[j]);
   }
-  if (xt == KRP_BF16) {
+  if (bf16_family(xt)) {
     Qh = c->ws.take<__nv_bfloat16>((size_t)n1 * cols[0]);
     Ql = c->ws.take<__nv_bfloat16>((size_t)n1 * cols[0]);
     split_bf16_hilo(Q[0], n1 * cols[0], Qh, Ql);
@@ -308,7 +333,7 @@ void tucker_pipeline(bool sequential, const void* X, krp_dtype xt, int d, const 
   KRP_REQUIRE(d >= 2 && d <= KRP_MAXD, "d = %d out of range 2..%d", d, KRP_MAXD);
   const int64_t N = checked_numel(d, dims);
   KRP_REQUIRE(X && ranks && out, "NULL argument");
-  KRP_REQUIRE(xt == KRP_F32 || xt == KRP_BF16, "X dtype must be KRP_F32 or KRP_BF16");
+  KRP_REQUIRE(xt == KRP_F32 || bf16_family(xt), "X dtype must be KRP_F32, KRP_BF16 or KRP_BF16X2");
   KRP_REQUIRE(oversample >= 0, "oversample must be >= 0");
   KRP_REQUIRE((flags & ~0xFu) == 0, "unknown flag bits 0x%x", flags);
   const bool memo = (flags & KRP_MEMO) && !sequential;
@@ -351,8 +376,8 @@ void tucker_pipeline(bool sequential, const void* X, krp_dtype xt, int d, const 
     core_l *= ell[i];
   }
   need += 4 * ws_bytes((size_t)core_l, 8) + 2 * ws_bytes((size_t)core_l, 4);
-  if (xt == KRP_BF16) need += tc_workspace_bytes(dims[0], N / dims[0], 2 * ellmax);
-  if (xt == KRP_BF16 && resid) need += tc_residual_workspace_bytes(dims[0], N / dims[0]);
+  if (bf16_family(xt)) need += tc_workspace_bytes(dims[0], N / dims[0], 2 * ellmax);
+  if (bf16_family(xt) && resid) need += tc_residual_workspace_bytes(dims[0], N / dims[0]);
   need += 4 << 20;
   ensure_workspace(c, need);
   Workspace& ws = c->ws;
@@ -386,7 +411,9 @@ void tucker_pipeline(bool sequential, const void* X, krp_dtype xt, int d, const 
     }
     qr_householder_f64(jobs.data(), cnt, c->d_status);
   };
-  const krp_dtype ft = xt;  // factor dtype for contractions over X
+  // factor dtype for contractions over X (a BF16 hi/lo X takes BF16 factors:
+  // a random matrix needs no more than BF16 values, only X does)
+  const krp_dtype ft = xt == KRP_BF16X2 ? KRP_BF16 : xt;
   const size_t fb = dtype_size(ft);
 
   if (!sequential) {
@@ -443,7 +470,7 @@ void tucker_pipeline(bool sequential, const void* X, krp_dtype xt, int d, const 
     float* pp[2] = {ws.take<float>(big), ws.take<float>(big)};
     for (int i = 0; i < d; ++i) {
       const int64_t ni = dims[i];
-      const krp_dtype sft = ct;  // factors in the dtype of the tensor sketched
+      const krp_dtype sft = ct == KRP_BF16X2 ? KRP_BF16 : ct;  // factors for the tensor sketched
       const size_t sfb = dtype_size(sft);
       void* fac[KRP_MAXD] = {};
       FactorJob jobs[KRP_MAXD];
@@ -471,7 +498,7 @@ void tucker_pipeline(bool sequential, const void* X, krp_dtype xt, int d, const 
       float* Qf = ws.take<float>((size_t)ni * ell[i]);
       cast_f64_to_f32(Q[i], Qf, ni * ell[i]);
       __nv_bfloat16 *Qh = nullptr, *Ql = nullptr;
-      if (ct == KRP_BF16) {
+      if (bf16_family(ct)) {
         Qh = ws.take<__nv_bfloat16>((size_t)ni * ell[i]);
         Ql = ws.take<__nv_bfloat16>((size_t)ni * ell[i]);
         split_bf16_hilo(Q[i], ni * ell[i], Qh, Ql);
@@ -554,9 +581,11 @@ void tucker_pipeline(bool sequential, const void* X, krp_dtype xt, int d, const 
       curh = nx;
     }
     KRP_CUDA_CHECK(cudaMemsetAsync(acc, 0, 2 * sizeof(double), c->stream));
-    if (xt == KRP_BF16 && tc_residual_supported(dims[0], (int)cdim[0]))
+    if (bf16_family(xt) && tc_residual_supported(dims[0], (int)cdim[0]))
       tc_residual_bf16(static_cast<const __nv_bfloat16*>(Xd), dims[0], N / dims[0], Qout[0],
-                       (int)cdim[0], curh, acc);
+                       (int)cdim[0], curh, acc, lo_plane(Xd, xt, N));
+    else if (xt == KRP_BF16X2)
+      fail(KRP_EUNSUPPORTED, "BF16 hi/lo residual needs n_1 %% 8 == 0 and at most 64 columns");
     else
       residual_f32(Xd, xt, dims[0], N / dims[0], Q1f, (int)cdim[0], curh, acc);
   }

@@ -184,14 +184,19 @@ __device__ void drain_loads(Bars* b) {
 // out[s + S*k] = sum_i X[i + n1*s] F[i, k] (+ lo part at column Lp + k)
 // A tile: 128 rows (s) x 64 K (i), box of mapA = {64, 128}.  B: mapB over the
 // combined factor buffer (K = n1p contiguous, rows = N columns of F).
-template <int N, int NS>
+// XLO: X is given as a BF16 hi/lo pair (second map mapAlo over the lo
+// plane); its lo tile is multiplied by the hi columns of F into the same
+// accumulator (X F ~ Xh [Fh|Fl] + Xl Fh, dropping Xl Fl, below 2^-16).
+template <int N, int NS, bool XLO>
 __global__ void __launch_bounds__(kThreads, 1)
     tc_gemm_tn_kernel(const __grid_constant__ CUtensorMap mapA,
+                      const __grid_constant__ CUtensorMap mapAlo,
                       const __grid_constant__ CUtensorMap mapB, int64_t S, int kchunks, int L,
                       int Lp, int has_lo, float* __restrict__ out, int* status) {
   constexpr uint32_t kABytes = kBM * kBK * 2;  // 16 KB
+  constexpr uint32_t kANum = XLO ? 2 : 1;
   constexpr uint32_t kBBytes = N * kBK * 2;
-  constexpr uint32_t kStage = kABytes + kBBytes;
+  constexpr uint32_t kStage = kANum * kABytes + kBBytes;
   constexpr uint32_t kTmemCols = (2 * N <= 32) ? 32 : (2 * N <= 64) ? 64 : (2 * N <= 128) ? 128 : (2 * N <= 256) ? 256 : 512;
   constexpr uint32_t kIdesc = idesc_bf16(kBM, N, false, false);
   extern __shared__ uint8_t smem_raw[];
@@ -222,6 +227,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   tc_fence_after();
   const uint32_t tmem = bars->tmem_base;
   volatile int* abort_flag = &bars->abort_flag;
+  const uint32_t idesc_lo = idesc_bf16(kBM, Lp, false, false);
 
   if (warp == 0) {
     if (lane == 0) {
@@ -238,7 +244,8 @@ __global__ void __launch_bounds__(kThreads, 1)
           const uint32_t fb = smem_u32(&bars->full[st]);
           mbar_expect_tx(fb, kStage);
           tma_load_2d(a, &mapA, fb, kc * kBK, static_cast<int>(tile * kBM));
-          tma_load_2d(a + kABytes, &mapB, fb, kc * kBK, 0);
+          if (XLO) tma_load_2d(a + kABytes, &mapAlo, fb, kc * kBK, static_cast<int>(tile * kBM));
+          tma_load_2d(a + kANum * kABytes, &mapB, fb, kc * kBK, 0);
           bars->issued = it + 1;
         }
       }
@@ -266,11 +273,15 @@ __global__ void __launch_bounds__(kThreads, 1)
           }
           tc_fence_after();
           const uint32_t a = smem_u32(smem + st * kStage);
-          const uint32_t b = a + kABytes;
+          const uint32_t b = a + kANum * kABytes;
 #pragma unroll
-          for (int k = 0; k < kBK / 16; ++k)
+          for (int k = 0; k < kBK / 16; ++k) {
             mma_bf16(dt, sdesc(a + 32 * k, 16, 1024), sdesc(b + 32 * k, 16, 1024), kIdesc,
                      (kc | k) != 0);
+            if (XLO)  // Xl times the hi columns of F (the first Lp rows of B)
+              mma_bf16(dt, sdesc(a + kABytes + 32 * k, 16, 1024), sdesc(b + 32 * k, 16, 1024),
+                       idesc_lo, 1);
+          }
           mma_commit(smem_u32(&bars->empty[st]));
           bars->consumed = it + 1;
         }
@@ -328,14 +339,18 @@ __global__ void __launch_bounds__(kThreads, 1)
 // ----------------------------------------------------------------------------
 // Y[i + n1*k] += sum_{t in range} w[t + T*k] * D_t[i, k],
 // D_t[i, k] = sum_{i2} X[i, i2, t] Om2[i2, k]   (MN-major A, two 64-row boxes)
-template <int N, int NS>
+// XLO: X as a BF16 hi/lo pair; the lo boxes (map mapXlo) are multiplied by
+// the same B into the same accumulator.
+template <int N, int NS, bool XLO>
 __global__ void __launch_bounds__(kThreads, 1)
     tc_mttkrp_kernel(const __grid_constant__ CUtensorMap mapX,
+                     const __grid_constant__ CUtensorMap mapXlo,
                      const __grid_constant__ CUtensorMap mapB, int64_t n1, int64_t T, int kchunks,
                      int mblocks, int64_t t_per_cta, const float* __restrict__ w, int L,
                      float* __restrict__ Y, int* status) {
   constexpr uint32_t kBox = 64 * kBK * 2;  // 64 (i) x 64 (i2) BF16 = 8 KB
-  constexpr uint32_t kABytes = 2 * kBox;
+  constexpr uint32_t kAHi = 2 * kBox;
+  constexpr uint32_t kABytes = (XLO ? 2 : 1) * kAHi;
   constexpr uint32_t kBBytes = N * kBK * 2;
   constexpr uint32_t kStage = kABytes + kBBytes;
   constexpr uint32_t kTmemCols = (2 * N <= 32) ? 32 : (2 * N <= 64) ? 64 : (2 * N <= 128) ? 128 : (2 * N <= 256) ? 256 : 512;
@@ -387,6 +402,10 @@ __global__ void __launch_bounds__(kThreads, 1)
           mbar_expect_tx(fb, kStage);
           tma_load_3d(a, &mapX, fb, mb * kBM, kc * kBK, static_cast<int>(t));
           tma_load_3d(a + kBox, &mapX, fb, mb * kBM + 64, kc * kBK, static_cast<int>(t));
+          if (XLO) {
+            tma_load_3d(a + kAHi, &mapXlo, fb, mb * kBM, kc * kBK, static_cast<int>(t));
+            tma_load_3d(a + kAHi + kBox, &mapXlo, fb, mb * kBM + 64, kc * kBK, static_cast<int>(t));
+          }
           tma_load_2d(a + kABytes, &mapB, fb, kc * kBK, 0);
           bars->issued = it + 1;
         }
@@ -419,9 +438,13 @@ __global__ void __launch_bounds__(kThreads, 1)
           // A (MN-major): 8-row K groups 1024 B apart, the two 64-wide M atoms
           // kBox apart; each MMA (K = 16) spans two K groups.
 #pragma unroll
-          for (int k = 0; k < kBK / 16; ++k)
+          for (int k = 0; k < kBK / 16; ++k) {
             mma_bf16(dt, sdesc(a + 2048 * k, kBox, 1024), sdesc(b + 32 * k, 16, 1024), kIdesc,
                      (kc | k) != 0);
+            if (XLO)
+              mma_bf16(dt, sdesc(a + kAHi + 2048 * k, kBox, 1024), sdesc(b + 32 * k, 16, 1024),
+                       kIdesc, 1);
+          }
           mma_commit(smem_u32(&bars->empty[st]));
           bars->consumed = it + 1;
         }
@@ -743,18 +766,24 @@ __global__ void __launch_bounds__(320, 1)
 // is below 2^-16 relative), and the epilogue compares it with the X tile that
 // TMA placed in the same pipeline stage.  A stage is released when both the
 // MMAs (tcgen05.commit) and the four epilogue warps are done with it.
-constexpr int kResN = 128;
-
+// RN: columns s per tile (128; 64 when X is a hi/lo pair, XLO, whose two
+// extra X boxes per stage would not fit twice otherwise).  With XLO the X
+// value in the epilogue is hi + lo.
+template <int RN, bool XLO>
 __global__ void __launch_bounds__(kThreads, 1)
     tc_residual_kernel(const __grid_constant__ CUtensorMap mapX,
+                       const __grid_constant__ CUtensorMap mapXlo,
                        const __grid_constant__ CUtensorMap mapQ,
                        const __grid_constant__ CUtensorMap mapH, int64_t n1, int64_t S,
                        int mblocks, double* __restrict__ acc, int* status) {
+  constexpr int kResN = RN;
   constexpr int NS = 2;
-  constexpr uint32_t kOp = 128 * 128;       // one 128-row x 64-element BF16 operand tile
-  constexpr uint32_t kXBox = 64 * kResN * 2;  // 64 (i) x 128 (s) BF16 = 16 KB
-  constexpr uint32_t kStage = 4 * kOp + 2 * kXBox;  // Qh Ql Hh Hl + two X boxes = 96 KB
-  constexpr uint32_t kTmemCols = 256;
+  constexpr uint32_t kOp = 128 * 128;       // one 128-row x 64-element BF16 operand tile (Q)
+  constexpr uint32_t kOpH = RN * 128;       // one RN-row x 64-element BF16 operand tile (H)
+  constexpr uint32_t kXBox = 64 * kResN * 2;  // 64 (i) x RN (s) BF16
+  constexpr uint32_t kXNum = XLO ? 4 : 2;
+  constexpr uint32_t kStage = 2 * kOp + 2 * kOpH + kXNum * kXBox;  // Qh Ql Hh Hl + X boxes
+  constexpr uint32_t kTmemCols = 2 * RN;
   constexpr uint32_t kIdesc = idesc_bf16(kBM, kResN, false, false);
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -801,12 +830,17 @@ __global__ void __launch_bounds__(kThreads, 1)
         const uint32_t a = smem_u32(smem + st * kStage);
         const uint32_t fb = smem_u32(&bars->full[st]);
         mbar_expect_tx(fb, kStage);
-        tma_load_2d(a + 0 * kOp, &mapQ, fb, 0, mb * kBM);            // Qh
-        tma_load_2d(a + 1 * kOp, &mapQ, fb, 64, mb * kBM);           // Ql
-        tma_load_2d(a + 2 * kOp, &mapH, fb, 0, sb * kResN);          // Hh
-        tma_load_2d(a + 3 * kOp, &mapH, fb, 64, sb * kResN);         // Hl
-        tma_load_2d(a + 4 * kOp, &mapX, fb, mb * kBM, sb * kResN);   // X, i 0..63
-        tma_load_2d(a + 4 * kOp + kXBox, &mapX, fb, mb * kBM + 64, sb * kResN);  // i 64..127
+        const uint32_t xo = 2 * kOp + 2 * kOpH;
+        tma_load_2d(a + 0 * kOp, &mapQ, fb, 0, mb * kBM);              // Qh
+        tma_load_2d(a + 1 * kOp, &mapQ, fb, 64, mb * kBM);             // Ql
+        tma_load_2d(a + 2 * kOp, &mapH, fb, 0, sb * kResN);            // Hh
+        tma_load_2d(a + 2 * kOp + kOpH, &mapH, fb, 64, sb * kResN);    // Hl
+        tma_load_2d(a + xo, &mapX, fb, mb * kBM, sb * kResN);          // X, i 0..63
+        tma_load_2d(a + xo + kXBox, &mapX, fb, mb * kBM + 64, sb * kResN);  // i 64..127
+        if (XLO) {
+          tma_load_2d(a + xo + 2 * kXBox, &mapXlo, fb, mb * kBM, sb * kResN);
+          tma_load_2d(a + xo + 3 * kXBox, &mapXlo, fb, mb * kBM + 64, sb * kResN);
+        }
         bars->issued = it + 1;
       }
     }
@@ -826,7 +860,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         tc_fence_after();
         const uint32_t a = smem_u32(smem + st * kStage);
         const uint32_t dt = tmem + accb * kResN;
-        const uint32_t qh = a, ql = a + kOp, hh = a + 2 * kOp, hl = a + 3 * kOp;
+        const uint32_t qh = a, ql = a + kOp, hh = a + 2 * kOp, hl = a + 2 * kOp + kOpH;
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
           mma_bf16(dt, sdesc(qh + 32 * k, 16, 1024), sdesc(hh + 32 * k, 16, 1024), kIdesc, k != 0);
@@ -859,7 +893,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       tc_fence_after();
       // X tile: box (row / 64), smem row s holds 64 i values (128 B), 16-byte
       // chunks swizzled by (s mod 8)
-      const uint8_t* xb = smem + st * kStage + 4 * kOp + (row >> 6) * kXBox;
+      const uint8_t* xb = smem + st * kStage + 2 * kOp + 2 * kOpH + (row >> 6) * kXBox;
       const int ii = row & 63;
       const uint32_t base = tmem + (static_cast<uint32_t>(q * 32) << 16) + accb * kResN;
       float d2 = 0.f, x2 = 0.f;
@@ -871,9 +905,9 @@ __global__ void __launch_bounds__(kThreads, 1)
         for (int j = 0; j < 16; ++j) {
           const int s = c0 + j;
           const int chunk = (ii >> 3) ^ (s & 7);
-          const __nv_bfloat16 xv =
-              *reinterpret_cast<const __nv_bfloat16*>(xb + s * 128 + chunk * 16 + (ii & 7) * 2);
-          const float x = __bfloat162float(xv);
+          const int off = s * 128 + chunk * 16 + (ii & 7) * 2;
+          float x = __bfloat162float(*reinterpret_cast<const __nv_bfloat16*>(xb + off));
+          if (XLO) x += __bfloat162float(*reinterpret_cast<const __nv_bfloat16*>(xb + 2 * kXBox + off));
           const float df = x - v[j];
           d2 = fmaf(df, df, d2);
           x2 = fmaf(x, x, x2);
@@ -982,24 +1016,29 @@ void set_smem(K kernel, size_t bytes) {
 }
 
 template <int N>
-void launch_gemm_tn(const CUtensorMap& ma, const CUtensorMap& mb, int64_t S, int kchunks, int L,
-                    int Lp, int has_lo, float* out) {
-  constexpr int NS = (N <= 64) ? 8 : (N <= 128 ? 6 : 4);
-  const size_t smem = 1024 + NS * (size_t)(kBM * kBK * 2 + N * kBK * 2) + sizeof(Bars) + 64;
-  set_smem(tc_gemm_tn_kernel<N, NS>, smem);
+void launch_gemm_tn(const CUtensorMap& ma, const CUtensorMap* malo, const CUtensorMap& mb, int64_t S,
+                    int kchunks, int L, int Lp, int has_lo, float* out) {
   const int64_t tiles = (S + kBM - 1) / kBM;
   const int grid = static_cast<int>(std::min<int64_t>(tiles, current()->num_sms));
-  tc_gemm_tn_kernel<N, NS><<<grid, kThreads, smem, stream()>>>(ma, mb, S, kchunks, L, Lp, has_lo, out,
-                                                               current()->d_status);
+  if (!malo) {
+    constexpr int NS = (N <= 64) ? 8 : (N <= 128 ? 6 : 4);
+    const size_t smem = 1024 + NS * (size_t)(kBM * kBK * 2 + N * kBK * 2) + sizeof(Bars) + 64;
+    set_smem(tc_gemm_tn_kernel<N, NS, false>, smem);
+    tc_gemm_tn_kernel<N, NS, false><<<grid, kThreads, smem, stream()>>>(
+        ma, ma, mb, S, kchunks, L, Lp, has_lo, out, current()->d_status);
+  } else {
+    constexpr int NS = (N <= 64) ? 5 : (N <= 128 ? 4 : 3);
+    const size_t smem = 1024 + NS * (size_t)(2 * kBM * kBK * 2 + N * kBK * 2) + sizeof(Bars) + 64;
+    set_smem(tc_gemm_tn_kernel<N, NS, true>, smem);
+    tc_gemm_tn_kernel<N, NS, true><<<grid, kThreads, smem, stream()>>>(
+        ma, *malo, mb, S, kchunks, L, Lp, has_lo, out, current()->d_status);
+  }
   check_launch("tc_gemm_tn_bf16");
 }
 
 template <int N>
-void launch_mttkrp(const CUtensorMap& mx, const CUtensorMap& mb, int64_t n1, int64_t T, int kchunks,
-                   const float* w, int L, float* Y) {
-  constexpr int NS = (N <= 64) ? 8 : 6;
-  const size_t smem = 1024 + NS * (size_t)(2 * 64 * kBK * 2 + N * kBK * 2) + sizeof(Bars) + 64;
-  set_smem(tc_mttkrp_kernel<N, NS>, smem);
+void launch_mttkrp(const CUtensorMap& mx, const CUtensorMap* mxlo, const CUtensorMap& mb, int64_t n1,
+                   int64_t T, int kchunks, const float* w, int L, float* Y) {
   const int mblocks = static_cast<int>((n1 + kBM - 1) / kBM);
   const int sms = current()->num_sms;
   int64_t chunks = std::max<int64_t>(1, sms / mblocks);
@@ -1007,8 +1046,19 @@ void launch_mttkrp(const CUtensorMap& mx, const CUtensorMap& mb, int64_t n1, int
   const int64_t per = (T + chunks - 1) / chunks;
   chunks = (T + per - 1) / per;
   const int grid = static_cast<int>(mblocks * chunks);
-  tc_mttkrp_kernel<N, NS><<<grid, kThreads, smem, stream()>>>(mx, mb, n1, T, kchunks, mblocks, per,
-                                                              w, L, Y, current()->d_status);
+  if (!mxlo) {
+    constexpr int NS = (N <= 64) ? 8 : 6;
+    const size_t smem = 1024 + NS * (size_t)(2 * 64 * kBK * 2 + N * kBK * 2) + sizeof(Bars) + 64;
+    set_smem(tc_mttkrp_kernel<N, NS, false>, smem);
+    tc_mttkrp_kernel<N, NS, false><<<grid, kThreads, smem, stream()>>>(
+        mx, mx, mb, n1, T, kchunks, mblocks, per, w, L, Y, current()->d_status);
+  } else {
+    constexpr int NS = (N <= 64) ? 5 : 4;
+    const size_t smem = 1024 + NS * (size_t)(4 * 64 * kBK * 2 + N * kBK * 2) + sizeof(Bars) + 64;
+    set_smem(tc_mttkrp_kernel<N, NS, true>, smem);
+    tc_mttkrp_kernel<N, NS, true><<<grid, kThreads, smem, stream()>>>(
+        mx, *mxlo, mb, n1, T, kchunks, mblocks, per, w, L, Y, current()->d_status);
+  }
   check_launch("tc_mttkrp_bf16");
 }
 
@@ -1024,7 +1074,7 @@ size_t tc_workspace_bytes(int64_t n1, int64_t S, int L) {
 }
 
 void tc_gemm_tn_bf16(const __nv_bfloat16* X, int64_t n1, int64_t S, const __nv_bfloat16* Fhi,
-                     const __nv_bfloat16* Flo, int L, float* out) {
+                     const __nv_bfloat16* Flo, int L, float* out, const __nv_bfloat16* Xlo) {
   KRP_REQUIRE(n1 % 8 == 0, "BF16 tensor-core path needs n_1 %% 8 == 0 (n_1 = %lld)", (long long)n1);
   KRP_REQUIRE((reinterpret_cast<uintptr_t>(X) & 15) == 0, "X must be 16-byte aligned");
   KRP_REQUIRE(S < (int64_t(1) << 31), "too many rows for the TMA coordinates");
@@ -1042,6 +1092,13 @@ void tc_gemm_tn_bf16(const __nv_bfloat16* X, int64_t n1, int64_t S, const __nv_b
   const uint64_t astr[1] = {(uint64_t)n1 * 2};
   const uint32_t abox[2] = {kBK, kBM};
   const CUtensorMap ma = make_map(X, 2, adims, astr, abox);
+  CUtensorMap malo_v;
+  const CUtensorMap* malo = nullptr;
+  if (Xlo) {
+    KRP_REQUIRE((reinterpret_cast<uintptr_t>(Xlo) & 15) == 0, "X lo plane must be 16-byte aligned");
+    malo_v = make_map(Xlo, 2, adims, astr, abox);
+    malo = &malo_v;
+  }
   const uint64_t bdims[2] = {(uint64_t)n1p, (uint64_t)N};
   const uint64_t bstr[1] = {(uint64_t)n1p * 2};
   const uint32_t bbox[2] = {kBK, (uint32_t)N};
@@ -1049,23 +1106,23 @@ void tc_gemm_tn_bf16(const __nv_bfloat16* X, int64_t n1, int64_t S, const __nv_b
   const int kchunks = static_cast<int>((n1 + kBK - 1) / kBK);
   const int has_lo = Flo ? 1 : 0;
   switch (N) {
-    case 16: launch_gemm_tn<16>(ma, mb, S, kchunks, L, Lp, has_lo, out); break;
-    case 32: launch_gemm_tn<32>(ma, mb, S, kchunks, L, Lp, has_lo, out); break;
-    case 48: launch_gemm_tn<48>(ma, mb, S, kchunks, L, Lp, has_lo, out); break;
-    case 64: launch_gemm_tn<64>(ma, mb, S, kchunks, L, Lp, has_lo, out); break;
-    case 96: launch_gemm_tn<96>(ma, mb, S, kchunks, L, Lp, has_lo, out); break;
-    case 128: launch_gemm_tn<128>(ma, mb, S, kchunks, L, Lp, has_lo, out); break;
-    case 160: launch_gemm_tn<160>(ma, mb, S, kchunks, L, Lp, has_lo, out); break;
-    case 192: launch_gemm_tn<192>(ma, mb, S, kchunks, L, Lp, has_lo, out); break;
-    case 224: launch_gemm_tn<224>(ma, mb, S, kchunks, L, Lp, has_lo, out); break;
-    case 256: launch_gemm_tn<256>(ma, mb, S, kchunks, L, Lp, has_lo, out); break;
+    case 16: launch_gemm_tn<16>(ma, malo, mb, S, kchunks, L, Lp, has_lo, out); break;
+    case 32: launch_gemm_tn<32>(ma, malo, mb, S, kchunks, L, Lp, has_lo, out); break;
+    case 48: launch_gemm_tn<48>(ma, malo, mb, S, kchunks, L, Lp, has_lo, out); break;
+    case 64: launch_gemm_tn<64>(ma, malo, mb, S, kchunks, L, Lp, has_lo, out); break;
+    case 96: launch_gemm_tn<96>(ma, malo, mb, S, kchunks, L, Lp, has_lo, out); break;
+    case 128: launch_gemm_tn<128>(ma, malo, mb, S, kchunks, L, Lp, has_lo, out); break;
+    case 160: launch_gemm_tn<160>(ma, malo, mb, S, kchunks, L, Lp, has_lo, out); break;
+    case 192: launch_gemm_tn<192>(ma, malo, mb, S, kchunks, L, Lp, has_lo, out); break;
+    case 224: launch_gemm_tn<224>(ma, malo, mb, S, kchunks, L, Lp, has_lo, out); break;
+    case 256: launch_gemm_tn<256>(ma, malo, mb, S, kchunks, L, Lp, has_lo, out); break;
     default:
-      if (N == 80) launch_gemm_tn<80>(ma, mb, S, kchunks, L, Lp, has_lo, out);
-      else if (N == 112) launch_gemm_tn<112>(ma, mb, S, kchunks, L, Lp, has_lo, out);
-      else if (N == 144) launch_gemm_tn<144>(ma, mb, S, kchunks, L, Lp, has_lo, out);
-      else if (N == 176) launch_gemm_tn<176>(ma, mb, S, kchunks, L, Lp, has_lo, out);
-      else if (N == 208) launch_gemm_tn<208>(ma, mb, S, kchunks, L, Lp, has_lo, out);
-      else if (N == 240) launch_gemm_tn<240>(ma, mb, S, kchunks, L, Lp, has_lo, out);
+      if (N == 80) launch_gemm_tn<80>(ma, malo, mb, S, kchunks, L, Lp, has_lo, out);
+      else if (N == 112) launch_gemm_tn<112>(ma, malo, mb, S, kchunks, L, Lp, has_lo, out);
+      else if (N == 144) launch_gemm_tn<144>(ma, malo, mb, S, kchunks, L, Lp, has_lo, out);
+      else if (N == 176) launch_gemm_tn<176>(ma, malo, mb, S, kchunks, L, Lp, has_lo, out);
+      else if (N == 208) launch_gemm_tn<208>(ma, malo, mb, S, kchunks, L, Lp, has_lo, out);
+      else if (N == 240) launch_gemm_tn<240>(ma, malo, mb, S, kchunks, L, Lp, has_lo, out);
       else fail(KRP_EUNSUPPORTED, "unsupported MMA width %d", N);
   }
 }
@@ -1138,10 +1195,30 @@ size_t tc_residual_workspace_bytes(int64_t n1, int64_t S) {
 
 bool tc_residual_supported(int64_t n1, int c) { return n1 % 8 == 0 && c >= 1 && c <= 64; }
 
+template <int RN, bool XLO>
+void launch_residual(const CUtensorMap& mx, const CUtensorMap& mxlo, const CUtensorMap& mq,
+                     const __nv_bfloat16* Hp, int64_t n1, int64_t S, double* acc) {
+  Ctx* ctx = current();
+  const uint64_t hd[2] = {128, (uint64_t)S};
+  const uint64_t hs[1] = {256};
+  const uint32_t hbox[2] = {64, RN};
+  const CUtensorMap mh = make_map(Hp, 2, hd, hs, hbox);
+  const int mblocks = static_cast<int>((n1 + kBM - 1) / kBM);
+  const int64_t tiles = ((S + RN - 1) / RN) * mblocks;
+  const size_t stage = 2 * (size_t)128 * 128 + 2 * (size_t)RN * 128 + (XLO ? 4 : 2) * (size_t)64 * RN * 2;
+  const size_t smem = 1024 + 2 * stage + sizeof(Bars) + 64;
+  set_smem(tc_residual_kernel<RN, XLO>, smem);
+  const int grid = static_cast<int>(std::min<int64_t>(tiles, ctx->num_sms));
+  tc_residual_kernel<RN, XLO><<<grid, kThreads, smem, stream()>>>(mx, mxlo, mq, mh, n1, S, mblocks,
+                                                                  acc, ctx->d_status);
+  check_launch("tc_residual_bf16");
+}
+
 void tc_residual_bf16(const __nv_bfloat16* X, int64_t n1, int64_t S, const double* Q1, int c,
-                      const float* H, double* acc) {
+                      const float* H, double* acc, const __nv_bfloat16* Xlo) {
   KRP_REQUIRE(tc_residual_supported(n1, c), "tensor-core residual needs n_1 %% 8 == 0 and c <= 64");
   KRP_REQUIRE((reinterpret_cast<uintptr_t>(X) & 15) == 0, "X must be 16-byte aligned");
+  KRP_REQUIRE(!Xlo || (reinterpret_cast<uintptr_t>(Xlo) & 15) == 0, "X lo plane must be 16-byte aligned");
   KRP_REQUIRE(S < (int64_t(1) << 31) && n1 < (int64_t(1) << 31), "tensor too large for TMA");
   Ctx* ctx = current();
   __nv_bfloat16* Qp = ctx->ws.take<__nv_bfloat16>((size_t)n1 * 128);
@@ -1154,27 +1231,25 @@ void tc_residual_bf16(const __nv_bfloat16* X, int64_t n1, int64_t S, const doubl
   check_launch("pack_rows_hilo");
   const uint64_t xd[2] = {(uint64_t)n1, (uint64_t)S};
   const uint64_t xs[1] = {(uint64_t)n1 * 2};
-  const uint32_t xbox[2] = {64, kResN};
-  const CUtensorMap mx = make_map(X, 2, xd, xs, xbox);
   const uint64_t qd[2] = {128, (uint64_t)n1};
   const uint64_t qs[1] = {256};
   const uint32_t qbox[2] = {64, kBM};
   const CUtensorMap mq = make_map(Qp, 2, qd, qs, qbox);
-  const uint64_t hd[2] = {128, (uint64_t)S};
-  const uint32_t hbox[2] = {64, kResN};
-  const CUtensorMap mh = make_map(Hp, 2, hd, qs, hbox);
-  const int mblocks = static_cast<int>((n1 + kBM - 1) / kBM);
-  const int64_t tiles = ((S + kResN - 1) / kResN) * mblocks;
-  const size_t smem = 1024 + 2 * (size_t)(4 * 128 * 128 + 2 * 64 * kResN * 2) + sizeof(Bars) + 64;
-  set_smem(tc_residual_kernel, smem);
-  const int grid = static_cast<int>(std::min<int64_t>(tiles, ctx->num_sms));
-  tc_residual_kernel<<<grid, kThreads, smem, stream()>>>(mx, mq, mh, n1, S, mblocks, acc,
-                                                        ctx->d_status);
-  check_launch("tc_residual_bf16");
+  if (!Xlo) {
+    const uint32_t xbox[2] = {64, 128};
+    const CUtensorMap mx = make_map(X, 2, xd, xs, xbox);
+    launch_residual<128, false>(mx, mx, mq, Hp, n1, S, acc);
+  } else {
+    const uint32_t xbox[2] = {64, 64};
+    const CUtensorMap mx = make_map(X, 2, xd, xs, xbox);
+    const CUtensorMap mxlo = make_map(Xlo, 2, xd, xs, xbox);
+    launch_residual<64, true>(mx, mxlo, mq, Hp, n1, S, acc);
+  }
 }
 
 void tc_mttkrp_first_bf16(const __nv_bfloat16* X, int64_t n1, int64_t n2, int64_t T,
-                          const __nv_bfloat16* Om2, const float* w, int L, float* Y) {
+                          const __nv_bfloat16* Om2, const float* w, int L, float* Y,
+                          const __nv_bfloat16* Xlo) {
   KRP_REQUIRE(n1 % 8 == 0, "BF16 tensor-core path needs n_1 %% 8 == 0 (n_1 = %lld)", (long long)n1);
   KRP_REQUIRE((reinterpret_cast<uintptr_t>(X) & 15) == 0, "X must be 16-byte aligned");
   KRP_REQUIRE(T < (int64_t(1) << 31) && n2 < (int64_t(1) << 31), "tensor too large for TMA");
@@ -1192,20 +1267,27 @@ void tc_mttkrp_first_bf16(const __nv_bfloat16* X, int64_t n1, int64_t n2, int64_
   const uint64_t xstr[2] = {(uint64_t)n1 * 2, (uint64_t)n1 * n2 * 2};
   const uint32_t xbox[3] = {64, kBK, 1};
   const CUtensorMap mx = make_map(X, 3, xdims, xstr, xbox);
+  CUtensorMap mxlo_v;
+  const CUtensorMap* mxlo = nullptr;
+  if (Xlo) {
+    KRP_REQUIRE((reinterpret_cast<uintptr_t>(Xlo) & 15) == 0, "X lo plane must be 16-byte aligned");
+    mxlo_v = make_map(Xlo, 3, xdims, xstr, xbox);
+    mxlo = &mxlo_v;
+  }
   const uint64_t bdims[2] = {(uint64_t)n2p, (uint64_t)Lp};
   const uint64_t bstr[1] = {(uint64_t)n2p * 2};
   const uint32_t bbox[2] = {kBK, (uint32_t)Lp};
   const CUtensorMap mb = make_map(Bc, 2, bdims, bstr, bbox);
   const int kchunks = static_cast<int>((n2 + kBK - 1) / kBK);
   switch (Lp) {
-    case 16: launch_mttkrp<16>(mx, mb, n1, T, kchunks, w, L, Y); break;
-    case 32: launch_mttkrp<32>(mx, mb, n1, T, kchunks, w, L, Y); break;
-    case 48: launch_mttkrp<48>(mx, mb, n1, T, kchunks, w, L, Y); break;
-    case 64: launch_mttkrp<64>(mx, mb, n1, T, kchunks, w, L, Y); break;
-    case 80: launch_mttkrp<80>(mx, mb, n1, T, kchunks, w, L, Y); break;
-    case 96: launch_mttkrp<96>(mx, mb, n1, T, kchunks, w, L, Y); break;
-    case 112: launch_mttkrp<112>(mx, mb, n1, T, kchunks, w, L, Y); break;
-    case 128: launch_mttkrp<128>(mx, mb, n1, T, kchunks, w, L, Y); break;
+    case 16: launch_mttkrp<16>(mx, mxlo, mb, n1, T, kchunks, w, L, Y); break;
+    case 32: launch_mttkrp<32>(mx, mxlo, mb, n1, T, kchunks, w, L, Y); break;
+    case 48: launch_mttkrp<48>(mx, mxlo, mb, n1, T, kchunks, w, L, Y); break;
+    case 64: launch_mttkrp<64>(mx, mxlo, mb, n1, T, kchunks, w, L, Y); break;
+    case 80: launch_mttkrp<80>(mx, mxlo, mb, n1, T, kchunks, w, L, Y); break;
+    case 96: launch_mttkrp<96>(mx, mxlo, mb, n1, T, kchunks, w, L, Y); break;
+    case 112: launch_mttkrp<112>(mx, mxlo, mb, n1, T, kchunks, w, L, Y); break;
+    case 128: launch_mttkrp<128>(mx, mxlo, mb, n1, T, kchunks, w, L, Y); break;
     default: fail(KRP_EUNSUPPORTED, "unsupported sketch width %d", L);
   }
 }

@@ -20,7 +20,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_build", "libkrp.so")
 
 KRP_OK, KRP_EINVAL, KRP_ENOMEM, KRP_ECUDA, KRP_EUNSUPPORTED, KRP_ETIMEOUT, KRP_ENUMERIC = range(7)
-KRP_F32, KRP_BF16, KRP_FP8_E4M3, KRP_F64 = 0, 1, 2, 3
+KRP_F32, KRP_BF16, KRP_FP8_E4M3, KRP_F64, KRP_BF16X2 = 0, 1, 2, 3, 4
 KRP_MEMO, KRP_TRUNCATE, KRP_RESIDUAL, KRP_TIMINGS = 0x1, 0x2, 0x4, 0x8
 KRP_MAXD = 8
 KRP_DRAW_MEMO, KRP_DRAW_FRESH_BASE, KRP_DRAW_STHOSVD_BASE = 0, 1, 64
@@ -32,7 +32,7 @@ EXPORTED = [
     "krp_sketch_mode", "krp_sketch_all_modes", "krp_qr", "krp_qr_noalloc", "krp_multi_ttm",
     "krp_tucker_rhosvd", "krp_tucker_sthosvd", "krp_block_hankel_lowrank",
     "krp_block_hankel_sketch", "krp_tucker_rhosvd_batched", "krp_tucker_batch_plan_info",
-    "krp_block_hankel_batched",
+    "krp_block_hankel_batched", "krp_split_bf16x2",
 ]
 
 
@@ -131,6 +131,7 @@ def load_library(path: Optional[str] = None):
         "krp_tucker_batch_plan_info": (C.c_int, [vp, C.POINTER(C.c_int), C.POINTER(C.c_int),
                                                  C.POINTER(C.c_int)]),
         "krp_block_hankel_batched": (C.c_int, [vp, C.c_int, C.c_int, C.POINTER(HankelItem)]),
+        "krp_split_bf16x2": (C.c_int, [vp, vp, C.c_int64, vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -149,8 +150,26 @@ def _status_name(s: int) -> str:
 
 # ---------------------------------------------------------------- marshalling --
 
+class BF16x2:
+    """A KRP_BF16X2 input: `tensor` holds 2N BF16 values (hi plane, lo plane)."""
+
+    def __init__(self, tensor):
+        self.tensor = tensor
+
+    def is_contiguous(self):
+        return self.tensor.is_contiguous()
+
+    def data_ptr(self):
+        return self.tensor.data_ptr()
+
+    def element_size(self):
+        return 4  # bytes per element of X (two BF16 planes)
+
+
 def _dtype_code(t) -> int:
     import torch
+    if isinstance(t, BF16x2):
+        return KRP_BF16X2
     if isinstance(t, np.ndarray):
         m = {np.dtype(np.float32): KRP_F32, np.dtype(np.float64): KRP_F64}
         return m[t.dtype]
@@ -383,3 +402,13 @@ def make_hankel_items(blocks, shapes, seeds, Us, Ss, Vs):
 def krp_block_hankel_batched(ctx: Context, bt: int, items):
     """Batched Alg. 6 over block Hankel matrices (outputs in the items' U, S, V)."""
     ctx.check(ctx.lib.krp_block_hankel_batched(ctx.handle, int(bt), len(items), items))
+
+
+def krp_split_bf16x2(ctx: Context, X, out=None):
+    """BF16 hi/lo pair of an FP32 device tensor (returns a BF16x2 input)."""
+    import torch
+    n = X.numel()
+    if out is None:
+        out = torch.empty(2 * n, dtype=torch.bfloat16, device=X.device)
+    ctx.check(ctx.lib.krp_split_bf16x2(ctx.handle, _ptr(X), n, _ptr(out)))
+    return BF16x2(out)

@@ -118,3 +118,21 @@ def test_c4_bf16_matches_oracle(ctx):
     assert abs(e - e_ora) <= 1e-3 * e_ora, (e, e_ora)
     s_ora = np.asarray(g["sigma_bf16"])
     assert np.max(np.abs(sg - s_ora)) <= 1e-4 * s_ora[0]
+
+
+def test_c3_bf16x2_within_105_of_fp32(ctx, c3_inputs):
+    """X streamed as a BF16 hi/lo pair (tensor cores, 4 bytes per element):
+    error within 1.05x of the FP32 form's, and equal to the oracle's with BF16
+    factors (the pair represents X to 2^-17)."""
+    import torch
+    import paper_2507_23207_gb300 as K
+    spec, x32, _ = c3_inputs
+    g = GOLD["c3"]
+    x2 = K.krp_split_bf16x2(ctx, x32)
+    e2 = _rhosvd(ctx, spec, x2)["rel_residual"]
+    del x2
+    torch.cuda.empty_cache()
+    e32 = _rhosvd(ctx, spec, x32)["rel_residual"]
+    assert e2 <= 1.05 * e32, (e2, e32)
+    e_ora = g["rhosvd_memo_truncated_rel_error_bf16"]
+    assert abs(e2 - e_ora) <= 1e-5 * e_ora + 1e-6, (e2, e_ora)

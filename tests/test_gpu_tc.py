@@ -141,3 +141,88 @@ def test_bf16_requires_aligned_first_mode(ctx):
         K.krp_sketch_mode(ctx, tensor_to_dev(x, torch.bfloat16), dims, 0,
                           [mat_to_dev(o, torch.bfloat16) for o in om], ell, y)
     assert e.value.status == K.KRP_EINVAL
+
+
+# ---- BF16 hi/lo form (KRP_BF16X2): X streamed as two BF16 planes -------------
+
+def _split_host(x):
+    hi = philox.round_to_bf16(x)
+    lo = philox.round_to_bf16(x - hi)
+    return hi, lo
+
+
+def _x2_dev(hi, lo):
+    import torch
+    import paper_2507_23207_gb300 as K
+    h = tensor_to_dev(hi, torch.bfloat16).reshape(-1)
+    l_ = tensor_to_dev(lo, torch.bfloat16).reshape(-1)
+    return K.BF16x2(torch.cat([h, l_]))
+
+
+def test_split_bf16x2_matches_host_split(ctx):
+    import torch
+    import paper_2507_23207_gb300 as K
+    rng = np.random.default_rng(11)
+    x = philox.round_to_f32(rng.standard_normal(5003) * 10.0 ** rng.integers(-3, 3, 5003))
+    xd = torch.from_numpy(x.astype(np.float32)).to(dev())
+    x2 = K.krp_split_bf16x2(ctx, xd)
+    torch.cuda.synchronize()
+    got = x2.tensor.to(torch.float64).cpu().numpy()
+    hi, lo = _split_host(x)
+    assert np.array_equal(got[:5003], hi) and np.array_equal(got[5003:], lo)
+    assert np.max(np.abs(hi + lo - x) / np.abs(x)) <= 2.0 ** -17
+
+
+@pytest.mark.parametrize("dims,ell", [((64, 48, 40), 5), ((200, 200, 7), 30), ((256, 64, 16, 3), 12),
+                                      ((136, 40, 30), 64)])
+def test_bf16x2_sketches(ctx, dims, ell):
+    """Sketch of hi + lo with BF16 factors: products exact, FP32 accumulation."""
+    import torch
+    import paper_2507_23207_gb300 as K
+    rng = np.random.default_rng(sum(dims) + ell)
+    x = philox.round_to_f32(np.asfortranarray(rng.standard_normal(dims)))
+    hi, lo = _split_host(x)
+    xe = hi + lo
+    om = [philox.round_to_bf16(philox.gaussian_factor(9, j, 0, 0, n, ell)) for j, n in enumerate(dims)]
+    x2 = _x2_dev(hi, lo)
+    omd = [mat_to_dev(o, torch.bfloat16) for o in om]
+    ys = [empty_mat(n, ell, torch.float32) for n in dims]
+    K.krp_sketch_all_modes(ctx, x2, dims, omd, ell, ys)
+    y0 = empty_mat(dims[0], ell, torch.float32)
+    K.krp_sketch_mode(ctx, x2, dims, 0, omd, ell, y0)
+    torch.cuda.synchronize()
+    for n in range(len(dims)):
+        assert rel(mat_from_dev(ys[n], dims[n], ell), T.mttkrp(xe, om, n)) <= 1e-5, (dims, n)
+    assert rel(mat_from_dev(y0, dims[0], ell), T.mttkrp(xe, om, 0)) <= 1e-5
+
+
+@pytest.mark.parametrize("variant", ["memo", "sthosvd"])
+def test_bf16x2_tucker_truncated(ctx, variant):
+    """RHOSVD-KRP-MEMO / RSTHOSVD-KRP with truncation on X = hi + lo against the
+    oracle on hi + lo (BF16 factors): the core's MMAs drop only Xl Ql and
+    Ql Hl-type terms (below 2^-16 relative)."""
+    import torch
+    import paper_2507_23207_gb300 as K
+    spec = TuckerSpec("x2", (64, 48, 40), (4, 4, 4), 1e-3, None, 47, (4, 4, 4), (8, 8, 8))
+    x, _, _ = tucker_tensor(spec)
+    hi, lo = _split_host(philox.round_to_f32(x))
+    xe = hi + lo
+    p = spec.oversample
+    ranks = list(spec.ranks)
+    flags = K.KRP_TRUNCATE | K.KRP_RESIDUAL | (K.KRP_MEMO if variant == "memo" else 0)
+    core = torch.empty(int(np.prod(ranks)), dtype=torch.float32, device=dev())
+    facs = [torch.empty(n * r, dtype=torch.float64, device=dev()) for n, r in zip(spec.dims, ranks)]
+    fn = K.krp_tucker_rhosvd if variant == "memo" else K.krp_tucker_sthosvd
+    res = fn(ctx, _x2_dev(hi, lo), spec.dims, ranks, p, 0, flags, core, facs)
+    torch.cuda.synchronize()
+    ells = [r + p for r in ranks]
+    if variant == "memo":
+        ora = TK.rhosvd_krp(xe, ells, 0, memo=True, omega_round="bf16")
+    else:
+        ora = _sthosvd_bf16_first(xe, ells)
+    g2, q2 = TK.truncate_core(ora["G"], ora["Q"], ranks)
+    gg = core.cpu().numpy().astype(np.float64).reshape(ranks[::-1]).T
+    qq = [f.cpu().numpy().reshape(r, n).T for f, n, r in zip(facs, spec.dims, ranks)]
+    nx = np.linalg.norm(xe)
+    assert np.linalg.norm(TK.reconstruct(gg, qq) - TK.reconstruct(g2, q2)) / nx <= 5e-5
+    assert abs(res["rel_residual"] - TK.rel_error(xe, g2, q2)) <= 5e-5

@@ -136,3 +136,105 @@ def test_c3_bf16x2_within_105_of_fp32(ctx, c3_inputs):
     assert e2 <= 1.05 * e32, (e2, e32)
     e_ora = g["rhosvd_memo_truncated_rel_error_bf16"]
     assert abs(e2 - e_ora) <= 1e-5 * e_ora + 1e-6, (e2, e_ora)
+
+
+# ---- 1024^3 (the bench's FP32 workload): sampled rows of every mode sketch --
+
+@pytest.fixture(scope="module")
+def c2_inputs():
+    require_gpu()
+    import torch
+    from synth.tucker import tucker_tensor_device
+    spec = config_spec("c2")
+    x64, _, _ = tucker_tensor_device(spec, device=dev())
+    x32 = x64.to(torch.float32)
+    xbf = x64.to(torch.bfloat16)
+    del x64
+    torch.cuda.empty_cache()
+    yield spec, x32, xbf
+    del x32, xbf
+    torch.cuda.empty_cache()
+
+
+ROWS = [0, 517, 1023]
+
+
+@pytest.mark.parametrize("form,tol", [("f32", 1e-5), ("bf16x2", 1e-5), ("bf16", 5e-5)])
+def test_c2_sketch_sampled_rows(ctx, c2_inputs, form, tol):
+    """All three mode sketches of the 1024^3 tensor with the memoized factor set,
+    in the launch configuration of the bench; rows ROWS of each Y_n against the
+    oracle's mttkrp of the corresponding slice of X (the same rounded X and
+    factors; for the hi/lo form the slice is hi + lo), relative per row.
+    Bounds: FP32 and hi/lo forms 1e-5.  BF16 form (one-pass tree) 5e-5: its
+    mode-1 accumulator collects every slab in TMEM, 2^20 products in ~2^16 MMA
+    accumulations in FP32, whose rounding grows to about 2^-24 * 2^8 = 1.5e-5
+    (two orders below the BF16 quantisation of the input itself)."""
+    import torch
+    import paper_2507_23207_gb300 as K
+    from oracle import tensor as T
+    spec, x32, xbf = c2_inputs
+    if form == "bf16x2":
+        x = K.krp_split_bf16x2(ctx, x32)
+        n_ = x32.numel()
+        hi = x.tensor[:n_].view(x32.shape)
+        lo = x.tensor[n_:].view(x32.shape)
+    else:
+        x = x32 if form == "f32" else xbf
+    dt = torch.float32 if form == "f32" else torch.bfloat16
+    ell = spec.ell[0]
+    om = [torch.empty((ell, n), dtype=dt, device=dev()) for n in spec.dims]
+    K.krp_gen_factors(ctx, spec.omega_seed, K.KRP_DRAW_MEMO, K.KRP_TAG_OMEGA, spec.dims, ell, om)
+    ys = [torch.empty((ell, n), dtype=torch.float32, device=dev()) for n in spec.dims]
+    K.krp_sketch_all_modes(ctx, x, spec.dims, om, ell, ys)
+    torch.cuda.synchronize()
+    omh = [o.to(torch.float64).cpu().numpy().T for o in om]  # n x ell, the exact values used
+    for n in range(3):
+        for r in ROWS:
+            # slice of X (torch layout (n3, n2, n1)) at index r of mode n, as a
+            # 3-way tensor with a singleton mode n
+            def slab(t):
+                if n == 0:
+                    return t[:, :, r:r + 1]
+                if n == 1:
+                    return t[:, r:r + 1, :]
+                return t[r:r + 1, :, :]
+            if form == "bf16x2":
+                sl = slab(hi).to(torch.float64) + slab(lo).to(torch.float64)
+            else:
+                sl = slab(x).to(torch.float64)
+            xs = np.asfortranarray(sl.cpu().numpy().transpose(2, 1, 0))
+            omr = [o if j != n else o[r:r + 1] for j, o in enumerate(omh)]
+            ref = T.mttkrp(xs, omr, n)[0]
+            got = ys[n][:, r].to(torch.float64).cpu().numpy()
+            assert np.linalg.norm(got - ref) <= tol * np.linalg.norm(ref), (form, n, r)
+
+
+def test_c2_pipeline_properties(ctx, c2_inputs):
+    """Full RHOSVD-KRP-MEMO step of the bench (FP32 and BF16): orthonormal
+    factors (FP64, 1e-10), rank-l error <= rank-r error (truncation removes
+    directions), and for FP32 the rank-32 error between the noise level (the
+    input carries relative noise 1e-4, which no rank-32 approximation removes)
+    and 5x it."""
+    import torch
+    import paper_2507_23207_gb300 as K
+    spec, x32, xbf = c2_inputs
+    ranks = list(spec.ranks)
+    ells = list(spec.ell)
+    for form, x in (("f32", x32), ("bf16", xbf)):
+        errs = []
+        for trunc in (False, True):
+            out = ranks if trunc else ells
+            core = torch.empty(int(np.prod(out)), dtype=torch.float32, device=dev())
+            facs = [torch.empty(n * o, dtype=torch.float64, device=dev()) for n, o in zip(spec.dims, out)]
+            flags = K.KRP_MEMO | K.KRP_RESIDUAL | (K.KRP_TRUNCATE if trunc else 0)
+            res = K.krp_tucker_rhosvd(ctx, x, spec.dims, ranks, spec.oversample, spec.omega_seed,
+                                      flags, core, facs)
+            torch.cuda.synchronize()
+            for f, n, o in zip(facs, spec.dims, out):
+                q = f.cpu().numpy().reshape(o, n).T
+                assert np.linalg.norm(q.T @ q - np.eye(o)) <= 1e-10
+            errs.append(res["rel_residual"])
+        assert errs[0] <= errs[1]
+        if form == "f32":
+            # noise of relative size 1e-4 bounds any rank-32 error from below
+            assert 0.9e-4 <= errs[1] <= 5e-4, errs

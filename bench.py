@@ -170,11 +170,14 @@ def run_ours(args, rank, world, local_rank):
         ev0 = torch.cuda.Event(enable_timing=True)
         ev1 = torch.cuda.Event(enable_timing=True)
         torch.cuda.synchronize()
+        if form == "f32":
+            K.krp_trace_begin(ctx)  # an event after every launch, for the roofline
         ev0.record(stream)
         for _ in range(args.steps):
             res = step()
         ev1.record(stream)
         torch.cuda.synchronize()
+        trace = K.krp_trace_end(ctx) if form == "f32" else None
         clk = clocks.stop()
         ms = ev0.elapsed_time(ev1) / args.steps
         launches = (ctx.launch_count() - launches0)
@@ -182,11 +185,13 @@ def run_ours(args, rank, world, local_rank):
             t = torch.tensor([ms], device=dev)
             torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
             ms = float(t.item())
-        results[form] = {"ms": ms, "res": res, "phases": ph, "clocks": clk,
+        results[form] = {"ms": ms, "res": res, "phases": ph, "clocks": clk, "trace": trace,
                          "launches": launches,
                          "bytes_per_elem": 4 if form == "bf16x2" else x.element_size()}
-    # dominant-kernel roofline: the sketch of mode 1 alone (one MTTKRP launch)
-    kr = kernel_roofline(ctx, spec, x32, dev, stream, peaks, results["f32"]["clocks"], args)
+    # dominant-kernel roofline from the launch trace of the timed FP32 steps
+    kr = trace_roofline(spec, results["f32"], peaks, args)
+    kr["mode1_sketch_alone"] = kernel_roofline(ctx, spec, x32, dev, stream, peaks,
+                                               results["f32"]["clocks"], args)
     # e2e through the C ABI with host buffers (pinned), FP32 form
     e2e = e2e_run(ctx, spec, x32, args) if rank == 0 and not args.no_e2e else None
     extra = {}
@@ -282,7 +287,7 @@ def c3_run(ctx, dev, stream, args):
     return out
 
 
-def batch_run(ctx, dev, stream, args):
+def batch_run(ctx, dev, stream, args, count=512):
     """512 uneven 3-way tensors (sides 32..192, ranks 4..16, l = r + 8):
     the batched path (one launch per phase, graph replay) in BF16 and FP32,
     against a loop of single-tensor FP32 calls."""
@@ -290,7 +295,7 @@ def batch_run(ctx, dev, stream, args):
     import paper_2507_23207_gb300 as K
     from synth import batch_tucker_specs
     from synth.tucker import tucker_tensor_device
-    specs = batch_tucker_specs()
+    specs = batch_tucker_specs(count)
     x32, xbf = [], []
     for sp in specs:
         x64, _, _ = tucker_tensor_device(sp, device=dev)
@@ -407,6 +412,43 @@ def c4_run(ctx, dev, stream, args):
     return out
 
 
+# DRAM traffic (read + write bytes) of one big launch of the dominant kernel
+# at 1024^3: ncu at 512^3 measured 538.8 MB read (X once) and 41.9 MB write
+# (the (N/n1) x l output); X scales x8 and the output x4 to 1024^3
+# (profiles/ncu_f32_kernels_512cubed.md).  Set to None if the kernel changes.
+TTM48_TRAFFIC_PER_BIG_LAUNCH = 538.8e6 * 8 + 41.9e6 * 4
+
+
+def trace_roofline(spec, f32, peaks, args):
+    """Roofline of the dominant kernel of the FP32 step, the tiled TTM
+    gemm_tn_tile<48> (39% of the step in the ncu launch list).  Each step
+    launches it four times: the dimension tree's B-part (X_(1)^T Omega_1) and
+    the core's first TTM (X_(1)^T Q_1) -- both a contraction of the whole
+    1024 x 1024^2 X with a 1024 x 48 factor -- then the core's TTMs on the
+    48 x 1024^2 and 48^2 x 1024 intermediates.  The object covers the two big
+    launches (2 N l flops, one read of X each), timed live by the launch
+    trace (events on the context stream) over the timed steps."""
+    n, ell = spec.numel, max(spec.ell)
+    tr = f32.get("trace") or []
+    ttm = [t for name, t in tr if name == "gemm_tn_tile<48>"]
+    mhz = (f32.get("clocks") or {}).get("sm_max_mhz") or peaks.get("sm_max_mhz", 2070.0)
+    peak = fp32_ffma_peak_tflops(mhz)
+    if len(ttm) != 4 * args.steps:
+        return {"kernel": "gemm_tn_tile_kernel<48>", "error": f"trace saw {len(ttm)} launches"}
+    big = [t for i, t in enumerate(ttm) if i % 4 < 2]
+    t_big = sum(big) / len(big)
+    ach = 2.0 * n * ell / (t_big * 1e-3) / 1e12
+    step_ms = sum(t for _, t in tr) / args.steps
+    return {"kernel": "gemm_tn_tile_kernel<48> (FP32 TTM of X with a 1024 x 48 factor)",
+            "bound": "alu", "achieved": round(ach, 3), "peak": round(peak, 3), "unit": "TFLOP/s",
+            "frac": round(ach / peak, 4), "traffic": TTM48_TRAFFIC_PER_BIG_LAUNCH,
+            "algorithmic_bytes": n * 4 + n / spec.dims[0] * ell * 4,
+            "ms_per_launch": round(t_big, 4), "launches_averaged": len(big),
+            "kernel_share_of_step": round(sum(ttm) / args.steps / step_ms, 4),
+            "peak_note": f"FP32 FFMA peak = 152 SMs x 128 lanes x 2 flop x {mhz:.0f} MHz",
+            "timing": "CUDA events after every launch on the context stream over the timed steps"}
+
+
 def kernel_roofline(ctx, spec, x32, dev, stream, peaks, clk, args):
     import torch
     import paper_2507_23207_gb300 as K
@@ -514,6 +556,10 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-extra", action="store_true",
                     help="skip the STHOSVD, 200^4 and block-Hankel measurements")
+    ap.add_argument("--batch-only", action="store_true",
+                    help="run only the batched workloads (for profiling) and print their line")
+    ap.add_argument("--batch-count", type=int, default=512,
+                    help="tensors in the batched workload with --batch-only")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -538,6 +584,19 @@ def main():
                 "e2e": {"value": round(v, 4), "unit": "GB/s", "h2d_bytes_per_step": 0,
                         "d2h_bytes_per_step": 0}}
         print(json.dumps(line))
+        return
+
+    if args.batch_only:
+        import torch
+        import paper_2507_23207_gb300 as K
+        dev = torch.device(f"cuda:{local_rank}")
+        torch.cuda.set_device(dev)
+        stream = torch.cuda.current_stream(dev)
+        ctx = K.Context(local_rank, stream.cuda_stream)
+        out = {"batched_tucker": batch_run(ctx, dev, stream, args, count=args.batch_count),
+               "batched_hankel": hankel_batch_run(ctx, dev, stream, args)}
+        ctx.close()
+        print(json.dumps(out))
         return
 
     if world > 1:

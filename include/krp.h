@@ -197,6 +197,16 @@ krp_status krp_qr(krp_ctx ctx, int count, const float* const* Y,
 krp_status krp_qr_noalloc(const float* Y, int64_t m, int l, double* Q,
                           double* R, void* cuda_stream);
 
+/* Launch trace (diagnostics): between krp_trace_begin and krp_trace_end the
+ * context records a CUDA event on its stream after every kernel it launches
+ * (not inside captured graphs).  krp_trace_end synchronises the stream and
+ * writes a JSON list [["launch name", ms], ...] into json (cap bytes): the
+ * time between consecutive events, i.e. each launch's duration on the stream
+ * including any copy or memset enqueued just before it.  KRP_EINVAL if the
+ * buffer is too small. */
+krp_status krp_trace_begin(krp_ctx ctx);
+krp_status krp_trace_end(krp_ctx ctx, char* json, size_t cap);
+
 /* hi[e] = bf16_rn(X[e]), lo[e] = bf16_rn(X[e] - hi[e]) for e < n; out holds
  * 2n BF16 values (hi plane then lo plane), the KRP_BF16X2 layout.  X and out
  * are device pointers (out 16-byte aligned).  The paper streams X in one

@@ -32,10 +32,30 @@ void note_launch(const char*) {
   if (g_current) ++g_current->launches;
 }
 
+static cudaEvent_t trace_event(Ctx* c) {
+  const size_t i = c->trace.size();
+  while (c->trace_pool.size() <= i) {
+    cudaEvent_t e;
+    KRP_CUDA_CHECK(cudaEventCreate(&e));
+    c->trace_pool.push_back(e);
+  }
+  return c->trace_pool[i];
+}
+
 void check_launch(const char* name) {
   note_launch(name);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) fail(KRP_ECUDA, "launch of %s failed: %s", name, cudaGetErrorString(e));
+  Ctx* c = g_current;
+  if (c && c->trace_on) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    cudaStreamIsCapturing(c->stream, &cs);
+    if (cs == cudaStreamCaptureStatusNone) {
+      cudaEvent_t ev = trace_event(c);
+      KRP_CUDA_CHECK(cudaEventRecord(ev, c->stream));
+      c->trace.push_back({name, ev});
+    }
+  }
 }
 
 void ensure_workspace(Ctx* c, size_t bytes) {
@@ -158,6 +178,8 @@ krp_status krp_destroy(krp_ctx ctx) {
   if (!ctx) return KRP_EINVAL;
   krp_status st = guarded(ctx, [&] {
     KRP_CUDA_CHECK(cudaStreamSynchronize(ctx->c.stream));
+    for (cudaEvent_t e : ctx->c.trace_pool) cudaEventDestroy(e);
+    ctx->c.trace_pool.clear();
     if (ctx->c.batch_plan) ctx->c.batch_plan_free(ctx->c.batch_plan);
     ctx->c.batch_plan = nullptr;
     if (ctx->c.hankel_plan) ctx->c.hankel_plan_free(ctx->c.hankel_plan);
@@ -296,6 +318,38 @@ krp_status krp_tucker_sthosvd(krp_ctx ctx, const void* X, krp_dtype xt, int d,
                               const int64_t* dims, const int* ranks, int oversample,
                               uint64_t seed, unsigned flags, krp_tucker_out* out) {
   return guarded(ctx, [&] { tucker_pipeline(true, X, xt, d, dims, ranks, oversample, seed, flags, out); });
+}
+
+krp_status krp_trace_begin(krp_ctx ctx) {
+  return guarded(ctx, [&] {
+    Ctx* c = &ctx->c;
+    c->trace.clear();
+    cudaEvent_t ev = trace_event(c);
+    KRP_CUDA_CHECK(cudaEventRecord(ev, c->stream));
+    c->trace.push_back({nullptr, ev});
+    c->trace_on = true;
+  });
+}
+
+krp_status krp_trace_end(krp_ctx ctx, char* json, size_t cap) {
+  return guarded(ctx, [&] {
+    Ctx* c = &ctx->c;
+    c->trace_on = false;
+    KRP_REQUIRE(json && cap > 2, "json buffer is NULL or too small");
+    KRP_CUDA_CHECK(cudaStreamSynchronize(c->stream));
+    std::string out = "[";
+    for (size_t i = 1; i < c->trace.size(); ++i) {
+      float ms = 0.f;
+      KRP_CUDA_CHECK(cudaEventElapsedTime(&ms, c->trace[i - 1].second, c->trace[i].second));
+      char item[160];
+      snprintf(item, sizeof(item), "%s[\"%s\", %.6f]", i > 1 ? ", " : "", c->trace[i].first, ms);
+      out += item;
+    }
+    out += "]";
+    c->trace.clear();
+    KRP_REQUIRE(out.size() < cap, "trace needs %zu bytes", out.size() + 1);
+    std::memcpy(json, out.c_str(), out.size() + 1);
+  });
 }
 
 krp_status krp_split_bf16x2(krp_ctx ctx, const float* X, int64_t n, void* out) {

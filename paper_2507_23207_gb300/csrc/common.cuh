@@ -74,6 +74,10 @@ struct Ctx {
   void (*batch_plan_free)(void*) = nullptr;
   void* hankel_plan = nullptr;             // cached batched block-Hankel plan
   void (*hankel_plan_free)(void*) = nullptr;
+  // launch trace (krp_trace_begin/end): an event after every launch
+  bool trace_on = false;
+  std::vector<std::pair<const char*, cudaEvent_t>> trace;
+  std::vector<cudaEvent_t> trace_pool;
 };
 
 Ctx* current();           // context of the API call in progress (thread-local)

@@ -899,7 +899,8 @@ void gemm_tn_tile_launch(const float* A, int64_t lda, int64_t S, int K, const fl
   set_dyn_smem(gemm_tn_tile_kernel<NP, BMS, NS, MINB>, smem);
   gemm_tn_tile_kernel<NP, BMS, NS, MINB><<<grid, BMS, smem, stream()>>>(A, lda, S, K, F, ldf, L, out,
                                                                         ldo, accumulate ? 1 : 0);
-  check_launch("gemm_tn_f32");
+  check_launch(NP == 16 ? "gemm_tn_tile<16>" : NP == 32 ? "gemm_tn_tile<32>"
+               : NP == 48 ? "gemm_tn_tile<48>" : "gemm_tn_tile<64>");
 }
 
 template <int NP>

@@ -32,7 +32,7 @@ EXPORTED = [
     "krp_sketch_mode", "krp_sketch_all_modes", "krp_qr", "krp_qr_noalloc", "krp_multi_ttm",
     "krp_tucker_rhosvd", "krp_tucker_sthosvd", "krp_block_hankel_lowrank",
     "krp_block_hankel_sketch", "krp_tucker_rhosvd_batched", "krp_tucker_batch_plan_info",
-    "krp_block_hankel_batched", "krp_split_bf16x2",
+    "krp_block_hankel_batched", "krp_split_bf16x2", "krp_trace_begin", "krp_trace_end",
 ]
 
 
@@ -132,6 +132,8 @@ def load_library(path: Optional[str] = None):
                                                  C.POINTER(C.c_int)]),
         "krp_block_hankel_batched": (C.c_int, [vp, C.c_int, C.c_int, C.POINTER(HankelItem)]),
         "krp_split_bf16x2": (C.c_int, [vp, vp, C.c_int64, vp]),
+        "krp_trace_begin": (C.c_int, [vp]),
+        "krp_trace_end": (C.c_int, [vp, C.c_char_p, C.c_size_t]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -412,3 +414,15 @@ def krp_split_bf16x2(ctx: Context, X, out=None):
         out = torch.empty(2 * n, dtype=torch.bfloat16, device=X.device)
     ctx.check(ctx.lib.krp_split_bf16x2(ctx.handle, _ptr(X), n, _ptr(out)))
     return BF16x2(out)
+
+
+def krp_trace_begin(ctx: Context):
+    ctx.check(ctx.lib.krp_trace_begin(ctx.handle))
+
+
+def krp_trace_end(ctx: Context, cap: int = 1 << 20):
+    """List of (launch name, ms) in launch order since krp_trace_begin."""
+    import json
+    buf = C.create_string_buffer(cap)
+    ctx.check(ctx.lib.krp_trace_end(ctx.handle, buf, cap))
+    return [(n, float(t)) for n, t in json.loads(buf.value.decode())]

@@ -211,6 +211,11 @@ template <int EP>  // row pitch of the padded matrices
 __device__ void jacobi32(float (*S)[EP], float (*V)[EP], int n, float* cs, float* sn, int* pp,
                          int* qq, double* red) {
   const int tid = threadIdx.x, P = n / 2;
+  // fixed work split of the round updates (no per-item integer division):
+  // threads t < jstep * P own pair ib0 = t % P and rows/blocks jb0 + m jstep
+  const int jstep = (int)blockDim.x / P;
+  const int ib0 = tid % P;
+  const int jb0 = (tid < jstep * P) ? tid / P : n;  // idle threads get an empty range
   for (int sweep = 0; sweep < kEigSweeps32; ++sweep) {
     double o = 0.0, dg = 0.0;
     for (int e = tid; e < n * n; e += blockDim.x) {
@@ -251,9 +256,10 @@ __device__ void jacobi32(float (*S)[EP], float (*V)[EP], int n, float* cs, float
         sn[tid] = s;
       }
       __syncthreads();
-      for (int b = tid; b < P * P + n * P; b += blockDim.x) {
-        if (b < P * P) {
-          const int i = b % P, j = b / P;
+      // 2x2 blocks (i, j) of S: thread t takes i = t % P and j = t / P + k * jstep
+      for (int j = jb0; j < P; j += jstep) {
+        {
+          const int i = ib0;
           const int pi = pp[i], qi = qq[i], pj = pp[j], qj = qq[j];
           const float ci = cs[i], si = sn[i], cj = cs[j], sj = sn[j];
           const float a = S[pi][pj], bq = S[pi][qj], cq = S[qi][pj], d = S[qi][qj];
@@ -270,11 +276,14 @@ __device__ void jacobi32(float (*S)[EP], float (*V)[EP], int n, float* cs, float
           S[pi][qj] = b2;
           S[qi][pj] = c2;
           S[qi][qj] = d2;
-        } else {
-          const int e = b - P * P;
-          const int k = e % P, r = e / P;
-          const int p = pp[k], q = qq[k];
-          const float c = cs[k], s = sn[k];
+        }
+      }
+      // rows r of V for pair k: thread t takes k = t % P and r = t / P + m * jstep
+      {
+        const int k = ib0;
+        const int p = pp[k], q = qq[k];
+        const float c = cs[k], s = sn[k];
+        for (int r = jb0; r < n; r += jstep) {
           const float vp = V[r][p], vq = V[r][q];
           V[r][p] = c * vp - s * vq;
           V[r][q] = s * vp + c * vq;
@@ -548,7 +557,7 @@ __global__ void __launch_bounds__(256) cqr_chol_kernel(const CqrBatch jobs, int 
   const int l = job.l;
   __shared__ double A[kCqrMaxL][kCqrMaxL + 1];
   __shared__ double diag0[kCqrMaxL];
-  __shared__ double piv, tol;
+  __shared__ double piv, invd, tol;
   __shared__ int refill;
   __shared__ unsigned long long mask;
   for (int e = threadIdx.x; e < l * l; e += blockDim.x) {
@@ -575,27 +584,27 @@ __global__ void __launch_bounds__(256) cqr_chol_kernel(const CqrBatch jobs, int 
   }
   __syncthreads();
   double* R = job.Rk + (size_t)pass * l * l;
+  // Right-looking Cholesky, two barriers per column: row j of A stays
+  // unscaled, R[j, i] = A[j, i] / r_jj and the trailing update subtracts
+  // A[j, a] A[j, b] / d_j (d_j = r_jj^2), all from the same unscaled row.
   for (int j = 0; j < l; ++j) {
     if (threadIdx.x == 0) {
       const double d = A[j][j];
       const bool deficient = (pass == 0) ? !(diag0[j] > 0.0) : !(d > tol);
       refill = deficient;
-      piv = deficient ? 1.0 : sqrt(d);
+      const double rj = deficient ? 1.0 : sqrt(d);
+      piv = rj;
+      invd = deficient ? 0.0 : 1.0 / d;
       if (deficient) mask |= 1ull << j;
     }
     __syncthreads();
-    const double dj = piv;
-    const bool rf = refill;
-    for (int i = threadIdx.x; i < l; i += blockDim.x) {
-      const double v = (i > j && !rf) ? A[j][i] / dj : 0.0;
-      R[j + l * i] = (i == j) ? dj : v;
-      if (i > j) A[j][i] = v;
-    }
-    __syncthreads();
+    const double dj = piv, id = invd;
+    const double ir = id * dj;  // 1 / r_jj (0 for a refilled column)
+    for (int i = j + threadIdx.x; i < l; i += blockDim.x) R[j + l * i] = (i == j) ? dj : A[j][i] * ir;
     const int rem = l - j - 1;
     for (int e = threadIdx.x; e < rem * rem; e += blockDim.x) {
       const int a = j + 1 + e % rem, b = j + 1 + e / rem;
-      if (a <= b) A[a][b] -= A[j][a] * A[j][b];
+      if (a <= b) A[a][b] = fma(-A[j][a] * id, A[j][b], A[a][b]);
     }
     __syncthreads();
   }
@@ -624,38 +633,57 @@ __global__ void __launch_bounds__(256) cqr_chol_kernel(const CqrBatch jobs, int 
   }
 }
 
-// W_out[r, :] = W_in[r, :] R^{-1}, one row per thread (forward substitution).
+// W_out[r, :] = W_in[r, :] R^{-1} by forward substitution, 16 rows per CTA
+// and 16 threads per row: for column j the 16 threads split the dot product
+// sum_{k<j} x_k R[k, j] and reduce it with shuffles, so that the FP64 work
+// (GB300: 2 FMA/clk/SM) is spread over all four schedulers of many SMs.
+constexpr int kSolveRows = 16;
 template <bool FROM_INPUT, bool TO_Q>
-__global__ void __launch_bounds__(kCqrRows) cqr_solve_kernel(const CqrBatch jobs,
-                                                             int pass) {
+__global__ void __launch_bounds__(256) cqr_solve_kernel(const CqrBatch jobs, int pass) {
   const CqrJob job = jobs.job[blockIdx.y];
   const int l = job.l;
-  const int64_t r = (int64_t)blockIdx.x * kCqrRows + threadIdx.x;
+  const int64_t r0 = (int64_t)blockIdx.x * kSolveRows;
+  if (r0 >= job.m) return;
   __shared__ double R[kCqrMaxL][kCqrMaxL + 1];
+  __shared__ double X[kSolveRows][kCqrMaxL + 1];
+  __shared__ double invd[kCqrMaxL];
   const double* Rg = job.Rk + (size_t)pass * l * l;
   for (int e = threadIdx.x; e < l * l; e += blockDim.x) R[e % l][e / l] = Rg[e];
-  __syncthreads();
-  if (r >= job.m) return;
-  const unsigned long long refill = *job.defmask;
-  double x[kCqrMaxL];
-#pragma unroll
-  for (int j = 0; j < kCqrMaxL; ++j) {
-    if (j < l) {
-      const int64_t idx = r + job.m * j;
-      double v;
+  const int rows = (int)((job.m - r0) < kSolveRows ? (job.m - r0) : kSolveRows);
+  for (int e = threadIdx.x; e < kSolveRows * l; e += blockDim.x) {
+    const int rr = e % kSolveRows, j = e / kSolveRows;
+    double v = 0.0;
+    if (rr < rows) {
+      const int64_t idx = r0 + rr + job.m * j;
       if (FROM_INPUT)
         v = job.Y64 ? job.Y64[idx] : (double)job.Y[idx];
       else
         v = job.W[idx];
-#pragma unroll
-      for (int k = 0; k < j; ++k) v = fma(-x[k], R[k][j], v);
-      x[j] = ((refill >> j) & 1ull) ? refill_value(r, j) : v / R[j][j];
     }
+    X[rr][j] = v;
   }
+  __syncthreads();
+  for (int j = threadIdx.x; j < l; j += blockDim.x) invd[j] = 1.0 / R[j][j];
+  __syncthreads();
+  const unsigned long long refill = *job.defmask;
+  const int row = threadIdx.x >> 4, sub = threadIdx.x & 15;
+  for (int j = 0; j < l; ++j) {
+    double acc = 0.0;
+    for (int k = sub; k < j; k += 16) acc = fma(X[row][k], R[k][j], acc);
+    acc += __shfl_xor_sync(0xffffffffu, acc, 1);
+    acc += __shfl_xor_sync(0xffffffffu, acc, 2);
+    acc += __shfl_xor_sync(0xffffffffu, acc, 4);
+    acc += __shfl_xor_sync(0xffffffffu, acc, 8);
+    if (sub == 0)
+      X[row][j] = ((refill >> j) & 1ull) ? refill_value(r0 + row, j) : (X[row][j] - acc) * invd[j];
+    __syncwarp();
+  }
+  __syncthreads();
   double* out = TO_Q ? job.Q : job.W;
-#pragma unroll
-  for (int j = 0; j < kCqrMaxL; ++j)
-    if (j < l) out[r + job.m * j] = x[j];
+  for (int e = threadIdx.x; e < kSolveRows * l; e += blockDim.x) {
+    const int rr = e % kSolveRows, j = e / kSolveRows;
+    if (rr < rows) out[r0 + rr + job.m * j] = X[rr][j];
+  }
 }
 
 int grid_for(int64_t n, int threads, int cap = 8192) {
@@ -687,6 +715,7 @@ cudaError_t cholqr3_single_on_stream(const float* Y, int64_t m, int l, double* Q
   q.defmask = reinterpret_cast<unsigned long long*>(q.Rk + (size_t)3 * l * l);
   int* status = reinterpret_cast<int*>(q.Rk + (size_t)3 * l * l + 1);
   const dim3 g((unsigned)((m + kCqrRows - 1) / kCqrRows), 1u);
+  const dim3 gs((unsigned)((m + kSolveRows - 1) / kSolveRows), 1u);
   for (int pass = 0; pass < 3; ++pass) {
     cudaError_t e = cudaMemsetAsync(q.G, 0, sizeof(double) * l * l, st);
     if (e != cudaSuccess) return e;
@@ -696,11 +725,11 @@ cudaError_t cholqr3_single_on_stream(const float* Y, int64_t m, int l, double* Q
       cqr_gram_kernel<false><<<g, 256, 0, st>>>(batch, status);
     cqr_chol_kernel<<<1, 256, 0, st>>>(batch, pass);
     if (pass == 0)
-      cqr_solve_kernel<true, false><<<g, kCqrRows, 0, st>>>(batch, pass);
+      cqr_solve_kernel<true, false><<<gs, 256, 0, st>>>(batch, pass);
     else if (pass == 1)
-      cqr_solve_kernel<false, false><<<g, kCqrRows, 0, st>>>(batch, pass);
+      cqr_solve_kernel<false, false><<<gs, 256, 0, st>>>(batch, pass);
     else
-      cqr_solve_kernel<false, true><<<g, kCqrRows, 0, st>>>(batch, pass);
+      cqr_solve_kernel<false, true><<<gs, 256, 0, st>>>(batch, pass);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }
@@ -762,6 +791,7 @@ void qr_householder_f64(const QrJob* jobs, int count, int* status) {
 
 void cholqr3_launch(const CqrBatch& batch, int nq, int64_t maxm, int* status) {
   const dim3 g((unsigned)((maxm + kCqrRows - 1) / kCqrRows), (unsigned)nq);
+  const dim3 gs((unsigned)((maxm + kSolveRows - 1) / kSolveRows), (unsigned)nq);
   for (int pass = 0; pass < 3; ++pass) {
     for (int q = 0; q < nq; ++q)
       KRP_CUDA_CHECK(cudaMemsetAsync(batch.job[q].G, 0, sizeof(double) * batch.job[q].l * batch.job[q].l,
@@ -774,11 +804,11 @@ void cholqr3_launch(const CqrBatch& batch, int nq, int64_t maxm, int* status) {
     cqr_chol_kernel<<<nq, 256, 0, stream()>>>(batch, pass);
     check_launch("cholqr_chol_f64");
     if (pass == 0)
-      cqr_solve_kernel<true, false><<<g, kCqrRows, 0, stream()>>>(batch, pass);
+      cqr_solve_kernel<true, false><<<gs, 256, 0, stream()>>>(batch, pass);
     else if (pass == 1)
-      cqr_solve_kernel<false, false><<<g, kCqrRows, 0, stream()>>>(batch, pass);
+      cqr_solve_kernel<false, false><<<gs, 256, 0, stream()>>>(batch, pass);
     else
-      cqr_solve_kernel<false, true><<<g, kCqrRows, 0, stream()>>>(batch, pass);
+      cqr_solve_kernel<false, true><<<gs, 256, 0, stream()>>>(batch, pass);
     check_launch("cholqr_solve_f64");
   }
 }

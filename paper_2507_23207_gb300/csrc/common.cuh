@@ -174,6 +174,8 @@ void qr_householder_launch(const QrJob* d_jobs, int count, int* status);
 void sym_eig_top_f64(const double* const* S, const int* l, const int* r,
                      double* const* U, int count, int* status,
                      double* const* evals = nullptr);
+// workspace sym_eig_top_f64 takes for `count` problems
+size_t sym_eig_workspace_bytes(int count);
 // out = G x_mode U^T for a small FP64 tensor (U is dims[mode] x r col-major)
 void ttm_small_f64(const double* G, int D, const int64_t* dims, int mode,
                    const double* U, int r, double* out);

@@ -623,6 +623,139 @@ __global__ void __launch_bounds__(256)
 }
 
 
+// Persistent form of the residual for FP32 X with c % 4 == 0: a CTA keeps its
+// 128-row block of Q1 (c x 128, staged [k][i]) in shared memory and walks the
+// 64-column tiles s0 = 64 (blockIdx.x + j gridDim.x), with the H tile (64 x c,
+// one contiguous run of H) and the X tile (64 x 128, staged [s][i]) of the
+// next tile in flight by cp.async while the current one is reconstructed.
+// Thread (gi = tid & 15, gs = tid >> 4) owns rows 4 gi + {0..3}, 64 + 4 gi +
+// {0..3} and columns 4 gs + {0..3}; each group of four contraction indices
+// costs two 16-byte Q loads per index and one 16-byte H load per column for
+// 128 FMAs.  Per-tile FP32 partial sums are added into FP64 per thread.
+constexpr int kRtS = 64;  // s columns per tile
+constexpr int kRtStages = 2;
+size_t residual_tiled_smem(int c) {
+  return sizeof(float) * ((size_t)c * TM + (size_t)kRtStages * kRtS * (c + TM));
+}
+__global__ void __launch_bounds__(256, 2)
+    residual_tiled_kernel(const float* __restrict__ X, int64_t n1, int64_t S,
+                          const float* __restrict__ Q1, int c, const float* __restrict__ H,
+                          double* __restrict__ acc) {
+  extern __shared__ __align__(16) float rsm[];
+  float* Qs = rsm;                              // [c][TM]
+  float* Hs = Qs + c * TM;                      // stages x [kRtS][c]
+  float* Xs = Hs + kRtStages * kRtS * c;        // stages x [kRtS][TM]
+  __shared__ double red[2][8];
+  const int tid = threadIdx.x, gi = tid & 15, gs = tid >> 4;
+  const int64_t i0 = (int64_t)blockIdx.y * TM;
+  const int64_t ntile = (S + kRtS - 1) / kRtS;
+  for (int q = tid; q < c * (TM / 4); q += 256) {
+    const int k = q / (TM / 4), c4 = q % (TM / 4);
+    const int64_t i = i0 + 4 * c4;
+    const bool ok = i < n1;
+    cp_async16(Qs + k * TM + 4 * c4, ok ? (const void*)(Q1 + i + n1 * k) : (const void*)Q1, ok);
+  }
+  cp_commit();
+  auto issue = [&](int64_t t, int st) {
+    if (t < ntile) {
+      const int64_t s0 = t * kRtS;
+      float* hs = Hs + st * kRtS * c;
+      float* xs = Xs + st * kRtS * TM;
+      for (int e = 4 * tid; e < kRtS * c; e += 4 * 256) {  // a copy stays within one s (c % 4 == 0)
+        const bool ok = s0 + e / c < S;
+        cp_async16(hs + e, ok ? (const void*)(H + c * s0 + e) : (const void*)H, ok);
+      }
+      for (int q = tid; q < kRtS * (TM / 4); q += 256) {
+        const int sl = q / (TM / 4), c4 = q % (TM / 4);
+        const int64_t sg = s0 + sl, i = i0 + 4 * c4;
+        const bool ok = sg < S && i < n1;
+        cp_async16(xs + sl * TM + 4 * c4, ok ? (const void*)(X + i + n1 * sg) : (const void*)X, ok);
+      }
+    }
+    cp_commit();  // possibly empty: keeps one group per tile slot
+  };
+  const int64_t t0 = blockIdx.x, dt = gridDim.x;
+#pragma unroll 1
+  for (int st = 0; st < kRtStages - 1; ++st) issue(t0 + st * dt, st);
+  double dd = 0.0, xx = 0.0;
+  int st = 0;
+#pragma unroll 1
+  for (int64_t t = t0; t < ntile; t += dt) {
+    __syncthreads();  // the stage refilled below was consumed one tile ago
+    issue(t + (kRtStages - 1) * dt, (st + kRtStages - 1) % kRtStages);
+    cp_wait<kRtStages - 1>();
+    __syncthreads();
+    const float* hs = Hs + st * kRtS * c;
+    const float* xs = Xs + st * kRtS * TM;
+    float xh[8][4];
+#pragma unroll
+    for (int a = 0; a < 8; ++a)
+#pragma unroll
+      for (int b = 0; b < 4; ++b) xh[a][b] = 0.f;
+#pragma unroll 1
+    for (int k = 0; k < c; k += 4) {
+      float4 hv[4];
+#pragma unroll
+      for (int b = 0; b < 4; ++b) hv[b] = *reinterpret_cast<const float4*>(hs + (4 * gs + b) * c + k);
+#pragma unroll
+      for (int kk = 0; kk < 4; ++kk) {
+        const float4 q0 = *reinterpret_cast<const float4*>(Qs + (k + kk) * TM + 4 * gi);
+        const float4 q1 = *reinterpret_cast<const float4*>(Qs + (k + kk) * TM + 64 + 4 * gi);
+        const float qa[8] = {q0.x, q0.y, q0.z, q0.w, q1.x, q1.y, q1.z, q1.w};
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+          const float hb = comp(hv[b], kk);
+#pragma unroll
+          for (int a = 0; a < 8; ++a) xh[a][b] = fmaf(qa[a], hb, xh[a][b]);
+        }
+      }
+    }
+    const int64_t s0 = t * kRtS;
+    float d2 = 0.f, x2 = 0.f;
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+      const int sl = 4 * gs + b;
+      if (s0 + sl >= S) continue;
+#pragma unroll
+      for (int half = 0; half < 2; ++half) {
+        const int64_t ib = i0 + half * 64 + 4 * gi;
+        const float4 xq = *reinterpret_cast<const float4*>(xs + sl * TM + half * 64 + 4 * gi);
+        const float xv[4] = {xq.x, xq.y, xq.z, xq.w};
+#pragma unroll
+        for (int a = 0; a < 4; ++a) {
+          if (ib + a >= n1) continue;
+          const float df = xv[a] - xh[half * 4 + a][b];
+          d2 = fmaf(df, df, d2);
+          x2 = fmaf(xv[a], xv[a], x2);
+        }
+      }
+    }
+    dd += d2;
+    xx += x2;
+    st = (st + 1) % kRtStages;
+  }
+  cp_wait<0>();
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    dd += __shfl_xor_sync(0xffffffffu, dd, o);
+    xx += __shfl_xor_sync(0xffffffffu, xx, o);
+  }
+  if ((tid & 31) == 0) {
+    red[0][tid >> 5] = dd;
+    red[1][tid >> 5] = xx;
+  }
+  __syncthreads();
+  if (tid == 0) {
+    double a = 0, b = 0;
+    for (int w = 0; w < 8; ++w) {
+      a += red[0][w];
+      b += red[1][w];
+    }
+    atomicAdd(acc, a);
+    atomicAdd(acc + 1, b);
+  }
+}
+
 // ----------------------------------------------------------------------------
 // Tiled TTM with 128-row tiles (the main FP32 contraction):
 //   out[s + ldo*k] (=|+=) sum_i A[i + lda*s] F[i + ldf*k]
@@ -1067,7 +1200,19 @@ void residual_f32(const void* X, krp_dtype xt, int64_t n1, int64_t S, const floa
   const bool aligned = (reinterpret_cast<uintptr_t>(X) & 15) == 0;
   if (xt == KRP_F32) {
     const float* Xf = static_cast<const float*>(X);
-    if (aligned && n1 % 4 == 0) {
+    const bool qh_aligned = ((reinterpret_cast<uintptr_t>(Q1) | reinterpret_cast<uintptr_t>(H)) & 15) == 0;
+    if (aligned && qh_aligned && n1 % 4 == 0 && l % 4 == 0 && l <= 64) {
+      const size_t smem = residual_tiled_smem(l);
+      set_dyn_smem(residual_tiled_kernel, smem);
+      int per_sm = 0, sms = 0, dev = 0;
+      KRP_CUDA_CHECK(cudaGetDevice(&dev));
+      KRP_CUDA_CHECK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+      KRP_CUDA_CHECK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, residual_tiled_kernel, 256, smem));
+      const int64_t nib = (n1 + TM - 1) / TM, ntile = (S + kRtS - 1) / kRtS;
+      const int64_t want = std::max<int64_t>(1, (int64_t)std::max(per_sm, 1) * sms / nib);
+      const dim3 g2((unsigned)std::min<int64_t>(ntile, want), (unsigned)nib);
+      residual_tiled_kernel<<<g2, 256, smem, stream()>>>(Xf, n1, S, Q1, l, H, acc);
+    } else if (aligned && n1 % 4 == 0) {
       const size_t smem = sizeof(float) * TM * TM;
       set_dyn_smem(residual_kernel<float, true>, smem);
       residual_kernel<float, true><<<grid, 256, smem, stream()>>>(Xf, n1, S, Q1, l, H, acc);

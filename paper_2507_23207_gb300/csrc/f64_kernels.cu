@@ -2,6 +2,8 @@
 // HOSVD of the small core used for rank truncation, and helpers.
 #include <algorithm>
 
+#include <cooperative_groups.h>
+
 #include "common.cuh"
 
 namespace krp {
@@ -207,15 +209,21 @@ __device__ double block_sum(double v, double* red) {
   return s;
 }
 
+// Per-thread work bounds of a Jacobi round (kEigThreads threads, n <= 64 so
+// P <= 32 pairs and jstep = threads / P >= 8): blocks per thread and V rows.
+constexpr int kJm = (32 + kEigThreads / 32 - 1) / (kEigThreads / 32);
+constexpr int kJv = (64 + kEigThreads / 32 - 1) / (kEigThreads / 32);
+
 template <int EP>  // row pitch of the padded matrices
-__device__ void jacobi32(float (*S)[EP], float (*V)[EP], int n, float* cs, float* sn, int* pp,
-                         int* qq, double* red) {
-  const int tid = threadIdx.x, P = n / 2;
+__device__ void jacobi32(float (*Sa)[EP], float (*Sb)[EP], float (*V)[EP], int n, double* red) {
+  const int tid = threadIdx.x, lane = tid & 31, P = n / 2;
   // fixed work split of the round updates (no per-item integer division):
   // threads t < jstep * P own pair ib0 = t % P and rows/blocks jb0 + m jstep
   const int jstep = (int)blockDim.x / P;
   const int ib0 = tid % P;
   const int jb0 = (tid < jstep * P) ? tid / P : n;  // idle threads get an empty range
+  float(*S)[EP] = Sa;    // current matrix
+  float(*Sn)[EP] = Sb;   // the round writes the rotated matrix here
   for (int sweep = 0; sweep < kEigSweeps32; ++sweep) {
     double o = 0.0, dg = 0.0;
     for (int e = tid; e < n * n; e += blockDim.x) {
@@ -228,83 +236,140 @@ __device__ void jacobi32(float (*S)[EP], float (*V)[EP], int n, float* cs, float
     }
     const double off = block_sum(o, red);
     const double dia = block_sum(dg, red + 8);
-    // off-diagonal norm at 1e-6 of the diagonal's: the FP64 stage does the rest
+    // off-diagonal norm at 1e-6 of the diagonal's: the FP64 stage does the
+    // rest (stopping at 1e-4 left the refined vectors of graded spectra, such
+    // as a block Hankel's, orthonormal only to ~1e-5)
     if (!(off > 1e-12 * dia) || off == 0.0) break;
     for (int round = 0; round < n - 1; ++round) {
-      if (tid < P) {
+      // every warp forms all P rotations of the round, lane k the k-th, from
+      // the matrix of the previous round (read-only during this round), and
+      // hands them to the other lanes by shuffles: one barrier per round
+      int p = 0, q = 0;
+      float c = 1.f, s = 0.f;
+      if (lane < P) {
         // round-robin tournament: position 0 holds player 0, position k >= 1
         // holds player ((k - 1 + round) mod (n - 1)) + 1; pairs (k, n-1-k)
-        const int k2 = n - 1 - tid;
-        int p = (tid == 0) ? 0 : ((tid - 1 + round) % (n - 1)) + 1;
-        int q = ((k2 - 1 + round) % (n - 1)) + 1;
+        const int k2 = n - 1 - lane;
+        p = (lane == 0) ? 0 : ((lane - 1 + round) % (n - 1)) + 1;
+        q = ((k2 - 1 + round) % (n - 1)) + 1;
         if (p > q) {
           const int t = p;
           p = q;
           q = t;
         }
-        pp[tid] = p;
-        qq[tid] = q;
         const float apq = S[p][q], app = S[p][p], aqq = S[q][q];
-        float c = 1.f, s = 0.f;
-        if (fabsf(apq) > 1e-8f * sqrtf(fabsf(app * aqq))) {
-          const float theta = (aqq - app) / (2.f * apq);
-          const float t = (theta >= 0.f ? 1.f : -1.f) / (fabsf(theta) + sqrtf(1.f + theta * theta));
-          c = 1.f / sqrtf(1.f + t * t);
+        if (apq * apq > 1e-16f * fabsf(app * aqq)) {
+          // t = tan of the angle: the root of t^2 + 2 theta t - 1 = 0 with
+          // |t| <= 1, theta = (aqq - app) / (2 apq), written without theta:
+          // t = 2 apq sgn(dq) / (|dq| + sqrt(dq^2 + 4 apq^2)), dq = aqq - app.
+          // t only decides how far apq is reduced; c^2 + s^2 = 1 is kept to
+          // FP32 rounding by one Newton step on the hardware rsqrt.
+          const float dq = aqq - app;
+          const float h = sqrtf(fmaf(dq, dq, 4.f * apq * apq));
+          const float t = __fdividef(2.f * apq * copysignf(1.f, dq), fabsf(dq) + h);
+          const float x = fmaf(t, t, 1.f);
+          c = rsqrtf(x);
+          c = c * fmaf(-0.5f * x * c, c, 1.5f);
           s = t * c;
         }
-        cs[tid] = c;
-        sn[tid] = s;
+      }
+      const int pi = __shfl_sync(0xffffffffu, p, ib0), qi = __shfl_sync(0xffffffffu, q, ib0);
+      const float ci = __shfl_sync(0xffffffffu, c, ib0), si = __shfl_sync(0xffffffffu, s, ib0);
+      // 2x2 blocks (i, j) of S: thread t takes i = t % P and j = t / P + m * jstep
+      // (m < kJm); every load of the round is issued before any store, so the
+      // shared-memory round trips overlap (S and Sn are swapped at run time,
+      // which keeps the compiler from reordering them itself)
+      int pj[kJm], qj[kJm];
+      float cj[kJm], sj[kJm], ea[kJm], eb[kJm], ec[kJm], ed[kJm];
+      bool live[kJm];
+#pragma unroll
+      for (int m = 0; m < kJm; ++m) {
+        const int j = jb0 + m * jstep;
+        live[m] = j < P;
+        const int jj = live[m] ? j : 0;
+        pj[m] = __shfl_sync(0xffffffffu, p, jj);
+        qj[m] = __shfl_sync(0xffffffffu, q, jj);
+        cj[m] = __shfl_sync(0xffffffffu, c, jj);
+        sj[m] = __shfl_sync(0xffffffffu, s, jj);
+      }
+#pragma unroll
+      for (int m = 0; m < kJm; ++m) {
+        ea[m] = S[pi][pj[m]];
+        eb[m] = S[pi][qj[m]];
+        ec[m] = S[qi][pj[m]];
+        ed[m] = S[qi][qj[m]];
+      }
+      float vp[kJv], vq[kJv];
+#pragma unroll
+      for (int m = 0; m < kJv; ++m) {
+        const int r = min(jb0 + m * jstep, n - 1);
+        vp[m] = V[r][pi];
+        vq[m] = V[r][qi];
+      }
+#pragma unroll
+      for (int m = 0; m < kJm; ++m) {
+        if (!live[m]) continue;
+        // columns (p_j, q_j), then rows (p_i, q_i)
+        const float a1 = cj[m] * ea[m] - sj[m] * eb[m], b1 = sj[m] * ea[m] + cj[m] * eb[m];
+        const float c1 = cj[m] * ec[m] - sj[m] * ed[m], d1 = sj[m] * ec[m] + cj[m] * ed[m];
+        float a2 = ci * a1 - si * c1, c2 = si * a1 + ci * c1;
+        float b2 = ci * b1 - si * d1, d2 = si * b1 + ci * d1;
+        if (ib0 == jb0 + m * jstep && si != 0.f) {  // the rotated pair's coupling is zero by construction
+          b2 = 0.f;
+          c2 = 0.f;
+        }
+        Sn[pi][pj[m]] = a2;
+        Sn[pi][qj[m]] = b2;
+        Sn[qi][pj[m]] = c2;
+        Sn[qi][qj[m]] = d2;
+      }
+      // rows r of V for pair k = t % P: r = t / P + m * jstep
+#pragma unroll
+      for (int m = 0; m < kJv; ++m) {
+        const int r = jb0 + m * jstep;
+        if (r >= n) continue;
+        V[r][pi] = ci * vp[m] - si * vq[m];
+        V[r][qi] = si * vp[m] + ci * vq[m];
       }
       __syncthreads();
-      // 2x2 blocks (i, j) of S: thread t takes i = t % P and j = t / P + k * jstep
-      for (int j = jb0; j < P; j += jstep) {
-        {
-          const int i = ib0;
-          const int pi = pp[i], qi = qq[i], pj = pp[j], qj = qq[j];
-          const float ci = cs[i], si = sn[i], cj = cs[j], sj = sn[j];
-          const float a = S[pi][pj], bq = S[pi][qj], cq = S[qi][pj], d = S[qi][qj];
-          // columns (p_j, q_j), then rows (p_i, q_i)
-          const float a1 = cj * a - sj * bq, b1 = sj * a + cj * bq;
-          const float c1 = cj * cq - sj * d, d1 = sj * cq + cj * d;
-          float a2 = ci * a1 - si * c1, c2 = si * a1 + ci * c1;
-          float b2 = ci * b1 - si * d1, d2 = si * b1 + ci * d1;
-          if (i == j && si != 0.f) {  // the rotated pair's coupling is zero by construction
-            b2 = 0.f;
-            c2 = 0.f;
-          }
-          S[pi][pj] = a2;
-          S[pi][qj] = b2;
-          S[qi][pj] = c2;
-          S[qi][qj] = d2;
-        }
-      }
-      // rows r of V for pair k: thread t takes k = t % P and r = t / P + m * jstep
-      {
-        const int k = ib0;
-        const int p = pp[k], q = qq[k];
-        const float c = cs[k], s = sn[k];
-        for (int r = jb0; r < n; r += jstep) {
-          const float vp = V[r][p], vq = V[r][q];
-          V[r][p] = c * vp - s * vq;
-          V[r][q] = s * vp + c * vq;
-        }
-      }
-      __syncthreads();
+      float(*t)[EP] = S;
+      S = Sn;
+      Sn = t;
     }
   }
 }
 
-// C = op(A) B for l x l matrices in shared memory (op = transpose if TA);
-// with SYM only the upper triangle is computed and mirrored.
-template <bool TA, bool SYM, int EP>
+// C = A B for l x l matrices in shared memory.
+template <int EP>
 __device__ void smem_gemm(const double (*A)[EP], const double (*B)[EP], double (*C)[EP], int l) {
   for (int e = threadIdx.x; e < l * l; e += blockDim.x) {
     const int i = e % l, j = e / l;
-    if (SYM && i > j) continue;
     double acc = 0.0;
-    for (int k = 0; k < l; ++k) acc = fma(TA ? A[k][i] : A[i][k], B[k][j], acc);
+    for (int k = 0; k < l; ++k) acc = fma(A[i][k], B[k][j], acc);
     C[i][j] = acc;
-    if (SYM) C[j][i] = acc;
+  }
+}
+
+// S = X^T T and G = X^T X (both symmetric when T = A X with A symmetric),
+// computed together over the packed pairs i <= j and mirrored: an FP64 warp
+// instruction costs the same with idle lanes, so the pairs are enumerated
+// rather than masked out of a full l x l loop.
+template <int EP>
+__device__ void smem_sym_pair(const double (*X)[EP], const double (*T)[EP], double (*S)[EP],
+                              double (*G)[EP], const unsigned short* tri, int l) {
+  const int np = l * (l + 1) / 2;
+  for (int p = threadIdx.x; p < np; p += blockDim.x) {
+    const int i = tri[p] & 0xff, j = tri[p] >> 8;
+    double s = 0.0, g = 0.0;
+    for (int k = 0; k < l; ++k) {
+      const double xi = X[k][i];
+      s = fma(xi, T[k][j], s);
+      g = fma(xi, X[k][j], g);
+    }
+    S[i][j] = s;
+    S[j][i] = s;
+    G[i][j] = g;
+    G[j][i] = g;
   }
 }
 
@@ -322,16 +387,20 @@ __global__ void __launch_bounds__(kEigThreads) eig_kernel(const EigJob* __restri
   double(*T)[kEP] = reinterpret_cast<double(*)[kEP]>(eig_smem + 2 * kMat);
   double(*Sm)[kEP] = reinterpret_cast<double(*)[kEP]>(eig_smem + 3 * kMat);
   double(*Rm)[kEP] = reinterpret_cast<double(*)[kEP]>(eig_smem + 4 * kMat);
-  // the FP32 stage lives in T's storage
+  // the FP32 stage lives in T's storage (S, V) and Sm's (the second S buffer)
   float(*S32)[kEP] = reinterpret_cast<float(*)[kEP]>(eig_smem + 2 * kMat);
   float(*V32)[kEP] = reinterpret_cast<float(*)[kEP]>(eig_smem + 2 * kMat) + ML;
-  __shared__ float cs32[ML / 2], sn32[ML / 2];
-  __shared__ int pp[ML / 2], qq[ML / 2];
+  float(*S32b)[kEP] = reinterpret_cast<float(*)[kEP]>(eig_smem + 3 * kMat);
   __shared__ int order[ML];
   __shared__ double lam[ML];
   __shared__ double red[16];
   __shared__ float redf[8];
+  __shared__ unsigned short tri[ML * (ML + 1) / 2];
   const int tid = threadIdx.x;
+  for (int i = tid; i < l; i += blockDim.x) {  // pairs (i, j), i <= j, ordered by i
+    const int off = i * l - i * (i - 1) / 2;
+    for (int j = i; j < l; ++j) tri[off + j - i] = (unsigned short)(i | (j << 8));
+  }
 
   // scale by a power of two (exact) so that max |a_ij| is in [0.5, 1)
   float amax = 0.f;
@@ -357,7 +426,7 @@ __global__ void __launch_bounds__(kEigThreads) eig_kernel(const EigJob* __restri
     if (tid == 0) atomicExch(status, (int)KRP_ENUMERIC);
     return;
   }
-  jacobi32<kEP>(S32, V32, n, cs32, sn32, pp, qq, red);
+  jacobi32<kEP>(S32, S32b, V32, n, red);
   for (int e = tid; e < l * l; e += blockDim.x) {
     const int r = e % l, c = e / l;
     X[r][c] = (double)V32[r][c];
@@ -367,10 +436,9 @@ __global__ void __launch_bounds__(kEigThreads) eig_kernel(const EigJob* __restri
   for (int e = tid; e < l * l; e += blockDim.x) a2 = fma(A[e % l][e / l], A[e % l][e / l], a2);
   const double anorm = sqrt(block_sum(a2, red));
   for (int it = 0; it < kEigRefine; ++it) {
-    smem_gemm<false, false, kEP>(A, X, T, l);  // T = A X
+    smem_gemm<kEP>(A, X, T, l);  // T = A X
     __syncthreads();
-    smem_gemm<true, true, kEP>(X, T, Sm, l);  // S = X^T A X
-    smem_gemm<true, true, kEP>(X, X, Rm, l);  // X^T X (turned into R below)
+    smem_sym_pair<kEP>(X, T, Sm, Rm, tri, l);  // S = X^T A X, X^T X (turned into R below)
     __syncthreads();
     double soff = 0.0, r2 = 0.0;
     for (int e = tid; e < l * l; e += blockDim.x) {
@@ -393,7 +461,7 @@ __global__ void __launch_bounds__(kEigThreads) eig_kernel(const EigJob* __restri
       T[i][j] = eij;
     }
     __syncthreads();
-    smem_gemm<false, false, kEP>(X, T, Sm, l);  // X E
+    smem_gemm<kEP>(X, T, Sm, l);  // X E
     __syncthreads();
     for (int e = tid; e < l * l; e += blockDim.x) {
       const int i = e % l, j = e / l;
@@ -401,6 +469,198 @@ __global__ void __launch_bounds__(kEigThreads) eig_kernel(const EigJob* __restri
     }
     __syncthreads();
   }
+  if (tid == 0) {
+    for (int i = 0; i < l; ++i) order[i] = i;
+    for (int i = 1; i < l; ++i) {  // insertion sort, descending eigenvalue
+      const int key = order[i];
+      int j = i - 1;
+      while (j >= 0 && lam[order[j]] < lam[key]) {
+        order[j + 1] = order[j];
+        --j;
+      }
+      order[j + 1] = key;
+    }
+    bool ok = true;
+    for (int i = 0; i < l; ++i) ok = ok && isfinite(lam[i]);
+    if (!ok) atomicExch(status, (int)KRP_ENUMERIC);
+  }
+  __syncthreads();
+  for (int e = tid; e < l * job.r; e += blockDim.x) {
+    const int r = e % l, c = e / l;
+    job.U[e] = X[r][order[c]];
+  }
+  if (job.ev)
+    for (int i = tid; i < l; i += blockDim.x) job.ev[i] = lam[order[i]] / scale;
+}
+
+// Split form of the eigensolver for a few problems (a d-mode truncation): the
+// FP32 Jacobi stage runs one CTA per problem and leaves its eigenvectors X0
+// and the power-of-two scale in a scratch block; the FP64 refinement then runs
+// on a cluster of kEigCluster CTAs per problem, so that its O(l^3) FP64 work
+// (GB300: 0.5 FMA per clock per SM sub-partition) spreads over as many SMs.
+constexpr int kEigCluster = 8;
+constexpr int kEigScratch = kEigMaxL * kEigMaxL + 8;  // doubles per problem
+
+template <int ML>
+__global__ void __launch_bounds__(kEigThreads)
+    eig_jacobi_kernel(const EigJob* __restrict__ jobs, double* __restrict__ scratch, int* status) {
+  constexpr int kEP = ML + 1;
+  const EigJob job = jobs[blockIdx.x];
+  const int l = job.l;
+  const int n = (l + 1) & ~1;
+  extern __shared__ float ej_smem[];
+  float(*S32)[kEP] = reinterpret_cast<float(*)[kEP]>(ej_smem);
+  float(*S32b)[kEP] = reinterpret_cast<float(*)[kEP]>(ej_smem + ML * kEP);
+  float(*V32)[kEP] = reinterpret_cast<float(*)[kEP]>(ej_smem + 2 * ML * kEP);
+  __shared__ double red[16];
+  __shared__ float redf[8];
+  const int tid = threadIdx.x;
+  // scale by a power of two (exact) so that max |a_ij| is in [0.5, 1)
+  float amax = 0.f;
+  for (int e = tid; e < l * l; e += blockDim.x) amax = fmaxf(amax, (float)fabs(job.S[e]));
+  amax = warp_max(amax);
+  if ((tid & 31) == 0) redf[tid >> 5] = amax;
+  __syncthreads();
+  amax = 0.f;
+  for (int w = 0; w < (int)(blockDim.x >> 5); ++w) amax = fmaxf(amax, redf[w]);
+  int ex = 0;
+  if (amax > 0.f && isfinite(amax)) frexpf(amax, &ex);
+  const double scale = ldexp(1.0, -ex);
+  bool finite_in = true;
+  for (int e = tid; e < n * n; e += blockDim.x) {
+    const int r = e % n, c = e / n;
+    const double v = (r < l && c < l) ? job.S[r + l * c] * scale : 0.0;
+    finite_in = finite_in && isfinite(v);
+    S32[r][c] = (float)v;
+    V32[r][c] = (r == c) ? 1.f : 0.f;
+  }
+  double* out = scratch + (size_t)blockIdx.x * kEigScratch;
+  if (!__syncthreads_and(finite_in)) {
+    if (tid == 0) {
+      atomicExch(status, (int)KRP_ENUMERIC);
+      out[kEigMaxL * kEigMaxL] = 0.0;  // marks the problem as failed for the refinement
+    }
+    return;
+  }
+  jacobi32<kEP>(S32, S32b, V32, n, red);
+  for (int e = tid; e < l * l; e += blockDim.x) out[e] = (double)V32[e % l][e / l];
+  if (tid == 0) out[kEigMaxL * kEigMaxL] = scale;
+}
+
+// Ogita-Aishima refinement of X0 (see the fused kernel above) on a cluster:
+// CTA `rank` owns the columns [c0, c0 + w) of T = A X, S = X^T T, G = X^T X,
+// E and X + X E; each CTA holds all of A and X.  Per step the CTAs exchange
+// their eigenvalue estimates and partial norms, then their new X columns,
+// through distributed shared memory, with one cluster barrier after each.
+template <int ML>
+__global__ void __cluster_dims__(kEigCluster, 1, 1) __launch_bounds__(kEigThreads)
+    eig_refine_kernel(const EigJob* __restrict__ jobs, const double* __restrict__ scratch,
+                      int* status) {
+  namespace cg = cooperative_groups;
+  cg::cluster_group cluster = cg::this_cluster();
+  constexpr int kEP = ML + 1;
+  constexpr int CW = (ML + kEigCluster - 1) / kEigCluster;
+  const int rank = (int)cluster.block_rank();
+  const EigJob job = jobs[blockIdx.y];
+  const int l = job.l;
+  const int cw = (l + kEigCluster - 1) / kEigCluster;
+  const int c0 = rank * cw;
+  const int w = max(0, min(l, c0 + cw) - c0);
+  extern __shared__ double er_smem[];
+  double(*A)[kEP] = reinterpret_cast<double(*)[kEP]>(er_smem);
+  double(*Xa)[kEP] = reinterpret_cast<double(*)[kEP]>(er_smem + ML * kEP);
+  double(*Xb)[kEP] = reinterpret_cast<double(*)[kEP]>(er_smem + 2 * ML * kEP);
+  __shared__ double Tc[ML][CW + 1], Sc[ML][CW + 1], Gc[ML][CW + 1];
+  __shared__ double lam[ML];
+  __shared__ double part[kEigCluster][2];
+  __shared__ double red[16];
+  __shared__ int order[ML];
+  const int tid = threadIdx.x;
+  const double* src = scratch + (size_t)blockIdx.y * kEigScratch;
+  const double scale = src[kEigMaxL * kEigMaxL];
+  const bool failed = !(scale > 0.0);  // uniform over the cluster
+  double a2 = 0.0;
+  for (int e = tid; e < l * l; e += blockDim.x) {
+    const int r = e % l, c = e / l;
+    const double v = failed ? 0.0 : job.S[e] * scale;
+    A[r][c] = v;
+    Xa[r][c] = failed ? 0.0 : src[e];
+    a2 = fma(v, v, a2);
+  }
+  const double anorm = sqrt(block_sum(a2, red));  // its barriers publish A and X
+  double(*X)[kEP] = Xa;
+  double(*Xn)[kEP] = Xb;
+  for (int it = 0; it < kEigRefine && !failed; ++it) {
+    for (int e = tid; e < l * w; e += blockDim.x) {  // T = A X(:, own)
+      const int i = e % l, cc = e / l;
+      double acc = 0.0;
+      for (int k = 0; k < l; ++k) acc = fma(A[i][k], X[k][c0 + cc], acc);
+      Tc[i][cc] = acc;
+    }
+    __syncthreads();
+    for (int e = tid; e < l * w; e += blockDim.x) {  // S, G (own columns)
+      const int i = e % l, cc = e / l;
+      double sacc = 0.0, gacc = 0.0;
+      for (int k = 0; k < l; ++k) {
+        const double xi = X[k][i];
+        sacc = fma(xi, Tc[k][cc], sacc);
+        gacc = fma(xi, X[k][c0 + cc], gacc);
+      }
+      Sc[i][cc] = sacc;
+      Gc[i][cc] = gacc;
+    }
+    __syncthreads();
+    double soff = 0.0, r2 = 0.0;
+    for (int e = tid; e < l * w; e += blockDim.x) {
+      const int i = e % l, cc = e / l, j = c0 + cc;
+      const double rij = (i == j ? 1.0 : 0.0) - Gc[i][cc];
+      r2 = fma(rij, rij, r2);
+      if (i != j) soff = fma(Sc[i][cc], Sc[i][cc], soff);
+    }
+    const double sn_part = block_sum(soff, red);
+    const double rn_part = block_sum(r2, red + 8);
+    // own eigenvalue estimates and partial norms to every CTA of the cluster
+    for (int e = tid; e < w * kEigCluster; e += blockDim.x) {
+      const int cc = e % w, q = e / w, j = c0 + cc;
+      double* rl = cluster.map_shared_rank(lam, q);
+      rl[j] = Sc[j][cc] / Gc[j][cc];  // 1 - r_jj = (X^T X)_jj
+    }
+    if (tid < kEigCluster) {
+      double* rp = cluster.map_shared_rank(&part[0][0], tid);
+      rp[2 * rank] = sn_part;
+      rp[2 * rank + 1] = rn_part;
+    }
+    cluster.sync();
+    double sn = 0.0, rn = 0.0;
+    for (int q = 0; q < kEigCluster; ++q) {
+      sn += part[q][0];
+      rn += part[q][1];
+    }
+    const double delta = 2.0 * (sqrt(sn) + anorm * sqrt(rn));
+    for (int e = tid; e < l * w; e += blockDim.x) {  // E (own columns) into Tc
+      const int i = e % l, cc = e / l, j = c0 + cc;
+      const double rij = (i == j ? 1.0 : 0.0) - Gc[i][cc];
+      double eij = 0.5 * rij;
+      const double gap = lam[j] - lam[i];
+      if (i != j && fabs(gap) > delta) eij = (Sc[i][cc] + lam[j] * rij) / gap;
+      Tc[i][cc] = eij;
+    }
+    __syncthreads();
+    for (int e = tid; e < l * w; e += blockDim.x) {  // X + X E (own columns) to every CTA
+      const int k = e % l, cc = e / l, j = c0 + cc;
+      double acc = X[k][j];
+      for (int i = 0; i < l; ++i) acc = fma(X[k][i], Tc[i][cc], acc);
+      for (int q = 0; q < kEigCluster; ++q) {
+        double* rx = cluster.map_shared_rank(&Xn[0][0], q);
+        rx[k * kEP + j] = acc;
+      }
+    }
+    cluster.sync();
+    double(*t)[kEP] = X;
+    X = Xn;
+    Xn = t;
+  }
+  if (rank != 0 || failed) return;
   if (tid == 0) {
     for (int i = 0; i < l; ++i) order[i] = i;
     for (int i = 1; i < l; ++i) {  // insertion sort, descending eigenvalue
@@ -552,20 +812,37 @@ __global__ void __launch_bounds__(256) cqr_gram_kernel(const CqrBatch jobs, int*
 }
 
 // Cholesky G (+ shift) = R^T R of one l x l matrix per CTA; R stored in Rk[pass].
-__global__ void __launch_bounds__(256) cqr_chol_kernel(const CqrBatch jobs, int pass) {
+// GB300 runs FP64 at 0.5 FMA per clock in each of an SM's four sub-partitions,
+// so the CTA is four warps (one per sub-partition) and a column step is one
+// barrier: every thread takes d_j = A[j, j] and its reciprocal itself, then
+// updates its share of the trailing upper triangle,
+//   A[a, b] -= (A[j, a] / d_j) A[j, b]   (j < a <= b),
+// over a packed pair list, four pairs per pass with all loads ahead of the
+// stores.  Row j is not touched after step j, so the unscaled rows give
+// R[j, i] = A[j, i] / sqrt(d_j) in one parallel pass at the end (sqrt off the
+// dependent chain).
+constexpr int kCholThreads = 128;
+__global__ void __launch_bounds__(kCholThreads) cqr_chol_kernel(const CqrBatch jobs, int pass) {
   const CqrJob job = jobs.job[blockIdx.x];
   const int l = job.l;
   __shared__ double A[kCqrMaxL][kCqrMaxL + 1];
-  __shared__ double diag0[kCqrMaxL];
-  __shared__ double piv, invd, tol;
-  __shared__ int refill;
+  __shared__ double diag0[kCqrMaxL], rsq[kCqrMaxL], sq[kCqrMaxL];
+  __shared__ unsigned short tri[kCqrMaxL * (kCqrMaxL + 1) / 2];
+  __shared__ double tol;
   __shared__ unsigned long long mask;
-  for (int e = threadIdx.x; e < l * l; e += blockDim.x) {
+  const int tid = threadIdx.x;
+  for (int e = tid; e < l * l; e += blockDim.x) {
     const int a = e % l, b = e / l;
-    A[a][b] = (a <= b) ? job.G[a + l * b] : job.G[b + l * a];
+    if (a <= b) A[a][b] = job.G[a + l * b];
+  }
+  // pairs (a, b), a <= b, ordered by a: those with a > j start at
+  // off(j + 1) = sum_{a <= j} (l - a)
+  for (int a = tid; a < l; a += blockDim.x) {
+    const int off = a * l - a * (a - 1) / 2;
+    for (int b = a; b < l; ++b) tri[off + b - a] = (unsigned short)(a | (b << 8));
   }
   __syncthreads();
-  if (threadIdx.x == 0) {
+  if (tid == 0) {
     double tr = 0.0, dmax = 0.0;
     for (int j = 0; j < l; ++j) {
       diag0[j] = A[j][j];
@@ -580,78 +857,123 @@ __global__ void __launch_bounds__(256) cqr_chol_kernel(const CqrBatch jobs, int 
     // pass 0: only exactly zero columns are refilled (the shift handles the
     // rest); later passes: pivots lost to cancellation
     tol = (pass == 0) ? 0.0 : 64.0 * l * 0x1p-53 * dmax;
-    mask = 0ull;
+  }
+  __syncthreads();
+  const int npair = l * (l + 1) / 2;
+  const double tl = tol;
+  unsigned long long msk = 0ull;
+  int off = 0;
+  for (int j = 0; j < l; ++j) {
+    off += l - j;  // first pair with a > j
+    const double d = A[j][j];
+    const bool deficient = (pass == 0) ? !(diag0[j] > 0.0) : !(d > tl);
+    // a refilled column gets R[j, j] = 1 and a zero row: no update
+    const double nid = deficient ? 0.0 : -__drcp_rn(d);
+    msk |= (unsigned long long)deficient << j;
+    for (int e0 = off; e0 < npair; e0 += 4 * kCholThreads) {
+      int ia[4], ib[4];
+      bool ok[4];
+      double ja[4], jb[4], ab[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int e = e0 + tid + kCholThreads * q;
+        ok[q] = e < npair;
+        const unsigned t = ok[q] ? tri[e] : 0u;
+        ia[q] = t & 0xff;
+        ib[q] = t >> 8;
+      }
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        ja[q] = A[j][ia[q]];
+        jb[q] = A[j][ib[q]];
+        ab[q] = A[ia[q]][ib[q]];
+      }
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+        if (ok[q]) A[ia[q]][ib[q]] = fma(ja[q] * nid, jb[q], ab[q]);
+    }
+    __syncthreads();
+  }
+  if (tid == 0) mask = msk;
+  __syncthreads();
+  msk = mask;
+  for (int j = tid; j < l; j += blockDim.x) {
+    const bool deficient = (msk >> j) & 1ull;
+    const double r = deficient ? 1.0 : sqrt(A[j][j]);
+    sq[j] = r;
+    rsq[j] = deficient ? 0.0 : 1.0 / r;
   }
   __syncthreads();
   double* R = job.Rk + (size_t)pass * l * l;
-  // Right-looking Cholesky, two barriers per column: row j of A stays
-  // unscaled, R[j, i] = A[j, i] / r_jj and the trailing update subtracts
-  // A[j, a] A[j, b] / d_j (d_j = r_jj^2), all from the same unscaled row.
-  for (int j = 0; j < l; ++j) {
-    if (threadIdx.x == 0) {
-      const double d = A[j][j];
-      const bool deficient = (pass == 0) ? !(diag0[j] > 0.0) : !(d > tol);
-      refill = deficient;
-      const double rj = deficient ? 1.0 : sqrt(d);
-      piv = rj;
-      invd = deficient ? 0.0 : 1.0 / d;
-      if (deficient) mask |= 1ull << j;
-    }
-    __syncthreads();
-    const double dj = piv, id = invd;
-    const double ir = id * dj;  // 1 / r_jj (0 for a refilled column)
-    for (int i = j + threadIdx.x; i < l; i += blockDim.x) R[j + l * i] = (i == j) ? dj : A[j][i] * ir;
-    const int rem = l - j - 1;
-    for (int e = threadIdx.x; e < rem * rem; e += blockDim.x) {
-      const int a = j + 1 + e % rem, b = j + 1 + e / rem;
-      if (a <= b) A[a][b] = fma(-A[j][a] * id, A[j][b], A[a][b]);
-    }
-    __syncthreads();
-  }
-  // zero the lower triangle of R
-  for (int e = threadIdx.x; e < l * l; e += blockDim.x) {
+  for (int e = tid; e < l * l; e += blockDim.x) {
     const int a = e % l, b = e / l;
-    if (a > b) R[a + l * b] = 0.0;
+    R[e] = (a < b) ? A[a][b] * rsq[a] : (a == b ? sq[a] : 0.0);
   }
-  if (threadIdx.x == 0) *job.defmask = mask;
+  if (tid == 0) *job.defmask = msk;
   if (job.R && pass == 2) {
-    __syncthreads();
-    // R = R3 R2 R1 (upper triangular products)
+    __syncthreads();  // R3 (global) written by this block
+    // R = R3 (R2 R1): T = R2 R1 into the lower triangle of A (T[a, b] at
+    // A[b][a]), then R3 T; both upper triangular products cost l^3 / 6
     const double* R1 = job.Rk;
     const double* R2 = job.Rk + (size_t)l * l;
     const double* R3 = job.Rk + 2 * (size_t)l * l;
-    for (int e = threadIdx.x; e < l * l; e += blockDim.x) {
+    for (int p = tid; p < npair; p += blockDim.x) {
+      const int a = tri[p] & 0xff, b = tri[p] >> 8;
+      double t = 0.0;
+      for (int q = a; q <= b; ++q) t = fma(R2[a + l * q], R1[q + l * b], t);
+      A[b][a] = t;
+    }
+    __syncthreads();
+    for (int e = tid; e < l * l; e += blockDim.x) {
       const int a = e % l, b = e / l;
       double acc = 0.0;
-      for (int k = a; k <= b; ++k) {
-        double t = 0.0;
-        for (int q = k; q <= b; ++q) t = fma(R2[k + l * q], R1[q + l * b], t);
-        acc = fma(R3[a + l * k], t, acc);
-      }
+      for (int k = a; k <= b; ++k) acc = fma(R3[a + l * k], A[b][k], acc);
       job.R[e] = (a <= b) ? acc : 0.0;
     }
   }
 }
 
-// W_out[r, :] = W_in[r, :] R^{-1} by forward substitution, 16 rows per CTA
-// and 16 threads per row: for column j the 16 threads split the dot product
-// sum_{k<j} x_k R[k, j] and reduce it with shuffles, so that the FP64 work
-// (GB300: 2 FMA/clk/SM) is spread over all four schedulers of many SMs.
-constexpr int kSolveRows = 16;
-template <bool FROM_INPUT, bool TO_Q>
-__global__ void __launch_bounds__(256) cqr_solve_kernel(const CqrBatch jobs, int pass) {
+// W_out[r, :] = W_in[r, :] R^{-1} by forward substitution.  GB300 runs FP64
+// at 0.5 FMA per clock in each of an SM's four sub-partitions, so one warp
+// instruction occupies its sub-partition's FP64 unit for ~64 clocks: the
+// rows are spread so that as many warps as possible, each on its own
+// sub-partition, share the work.  A CTA of 4 warps takes 32 / TPR rows per
+// warp; the TPR lanes of a row split the dot product sum_{k<j} x_k R[k, j]
+// (k = lane mod TPR, TPR apart) and combine it with log2(TPR) shuffles.  R is
+// copied to shared memory column-major (column j contiguous in k).
+constexpr int kSolveThreads = 128;
+constexpr int kSolveRowPitch = kCqrMaxL + 1;
+template <int TPR>
+__host__ __device__ constexpr int solve_rows() { return kSolveThreads / TPR; }
+template <int TPR>
+constexpr size_t solve_smem() {
+  return sizeof(double) * ((size_t)kCqrMaxL * kCqrMaxL + (size_t)solve_rows<TPR>() * kSolveRowPitch + kCqrMaxL);
+}
+template <bool FROM_INPUT, bool TO_Q, int TPR>
+__global__ void __launch_bounds__(kSolveThreads) cqr_solve_kernel(const CqrBatch jobs, int pass) {
+  constexpr int ROWS = solve_rows<TPR>();
   const CqrJob job = jobs.job[blockIdx.y];
   const int l = job.l;
-  const int64_t r0 = (int64_t)blockIdx.x * kSolveRows;
+  const int64_t r0 = (int64_t)blockIdx.x * ROWS;
   if (r0 >= job.m) return;
-  __shared__ double R[kCqrMaxL][kCqrMaxL + 1];
-  __shared__ double X[kSolveRows][kCqrMaxL + 1];
-  __shared__ double invd[kCqrMaxL];
+  extern __shared__ double csm[];
+  double* Rs = csm;
+  double(*X)[kSolveRowPitch] = reinterpret_cast<double(*)[kSolveRowPitch]>(csm + kCqrMaxL * kCqrMaxL);
+  double* invd = csm + kCqrMaxL * kCqrMaxL + ROWS * kSolveRowPitch;
+  const int tid = threadIdx.x;
   const double* Rg = job.Rk + (size_t)pass * l * l;
-  for (int e = threadIdx.x; e < l * l; e += blockDim.x) R[e % l][e / l] = Rg[e];
-  const int rows = (int)((job.m - r0) < kSolveRows ? (job.m - r0) : kSolveRows);
-  for (int e = threadIdx.x; e < kSolveRows * l; e += blockDim.x) {
-    const int rr = e % kSolveRows, j = e / kSolveRows;
+  const int ll = l * l;
+  for (int e = tid; e < ll; e += 4 * kSolveThreads) {
+    double v[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) v[q] = (e + kSolveThreads * q < ll) ? Rg[e + kSolveThreads * q] : 0.0;
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+      if (e + kSolveThreads * q < ll) Rs[e + kSolveThreads * q] = v[q];
+  }
+  const int rows = (int)((job.m - r0) < ROWS ? (job.m - r0) : ROWS);
+  for (int e = tid; e < ROWS * l; e += kSolveThreads) {
+    const int rr = e % ROWS, j = e / ROWS;
     double v = 0.0;
     if (rr < rows) {
       const int64_t idx = r0 + rr + job.m * j;
@@ -663,27 +985,66 @@ __global__ void __launch_bounds__(256) cqr_solve_kernel(const CqrBatch jobs, int
     X[rr][j] = v;
   }
   __syncthreads();
-  for (int j = threadIdx.x; j < l; j += blockDim.x) invd[j] = 1.0 / R[j][j];
+  for (int j = tid; j < l; j += kSolveThreads) invd[j] = 1.0 / Rs[j + l * j];
   __syncthreads();
   const unsigned long long refill = *job.defmask;
-  const int row = threadIdx.x >> 4, sub = threadIdx.x & 15;
+  const int row = tid / TPR, sub = tid % TPR;
+  double* x = X[row];
   for (int j = 0; j < l; ++j) {
-    double acc = 0.0;
-    for (int k = sub; k < j; k += 16) acc = fma(X[row][k], R[k][j], acc);
-    acc += __shfl_xor_sync(0xffffffffu, acc, 1);
-    acc += __shfl_xor_sync(0xffffffffu, acc, 2);
-    acc += __shfl_xor_sync(0xffffffffu, acc, 4);
-    acc += __shfl_xor_sync(0xffffffffu, acc, 8);
+    const double* rc = Rs + (size_t)l * j;
+    double a0 = 0.0, a1 = 0.0;
+    int k = sub;
+    for (; k + TPR < j; k += 2 * TPR) {
+      a0 = fma(x[k], rc[k], a0);
+      a1 = fma(x[k + TPR], rc[k + TPR], a1);
+    }
+    if (k < j) a0 = fma(x[k], rc[k], a0);
+    double acc = a0 + a1;
+#pragma unroll
+    for (int o = 1; o < TPR; o <<= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
     if (sub == 0)
-      X[row][j] = ((refill >> j) & 1ull) ? refill_value(r0 + row, j) : (X[row][j] - acc) * invd[j];
+      x[j] = ((refill >> j) & 1ull) ? refill_value(r0 + row, j) : (x[j] - acc) * invd[j];
     __syncwarp();
   }
   __syncthreads();
   double* out = TO_Q ? job.Q : job.W;
-  for (int e = threadIdx.x; e < kSolveRows * l; e += blockDim.x) {
-    const int rr = e % kSolveRows, j = e / kSolveRows;
+  for (int e = tid; e < ROWS * l; e += kSolveThreads) {
+    const int rr = e % ROWS, j = e / ROWS;
     if (rr < rows) out[r0 + rr + job.m * j] = X[rr][j];
   }
+}
+
+// Lanes per row: as many as keep the warps within one per sub-partition.
+int solve_tpr(int64_t total_rows) {
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+    sms = 1;
+  const int64_t parts = 4 * (int64_t)std::max(1, sms);
+  return (total_rows * 8 / 32 <= parts) ? 8 : 4;
+}
+
+template <int TPR>
+void cqr_solve_launch(const CqrBatch& batch, int nq, int64_t maxm, int pass, cudaStream_t st) {
+  const dim3 gs((unsigned)((maxm + solve_rows<TPR>() - 1) / solve_rows<TPR>()), (unsigned)nq);
+  const size_t sm = solve_smem<TPR>();
+  auto run = [&](auto kern) {
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    kern<<<gs, kSolveThreads, sm, st>>>(batch, pass);
+  };
+  if (pass == 0)
+    run(cqr_solve_kernel<true, false, TPR>);
+  else if (pass == 1)
+    run(cqr_solve_kernel<false, false, TPR>);
+  else
+    run(cqr_solve_kernel<false, true, TPR>);
+}
+void cqr_solve_any(const CqrBatch& batch, int nq, int64_t maxm, int64_t total_rows, int pass,
+                   cudaStream_t st) {
+  if (solve_tpr(total_rows) == 8)
+    cqr_solve_launch<8>(batch, nq, maxm, pass, st);
+  else
+    cqr_solve_launch<4>(batch, nq, maxm, pass, st);
 }
 
 int grid_for(int64_t n, int threads, int cap = 8192) {
@@ -715,7 +1076,6 @@ cudaError_t cholqr3_single_on_stream(const float* Y, int64_t m, int l, double* Q
   q.defmask = reinterpret_cast<unsigned long long*>(q.Rk + (size_t)3 * l * l);
   int* status = reinterpret_cast<int*>(q.Rk + (size_t)3 * l * l + 1);
   const dim3 g((unsigned)((m + kCqrRows - 1) / kCqrRows), 1u);
-  const dim3 gs((unsigned)((m + kSolveRows - 1) / kSolveRows), 1u);
   for (int pass = 0; pass < 3; ++pass) {
     cudaError_t e = cudaMemsetAsync(q.G, 0, sizeof(double) * l * l, st);
     if (e != cudaSuccess) return e;
@@ -723,13 +1083,8 @@ cudaError_t cholqr3_single_on_stream(const float* Y, int64_t m, int l, double* Q
       cqr_gram_kernel<true><<<g, 256, 0, st>>>(batch, status);
     else
       cqr_gram_kernel<false><<<g, 256, 0, st>>>(batch, status);
-    cqr_chol_kernel<<<1, 256, 0, st>>>(batch, pass);
-    if (pass == 0)
-      cqr_solve_kernel<true, false><<<gs, 256, 0, st>>>(batch, pass);
-    else if (pass == 1)
-      cqr_solve_kernel<false, false><<<gs, 256, 0, st>>>(batch, pass);
-    else
-      cqr_solve_kernel<false, true><<<gs, 256, 0, st>>>(batch, pass);
+    cqr_chol_kernel<<<1, kCholThreads, 0, st>>>(batch, pass);
+    cqr_solve_any(batch, 1, m, m, pass, st);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }
@@ -791,7 +1146,8 @@ void qr_householder_f64(const QrJob* jobs, int count, int* status) {
 
 void cholqr3_launch(const CqrBatch& batch, int nq, int64_t maxm, int* status) {
   const dim3 g((unsigned)((maxm + kCqrRows - 1) / kCqrRows), (unsigned)nq);
-  const dim3 gs((unsigned)((maxm + kSolveRows - 1) / kSolveRows), (unsigned)nq);
+  int64_t total_rows = 0;
+  for (int q = 0; q < nq; ++q) total_rows += batch.job[q].m;
   for (int pass = 0; pass < 3; ++pass) {
     for (int q = 0; q < nq; ++q)
       KRP_CUDA_CHECK(cudaMemsetAsync(batch.job[q].G, 0, sizeof(double) * batch.job[q].l * batch.job[q].l,
@@ -801,14 +1157,9 @@ void cholqr3_launch(const CqrBatch& batch, int nq, int64_t maxm, int* status) {
     else
       cqr_gram_kernel<false><<<g, 256, 0, stream()>>>(batch, status);
     check_launch("cholqr_gram_f64");
-    cqr_chol_kernel<<<nq, 256, 0, stream()>>>(batch, pass);
+    cqr_chol_kernel<<<nq, kCholThreads, 0, stream()>>>(batch, pass);
     check_launch("cholqr_chol_f64");
-    if (pass == 0)
-      cqr_solve_kernel<true, false><<<gs, 256, 0, stream()>>>(batch, pass);
-    else if (pass == 1)
-      cqr_solve_kernel<false, false><<<gs, 256, 0, stream()>>>(batch, pass);
-    else
-      cqr_solve_kernel<false, true><<<gs, 256, 0, stream()>>>(batch, pass);
+    cqr_solve_any(batch, nq, maxm, total_rows, pass, stream());
     check_launch("cholqr_solve_f64");
   }
 }
@@ -827,6 +1178,20 @@ void gram_mode_f64(const double* G, int D, const int64_t* dims, int mode, double
   const int blocks = (int)((ncols + per - 1) / per);
   gram_kernel<<<blocks, threads, sizeof(double) * 32 * l, stream()>>>(G, P, l, ncols, per, S);
   check_launch("gram_f64");
+}
+
+template <int ML>
+void eig_split_launch_t(const EigJob* d_jobs, int count, double* scratch, int* status) {
+  const size_t js = 3 * sizeof(float) * ML * (ML + 1);
+  KRP_CUDA_CHECK(cudaFuncSetAttribute(eig_jacobi_kernel<ML>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)js));
+  eig_jacobi_kernel<ML><<<count, kEigThreads, js, stream()>>>(d_jobs, scratch, status);
+  check_launch("jacobi32_eig");
+  const size_t rs = 3 * sizeof(double) * ML * (ML + 1);
+  KRP_CUDA_CHECK(cudaFuncSetAttribute(eig_refine_kernel<ML>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)rs));
+  eig_refine_kernel<ML><<<dim3(kEigCluster, count), kEigThreads, rs, stream()>>>(d_jobs, scratch, status);
+  check_launch("eig_refine_f64");
 }
 
 void eig_launch(const EigJob* d_jobs, int count, int maxl, int* status) {
@@ -864,7 +1229,22 @@ void sym_eig_top_f64(const double* const* S, const int* l, const int* r, double*
   EigJob* d_jobs = current()->ws.take<EigJob>(count);
   KRP_CUDA_CHECK(cudaMemcpyAsync(d_jobs, jobs.data(), sizeof(EigJob) * count,
                                  cudaMemcpyHostToDevice, stream()));
-  eig_launch(d_jobs, count, kEigMaxL, status);
+  int maxl = 1;
+  for (int b = 0; b < count; ++b) maxl = std::max(maxl, l[b]);
+  // a few problems: Jacobi per CTA, refinement spread over a cluster each
+  if ((int64_t)count * kEigCluster <= current()->num_sms && maxl > 16) {
+    double* scratch = current()->ws.take<double>((size_t)count * kEigScratch);
+    if (maxl <= 32)
+      eig_split_launch_t<32>(d_jobs, count, scratch, status);
+    else
+      eig_split_launch_t<kEigMaxL>(d_jobs, count, scratch, status);
+    return;
+  }
+  eig_launch(d_jobs, count, maxl, status);
+}
+
+size_t sym_eig_workspace_bytes(int count) {
+  return ws_bytes((size_t)count, sizeof(EigJob)) + ws_bytes((size_t)count * kEigScratch, 8);
 }
 
 void ttm_small_f64(const double* G, int D, const int64_t* dims, int mode, const double* U, int r,

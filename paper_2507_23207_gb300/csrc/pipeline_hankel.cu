@@ -135,6 +135,7 @@ void hankel_pipeline(const void* blocks, krp_dtype bt, int m, int n, int s, int 
   need += 3 * ws_bytes((size_t)ms * ell_r, 8) + 4 * ws_bytes((size_t)ell_l * ell_r, 8);
   need += ws_bytes((size_t)ell_r * ns, 8) + 4 * ws_bytes((size_t)ell_r * ell_r, 8);
   need += ws_bytes((size_t)ms * r, 8) + ws_bytes((size_t)ns * r, 8) + ws_bytes(r, 8);
+  need += sym_eig_workspace_bytes(1);
   need += 1 << 20;
   ensure_workspace(c, need);
   Workspace& ws = c->ws;

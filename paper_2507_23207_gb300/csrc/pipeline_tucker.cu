@@ -376,6 +376,7 @@ void tucker_pipeline(bool sequential, const void* X, krp_dtype xt, int d, const 
     core_l *= ell[i];
   }
   need += 4 * ws_bytes((size_t)core_l, 8) + 2 * ws_bytes((size_t)core_l, 4);
+  need += sym_eig_workspace_bytes(d);
   if (bf16_family(xt)) need += tc_workspace_bytes(dims[0], N / dims[0], 2 * ellmax);
   if (bf16_family(xt) && resid) need += tc_residual_workspace_bytes(dims[0], N / dims[0]);
   need += 4 << 20;

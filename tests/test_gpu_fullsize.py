@@ -211,8 +211,8 @@ def test_c2_sketch_sampled_rows(ctx, c2_inputs, form, tol):
 
 def test_c2_pipeline_properties(ctx, c2_inputs):
     """Full RHOSVD-KRP-MEMO step of the bench (FP32 and BF16): orthonormal
-    factors (FP64, 1e-10), rank-l error <= rank-r error (truncation removes
-    directions), and for FP32 the rank-32 error between the noise level (the
+    factors (FP64, 1e-10), rank-l error <= rank-r error to 1e-5 relative
+    (truncation removes directions), and for FP32 the rank-32 error between the noise level (the
     input carries relative noise 1e-4, which no rank-32 approximation removes)
     and 5x it."""
     import torch
@@ -234,7 +234,12 @@ def test_c2_pipeline_properties(ctx, c2_inputs):
                 q = f.cpu().numpy().reshape(o, n).T
                 assert np.linalg.norm(q.T @ q - np.eye(o)) <= 1e-10
             errs.append(res["rel_residual"])
-        assert errs[0] <= errs[1]
+        # Exactly, the rank-l error is at most the rank-r error (here by only
+        # ~1e-9 absolute: the extra directions hold noise).  The FP32 core's
+        # rounding dG lies inside the factor span and adds ||dG||^2 to each
+        # squared residual, more for the larger core, so the ordering is
+        # checked to the FP32 parity bar.
+        assert errs[0] <= errs[1] * (1 + 1e-5), errs
         if form == "f32":
             # noise of relative size 1e-4 bounds any rank-32 error from below
             assert 0.9e-4 <= errs[1] <= 5e-4, errs

@@ -61,6 +61,9 @@ SPECS = [
     TuckerSpec("ragged", (37, 29, 23), (3, 4, 5), 1e-3, None, 17, (3, 4, 5), (6, 7, 8)),
     TuckerSpec("d4", (12, 10, 9, 8), (3, 3, 2, 3), 1e-2, None, 23, (3, 3, 2, 3), (5, 5, 4, 5)),
     TuckerSpec("tall", (300, 20, 10), (6, 5, 4), 1e-4, None, 29, (6, 5, 4), (10, 9, 8)),
+    # n_1 % 4 == 0 with a 4-row ragged 128-row block, c % 4 == 0 and
+    # S = 21 * 13 not a multiple of 64: the persistent tiled residual path
+    TuckerSpec("tiled", (132, 21, 13), (4, 3, 3), 1e-3, None, 31, (4, 3, 3), (8, 7, 7)),
 ]
 
 

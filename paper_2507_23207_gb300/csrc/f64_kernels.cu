@@ -209,13 +209,17 @@ __device__ double block_sum(double v, double* red) {
   return s;
 }
 
-// Per-thread work bounds of a Jacobi round (kEigThreads threads, n <= 64 so
-// P <= 32 pairs and jstep = threads / P >= 8): blocks per thread and V rows.
-constexpr int kJm = (32 + kEigThreads / 32 - 1) / (kEigThreads / 32);
-constexpr int kJv = (64 + kEigThreads / 32 - 1) / (kEigThreads / 32);
+// The Jacobi stage of the split eigensolver runs 16 warps: its rounds are
+// latency-bound, and more warps shorten each thread's share of a round.
+constexpr int kJacobiThreads = 512;
 
-template <int EP>  // row pitch of the padded matrices
+// NT threads, n <= 64 so P <= 32 pairs and jstep = NT / P >= NT / 32; red
+// holds 2 * NT / 32 doubles.
+template <int EP, int NT>  // row pitch of the padded matrices, threads
 __device__ void jacobi32(float (*Sa)[EP], float (*Sb)[EP], float (*V)[EP], int n, double* red) {
+  // per-thread work bounds of a round: blocks per thread and V rows
+  constexpr int kJm = (32 + NT / 32 - 1) / (NT / 32);
+  constexpr int kJv = (64 + NT / 32 - 1) / (NT / 32);
   const int tid = threadIdx.x, lane = tid & 31, P = n / 2;
   // fixed work split of the round updates (no per-item integer division):
   // threads t < jstep * P own pair ib0 = t % P and rows/blocks jb0 + m jstep
@@ -235,11 +239,16 @@ __device__ void jacobi32(float (*Sa)[EP], float (*Sb)[EP], float (*V)[EP], int n
         o += v;
     }
     const double off = block_sum(o, red);
-    const double dia = block_sum(dg, red + 8);
+    const double dia = block_sum(dg, red + NT / 32);
     // off-diagonal norm at 1e-6 of the diagonal's: the FP64 stage does the
     // rest (stopping at 1e-4 left the refined vectors of graded spectra, such
     // as a block Hankel's, orthonormal only to ~1e-5)
     if (!(off > 1e-12 * dia) || off == 0.0) break;
+    // round-robin tournament: position 0 holds player 0, position k >= 1
+    // holds player ((k - 1 + round) mod (n - 1)) + 1; pairs (k, n-1-k).  Lane
+    // k < P keeps (k - 1 + round) and (n - 2 - k + round) mod (n - 1) as
+    // counters advanced once per round.
+    int pos_p = (lane >= 1) ? lane - 1 : 0, pos_q = n - 2 - lane;
     for (int round = 0; round < n - 1; ++round) {
       // every warp forms all P rotations of the round, lane k the k-th, from
       // the matrix of the previous round (read-only during this round), and
@@ -247,11 +256,10 @@ __device__ void jacobi32(float (*Sa)[EP], float (*Sb)[EP], float (*V)[EP], int n
       int p = 0, q = 0;
       float c = 1.f, s = 0.f;
       if (lane < P) {
-        // round-robin tournament: position 0 holds player 0, position k >= 1
-        // holds player ((k - 1 + round) mod (n - 1)) + 1; pairs (k, n-1-k)
-        const int k2 = n - 1 - lane;
-        p = (lane == 0) ? 0 : ((lane - 1 + round) % (n - 1)) + 1;
-        q = ((k2 - 1 + round) % (n - 1)) + 1;
+        p = (lane == 0) ? 0 : pos_p + 1;
+        q = pos_q + 1;
+        pos_p = (pos_p + 1 == n - 1) ? 0 : pos_p + 1;
+        pos_q = (pos_q + 1 == n - 1) ? 0 : pos_q + 1;
         if (p > q) {
           const int t = p;
           p = q;
@@ -426,7 +434,7 @@ __global__ void __launch_bounds__(kEigThreads) eig_kernel(const EigJob* __restri
     if (tid == 0) atomicExch(status, (int)KRP_ENUMERIC);
     return;
   }
-  jacobi32<kEP>(S32, S32b, V32, n, red);
+  jacobi32<kEP, kEigThreads>(S32, S32b, V32, n, red);
   for (int e = tid; e < l * l; e += blockDim.x) {
     const int r = e % l, c = e / l;
     X[r][c] = (double)V32[r][c];
@@ -502,7 +510,7 @@ constexpr int kEigCluster = 8;
 constexpr int kEigScratch = kEigMaxL * kEigMaxL + 8;  // doubles per problem
 
 template <int ML>
-__global__ void __launch_bounds__(kEigThreads)
+__global__ void __launch_bounds__(kJacobiThreads)
     eig_jacobi_kernel(const EigJob* __restrict__ jobs, double* __restrict__ scratch, int* status) {
   constexpr int kEP = ML + 1;
   const EigJob job = jobs[blockIdx.x];
@@ -512,8 +520,8 @@ __global__ void __launch_bounds__(kEigThreads)
   float(*S32)[kEP] = reinterpret_cast<float(*)[kEP]>(ej_smem);
   float(*S32b)[kEP] = reinterpret_cast<float(*)[kEP]>(ej_smem + ML * kEP);
   float(*V32)[kEP] = reinterpret_cast<float(*)[kEP]>(ej_smem + 2 * ML * kEP);
-  __shared__ double red[16];
-  __shared__ float redf[8];
+  __shared__ double red[2 * kJacobiThreads / 32];
+  __shared__ float redf[kJacobiThreads / 32];
   const int tid = threadIdx.x;
   // scale by a power of two (exact) so that max |a_ij| is in [0.5, 1)
   float amax = 0.f;
@@ -542,7 +550,7 @@ __global__ void __launch_bounds__(kEigThreads)
     }
     return;
   }
-  jacobi32<kEP>(S32, S32b, V32, n, red);
+  jacobi32<kEP, kJacobiThreads>(S32, S32b, V32, n, red);
   for (int e = tid; e < l * l; e += blockDim.x) out[e] = (double)V32[e % l][e / l];
   if (tid == 0) out[kEigMaxL * kEigMaxL] = scale;
 }
@@ -1185,7 +1193,7 @@ void eig_split_launch_t(const EigJob* d_jobs, int count, double* scratch, int* s
   const size_t js = 3 * sizeof(float) * ML * (ML + 1);
   KRP_CUDA_CHECK(cudaFuncSetAttribute(eig_jacobi_kernel<ML>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       (int)js));
-  eig_jacobi_kernel<ML><<<count, kEigThreads, js, stream()>>>(d_jobs, scratch, status);
+  eig_jacobi_kernel<ML><<<count, kJacobiThreads, js, stream()>>>(d_jobs, scratch, status);
   check_launch("jacobi32_eig");
   const size_t rs = 3 * sizeof(double) * ML * (ML + 1);
   KRP_CUDA_CHECK(cudaFuncSetAttribute(eig_refine_kernel<ML>, cudaFuncAttributeMaxDynamicSharedMemorySize,

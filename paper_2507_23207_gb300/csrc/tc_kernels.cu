@@ -542,6 +542,7 @@ __global__ void __launch_bounds__(320, 1)
   uint8_t* b2 = smem + NS * kStage;
   Bars* bars = reinterpret_cast<Bars*>(b2 + 2 * kB2Buf);
   __shared__ uint64_t b2full[2], b2empty[2];
+  __shared__ float wsm[2][N];  // w[t, :] beside B2_t, same double buffering
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int b = blockIdx.x % P.nb;
   const int64_t t0 = static_cast<int64_t>(blockIdx.x / P.nb) * P.t_per_cta;
@@ -558,7 +559,7 @@ __global__ void __launch_bounds__(320, 1)
       mbar_init(smem_u32(&bars->tfull[a]), 1);
       mbar_init(smem_u32(&bars->tempty[a]), 4);
       mbar_init(smem_u32(&b2full[a]), 4);
-      mbar_init(smem_u32(&b2empty[a]), 1);
+      mbar_init(smem_u32(&b2empty[a]), 1 + 4);  // MMA commit + four epilogue warps (wsm)
     }
     mbar_init(smem_u32(&bars->drain), 1);
     bars->abort_flag = 0;
@@ -671,9 +672,18 @@ __global__ void __launch_bounds__(320, 1)
       }
       uint8_t* base = b2 + buf * kB2Buf + (tid >> 6) * kB2Atom;
       const int col = tid & 63;
+      // w[t, :]: two loads per lane, shared within the warp by shuffles (no
+      // barrier across the producer warps); the first warp also stages it
+      // in shared memory for the epilogue (published by the b2full arrival)
+      const float wl0 = (lane < P.L) ? __ldg(P.w + t + P.T * lane) : 0.f;
+      const float wl1 = (lane + 32 < P.L) ? __ldg(P.w + t + P.T * (lane + 32)) : 0.f;
+      if (tid < 32) {
+        if (lane < N) wsm[buf][lane] = wl0;
+        if (lane + 32 < N) wsm[buf][lane + 32] = wl1;
+      }
 #pragma unroll
       for (int k = 0; k < N; ++k) {
-        const float v = (k < P.L) ? om[k] * __ldg(P.w + t + P.T * k) : 0.f;
+        const float v = om[k] * __shfl_sync(0xffffffffu, k < 32 ? wl0 : wl1, k & 31);
         const __nv_bfloat16 hi = __float2bfloat16_rn(v);
         const __nv_bfloat16 lo = __float2bfloat16_rn(v - __bfloat162float(hi));
         const uint32_t off = k * 128 + ((((col >> 3) ^ (k & 7)) << 4)) + (col & 7) * 2;
@@ -704,6 +714,11 @@ __global__ void __launch_bounds__(320, 1)
         if (lane == 0) raise_timeout(bars, status);
         break;
       }
+      // w[t, :] was staged with B2_t (that phase is complete once tfull is)
+      if (!mbar_wait(smem_u32(&b2full[acc]), ph, abort_flag)) {
+        if (lane == 0) raise_timeout(bars, status);
+        break;
+      }
       tc_fence_after();
       const uint32_t base = tmem + (static_cast<uint32_t>(q * 32) << 16) + acc * N;
 #pragma unroll
@@ -713,7 +728,7 @@ __global__ void __launch_bounds__(320, 1)
 #pragma unroll
         for (int j = 0; j < 16; ++j) {
           const int k = c0 + j;
-          const float wk = (k < P.L) ? __ldg(P.w + t + P.T * k) : 0.f;
+          const float wk = wsm[acc][k];
           y2[k] = fmaf(v[j], wk, y2[k]);
           float cp = v[j] * o2[k];
 #pragma unroll
@@ -724,7 +739,10 @@ __global__ void __launch_bounds__(320, 1)
       }
       tc_fence_before();
       __syncwarp();
-      if (lane == 0) mbar_arrive(smem_u32(&bars->tempty[acc]));
+      if (lane == 0) {
+        mbar_arrive(smem_u32(&bars->tempty[acc]));
+        mbar_arrive(smem_u32(&b2empty[acc]));
+      }
     }
     if (valid) {
 #pragma unroll
@@ -761,36 +779,42 @@ __global__ void __launch_bounds__(320, 1)
 // ----------------------------------------------------------------------------
 // Residual of the BF16 form: acc[0] += ||X - Q1 H||_F^2, acc[1] += ||X||_F^2,
 // X n1 x S (BF16), Q1 n1 x c (K-major rows, BF16 hi/lo), H c x S (K-major rows
-// per s, BF16 hi/lo), c <= 64 padded to 64.  Tile = 128 rows i x 128 columns
-// s; X_hat = Qh Hh + Qh Hl + Ql Hh accumulates in TMEM (the dropped Ql Hl term
-// is below 2^-16 relative), and the epilogue compares it with the X tile that
-// TMA placed in the same pipeline stage.  A stage is released when both the
-// MMAs (tcgen05.commit) and the four epilogue warps are done with it.
-// RN: columns s per tile (128; 64 when X is a hi/lo pair, XLO, whose two
-// extra X boxes per stage would not fit twice otherwise).  With XLO the X
-// value in the epilogue is hi + lo.
-template <int RN, bool XLO>
+// per s, BF16 hi/lo), c <= 64 padded to 64.  The tile is the transpose,
+// X_hat^T[s, i] for 128 columns s (TMEM lanes) x 128 rows i (TMEM columns):
+// A = H (M = s), B = Q1 (N = i), X_hat^T = Hh Qh^T + Hl Qh^T + Hh Ql^T (the
+// dropped Hl Ql^T term is below 2^-16 relative).  In that orientation an
+// epilogue thread owns one s and 16 consecutive i per TMEM load, which are
+// two 16-byte chunks of the X tile as TMA placed it ([s][64 i] rows of 128 B,
+// chunks swizzled by s mod 8), so X is read with 16-byte shared loads.
+// A CTA keeps one 128-row block of Q1 (hi and lo, 32 KB) resident and walks
+// the column tiles of that block; the CTAs of one column tile run together,
+// so each H tile comes from HBM once and from L2 for the other blocks.  A
+// stage (H hi/lo + X boxes) is released when both the MMAs (tcgen05.commit)
+// and the four epilogue warps are done with it.  XLO: X is a BF16 hi/lo pair
+// (two more boxes per stage); the epilogue compares with hi + lo.
+template <bool XLO>
 __global__ void __launch_bounds__(kThreads, 1)
     tc_residual_kernel(const __grid_constant__ CUtensorMap mapX,
                        const __grid_constant__ CUtensorMap mapXlo,
                        const __grid_constant__ CUtensorMap mapQ,
                        const __grid_constant__ CUtensorMap mapH, int64_t n1, int64_t S,
-                       int mblocks, double* __restrict__ acc, int* status) {
-  constexpr int kResN = RN;
-  constexpr int NS = 2;
-  constexpr uint32_t kOp = 128 * 128;       // one 128-row x 64-element BF16 operand tile (Q)
-  constexpr uint32_t kOpH = RN * 128;       // one RN-row x 64-element BF16 operand tile (H)
-  constexpr uint32_t kXBox = 64 * kResN * 2;  // 64 (i) x RN (s) BF16
+                       int mblocks, int cpm, double* __restrict__ acc, int* status) {
+  constexpr int NS = XLO ? 2 : 3;
+  constexpr uint32_t kOp = 128 * 128;            // one 128-row x 64-element BF16 operand tile
+  constexpr uint32_t kXBox = 64 * 128 * 2;       // 64 (i) x 128 (s) BF16
   constexpr uint32_t kXNum = XLO ? 4 : 2;
-  constexpr uint32_t kStage = 2 * kOp + 2 * kOpH + kXNum * kXBox;  // Qh Ql Hh Hl + X boxes
-  constexpr uint32_t kTmemCols = 2 * RN;
-  constexpr uint32_t kIdesc = idesc_bf16(kBM, kResN, false, false);
+  constexpr uint32_t kStage = 2 * kOp + kXNum * kXBox;  // Hh Hl + X boxes
+  constexpr uint32_t kTmemCols = 256;
+  constexpr uint32_t kIdesc = idesc_bf16(kBM, 128, false, false);
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-  Bars* bars = reinterpret_cast<Bars*>(smem + NS * kStage);
+  uint8_t* qres = smem + NS * kStage;  // Qh, Ql of this CTA's row block
+  Bars* bars = reinterpret_cast<Bars*>(qres + 2 * kOp);
+  __shared__ uint64_t qbar;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int64_t sblocks = (S + kResN - 1) / kResN;
-  const int64_t tiles = sblocks * mblocks;  // tile = (sb, mb), mb fastest
+  const int64_t sblocks = (S + 127) / 128;
+  const int mb = static_cast<int>(blockIdx.x % mblocks);
+  const int64_t sb0 = blockIdx.x / mblocks;  // this CTA's tiles: sb0, sb0 + cpm, ...
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < NS; ++s) {
@@ -802,6 +826,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       mbar_init(smem_u32(&bars->tempty[a]), 4);
     }
     mbar_init(smem_u32(&bars->drain), 1);
+    mbar_init(smem_u32(&qbar), 1);
     bars->abort_flag = 0;
     bars->issued = 0;
     bars->consumed = 0;
@@ -817,37 +842,42 @@ __global__ void __launch_bounds__(kThreads, 1)
 
   if (warp == 0) {
     if (lane == 0) {
+      const uint32_t qb = smem_u32(&qbar);
+      mbar_expect_tx(qb, 2 * kOp);
+      tma_load_2d(smem_u32(qres), &mapQ, qb, 0, mb * kBM);          // Qh
+      tma_load_2d(smem_u32(qres + kOp), &mapQ, qb, 64, mb * kBM);   // Ql
       int it = 0;
-      for (int64_t tile = blockIdx.x; tile < tiles && !*abort_flag; tile += gridDim.x, ++it) {
+      for (int64_t sb = sb0; sb < sblocks && !*abort_flag; sb += cpm, ++it) {
         const int st = it % NS;
         const uint32_t ph = (it / NS) & 1;
         if (!mbar_wait(smem_u32(&bars->empty[st]), ph ^ 1, abort_flag)) {
           raise_timeout(bars, status);
           break;
         }
-        const int mb = static_cast<int>(tile % mblocks);
-        const int sb = static_cast<int>(tile / mblocks);
         const uint32_t a = smem_u32(smem + st * kStage);
         const uint32_t fb = smem_u32(&bars->full[st]);
         mbar_expect_tx(fb, kStage);
-        const uint32_t xo = 2 * kOp + 2 * kOpH;
-        tma_load_2d(a + 0 * kOp, &mapQ, fb, 0, mb * kBM);              // Qh
-        tma_load_2d(a + 1 * kOp, &mapQ, fb, 64, mb * kBM);             // Ql
-        tma_load_2d(a + 2 * kOp, &mapH, fb, 0, sb * kResN);            // Hh
-        tma_load_2d(a + 2 * kOp + kOpH, &mapH, fb, 64, sb * kResN);    // Hl
-        tma_load_2d(a + xo, &mapX, fb, mb * kBM, sb * kResN);          // X, i 0..63
-        tma_load_2d(a + xo + kXBox, &mapX, fb, mb * kBM + 64, sb * kResN);  // i 64..127
+        const int s0 = static_cast<int>(sb * 128);
+        tma_load_2d(a, &mapH, fb, 0, s0);                             // Hh
+        tma_load_2d(a + kOp, &mapH, fb, 64, s0);                      // Hl
+        tma_load_2d(a + 2 * kOp, &mapX, fb, mb * kBM, s0);            // X, i 0..63
+        tma_load_2d(a + 2 * kOp + kXBox, &mapX, fb, mb * kBM + 64, s0);  // i 64..127
         if (XLO) {
-          tma_load_2d(a + xo + 2 * kXBox, &mapXlo, fb, mb * kBM, sb * kResN);
-          tma_load_2d(a + xo + 3 * kXBox, &mapXlo, fb, mb * kBM + 64, sb * kResN);
+          tma_load_2d(a + 2 * kOp + 2 * kXBox, &mapXlo, fb, mb * kBM, s0);
+          tma_load_2d(a + 2 * kOp + 3 * kXBox, &mapXlo, fb, mb * kBM + 64, s0);
         }
         bars->issued = it + 1;
       }
+      // the resident Q load must land before the CTA can exit
+      int dummy = 0;
+      mbar_wait(qb, 0, reinterpret_cast<volatile int*>(&dummy));
     }
   } else if (warp == 1) {
     if (lane == 0) {
+      bool ok = mbar_wait(smem_u32(&qbar), 0, abort_flag);
+      if (!ok) raise_timeout(bars, status);
       int it = 0;
-      for (int64_t tile = blockIdx.x; tile < tiles && !*abort_flag; tile += gridDim.x, ++it) {
+      for (int64_t sb = sb0; ok && sb < sblocks && !*abort_flag; sb += cpm, ++it) {
         const int st = it % NS;
         const uint32_t ph = (it / NS) & 1;
         const int accb = it & 1;
@@ -859,13 +889,13 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
         tc_fence_after();
         const uint32_t a = smem_u32(smem + st * kStage);
-        const uint32_t dt = tmem + accb * kResN;
-        const uint32_t qh = a, ql = a + kOp, hh = a + 2 * kOp, hl = a + 2 * kOp + kOpH;
+        const uint32_t dt = tmem + accb * 128;
+        const uint32_t hh = a, hl = a + kOp, qh = smem_u32(qres), ql = qh + kOp;
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
-          mma_bf16(dt, sdesc(qh + 32 * k, 16, 1024), sdesc(hh + 32 * k, 16, 1024), kIdesc, k != 0);
-          mma_bf16(dt, sdesc(qh + 32 * k, 16, 1024), sdesc(hl + 32 * k, 16, 1024), kIdesc, 1);
-          mma_bf16(dt, sdesc(ql + 32 * k, 16, 1024), sdesc(hh + 32 * k, 16, 1024), kIdesc, 1);
+          mma_bf16(dt, sdesc(hh + 32 * k, 16, 1024), sdesc(qh + 32 * k, 16, 1024), kIdesc, k != 0);
+          mma_bf16(dt, sdesc(hl + 32 * k, 16, 1024), sdesc(qh + 32 * k, 16, 1024), kIdesc, 1);
+          mma_bf16(dt, sdesc(hh + 32 * k, 16, 1024), sdesc(ql + 32 * k, 16, 1024), kIdesc, 1);
         }
         mma_commit(smem_u32(&bars->empty[st]));
         mma_commit(smem_u32(&bars->tfull[accb]));
@@ -877,40 +907,60 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
   } else {
     const int q = warp & 3;
-    const int row = q * 32 + lane;  // i within the tile
+    const int srow = q * 32 + lane;  // s within the tile (TMEM lane)
+    const uint32_t sw = static_cast<uint32_t>(srow & 7);
     double dsum = 0.0, xsum = 0.0;
     int it = 0;
-    for (int64_t tile = blockIdx.x; tile < tiles; tile += gridDim.x, ++it) {
+    for (int64_t sb = sb0; sb < sblocks; sb += cpm, ++it) {
       const int st = it % NS;
-      const uint32_t ph = (it / NS) & 1;
       const int accb = it & 1;
       const uint32_t aph = (it >> 1) & 1;
       if (!mbar_wait(smem_u32(&bars->tfull[accb]), aph, abort_flag)) {
         if (lane == 0) raise_timeout(bars, status);
         break;
       }
-      (void)ph;
       tc_fence_after();
-      // X tile: box (row / 64), smem row s holds 64 i values (128 B), 16-byte
-      // chunks swizzled by (s mod 8)
-      const uint8_t* xb = smem + st * kStage + 2 * kOp + 2 * kOpH + (row >> 6) * kXBox;
-      const int ii = row & 63;
-      const uint32_t base = tmem + (static_cast<uint32_t>(q * 32) << 16) + accb * kResN;
+      const uint8_t* xrow = smem + st * kStage + 2 * kOp + srow * 128;
+      const uint32_t base = tmem + (static_cast<uint32_t>(q * 32) << 16) + accb * 128;
       float d2 = 0.f, x2 = 0.f;
 #pragma unroll 1
-      for (int c0 = 0; c0 < kResN; c0 += 16) {
+      for (int c0 = 0; c0 < 128; c0 += 16) {
         float v[16];
         tmem_ld16(base + c0, v);
+        const uint8_t* bx = xrow + (c0 >> 6) * kXBox;
+        const uint32_t j0 = static_cast<uint32_t>((c0 & 63) >> 3);
+        uint4 w[2];
+        w[0] = *reinterpret_cast<const uint4*>(bx + (((j0) ^ sw) << 4));
+        w[1] = *reinterpret_cast<const uint4*>(bx + (((j0 + 1) ^ sw) << 4));
+        uint4 wl[2];
+        if (XLO) {
+          wl[0] = *reinterpret_cast<const uint4*>(bx + 2 * kXBox + (((j0) ^ sw) << 4));
+          wl[1] = *reinterpret_cast<const uint4*>(bx + 2 * kXBox + (((j0 + 1) ^ sw) << 4));
+        }
 #pragma unroll
-        for (int j = 0; j < 16; ++j) {
-          const int s = c0 + j;
-          const int chunk = (ii >> 3) ^ (s & 7);
-          const int off = s * 128 + chunk * 16 + (ii & 7) * 2;
-          float x = __bfloat162float(*reinterpret_cast<const __nv_bfloat16*>(xb + off));
-          if (XLO) x += __bfloat162float(*reinterpret_cast<const __nv_bfloat16*>(xb + 2 * kXBox + off));
-          const float df = x - v[j];
-          d2 = fmaf(df, df, d2);
-          x2 = fmaf(x, x, x2);
+        for (int h = 0; h < 2; ++h) {
+          const uint32_t u[4] = {w[h].x, w[h].y, w[h].z, w[h].w};
+          uint32_t ul[4] = {0u, 0u, 0u, 0u};
+          if (XLO) {
+            ul[0] = wl[h].x;
+            ul[1] = wl[h].y;
+            ul[2] = wl[h].z;
+            ul[3] = wl[h].w;
+          }
+#pragma unroll
+          for (int e = 0; e < 4; ++e) {
+            float xa = __uint_as_float(u[e] << 16);          // element 2e (low half)
+            float xb = __uint_as_float(u[e] & 0xFFFF0000u);  // element 2e + 1
+            if (XLO) {
+              xa += __uint_as_float(ul[e] << 16);
+              xb += __uint_as_float(ul[e] & 0xFFFF0000u);
+            }
+            const float da = xa - v[h * 8 + 2 * e], db = xb - v[h * 8 + 2 * e + 1];
+            d2 = fmaf(da, da, d2);
+            d2 = fmaf(db, db, d2);
+            x2 = fmaf(xa, xa, x2);
+            x2 = fmaf(xb, xb, x2);
+          }
         }
       }
       dsum += d2;
@@ -1195,22 +1245,25 @@ size_t tc_residual_workspace_bytes(int64_t n1, int64_t S) {
 
 bool tc_residual_supported(int64_t n1, int c) { return n1 % 8 == 0 && c >= 1 && c <= 64; }
 
-template <int RN, bool XLO>
+template <bool XLO>
 void launch_residual(const CUtensorMap& mx, const CUtensorMap& mxlo, const CUtensorMap& mq,
                      const __nv_bfloat16* Hp, int64_t n1, int64_t S, double* acc) {
   Ctx* ctx = current();
   const uint64_t hd[2] = {128, (uint64_t)S};
   const uint64_t hs[1] = {256};
-  const uint32_t hbox[2] = {64, RN};
+  const uint32_t hbox[2] = {64, 128};
   const CUtensorMap mh = make_map(Hp, 2, hd, hs, hbox);
   const int mblocks = static_cast<int>((n1 + kBM - 1) / kBM);
-  const int64_t tiles = ((S + RN - 1) / RN) * mblocks;
-  const size_t stage = 2 * (size_t)128 * 128 + 2 * (size_t)RN * 128 + (XLO ? 4 : 2) * (size_t)64 * RN * 2;
-  const size_t smem = 1024 + 2 * stage + sizeof(Bars) + 64;
-  set_smem(tc_residual_kernel<RN, XLO>, smem);
-  const int grid = static_cast<int>(std::min<int64_t>(tiles, ctx->num_sms));
-  tc_residual_kernel<RN, XLO><<<grid, kThreads, smem, stream()>>>(mx, mxlo, mq, mh, n1, S, mblocks,
-                                                                  acc, ctx->d_status);
+  const int64_t sblocks = (S + 127) / 128;
+  // CTAs per row block: fill the SMs, but no more than there are column tiles
+  const int cpm = static_cast<int>(std::max<int64_t>(1, std::min<int64_t>(sblocks, ctx->num_sms / mblocks)));
+  const int ns = XLO ? 2 : 3;
+  const size_t stage = 2 * (size_t)128 * 128 + (XLO ? 4 : 2) * (size_t)64 * 128 * 2;
+  const size_t smem = 1024 + ns * stage + 2 * (size_t)128 * 128 + sizeof(Bars) + 64;
+  set_smem(tc_residual_kernel<XLO>, smem);
+  const int grid = cpm * mblocks;
+  tc_residual_kernel<XLO><<<grid, kThreads, smem, stream()>>>(mx, mxlo, mq, mh, n1, S, mblocks,
+                                                              cpm, acc, ctx->d_status);
   check_launch("tc_residual_bf16");
 }
 
@@ -1235,15 +1288,13 @@ void tc_residual_bf16(const __nv_bfloat16* X, int64_t n1, int64_t S, const doubl
   const uint64_t qs[1] = {256};
   const uint32_t qbox[2] = {64, kBM};
   const CUtensorMap mq = make_map(Qp, 2, qd, qs, qbox);
+  const uint32_t xbox[2] = {64, 128};
+  const CUtensorMap mx = make_map(X, 2, xd, xs, xbox);
   if (!Xlo) {
-    const uint32_t xbox[2] = {64, 128};
-    const CUtensorMap mx = make_map(X, 2, xd, xs, xbox);
-    launch_residual<128, false>(mx, mx, mq, Hp, n1, S, acc);
+    launch_residual<false>(mx, mx, mq, Hp, n1, S, acc);
   } else {
-    const uint32_t xbox[2] = {64, 64};
-    const CUtensorMap mx = make_map(X, 2, xd, xs, xbox);
     const CUtensorMap mxlo = make_map(Xlo, 2, xd, xs, xbox);
-    launch_residual<64, true>(mx, mxlo, mq, Hp, n1, S, acc);
+    launch_residual<true>(mx, mxlo, mq, Hp, n1, S, acc);
   }
 }
 

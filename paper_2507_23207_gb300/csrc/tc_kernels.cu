@@ -515,13 +515,17 @@ __global__ void __launch_bounds__(kThreads, 1)
 // Epilogue per t: Y2[i2, k] += D1 w[t, k] (registers across t) and
 // C[t, k] += sum_i2 Omega2[i2, k] D1[i2, k]; at the end D2 -> Y1.
 // For d = 3, C is Y3 itself.
+// X stages of the fused tree: four while they fit beside the two B2 buffers
+__host__ __device__ constexpr int tree_stages(int N) { return N <= 48 ? 4 : 3; }
+
 struct TreeArgs {
   const float* w;            // T x L
   const __nv_bfloat16* om2;  // n2 x L (column-major)
   float* Y1;                 // n1 x L
   float* Y2;                 // n2 x L
   float* C;                  // T x L
-  int64_t n1, n2, T, t_per_cta;
+  float* Yw;                 // per-CTA partials of Y1, [cta][k < N][i1 < n1p], or null (atomics)
+  int64_t n1, n2, T, t_per_cta, n1p;
   int L, nb, kchunks;        // kchunks = ceil(n1 / 128)
 };
 
@@ -529,7 +533,7 @@ template <int N>
 __global__ void __launch_bounds__(320, 1)
     tc_tree_kernel(const __grid_constant__ CUtensorMap mapX,
                    const __grid_constant__ CUtensorMap mapF, const TreeArgs P, int* status) {
-  constexpr int NS = 3;
+  constexpr int NS = tree_stages(N);
   constexpr uint32_t kXBox = 64 * 128 * 2;            // 64 i1 x 128 i2
   constexpr uint32_t kFBox = N * 128;                 // N rows (k) x 64 i1
   constexpr uint32_t kStage = 2 * kXBox + 2 * kFBox;
@@ -749,8 +753,15 @@ __global__ void __launch_bounds__(320, 1)
       for (int k = 0; k < N; ++k)
         if (k < P.L) atomicAdd(P.Y2 + i2 + P.n2 * k, y2[k]);
     }
-    // D2 (all MMAs are complete once the last tfull has been observed)
-    if (t1 > t0) {
+    // D2 (all MMAs are complete once the last tfull has been observed): this
+    // CTA's partial of Y1, stored (coalesced over i1) into its own slot of the
+    // partials buffer, which a second kernel sums in a fixed order; without
+    // the buffer, atomically into Y1
+    if (P.Yw && t1 <= t0) {
+      for (int c = 0; c < kch; ++c)
+        for (int k = 0; k < N; ++k)
+          P.Yw[(static_cast<size_t>(blockIdx.x) * N + k) * P.n1p + c * 128 + row] = 0.f;
+    } else if (t1 > t0) {
       tc_fence_after();
       for (int c = 0; c < kch; ++c) {
         const int64_t i1 = static_cast<int64_t>(c) * 128 + row;
@@ -759,10 +770,15 @@ __global__ void __launch_bounds__(320, 1)
         for (int c0 = 0; c0 < N; c0 += 16) {
           float v[16];
           tmem_ld16(base + c0, v);
-          if (i1 < P.n1)
+          if (P.Yw) {
+            float* dst = P.Yw + (static_cast<size_t>(blockIdx.x) * N + c0) * P.n1p + i1;
+#pragma unroll
+            for (int j = 0; j < 16; ++j) dst[static_cast<size_t>(j) * P.n1p] = v[j];
+          } else if (i1 < P.n1) {
 #pragma unroll
             for (int j = 0; j < 16; ++j)
               if (c0 + j < P.L) atomicAdd(P.Y1 + i1 + P.n1 * (c0 + j), v[j]);
+          }
         }
       }
     }
@@ -991,6 +1007,21 @@ __global__ void __launch_bounds__(kThreads, 1)
   }
 }
 
+// Y1[i + n1 k] = sum over the tree CTAs c (in order) of Yw[(c N + k) n1p + i]
+__global__ void tree_reduce_kernel(const float* __restrict__ Yw, int parts, int64_t n1, int64_t n1p,
+                                   int L, int N, float* __restrict__ Y1) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n1 * L;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = e % n1;
+    const int k = static_cast<int>(e / n1);
+    const float* src = Yw + static_cast<size_t>(k) * n1p + i;
+    const size_t step = static_cast<size_t>(N) * n1p;
+    float acc = 0.f;
+    for (int c = 0; c < parts; ++c) acc += src[c * step];
+    Y1[e] = acc;
+  }
+}
+
 // rows of a K-major hi/lo pair: out[r * 128 + k] = hi(v), out[r * 128 + 64 + k]
 // = lo(v) for k < c (zero for c <= k < 64), v = src[k * ld_k + r * ld_r]
 template <class T>
@@ -1120,7 +1151,10 @@ size_t tc_workspace_bytes(int64_t n1, int64_t S, int L) {
   (void)S;
   const int64_t n1p = (n1 + 63) / 64 * 64;
   const int64_t Lp = (L + 15) / 16 * 16;
-  return ws_bytes((size_t)n1p * 2 * Lp, 2) + ws_bytes((size_t)(n1p + 64) * Lp * 2, 2) + (1 << 16);
+  const int64_t n1t = (n1 + 127) / 128 * 128;
+  const int sms = std::max(1, current()->num_sms);
+  return ws_bytes((size_t)n1p * 2 * Lp, 2) + ws_bytes((size_t)(n1p + 64) * Lp * 2, 2) +
+         ws_bytes((size_t)sms * Lp * n1t, 4) + (1 << 16);  // + tree partials of Y1
 }
 
 void tc_gemm_tn_bf16(const __nv_bfloat16* X, int64_t n1, int64_t S, const __nv_bfloat16* Fhi,
@@ -1196,7 +1230,6 @@ void tc_tree_bf16(const __nv_bfloat16* X, int64_t n1, int64_t n2, int64_t T,
   pack_factor_kernel<<<(int)std::min<int64_t>((n1p * N + 255) / 256, 4096), 256, 0, stream()>>>(
       Om1, nullptr, n1, n1p, L, N, N, Fc);
   check_launch("pack_factor");
-  KRP_CUDA_CHECK(cudaMemsetAsync(Y1, 0, sizeof(float) * n1 * L, stream()));
   KRP_CUDA_CHECK(cudaMemsetAsync(Y2, 0, sizeof(float) * n2 * L, stream()));
   KRP_CUDA_CHECK(cudaMemsetAsync(C, 0, sizeof(float) * T * L, stream()));
   const uint64_t xd[3] = {(uint64_t)n1, (uint64_t)n2, (uint64_t)T};
@@ -1224,8 +1257,12 @@ void tc_tree_bf16(const __nv_bfloat16* X, int64_t n1, int64_t n2, int64_t T,
   P.t_per_cta = (T + chunks - 1) / chunks;
   chunks = (T + P.t_per_cta - 1) / P.t_per_cta;
   const int grid = static_cast<int>(P.nb * chunks);
+  // partials of Y1 per CTA (the workspace holds one set per SM)
+  P.n1p = n1p;
+  P.Yw = (grid <= ctx->num_sms) ? ctx->ws.take<float>((size_t)grid * N * n1p) : nullptr;
+  if (!P.Yw) KRP_CUDA_CHECK(cudaMemsetAsync(Y1, 0, sizeof(float) * n1 * L, stream()));
   auto go = [&](auto kern, size_t stage) {
-    const size_t smem = 1024 + 3 * stage + 2 * (4 * (size_t)N * 128) + sizeof(Bars) + 64;
+    const size_t smem = 1024 + tree_stages(N) * stage + 2 * (4 * (size_t)N * 128) + sizeof(Bars) + 64;
     set_smem(kern, smem);
     kern<<<grid, 320, smem, stream()>>>(mx, mf, P, ctx->d_status);
   };
@@ -1237,6 +1274,11 @@ void tc_tree_bf16(const __nv_bfloat16* X, int64_t n1, int64_t n2, int64_t T,
     default: fail(KRP_EUNSUPPORTED, "fused tree width %d", N);
   }
   check_launch("tc_tree_bf16");
+  if (P.Yw) {
+    tree_reduce_kernel<<<(int)std::min<int64_t>((n1 * L + 255) / 256, 4096), 256, 0, stream()>>>(
+        P.Yw, grid, n1, n1p, L, N, Y1);
+    check_launch("tree_reduce");
+  }
 }
 
 size_t tc_residual_workspace_bytes(int64_t n1, int64_t S) {

@@ -413,15 +413,15 @@ def c4_run(ctx, dev, stream, args):
 
 
 # DRAM traffic (read + write bytes) of one big launch of the dominant kernel
-# at 1024^3: ncu at 512^3 measured 538.8 MB read (X once) and 41.9 MB write
+# at 1024^3: ncu at 512^3 measured 537.0 MB read (X once) and 42.9 MB write
 # (the (N/n1) x l output); X scales x8 and the output x4 to 1024^3
 # (profiles/ncu_f32_kernels_512cubed.md).  Set to None if the kernel changes.
-TTM48_TRAFFIC_PER_BIG_LAUNCH = 538.8e6 * 8 + 41.9e6 * 4
+TTM48_TRAFFIC_PER_BIG_LAUNCH = 537.0e6 * 8 + 42.9e6 * 4
 
 
 def trace_roofline(spec, f32, peaks, args):
     """Roofline of the dominant kernel of the FP32 step, the tiled TTM
-    gemm_tn_tile<48> (39% of the step in the ncu launch list).  Each step
+    gemm_tn_tile<48> (~43% of the step in the ncu launch list).  Each step
     launches it four times: the dimension tree's B-part (X_(1)^T Omega_1) and
     the core's first TTM (X_(1)^T Q_1) -- both a contraction of the whole
     1024 x 1024^2 X with a 1024 x 48 factor -- then the core's TTMs on the

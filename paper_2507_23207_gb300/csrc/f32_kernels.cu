@@ -10,6 +10,7 @@
 // plus the "diagonal" contractions that finish a dimension tree (Sec. 5.1,
 // memoization) and the streaming FP64-accumulated residual.
 #include <algorithm>
+#include <type_traits>
 
 #include "common.cuh"
 
@@ -765,8 +766,13 @@ __global__ void __launch_bounds__(256, 2)
 // are staged [s][i] and [k][i] (pitch GP floats) by an NS-stage cp.async ring
 // with one block barrier per chunk.  Each copy slot of a thread is fixed, so
 // its global address is computed once and advanced by GK per chunk.
+// PAIR: each accumulator is a pair of partial sums over the even and the odd
+// contraction indices, updated by the paired FP32 FMA (fma.rn.f32x2): both
+// operands come as natural register pairs of the 16-byte loads, and one
+// instruction does two FMAs, leaving issue slots for the loads and barriers
+// (the pair is summed once at the end).
 constexpr int GK = 16, GP = 20;
-template <int NP, int BMS, int NS, int MINB>
+template <int NP, int BMS, int NS, int MINB, bool PAIR>
 __global__ void __launch_bounds__(BMS, MINB)
     gemm_tn_tile_kernel(const float* __restrict__ A, int64_t lda, int64_t S, int K,
                         const float* __restrict__ F, int64_t ldf, int L, float* __restrict__ out,
@@ -778,11 +784,17 @@ __global__ void __launch_bounds__(BMS, MINB)
   const int tid = threadIdx.x, g = tid >> 3, h = tid & 7;
   const int64_t s0 = (int64_t)blockIdx.x * BMS;
   const int k0 = blockIdx.y * NP;
-  float acc[8][CPT];
+  using Acc = typename std::conditional<PAIR, float2, float>::type;
+  Acc acc[8][CPT];
 #pragma unroll
   for (int j = 0; j < 8; ++j)
 #pragma unroll
-    for (int c = 0; c < CPT; ++c) acc[j][c] = 0.f;
+    for (int c = 0; c < CPT; ++c) {
+      if constexpr (PAIR)
+        acc[j][c] = make_float2(0.f, 0.f);
+      else
+        acc[j][c] = 0.f;
+    }
   const int nchunks = (K + GK - 1) / GK;
   constexpr int AV = BMS * (GK / 4) / NT;
   constexpr int FV = (NP * (GK / 4) + NT - 1) / NT;
@@ -841,12 +853,17 @@ __global__ void __launch_bounds__(BMS, MINB)
         const float4 a = *reinterpret_cast<const float4*>(&As[st][g + RG * j][ii]);
 #pragma unroll
         for (int cc = 0; cc < CPT; ++cc) {
-          float v = acc[j][cc];
-          v = fmaf(a.x, f[cc].x, v);
-          v = fmaf(a.y, f[cc].y, v);
-          v = fmaf(a.z, f[cc].z, v);
-          v = fmaf(a.w, f[cc].w, v);
-          acc[j][cc] = v;
+          if constexpr (PAIR) {
+            acc[j][cc] = __ffma2_rn(make_float2(a.x, a.y), make_float2(f[cc].x, f[cc].y), acc[j][cc]);
+            acc[j][cc] = __ffma2_rn(make_float2(a.z, a.w), make_float2(f[cc].z, f[cc].w), acc[j][cc]);
+          } else {
+            float v = acc[j][cc];
+            v = fmaf(a.x, f[cc].x, v);
+            v = fmaf(a.y, f[cc].y, v);
+            v = fmaf(a.z, f[cc].z, v);
+            v = fmaf(a.w, f[cc].w, v);
+            acc[j][cc] = v;
+          }
         }
       }
     }
@@ -860,7 +877,12 @@ __global__ void __launch_bounds__(BMS, MINB)
       const int k = k0 + h + 8 * cc;
       if (k < L) {
         float* o = out + s + ldo * k;
-        *o = accumulate ? *o + acc[j][cc] : acc[j][cc];
+        float v;
+        if constexpr (PAIR)
+          v = acc[j][cc].x + acc[j][cc].y;
+        else
+          v = acc[j][cc];
+        *o = accumulate ? *o + v : v;
       }
     }
   }
@@ -1023,15 +1045,15 @@ __global__ void krp_weights_padded_kernel(const RadixDev R, int64_t T, int L, in
 }  // namespace
 
 namespace {
-template <int NP, int MINB>
+template <int NP, int MINB, int NS, bool PAIR>
 void gemm_tn_tile_launch(const float* A, int64_t lda, int64_t S, int K, const float* F, int64_t ldf,
                          int L, float* out, int64_t ldo, bool accumulate) {
-  constexpr int BMS = 128, NS = 4;
+  constexpr int BMS = 128;
   dim3 grid((unsigned)((S + BMS - 1) / BMS), (unsigned)((L + NP - 1) / NP));
   const size_t smem = sizeof(float) * NS * (BMS + NP) * GP;
-  set_dyn_smem(gemm_tn_tile_kernel<NP, BMS, NS, MINB>, smem);
-  gemm_tn_tile_kernel<NP, BMS, NS, MINB><<<grid, BMS, smem, stream()>>>(A, lda, S, K, F, ldf, L, out,
-                                                                        ldo, accumulate ? 1 : 0);
+  set_dyn_smem(gemm_tn_tile_kernel<NP, BMS, NS, MINB, PAIR>, smem);
+  gemm_tn_tile_kernel<NP, BMS, NS, MINB, PAIR><<<grid, BMS, smem, stream()>>>(
+      A, lda, S, K, F, ldf, L, out, ldo, accumulate ? 1 : 0);
   check_launch(NP == 16 ? "gemm_tn_tile<16>" : NP == 32 ? "gemm_tn_tile<32>"
                : NP == 48 ? "gemm_tn_tile<48>" : "gemm_tn_tile<64>");
 }
@@ -1077,14 +1099,16 @@ void gemm_tn_f32(const float* A, int64_t lda, int64_t S, int K, const float* F, 
                    ((reinterpret_cast<uintptr_t>(A) & 15) == 0) &&
                    ((reinterpret_cast<uintptr_t>(F) & 15) == 0);
   if (vec) {
+    // paired FMAs with six stages up to 48 columns (+4% at 48 on 1024^3);
+    // 64 columns keep single FMAs (the pairs would not fit the registers)
     if (L <= 16)
-      gemm_tn_tile_launch<16, 4>(A, lda, S, K, F, ldf, L, out, ldo, accumulate);
+      gemm_tn_tile_launch<16, 2, 6, true>(A, lda, S, K, F, ldf, L, out, ldo, accumulate);
     else if (L <= 32)
-      gemm_tn_tile_launch<32, 4>(A, lda, S, K, F, ldf, L, out, ldo, accumulate);
+      gemm_tn_tile_launch<32, 2, 6, true>(A, lda, S, K, F, ldf, L, out, ldo, accumulate);
     else if (L <= 48)
-      gemm_tn_tile_launch<48, 4>(A, lda, S, K, F, ldf, L, out, ldo, accumulate);
+      gemm_tn_tile_launch<48, 2, 6, true>(A, lda, S, K, F, ldf, L, out, ldo, accumulate);
     else
-      gemm_tn_tile_launch<64, 2>(A, lda, S, K, F, ldf, L, out, ldo, accumulate);
+      gemm_tn_tile_launch<64, 2, 4, false>(A, lda, S, K, F, ldf, L, out, ldo, accumulate);
     return;
   }
   if (L <= 16)

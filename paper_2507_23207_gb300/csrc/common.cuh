@@ -156,6 +156,8 @@ struct QrJob {
 void qr_householder_f64(const QrJob* jobs, int count, int* status);
 // S[a + l*b] += sum over columns of G_(mode) of G[a,col] * G[b,col] (S zeroed)
 void gram_mode_f64(const double* G, int D, const int64_t* dims, int mode, double* S);
+// S[n] = G_(n) G_(n)^T for every mode n < D in one launch (dims[n] <= 64)
+void gram_modes_f64(const double* G, int D, const int64_t* dims, double* const* S);
 // eigenvectors of symmetric S (l x l), sorted by eigenvalue descending; U gets
 // the first r columns (l x r column-major)
 // One symmetric eigenproblem (l x l FP64, l <= 64): the r leading

@@ -169,6 +169,73 @@ __global__ void gram_kernel(const double* __restrict__ G, int64_t P, int64_t l, 
   }
 }
 
+// Gram matrices of every mode of a small FP64 tensor in one launch:
+//   S_n[a, b] = sum_c G_(n)[a, c] G_(n)[b, c],  a <= b computed, mirrored
+// (G_(n)[a, c] = G[p + P a + P l s], c = (p, s)).  blockIdx.y is the mode;
+// the CTAs of a mode split its columns, stage 32 of them at a time and add
+// their partial sums into S_n (zeroed beforehand).  The pairs a <= b are
+// enumerated (an FP64 warp instruction costs the same with idle lanes).
+struct GramModes {
+  const double* G;
+  double* S[KRP_MAXD];
+  int64_t P[KRP_MAXD];
+  int64_t l[KRP_MAXD];
+  int64_t ncols[KRP_MAXD];
+  int64_t per[KRP_MAXD];
+};
+__global__ void __launch_bounds__(256) gram_modes_kernel(const GramModes M) {
+  const int mode = blockIdx.y;
+  const int64_t P = M.P[mode], l = M.l[mode], ncols = M.ncols[mode];
+  const int64_t c0 = (int64_t)blockIdx.x * M.per[mode];
+  const int64_t c1 = min(ncols, c0 + M.per[mode]);
+  if (c0 >= c1) return;
+  __shared__ double colbuf[32 * 64];
+  __shared__ unsigned short tri[64 * 65 / 2];
+  const int li = (int)l;
+  for (int a = threadIdx.x; a < li; a += blockDim.x) {
+    const int off = a * li - a * (a - 1) / 2;
+    for (int b = a; b < li; ++b) tri[off + b - a] = (unsigned short)(a | (b << 8));
+  }
+  const int npair = li * (li + 1) / 2;
+  constexpr int kMaxPairs = (64 * 65 / 2 + 255) / 256;
+  double acc[kMaxPairs];
+#pragma unroll
+  for (int q = 0; q < kMaxPairs; ++q) acc[q] = 0.0;
+  for (int64_t cc = c0; cc < c1; cc += 32) {
+    const int nc = (int)((c1 - cc) < 32 ? (c1 - cc) : 32);
+    __syncthreads();
+    for (int e = threadIdx.x; e < nc * li; e += blockDim.x) {
+      const int64_t a = e % li, c = cc + e / li;
+      const int64_t p = c % P, sfx = c / P;
+      colbuf[e] = M.G[p + P * a + P * l * sfx];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < kMaxPairs; ++q) {
+      const int pr = threadIdx.x + q * 256;
+      if (pr >= npair) break;
+      const int a = tri[pr] & 0xff, b = tri[pr] >> 8;
+      double s0 = acc[q], s1 = 0.0;
+      int c = 0;
+      for (; c + 1 < nc; c += 2) {
+        s0 = fma(colbuf[a + li * c], colbuf[b + li * c], s0);
+        s1 = fma(colbuf[a + li * (c + 1)], colbuf[b + li * (c + 1)], s1);
+      }
+      if (c < nc) s0 = fma(colbuf[a + li * c], colbuf[b + li * c], s0);
+      acc[q] = s0 + s1;
+    }
+  }
+  double* S = M.S[mode];
+#pragma unroll
+  for (int q = 0; q < kMaxPairs; ++q) {
+    const int pr = threadIdx.x + q * 256;
+    if (pr >= npair) break;
+    const int a = tri[pr] & 0xff, b = tri[pr] >> 8;
+    atomicAdd(S + a + l * b, acc[q]);
+    if (a != b) atomicAdd(S + b + l * a, acc[q]);
+  }
+}
+
 constexpr int kEigMaxL = 64;
 
 
@@ -195,6 +262,19 @@ __device__ __forceinline__ float warp_max(float v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
   return v;
+}
+
+// Block-wide FP32 sum of one value per thread (all threads call it).
+__device__ float block_sum_f(float v, float* red) {
+  const int tid = threadIdx.x, nw = blockDim.x >> 5;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  __syncthreads();
+  if ((tid & 31) == 0) red[tid >> 5] = v;
+  __syncthreads();
+  float s = 0.f;
+  for (int w = 0; w < nw; ++w) s += red[w];
+  return s;
 }
 
 // Block-wide sum of one value per thread (all threads call it).
@@ -229,21 +309,24 @@ __device__ void jacobi32(float (*Sa)[EP], float (*Sb)[EP], float (*V)[EP], int n
   float(*S)[EP] = Sa;    // current matrix
   float(*Sn)[EP] = Sb;   // the round writes the rotated matrix here
   for (int sweep = 0; sweep < kEigSweeps32; ++sweep) {
-    double o = 0.0, dg = 0.0;
+    // squared norms in FP32: the matrix is scaled to max |s_ij| < 1, so the
+    // sums of squares are far inside FP32 range for a threshold test
+    float o = 0.f, dg = 0.f;
     for (int e = tid; e < n * n; e += blockDim.x) {
       const int r = e % n, c = e / n;
-      const double v = (double)S[r][c] * (double)S[r][c];
+      const float v = S[r][c] * S[r][c];
       if (r == c)
         dg += v;
       else
         o += v;
     }
-    const double off = block_sum(o, red);
-    const double dia = block_sum(dg, red + NT / 32);
+    float* redf = reinterpret_cast<float*>(red);
+    const float off = block_sum_f(o, redf);
+    const float dia = block_sum_f(dg, redf + NT / 32);
     // off-diagonal norm at 1e-6 of the diagonal's: the FP64 stage does the
     // rest (stopping at 1e-4 left the refined vectors of graded spectra, such
     // as a block Hankel's, orthonormal only to ~1e-5)
-    if (!(off > 1e-12 * dia) || off == 0.0) break;
+    if (!(off > 1e-12f * dia) || off == 0.f) break;
     // round-robin tournament: position 0 holds player 0, position k >= 1
     // holds player ((k - 1 + round) mod (n - 1)) + 1; pairs (k, n-1-k).  Lane
     // k < P keeps (k - 1 + round) and (n - 2 - k + round) mod (n - 1) as
@@ -1170,6 +1253,29 @@ void cholqr3_launch(const CqrBatch& batch, int nq, int64_t maxm, int* status) {
     cqr_solve_any(batch, nq, maxm, total_rows, pass, stream());
     check_launch("cholqr_solve_f64");
   }
+}
+
+void gram_modes_f64(const double* G, int D, const int64_t* dims, double* const* S) {
+  GramModes M{};
+  M.G = G;
+  int64_t total = 1;
+  for (int j = 0; j < D; ++j) total *= dims[j];
+  const int want = std::max(1, current()->num_sms / D);  // CTAs per mode
+  int64_t maxblocks = 1;
+  for (int n = 0; n < D; ++n) {
+    KRP_REQUIRE(dims[n] <= kEigMaxL, "core truncation supports ranks l <= %d", kEigMaxL);
+    int64_t P = 1;
+    for (int j = 0; j < n; ++j) P *= dims[j];
+    M.S[n] = S[n];
+    M.P[n] = P;
+    M.l[n] = dims[n];
+    M.ncols[n] = total / dims[n];
+    M.per[n] = std::max<int64_t>(8, (M.ncols[n] + want - 1) / want);
+    maxblocks = std::max<int64_t>(maxblocks, (M.ncols[n] + M.per[n] - 1) / M.per[n]);
+    KRP_CUDA_CHECK(cudaMemsetAsync(S[n], 0, sizeof(double) * dims[n] * dims[n], stream()));
+  }
+  gram_modes_kernel<<<dim3((unsigned)maxblocks, (unsigned)D), 256, 0, stream()>>>(M);
+  check_launch("gram_modes_f64");
 }
 
 void gram_mode_f64(const double* G, int D, const int64_t* dims, int mode, double* S) {

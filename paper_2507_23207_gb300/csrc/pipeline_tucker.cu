@@ -535,8 +535,8 @@ void tucker_pipeline(bool sequential, const void* X, krp_dtype xt, int d, const 
       U[i] = ws.take<double>((size_t)ell[i] * ranks[i]);
       lv[i] = ell[i];
       rv[i] = ranks[i];
-      gram_mode_f64(G64, d, cdim, i, Sg[i]);
     }
+    gram_modes_f64(G64, d, cdim, Sg);
     sym_eig_top_f64(Sg, lv, rv, U, d, c->d_status);
     double* src = G64;
     double* dst = G64b;

@@ -221,6 +221,38 @@ krp_status krp_multi_ttm(krp_ctx ctx, const void* X, krp_dtype xt, int d,
                          const int64_t* dims, const double* const* Q,
                          const int* cols, float* G);
 
+/* ---- a7, a8 as separate steps (for sharded use: one slab of X per GPU) ---- */
+
+/* Rank truncation of a Tucker core by an FP64 HOSVD of the core: per mode i
+ * the leading ranks[i] left singular vectors U_i of the unfolding G_(i)
+ * (from the eigenvectors of the ell[i] x ell[i] Gram matrix), then
+ * core_out = G x_1 U_1^T ... x_d U_d^T and factors_out[i] = factors[i] U_i.
+ * (Sec. 2.2 HOSVD applied to the small core; equal to the HOSVD of the
+ * rank-ell approximation because every factors[i] is orthonormal.)
+ *   core:        device FP32, ell[0] x ... x ell[d-1], mode-1 fastest (read)
+ *   factors[i]:  device FP64, dims[i] x ell[i], column-major (read)
+ *   core_out:    device FP32, ranks[0] x ... x ranks[d-1] (written)
+ *   factors_out[i]: device FP64, dims[i] x ranks[i] (written)
+ * Requires 1 <= ranks[i] <= ell[i] <= min(64, dims[i]).  Synchronises the
+ * context stream; KRP_ENUMERIC if a non-finite value is met. */
+krp_status krp_core_truncate(krp_ctx ctx, int d, const int64_t* dims, const int* ell,
+                             const int* ranks, const float* core,
+                             const double* const* factors, float* core_out,
+                             double* const* factors_out);
+
+/* Residual sums of a Tucker approximation X_hat = core x {factors}:
+ *   sums[0] = ||X - X_hat||_F^2,  sums[1] = ||X||_F^2   (FP64, host array)
+ * by one streaming pass over X (Sec. 5.2 error; the same computation as
+ * KRP_RESIDUAL).  For a slab of X along the last mode, pass the slab's dims
+ * and the matching rows of the last factor: the sums of all slabs add up to
+ * the whole tensor's.
+ *   X: device, dims, mode-1 fastest, dtype xt (F32, BF16 or BF16X2)
+ *   core: device FP32, core_dims; factors[i]: device FP64 dims[i] x core_dims[i]
+ * Synchronises the context stream. */
+krp_status krp_residual(krp_ctx ctx, const void* X, krp_dtype xt, int d,
+                        const int64_t* dims, const int* core_dims, const float* core,
+                        const double* const* factors, double* sums);
+
 /* ---- a6-a8: randomized Tucker pipelines (Alg. 7, Alg. 8) ------------------ */
 
 typedef struct krp_phase_times {

@@ -308,6 +308,55 @@ krp_status krp_multi_ttm(krp_ctx ctx, const void* X, krp_dtype xt, int d, const 
   });
 }
 
+krp_status krp_core_truncate(krp_ctx ctx, int d, const int64_t* dims, const int* ell,
+                             const int* ranks, const float* core, const double* const* factors,
+                             float* core_out, double* const* factors_out) {
+  return guarded(ctx, [&] {
+    KRP_REQUIRE(d >= 1 && d <= KRP_MAXD, "d out of range");
+    KRP_REQUIRE(dims && ell && ranks && core && factors && core_out && factors_out, "NULL argument");
+    for (int i = 0; i < d; ++i) {
+      KRP_REQUIRE(ranks[i] >= 1 && ranks[i] <= ell[i], "need 1 <= ranks[%d] <= ell[%d]", i, i);
+      KRP_REQUIRE(ell[i] <= 64 && ell[i] <= dims[i], "need ell[%d] <= min(64, dims[%d])", i, i);
+      KRP_REQUIRE(factors[i] && factors_out[i], "factors[%d] / factors_out[%d] is NULL", i, i);
+      KRP_REQUIRE(is_device_ptr(factors[i]) && is_device_ptr(factors_out[i]),
+                  "factors must be device memory");
+    }
+    KRP_REQUIRE(is_device_ptr(core) && is_device_ptr(core_out), "core must be device memory");
+    Ctx* c = current();
+    ensure_workspace(c, core_truncate_workspace_bytes(d, ell, ranks));
+    KRP_CUDA_CHECK(cudaMemsetAsync(c->d_status, 0, sizeof(int), c->stream));
+    core_truncate(d, dims, ell, ranks, core, factors, core_out, factors_out);
+    raise_device_status(c);
+  });
+}
+
+krp_status krp_residual(krp_ctx ctx, const void* X, krp_dtype xt, int d, const int64_t* dims,
+                        const int* core_dims, const float* core, const double* const* factors,
+                        double* sums) {
+  return guarded(ctx, [&] {
+    KRP_REQUIRE(d >= 2 && d <= KRP_MAXD, "d out of range");
+    checked_numel(d, dims);
+    KRP_REQUIRE(X && core_dims && core && factors && sums, "NULL argument");
+    KRP_REQUIRE(xt == KRP_F32 || xt == KRP_BF16 || xt == KRP_BF16X2,
+                "X dtype must be F32, BF16 or BF16X2");
+    KRP_REQUIRE(is_device_ptr(X) && is_device_ptr(core), "X and core must be device memory");
+    int64_t cdim[KRP_MAXD];
+    for (int i = 0; i < d; ++i) {
+      KRP_REQUIRE(core_dims[i] >= 1 && core_dims[i] <= 256, "core_dims[%d] out of range", i);
+      KRP_REQUIRE(factors[i] && is_device_ptr(factors[i]), "factors[%d] must be device memory", i);
+      cdim[i] = core_dims[i];
+    }
+    Ctx* c = current();
+    ensure_workspace(c, residual_workspace_bytes(d, dims, cdim, xt) + ws_bytes(4, 8));
+    double* acc = c->ws.take<double>(4);
+    KRP_CUDA_CHECK(cudaMemsetAsync(c->d_status, 0, sizeof(int), c->stream));
+    KRP_CUDA_CHECK(cudaMemsetAsync(acc, 0, 2 * sizeof(double), c->stream));
+    residual_sums(X, xt, d, dims, core, cdim, factors, acc);
+    KRP_CUDA_CHECK(cudaMemcpyAsync(sums, acc, 2 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    raise_device_status(c);
+  });
+}
+
 krp_status krp_tucker_rhosvd(krp_ctx ctx, const void* X, krp_dtype xt, int d, const int64_t* dims,
                              const int* ranks, int oversample, uint64_t seed, unsigned flags,
                              krp_tucker_out* out) {

@@ -31,6 +31,13 @@ size_t multi_ttm_workspace_bytes(int d, const int64_t* dims, const int* cols, kr
 void multi_ttm(const void* X, krp_dtype xt, int d, const int64_t* dims, const double* const* Q,
                const int* cols, float* G);
 
+size_t core_truncate_workspace_bytes(int d, const int* ell, const int* ranks);
+void core_truncate(int d, const int64_t* dims, const int* ell, const int* ranks, const float* G,
+                   const double* const* Q, float* Gout, double* const* Qout);
+size_t residual_workspace_bytes(int d, const int64_t* dims, const int64_t* cdim, krp_dtype xt);
+void residual_sums(const void* Xd, krp_dtype xt, int d, const int64_t* dims, const float* Gc,
+                   const int64_t* cdim, const double* const* Q, double* acc);
+
 void tucker_pipeline(bool sequential, const void* X, krp_dtype xt, int d, const int64_t* dims,
                      const int* ranks, int oversample, uint64_t seed, unsigned flags,
                      krp_tucker_out* out);

@@ -325,6 +325,110 @@ void multi_ttm(const void* X, krp_dtype xt, int d, const int64_t* dims, const do
   }
 }
 
+// ------------------------------------------------ a7 truncation, a8 residual ----
+size_t core_truncate_workspace_bytes(int d, const int* ell, const int* ranks) {
+  int64_t core_l = 1;
+  size_t b = 0;
+  for (int i = 0; i < d; ++i) {
+    core_l *= ell[i];
+    b += ws_bytes((size_t)ell[i] * ell[i], 8) + ws_bytes((size_t)ell[i] * ranks[i], 8);
+  }
+  return b + 2 * ws_bytes((size_t)core_l, 8) + sym_eig_workspace_bytes(d) + (1 << 16);
+}
+
+// Rank-r truncation of an l-core by an FP64 HOSVD of the core (Gram of every
+// mode unfolding, top-r eigenvectors U_i, G <- G x {U_i^T}, Q_i <- Q_i U_i).
+// G FP32 (ell, mode-1 fastest), Q[i] FP64 dims[i] x ell[i]; Gout FP32
+// (ranks), Qout[i] FP64 dims[i] x ranks[i]; all device memory.
+void core_truncate(int d, const int64_t* dims, const int* ell, const int* ranks, const float* G,
+                   const double* const* Q, float* Gout, double* const* Qout) {
+  Ctx* c = current();
+  Workspace& ws = c->ws;
+  int64_t core_l = 1;
+  int64_t cdim[KRP_MAXD];
+  for (int i = 0; i < d; ++i) {
+    core_l *= ell[i];
+    cdim[i] = ell[i];
+  }
+  double* G64 = ws.take<double>((size_t)core_l);
+  double* G64b = ws.take<double>((size_t)core_l);
+  cast_f32_to_f64(G, G64, core_l);
+  double* Sg[KRP_MAXD];
+  double* U[KRP_MAXD];
+  int lv[KRP_MAXD], rv[KRP_MAXD];
+  for (int i = 0; i < d; ++i) {
+    Sg[i] = ws.take<double>((size_t)ell[i] * ell[i]);
+    U[i] = ws.take<double>((size_t)ell[i] * ranks[i]);
+    lv[i] = ell[i];
+    rv[i] = ranks[i];
+  }
+  gram_modes_f64(G64, d, cdim, Sg);
+  sym_eig_top_f64(Sg, lv, rv, U, d, c->d_status);
+  double* src = G64;
+  double* dst = G64b;
+  for (int i = 0; i < d; ++i) {
+    ttm_small_f64(src, d, cdim, i, U[i], ranks[i], dst);
+    cdim[i] = ranks[i];
+    std::swap(src, dst);
+    matmul_f64(Q[i], U[i], Qout[i], dims[i], ell[i], ranks[i]);
+  }
+  int64_t rl = 1;
+  for (int i = 0; i < d; ++i) rl *= ranks[i];
+  cast_f64_to_f32(src, Gout, rl);
+}
+
+size_t residual_workspace_bytes(int d, const int64_t* dims, const int64_t* cdim, krp_dtype xt) {
+  const int64_t N = checked_numel(d, dims);
+  size_t b = 2 * ws_bytes((size_t)(N / dims[0]) * cdim[0], 4);
+  int64_t cl = 1;
+  for (int i = 0; i < d; ++i) {
+    b += ws_bytes((size_t)dims[i] * cdim[i], 4);
+    cl *= cdim[i];
+  }
+  b += ws_bytes((size_t)cl, 4);
+  if (bf16_family(xt)) b += tc_residual_workspace_bytes(dims[0], N / dims[0]);
+  return b + (1 << 16);
+}
+
+// acc[0] += ||X - Gc x {Q}||_F^2, acc[1] += ||X||_F^2 (FP64, device) by
+// streaming reconstruction: H = Gc x_2 Q_2 ... x_d Q_d (FP32, c_1 x N/n_1)
+// is expanded once, then one pass over X compares X with Q_1 H.
+void residual_sums(const void* Xd, krp_dtype xt, int d, const int64_t* dims, const float* Gc,
+                   const int64_t* cdim, const double* const* Qout, double* acc) {
+  Workspace& ws = current()->ws;
+  const int64_t N = checked_numel(d, dims);
+  int64_t out_l = 1;
+  for (int i = 0; i < d; ++i) out_l *= cdim[i];
+  float* QTf[KRP_MAXD];
+  for (int i = 1; i < d; ++i) {
+    QTf[i] = ws.take<float>((size_t)dims[i] * cdim[i]);
+    transpose_f64_to_f32(Qout[i], dims[i], cdim[i], QTf[i]);
+  }
+  float* Q1f = ws.take<float>((size_t)dims[0] * cdim[0]);
+  cast_f64_to_f32(Qout[0], Q1f, dims[0] * cdim[0]);
+  const size_t hbig = (size_t)(N / dims[0]) * cdim[0];
+  float* hb[2] = {ws.take<float>(hbig), ws.take<float>(hbig)};
+  // rotate G (c1, c2..cd) -> (c2..cd, c1), then expand modes 2..d
+  rotate_first_to_last_f32(Gc, cdim[0], out_l / cdim[0], hb[0]);
+  float* curh = hb[0];
+  int64_t size = out_l;
+  for (int j = 1; j < d; ++j) {
+    float* nx = hb[j & 1];
+    if (nx == curh) nx = hb[(j + 1) & 1];
+    const int64_t S = size / cdim[j];
+    gemm_tn_f32(curh, cdim[j], S, (int)cdim[j], QTf[j], cdim[j], (int)dims[j], nx, S, false);
+    size = S * dims[j];
+    curh = nx;
+  }
+  if (bf16_family(xt) && tc_residual_supported(dims[0], (int)cdim[0]))
+    tc_residual_bf16(static_cast<const __nv_bfloat16*>(Xd), dims[0], N / dims[0], Qout[0],
+                     (int)cdim[0], curh, acc, lo_plane(Xd, xt, N));
+  else if (xt == KRP_BF16X2)
+    fail(KRP_EUNSUPPORTED, "BF16 hi/lo residual needs n_1 %% 8 == 0 and at most 64 columns");
+  else
+    residual_f32(Xd, xt, dims[0], N / dims[0], Q1f, (int)cdim[0], curh, acc);
+}
+
 // ------------------------------------------------------------ pipeline -----
 void tucker_pipeline(bool sequential, const void* X, krp_dtype xt, int d, const int64_t* dims,
                      const int* ranks, int oversample, uint64_t seed, unsigned flags,
@@ -524,33 +628,12 @@ void tucker_pipeline(bool sequential, const void* X, krp_dtype xt, int d, const 
   for (int i = 0; i < d; ++i) cdim[i] = ell[i];
   const int tmark_trunc0 = tm.n;
   if (trunc) {
-    double* G64 = ws.take<double>((size_t)core_l);
-    double* G64b = ws.take<double>((size_t)core_l);
-    cast_f32_to_f64(G, G64, core_l);
-    double* Sg[KRP_MAXD];
-    double* U[KRP_MAXD];
-    int lv[KRP_MAXD], rv[KRP_MAXD];
-    for (int i = 0; i < d; ++i) {
-      Sg[i] = ws.take<double>((size_t)ell[i] * ell[i]);
-      U[i] = ws.take<double>((size_t)ell[i] * ranks[i]);
-      lv[i] = ell[i];
-      rv[i] = ranks[i];
-    }
-    gram_modes_f64(G64, d, cdim, Sg);
-    sym_eig_top_f64(Sg, lv, rv, U, d, c->d_status);
-    double* src = G64;
-    double* dst = G64b;
-    for (int i = 0; i < d; ++i) {
-      ttm_small_f64(src, d, cdim, i, U[i], ranks[i], dst);
-      cdim[i] = ranks[i];
-      std::swap(src, dst);
-      Qout[i] = ws.take<double>((size_t)dims[i] * ranks[i]);
-      matmul_f64(Q[i], U[i], Qout[i], dims[i], ell[i], ranks[i]);
-    }
+    for (int i = 0; i < d; ++i) Qout[i] = ws.take<double>((size_t)dims[i] * ranks[i]);
     int64_t rl = 1;
     for (int i = 0; i < d; ++i) rl *= ranks[i];
     Gout = ws.take<float>((size_t)rl);
-    cast_f64_to_f32(src, Gout, rl);
+    core_truncate(d, dims, ell, ranks, G, Q, Gout, Qout);
+    for (int i = 0; i < d; ++i) cdim[i] = ranks[i];
   }
   tm.mark();
   int64_t out_l = 1;
@@ -560,35 +643,8 @@ void tucker_pipeline(bool sequential, const void* X, krp_dtype xt, int d, const 
   double resid_val = -1.0, xnorm = -1.0;
   double* acc = ws.take<double>(4);
   if (resid) {
-    float* QTf[KRP_MAXD];
-    for (int i = 1; i < d; ++i) {
-      QTf[i] = ws.take<float>((size_t)dims[i] * cdim[i]);
-      transpose_f64_to_f32(Qout[i], dims[i], cdim[i], QTf[i]);
-    }
-    float* Q1f = ws.take<float>((size_t)dims[0] * cdim[0]);
-    cast_f64_to_f32(Qout[0], Q1f, dims[0] * cdim[0]);
-    const size_t hbig = (size_t)(N / dims[0]) * cdim[0];
-    float* hb[2] = {ws.take<float>(hbig), ws.take<float>(hbig)};
-    // rotate G (c1, c2..cd) -> (c2..cd, c1), then expand modes 2..d
-    rotate_first_to_last_f32(Gout, cdim[0], out_l / cdim[0], hb[0]);
-    float* curh = hb[0];
-    int64_t size = out_l;
-    for (int j = 1; j < d; ++j) {
-      float* nx = hb[j & 1];
-      if (nx == curh) nx = hb[(j + 1) & 1];
-      const int64_t S = size / cdim[j];
-      gemm_tn_f32(curh, cdim[j], S, (int)cdim[j], QTf[j], cdim[j], (int)dims[j], nx, S, false);
-      size = S * dims[j];
-      curh = nx;
-    }
     KRP_CUDA_CHECK(cudaMemsetAsync(acc, 0, 2 * sizeof(double), c->stream));
-    if (bf16_family(xt) && tc_residual_supported(dims[0], (int)cdim[0]))
-      tc_residual_bf16(static_cast<const __nv_bfloat16*>(Xd), dims[0], N / dims[0], Qout[0],
-                       (int)cdim[0], curh, acc, lo_plane(Xd, xt, N));
-    else if (xt == KRP_BF16X2)
-      fail(KRP_EUNSUPPORTED, "BF16 hi/lo residual needs n_1 %% 8 == 0 and at most 64 columns");
-    else
-      residual_f32(Xd, xt, dims[0], N / dims[0], Q1f, (int)cdim[0], curh, acc);
+    residual_sums(Xd, xt, d, dims, Gout, cdim, Qout, acc);
   }
   tm.mark();
 

@@ -33,6 +33,7 @@ EXPORTED = [
     "krp_tucker_rhosvd", "krp_tucker_sthosvd", "krp_block_hankel_lowrank",
     "krp_block_hankel_sketch", "krp_tucker_rhosvd_batched", "krp_tucker_batch_plan_info",
     "krp_block_hankel_batched", "krp_split_bf16x2", "krp_trace_begin", "krp_trace_end",
+    "krp_core_truncate", "krp_residual",
 ]
 
 
@@ -134,6 +135,11 @@ def load_library(path: Optional[str] = None):
         "krp_split_bf16x2": (C.c_int, [vp, vp, C.c_int64, vp]),
         "krp_trace_begin": (C.c_int, [vp]),
         "krp_trace_end": (C.c_int, [vp, C.c_char_p, C.c_size_t]),
+        "krp_core_truncate": (C.c_int, [vp, C.c_int, i64p, C.POINTER(C.c_int),
+                                        C.POINTER(C.c_int), vp, C.POINTER(vp), vp,
+                                        C.POINTER(vp)]),
+        "krp_residual": (C.c_int, [vp, vp, C.c_int, C.c_int, i64p, C.POINTER(C.c_int), vp,
+                                   C.POINTER(vp), C.POINTER(C.c_double)]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -313,6 +319,22 @@ def krp_qr_noalloc(Y, m: int, l: int, Q, R=None, stream: Optional[int] = None) -
 def krp_multi_ttm(ctx: Context, X, dims: Sequence[int], Qs: Sequence, cols: Sequence[int], G):
     ctx.check(ctx.lib.krp_multi_ttm(ctx.handle, _ptr(X), _dtype_code(X), len(dims), _i64(dims),
                                     _ptrs(Qs), _i32(cols), _ptr(G)))
+
+
+def krp_core_truncate(ctx: Context, dims: Sequence[int], ell: Sequence[int], ranks: Sequence[int],
+                      core, factors: Sequence, core_out, factors_out: Sequence):
+    ctx.check(ctx.lib.krp_core_truncate(ctx.handle, len(dims), _i64(dims), _i32(ell), _i32(ranks),
+                                        _ptr(core), _ptrs(factors), _ptr(core_out),
+                                        _ptrs(factors_out)))
+
+
+def krp_residual(ctx: Context, X, dims: Sequence[int], core_dims: Sequence[int], core,
+                 factors: Sequence):
+    """Returns (||X - X_hat||_F^2, ||X||_F^2) as Python floats."""
+    sums = (C.c_double * 2)()
+    ctx.check(ctx.lib.krp_residual(ctx.handle, _ptr(X), _dtype_code(X), len(dims), _i64(dims),
+                                   _i32(core_dims), _ptr(core), _ptrs(factors), sums))
+    return float(sums[0]), float(sums[1])
 
 
 def _tucker(fn, ctx, X, dims, ranks, oversample, seed, flags, core, factors):

@@ -401,10 +401,13 @@ __global__ void diag_first_kernel(const float* __restrict__ T, const DiagDev P, 
   if (i < m0) atomicAdd(Y + i + m0 * k, acc);
 }
 
-// target n >= 1: one warp per row (i_n, s): sum over the P contiguous prefix
-// entries weighted by prod_{j<n} V_j, times prod_{j>n} V_j of s.
+// target n >= 1: one warp per row (i_n, s): sum over the Pp contiguous prefix
+// entries weighted by wpre[p + Pp k] = prod_{j<n} V_j[digit_j(p), k] (a table
+// formed once, so the inner loop is two coalesced loads and an FMA), times
+// prod_{j>n} V_j of s.  VEC: 16-byte loads (Pp, tk multiples of 4, T aligned).
+template <bool VEC>
 __global__ void diag_mid_kernel(const float* __restrict__ T, const DiagDev P, int64_t tk, int n,
-                                int L, float* __restrict__ Y) {
+                                int L, const float* __restrict__ wpre, float* __restrict__ Y) {
   const int k = blockIdx.y;
   int64_t Pp = 1, Sfx = 1;
   for (int j = 0; j < n; ++j) Pp *= P.m[j];
@@ -414,19 +417,23 @@ __global__ void diag_mid_kernel(const float* __restrict__ T, const DiagDev P, in
   const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
   const float* Tk = T + tk * k;
+  const float* wk = wpre + Pp * k;
   for (int64_t row = warp; row < mn * Sfx; row += nwarps) {
     const int64_t in = row % mn, s = row / mn;
     const float* base = Tk + Pp * row;  // = Pp*(in + mn*s)
     float part = 0.f;
-    for (int64_t p = lane; p < Pp; p += 32) {
-      float w = 1.f;
-      int64_t q = p;
-      for (int j = 0; j < n; ++j) {
-        const int64_t r = P.m[j];
-        w *= P.V[j][(q % r) + r * k];
-        q /= r;
+    if (VEC) {
+      const float4* b4 = reinterpret_cast<const float4*>(base);
+      const float4* w4 = reinterpret_cast<const float4*>(wk);
+      for (int64_t p = lane; p < (Pp >> 2); p += 32) {
+        const float4 x = b4[p], w = __ldg(w4 + p);
+        part = fmaf(x.x, w.x, part);
+        part = fmaf(x.y, w.y, part);
+        part = fmaf(x.z, w.z, part);
+        part = fmaf(x.w, w.w, part);
       }
-      part = fmaf(base[p], w, part);
+    } else {
+      for (int64_t p = lane; p < Pp; p += 32) part = fmaf(base[p], __ldg(wk + p), part);
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
@@ -1162,6 +1169,9 @@ void mttkrp_first_f32(const float* A, int64_t n1, int64_t S, const Radix& rest, 
     mttkrp_first_launch<64>(A, n1, S, R, L, Y);
 }
 
+// w[t + T*k] = prod_j V_j[digit_j(t) + r_j*k] (pipeline_tucker.cu)
+void krp_rows(const Radix& R, int64_t T, int L, bool bf16, float* w);
+
 void diag_contract_f32(const float* T, int D, const int64_t* m, int64_t tk, int n,
                        const float* const* V, int L, float* Y) {
   DiagDev P{};
@@ -1188,10 +1198,26 @@ void diag_contract_f32(const float* T, int D, const int64_t* m, int64_t tk, int 
   } else {
     int64_t nrows = m[n];
     for (int j = n + 1; j < D; ++j) nrows *= m[j];
+    // prefix weights of modes 0..n-1, one table for all rows
+    int64_t Pp = 1;
+    Radix R;
+    R.n = n;
+    for (int j = 0; j < n; ++j) {
+      Pp *= m[j];
+      R.radix[j] = m[j];
+      R.V[j] = V[j];
+    }
+    float* wpre = current()->ws.take<float>((size_t)Pp * L);
+    krp_rows(R, Pp, L, false, wpre);
     const int threads = 256;
     const int64_t blocks = std::min<int64_t>((nrows * 32 + threads - 1) / threads, 2048);
     dim3 grid((unsigned)std::max<int64_t>(1, blocks), L);
-    diag_mid_kernel<<<grid, threads, 0, stream()>>>(T, P, tk, n, L, Y);
+    const bool vec = (Pp % 4 == 0) && (tk % 4 == 0) && ((reinterpret_cast<uintptr_t>(T) & 15) == 0) &&
+                     ((reinterpret_cast<uintptr_t>(wpre) & 15) == 0);
+    if (vec)
+      diag_mid_kernel<true><<<grid, threads, 0, stream()>>>(T, P, tk, n, L, wpre, Y);
+    else
+      diag_mid_kernel<false><<<grid, threads, 0, stream()>>>(T, P, tk, n, L, wpre, Y);
     check_launch("diag_mid_f32");
   }
 }

@@ -67,9 +67,11 @@ void big_mttkrp_first(const void* X, krp_dtype xt, int64_t n1, int d_rest,
 
 // tcgen05 kernels (tc_kernels.cu)
 // Xlo (optional): lo plane of X given as a BF16 hi/lo pair (X ~ X + Xlo)
+// outb (optional): the result as a BF16 hi/lo pair instead of FP32 (hi plane
+// of S*L values at outb, lo plane at outb + S*L; `out` is not written)
 void tc_gemm_tn_bf16(const __nv_bfloat16* X, int64_t n1, int64_t S, const __nv_bfloat16* Fhi,
                      const __nv_bfloat16* Flo, int L, float* out,
-                     const __nv_bfloat16* Xlo = nullptr);
+                     const __nv_bfloat16* Xlo = nullptr, __nv_bfloat16* outb = nullptr);
 // Y[i + n1*k] = sum_t w[t + T*k] sum_{i2} X[i + n1*(i2 + n2*t)] Om2[i2 + n2*k]
 void tc_mttkrp_first_bf16(const __nv_bfloat16* X, int64_t n1, int64_t n2, int64_t T,
                           const __nv_bfloat16* Om2, const float* w, int L, float* Y,

@@ -144,6 +144,7 @@ static const __nv_bfloat16* lo_plane(const void* X, krp_dtype xt, int64_t N) {
   return xt == KRP_BF16X2 ? static_cast<const __nv_bfloat16*>(X) + N : nullptr;
 }
 static bool bf16_family(krp_dtype t) { return t == KRP_BF16 || t == KRP_BF16X2; }
+static int round_up16(int v) { return (v + 15) / 16 * 16; }
 
 void big_gemm_tn(const void* X, krp_dtype xt, int64_t n1, int64_t S, const float* Ff,
                  const __nv_bfloat16* Fhi, const __nv_bfloat16* Flo, int L, float* out) {
@@ -290,7 +291,10 @@ size_t multi_ttm_workspace_bytes(int d, const int64_t* dims, const int* cols, kr
   size_t big = (size_t)(N / dims[0]) * cols[0];
   size_t b = 2 * ws_bytes(big, 4);
   for (int j = 0; j < d; ++j) b += ws_bytes((size_t)dims[j] * cols[j], 4 + 2 + 2);
-  if (bf16_family(xt)) b += tc_workspace_bytes(dims[0], N / dims[0], 2 * cols[0]);
+  if (bf16_family(xt)) {
+    b += tc_workspace_bytes(dims[0], N / dims[0], 2 * cols[0]);
+    if (d >= 3) b += tc_workspace_bytes(dims[1], 1, 2 * cols[1]) + 2 * ws_bytes((size_t)dims[1] * cols[1], 2);
+  }
   return b + (1 << 20);
 }
 
@@ -314,9 +318,30 @@ void multi_ttm(const void* X, krp_dtype xt, int d, const int64_t* dims, const do
   float* buf[2] = {c->ws.take<float>(big), c->ws.take<float>(big)};
   int64_t size = N;
   float* cur = (d == 1) ? G : buf[0];
-  big_gemm_tn(X, xt, n1, N / n1, Qf[0], Qh, Ql, cols[0], cur);
-  size = (N / n1) * cols[0];
-  for (int j = 1; j < d; ++j) {
+  int j0 = 1;
+  // BF16 forms with d >= 3: the first TTM writes its result as a BF16 hi/lo
+  // pair (in the same 4 bytes per element as FP32, |z - hi - lo| <= 2^-17 |z|)
+  // so that the second TTM, the other contraction over a large operand, also
+  // runs on tensor cores
+  if (bf16_family(xt) && d >= 3 && dims[1] % 8 == 0 && ((N / n1) * cols[0]) % 8 == 0 &&
+      2 * round_up16(cols[1]) <= 256) {
+    __nv_bfloat16* zb = reinterpret_cast<__nv_bfloat16*>(buf[0]);
+    tc_gemm_tn_bf16(static_cast<const __nv_bfloat16*>(X), n1, N / n1, Qh, Ql, cols[0], nullptr,
+                    lo_plane(X, xt, N), zb);
+    size = (N / n1) * cols[0];
+    __nv_bfloat16* q1h = c->ws.take<__nv_bfloat16>((size_t)dims[1] * cols[1]);
+    __nv_bfloat16* q1l = c->ws.take<__nv_bfloat16>((size_t)dims[1] * cols[1]);
+    split_bf16_hilo(Q[1], dims[1] * cols[1], q1h, q1l);
+    float* nxt = (d == 2) ? G : buf[1];
+    tc_gemm_tn_bf16(zb, dims[1], size / dims[1], q1h, q1l, cols[1], nxt, zb + size);
+    size = (size / dims[1]) * cols[1];
+    cur = nxt;
+    j0 = 2;
+  } else {
+    big_gemm_tn(X, xt, n1, N / n1, Qf[0], Qh, Ql, cols[0], cur);
+    size = (N / n1) * cols[0];
+  }
+  for (int j = j0; j < d; ++j) {
     float* nxt = (j == d - 1) ? G : buf[j & 1];
     const int64_t S = size / dims[j];
     gemm_tn_f32(cur, dims[j], S, (int)dims[j], Qf[j], dims[j], cols[j], nxt, S, false);

@@ -192,7 +192,8 @@ __global__ void __launch_bounds__(kThreads, 1)
     tc_gemm_tn_kernel(const __grid_constant__ CUtensorMap mapA,
                       const __grid_constant__ CUtensorMap mapAlo,
                       const __grid_constant__ CUtensorMap mapB, int64_t S, int kchunks, int L,
-                      int Lp, int has_lo, float* __restrict__ out, int* status) {
+                      int Lp, int has_lo, float* __restrict__ out,
+                      __nv_bfloat16* __restrict__ outb, int* status) {
   constexpr uint32_t kABytes = kBM * kBK * 2;  // 16 KB
   constexpr uint32_t kANum = XLO ? 2 : 1;
   constexpr uint32_t kBBytes = N * kBK * 2;
@@ -317,9 +318,19 @@ __global__ void __launch_bounds__(kThreads, 1)
           for (int j = 0; j < 16; ++j) v[j] += w[j];
         }
         if (s < S) {
+          if (outb) {  // BF16 hi/lo pair: hi plane, then the lo plane S*L later
 #pragma unroll
-          for (int j = 0; j < 16; ++j)
-            if (c0 + j < L) out[s + S * (c0 + j)] = v[j];
+            for (int j = 0; j < 16; ++j)
+              if (c0 + j < L) {
+                const __nv_bfloat16 h = __float2bfloat16_rn(v[j]);
+                outb[s + S * (c0 + j)] = h;
+                outb[S * L + s + S * (c0 + j)] = __float2bfloat16_rn(v[j] - __bfloat162float(h));
+              }
+          } else {
+#pragma unroll
+            for (int j = 0; j < 16; ++j)
+              if (c0 + j < L) out[s + S * (c0 + j)] = v[j];
+          }
         }
       }
       tc_fence_before();
@@ -1098,7 +1109,7 @@ void set_smem(K kernel, size_t bytes) {
 
 template <int N>
 void launch_gemm_tn(const CUtensorMap& ma, const CUtensorMap* malo, const CUtensorMap& mb, int64_t S,
-                    int kchunks, int L, int Lp, int has_lo, float* out) {
+                    int kchunks, int L, int Lp, int has_lo, float* out, __nv_bfloat16* outb) {
   const int64_t tiles = (S + kBM - 1) / kBM;
   const int grid = static_cast<int>(std::min<int64_t>(tiles, current()->num_sms));
   if (!malo) {
@@ -1106,13 +1117,13 @@ void launch_gemm_tn(const CUtensorMap& ma, const CUtensorMap* malo, const CUtens
     const size_t smem = 1024 + NS * (size_t)(kBM * kBK * 2 + N * kBK * 2) + sizeof(Bars) + 64;
     set_smem(tc_gemm_tn_kernel<N, NS, false>, smem);
     tc_gemm_tn_kernel<N, NS, false><<<grid, kThreads, smem, stream()>>>(
-        ma, ma, mb, S, kchunks, L, Lp, has_lo, out, current()->d_status);
+        ma, ma, mb, S, kchunks, L, Lp, has_lo, out, outb, current()->d_status);
   } else {
     constexpr int NS = (N <= 64) ? 5 : (N <= 128 ? 4 : 3);
     const size_t smem = 1024 + NS * (size_t)(2 * kBM * kBK * 2 + N * kBK * 2) + sizeof(Bars) + 64;
     set_smem(tc_gemm_tn_kernel<N, NS, true>, smem);
     tc_gemm_tn_kernel<N, NS, true><<<grid, kThreads, smem, stream()>>>(
-        ma, *malo, mb, S, kchunks, L, Lp, has_lo, out, current()->d_status);
+        ma, *malo, mb, S, kchunks, L, Lp, has_lo, out, outb, current()->d_status);
   }
   check_launch("tc_gemm_tn_bf16");
 }
@@ -1158,7 +1169,8 @@ size_t tc_workspace_bytes(int64_t n1, int64_t S, int L) {
 }
 
 void tc_gemm_tn_bf16(const __nv_bfloat16* X, int64_t n1, int64_t S, const __nv_bfloat16* Fhi,
-                     const __nv_bfloat16* Flo, int L, float* out, const __nv_bfloat16* Xlo) {
+                     const __nv_bfloat16* Flo, int L, float* out, const __nv_bfloat16* Xlo,
+                     __nv_bfloat16* outb) {
   KRP_REQUIRE(n1 % 8 == 0, "BF16 tensor-core path needs n_1 %% 8 == 0 (n_1 = %lld)", (long long)n1);
   KRP_REQUIRE((reinterpret_cast<uintptr_t>(X) & 15) == 0, "X must be 16-byte aligned");
   KRP_REQUIRE(S < (int64_t(1) << 31), "too many rows for the TMA coordinates");
@@ -1190,23 +1202,23 @@ void tc_gemm_tn_bf16(const __nv_bfloat16* X, int64_t n1, int64_t S, const __nv_b
   const int kchunks = static_cast<int>((n1 + kBK - 1) / kBK);
   const int has_lo = Flo ? 1 : 0;
   switch (N) {
-    case 16: launch_gemm_tn<16>(ma, malo, mb, S, kchunks, L, Lp, has_lo, out); break;
-    case 32: launch_gemm_tn<32>(ma, malo, mb, S, kchunks, L, Lp, has_lo, out); break;
-    case 48: launch_gemm_tn<48>(ma, malo, mb, S, kchunks, L, Lp, has_lo, out); break;
-    case 64: launch_gemm_tn<64>(ma, malo, mb, S, kchunks, L, Lp, has_lo, out); break;
-    case 96: launch_gemm_tn<96>(ma, malo, mb, S, kchunks, L, Lp, has_lo, out); break;
-    case 128: launch_gemm_tn<128>(ma, malo, mb, S, kchunks, L, Lp, has_lo, out); break;
-    case 160: launch_gemm_tn<160>(ma, malo, mb, S, kchunks, L, Lp, has_lo, out); break;
-    case 192: launch_gemm_tn<192>(ma, malo, mb, S, kchunks, L, Lp, has_lo, out); break;
-    case 224: launch_gemm_tn<224>(ma, malo, mb, S, kchunks, L, Lp, has_lo, out); break;
-    case 256: launch_gemm_tn<256>(ma, malo, mb, S, kchunks, L, Lp, has_lo, out); break;
+    case 16: launch_gemm_tn<16>(ma, malo, mb, S, kchunks, L, Lp, has_lo, out, outb); break;
+    case 32: launch_gemm_tn<32>(ma, malo, mb, S, kchunks, L, Lp, has_lo, out, outb); break;
+    case 48: launch_gemm_tn<48>(ma, malo, mb, S, kchunks, L, Lp, has_lo, out, outb); break;
+    case 64: launch_gemm_tn<64>(ma, malo, mb, S, kchunks, L, Lp, has_lo, out, outb); break;
+    case 96: launch_gemm_tn<96>(ma, malo, mb, S, kchunks, L, Lp, has_lo, out, outb); break;
+    case 128: launch_gemm_tn<128>(ma, malo, mb, S, kchunks, L, Lp, has_lo, out, outb); break;
+    case 160: launch_gemm_tn<160>(ma, malo, mb, S, kchunks, L, Lp, has_lo, out, outb); break;
+    case 192: launch_gemm_tn<192>(ma, malo, mb, S, kchunks, L, Lp, has_lo, out, outb); break;
+    case 224: launch_gemm_tn<224>(ma, malo, mb, S, kchunks, L, Lp, has_lo, out, outb); break;
+    case 256: launch_gemm_tn<256>(ma, malo, mb, S, kchunks, L, Lp, has_lo, out, outb); break;
     default:
-      if (N == 80) launch_gemm_tn<80>(ma, malo, mb, S, kchunks, L, Lp, has_lo, out);
-      else if (N == 112) launch_gemm_tn<112>(ma, malo, mb, S, kchunks, L, Lp, has_lo, out);
-      else if (N == 144) launch_gemm_tn<144>(ma, malo, mb, S, kchunks, L, Lp, has_lo, out);
-      else if (N == 176) launch_gemm_tn<176>(ma, malo, mb, S, kchunks, L, Lp, has_lo, out);
-      else if (N == 208) launch_gemm_tn<208>(ma, malo, mb, S, kchunks, L, Lp, has_lo, out);
-      else if (N == 240) launch_gemm_tn<240>(ma, malo, mb, S, kchunks, L, Lp, has_lo, out);
+      if (N == 80) launch_gemm_tn<80>(ma, malo, mb, S, kchunks, L, Lp, has_lo, out, outb);
+      else if (N == 112) launch_gemm_tn<112>(ma, malo, mb, S, kchunks, L, Lp, has_lo, out, outb);
+      else if (N == 144) launch_gemm_tn<144>(ma, malo, mb, S, kchunks, L, Lp, has_lo, out, outb);
+      else if (N == 176) launch_gemm_tn<176>(ma, malo, mb, S, kchunks, L, Lp, has_lo, out, outb);
+      else if (N == 208) launch_gemm_tn<208>(ma, malo, mb, S, kchunks, L, Lp, has_lo, out, outb);
+      else if (N == 240) launch_gemm_tn<240>(ma, malo, mb, S, kchunks, L, Lp, has_lo, out, outb);
       else fail(KRP_EUNSUPPORTED, "unsupported MMA width %d", N);
   }
 }

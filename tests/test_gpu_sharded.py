@@ -110,8 +110,11 @@ def test_core_truncate_and_residual_entry_points(ctx, spec):
     d2, x2 = K.krp_residual(ctx, xd, spec.dims, ranks, core_r, facs_r)
     # ||X||^2: FP32 partial sums of at most 64 squares per thread, then FP64
     assert abs(x2 - float(np.sum(x32.astype(np.float64) ** 2))) <= 64 * 2.0 ** -24 * x2
-    assert abs(math.sqrt(d2 / x2) - res_t["rel_residual"]) <= 1e-5 * res_t["rel_residual"] + 1e-9
-    assert abs(math.sqrt(d2 / x2) - TK.rel_error(x32, g_o, q_o)) <= 1e-5 * TK.rel_error(x32, g_o, q_o) + 1e-6
+    # | ||X - A|| - ||X - B|| | <= ||A - B||: the relative residuals agree to
+    # the bounds on the reconstructions above (1e-6 against the pipeline run,
+    # whose FP32 atomics order differs; 1e-5 against the oracle)
+    assert abs(math.sqrt(d2 / x2) - res_t["rel_residual"]) <= 1e-6
+    assert abs(math.sqrt(d2 / x2) - TK.rel_error(x32, g_o, q_o)) <= 1e-5
 
 
 @pytest.mark.parametrize("spec", SPECS, ids=[s.name for s in SPECS])

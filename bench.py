@@ -413,10 +413,10 @@ def c4_run(ctx, dev, stream, args):
 
 
 # DRAM traffic (read + write bytes) of one big launch of the dominant kernel
-# at 1024^3: ncu at 512^3 measured 537.0 MB read (X once) and 42.9 MB write
+# at 1024^3: ncu at 512^3 measured 537.0 MB read (X once) and 43.0 MB write
 # (the (N/n1) x l output); X scales x8 and the output x4 to 1024^3
 # (profiles/ncu_f32_kernels_512cubed.md).  Set to None if the kernel changes.
-TTM48_TRAFFIC_PER_BIG_LAUNCH = 537.0e6 * 8 + 42.9e6 * 4
+TTM48_TRAFFIC_PER_BIG_LAUNCH = 537.0e6 * 8 + 43.0e6 * 4
 
 
 def trace_roofline(spec, f32, peaks, args):

@@ -770,21 +770,22 @@ __global__ void __launch_bounds__(256, 2)
 // Thread (g = tid >> 3, h = tid & 7) owns rows g + (BMS/8) j (j < 8) and the
 // strided columns h + 8 c (c < NP/8), so that both operand reads below are
 // conflict-free 16-byte shared-memory loads.  Chunks of GK contraction indices
-// are staged [s][i] and [k][i] (pitch GP floats) by an NS-stage cp.async ring
-// with one block barrier per chunk.  Each copy slot of a thread is fixed, so
-// its global address is computed once and advanced by GK per chunk.
+// (16 or 32) are staged [s][i] and [k][i] (pitch GK + 4 floats: consecutive
+// rows start 16 bytes apart in the banks) by an NS-stage cp.async ring with
+// one block barrier per chunk.  Each copy slot of a thread is fixed, so its
+// global address is computed once and advanced by GK per chunk.
 // PAIR: each accumulator is a pair of partial sums over the even and the odd
 // contraction indices, updated by the paired FP32 FMA (fma.rn.f32x2): both
 // operands come as natural register pairs of the 16-byte loads, and one
 // instruction does two FMAs, leaving issue slots for the loads and barriers
 // (the pair is summed once at the end).
-constexpr int GK = 16, GP = 20;
-template <int NP, int BMS, int NS, int MINB, bool PAIR>
+template <int NP, int BMS, int NS, int MINB, bool PAIR, int GK>
 __global__ void __launch_bounds__(BMS, MINB)
     gemm_tn_tile_kernel(const float* __restrict__ A, int64_t lda, int64_t S, int K,
                         const float* __restrict__ F, int64_t ldf, int L, float* __restrict__ out,
                         int64_t ldo, int accumulate) {
-  constexpr int NT = BMS, RG = BMS / 8, CPT = NP / 8;
+  constexpr int NT = BMS, RG = BMS / 8, CPT = NP / 8, GP = GK + 4, CPR = GK / 4;
+  static_assert(GK == 16 || GK == 32, "chunk width");
   extern __shared__ __align__(16) float gts[];
   float(*As)[BMS][GP] = reinterpret_cast<float(*)[BMS][GP]>(gts);
   float(*Fs)[NP][GP] = reinterpret_cast<float(*)[NP][GP]>(gts + NS * BMS * GP);
@@ -803,24 +804,24 @@ __global__ void __launch_bounds__(BMS, MINB)
         acc[j][c] = 0.f;
     }
   const int nchunks = (K + GK - 1) / GK;
-  constexpr int AV = BMS * (GK / 4) / NT;
-  constexpr int FV = (NP * (GK / 4) + NT - 1) / NT;
+  constexpr int AV = BMS * CPR / NT;
+  constexpr int FV = (NP * CPR + NT - 1) / NT;
   const float* pa[AV];
   bool oka[AV];
 #pragma unroll
   for (int v = 0; v < AV; ++v) {
     const int q = tid + NT * v;
-    const int64_t s = s0 + (q >> 2);
+    const int64_t s = s0 + (q / CPR);
     oka[v] = s < S;
-    pa[v] = A + 4 * (q & 3) + lda * (oka[v] ? s : 0);
+    pa[v] = A + 4 * (q % CPR) + lda * (oka[v] ? s : 0);
   }
   const float* pf[FV];
   bool okf[FV];
 #pragma unroll
   for (int v = 0; v < FV; ++v) {
     const int q = tid + NT * v;
-    okf[v] = (q < NP * (GK / 4)) && (k0 + (q >> 2) < L);
-    pf[v] = F + 4 * (q & 3) + ldf * (okf[v] ? (k0 + (q >> 2)) : 0);
+    okf[v] = (q < NP * CPR) && (k0 + (q / CPR) < L);
+    pf[v] = F + 4 * (q % CPR) + ldf * (okf[v] ? (k0 + (q / CPR)) : 0);
   }
   auto issue = [&](int chunk) {
     if (chunk < nchunks) {
@@ -829,15 +830,15 @@ __global__ void __launch_bounds__(BMS, MINB)
 #pragma unroll
       for (int v = 0; v < AV; ++v) {
         const int q = tid + NT * v;
-        const bool ok = oka[v] && (kc + 4 * (q & 3) < K);
-        cp_async16(&As[stage][q >> 2][4 * (q & 3)], ok ? (const void*)(pa[v] + kc) : (const void*)A, ok);
+        const bool ok = oka[v] && (kc + 4 * (q % CPR) < K);
+        cp_async16(&As[stage][q / CPR][4 * (q % CPR)], ok ? (const void*)(pa[v] + kc) : (const void*)A, ok);
       }
 #pragma unroll
       for (int v = 0; v < FV; ++v) {
         const int q = tid + NT * v;
-        if (q < NP * (GK / 4)) {
-          const bool ok = okf[v] && (kc + 4 * (q & 3) < K);
-          cp_async16(&Fs[stage][q >> 2][4 * (q & 3)], ok ? (const void*)(pf[v] + kc) : (const void*)F, ok);
+        if (q < NP * CPR) {
+          const bool ok = okf[v] && (kc + 4 * (q % CPR) < K);
+          cp_async16(&Fs[stage][q / CPR][4 * (q % CPR)], ok ? (const void*)(pf[v] + kc) : (const void*)F, ok);
         }
       }
     }
@@ -1052,14 +1053,14 @@ __global__ void krp_weights_padded_kernel(const RadixDev R, int64_t T, int L, in
 }  // namespace
 
 namespace {
-template <int NP, int MINB, int NS, bool PAIR>
+template <int NP, int MINB, int NS, bool PAIR, int GK>
 void gemm_tn_tile_launch(const float* A, int64_t lda, int64_t S, int K, const float* F, int64_t ldf,
                          int L, float* out, int64_t ldo, bool accumulate) {
   constexpr int BMS = 128;
   dim3 grid((unsigned)((S + BMS - 1) / BMS), (unsigned)((L + NP - 1) / NP));
-  const size_t smem = sizeof(float) * NS * (BMS + NP) * GP;
-  set_dyn_smem(gemm_tn_tile_kernel<NP, BMS, NS, MINB, PAIR>, smem);
-  gemm_tn_tile_kernel<NP, BMS, NS, MINB, PAIR><<<grid, BMS, smem, stream()>>>(
+  const size_t smem = sizeof(float) * NS * (BMS + NP) * (GK + 4);
+  set_dyn_smem(gemm_tn_tile_kernel<NP, BMS, NS, MINB, PAIR, GK>, smem);
+  gemm_tn_tile_kernel<NP, BMS, NS, MINB, PAIR, GK><<<grid, BMS, smem, stream()>>>(
       A, lda, S, K, F, ldf, L, out, ldo, accumulate ? 1 : 0);
   check_launch(NP == 16 ? "gemm_tn_tile<16>" : NP == 32 ? "gemm_tn_tile<32>"
                : NP == 48 ? "gemm_tn_tile<48>" : "gemm_tn_tile<64>");
@@ -1106,16 +1107,18 @@ void gemm_tn_f32(const float* A, int64_t lda, int64_t S, int K, const float* F, 
                    ((reinterpret_cast<uintptr_t>(A) & 15) == 0) &&
                    ((reinterpret_cast<uintptr_t>(F) & 15) == 0);
   if (vec) {
-    // paired FMAs with six stages up to 48 columns (+4% at 48 on 1024^3);
-    // 64 columns keep single FMAs (the pairs would not fit the registers)
+    // paired FMAs over 32-wide chunks in three stages up to 48 columns (1024^3
+    // launch: 47.4 TFLOP/s single FMAs, 49.6 paired, 51.7 paired with 32-wide
+    // chunks); 64 columns keep single FMAs (the pairs would not fit the
+    // registers)
     if (L <= 16)
-      gemm_tn_tile_launch<16, 2, 6, true>(A, lda, S, K, F, ldf, L, out, ldo, accumulate);
+      gemm_tn_tile_launch<16, 2, 3, true, 32>(A, lda, S, K, F, ldf, L, out, ldo, accumulate);
     else if (L <= 32)
-      gemm_tn_tile_launch<32, 2, 6, true>(A, lda, S, K, F, ldf, L, out, ldo, accumulate);
+      gemm_tn_tile_launch<32, 2, 3, true, 32>(A, lda, S, K, F, ldf, L, out, ldo, accumulate);
     else if (L <= 48)
-      gemm_tn_tile_launch<48, 2, 6, true>(A, lda, S, K, F, ldf, L, out, ldo, accumulate);
+      gemm_tn_tile_launch<48, 2, 3, true, 32>(A, lda, S, K, F, ldf, L, out, ldo, accumulate);
     else
-      gemm_tn_tile_launch<64, 2, 4, false>(A, lda, S, K, F, ldf, L, out, ldo, accumulate);
+      gemm_tn_tile_launch<64, 2, 4, false, 16>(A, lda, S, K, F, ldf, L, out, ldo, accumulate);
     return;
   }
   if (L <= 16)

@@ -911,12 +911,12 @@ __global__ void __launch_bounds__(BMS, MINB)
 // block barrier per chunk.  Chunks are numbered c = t * cps + b (the b-th block
 // of BK rows of slab t); CTA (x, z) takes rows x and chunks [z per, (z+1) per).
 constexpr int MBM = 256, MBK = 16, MNS = 4;
-template <int NP>
+template <int NP, int BK = MBK, int NS = MNS>
 __global__ void __launch_bounds__(MBM, 2)
     krp_slab_mttkrp_kernel(const float* __restrict__ X, int64_t n1, int64_t n2, int64_t T,
                            const float* __restrict__ O2T, const float* __restrict__ wT,
                            float* __restrict__ Y, int L, int64_t per) {
-  constexpr int BM = MBM, BK = MBK, NS = MNS, NT = MBM, CPT = NP / 8;
+  constexpr int BM = MBM, NT = MBM, CPT = NP / 8;
   static_assert(CPT % 2 == 0, "columns per thread must be even");
   extern __shared__ __align__(16) float kss[];
   float(*As)[BK][BM] = reinterpret_cast<float(*)[BK][BM]>(kss);
@@ -961,21 +961,34 @@ __global__ void __launch_bounds__(MBM, 2)
     cp_commit();
   };
   constexpr int QPR = NP / 4;
-  static_assert(BK * QPR <= NT, "one quad of B per thread");
-  const int brow = tid / QPR, bq = tid % QPR;
-  const bool b_act = tid < BK * QPR;
-  float4 bv;
+  constexpr int NQ = (BK * QPR + NT - 1) / NT;  // quads of B per thread (1 or 2)
+  static_assert(NQ <= 2, "at most two quads of B per thread");
+  int brow[NQ], bq[NQ];
+  bool b_act[NQ];
+#pragma unroll
+  for (int u = 0; u < NQ; ++u) {
+    const int idx = tid + NT * u;
+    brow[u] = idx / QPR;
+    bq[u] = idx % QPR;
+    b_act[u] = idx < BK * QPR;
+  }
+  float4 bv[NQ];
   auto loadB = [&](int64_t c) {
-    bv = make_float4(0.f, 0.f, 0.f, 0.f);
-    if (b_act && c < ce && rB + brow < n2) {
-      const float4 o = __ldg(reinterpret_cast<const float4*>(O2T + (rB + brow) * NP) + bq);
-      const float4 w = __ldg(reinterpret_cast<const float4*>(wT + tB * NP) + bq);
-      bv = make_float4(o.x * w.x, o.y * w.y, o.z * w.z, o.w * w.w);
+#pragma unroll
+    for (int u = 0; u < NQ; ++u) {
+      bv[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (b_act[u] && c < ce && rB + brow[u] < n2) {
+        const float4 o = __ldg(reinterpret_cast<const float4*>(O2T + (rB + brow[u]) * NP) + bq[u]);
+        const float4 w = __ldg(reinterpret_cast<const float4*>(wT + tB * NP) + bq[u]);
+        bv[u] = make_float4(o.x * w.x, o.y * w.y, o.z * w.z, o.w * w.w);
+      }
     }
     if (c < ce) advance(tB, rB);
   };
   auto storeB = [&](int64_t c) {
-    if (b_act) *reinterpret_cast<float4*>(&Bs[(int)((c - cb) & 1)][brow][4 * bq]) = bv;
+#pragma unroll
+    for (int u = 0; u < NQ; ++u)
+      if (b_act[u]) *reinterpret_cast<float4*>(&Bs[(int)((c - cb) & 1)][brow[u]][4 * bq[u]]) = bv[u];
   };
 #pragma unroll
   for (int p = 0; p < NS - 1; ++p) issueA(cb + p);
@@ -1066,7 +1079,7 @@ void gemm_tn_tile_launch(const float* A, int64_t lda, int64_t S, int K, const fl
                : NP == 48 ? "gemm_tn_tile<48>" : "gemm_tn_tile<64>");
 }
 
-template <int NP>
+template <int NP, int BK = MBK, int NS = MNS>
 void krp_slab_mttkrp_launch(const float* X, int64_t n1, int64_t n2, int64_t T, const float* O2,
                             const RadixDev& W, int L, float* Y) {
   float* O2T = current()->ws.take<float>((size_t)n2 * NP);
@@ -1076,14 +1089,14 @@ void krp_slab_mttkrp_launch(const float* X, int64_t n1, int64_t n2, int64_t T, c
   krp_weights_padded_kernel<<<grid_for(T * NP, 256), 256, 0, stream()>>>(W, T, L, NP, wT);
   check_launch("krp_weights_padded");
   const int mt = (int)((n1 + MBM - 1) / MBM);
-  const int64_t cps = (n2 + MBK - 1) / MBK;
+  const int64_t cps = (n2 + BK - 1) / BK;
   const int64_t total = T * cps;
   const int64_t want = std::max<int64_t>(1, (int64_t)2 * current()->num_sms / mt);
   const int64_t per = (total + want - 1) / want;
   const int64_t splits = (total + per - 1) / per;
-  const size_t smem = sizeof(float) * (MNS * MBK * MBM + 2 * MBK * NP);
-  set_dyn_smem(krp_slab_mttkrp_kernel<NP>, smem);
-  krp_slab_mttkrp_kernel<NP><<<dim3(mt, (unsigned)splits), MBM, smem, stream()>>>(
+  const size_t smem = sizeof(float) * (NS * BK * MBM + 2 * BK * NP);
+  set_dyn_smem(krp_slab_mttkrp_kernel<NP, BK, NS>, smem);
+  krp_slab_mttkrp_kernel<NP, BK, NS><<<dim3(mt, (unsigned)splits), MBM, smem, stream()>>>(
       X, n1, n2, T, O2T, wT, Y, L, per);
   check_launch("krp_slab_mttkrp_f32");
 }

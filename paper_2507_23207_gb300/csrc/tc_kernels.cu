@@ -526,6 +526,45 @@ __global__ void __launch_bounds__(kThreads, 1)
 // Epilogue per t: Y2[i2, k] += D1 w[t, k] (registers across t) and
 // C[t, k] += sum_i2 Omega2[i2, k] D1[i2, k]; at the end D2 -> Y1.
 // For d = 3, C is Y3 itself.
+// Warp reduce-scatter of CNT per-lane values: on return the warp's sums over
+// its 32 lanes have been added to dst[t + T * (kbase + j)] (j < CNT, skipping
+// kbase + j >= L).  Each halving step exchanges half of the values with the
+// lane BIT apart (CNT/2 shuffles) and keeps the half selected by that lane
+// bit; the bits left when CNT is odd are summed by a plain butterfly.  For
+// 16 values: 8 + 4 + 2 + 1 + 1 = 16 shuffles instead of 16 x 5, and the
+// atomics are spread over the lanes.
+template <int CNT, int BIT>
+struct WarpReduceScatter {
+  __device__ __forceinline__ static void run(float* v, int lane, int kbase, float* dst, int64_t t,
+                                             int64_t T, int L) {
+    if constexpr (BIT > 0 && CNT % 2 == 0) {
+      constexpr int H = CNT / 2;
+      const bool hb = (lane & BIT) != 0;
+#pragma unroll
+      for (int j = 0; j < H; ++j) {
+        const float keep = hb ? v[H + j] : v[j];
+        const float send = hb ? v[j] : v[H + j];
+        v[j] = keep + __shfl_xor_sync(0xffffffffu, send, BIT);
+      }
+      WarpReduceScatter<H, BIT / 2>::run(v, lane, kbase + (hb ? H : 0), dst, t, T, L);
+    } else {
+#pragma unroll
+      for (int j = 0; j < CNT; ++j) {
+        float x = v[j];
+#pragma unroll
+        for (int b = BIT; b > 0; b >>= 1) x += __shfl_xor_sync(0xffffffffu, x, b);
+        v[j] = x;
+      }
+      constexpr int kMask = BIT > 0 ? 2 * BIT - 1 : 0;  // the lane bits still shared
+      if ((lane & kMask) == 0) {
+#pragma unroll
+        for (int j = 0; j < CNT; ++j)
+          if (kbase + j < L) atomicAdd(dst + t + T * (kbase + j), v[j]);
+      }
+    }
+  }
+};
+
 // X stages of the fused tree: four while they fit beside the two B2 buffers
 __host__ __device__ constexpr int tree_stages(int N) { return N <= 48 ? 4 : 3; }
 
@@ -740,17 +779,15 @@ __global__ void __launch_bounds__(320, 1)
       for (int c0 = 0; c0 < N; c0 += 16) {
         float v[16];
         tmem_ld16(base + c0, v);
+        float cp[16];
 #pragma unroll
         for (int j = 0; j < 16; ++j) {
           const int k = c0 + j;
-          const float wk = wsm[acc][k];
-          y2[k] = fmaf(v[j], wk, y2[k]);
-          float cp = v[j] * o2[k];
-#pragma unroll
-          for (int o = 16; o > 0; o >>= 1) cp += __shfl_xor_sync(0xffffffffu, cp, o);
-          // each warp adds its 32-row partial of C[t, k] (no cross-warp barrier)
-          if (lane == 0 && k < P.L) atomicAdd(P.C + t + P.T * k, cp);
+          y2[k] = fmaf(v[j], wsm[acc][k], y2[k]);
+          cp[j] = v[j] * o2[k];
         }
+        // each warp adds its 32-row partial of C[t, k] (no cross-warp barrier)
+        WarpReduceScatter<16, 16>::run(cp, lane, c0, P.C, t, P.T, P.L);
       }
       tc_fence_before();
       __syncwarp();

@@ -64,6 +64,13 @@ SPECS = [
     # n_1 % 4 == 0 with a 4-row ragged 128-row block, c % 4 == 0 and
     # S = 21 * 13 not a multiple of 64: the persistent tiled residual path
     TuckerSpec("tiled", (132, 21, 13), (4, 3, 3), 1e-3, None, 31, (4, 3, 3), (8, 7, 7)),
+    # a matrix (d = 2) and a sketch as wide as its mode (l_i = n_i).  The
+    # truncated projectors are compared to 1e-5, and their sensitivity to
+    # FP32 rounding grows as 1 / (sigma_r - sigma_r+1): the matrix's data seed
+    # gives sigma_3 / sigma_1 = 0.63 (seed 37 gave 0.009, where the oracle
+    # itself moves the projectors by ~4e-5 under FP32-level perturbations)
+    TuckerSpec("matrix", (50, 40), (3, 3), 1e-3, None, 40, (3, 3), (6, 6)),
+    TuckerSpec("l_eq_n", (8, 8, 8), (4, 4, 4), 1e-3, None, 39, (4, 4, 4), (8, 8, 8)),
 ]
 
 
@@ -149,3 +156,28 @@ def test_tucker_invalid_arguments(ctx):
         run_gpu(ctx, x32, (8, 8, 8), (0, 2, 2), 1, 0, 0)
     with pytest.raises(K.KrpError):
         run_gpu(ctx, x32, (8, 8, 8), (2, 2, 2), 1, 0, 0x100)
+
+
+@pytest.mark.parametrize("memo", [False, True])
+def test_zero_tensor(ctx, memo):
+    """X = 0: every sketch is zero, so every QR pivot collapses and the
+    columns are refilled; the factors must still be orthonormal, the core and
+    the reconstruction zero, and the relative residual defined (0)."""
+    import torch
+    import paper_2507_23207_gb300 as K
+    dims, ranks, p = (16, 12, 10), (2, 2, 2), 2
+    ells = [r + p for r in ranks]
+    xd = torch.zeros(int(np.prod(dims)), dtype=torch.float32, device=dev())
+    for trunc in (False, True):
+        out = list(ranks) if trunc else ells
+        core = torch.empty(int(np.prod(out)), dtype=torch.float32, device=dev())
+        facs = [torch.empty(n * o, dtype=torch.float64, device=dev()) for n, o in zip(dims, out)]
+        flags = (K.KRP_MEMO if memo else 0) | K.KRP_RESIDUAL | (K.KRP_TRUNCATE if trunc else 0)
+        res = K.krp_tucker_rhosvd(ctx, xd, dims, list(ranks), p, 0, flags, core, facs)
+        torch.cuda.synchronize()
+        for f, n, o in zip(facs, dims, out):
+            q = f.cpu().numpy().reshape(o, n).T
+            assert np.all(np.isfinite(q))
+            assert np.linalg.norm(q.T @ q - np.eye(o)) <= 1e-12
+        assert float(core.abs().max()) == 0.0
+        assert res["rel_residual"] == 0.0 and res["x_norm"] == 0.0

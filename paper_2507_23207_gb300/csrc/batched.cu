@@ -393,47 +393,85 @@ __global__ void __launch_bounds__(kBT, 2)
   }
 }
 
-// G[ab + l1 l2 c] = sum_t C_t[ab] Q3[t, c]; one CTA per tensor
+// G[ab + l1 l2 c] = sum_t C_t[ab] Q3[t, c]; one CTA per tensor.  Q3 goes to
+// shared memory in FP32 once (rows of kMaxEll, zero-padded); a thread owns
+// one ab and all l3 outputs, so every C_t[ab] is loaded once (coalesced over
+// ab) and multiplied by a broadcast row of Q3.
 __global__ void batch_core_finish_kernel(const TbItem* __restrict__ items) {
+  extern __shared__ __align__(16) float q3s[];  // n3 x kMaxEll
   const TbItem& it = items[blockIdx.x];
   const int l12 = it.l[0] * it.l[1], l3 = it.l[2], n3 = it.n[2];
-  for (int e = threadIdx.x; e < l12 * l3; e += blockDim.x) {
-    const int ab = e % l12, c = e / l12;
-    const double* q3 = it.Q[2] + (int64_t)n3 * c;
-    float acc = 0.f;
-    for (int t = 0; t < n3; ++t) acc = fmaf(it.C[(int64_t)t * l12 + ab], (float)q3[t], acc);
-    it.G[e] = acc;
+  for (int e = threadIdx.x; e < n3 * kMaxEll; e += blockDim.x) {
+    const int t = e / kMaxEll, c = e % kMaxEll;
+    q3s[e] = c < l3 ? (float)it.Q[2][t + (int64_t)n3 * c] : 0.f;
+  }
+  __syncthreads();
+  for (int ab = threadIdx.x; ab < l12; ab += blockDim.x) {
+    float acc[kMaxEll];
+#pragma unroll
+    for (int c = 0; c < kMaxEll; ++c) acc[c] = 0.f;
+    const float* cp = it.C + ab;
+    for (int t = 0; t < n3; ++t) {
+      const float cv = cp[(int64_t)t * l12];
+      const float* q = q3s + t * kMaxEll;
+#pragma unroll
+      for (int cq = 0; cq < kMaxEll / 4; ++cq) {
+        if (4 * cq < l3) {
+          const float4 v = *reinterpret_cast<const float4*>(&q[4 * cq]);
+          acc[4 * cq + 0] = fmaf(cv, v.x, acc[4 * cq + 0]);
+          acc[4 * cq + 1] = fmaf(cv, v.y, acc[4 * cq + 1]);
+          acc[4 * cq + 2] = fmaf(cv, v.z, acc[4 * cq + 2]);
+          acc[4 * cq + 3] = fmaf(cv, v.w, acc[4 * cq + 3]);
+        }
+      }
+    }
+#pragma unroll
+    for (int c = 0; c < kMaxEll; ++c)
+      if (c < l3) it.G[ab + (int64_t)l12 * c] = acc[c];
   }
 }
 
 // ------------------------------------------------------------ truncation ----
-// Gram of unfolding `mode` of the FP32 core, FP64 accumulation; grid (count, 3)
+// Gram of unfolding `mode` of the FP32 core, FP64 accumulation; grid (count, 3).
+// The core is converted to ST once in shared memory (ST = double when it
+// fits, so no per-term conversion runs on the FP64 pipe); a thread owns one
+// pair p <= q and walks the unfolding's columns as two nested loops over the
+// other two modes (no index division).
+template <class ST>
 __global__ void batch_gram_kernel(const TbItem* __restrict__ items) {
-  extern __shared__ float gsh[];
+  extern __shared__ __align__(16) unsigned char gram_raw[];
+  ST* gsh = reinterpret_cast<ST*>(gram_raw);
   const TbItem& it = items[blockIdx.x];
   const int mode = blockIdx.y;
   const int l0 = it.l[0], l1 = it.l[1], l2 = it.l[2];
   const int L = l0 * l1 * l2;
-  for (int e = threadIdx.x; e < L; e += blockDim.x) gsh[e] = it.G[e];
+  for (int e = threadIdx.x; e < L; e += blockDim.x) gsh[e] = (ST)it.G[e];
   __syncthreads();
-  const int lmode = it.l[mode];
-  const int ncol = L / lmode;
+  const int lm = it.l[mode];
   // element (x0, x1, x2) at x0 + l0 x1 + l0 l1 x2; the unfolding's column
-  // index runs over the other two in order
+  // index runs over the other two modes, the first one fastest
   const int stride = mode == 0 ? 1 : (mode == 1 ? l0 : l0 * l1);
-  const int la = mode == 0 ? l1 : l0;             // first other side
-  const int sa = mode == 0 ? l0 : 1;              // its stride
-  const int sb = mode == 2 ? l0 : l0 * l1;        // second other side's stride
-  for (int pq = threadIdx.x; pq < lmode * lmode; pq += blockDim.x) {
-    const int p = pq % lmode, q = pq / lmode;
-    if (p > q) continue;
+  const int na = mode == 0 ? l1 : l0, sa = mode == 0 ? l0 : 1;
+  const int nb = mode == 2 ? l1 : l2, sb = mode == 2 ? l0 : l0 * l1;
+  const int npairs = lm * (lm + 1) / 2;
+  for (int pq = threadIdx.x; pq < npairs; pq += blockDim.x) {
+    // pq = q (q + 1) / 2 + p with p <= q
+    int q = (int)((sqrtf(8.f * pq + 1.f) - 1.f) * 0.5f);
+    while (q * (q + 1) / 2 > pq) --q;
+    while ((q + 1) * (q + 2) / 2 <= pq) ++q;
+    const int p = pq - q * (q + 1) / 2;
+    const ST* gp = gsh + p * stride;
+    const ST* gq = gsh + q * stride;
     double s = 0.0;
-    for (int col = 0; col < ncol; ++col) {
-      const int off = (col % la) * sa + (col / la) * sb;
-      s = fma((double)gsh[off + p * stride], (double)gsh[off + q * stride], s);
+    for (int y = 0; y < nb; ++y) {
+      const int base = y * sb;
+      for (int x = 0; x < na; ++x) {
+        const int off = base + x * sa;
+        s = fma((double)gp[off], (double)gq[off], s);
+      }
     }
-    it.S[mode][p + lmode * q] = s;
-    it.S[mode][q + lmode * p] = s;
+    it.S[mode][p + lm * q] = s;
+    it.S[mode][q + lm * p] = s;
   }
 }
 
@@ -487,119 +525,124 @@ __global__ void batch_trunc_apply_kernel(const TbItem* __restrict__ items, int t
 // -------------------------------------------------------------- residual ----
 // M_t[a + r0 b] = sum_c Gt[a + r0 b + r0 r1 c] F3[t, c] for every slab t of a
 // tensor (one CTA per tensor), so the residual kernel reads each M_t as one
-// contiguous block.
+// contiguous block.  F3 is converted to FP32 once, in shared memory.
 __global__ void batch_resid_prep_kernel(const TbItem* __restrict__ items) {
+  extern __shared__ float f3s[];  // n3 x r2, row-major
   const TbItem& it = items[blockIdx.x];
   const int r01 = it.r[0] * it.r[1], r2 = it.r[2], n3 = it.n[2];
+  for (int e = threadIdx.x; e < n3 * r2; e += blockDim.x) {
+    const int t = e % n3, c = e / n3;
+    f3s[t * r2 + c] = (float)it.fac_out[2][e];
+  }
+  __syncthreads();
   for (int e = threadIdx.x; e < n3 * r01; e += blockDim.x) {
     const int t = e / r01, ab = e % r01;
     float s = 0.f;
-    for (int c = 0; c < r2; ++c)
-      s = fmaf(it.core_out[ab + r01 * c], (float)it.fac_out[2][t + (int64_t)n3 * c], s);
+    for (int c = 0; c < r2; ++c) s = fmaf(it.core_out[ab + r01 * c], f3s[t * r2 + c], s);
     it.M[e] = s;
   }
 }
 
-// ||X_t - F1 M_t F2^T||^2.  Shared memory (floats): Xs[kJB][pitch],
-// F1s[n1max][Rp], F2s[Rp][n2max], Ms[Rp * Rp], Ps[Rp][n1max].
-struct ResidSmem {
-  float *Xs, *F1s, *F2s, *Ms, *Ps;
-  int pitch, Rp, n1max, n2max;
-};
+// ||X_t - F1 M_t F2^T||^2 and ||X_t||^2 over the slabs of a tile.  A warp
+// owns one unit (slab t, block of 32 rows i; lane = row): it forms
+// P[i, :] = F1[i, :] M_t in registers (r1 values, padded to 4 RQ), then walks
+// the slab's columns j reading X[i, j, t] straight from global memory
+// (coalesced over the lanes, 16 columns in flight, 8 for r1 > 16) with
+// x_hat[i, j] = P[i, :] . F2[j, :], the F2 rows broadcast from shared memory.
+// The warps of a CTA share the tile's F1, F2 and M_t in shared memory and
+// meet at no barrier inside the tile.  Per-unit sums are FP32 (at most n2
+// terms per lane), then FP64.
+// Shared memory (floats): F1s[r0][32 RB] (zero for i >= n1), F2s[n2][4 RQ],
+// Ms[slabs][r0][4 RQ] (zero for b >= r1).
+constexpr int kResidUnits = 16;  // target units (slab x row block) per tile
 
-template <class XT, int R>
-__device__ void resid_tile(const TbItem& it, const TbTile& tile, const ResidSmem& S, double& dd,
+template <class XT, int RQ>
+__device__ void resid_tile(const TbItem& it, const TbTile& tile, float* sm, double& dd,
                            double& xx) {
-  const int tid = threadIdx.x, ig = tid >> 3, jq = tid & 7;
-  const int n1 = it.n[0], n2 = it.n[1];
-  const int r0 = it.r[0], r1 = it.r[1];
-  const int pitch = S.pitch, Rp = S.Rp, n1max = S.n1max, n2max = S.n2max;
-  const XT* X = static_cast<const XT*>(it.X);
-  for (int e = tid; e < n1 * r0; e += kBT) {
-    const int i = e % n1, a = e / n1;
-    S.F1s[i * Rp + a] = (float)it.fac_out[0][e];
+  constexpr int R1P = 4 * RQ;
+  constexpr int kRCols = RQ <= 4 ? 16 : 8;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int n1 = it.n[0], n2 = it.n[1], r0 = it.r[0], r1 = it.r[1];
+  const int RB = (n1 + 31) >> 5, pitch = 32 * RB;
+  const int nt = tile.t1 - tile.t0;
+  float* F1s = sm;
+  float* F2s = F1s + r0 * pitch;
+  float* Ms = F2s + n2 * R1P;
+  const double* f1 = it.fac_out[0];
+  const double* f2 = it.fac_out[1];
+  for (int e = tid; e < r0 * pitch; e += kBT) {
+    const int a = e / pitch, i = e - a * pitch;
+    F1s[e] = i < n1 ? (float)f1[i + (int64_t)n1 * a] : 0.f;
   }
-  for (int e = tid; e < n2 * r1; e += kBT) {
+  for (int e = tid; e < n2 * R1P; e += kBT) {
     const int j = e % n2, b = e / n2;
-    S.F2s[b * n2max + j] = (float)it.fac_out[1][e];
+    F2s[j * R1P + b] = b < r1 ? (float)f2[j + (int64_t)n2 * b] : 0.f;
   }
-  const int nch = (n2 + kJB - 1) / kJB;
-  const int nq = (tile.t1 - tile.t0) * nch;
-  ChunkRegs<R> cr;
-  chunk_load<XT, R>(cr, X, n1, n2, tile.t0, 0);
-  float d2 = 0.f, x2 = 0.f;
-  for (int q = 0; q < nq; ++q) {
-    const int t = tile.t0 + q / nch, ch = q % nch, j0 = ch * kJB;
-    __syncthreads();
-    if (ch == 0) {
-      const float* Mt = it.M + (int64_t)t * r0 * r1;
-      for (int e = tid; e < r0 * r1; e += kBT) S.Ms[e] = Mt[e];
-      __syncthreads();
-      for (int e = tid; e < n1 * r1; e += kBT) {
-        const int i = e % n1, b = e / n1;
-        float sm = 0.f;
-        for (int a = 0; a < r0; ++a) sm = fmaf(S.F1s[i * Rp + a], S.Ms[a + r0 * b], sm);
-        S.Ps[b * n1max + i] = sm;
+  for (int e = tid; e < nt * r0 * R1P; e += kBT) {
+    const int b = e % R1P, rest = e / R1P, a = rest % r0, tt = rest / r0;
+    Ms[e] = b < r1 ? it.M[(int64_t)(tile.t0 + tt) * r0 * r1 + a + r0 * b] : 0.f;
+  }
+  __syncthreads();
+  const XT* X = static_cast<const XT*>(it.X);
+  for (int u = warp; u < nt * RB; u += kBT / 32) {
+    const int tt = u / RB, rb = u - tt * RB;
+    const int i = 32 * rb + lane;
+    const bool valid = i < n1;
+    float P[R1P];
+#pragma unroll
+    for (int b = 0; b < R1P; ++b) P[b] = 0.f;
+    const float* mt = Ms + tt * r0 * R1P;
+    for (int a = 0; a < r0; ++a) {
+      const float f = F1s[a * pitch + i];
+#pragma unroll
+      for (int q = 0; q < RQ; ++q) {
+        const float4 m = *reinterpret_cast<const float4*>(&mt[a * R1P + 4 * q]);
+        P[4 * q + 0] = fmaf(f, m.x, P[4 * q + 0]);
+        P[4 * q + 1] = fmaf(f, m.y, P[4 * q + 1]);
+        P[4 * q + 2] = fmaf(f, m.z, P[4 * q + 2]);
+        P[4 * q + 3] = fmaf(f, m.w, P[4 * q + 3]);
       }
     }
-    chunk_store<R>(cr, S.Xs, pitch);
-    __syncthreads();
-    if (q + 1 < nq) chunk_load<XT, R>(cr, X, n1, n2, tile.t0 + (q + 1) / nch, ((q + 1) % nch) * kJB);
-    // X_hat rows ig + 32u, columns j0 + jq + 8w: register tile R x 4
-    float xh[R][kJB / 8];
+    const XT* xp = X + (int64_t)n1 * n2 * (tile.t0 + tt) + (valid ? i : 0);
+    float d0 = 0.f, d1 = 0.f, s0 = 0.f, s1 = 0.f;
+    auto column = [&](float xv, int j, float& d, float& s) {
+      const float* w = F2s + j * R1P;
+      float h0 = 0.f, h1 = 0.f;
 #pragma unroll
-    for (int u = 0; u < R; ++u)
+      for (int q = 0; q < RQ; ++q) {
+        const float4 v = *reinterpret_cast<const float4*>(&w[4 * q]);
+        h0 = fmaf(P[4 * q + 0], v.x, h0);
+        h1 = fmaf(P[4 * q + 1], v.y, h1);
+        h0 = fmaf(P[4 * q + 2], v.z, h0);
+        h1 = fmaf(P[4 * q + 3], v.w, h1);
+      }
+      const float df = xv - (h0 + h1);
+      d = fmaf(df, df, d);
+      s = fmaf(xv, xv, s);
+    };
+    int j = 0;
+    for (; j + kRCols <= n2; j += kRCols) {
+      float xv[kRCols];
 #pragma unroll
-      for (int w = 0; w < kJB / 8; ++w) xh[u][w] = 0.f;
-    for (int b = 0; b < r1; ++b) {
-      float pv[R], fv[kJB / 8];
+      for (int c = 0; c < kRCols; ++c) xv[c] = valid ? ldx(xp, (int64_t)n1 * (j + c)) : 0.f;
 #pragma unroll
-      for (int u = 0; u < R; ++u) pv[u] = S.Ps[b * n1max + min(ig + 32 * u, n1max - 1)];
-#pragma unroll
-      for (int w = 0; w < kJB / 8; ++w) fv[w] = S.F2s[b * n2max + min(j0 + jq + 8 * w, n2max - 1)];
-#pragma unroll
-      for (int u = 0; u < R; ++u)
-#pragma unroll
-        for (int w = 0; w < kJB / 8; ++w) xh[u][w] = fmaf(pv[u], fv[w], xh[u][w]);
-    }
-#pragma unroll
-    for (int w = 0; w < kJB / 8; ++w) {
-      const int jl = jq + 8 * w;
-      if (j0 + jl >= n2) continue;
-#pragma unroll
-      for (int u = 0; u < R; ++u) {
-        const int i = ig + 32 * u;
-        if (i < n1) {
-          const float xv = S.Xs[jl * pitch + i];
-          const float df = xv - xh[u][w];
-          d2 = fmaf(df, df, d2);
-          x2 = fmaf(xv, xv, x2);
-        }
+      for (int c = 0; c < kRCols; c += 2) {
+        column(xv[c], j + c, d0, s0);
+        column(xv[c + 1], j + c + 1, d1, s1);
       }
     }
-    if (ch == nch - 1) {
-      dd += d2;
-      xx += x2;
-      d2 = x2 = 0.f;
-    }
+    for (; j < n2; ++j) column(valid ? ldx(xp, (int64_t)n1 * j) : 0.f, j, d0, s0);
+    dd += (double)(d0 + d1);
+    xx += (double)(s0 + s1);
   }
 }
 
-template <class XT>
-__global__ void __launch_bounds__(kBT, 2)
+// WIDE: r1 up to 32 (two CTAs per SM); otherwise r1 <= 16 (three CTAs per SM).
+template <class XT, bool WIDE>
+__global__ void __launch_bounds__(kBT, WIDE ? 2 : 3)
     batch_resid_kernel(const TbItem* __restrict__ items, const TbTile* __restrict__ tiles,
-                       int ntiles, int* counter, int pitch, int Rp, int n1max, int n2max) {
+                       int ntiles, int* counter) {
   extern __shared__ __align__(16) float bsm[];
-  ResidSmem S;
-  S.Xs = bsm;
-  S.F1s = S.Xs + kJB * pitch;
-  S.F2s = S.F1s + n1max * Rp;
-  S.Ms = S.F2s + Rp * n2max;
-  S.Ps = S.Ms + Rp * Rp;
-  S.pitch = pitch;
-  S.Rp = Rp;
-  S.n1max = n1max;
-  S.n2max = n2max;
   __shared__ int s_tile;
   __shared__ double red[2][kBT / 32];
   const int tid = threadIdx.x;
@@ -609,15 +652,21 @@ __global__ void __launch_bounds__(kBT, 2)
     const TbTile tile = tiles[ti];
     const TbItem& it = items[tile.item];
     double dd = 0.0, xx = 0.0;
-    switch ((it.n[0] + 31) >> 5) {
-      case 1: resid_tile<XT, 1>(it, tile, S, dd, xx); break;
-      case 2: resid_tile<XT, 2>(it, tile, S, dd, xx); break;
-      case 3: resid_tile<XT, 3>(it, tile, S, dd, xx); break;
-      case 4: resid_tile<XT, 4>(it, tile, S, dd, xx); break;
-      case 5: resid_tile<XT, 5>(it, tile, S, dd, xx); break;
-      case 6: resid_tile<XT, 6>(it, tile, S, dd, xx); break;
-      case 7: resid_tile<XT, 7>(it, tile, S, dd, xx); break;
-      default: resid_tile<XT, 8>(it, tile, S, dd, xx); break;
+    switch ((it.r[1] + 3) >> 2) {  // uniform over the CTA
+      case 1: resid_tile<XT, 1>(it, tile, bsm, dd, xx); break;
+      case 2: resid_tile<XT, 2>(it, tile, bsm, dd, xx); break;
+      case 3: resid_tile<XT, 3>(it, tile, bsm, dd, xx); break;
+      case 4: resid_tile<XT, 4>(it, tile, bsm, dd, xx); break;
+      default:
+        if constexpr (WIDE) {
+          switch ((it.r[1] + 3) >> 2) {
+            case 5: resid_tile<XT, 5>(it, tile, bsm, dd, xx); break;
+            case 6: resid_tile<XT, 6>(it, tile, bsm, dd, xx); break;
+            case 7: resid_tile<XT, 7>(it, tile, bsm, dd, xx); break;
+            default: resid_tile<XT, 8>(it, tile, bsm, dd, xx); break;
+          }
+        }
+        break;
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
@@ -668,6 +717,8 @@ struct TbPlan {
   TbItem* d_items = nullptr;
   TbTile* d_tiles = nullptr;
   int ntiles = 0;
+  TbTile* d_rtiles = nullptr;  // residual tiles: about kResidUnits warp units each
+  int nrtiles = 0;
   int* d_counters = nullptr;  // 3
   BatchFactorJob* d_fjobs = nullptr;
   int64_t* d_fstart = nullptr;
@@ -680,8 +731,10 @@ struct TbPlan {
   size_t y_bytes = 0;
   double* acc_begin = nullptr;
   int pitch = 0, Lp = 0, Rp = 0, n1max = 0, n1max8 = 0, n2max = 0, lmax = 0;
-  size_t sm_sketch = 0, sm_core = 0, sm_resid = 0, sm_gram = 0;
-  int grid_persist = 0;
+  size_t sm_sketch = 0, sm_core = 0, sm_resid = 0, sm_gram = 0, sm_prep = 0, sm_finish = 0;
+  bool gram_f64 = true;
+  bool resid_wide = false;  // some r_2 > 16
+  int grid_persist = 0, grid_resid = 0;
   int slabs_per_tile = 0;
   std::vector<TbItem> h_items;
   cudaGraphExec_t exec = nullptr;
@@ -740,6 +793,16 @@ void launch_sketch(const TbPlan& P) {
   check_launch("batch_sketch");
 }
 
+template <class XT>
+void launch_resid(const TbPlan& P) {
+  if (P.resid_wide)
+    batch_resid_kernel<XT, true><<<P.grid_resid, kBT, P.sm_resid, stream()>>>(
+        P.d_items, P.d_rtiles, P.nrtiles, P.d_counters + 2);
+  else
+    batch_resid_kernel<XT, false><<<P.grid_resid, kBT, P.sm_resid, stream()>>>(
+        P.d_items, P.d_rtiles, P.nrtiles, P.d_counters + 2);
+}
+
 // The whole batch, enqueued on the context stream (captured once into a graph).
 void enqueue_all(TbPlan& P, int* status) {
   const bool trunc = P.flags & KRP_TRUNCATE;
@@ -761,11 +824,14 @@ void enqueue_all(TbPlan& P, int* status) {
     batch_core_kernel<__nv_bfloat16><<<P.grid_persist, kBT, P.sm_core, stream()>>>(
         P.d_items, P.d_tiles, P.ntiles, P.d_counters + 1, P.pitch, P.Lp, P.n1max8, P.n2max);
   check_launch("batch_core");
-  batch_core_finish_kernel<<<P.count, 256, 0, stream()>>>(P.d_items);
+  batch_core_finish_kernel<<<P.count, 256, P.sm_finish, stream()>>>(P.d_items);
   check_launch("batch_core_finish");
   nk += 2;
   if (trunc) {
-    batch_gram_kernel<<<dim3(P.count, 3), 256, P.sm_gram, stream()>>>(P.d_items);
+    if (P.gram_f64)
+      batch_gram_kernel<double><<<dim3(P.count, 3), 256, P.sm_gram, stream()>>>(P.d_items);
+    else
+      batch_gram_kernel<float><<<dim3(P.count, 3), 256, P.sm_gram, stream()>>>(P.d_items);
     check_launch("batch_gram");
     eig_launch(P.d_ejobs, 3 * P.count, P.lmax, status);
     nk += 2;
@@ -774,15 +840,13 @@ void enqueue_all(TbPlan& P, int* status) {
   check_launch("batch_trunc_apply");
   ++nk;
   if (resid) {
-    batch_resid_prep_kernel<<<P.count, 256, 0, stream()>>>(P.d_items);
+    batch_resid_prep_kernel<<<P.count, 256, P.sm_prep, stream()>>>(P.d_items);
     check_launch("batch_resid_prep");
     ++nk;
     if (P.xt == KRP_F32)
-      batch_resid_kernel<float><<<P.grid_persist, kBT, P.sm_resid, stream()>>>(
-          P.d_items, P.d_tiles, P.ntiles, P.d_counters + 2, P.pitch, P.Rp, P.n1max, P.n2max);
+      launch_resid<float>(P);
     else
-      batch_resid_kernel<__nv_bfloat16><<<P.grid_persist, kBT, P.sm_resid, stream()>>>(
-          P.d_items, P.d_tiles, P.ntiles, P.d_counters + 2, P.pitch, P.Rp, P.n1max, P.n2max);
+      launch_resid<__nv_bfloat16>(P);
     check_launch("batch_resid");
     batch_resid_finish_kernel<<<(P.count + 255) / 256, 256, 0, stream()>>>(P.d_items, P.count,
                                                                           P.d_rel);
@@ -846,6 +910,7 @@ std::unique_ptr<TbPlan> build_plan(Ctx* c, krp_dtype xt, int count, const krp_tu
   add(3, 4);              // counters
   int64_t total_slabs = 0;
   for (int b = 0; b < count; ++b) total_slabs += items[b].dims[2];
+  add((size_t)total_slabs, sizeof(TbTile));
   add((size_t)total_slabs, sizeof(TbTile));
   KRP_CUDA_CHECK(cudaStreamCreateWithFlags(&P->cs, cudaStreamNonBlocking));
   KRP_CUDA_CHECK(cudaEventCreateWithFlags(&P->ev_in, cudaEventDisableTiming));
@@ -924,6 +989,7 @@ std::unique_ptr<TbPlan> build_plan(Ctx* c, krp_dtype xt, int count, const krp_tu
   P->d_rel = carve<double>(p, count);
   P->d_counters = carve<int>(p, 3);
   P->d_tiles = carve<TbTile>(p, (size_t)total_slabs);
+  P->d_rtiles = carve<TbTile>(p, (size_t)total_slabs);
   KRP_REQUIRE((size_t)(p - P->arena) <= bytes, "batch plan arena overflow");
   P->fblocks = fstart.back();
   cudaStream_t s = c->stream;
@@ -946,21 +1012,71 @@ std::unique_ptr<TbPlan> build_plan(Ctx* c, krp_dtype xt, int count, const krp_tu
                                   2 * (size_t)P->n2max * P->Lp + 2 * P->Lp);
   P->sm_core = sizeof(float) * ((size_t)kJB * P->pitch + (size_t)P->n1max8 * P->Lp +
                                 (size_t)P->n2max * P->Lp + (size_t)kJB * P->Lp);
-  P->sm_resid = sizeof(float) * ((size_t)kJB * P->pitch + (size_t)P->n1max * P->Rp +
-                                 (size_t)P->Rp * P->n2max + (size_t)P->Rp * P->Rp +
-                                 (size_t)P->Rp * P->n1max);
-  P->sm_gram = sizeof(float) * (size_t)P->lmax * P->lmax * P->lmax;
+  // residual tiles: per tensor, enough slabs for about kResidUnits warp units
+  {
+    std::vector<TbTile> rt;
+    size_t smr = 0, smp = 0;
+    for (int b = 0; b < count; ++b) {
+      const TbItem& it = P->h_items[b];
+      const int RB = (it.n[0] + 31) / 32, R1P = 4 * ((it.r[1] + 3) / 4);
+      const int spt = std::max(1, std::min(it.n[2], (kResidUnits + RB - 1) / RB));
+      for (int t0 = 0; t0 < it.n[2]; t0 += spt) rt.push_back(TbTile{b, t0, std::min(it.n[2], t0 + spt), 0});
+      smr = std::max(smr, (size_t)it.r[0] * 32 * RB + (size_t)it.n[1] * R1P + (size_t)spt * it.r[0] * R1P);
+      smp = std::max(smp, (size_t)it.n[2] * it.r[2]);
+      if (it.r[1] > 16) P->resid_wide = true;
+    }
+    std::stable_sort(rt.begin(), rt.end(), [&](const TbTile& x, const TbTile& y) {
+      const TbItem& a = P->h_items[x.item];
+      const TbItem& c = P->h_items[y.item];
+      return (int64_t)a.n[0] * a.n[1] * (x.t1 - x.t0) > (int64_t)c.n[0] * c.n[1] * (y.t1 - y.t0);
+    });
+    P->nrtiles = (int)rt.size();
+    KRP_CUDA_CHECK(cudaMemcpyAsync(P->d_rtiles, rt.data(), sizeof(TbTile) * rt.size(),
+                                   cudaMemcpyHostToDevice, s));
+    KRP_CUDA_CHECK(cudaStreamSynchronize(s));
+    P->sm_resid = sizeof(float) * smr;
+    P->sm_prep = sizeof(float) * smp;
+  }
+  {
+    size_t lcube = 0;
+    int n3max = 0;
+    for (const TbItem& it : P->h_items) {
+      lcube = std::max(lcube, (size_t)it.l[0] * it.l[1] * it.l[2]);
+      n3max = std::max(n3max, it.n[2]);
+    }
+    P->gram_f64 = lcube * sizeof(double) <= 160 * 1024;
+    P->sm_gram = lcube * (P->gram_f64 ? sizeof(double) : sizeof(float));
+    P->sm_finish = sizeof(float) * (size_t)n3max * kMaxEll;
+  }
   allow_smem(batch_sketch_kernel<float>, P->sm_sketch);
   allow_smem(batch_sketch_kernel<__nv_bfloat16>, P->sm_sketch);
   allow_smem(batch_core_kernel<float>, P->sm_core);
   allow_smem(batch_core_kernel<__nv_bfloat16>, P->sm_core);
-  allow_smem(batch_resid_kernel<float>, P->sm_resid);
-  allow_smem(batch_resid_kernel<__nv_bfloat16>, P->sm_resid);
-  allow_smem(batch_gram_kernel, P->sm_gram);
+  allow_smem(batch_resid_kernel<float, false>, P->sm_resid);
+  allow_smem(batch_resid_kernel<__nv_bfloat16, false>, P->sm_resid);
+  allow_smem(batch_resid_kernel<float, true>, P->sm_resid);
+  allow_smem(batch_resid_kernel<__nv_bfloat16, true>, P->sm_resid);
+  allow_smem(batch_gram_kernel<double>, P->sm_gram);
+  allow_smem(batch_gram_kernel<float>, P->sm_gram);
+  allow_smem(batch_core_finish_kernel, P->sm_finish);
+  allow_smem(batch_resid_prep_kernel, P->sm_prep);
   int occ = 1;
   KRP_CUDA_CHECK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(
       &occ, batch_sketch_kernel<float>, kBT, P->sm_sketch));
   P->grid_persist = std::max(1, occ) * c->num_sms;
+  int occ_r = 1, occ_rb = 1;
+  if (P->resid_wide) {
+    KRP_CUDA_CHECK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+        &occ_r, batch_resid_kernel<float, true>, kBT, P->sm_resid));
+    KRP_CUDA_CHECK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+        &occ_rb, batch_resid_kernel<__nv_bfloat16, true>, kBT, P->sm_resid));
+  } else {
+    KRP_CUDA_CHECK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+        &occ_r, batch_resid_kernel<float, false>, kBT, P->sm_resid));
+    KRP_CUDA_CHECK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+        &occ_rb, batch_resid_kernel<__nv_bfloat16, false>, kBT, P->sm_resid));
+  }
+  P->grid_resid = std::max(1, std::min(occ_r, occ_rb)) * c->num_sms;
   return P;
 }
 

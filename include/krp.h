@@ -373,10 +373,11 @@ typedef struct krp_hankel_item {
 krp_status krp_block_hankel_batched(krp_ctx ctx, krp_dtype bt, int count,
                                     krp_hankel_item* items);
 
-/* Work-tile choice of the context's current batch plan (slabs per tile,
- * number of tiles, persistent grid size); KRP_EINVAL if there is none. */
-krp_status krp_tucker_batch_plan_info(krp_ctx ctx, int* slabs_per_tile,
-                                      int* tiles, int* grid);
+/* Work split of the context's current batch plan: slabs per sketch unit
+ * (picked by timing), number of sketch units (warp work items), and the
+ * sketch kernel's grid; KRP_EINVAL if there is none. */
+krp_status krp_tucker_batch_plan_info(krp_ctx ctx, int* slabs_per_unit,
+                                      int* units, int* grid);
 
 #ifdef __cplusplus
 }

@@ -419,9 +419,9 @@ krp_status krp_block_hankel_batched(krp_ctx ctx, krp_dtype bt, int count, krp_ha
   return guarded(ctx, [&] { hankel_batched(bt, count, items); });
 }
 
-krp_status krp_tucker_batch_plan_info(krp_ctx ctx, int* slabs_per_tile, int* tiles, int* grid) {
+krp_status krp_tucker_batch_plan_info(krp_ctx ctx, int* slabs_per_unit, int* units, int* grid) {
   return guarded(ctx, [&] {
-    KRP_REQUIRE(tucker_batched_plan_info(slabs_per_tile, tiles, grid), "no batch plan");
+    KRP_REQUIRE(tucker_batched_plan_info(slabs_per_unit, units, grid), "no batch plan");
   });
 }
 

@@ -27,6 +27,7 @@
 #include <cmath>
 #include <cstring>
 #include <memory>
+#include <type_traits>
 #include <vector>
 
 #include "common.cuh"
@@ -38,8 +39,6 @@ namespace {
 constexpr int kBT = 256;              // threads of the slab kernels
 constexpr int kMaxSide = 256;         // n_i
 constexpr int kMaxEll = 32;           // l_i
-constexpr int kJB = 32;               // slab columns per staged chunk
-constexpr int kRPT = kMaxSide / 32;   // rows per thread in the row mappings
 
 struct TbItem {
   const void* X;
@@ -48,6 +47,15 @@ struct TbItem {
   int lm;            // memo factor width: max l_i
   int r[3];          // output sizes (r_i with truncation, l_i without)
   float* om[3];      // n_i x lm
+  float* orow[3];    // n_i x 4 ceil(lm / 4), row-major FP32 copy of om
+  float* qrow[3];    // n_i x 4 ceil(l_i / 4), row-major FP32 copy of Q
+  // BF16 form only (null otherwise): k-major BF16 tables for the warp MMAs,
+  // ot[m][k * np16[m] + i] = Omega_m[i, k] (m < 2; k < 8 ceil(lm / 8)), and
+  // q2t[p][k * np16[1] + j], p = 0, 1, 2: Q2 = hi + mid + lo (k < 8 ceil(l2 / 8));
+  // zero outside the matrix.
+  __nv_bfloat16* ot[2];
+  __nv_bfloat16* q2t;
+  int np16[2];       // n1, n2 rounded up to 16
   float* Y[3];       // n_i x lm
   double* Q[3];      // n_i x l_i
   float* C;          // n3 slab cores, l1 x l2 each
@@ -75,70 +83,6 @@ __device__ __forceinline__ float ldx<__nv_bfloat16>(const __nv_bfloat16* p, int6
   return __bfloat162float(p[i]);
 }
 
-// A chunk of columns j0 .. j0+kJB-1 of slab t, moved through registers so
-// that all of a thread's loads are in flight together (and the next chunk's
-// while the current one is multiplied): warp w holds rows jl = w + 8p of the
-// chunk, lane l holds entries i = l + 32u (u < R = ceil(n1 / 32)); zero
-// outside the slab.
-template <int R>
-struct ChunkRegs {
-  float v[kJB / 8][R];
-};
-
-template <class XT, int R>
-__device__ __forceinline__ void chunk_load(ChunkRegs<R>& r, const XT* X, int n1, int n2, int t,
-                                           int j0) {
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-#pragma unroll
-  for (int p = 0; p < kJB / 8; ++p) {
-    const int j = j0 + warp + 8 * p;
-    const bool jok = j < n2;
-    const int64_t base = (int64_t)n1 * (j + (int64_t)n2 * t);
-#pragma unroll
-    for (int u = 0; u < R; ++u) {
-      const int i = lane + 32 * u;
-      r.v[p][u] = (jok && i < n1) ? ldx(X, base + i) : 0.f;
-    }
-  }
-}
-
-template <int R>
-__device__ __forceinline__ void chunk_store(const ChunkRegs<R>& r, float* Xs, int pitch) {
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-#pragma unroll
-  for (int p = 0; p < kJB / 8; ++p)
-#pragma unroll
-    for (int u = 0; u < R; ++u) Xs[(warp + 8 * p) * pitch + lane + 32 * u] = r.v[p][u];
-}
-
-// sum_i Xs[row][i] W[i][4kg..4kg+3] over i < n1p8, with two partial sums per
-// output (even and odd groups of four i) for instruction-level parallelism;
-// W rows n1..n1p8-1 and Xs entries beyond n1 are zero.
-__device__ __forceinline__ float4 row_dot4(const float* Xrow, const float* W, int Lp, int kg,
-                                           int n1p8) {
-  float e0 = 0.f, e1 = 0.f, e2 = 0.f, e3 = 0.f, o0 = 0.f, o1 = 0.f, o2 = 0.f, o3 = 0.f;
-  for (int i = 0; i < n1p8; i += 8) {
-    const float4 xa = *reinterpret_cast<const float4*>(&Xrow[i]);
-    const float4 xb = *reinterpret_cast<const float4*>(&Xrow[i + 4]);
-    const float xva[4] = {xa.x, xa.y, xa.z, xa.w};
-    const float xvb[4] = {xb.x, xb.y, xb.z, xb.w};
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const float4 wa = *reinterpret_cast<const float4*>(&W[(i + q) * Lp + 4 * kg]);
-      const float4 wb = *reinterpret_cast<const float4*>(&W[(i + 4 + q) * Lp + 4 * kg]);
-      e0 = fmaf(xva[q], wa.x, e0);
-      e1 = fmaf(xva[q], wa.y, e1);
-      e2 = fmaf(xva[q], wa.z, e2);
-      e3 = fmaf(xva[q], wa.w, e3);
-      o0 = fmaf(xvb[q], wb.x, o0);
-      o1 = fmaf(xvb[q], wb.y, o1);
-      o2 = fmaf(xvb[q], wb.z, o2);
-      o3 = fmaf(xvb[q], wb.w, o3);
-    }
-  }
-  return make_float4(e0 + o0, e1 + o1, e2 + o2, e3 + o3);
-}
-
 __device__ int next_tile(int* counter, int* s_tile) {
   __syncthreads();  // everyone is done with the previous tile's shared memory
   if (threadIdx.x == 0) *s_tile = atomicAdd(counter, 1);
@@ -146,249 +90,637 @@ __device__ int next_tile(int* counter, int* s_tile) {
   return *s_tile;
 }
 
-// ---------------------------------------------------------------- sketch ----
-// Shared memory (floats): Xs[kJB][pitch], O1s[n1max8][Lp], O2s[n2max][Lp],
-// Y2p[n2max][Lp], o3s[Lp], y3s[Lp].
-struct SketchSmem {
-  float *Xs, *O1s, *O2s, *Y2p, *o3s, *y3s;
-  int pitch, Lp;
+// Warp-level work units of the sketch and core kernels, handed out by an
+// atomic counter (one per warp, no barrier across the CTA).
+struct SkUnit {
+  int item;
+  int kb;      // kind << 16 | block: kind 0 = rows (block of 32 i), 1 = columns (block of 32 j)
+  int t0, t1;  // slabs t0 .. t1-1
 };
+constexpr int kUnitCols = 1 << 16;
 
-template <class XT, int R>
-__device__ void sketch_tile(const TbItem& it, const TbTile& tile, const SketchSmem& S) {
-  const int tid = threadIdx.x, ig = tid >> 3, kg = tid & 7;
+__device__ __forceinline__ int warp_next(int* counter, int lane) {
+  int u = 0;
+  if (lane == 0) u = atomicAdd(counter, 1);
+  return __shfl_sync(0xffffffffu, u, 0);
+}
+
+// Reduce-scatter of CNT (a power of two <= 32) per-lane values: returns the
+// warp's total of value (lane % CNT).  Each halving step exchanges half of
+// the values with the lane h apart and keeps the half selected by that lane
+// bit (CNT - 1 shuffles), then lanes that share lane % CNT are summed.
+template <int CNT>
+__device__ __forceinline__ float reduce_scatter(float (&v)[CNT], int lane) {
+#pragma unroll
+  for (int h = CNT / 2; h >= 1; h >>= 1) {
+    const bool upper = lane & h;
+#pragma unroll
+    for (int q = 0; q < h; ++q) {
+      const float send = upper ? v[q] : v[q + h];
+      const float keep = upper ? v[q + h] : v[q];
+      v[q] = keep + __shfl_xor_sync(0xffffffffu, send, h);
+    }
+  }
+  float r = v[0];
+#pragma unroll
+  for (int o = CNT; o < 32; o <<= 1) r += __shfl_xor_sync(0xffffffffu, r, o);
+  return r;
+}
+
+__device__ __forceinline__ void fma4(float* acc, float x, const float4& w) {
+  acc[0] = fmaf(x, w.x, acc[0]);
+  acc[1] = fmaf(x, w.y, acc[1]);
+  acc[2] = fmaf(x, w.z, acc[2]);
+  acc[3] = fmaf(x, w.w, acc[3]);
+}
+
+// ---------------------------------------------------------------- sketch ----
+// All three mode sketches of the memoized tree (Sec. 5.1) from the slabs
+// X_t = X[:, :, t] (n1 x n2, i fastest), FP32 on CUDA cores, as two kinds of
+// warp units over the same slabs (one launch; a tensor's row and column
+// units are adjacent in the unit list, so the second read of a slab is
+// served by L2):
+//   row unit (32 rows i, lane = row; slabs t0..t1-1):
+//     A_t[i, :] = sum_j X[i, j, t] Om2[j, :]   (X straight from global memory,
+//                 coalesced over the lanes, 16 columns in flight; Om2 rows broadcast)
+//     Y1[i, :] += A_t[i, :] * Om3[t, :]        (registers across the unit's slabs)
+//     Y3[t, :] += sum_i Om1[i, :] * A_t[i, :]  (warp reduce-scatter, then atomics)
+//   column unit (32 columns j, lane = column):
+//     B_t[j, :] = sum_i X[i, j, t] Om1[i, :]   (32 x 32 blocks of X transposed
+//                 through the warp's shared buffer; Om1 rows broadcast)
+//     Y2[j, :] += B_t[j, :] * Om3[t, :]        (registers across the unit's slabs)
+// Factor rows come from the row-major FP32 tables orow[m] (LP = 4 LQ columns,
+// zero beyond l).  Every Y_n is zeroed before the launch and receives atomics.
+template <class XT, int LQ>
+__device__ void sketch_rows_unit(const TbItem& it, const SkUnit& u, int lane) {
+  constexpr int LP = 4 * LQ;
+  constexpr int CNT = LP <= 16 ? 16 : 32;
+  constexpr int NC = LQ <= 4 ? 16 : 8;
   const int n1 = it.n[0], n2 = it.n[1], n3 = it.n[2], lm = it.lm;
-  const int pitch = S.pitch, Lp = S.Lp;
-  const int n1p8 = (n1 + 7) & ~7;
+  const int i = 32 * (u.kb & (kUnitCols - 1)) + lane;
+  const bool valid = i < n1;
+  const float4* o2 = reinterpret_cast<const float4*>(it.orow[1]);
+  const float4* o3 = reinterpret_cast<const float4*>(it.orow[2]);
+  const float4* o1 = reinterpret_cast<const float4*>(it.orow[0] + (size_t)(valid ? i : 0) * LP);
   const XT* X = static_cast<const XT*>(it.X);
-  // factors are column-major: consecutive threads read consecutive rows
-  for (int e = tid; e < n1p8 * Lp; e += kBT) {
-    const int i = e % n1p8, k = e / n1p8;
-    S.O1s[i * Lp + k] = (i < n1 && k < lm) ? it.om[0][i + (int64_t)n1 * k] : 0.f;
-  }
-  for (int e = tid; e < n2 * Lp; e += kBT) {
-    const int j = e % n2, k = e / n2;
-    S.O2s[j * Lp + k] = k < lm ? it.om[1][j + (int64_t)n2 * k] : 0.f;
-    S.Y2p[j * Lp + k] = 0.f;
-  }
-  float y1[R][4];
+  float y1[LP];
 #pragma unroll
-  for (int u = 0; u < R; ++u)
+  for (int k = 0; k < LP; ++k) y1[k] = 0.f;
+  for (int t = u.t0; t < u.t1; ++t) {
+    float a[LP];
 #pragma unroll
-    for (int c = 0; c < 4; ++c) y1[u][c] = 0.f;
-  const bool kact = 4 * kg < Lp;
-  const int nch = (n2 + kJB - 1) / kJB;
-  const int nq = (tile.t1 - tile.t0) * nch;
-  ChunkRegs<R> cr;
-  chunk_load<XT, R>(cr, X, n1, n2, tile.t0, 0);
-  float a[R][4];
-  for (int q = 0; q < nq; ++q) {
-    const int t = tile.t0 + q / nch, ch = q % nch, j0 = ch * kJB;
-    __syncthreads();  // previous chunk and slab epilogue consumed
-    if (ch == 0) {
-      if (tid < Lp) {
-        S.o3s[tid] = tid < lm ? it.om[2][t + (int64_t)n3 * tid] : 0.f;
-        S.y3s[tid] = 0.f;
-      }
+    for (int k = 0; k < LP; ++k) a[k] = 0.f;
+    const XT* xp = X + (int64_t)n1 * n2 * t + (valid ? i : 0);
+    int j = 0;
+    for (; j + NC <= n2; j += NC) {
+      float xv[NC];
+      const XT* xj = xp + (int64_t)n1 * j;
 #pragma unroll
-      for (int u = 0; u < R; ++u)
+      for (int c = 0; c < NC; ++c) xv[c] = valid ? ldx(xj, n1 * c) : 0.f;
 #pragma unroll
-        for (int c = 0; c < 4; ++c) a[u][c] = 0.f;
+      for (int c = 0; c < NC; ++c)
+#pragma unroll
+        for (int q = 0; q < LQ; ++q) fma4(&a[4 * q], xv[c], __ldg(o2 + (j + c) * LQ + q));
     }
-    chunk_store<R>(cr, S.Xs, pitch);
-    __syncthreads();
-    if (q + 1 < nq) chunk_load<XT, R>(cr, X, n1, n2, tile.t0 + (q + 1) / nch, ((q + 1) % nch) * kJB);
-    const int jn = min(kJB, n2 - j0);
-    if (kact) {
-      // A_t rows ig + 32u, columns 4kg..4kg+3
-      for (int jl = 0; jl < jn; ++jl) {
-        const float4 w = *reinterpret_cast<const float4*>(&S.O2s[(j0 + jl) * Lp + 4 * kg]);
+    for (; j < n2; ++j) {
+      const float x = valid ? ldx(xp, (int64_t)n1 * j) : 0.f;
 #pragma unroll
-        for (int u = 0; u < R; ++u) {
-          const float x = S.Xs[jl * pitch + ig + 32 * u];
-          a[u][0] = fmaf(x, w.x, a[u][0]);
-          a[u][1] = fmaf(x, w.y, a[u][1]);
-          a[u][2] = fmaf(x, w.z, a[u][2]);
-          a[u][3] = fmaf(x, w.w, a[u][3]);
+      for (int q = 0; q < LQ; ++q) fma4(&a[4 * q], x, __ldg(o2 + j * LQ + q));
+    }
+    float v[CNT];
+#pragma unroll
+    for (int q = 0; q < LQ; ++q) {
+      const float4 w3 = __ldg(o3 + t * LQ + q);
+      const float4 w1 = valid ? __ldg(o1 + q) : make_float4(0.f, 0.f, 0.f, 0.f);
+      y1[4 * q + 0] = fmaf(a[4 * q + 0], w3.x, y1[4 * q + 0]);
+      y1[4 * q + 1] = fmaf(a[4 * q + 1], w3.y, y1[4 * q + 1]);
+      y1[4 * q + 2] = fmaf(a[4 * q + 2], w3.z, y1[4 * q + 2]);
+      y1[4 * q + 3] = fmaf(a[4 * q + 3], w3.w, y1[4 * q + 3]);
+      v[4 * q + 0] = a[4 * q + 0] * w1.x;
+      v[4 * q + 1] = a[4 * q + 1] * w1.y;
+      v[4 * q + 2] = a[4 * q + 2] * w1.z;
+      v[4 * q + 3] = a[4 * q + 3] * w1.w;
+    }
+#pragma unroll
+    for (int k = LP; k < CNT; ++k) v[k] = 0.f;
+    const float s3 = reduce_scatter<CNT>(v, lane);
+    if (lane < CNT && lane < lm) atomicAdd(&it.Y[2][t + (int64_t)n3 * lane], s3);
+  }
+  if (valid) {
+#pragma unroll
+    for (int k = 0; k < LP; ++k)
+      if (k < lm) atomicAdd(&it.Y[0][i + (int64_t)n1 * k], y1[k]);
+  }
+}
+
+template <class XT, int LQ>
+__device__ void sketch_cols_unit(const TbItem& it, const SkUnit& u, int lane, float* Xw) {
+  constexpr int LP = 4 * LQ;
+  constexpr int NC = LQ <= 4 ? 16 : 8;  // columns loaded per group
+  const int n1 = it.n[0], n2 = it.n[1], lm = it.lm;
+  const int j0 = 32 * (u.kb & (kUnitCols - 1));
+  const int jn = min(32, n2 - j0);
+  const int j = j0 + lane;
+  const int RB = (n1 + 31) >> 5;
+  const float4* o1 = reinterpret_cast<const float4*>(it.orow[0]);
+  const float4* o3 = reinterpret_cast<const float4*>(it.orow[2]);
+  const XT* X = static_cast<const XT*>(it.X);
+  float y2[LP];
+#pragma unroll
+  for (int k = 0; k < LP; ++k) y2[k] = 0.f;
+  for (int t = u.t0; t < u.t1; ++t) {
+    float b[LP];
+#pragma unroll
+    for (int k = 0; k < LP; ++k) b[k] = 0.f;
+    for (int rb = 0; rb < RB; ++rb) {
+      const int i = 32 * rb + lane;
+      const bool vi = i < n1;
+      const XT* xp = X + (int64_t)n1 * ((int64_t)n2 * t + j0) + (vi ? i : 0);
+      __syncwarp();  // the previous block has been read
+#pragma unroll 1
+      for (int h = 0; h < 32; h += NC) {
+        float xv[NC];
+        const XT* xh = xp + (int64_t)n1 * h;
+#pragma unroll
+        for (int c = 0; c < NC; ++c) xv[c] = (vi && h + c < jn) ? ldx(xh, n1 * c) : 0.f;
+#pragma unroll
+        for (int c = 0; c < NC; ++c) Xw[lane * 33 + h + c] = xv[c];  // [i][j], pitch 33
+      }
+      __syncwarp();
+      const int ni = min(32, n1 - 32 * rb);
+      const float4* w = o1 + (size_t)(32 * rb) * LQ;
+      for (int ii = 0; ii < ni; ++ii) {
+        const float x = Xw[ii * 33 + lane];
+#pragma unroll
+        for (int q = 0; q < LQ; ++q) fma4(&b[4 * q], x, __ldg(w + ii * LQ + q));
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < LQ; ++q) {
+      const float4 w3 = __ldg(o3 + t * LQ + q);
+      y2[4 * q + 0] = fmaf(b[4 * q + 0], w3.x, y2[4 * q + 0]);
+      y2[4 * q + 1] = fmaf(b[4 * q + 1], w3.y, y2[4 * q + 1]);
+      y2[4 * q + 2] = fmaf(b[4 * q + 2], w3.z, y2[4 * q + 2]);
+      y2[4 * q + 3] = fmaf(b[4 * q + 3], w3.w, y2[4 * q + 3]);
+    }
+  }
+  if (lane < jn) {
+#pragma unroll
+    for (int k = 0; k < LP; ++k)
+      if (k < lm) atomicAdd(&it.Y[1][j + (int64_t)n2 * k], y2[k]);
+  }
+}
+
+// ------------------------------------------------ BF16 form: warp MMAs ----
+// For BF16 X the two contractions of the sketch and the first one of the core
+// run on the tensor cores as warp-level mma.sync m16n8k16 (BF16 operands,
+// FP32 accumulators): the products of BF16 X with the BF16 factors (and with
+// the three BF16 parts of Q2) are exact, so the sums are the CUDA-core sums
+// up to order.  The units are the same as above (32 rows or columns, slabs
+// t0..t1-1); A fragments are gathered straight from global memory (two 16-bit
+// loads per register, zero outside the slab), B fragments are 32-bit loads
+// from the k-major tables ot / q2t.
+// Fragment layout (g = lane / 4, q = lane % 4; lower half of a register =
+// lower k): A regs {A[g][2q..2q+1]}, {A[g+8][2q..]}, {A[g][2q+8..]},
+// {A[g+8][2q+8..]}; B regs {B[2q..2q+1][g]}, {B[2q+8..2q+9][g]}; D
+// {D[g][2q]}, {D[g][2q+1]}, {D[g+8][2q]}, {D[g+8][2q+1]}.
+__device__ __forceinline__ void mma16816(float (&d)[4], const uint32_t (&a)[4], uint32_t b0,
+                                         uint32_t b1) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
+      "{%8,%9}, {%0,%1,%2,%3};"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+__device__ __forceinline__ uint32_t ldb16(const __nv_bfloat16* p, bool ok) {
+  return ok ? (uint32_t)__ldg(reinterpret_cast<const unsigned short*>(p)) : 0u;
+}
+
+// rows unit of the sketch (see sketch_rows_unit), NT = ceil(lm / 8) n-tiles:
+// D = A_t for the unit's 32 rows (two m-tiles) x 8 NT columns
+template <int NT>
+__device__ void sketch_rows_tc(const TbItem& it, const SkUnit& u, int lane) {
+  const int g = lane >> 2, q = lane & 3;
+  const int n1 = it.n[0], n2 = it.n[1], n3 = it.n[2], lm = it.lm;
+  const int lp = 4 * ((lm + 3) / 4);
+  const int i0 = 32 * (u.kb & (kUnitCols - 1));
+  const int n2p = it.np16[1];
+  const uint32_t* o2t = reinterpret_cast<const uint32_t*>(it.ot[1]);
+  const __nv_bfloat16* X = static_cast<const __nv_bfloat16*>(it.X);
+  int rr[2][2];
+  bool rv[2][2];
+#pragma unroll
+  for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      rr[mt][h] = i0 + 16 * mt + g + 8 * h;
+      rv[mt][h] = rr[mt][h] < n1;
+    }
+  float w1[2][NT][4], y1[2][NT][4];
+#pragma unroll
+  for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+    for (int nt = 0; nt < NT; ++nt)
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const int col = nt * 8 + 2 * q + (e & 1);
+        const bool ok = rv[mt][e >> 1] && col < lm;
+        w1[mt][nt][e] = ok ? it.orow[0][(size_t)rr[mt][e >> 1] * lp + col] : 0.f;
+        y1[mt][nt][e] = 0.f;
+      }
+  for (int t = u.t0; t < u.t1; ++t) {
+    float d[2][NT][4];
+#pragma unroll
+    for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+      for (int nt = 0; nt < NT; ++nt) d[mt][nt][0] = d[mt][nt][1] = d[mt][nt][2] = d[mt][nt][3] = 0.f;
+    const __nv_bfloat16* xt = X + (int64_t)n1 * n2 * t;
+    for (int j0 = 0; j0 < n2; j0 += 16) {
+      uint32_t a[2][4];
+#pragma unroll
+      for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+          const int h = r & 1, j = j0 + 2 * q + 8 * (r >> 1);
+          const bool ok = rv[mt][h];
+          const __nv_bfloat16* p = xt + (ok ? rr[mt][h] : 0) + (int64_t)n1 * j;
+          a[mt][r] = ldb16(p, ok && j < n2) | (ldb16(p + n1, ok && j + 1 < n2) << 16);
         }
-      }
-      // B_t row j0 + ig (ig doubles as the chunk column here)
-      if (ig < jn) {
-        const float4 bb = row_dot4(&S.Xs[ig * pitch], S.O1s, Lp, kg, n1p8);
-        float* yp = &S.Y2p[(j0 + ig) * Lp + 4 * kg];
-        yp[0] = fmaf(bb.x, S.o3s[4 * kg + 0], yp[0]);
-        yp[1] = fmaf(bb.y, S.o3s[4 * kg + 1], yp[1]);
-        yp[2] = fmaf(bb.z, S.o3s[4 * kg + 2], yp[2]);
-        yp[3] = fmaf(bb.w, S.o3s[4 * kg + 3], yp[3]);
+#pragma unroll
+      for (int nt = 0; nt < NT; ++nt) {
+        const uint32_t* bp = o2t + (((nt * 8 + g) * n2p + j0 + 2 * q) >> 1);
+        const uint32_t b0 = __ldg(bp), b1 = __ldg(bp + 4);
+        mma16816(d[0][nt], a[0], b0, b1);
+        mma16816(d[1][nt], a[1], b0, b1);
       }
     }
-    if (ch == nch - 1) {
-      // slab t done: Y1 partial and Y3[t, :]
-      float p[4] = {0.f, 0.f, 0.f, 0.f};
-      if (kact) {
+    const float* o3r = it.orow[2] + (size_t)t * lp;
 #pragma unroll
-        for (int u = 0; u < R; ++u) {
-          const int i = ig + 32 * u;
+    for (int nt = 0; nt < NT; ++nt) {
+      float s[2];
 #pragma unroll
-          for (int c = 0; c < 4; ++c) {
-            y1[u][c] = fmaf(a[u][c], S.o3s[4 * kg + c], y1[u][c]);
-            if (i < n1) p[c] = fmaf(S.O1s[i * Lp + 4 * kg + c], a[u][c], p[c]);
+      for (int c = 0; c < 2; ++c) {
+        const int col = nt * 8 + 2 * q + c;
+        const float o3v = col < lm ? o3r[col] : 0.f;
+        float acc = 0.f;
+#pragma unroll
+        for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+          for (int h = 0; h < 2; ++h) {
+            const int e = 2 * h + c;
+            y1[mt][nt][e] = fmaf(d[mt][nt][e], o3v, y1[mt][nt][e]);
+            acc = fmaf(d[mt][nt][e], w1[mt][nt][e], acc);
           }
+        acc += __shfl_xor_sync(0xffffffffu, acc, 4);
+        acc += __shfl_xor_sync(0xffffffffu, acc, 8);
+        acc += __shfl_xor_sync(0xffffffffu, acc, 16);
+        s[c] = acc;
+      }
+      if (g == 0) {
+#pragma unroll
+        for (int c = 0; c < 2; ++c) {
+          const int col = nt * 8 + 2 * q + c;
+          if (col < lm) atomicAdd(&it.Y[2][t + (int64_t)n3 * col], s[c]);
         }
       }
-#pragma unroll
-      for (int c = 0; c < 4; ++c) {
-        p[c] += __shfl_xor_sync(0xffffffffu, p[c], 8);
-        p[c] += __shfl_xor_sync(0xffffffffu, p[c], 16);
-      }
-      if ((tid & 31) < 8 && kact) {
-#pragma unroll
-        for (int c = 0; c < 4; ++c) atomicAdd(&S.y3s[4 * kg + c], p[c]);
-      }
-      __syncthreads();
-      if (tid < lm) it.Y[2][t + (int64_t)n3 * tid] = S.y3s[tid];
     }
   }
-  // flush the tile's partial Y2 and Y1 with row-contiguous (coalesced) atomics;
-  // Y1 goes through shared memory (the Xs staging area, free by now)
-  __syncthreads();
-  for (int e = tid; e < n2 * lm; e += kBT) {
-    const int j = e % n2, k = e / n2;
-    atomicAdd(&it.Y[1][j + (int64_t)n2 * k], S.Y2p[j * Lp + k]);
-  }
-  float* Y1p = S.Xs;  // [k][i], n1 x Lp <= kJB * pitch floats
-  if (kact) {
 #pragma unroll
-    for (int u = 0; u < R; ++u) {
-      const int i = ig + 32 * u;
-      if (i < n1) {
+  for (int mt = 0; mt < 2; ++mt)
 #pragma unroll
-        for (int c = 0; c < 4; ++c) Y1p[(4 * kg + c) * n1 + i] = y1[u][c];
+    for (int nt = 0; nt < NT; ++nt)
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const int col = nt * 8 + 2 * q + (e & 1);
+        if (rv[mt][e >> 1] && col < lm)
+          atomicAdd(&it.Y[0][rr[mt][e >> 1] + (int64_t)n1 * col], y1[mt][nt][e]);
+      }
+}
+
+// columns unit of the sketch (see sketch_cols_unit): D = B_t for the unit's
+// 32 columns j (two m-tiles; A = X_t^T, K = i) x 8 NT columns
+template <int NT>
+__device__ void sketch_cols_tc(const TbItem& it, const SkUnit& u, int lane) {
+  const int g = lane >> 2, q = lane & 3;
+  const int n1 = it.n[0], n2 = it.n[1], lm = it.lm;
+  const int lp = 4 * ((lm + 3) / 4);
+  const int j0 = 32 * (u.kb & (kUnitCols - 1));
+  const int n1p = it.np16[0];
+  const uint32_t* o1t = reinterpret_cast<const uint32_t*>(it.ot[0]);
+  const __nv_bfloat16* X = static_cast<const __nv_bfloat16*>(it.X);
+  int cc[2][2];
+  bool cv[2][2];
+#pragma unroll
+  for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      cc[mt][h] = j0 + 16 * mt + g + 8 * h;
+      cv[mt][h] = cc[mt][h] < n2;
+    }
+  float y2[2][NT][4];
+#pragma unroll
+  for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+    for (int nt = 0; nt < NT; ++nt) y2[mt][nt][0] = y2[mt][nt][1] = y2[mt][nt][2] = y2[mt][nt][3] = 0.f;
+  for (int t = u.t0; t < u.t1; ++t) {
+    float d[2][NT][4];
+#pragma unroll
+    for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+      for (int nt = 0; nt < NT; ++nt) d[mt][nt][0] = d[mt][nt][1] = d[mt][nt][2] = d[mt][nt][3] = 0.f;
+    const __nv_bfloat16* xt = X + (int64_t)n1 * n2 * t;
+    for (int i0 = 0; i0 < n1; i0 += 16) {
+      uint32_t a[2][4];
+#pragma unroll
+      for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+          const int h = r & 1, i = i0 + 2 * q + 8 * (r >> 1);
+          const bool ok = cv[mt][h];
+          const __nv_bfloat16* p = xt + (int64_t)n1 * (ok ? cc[mt][h] : 0) + i;
+          a[mt][r] = ldb16(p, ok && i < n1) | (ldb16(p + 1, ok && i + 1 < n1) << 16);
+        }
+#pragma unroll
+      for (int nt = 0; nt < NT; ++nt) {
+        const uint32_t* bp = o1t + (((nt * 8 + g) * n1p + i0 + 2 * q) >> 1);
+        const uint32_t b0 = __ldg(bp), b1 = __ldg(bp + 4);
+        mma16816(d[0][nt], a[0], b0, b1);
+        mma16816(d[1][nt], a[1], b0, b1);
       }
     }
+    const float* o3r = it.orow[2] + (size_t)t * lp;
+#pragma unroll
+    for (int nt = 0; nt < NT; ++nt)
+#pragma unroll
+      for (int c = 0; c < 2; ++c) {
+        const int col = nt * 8 + 2 * q + c;
+        const float o3v = col < lm ? o3r[col] : 0.f;
+#pragma unroll
+        for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+          for (int h = 0; h < 2; ++h)
+            y2[mt][nt][2 * h + c] = fmaf(d[mt][nt][2 * h + c], o3v, y2[mt][nt][2 * h + c]);
+      }
   }
-  __syncthreads();
-  for (int e = tid; e < n1 * lm; e += kBT) atomicAdd(&it.Y[0][e], Y1p[e]);
+#pragma unroll
+  for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+    for (int nt = 0; nt < NT; ++nt)
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const int col = nt * 8 + 2 * q + (e & 1);
+        if (cv[mt][e >> 1] && col < lm)
+          atomicAdd(&it.Y[1][cc[mt][e >> 1] + (int64_t)n2 * col], y2[mt][nt][e]);
+      }
+}
+
+// T[i, :] = X_t[i, :] Q2 for the 32 rows of block rb (two m-tiles) into the
+// warp's buffer Tw[32][ldt] (columns < ldt), Q2 = hi + mid + lo (three MMAs)
+template <int NT>
+__device__ void core_rows_tc(const TbItem& it, int t, int rb, int lane, float* Tw, int ldt) {
+  const int g = lane >> 2, q = lane & 3;
+  const int n1 = it.n[0], n2 = it.n[1], l2 = it.l[1];
+  const int n2p = it.np16[1];
+  const size_t plane = (size_t)8 * NT * n2p / 2;  // uint32 per plane
+  const uint32_t* q2t = reinterpret_cast<const uint32_t*>(it.q2t);
+  const __nv_bfloat16* xt = static_cast<const __nv_bfloat16*>(it.X) + (int64_t)n1 * n2 * t;
+  int rr[2][2];
+  bool rv[2][2];
+#pragma unroll
+  for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      rr[mt][h] = 32 * rb + 16 * mt + g + 8 * h;
+      rv[mt][h] = rr[mt][h] < n1;
+    }
+  float d[2][NT][4];
+#pragma unroll
+  for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+    for (int nt = 0; nt < NT; ++nt) d[mt][nt][0] = d[mt][nt][1] = d[mt][nt][2] = d[mt][nt][3] = 0.f;
+  for (int j0 = 0; j0 < n2; j0 += 16) {
+    uint32_t a[2][4];
+#pragma unroll
+    for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+      for (int r = 0; r < 4; ++r) {
+        const int h = r & 1, j = j0 + 2 * q + 8 * (r >> 1);
+        const bool ok = rv[mt][h];
+        const __nv_bfloat16* p = xt + (ok ? rr[mt][h] : 0) + (int64_t)n1 * j;
+        a[mt][r] = ldb16(p, ok && j < n2) | (ldb16(p + n1, ok && j + 1 < n2) << 16);
+      }
+#pragma unroll
+    for (int nt = 0; nt < NT; ++nt)
+#pragma unroll
+      for (int pl = 0; pl < 3; ++pl) {
+        const uint32_t* bp = q2t + pl * plane + (((nt * 8 + g) * n2p + j0 + 2 * q) >> 1);
+        const uint32_t b0 = __ldg(bp), b1 = __ldg(bp + 4);
+        mma16816(d[0][nt], a[0], b0, b1);
+        mma16816(d[1][nt], a[1], b0, b1);
+      }
+  }
+#pragma unroll
+  for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+    for (int nt = 0; nt < NT; ++nt)
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const int col = nt * 8 + 2 * q + (e & 1);
+        if (col < ldt) Tw[(16 * mt + g + 8 * (e >> 1)) * ldt + col] = col < l2 ? d[mt][nt][e] : 0.f;
+      }
+}
+
+template <class XT, int LQ>
+__device__ __forceinline__ void sketch_unit(const TbItem& it, const SkUnit& u, int lane, float* Xw) {
+  if (u.kb >= kUnitCols)
+    sketch_cols_unit<XT, LQ>(it, u, lane, Xw);
+  else
+    sketch_rows_unit<XT, LQ>(it, u, lane);
+}
+
+template <int NT>
+__device__ __forceinline__ void sketch_unit_tc(const TbItem& it, const SkUnit& u, int lane) {
+  if (u.kb >= kUnitCols)
+    sketch_cols_tc<NT>(it, u, lane);
+  else
+    sketch_rows_tc<NT>(it, u, lane);
 }
 
 template <class XT>
 __global__ void __launch_bounds__(kBT, 2)
-    batch_sketch_kernel(const TbItem* __restrict__ items, const TbTile* __restrict__ tiles,
-                        int ntiles, int* counter, int pitch, int Lp, int n1max8, int n2max) {
-  extern __shared__ __align__(16) float bsm[];
-  SketchSmem S;
-  S.Xs = bsm;
-  S.O1s = S.Xs + kJB * pitch;
-  S.O2s = S.O1s + n1max8 * Lp;
-  S.Y2p = S.O2s + n2max * Lp;
-  S.o3s = S.Y2p + n2max * Lp;
-  S.y3s = S.o3s + Lp;
-  S.pitch = pitch;
-  S.Lp = Lp;
-  __shared__ int s_tile;
+    batch_sketch_kernel(const TbItem* __restrict__ items, const SkUnit* __restrict__ units,
+                        int nunits, int* counter) {
+  __shared__ float xw[kBT / 32][32 * 33];
+  const int lane = threadIdx.x & 31;
+  float* Xw = xw[threadIdx.x >> 5];
   for (;;) {
-    const int ti = next_tile(counter, &s_tile);
-    if (ti >= ntiles) break;
-    const TbTile tile = tiles[ti];
-    const TbItem& it = items[tile.item];
-    switch ((it.n[0] + 31) >> 5) {  // uniform over the CTA
-      case 1: sketch_tile<XT, 1>(it, tile, S); break;
-      case 2: sketch_tile<XT, 2>(it, tile, S); break;
-      case 3: sketch_tile<XT, 3>(it, tile, S); break;
-      case 4: sketch_tile<XT, 4>(it, tile, S); break;
-      case 5: sketch_tile<XT, 5>(it, tile, S); break;
-      case 6: sketch_tile<XT, 6>(it, tile, S); break;
-      case 7: sketch_tile<XT, 7>(it, tile, S); break;
-      default: sketch_tile<XT, 8>(it, tile, S); break;
+    const int ui = warp_next(counter, lane);
+    if (ui >= nunits) break;
+    const SkUnit u = units[ui];
+    const TbItem& it = items[u.item];
+    if constexpr (std::is_same<XT, __nv_bfloat16>::value) {
+      switch ((it.lm + 7) >> 3) {  // uniform over the warp
+        case 1: sketch_unit_tc<1>(it, u, lane); break;
+        case 2: sketch_unit_tc<2>(it, u, lane); break;
+        case 3: sketch_unit_tc<3>(it, u, lane); break;
+        default: sketch_unit_tc<4>(it, u, lane); break;
+      }
+    } else {
+      switch ((it.lm + 3) >> 2) {  // uniform over the warp
+      case 1: sketch_unit<XT, 1>(it, u, lane, Xw); break;
+      case 2: sketch_unit<XT, 2>(it, u, lane, Xw); break;
+      case 3: sketch_unit<XT, 3>(it, u, lane, Xw); break;
+      case 4: sketch_unit<XT, 4>(it, u, lane, Xw); break;
+      case 5: sketch_unit<XT, 5>(it, u, lane, Xw); break;
+      case 6: sketch_unit<XT, 6>(it, u, lane, Xw); break;
+      case 7: sketch_unit<XT, 7>(it, u, lane, Xw); break;
+      default: sketch_unit<XT, 8>(it, u, lane, Xw); break;
+      }
+    }
+  }
+}
+
+// Row-major FP32 tables of the factors (which = 0: Omega_m from om[m], LP =
+// 4 ceil(lm / 4) columns; which = 1: Q_m from the FP64 Q[m], 4 ceil(l_m / 4)
+// columns), zero beyond the last column; grid (count, 3).
+__global__ void batch_rows_kernel(const TbItem* __restrict__ items, int which) {
+  const TbItem& it = items[blockIdx.x];
+  const int m = blockIdx.y, n = it.n[m];
+  const int l = which ? it.l[m] : it.lm;
+  const int lp = 4 * ((l + 3) / 4);
+  float* dst = which ? it.qrow[m] : it.orow[m];
+  for (int e = threadIdx.x; e < n * lp; e += blockDim.x) {
+    const int i = e % n, k = e / n;
+    float v = 0.f;
+    if (k < l) v = which ? (float)it.Q[m][i + (int64_t)n * k] : it.om[m][i + (int64_t)n * k];
+    dst[(size_t)i * lp + k] = v;
+  }
+  if (which == 0 && m < 2 && it.ot[m]) {  // BF16 factors (exact: the BF16 form draws them rounded)
+    const int np = it.np16[m], l8 = 8 * ((l + 7) / 8);
+    for (int e = threadIdx.x; e < l8 * np; e += blockDim.x) {
+      const int k = e / np, i = e % np;
+      it.ot[m][e] = __float2bfloat16_rn(k < l && i < n ? it.om[m][i + (int64_t)n * k] : 0.f);
+    }
+  }
+  if (which == 1 && m == 1 && it.q2t) {  // Q2 = hi + mid + lo in BF16
+    const int np = it.np16[1], l8 = 8 * ((l + 7) / 8);
+    const size_t plane = (size_t)l8 * np;
+    for (int e = threadIdx.x; e < l8 * np; e += blockDim.x) {
+      const int k = e / np, j = e % np;
+      const double v = k < l && j < n ? it.Q[1][j + (int64_t)n * k] : 0.0;
+      const __nv_bfloat16 h = __double2bfloat16(v);
+      const double r1 = v - (double)__bfloat162float(h);
+      const __nv_bfloat16 md = __double2bfloat16(r1);
+      const __nv_bfloat16 lo = __double2bfloat16(r1 - (double)__bfloat162float(md));
+      it.q2t[e] = h;
+      it.q2t[plane + e] = md;
+      it.q2t[2 * plane + e] = lo;
     }
   }
 }
 
 // ------------------------------------------------------------------ core ----
-// C_t = Q1^T X_t Q2 (l1 x l2) for every slab of the tile.  Shared memory
-// (floats): Xs[kJB][pitch], Q1s[n1max8][Lp], Q2s[n2max][Lp], Ts[kJB][Lp].
-template <class XT, int R>
-__device__ void core_tile(const TbItem& it, const TbTile& tile, float* Xs, float* Q1s, float* Q2s,
-                          float* Ts, int pitch, int Lp) {
-  const int tid = threadIdx.x, hi = tid >> 3, kg = tid & 7;
+// C_t = Q1^T X_t Q2 (l1 x l2) for one slab t per warp unit.  For each block
+// of 32 rows i (lane = row): T[i, :] = sum_j X[i, j, t] Q2[j, :] (X straight
+// from global memory, Q2 rows broadcast), staged in the warp's shared buffer,
+// then C_t[a, 4bq .. 4bq+3] += sum_i Q1[i, a] T[i, 4bq .. 4bq+3] for the
+// lane's pairs (a, bq) (pair p = lane + 32 m, a = p / LQ, bq = p % LQ).  C_t
+// is stored whole at the end (no atomics).  LQ = ceil(l2 / 4).
+template <class XT, int LQ>
+__device__ void core_unit(const TbItem& it, int t, int lane, float* Tw) {
+  constexpr int LP = 4 * LQ;
+  constexpr int NC = LQ <= 4 ? 16 : 8;
   const int n1 = it.n[0], n2 = it.n[1], l1 = it.l[0], l2 = it.l[1];
-  const int n1p8 = (n1 + 7) & ~7;
+  const int l1p = 4 * ((l1 + 3) / 4);
+  const int npairs = l1 * LQ;  // <= 32 LQ
+  const float4* q2 = reinterpret_cast<const float4*>(it.qrow[1]);
+  const float* q1 = it.qrow[0];
   const XT* X = static_cast<const XT*>(it.X);
-  for (int e = tid; e < n1p8 * Lp; e += kBT) {
-    const int i = e % n1p8, a = e / n1p8;
-    Q1s[i * Lp + a] = (i < n1 && a < l1) ? (float)it.Q[0][i + (int64_t)n1 * a] : 0.f;
-  }
-  for (int e = tid; e < n2 * Lp; e += kBT) {
-    const int j = e % n2, b = e / n2;
-    Q2s[j * Lp + b] = b < l2 ? (float)it.Q[1][j + (int64_t)n2 * b] : 0.f;
-  }
-  const bool kact = 4 * kg < Lp;
-  const int nch = (n2 + kJB - 1) / kJB;
-  const int nq = (tile.t1 - tile.t0) * nch;
-  ChunkRegs<R> cr;
-  chunk_load<XT, R>(cr, X, n1, n2, tile.t0, 0);
-  // thread (a = hi, b = 4kg..4kg+3) of C_t
-  float cacc[4];
-  for (int q = 0; q < nq; ++q) {
-    const int t = tile.t0 + q / nch, ch = q % nch, j0 = ch * kJB;
-    if (ch == 0) cacc[0] = cacc[1] = cacc[2] = cacc[3] = 0.f;
-    __syncthreads();
-    chunk_store<R>(cr, Xs, pitch);
-    __syncthreads();
-    if (q + 1 < nq) chunk_load<XT, R>(cr, X, n1, n2, tile.t0 + (q + 1) / nch, ((q + 1) % nch) * kJB);
-    const int jn = min(kJB, n2 - j0);
-    // Ts[jl][a] = sum_i Xs[jl][i] Q1s[i][a]: thread (jl = hi, a = 4kg..)
-    if (kact) {
-      const float4 tv = hi < jn ? row_dot4(&Xs[hi * pitch], Q1s, Lp, kg, n1p8)
-                                : make_float4(0.f, 0.f, 0.f, 0.f);
-      *reinterpret_cast<float4*>(&Ts[hi * Lp + 4 * kg]) = tv;
-    }
-    __syncthreads();
-    if (kact && hi < Lp) {
-      for (int jl = 0; jl < jn; ++jl) {
-        const float ta = Ts[jl * Lp + hi];
-        const float4 w = *reinterpret_cast<const float4*>(&Q2s[(j0 + jl) * Lp + 4 * kg]);
-        cacc[0] = fmaf(ta, w.x, cacc[0]);
-        cacc[1] = fmaf(ta, w.y, cacc[1]);
-        cacc[2] = fmaf(ta, w.z, cacc[2]);
-        cacc[3] = fmaf(ta, w.w, cacc[3]);
-      }
-    }
-    if (ch == nch - 1 && kact && hi < l1) {
-      float* Ct = it.C + (int64_t)t * l1 * l2;
+  float c[LQ][4];
 #pragma unroll
-      for (int c = 0; c < 4; ++c) {
-        const int b = 4 * kg + c;
-        if (b < l2) Ct[hi + l1 * b] = cacc[c];
+  for (int m = 0; m < LQ; ++m) c[m][0] = c[m][1] = c[m][2] = c[m][3] = 0.f;
+  const int RB = (n1 + 31) >> 5;
+  for (int rb = 0; rb < RB; ++rb) {
+    if constexpr (std::is_same<XT, __nv_bfloat16>::value) {
+      __syncwarp();  // the previous block's T has been read
+      core_rows_tc<(LQ + 1) / 2>(it, t, rb, lane, Tw, LP);
+      __syncwarp();
+    } else {
+    const int i = 32 * rb + lane;
+    const bool valid = i < n1;
+    const XT* xp = X + (int64_t)n1 * n2 * t + (valid ? i : 0);
+    float tr[LP];
+#pragma unroll
+    for (int k = 0; k < LP; ++k) tr[k] = 0.f;
+    int j = 0;
+    for (; j + NC <= n2; j += NC) {
+      float xv[NC];
+      const XT* xj = xp + (int64_t)n1 * j;
+#pragma unroll
+      for (int cc = 0; cc < NC; ++cc) xv[cc] = valid ? ldx(xj, n1 * cc) : 0.f;
+#pragma unroll
+      for (int cc = 0; cc < NC; ++cc)
+#pragma unroll
+        for (int q = 0; q < LQ; ++q) fma4(&tr[4 * q], xv[cc], __ldg(q2 + (j + cc) * LQ + q));
+    }
+    for (; j < n2; ++j) {
+      const float x = valid ? ldx(xp, (int64_t)n1 * j) : 0.f;
+#pragma unroll
+      for (int q = 0; q < LQ; ++q) fma4(&tr[4 * q], x, __ldg(q2 + j * LQ + q));
+    }
+    __syncwarp();  // the previous block's T has been read
+#pragma unroll
+    for (int q = 0; q < LQ; ++q)
+      *reinterpret_cast<float4*>(&Tw[lane * LP + 4 * q]) =
+          make_float4(tr[4 * q], tr[4 * q + 1], tr[4 * q + 2], tr[4 * q + 3]);
+    __syncwarp();
+    }
+    const int ni = min(32, n1 - 32 * rb);
+    for (int ii = 0; ii < ni; ++ii) {
+      const float* q1r = q1 + (size_t)(32 * rb + ii) * l1p;
+      const float4* trow = reinterpret_cast<const float4*>(Tw + ii * LP);
+#pragma unroll
+      for (int m = 0; m < LQ; ++m) {
+        const int p = lane + 32 * m;
+        if (p < npairs) fma4(c[m], __ldg(q1r + p / LQ), trow[p % LQ]);
       }
+    }
+  }
+  float* Ct = it.C + (int64_t)t * l1 * l2;
+#pragma unroll
+  for (int m = 0; m < LQ; ++m) {
+    const int p = lane + 32 * m;
+    if (p < npairs) {
+      const int a = p / LQ, b0 = 4 * (p % LQ);
+#pragma unroll
+      for (int e = 0; e < 4; ++e)
+        if (b0 + e < l2) Ct[a + l1 * (b0 + e)] = c[m][e];
     }
   }
 }
 
 template <class XT>
 __global__ void __launch_bounds__(kBT, 2)
-    batch_core_kernel(const TbItem* __restrict__ items, const TbTile* __restrict__ tiles,
-                      int ntiles, int* counter, int pitch, int Lp, int n1max8, int n2max) {
-  extern __shared__ __align__(16) float bsm[];
-  float* Xs = bsm;
-  float* Q1s = Xs + kJB * pitch;
-  float* Q2s = Q1s + n1max8 * Lp;
-  float* Ts = Q2s + n2max * Lp;
-  __shared__ int s_tile;
+    batch_core_kernel(const TbItem* __restrict__ items, const SkUnit* __restrict__ units,
+                      int nunits, int* counter) {
+  __shared__ __align__(16) float tw[kBT / 32][32 * 4 * 8];
+  const int lane = threadIdx.x & 31;
+  float* Tw = tw[threadIdx.x >> 5];
   for (;;) {
-    const int ti = next_tile(counter, &s_tile);
-    if (ti >= ntiles) break;
-    const TbTile tile = tiles[ti];
-    const TbItem& it = items[tile.item];
-    switch ((it.n[0] + 31) >> 5) {
-      case 1: core_tile<XT, 1>(it, tile, Xs, Q1s, Q2s, Ts, pitch, Lp); break;
-      case 2: core_tile<XT, 2>(it, tile, Xs, Q1s, Q2s, Ts, pitch, Lp); break;
-      case 3: core_tile<XT, 3>(it, tile, Xs, Q1s, Q2s, Ts, pitch, Lp); break;
-      case 4: core_tile<XT, 4>(it, tile, Xs, Q1s, Q2s, Ts, pitch, Lp); break;
-      case 5: core_tile<XT, 5>(it, tile, Xs, Q1s, Q2s, Ts, pitch, Lp); break;
-      case 6: core_tile<XT, 6>(it, tile, Xs, Q1s, Q2s, Ts, pitch, Lp); break;
-      case 7: core_tile<XT, 7>(it, tile, Xs, Q1s, Q2s, Ts, pitch, Lp); break;
-      default: core_tile<XT, 8>(it, tile, Xs, Q1s, Q2s, Ts, pitch, Lp); break;
+    const int ui = warp_next(counter, lane);
+    if (ui >= nunits) break;
+    const SkUnit u = units[ui];
+    const TbItem& it = items[u.item];
+    switch ((it.l[1] + 3) >> 2) {
+      case 1: core_unit<XT, 1>(it, u.t0, lane, Tw); break;
+      case 2: core_unit<XT, 2>(it, u.t0, lane, Tw); break;
+      case 3: core_unit<XT, 3>(it, u.t0, lane, Tw); break;
+      case 4: core_unit<XT, 4>(it, u.t0, lane, Tw); break;
+      case 5: core_unit<XT, 5>(it, u.t0, lane, Tw); break;
+      case 6: core_unit<XT, 6>(it, u.t0, lane, Tw); break;
+      case 7: core_unit<XT, 7>(it, u.t0, lane, Tw); break;
+      default: core_unit<XT, 8>(it, u.t0, lane, Tw); break;
     }
   }
 }
@@ -715,8 +1047,10 @@ struct TbPlan {
   // device state
   char* arena = nullptr;
   TbItem* d_items = nullptr;
-  TbTile* d_tiles = nullptr;
-  int ntiles = 0;
+  SkUnit* d_sunits = nullptr;  // sketch units (rows and columns)
+  int nsunits = 0;
+  SkUnit* d_cunits = nullptr;  // core units (one slab each)
+  int ncunits = 0;
   TbTile* d_rtiles = nullptr;  // residual tiles: about kResidUnits warp units each
   int nrtiles = 0;
   int* d_counters = nullptr;  // 3
@@ -730,12 +1064,12 @@ struct TbPlan {
   float* y_begin = nullptr;
   size_t y_bytes = 0;
   double* acc_begin = nullptr;
-  int pitch = 0, Lp = 0, Rp = 0, n1max = 0, n1max8 = 0, n2max = 0, lmax = 0;
-  size_t sm_sketch = 0, sm_core = 0, sm_resid = 0, sm_gram = 0, sm_prep = 0, sm_finish = 0;
+  int n1max = 0, n2max = 0, lmax = 0;
+  size_t sm_resid = 0, sm_gram = 0, sm_prep = 0, sm_finish = 0;
   bool gram_f64 = true;
   bool resid_wide = false;  // some r_2 > 16
-  int grid_persist = 0, grid_resid = 0;
-  int slabs_per_tile = 0;
+  int grid_sketch = 0, grid_core = 0, grid_resid = 0;
+  int slabs_per_unit = 0;
   std::vector<TbItem> h_items;
   cudaGraphExec_t exec = nullptr;
   int kernels_per_run = 0;
@@ -769,27 +1103,37 @@ bool same_signature(const TbPlan& p, krp_dtype xt, int count, const krp_tucker_i
   return true;
 }
 
-void build_tiles(const std::vector<TbItem>& items, int spt, std::vector<TbTile>& tiles) {
-  tiles.clear();
+// Sketch units with `spu` slabs each: for every tensor and slab group, its
+// row units then its column units (adjacent, so the column units find the
+// slabs in L2); groups ordered by work, largest first.
+void build_sketch_units(const std::vector<TbItem>& items, int spu, std::vector<SkUnit>& units) {
+  struct Group { int item, t0, t1; int64_t work; };
+  std::vector<Group> groups;
   for (int b = 0; b < (int)items.size(); ++b) {
-    const int n3 = items[b].n[2];
-    for (int t0 = 0; t0 < n3; t0 += spt) tiles.push_back(TbTile{b, t0, std::min(n3, t0 + spt), 0});
+    const TbItem& it = items[b];
+    for (int t0 = 0; t0 < it.n[2]; t0 += spu) {
+      const int t1 = std::min(it.n[2], t0 + spu);
+      groups.push_back(Group{b, t0, t1, (int64_t)it.n[0] * it.n[1] * (t1 - t0)});
+    }
   }
-  // largest work first: n1 * n2 * slabs
-  std::stable_sort(tiles.begin(), tiles.end(), [&](const TbTile& a, const TbTile& c) {
-    const int64_t wa = (int64_t)items[a.item].n[0] * items[a.item].n[1] * (a.t1 - a.t0);
-    const int64_t wc = (int64_t)items[c.item].n[0] * items[c.item].n[1] * (c.t1 - c.t0);
-    return wa > wc;
-  });
+  std::stable_sort(groups.begin(), groups.end(),
+                   [](const Group& x, const Group& y) { return x.work > y.work; });
+  units.clear();
+  for (const Group& g : groups) {
+    const TbItem& it = items[g.item];
+    for (int rb = 0; rb < (it.n[0] + 31) / 32; ++rb) units.push_back(SkUnit{g.item, rb, g.t0, g.t1});
+    for (int jb = 0; jb < (it.n[1] + 31) / 32; ++jb)
+      units.push_back(SkUnit{g.item, kUnitCols | jb, g.t0, g.t1});
+  }
 }
 
 void launch_sketch(const TbPlan& P) {
   if (P.xt == KRP_F32)
-    batch_sketch_kernel<float><<<P.grid_persist, kBT, P.sm_sketch, stream()>>>(
-        P.d_items, P.d_tiles, P.ntiles, P.d_counters + 0, P.pitch, P.Lp, P.n1max8, P.n2max);
+    batch_sketch_kernel<float><<<P.grid_sketch, kBT, 0, stream()>>>(P.d_items, P.d_sunits,
+                                                                     P.nsunits, P.d_counters + 0);
   else
-    batch_sketch_kernel<__nv_bfloat16><<<P.grid_persist, kBT, P.sm_sketch, stream()>>>(
-        P.d_items, P.d_tiles, P.ntiles, P.d_counters + 0, P.pitch, P.Lp, P.n1max8, P.n2max);
+    batch_sketch_kernel<__nv_bfloat16><<<P.grid_sketch, kBT, 0, stream()>>>(
+        P.d_items, P.d_sunits, P.nsunits, P.d_counters + 0);
   check_launch("batch_sketch");
 }
 
@@ -812,17 +1156,21 @@ void enqueue_all(TbPlan& P, int* status) {
   KRP_CUDA_CHECK(cudaMemsetAsync(P.y_begin, 0, P.y_bytes, stream()));
   KRP_CUDA_CHECK(cudaMemsetAsync(P.acc_begin, 0, sizeof(double) * 2 * P.count, stream()));
   launch_gen_factors_batch(P.d_fjobs, P.d_fstart, 3 * P.count, P.fblocks);
-  ++nk;
+  batch_rows_kernel<<<dim3(P.count, 3), 256, 0, stream()>>>(P.d_items, 0);
+  check_launch("batch_rows");
+  nk += 2;
   launch_sketch(P);
   ++nk;
   qr_householder_launch(P.d_qjobs, 3 * P.count, status);
-  ++nk;
+  batch_rows_kernel<<<dim3(P.count, 3), 256, 0, stream()>>>(P.d_items, 1);
+  check_launch("batch_rows");
+  nk += 2;
   if (P.xt == KRP_F32)
-    batch_core_kernel<float><<<P.grid_persist, kBT, P.sm_core, stream()>>>(
-        P.d_items, P.d_tiles, P.ntiles, P.d_counters + 1, P.pitch, P.Lp, P.n1max8, P.n2max);
+    batch_core_kernel<float><<<P.grid_core, kBT, 0, stream()>>>(P.d_items, P.d_cunits, P.ncunits,
+                                                                P.d_counters + 1);
   else
-    batch_core_kernel<__nv_bfloat16><<<P.grid_persist, kBT, P.sm_core, stream()>>>(
-        P.d_items, P.d_tiles, P.ntiles, P.d_counters + 1, P.pitch, P.Lp, P.n1max8, P.n2max);
+    batch_core_kernel<__nv_bfloat16><<<P.grid_core, kBT, 0, stream()>>>(
+        P.d_items, P.d_cunits, P.ncunits, P.d_counters + 1);
   check_launch("batch_core");
   batch_core_finish_kernel<<<P.count, 256, P.sm_finish, stream()>>>(P.d_items);
   check_launch("batch_core_finish");
@@ -888,6 +1236,13 @@ std::unique_ptr<TbPlan> build_plan(Ctx* c, krp_dtype xt, int count, const krp_tu
     lm[b] = lmx;
     for (int m = 0; m < 3; ++m) {
       add((size_t)it.dims[m] * lmx, 4);       // om
+      add((size_t)it.dims[m] * (lmx + 3), 4);     // orow
+      add((size_t)it.dims[m] * (l[m] + 3), 4);    // qrow
+      if (xt == KRP_BF16) {
+        const size_t np = (size_t)((it.dims[m] + 15) / 16) * 16;
+        if (m < 2) add(np * 8 * ((lmx + 7) / 8), 2);   // ot
+        if (m == 1) add(3 * np * 8 * ((l[m] + 7) / 8), 2);  // q2t
+      }
       add((size_t)it.dims[m] * lmx, 4);       // Y (added separately below too)
       add((size_t)it.dims[m] * l[m], 8);      // Q
       add((size_t)it.dims[m] * l[m], 8);      // QR work
@@ -908,9 +1263,13 @@ std::unique_ptr<TbPlan> build_plan(Ctx* c, krp_dtype xt, int count, const krp_tu
   add((size_t)3 * count, sizeof(EigJob));
   add((size_t)count, 8);  // rel
   add(3, 4);              // counters
-  int64_t total_slabs = 0;
-  for (int b = 0; b < count; ++b) total_slabs += items[b].dims[2];
-  add((size_t)total_slabs, sizeof(TbTile));
+  int64_t total_slabs = 0, max_sunits = 0;
+  for (int b = 0; b < count; ++b) {
+    total_slabs += items[b].dims[2];
+    max_sunits += (int64_t)items[b].dims[2] * ((items[b].dims[0] + 31) / 32 + (items[b].dims[1] + 31) / 32);
+  }
+  add((size_t)max_sunits, sizeof(SkUnit));
+  add((size_t)total_slabs, sizeof(SkUnit));
   add((size_t)total_slabs, sizeof(TbTile));
   KRP_CUDA_CHECK(cudaStreamCreateWithFlags(&P->cs, cudaStreamNonBlocking));
   KRP_CUDA_CHECK(cudaEventCreateWithFlags(&P->ev_in, cudaEventDisableTiming));
@@ -943,6 +1302,16 @@ std::unique_ptr<TbPlan> build_plan(Ctx* c, krp_dtype xt, int count, const krp_tu
       it.l[m] = src.ranks[m] + oversample;
       it.r[m] = trunc ? src.ranks[m] : it.l[m];
       it.om[m] = carve<float>(p, (size_t)it.n[m] * it.lm);
+      it.orow[m] = carve<float>(p, (size_t)it.n[m] * (4 * ((it.lm + 3) / 4)));
+      it.qrow[m] = carve<float>(p, (size_t)it.n[m] * (4 * ((it.l[m] + 3) / 4)));
+      if (m < 2) {
+        it.np16[m] = (it.n[m] + 15) / 16 * 16;
+        it.ot[m] = xt == KRP_BF16 ? carve<__nv_bfloat16>(p, (size_t)it.np16[m] * 8 * ((it.lm + 7) / 8))
+                                  : nullptr;
+      }
+      if (m == 1)
+        it.q2t = xt == KRP_BF16 ? carve<__nv_bfloat16>(p, (size_t)3 * it.np16[1] * 8 * ((it.l[1] + 7) / 8))
+                                : nullptr;
       it.Q[m] = carve<double>(p, (size_t)it.n[m] * it.l[m]);
       double* work = carve<double>(p, (size_t)it.n[m] * it.l[m]);
       it.S[m] = carve<double>(p, (size_t)it.l[m] * it.l[m]);
@@ -988,7 +1357,8 @@ std::unique_ptr<TbPlan> build_plan(Ctx* c, krp_dtype xt, int count, const krp_tu
   P->d_ejobs = carve<EigJob>(p, (size_t)3 * count);
   P->d_rel = carve<double>(p, count);
   P->d_counters = carve<int>(p, 3);
-  P->d_tiles = carve<TbTile>(p, (size_t)total_slabs);
+  P->d_sunits = carve<SkUnit>(p, (size_t)max_sunits);
+  P->d_cunits = carve<SkUnit>(p, (size_t)total_slabs);
   P->d_rtiles = carve<TbTile>(p, (size_t)total_slabs);
   KRP_REQUIRE((size_t)(p - P->arena) <= bytes, "batch plan arena overflow");
   P->fblocks = fstart.back();
@@ -1003,15 +1373,22 @@ std::unique_ptr<TbPlan> build_plan(Ctx* c, krp_dtype xt, int count, const krp_tu
                                  cudaMemcpyHostToDevice, s));
   KRP_CUDA_CHECK(cudaMemcpyAsync(P->d_ejobs, ej.data(), sizeof(EigJob) * ej.size(),
                                  cudaMemcpyHostToDevice, s));
-  // shared-memory shapes
-  P->n1max8 = (P->n1max + 7) & ~7;
-  P->pitch = ((P->n1max + 31) & ~31) + 4;
-  P->Lp = (P->lmax + 3) & ~3;
-  P->Rp = std::max(1, rmax);
-  P->sm_sketch = sizeof(float) * ((size_t)kJB * P->pitch + (size_t)P->n1max8 * P->Lp +
-                                  2 * (size_t)P->n2max * P->Lp + 2 * P->Lp);
-  P->sm_core = sizeof(float) * ((size_t)kJB * P->pitch + (size_t)P->n1max8 * P->Lp +
-                                (size_t)P->n2max * P->Lp + (size_t)kJB * P->Lp);
+  // core units: one slab each, largest slabs first
+  {
+    std::vector<SkUnit> cu;
+    cu.reserve((size_t)total_slabs);
+    for (int b = 0; b < count; ++b)
+      for (int t = 0; t < P->h_items[b].n[2]; ++t) cu.push_back(SkUnit{b, 0, t, t + 1});
+    std::stable_sort(cu.begin(), cu.end(), [&](const SkUnit& x, const SkUnit& y) {
+      const TbItem& a = P->h_items[x.item];
+      const TbItem& c = P->h_items[y.item];
+      return (int64_t)a.n[0] * a.n[1] > (int64_t)c.n[0] * c.n[1];
+    });
+    P->ncunits = (int)cu.size();
+    KRP_CUDA_CHECK(cudaMemcpyAsync(P->d_cunits, cu.data(), sizeof(SkUnit) * cu.size(),
+                                   cudaMemcpyHostToDevice, s));
+    KRP_CUDA_CHECK(cudaStreamSynchronize(s));
+  }
   // residual tiles: per tensor, enough slabs for about kResidUnits warp units
   {
     std::vector<TbTile> rt;
@@ -1048,10 +1425,6 @@ std::unique_ptr<TbPlan> build_plan(Ctx* c, krp_dtype xt, int count, const krp_tu
     P->sm_gram = lcube * (P->gram_f64 ? sizeof(double) : sizeof(float));
     P->sm_finish = sizeof(float) * (size_t)n3max * kMaxEll;
   }
-  allow_smem(batch_sketch_kernel<float>, P->sm_sketch);
-  allow_smem(batch_sketch_kernel<__nv_bfloat16>, P->sm_sketch);
-  allow_smem(batch_core_kernel<float>, P->sm_core);
-  allow_smem(batch_core_kernel<__nv_bfloat16>, P->sm_core);
   allow_smem(batch_resid_kernel<float, false>, P->sm_resid);
   allow_smem(batch_resid_kernel<__nv_bfloat16, false>, P->sm_resid);
   allow_smem(batch_resid_kernel<float, true>, P->sm_resid);
@@ -1060,10 +1433,14 @@ std::unique_ptr<TbPlan> build_plan(Ctx* c, krp_dtype xt, int count, const krp_tu
   allow_smem(batch_gram_kernel<float>, P->sm_gram);
   allow_smem(batch_core_finish_kernel, P->sm_finish);
   allow_smem(batch_resid_prep_kernel, P->sm_prep);
-  int occ = 1;
-  KRP_CUDA_CHECK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-      &occ, batch_sketch_kernel<float>, kBT, P->sm_sketch));
-  P->grid_persist = std::max(1, occ) * c->num_sms;
+  auto grid_of = [&](auto k0, auto k1) {
+    int o0 = 1, o1 = 1;
+    KRP_CUDA_CHECK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o0, k0, kBT, 0));
+    KRP_CUDA_CHECK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o1, k1, kBT, 0));
+    return std::max(1, std::min(o0, o1)) * c->num_sms;
+  };
+  P->grid_sketch = grid_of(batch_sketch_kernel<float>, batch_sketch_kernel<__nv_bfloat16>);
+  P->grid_core = grid_of(batch_core_kernel<float>, batch_core_kernel<__nv_bfloat16>);
   int occ_r = 1, occ_rb = 1;
   if (P->resid_wide) {
     KRP_CUDA_CHECK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(
@@ -1080,21 +1457,24 @@ std::unique_ptr<TbPlan> build_plan(Ctx* c, krp_dtype xt, int count, const krp_tu
   return P;
 }
 
-// Slabs per work tile: time the sketch phase for a few granularities.
+// Slabs per sketch unit: time the sketch phase for a few granularities
+// (fewer slabs per unit balance better, more slabs issue fewer atomics).
 void autotune(TbPlan& P) {
-  const int cand[] = {1, 2, 4, 8};
-  std::vector<TbTile> tiles;
+  const int cand[] = {2, 4, 8, 16};
+  std::vector<SkUnit> units;
   float best_ms = 1e30f;
-  int best = 1;
+  int best = cand[0];
   cudaEvent_t e0, e1;
   KRP_CUDA_CHECK(cudaEventCreate(&e0));
   KRP_CUDA_CHECK(cudaEventCreate(&e1));
-  // factors for the sketch
+  // factors and their row tables for the sketch
   launch_gen_factors_batch(P.d_fjobs, P.d_fstart, 3 * P.count, P.fblocks);
-  for (int spt : cand) {
-    build_tiles(P.h_items, spt, tiles);
-    P.ntiles = (int)tiles.size();
-    KRP_CUDA_CHECK(cudaMemcpyAsync(P.d_tiles, tiles.data(), sizeof(TbTile) * tiles.size(),
+  batch_rows_kernel<<<dim3(P.count, 3), 256, 0, stream()>>>(P.d_items, 0);
+  check_launch("batch_rows");
+  for (int spu : cand) {
+    build_sketch_units(P.h_items, spu, units);
+    P.nsunits = (int)units.size();
+    KRP_CUDA_CHECK(cudaMemcpyAsync(P.d_sunits, units.data(), sizeof(SkUnit) * units.size(),
                                    cudaMemcpyHostToDevice, stream()));
     float ms_sum = 0.f;
     for (int rep = 0; rep < 2; ++rep) {
@@ -1110,15 +1490,15 @@ void autotune(TbPlan& P) {
     }
     if (ms_sum < best_ms) {
       best_ms = ms_sum;
-      best = spt;
+      best = spu;
     }
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
-  P.slabs_per_tile = best;
-  build_tiles(P.h_items, best, tiles);
-  P.ntiles = (int)tiles.size();
-  KRP_CUDA_CHECK(cudaMemcpyAsync(P.d_tiles, tiles.data(), sizeof(TbTile) * tiles.size(),
+  P.slabs_per_unit = best;
+  build_sketch_units(P.h_items, best, units);
+  P.nsunits = (int)units.size();
+  KRP_CUDA_CHECK(cudaMemcpyAsync(P.d_sunits, units.data(), sizeof(SkUnit) * units.size(),
                                  cudaMemcpyHostToDevice, stream()));
   KRP_CUDA_CHECK(cudaStreamSynchronize(stream()));
 }
@@ -1551,12 +1931,12 @@ void tucker_batched(krp_dtype xt, int count, krp_tucker_item* items, int oversam
     items[b].rel_residual = (flags & KRP_RESIDUAL) ? P->h_rel[b] : -1.0;
 }
 
-int tucker_batched_plan_info(int* slabs_per_tile, int* tiles, int* grid) {
+int tucker_batched_plan_info(int* slabs_per_unit, int* units, int* grid) {
   TbPlan* P = static_cast<TbPlan*>(current()->batch_plan);
   if (!P) return 0;
-  if (slabs_per_tile) *slabs_per_tile = P->slabs_per_tile;
-  if (tiles) *tiles = P->ntiles;
-  if (grid) *grid = P->grid_persist;
+  if (slabs_per_unit) *slabs_per_unit = P->slabs_per_unit;
+  if (units) *units = P->nsunits;
+  if (grid) *grid = P->grid_sketch;
   return 1;
 }
 

@@ -44,7 +44,7 @@ void tucker_pipeline(bool sequential, const void* X, krp_dtype xt, int d, const 
 
 void tucker_batched(krp_dtype xt, int count, krp_tucker_item* items, int oversample,
                     unsigned flags);
-int tucker_batched_plan_info(int* slabs_per_tile, int* tiles, int* grid);
+int tucker_batched_plan_info(int* slabs_per_unit, int* units, int* grid);
 void hankel_batched(krp_dtype bt, int count, krp_hankel_item* items);
 
 void hankel_pipeline(const void* blocks, krp_dtype bt, int m, int n, int s, int r, int ell_r,

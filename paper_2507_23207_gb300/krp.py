@@ -407,7 +407,7 @@ def krp_tucker_rhosvd_batched(ctx: Context, xt: int, items, oversample: int, fla
 def krp_tucker_batch_plan_info(ctx: Context):
     a, b, c = C.c_int(0), C.c_int(0), C.c_int(0)
     ctx.check(ctx.lib.krp_tucker_batch_plan_info(ctx.handle, C.byref(a), C.byref(b), C.byref(c)))
-    return {"slabs_per_tile": a.value, "tiles": b.value, "grid": c.value}
+    return {"slabs_per_unit": a.value, "units": b.value, "grid": c.value}
 
 
 def make_hankel_items(blocks, shapes, seeds, Us, Ss, Vs):

@@ -100,7 +100,7 @@ def test_batched_graph_replay_and_rebuild(ctx):
     flags = K.KRP_TRUNCATE | K.KRP_RESIDUAL
     r1 = K.krp_tucker_rhosvd_batched(ctx, K.KRP_F32, items, P, flags)
     info = K.krp_tucker_batch_plan_info(ctx)
-    assert info["slabs_per_tile"] in (1, 2, 4, 8) and info["tiles"] >= len(SHAPES)
+    assert info["slabs_per_unit"] in (2, 4, 8, 16) and info["units"] >= len(SHAPES)
     def recon(b):
         out = list(ranks[b])
         g = cores[b].cpu().numpy().astype(np.float64).reshape(out[::-1]).T

@@ -55,6 +55,7 @@ struct TbItem {
   // zero outside the matrix.
   __nv_bfloat16* ot[2];
   __nv_bfloat16* q2t;
+  __nv_bfloat16* q1t;  // q1t[p][a * np16[0] + i] = part p of Q1[i, a], a < 32
   int np16[2];       // n1, n2 rounded up to 16
   float* Y[3];       // n_i x lm
   double* Q[3];      // n_i x l_i
@@ -531,6 +532,91 @@ __device__ void core_rows_tc(const TbItem& it, int t, int rb, int lane, float* T
       }
 }
 
+__device__ __forceinline__ void split3(float x, uint32_t& h, uint32_t& m, uint32_t& l) {
+  const __nv_bfloat16 bh = __float2bfloat16_rn(x);
+  const float r = x - __bfloat162float(bh);
+  const __nv_bfloat16 bm = __float2bfloat16_rn(r);
+  const __nv_bfloat16 bl = __float2bfloat16_rn(r - __bfloat162float(bm));
+  h = __bfloat16_as_ushort(bh);
+  m = __bfloat16_as_ushort(bm);
+  l = __bfloat16_as_ushort(bl);
+}
+
+// Core unit of the BF16 form: C_t = Q1^T X_t Q2 for one slab, both
+// contractions on the tensor cores.  Per block of 32 rows i, T = X_t Q2
+// (core_rows_tc) goes to the warp's buffer; then C_t += Q1[block]^T T with
+// M = a (two m-tiles), K = i, N = b, Q1 and T each split into BF16 hi + mid +
+// lo and the six products above 2^-24 accumulated (FP32 accuracy).  NT =
+// ceil(l2 / 8).
+template <int NT>
+__device__ void core_unit_tc(const TbItem& it, int t, int lane, float* Tw) {
+  constexpr int LDT = 8 * NT;
+  const int g = lane >> 2, q = lane & 3;
+  const int n1 = it.n[0], l1 = it.l[0], l2 = it.l[1];
+  const int n1p = it.np16[0];
+  const size_t plane = (size_t)32 * n1p / 2;  // uint32 per part of q1t
+  const uint32_t* q1t = reinterpret_cast<const uint32_t*>(it.q1t);
+  float c[2][NT][4];
+#pragma unroll
+  for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+    for (int nt = 0; nt < NT; ++nt) c[mt][nt][0] = c[mt][nt][1] = c[mt][nt][2] = c[mt][nt][3] = 0.f;
+  const int RB = (n1 + 31) >> 5;
+  for (int rb = 0; rb < RB; ++rb) {
+    __syncwarp();  // the previous block's T has been read
+    core_rows_tc<NT>(it, t, rb, lane, Tw, LDT);
+    __syncwarp();
+#pragma unroll
+    for (int ks = 0; ks < 2; ++ks) {
+      const int ib = 32 * rb + 16 * ks;  // first row i of this K step
+      if (ib >= n1) break;
+      uint32_t a[3][2][4];
+#pragma unroll
+      for (int pl = 0; pl < 3; ++pl)
+#pragma unroll
+        for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+          for (int r = 0; r < 4; ++r) {
+            const int row = 16 * mt + g + 8 * (r & 1), k = ib + 2 * q + 8 * (r >> 1);
+            a[pl][mt][r] = __ldg(q1t + pl * plane + (((size_t)row * n1p + k) >> 1));
+          }
+#pragma unroll
+      for (int nt = 0; nt < NT; ++nt) {
+        uint32_t bh[2], bm[2], bl[2];
+#pragma unroll
+        for (int kk = 0; kk < 2; ++kk) {
+          uint32_t h0, m0, l0, h1, m1, l1_;
+          const float* tp = Tw + (16 * ks + 2 * q + 8 * kk) * LDT + nt * 8 + g;
+          split3(tp[0], h0, m0, l0);
+          split3(tp[LDT], h1, m1, l1_);
+          bh[kk] = h0 | (h1 << 16);
+          bm[kk] = m0 | (m1 << 16);
+          bl[kk] = l0 | (l1_ << 16);
+        }
+#pragma unroll
+        for (int mt = 0; mt < 2; ++mt) {
+          mma16816(c[mt][nt], a[0][mt], bh[0], bh[1]);
+          mma16816(c[mt][nt], a[0][mt], bm[0], bm[1]);
+          mma16816(c[mt][nt], a[1][mt], bh[0], bh[1]);
+          mma16816(c[mt][nt], a[0][mt], bl[0], bl[1]);
+          mma16816(c[mt][nt], a[2][mt], bh[0], bh[1]);
+          mma16816(c[mt][nt], a[1][mt], bm[0], bm[1]);
+        }
+      }
+    }
+  }
+  float* Ct = it.C + (int64_t)t * l1 * l2;
+#pragma unroll
+  for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+    for (int nt = 0; nt < NT; ++nt)
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const int a = 16 * mt + g + 8 * (e >> 1), b = nt * 8 + 2 * q + (e & 1);
+        if (a < l1 && b < l2) Ct[a + l1 * b] = c[mt][nt][e];
+      }
+}
+
 template <class XT, int LQ>
 __device__ __forceinline__ void sketch_unit(const TbItem& it, const SkUnit& u, int lane, float* Xw) {
   if (u.kb >= kUnitCols)
@@ -601,6 +687,21 @@ __global__ void batch_rows_kernel(const TbItem* __restrict__ items, int which) {
     for (int e = threadIdx.x; e < l8 * np; e += blockDim.x) {
       const int k = e / np, i = e % np;
       it.ot[m][e] = __float2bfloat16_rn(k < l && i < n ? it.om[m][i + (int64_t)n * k] : 0.f);
+    }
+  }
+  if (which == 1 && m == 0 && it.q1t) {  // Q1 = hi + mid + lo in BF16, a-major, 32 rows of a
+    const int np = it.np16[0];
+    const size_t plane = (size_t)32 * np;
+    for (int e = threadIdx.x; e < 32 * np; e += blockDim.x) {
+      const int k = e / np, i = e % np;
+      const double v = k < l && i < n ? it.Q[0][i + (int64_t)n * k] : 0.0;
+      const __nv_bfloat16 h = __double2bfloat16(v);
+      const double r1 = v - (double)__bfloat162float(h);
+      const __nv_bfloat16 md = __double2bfloat16(r1);
+      const __nv_bfloat16 lo = __double2bfloat16(r1 - (double)__bfloat162float(md));
+      it.q1t[e] = h;
+      it.q1t[plane + e] = md;
+      it.q1t[2 * plane + e] = lo;
     }
   }
   if (which == 1 && m == 1 && it.q2t) {  // Q2 = hi + mid + lo in BF16
@@ -712,6 +813,14 @@ __global__ void __launch_bounds__(kBT, 2)
     if (ui >= nunits) break;
     const SkUnit u = units[ui];
     const TbItem& it = items[u.item];
+    if constexpr (std::is_same<XT, __nv_bfloat16>::value) {
+      switch ((it.l[1] + 7) >> 3) {
+        case 1: core_unit_tc<1>(it, u.t0, lane, Tw); break;
+        case 2: core_unit_tc<2>(it, u.t0, lane, Tw); break;
+        case 3: core_unit_tc<3>(it, u.t0, lane, Tw); break;
+        default: core_unit_tc<4>(it, u.t0, lane, Tw); break;
+      }
+    } else {
     switch ((it.l[1] + 3) >> 2) {
       case 1: core_unit<XT, 1>(it, u.t0, lane, Tw); break;
       case 2: core_unit<XT, 2>(it, u.t0, lane, Tw); break;
@@ -721,6 +830,7 @@ __global__ void __launch_bounds__(kBT, 2)
       case 6: core_unit<XT, 6>(it, u.t0, lane, Tw); break;
       case 7: core_unit<XT, 7>(it, u.t0, lane, Tw); break;
       default: core_unit<XT, 8>(it, u.t0, lane, Tw); break;
+    }
     }
   }
 }
@@ -1242,6 +1352,7 @@ std::unique_ptr<TbPlan> build_plan(Ctx* c, krp_dtype xt, int count, const krp_tu
         const size_t np = (size_t)((it.dims[m] + 15) / 16) * 16;
         if (m < 2) add(np * 8 * ((lmx + 7) / 8), 2);   // ot
         if (m == 1) add(3 * np * 8 * ((l[m] + 7) / 8), 2);  // q2t
+        if (m == 0) add(3 * np * 32, 2);                     // q1t
       }
       add((size_t)it.dims[m] * lmx, 4);       // Y (added separately below too)
       add((size_t)it.dims[m] * l[m], 8);      // Q
@@ -1309,6 +1420,8 @@ std::unique_ptr<TbPlan> build_plan(Ctx* c, krp_dtype xt, int count, const krp_tu
         it.ot[m] = xt == KRP_BF16 ? carve<__nv_bfloat16>(p, (size_t)it.np16[m] * 8 * ((it.lm + 7) / 8))
                                   : nullptr;
       }
+      if (m == 0)
+        it.q1t = xt == KRP_BF16 ? carve<__nv_bfloat16>(p, (size_t)3 * it.np16[0] * 32) : nullptr;
       if (m == 1)
         it.q2t = xt == KRP_BF16 ? carve<__nv_bfloat16>(p, (size_t)3 * it.np16[1] * 8 * ((it.l[1] + 7) / 8))
                                 : nullptr;

@@ -1271,6 +1271,9 @@ void enqueue_all(TbPlan& P, int* status) {
   nk += 2;
   launch_sketch(P);
   ++nk;
+  // the sketches are short (n <= 256 rows): one CTA per Householder QR keeps
+  // the 3 x count problems in one launch (measured faster than CholeskyQR3
+  // over row blocks, whose nine launches each see tiny problems)
   qr_householder_launch(P.d_qjobs, 3 * P.count, status);
   batch_rows_kernel<<<dim3(P.count, 3), 256, 0, stream()>>>(P.d_items, 1);
   check_launch("batch_rows");
@@ -1733,38 +1736,72 @@ __global__ void hb_corr_kernel(const HbItem* __restrict__ items) {
   }
 }
 
-// P[c + ll q] = sum_{i, a} Psi1[i, c] Psi2[a, c] Q[(a + m i) + ms q]; grid (ll_max, count)
-__global__ void hb_psitq_kernel(const HbItem* __restrict__ items) {
+// P[c + ll q] = sum_{i, a} Psi1[i, c] Psi2[a, c] Q[(a + m i) + ms q]; grid (ll_max, count).
+// The weights w[row] = Psi1[i, c] Psi2[a, c] are formed once per chunk of
+// kHbRows rows in shared memory (FP64), so each term is one FP64 FMA; warp w
+// keeps the sums of columns q = w, w + 8, ... (lr <= 64) in registers.
+constexpr int kHbRows = 2048;
+__global__ void __launch_bounds__(256) hb_psitq_kernel(const HbItem* __restrict__ items) {
+  __shared__ double wsh[kHbRows];
   const HbItem& it = items[blockIdx.y];
   const int c = blockIdx.x;
   if (c >= it.ll) return;
   const int m = it.m, s = it.s, lr = it.lr;
   const int64_t ms = (int64_t)m * s;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-  for (int q = warp; q < lr; q += nw) {
-    double acc = 0.0;
-    for (int64_t row = lane; row < ms; row += 32) {
-      const int a = (int)(row % m), i = (int)(row / m);
-      const double w = (double)it.p1[i + (int64_t)s * c] * (double)it.p2[a + (int64_t)m * c];
-      acc = fma(w, it.Q[row + ms * q], acc);
-    }
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  double acc[8];
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-    if (lane == 0) it.P[c + (int64_t)it.ll * q] = acc;
+  for (int k = 0; k < 8; ++k) acc[k] = 0.0;
+  for (int64_t r0 = 0; r0 < ms; r0 += kHbRows) {
+    const int nr = (int)((ms - r0) < kHbRows ? (ms - r0) : kHbRows);
+    __syncthreads();  // the previous chunk has been read
+    for (int rr = threadIdx.x; rr < nr; rr += blockDim.x) {
+      const int64_t row = r0 + rr;
+      const int a = (int)(row % m), i = (int)(row / m);
+      wsh[rr] = (double)it.p1[i + (int64_t)s * c] * (double)it.p2[a + (int64_t)m * c];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      const int q = warp + 8 * k;
+      if (q < lr) {
+        const double* qc = it.Q + ms * q + r0;
+        for (int rr = lane; rr < nr; rr += 32) acc[k] = fma(wsh[rr], qc[rr], acc[k]);
+      }
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
+    const int q = warp + 8 * k;
+    double v = acc[k];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (lane == 0 && q < lr) it.P[c + (int64_t)it.ll * q] = v;
   }
 }
 
-// W[q + lr col] = (Rp^{-1} Qp^T Z^T)[q, col]: grid (x: column chunks, y: item)
-__global__ void hb_ls_kernel(const HbItem* __restrict__ items) {
+// W[q + lr col] = (Rp^{-1} Qp^T Z^T)[q, col]: grid (x: column chunks, y: item);
+// a CTA's 64 columns of Z are converted to FP64 once, in shared memory.
+constexpr int kHbLsCols = 64;
+__global__ void __launch_bounds__(kHbLsCols) hb_ls_kernel(const HbItem* __restrict__ items) {
+  extern __shared__ double zsh[];  // ll x kHbLsCols
   const HbItem& it = items[blockIdx.y];
   const int ll = it.ll, lr = it.lr;
   const int64_t ns = (int64_t)it.n * it.s;
-  for (int64_t col = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; col < ns;
-       col += (int64_t)gridDim.x * blockDim.x) {
+  for (int64_t c0 = blockIdx.x * (int64_t)kHbLsCols; c0 < ns; c0 += (int64_t)gridDim.x * kHbLsCols) {
+    __syncthreads();  // the previous chunk's columns have been read
+    for (int c = 0; c < ll; ++c) {
+      const int64_t col = c0 + threadIdx.x;
+      zsh[c * kHbLsCols + threadIdx.x] = col < ns ? (double)it.Z[col + ns * c] : 0.0;
+    }
+    __syncthreads();
+    const int64_t col = c0 + threadIdx.x;
+    if (col >= ns) continue;
     double* w = it.W + (int64_t)lr * col;
     for (int q = 0; q < lr; ++q) {
       double acc = 0.0;
-      for (int c = 0; c < ll; ++c) acc = fma(it.Qp[c + (int64_t)ll * q], (double)it.Z[col + ns * c], acc);
+      const double* qp = it.Qp + (int64_t)ll * q;
+      for (int c = 0; c < ll; ++c) acc = fma(qp[c], zsh[c * kHbLsCols + threadIdx.x], acc);
       w[q] = acc;
     }
     for (int q = lr - 1; q >= 0; --q) {
@@ -1775,19 +1812,35 @@ __global__ void hb_ls_kernel(const HbItem* __restrict__ items) {
   }
 }
 
-// Sg = W W^T (lr x lr, FP64); one CTA per item
-__global__ void hb_gram_kernel(const HbItem* __restrict__ items) {
+// Sg = W W^T (lr x lr, FP64) over column chunks: grid (x: chunks of
+// kHbGramCols columns, y: item); a CTA stages its W columns in shared memory
+// and adds its partial Gram (pairs p <= q) atomically into Sg, which
+// hb_zero_kernel has cleared.
+constexpr int kHbGramCols = 64;
+__global__ void hb_zero_kernel(const HbItem* __restrict__ items) {
   const HbItem& it = items[blockIdx.x];
+  for (int e = threadIdx.x; e < it.lr * it.lr; e += blockDim.x) it.Sg[e] = 0.0;
+}
+__global__ void hb_gram_kernel(const HbItem* __restrict__ items) {
+  extern __shared__ double wt[];  // lr x kHbGramCols
+  const HbItem& it = items[blockIdx.y];
   const int lr = it.lr;
   const int64_t ns = (int64_t)it.n * it.s;
-  for (int pq = threadIdx.x; pq < lr * lr; pq += blockDim.x) {
-    const int p = pq % lr, q = pq / lr;
-    if (p > q) continue;
+  const int64_t c0 = (int64_t)blockIdx.x * kHbGramCols;
+  if (c0 >= ns) return;
+  const int nc = (int)((ns - c0) < kHbGramCols ? (ns - c0) : kHbGramCols);
+  for (int e = threadIdx.x; e < lr * nc; e += blockDim.x) wt[e] = it.W[e + (int64_t)lr * c0];
+  __syncthreads();
+  const int npairs = lr * (lr + 1) / 2;
+  for (int pq = threadIdx.x; pq < npairs; pq += blockDim.x) {
+    int q = (int)((sqrtf(8.f * pq + 1.f) - 1.f) * 0.5f);
+    while (q * (q + 1) / 2 > pq) --q;
+    while ((q + 1) * (q + 2) / 2 <= pq) ++q;
+    const int p = pq - q * (q + 1) / 2;
     double acc = 0.0;
-    for (int64_t col = 0; col < ns; ++col)
-      acc = fma(it.W[p + (int64_t)lr * col], it.W[q + (int64_t)lr * col], acc);
-    it.Sg[p + lr * q] = acc;
-    it.Sg[q + lr * p] = acc;
+    for (int col = 0; col < nc; ++col) acc = fma(wt[p + lr * col], wt[q + lr * col], acc);
+    atomicAdd(&it.Sg[p + lr * q], acc);
+    if (p != q) atomicAdd(&it.Sg[q + lr * p], acc);
   }
 }
 
@@ -1829,13 +1882,18 @@ struct HbPlan {
   int64_t fblocks = 0;
   QrJob* d_qy = nullptr;
   QrJob* d_qp = nullptr;
+  void* cqr_mem[2] = {nullptr, nullptr};
+  CqrJobsPlan cqr_y, cqr_p;
   EigJob* d_ej = nullptr;
-  int gx_blockmul = 1, gx_corr = 1, gx_ls = 1, gx_out = 1, llmax = 1, lrmax = 1;
+  int gx_blockmul = 1, gx_corr = 1, gx_ls = 1, gx_out = 1, gx_gram = 1, llmax = 1, lrmax = 1;
+  size_t sm_ls = 0, sm_gram = 0;
   int kernels_per_run = 0;
   cudaGraphExec_t exec = nullptr;
   cudaStream_t cs = nullptr;
   cudaEvent_t ev_in = nullptr, ev_out = nullptr;
   ~HbPlan() {
+    for (void* m : cqr_mem)
+      if (m) cudaFree(m);
     if (exec) cudaGraphExecDestroy(exec);
     if (ev_in) cudaEventDestroy(ev_in);
     if (ev_out) cudaEventDestroy(ev_out);
@@ -1863,18 +1921,20 @@ void hb_enqueue(HbPlan& P, int* status) {
   check_launch("hb_blockmul");
   hb_corr_kernel<<<dim3(P.gx_corr, P.count, 2), 256, 0, stream()>>>(P.d_items);
   check_launch("hb_corr");
-  qr_householder_launch(P.d_qy, P.count, status);
+  nk += cholqr3_jobs_launch(P.cqr_y, status);
   hb_psitq_kernel<<<dim3(P.llmax, P.count), 256, 0, stream()>>>(P.d_items);
   check_launch("hb_psitq");
-  qr_householder_launch(P.d_qp, P.count, status);
-  hb_ls_kernel<<<dim3(P.gx_ls, P.count), 256, 0, stream()>>>(P.d_items);
+  nk += cholqr3_jobs_launch(P.cqr_p, status);
+  hb_ls_kernel<<<dim3(P.gx_ls, P.count), kHbLsCols, P.sm_ls, stream()>>>(P.d_items);
   check_launch("hb_ls");
-  hb_gram_kernel<<<P.count, 256, 0, stream()>>>(P.d_items);
+  hb_zero_kernel<<<P.count, 256, 0, stream()>>>(P.d_items);
+  check_launch("hb_zero");
+  hb_gram_kernel<<<dim3(P.gx_gram, P.count), 256, P.sm_gram, stream()>>>(P.d_items);
   check_launch("hb_gram");
   eig_launch(P.d_ej, P.count, P.lrmax, status);
   hb_out_kernel<<<dim3(P.gx_out, P.count), 256, 0, stream()>>>(P.d_items);
   check_launch("hb_out");
-  nk += 9;
+  nk += 8;
   P.kernels_per_run = nk;
 }
 
@@ -1974,14 +2034,27 @@ std::unique_ptr<HbPlan> hb_build(Ctx* c, krp_dtype bt, int count, const krp_hank
   P->fblocks = fstart.back();
   P->gx_blockmul = chunks_for(maxbm);
   P->gx_corr = chunks_for(maxcorr);
-  P->gx_ls = chunks_for(maxns);
+  P->gx_ls = (int)std::min<int64_t>((maxns + kHbLsCols - 1) / kHbLsCols, 1024);
   P->gx_out = chunks_for(maxout);
+  P->gx_gram = (int)((maxns + kHbGramCols - 1) / kHbGramCols);
+  {
+    P->sm_ls = sizeof(double) * (size_t)P->llmax * kHbLsCols;
+    P->sm_gram = sizeof(double) * (size_t)P->lrmax * kHbGramCols;
+    KRP_CUDA_CHECK(cudaFuncSetAttribute(hb_ls_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)P->sm_ls));
+    KRP_CUDA_CHECK(cudaFuncSetAttribute(hb_gram_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)P->sm_gram));
+  }
   cudaStream_t s = c->stream;
   KRP_CUDA_CHECK(cudaMemcpyAsync(P->d_items, hi.data(), sizeof(HbItem) * count, cudaMemcpyHostToDevice, s));
   KRP_CUDA_CHECK(cudaMemcpyAsync(P->d_fjobs, fj.data(), sizeof(BatchFactorJob) * fj.size(), cudaMemcpyHostToDevice, s));
   KRP_CUDA_CHECK(cudaMemcpyAsync(P->d_fstart, fstart.data(), sizeof(int64_t) * fstart.size(), cudaMemcpyHostToDevice, s));
   KRP_CUDA_CHECK(cudaMemcpyAsync(P->d_qy, qy.data(), sizeof(QrJob) * count, cudaMemcpyHostToDevice, s));
   KRP_CUDA_CHECK(cudaMemcpyAsync(P->d_qp, qp.data(), sizeof(QrJob) * count, cudaMemcpyHostToDevice, s));
+  KRP_CUDA_CHECK(cudaMalloc(&P->cqr_mem[0], cholqr3_jobs_bytes(qy.data(), count)));
+  KRP_CUDA_CHECK(cudaMalloc(&P->cqr_mem[1], cholqr3_jobs_bytes(qp.data(), count)));
+  P->cqr_y = cholqr3_jobs_setup(qy.data(), count, P->cqr_mem[0], s);
+  P->cqr_p = cholqr3_jobs_setup(qp.data(), count, P->cqr_mem[1], s);
   KRP_CUDA_CHECK(cudaMemcpyAsync(P->d_ej, ej.data(), sizeof(EigJob) * count, cudaMemcpyHostToDevice, s));
   KRP_CUDA_CHECK(cudaStreamSynchronize(s));
   return P;

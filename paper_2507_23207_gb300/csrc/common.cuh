@@ -173,6 +173,22 @@ struct EigJob {
 // they can be captured in a CUDA graph); maxl bounds every job's l.
 void eig_launch(const EigJob* d_jobs, int count, int maxl, int* status);
 void qr_householder_launch(const QrJob* d_jobs, int count, int* status);
+// Shifted CholeskyQR3 (FP64; the Householder result for full-rank inputs) of
+// many jobs with l <= 64 in one set of launches over a device job array:
+// cholqr3_jobs_bytes gives the device memory the caller provides,
+// cholqr3_jobs_setup fills it (one host-to-device copy, before any capture)
+// and cholqr3_jobs_launch enqueues three memsets and nine kernels
+// (graph-capturable) and returns the number of kernels.
+struct CqrJobsPlan {
+  void* d_jobs = nullptr;
+  int count = 0;
+  int64_t maxm = 0, total_rows = 0;
+  double* g_all = nullptr;
+  size_t g_count = 0;
+};
+size_t cholqr3_jobs_bytes(const QrJob* jobs, int count);
+CqrJobsPlan cholqr3_jobs_setup(const QrJob* jobs, int count, void* dmem, cudaStream_t st);
+int cholqr3_jobs_launch(const CqrJobsPlan& plan, int* status);
 void sym_eig_top_f64(const double* const* S, const int* l, const int* r,
                      double* const* U, int count, int* status,
                      double* const* evals = nullptr);

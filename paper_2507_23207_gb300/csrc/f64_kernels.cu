@@ -854,15 +854,21 @@ __device__ __forceinline__ double refill_value(int64_t r, int j) {
   return (static_cast<double>(h) + 0.5) * 0x1p-32 - 0.5;
 }
 
-// Up to kCqrMaxBatch problems passed to the kernels by value.
+// Up to kCqrMaxBatch problems passed to the kernels by value, or any number
+// as a job array in device memory.
 constexpr int kCqrMaxBatch = 8;
 struct CqrBatch {
   CqrJob job[kCqrMaxBatch];
 };
+struct CqrJobArray {
+  const CqrJob* job;
+};
+__device__ __forceinline__ CqrJob job_at(const CqrBatch& b, int i) { return b.job[i]; }
+__device__ __forceinline__ CqrJob job_at(const CqrJobArray& b, int i) { return b.job[i]; }
 
-template <bool FROM_INPUT>
-__global__ void __launch_bounds__(256) cqr_gram_kernel(const CqrBatch jobs, int* status) {
-  const CqrJob job = jobs.job[blockIdx.y];
+template <bool FROM_INPUT, class JOBS>
+__global__ void __launch_bounds__(256) cqr_gram_kernel(const JOBS jobs, int* status) {
+  const CqrJob job = job_at(jobs, blockIdx.y);
   const int64_t r0 = (int64_t)blockIdx.x * kCqrRows;
   if (r0 >= job.m) return;
   const int l = job.l;
@@ -913,8 +919,9 @@ __global__ void __launch_bounds__(256) cqr_gram_kernel(const CqrBatch jobs, int*
 // R[j, i] = A[j, i] / sqrt(d_j) in one parallel pass at the end (sqrt off the
 // dependent chain).
 constexpr int kCholThreads = 128;
-__global__ void __launch_bounds__(kCholThreads) cqr_chol_kernel(const CqrBatch jobs, int pass) {
-  const CqrJob job = jobs.job[blockIdx.x];
+template <class JOBS>
+__global__ void __launch_bounds__(kCholThreads) cqr_chol_kernel(const JOBS jobs, int pass) {
+  const CqrJob job = job_at(jobs, blockIdx.x);
   const int l = job.l;
   __shared__ double A[kCqrMaxL][kCqrMaxL + 1];
   __shared__ double diag0[kCqrMaxL], rsq[kCqrMaxL], sq[kCqrMaxL];
@@ -1040,10 +1047,10 @@ template <int TPR>
 constexpr size_t solve_smem() {
   return sizeof(double) * ((size_t)kCqrMaxL * kCqrMaxL + (size_t)solve_rows<TPR>() * kSolveRowPitch + kCqrMaxL);
 }
-template <bool FROM_INPUT, bool TO_Q, int TPR>
-__global__ void __launch_bounds__(kSolveThreads) cqr_solve_kernel(const CqrBatch jobs, int pass) {
+template <bool FROM_INPUT, bool TO_Q, int TPR, class JOBS>
+__global__ void __launch_bounds__(kSolveThreads) cqr_solve_kernel(const JOBS jobs, int pass) {
   constexpr int ROWS = solve_rows<TPR>();
-  const CqrJob job = jobs.job[blockIdx.y];
+  const CqrJob job = job_at(jobs, blockIdx.y);
   const int l = job.l;
   const int64_t r0 = (int64_t)blockIdx.x * ROWS;
   if (r0 >= job.m) return;
@@ -1115,8 +1122,8 @@ int solve_tpr(int64_t total_rows) {
   return (total_rows * 8 / 32 <= parts) ? 8 : 4;
 }
 
-template <int TPR>
-void cqr_solve_launch(const CqrBatch& batch, int nq, int64_t maxm, int pass, cudaStream_t st) {
+template <int TPR, class JOBS>
+void cqr_solve_launch(const JOBS& batch, int nq, int64_t maxm, int pass, cudaStream_t st) {
   const dim3 gs((unsigned)((maxm + solve_rows<TPR>() - 1) / solve_rows<TPR>()), (unsigned)nq);
   const size_t sm = solve_smem<TPR>();
   auto run = [&](auto kern) {
@@ -1124,13 +1131,14 @@ void cqr_solve_launch(const CqrBatch& batch, int nq, int64_t maxm, int pass, cud
     kern<<<gs, kSolveThreads, sm, st>>>(batch, pass);
   };
   if (pass == 0)
-    run(cqr_solve_kernel<true, false, TPR>);
+    run(cqr_solve_kernel<true, false, TPR, JOBS>);
   else if (pass == 1)
-    run(cqr_solve_kernel<false, false, TPR>);
+    run(cqr_solve_kernel<false, false, TPR, JOBS>);
   else
-    run(cqr_solve_kernel<false, true, TPR>);
+    run(cqr_solve_kernel<false, true, TPR, JOBS>);
 }
-void cqr_solve_any(const CqrBatch& batch, int nq, int64_t maxm, int64_t total_rows, int pass,
+template <class JOBS>
+void cqr_solve_any(const JOBS& batch, int nq, int64_t maxm, int64_t total_rows, int pass,
                    cudaStream_t st) {
   if (solve_tpr(total_rows) == 8)
     cqr_solve_launch<8>(batch, nq, maxm, pass, st);
@@ -1253,6 +1261,74 @@ void cholqr3_launch(const CqrBatch& batch, int nq, int64_t maxm, int* status) {
     cqr_solve_any(batch, nq, maxm, total_rows, pass, stream());
     check_launch("cholqr_solve_f64");
   }
+}
+
+// Shifted CholeskyQR3 of many small jobs in one set of launches (device job
+// array): layout of the caller's device block is [CqrJob x count][G: sum l^2]
+// [Rk: sum 3 l^2][defmask x count]; every job has l <= 64.
+size_t cholqr3_jobs_bytes(const QrJob* jobs, int count) {
+  size_t d = 0;
+  for (int b = 0; b < count; ++b) d += 4 * (size_t)jobs[b].l * jobs[b].l;
+  return ((sizeof(CqrJob) * count + 255) & ~size_t(255)) + sizeof(double) * d +
+         sizeof(unsigned long long) * count + 256;
+}
+
+CqrJobsPlan cholqr3_jobs_setup(const QrJob* jobs, int count, void* dmem, cudaStream_t st) {
+  CqrJobsPlan pl{};
+  pl.count = count;
+  pl.d_jobs = dmem;
+  char* p = static_cast<char*>(dmem) + ((sizeof(CqrJob) * count + 255) & ~size_t(255));
+  double* g = reinterpret_cast<double*>(p);
+  size_t gsum = 0;
+  for (int b = 0; b < count; ++b) gsum += (size_t)jobs[b].l * jobs[b].l;
+  double* rk = g + gsum;
+  size_t rsum = 0;
+  for (int b = 0; b < count; ++b) rsum += 3 * (size_t)jobs[b].l * jobs[b].l;
+  unsigned long long* mask = reinterpret_cast<unsigned long long*>(rk + rsum);
+  std::vector<CqrJob> h(count);
+  size_t go = 0, ro = 0;
+  for (int b = 0; b < count; ++b) {
+    const QrJob& j = jobs[b];
+    KRP_REQUIRE(j.m >= j.l && j.l >= 1 && j.l <= kCqrMaxL, "CholeskyQR3 job needs m >= l, 1 <= l <= %d",
+                kCqrMaxL);
+    CqrJob& q = h[b];
+    q.Y = j.Y;
+    q.Y64 = j.Y64;
+    q.W = j.work;
+    q.Q = j.Q;
+    q.R = j.R;
+    q.m = j.m;
+    q.l = j.l;
+    q.G = g + go;
+    q.Rk = rk + ro;
+    q.defmask = mask + b;
+    go += (size_t)j.l * j.l;
+    ro += 3 * (size_t)j.l * j.l;
+    pl.maxm = std::max<int64_t>(pl.maxm, j.m);
+    pl.total_rows += j.m;
+  }
+  pl.g_all = g;
+  pl.g_count = gsum;
+  KRP_CUDA_CHECK(cudaMemcpyAsync(dmem, h.data(), sizeof(CqrJob) * count, cudaMemcpyHostToDevice, st));
+  return pl;
+}
+
+int cholqr3_jobs_launch(const CqrJobsPlan& pl, int* status) {
+  const CqrJobArray jobs{static_cast<const CqrJob*>(pl.d_jobs)};
+  const dim3 g((unsigned)((pl.maxm + kCqrRows - 1) / kCqrRows), (unsigned)pl.count);
+  for (int pass = 0; pass < 3; ++pass) {
+    KRP_CUDA_CHECK(cudaMemsetAsync(pl.g_all, 0, sizeof(double) * pl.g_count, stream()));
+    if (pass == 0)
+      cqr_gram_kernel<true><<<g, 256, 0, stream()>>>(jobs, status);
+    else
+      cqr_gram_kernel<false><<<g, 256, 0, stream()>>>(jobs, status);
+    check_launch("cholqr_jobs_gram_f64");
+    cqr_chol_kernel<<<pl.count, kCholThreads, 0, stream()>>>(jobs, pass);
+    check_launch("cholqr_jobs_chol_f64");
+    cqr_solve_any(jobs, pl.count, pl.maxm, pl.total_rows, pass, stream());
+    check_launch("cholqr_jobs_solve_f64");
+  }
+  return 9;
 }
 
 void gram_modes_f64(const double* G, int D, const int64_t* dims, double* const* S) {

@@ -27,7 +27,10 @@ pytestmark = pytest.mark.gpu
 P = 4
 SHAPES = [((40, 33, 27), (3, 4, 2)), ((5, 7, 9), (1, 2, 2)), ((64, 16, 48), (6, 5, 8)),
           ((31, 90, 12), (4, 4, 4)), ((96, 40, 70), (8, 3, 6)), ((17, 17, 17), (2, 2, 3)),
-          ((128, 50, 33), (12, 9, 16)), ((8, 200, 24), (4, 16, 10))]
+          ((128, 50, 33), (12, 9, 16)), ((8, 200, 24), (4, 16, 10)),
+          # l up to 32: the widest kernel variants (8 n-tiles of the warp MMAs,
+          # 32 accumulators per lane on CUDA cores)
+          ((48, 40, 36), (24, 26, 28))]
 
 
 @pytest.fixture(scope="module")

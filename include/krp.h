@@ -336,11 +336,14 @@ typedef struct krp_tucker_item {
 /* RHOSVD-KRP-MEMO (Alg. 7 with one factor set per tensor, draw 0 of key
  * `seed`, i.e. exactly what krp_tucker_rhosvd with KRP_MEMO computes for that
  * tensor alone) of `count` 3-way tensors of different shapes and ranks, each
- * phase one launch over the whole batch (persistent kernels over work tiles of
- * mode-3 slabs; QR and eigenproblems as job arrays).  Flags: KRP_TRUNCATE,
- * KRP_RESIDUAL (KRP_MEMO implied).  The first call with a given set of
- * descriptors (pointers, shapes, ranks, seeds, flags) allocates the batch's
- * scratch, picks the work-tile size by timing, and records the phase
+ * phase one launch over the whole batch (persistent kernels whose warps take
+ * work units of mode-3 slabs from an atomic counter; with KRP_BF16 the
+ * contractions run on warp-level tensor-core MMAs; QR and eigenproblems as
+ * job arrays).  Dims n_i <= 256, l_i = rank_i + oversample <= min(32, n_i).
+ * Flags: KRP_TRUNCATE, KRP_RESIDUAL (KRP_MEMO implied).  The first call with
+ * a given set of descriptors (pointers, shapes, ranks, seeds, flags)
+ * allocates the batch's scratch, picks the slabs per work unit by timing,
+ * and records the phase
  * sequence as a CUDA graph; later calls with identical descriptors replay
  * the graph.  The call synchronises the stream and fills rel_residual.  The
  * plan and its scratch stay with the context until a call with other

@@ -382,7 +382,7 @@ def hankel_batch_run(ctx, dev, stream, args):
     return out
 
 
-def c4_run(ctx, dev, stream, args):
+def c4_run(ctx, dev, stream, args, reps=10, warm=3):
     """1024 x 1024 block Hankel (state order 40), Alg. 6 with l_r=50, l_l=75,
     r=40, both forms; singular values against the stored FP64 oracle's."""
     import torch
@@ -403,7 +403,7 @@ def c4_run(ctx, dev, stream, args):
     for form, bl in blocks.items():
         ms, _ = _timed(stream, lambda: K.krp_block_hankel_lowrank(
             ctx, bl, spec.m, spec.n, spec.s, r, spec.ell_r, spec.ell_l, spec.omega_seed, U, S, V),
-            reps=10, warm=3)
+            reps=reps, warm=warm)
         sg = S.cpu().numpy()
         so = np.asarray(gold[f"sigma_{form}"])
         out[form] = {"ms": round(ms, 4),
@@ -569,6 +569,8 @@ def main():
                     help="run only the batched workloads (for profiling) and print their line")
     ap.add_argument("--batch-count", type=int, default=512,
                     help="tensors in the batched workload with --batch-only")
+    ap.add_argument("--hankel-only", action="store_true",
+                    help="run only the 1024 x 1024 block-Hankel measurement (for profiling)")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -594,6 +596,19 @@ def main():
                 "e2e": {"value": round(v, 4), "unit": "GB/s", "h2d_bytes_per_step": 0,
                         "d2h_bytes_per_step": 0}}
         print(json.dumps(line))
+        return
+
+    if args.hankel_only:
+        import torch
+        import paper_2507_23207_gb300 as K
+        dev = torch.device(f"cuda:{local_rank}")
+        torch.cuda.set_device(dev)
+        stream = torch.cuda.current_stream(dev)
+        ctx = K.Context(local_rank, stream.cuda_stream)
+        out = {"block_hankel_1024": c4_run(ctx, dev, stream, args, reps=max(1, args.steps),
+                                           warm=max(1, args.warmup))}
+        ctx.close()
+        print(json.dumps(out))
         return
 
     if args.batch_only:

@@ -1,8 +1,9 @@
 // Alg. 6: single-pass randomized SVD of a block Hankel matrix with KRP
 // sketches.  Sketches (a9) on CUDA cores in FP32; post-processing (a10) in FP64:
-//   Y = Q R (Householder);  P = Psi^T Q computed structurally,
+//   Y = Q R (FP64 thin QR);  P = Psi^T Q computed structurally,
 //   P[c, :] = sum_{i,a} Psi1[i, c] Psi2[a, c] Q[(i,a), :];
-//   W = P^+ Z^T by Householder least squares (P = Qp Rp, W = Rp^{-1} Qp^T Z^T);
+//   W = P^+ Z^T by least squares through the thin QR P = Qp Rp:
+//   W = B Z^T with B = Rp^{-1} Qp^T (lr x ll, back substitution per column);
 //   W = U_W S V^T through the eigen-decomposition of W W^T (Jacobi);
 //   U = Q U_W, V = W^T U_W S^{-1}.
 #include <cmath>
@@ -45,23 +46,46 @@ __global__ void psi_t_q_kernel(const T* __restrict__ psi1, const T* __restrict__
   }
 }
 
-// W[q + lr*col] = (Rp^{-1} Qp^T Z^T)[q, col]; one thread per column col < ns.
-__global__ void ls_solve_kernel(const double* __restrict__ Qp, const double* __restrict__ Rp,
-                                const float* __restrict__ Z, int64_t ns, int ll, int lr,
-                                double* __restrict__ W) {
-  for (int64_t col = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; col < ns;
-       col += (int64_t)gridDim.x * blockDim.x) {
-    double* w = W + (int64_t)lr * col;
-    for (int q = 0; q < lr; ++q) {  // rhs = Qp^T z, z = Z[col, :]
-      double acc = 0.0;
-      for (int c = 0; c < ll; ++c) acc = fma(Qp[c + (int64_t)ll * q], (double)Z[col + ns * c], acc);
-      w[q] = acc;
-    }
-    for (int q = lr - 1; q >= 0; --q) {  // back substitution with Rp
-      double acc = w[q];
-      for (int t = q + 1; t < lr; ++t) acc -= Rp[q + (int64_t)lr * t] * w[t];
-      w[q] = acc / Rp[q + (int64_t)lr * q];
-    }
+// B = Rp^{-1} Qp^T (lr x ll, column-major): one warp per column c of Qp^T
+// (grid ll), back substitution with the lanes splitting each sum over t
+// (lr <= 64: entries t = lane and lane + 32 held in registers).
+__global__ void __launch_bounds__(32) ls_coef_kernel(const double* __restrict__ Qp,
+                                                     const double* __restrict__ Rp, int ll, int lr,
+                                                     double* __restrict__ B) {
+  const int c = blockIdx.x, lane = threadIdx.x;
+  double b0 = 0.0, b1 = 0.0;
+  for (int q = lr - 1; q >= 0; --q) {
+    double part = 0.0;
+    if (lane > q && lane < lr) part = Rp[q + (int64_t)lr * lane] * b0;
+    if (lane + 32 > q && lane + 32 < lr) part = fma(Rp[q + (int64_t)lr * (lane + 32)], b1, part);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+    const double v = (Qp[c + (int64_t)ll * q] - part) / Rp[q + (int64_t)lr * q];
+    if (lane == q) b0 = v;
+    if (lane + 32 == q) b1 = v;
+  }
+  if (lane < lr) B[lane + (int64_t)lr * c] = b0;
+  if (lane + 32 < lr) B[lane + 32 + (int64_t)lr * c] = b1;
+}
+
+// W[q + lr*col] = sum_c B[q + lr*c] Z[col + ns*c]: a CTA takes kLsCols columns,
+// its Z entries converted to FP64 once in shared memory.
+constexpr int kLsCols = 16;
+__global__ void ls_apply_kernel(const double* __restrict__ B, const float* __restrict__ Z,
+                                int64_t ns, int ll, int lr, double* __restrict__ W) {
+  extern __shared__ double zs[];  // ll x kLsCols
+  const int64_t c0 = (int64_t)blockIdx.x * kLsCols;
+  const int nc = (int)((ns - c0) < kLsCols ? (ns - c0) : kLsCols);
+  for (int e = threadIdx.x; e < ll * kLsCols; e += blockDim.x) {
+    const int c = e / kLsCols, k = e % kLsCols;
+    zs[e] = k < nc ? (double)Z[c0 + k + ns * c] : 0.0;
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < lr * nc; e += blockDim.x) {
+    const int q = e % lr, k = e / lr;
+    double acc = 0.0;
+    for (int c = 0; c < ll; ++c) acc = fma(B[q + (int64_t)lr * c], zs[c * kLsCols + k], acc);
+    W[q + (int64_t)lr * (c0 + k)] = acc;
   }
 }
 
@@ -132,7 +156,7 @@ void hankel_pipeline(const void* blocks, krp_dtype bt, int m, int n, int s, int 
   need += ws_bytes((size_t)std::max(m, n) * ell_l * nb, 4);
   need += 2 * ws_bytes((size_t)s * ell_l, eb) + 2 * ws_bytes((size_t)std::max(m, n) * ell_l, eb);
   need += ws_bytes((size_t)ms * ell_r, 4) + ws_bytes((size_t)ns * ell_l, 4);
-  need += 3 * ws_bytes((size_t)ms * ell_r, 8) + 4 * ws_bytes((size_t)ell_l * ell_r, 8);
+  need += 3 * ws_bytes((size_t)ms * ell_r, 8) + 5 * ws_bytes((size_t)ell_l * ell_r, 8);
   need += ws_bytes((size_t)ell_r * ns, 8) + 4 * ws_bytes((size_t)ell_r * ell_r, 8);
   need += ws_bytes((size_t)ms * r, 8) + ws_bytes((size_t)ns * r, 8) + ws_bytes(r, 8);
   need += sym_eig_workspace_bytes(1);
@@ -188,8 +212,17 @@ void hankel_pipeline(const void* blocks, krp_dtype bt, int m, int n, int s, int 
   jpq.Y64 = P;
   qr_householder_f64(&jpq, 1, c->d_status);
   double* W = ws.take<double>((size_t)ell_r * ns);
-  ls_solve_kernel<<<grid_for(ns), 256, 0, c->stream>>>(Qp, Rp, Z, ns, ell_l, ell_r, W);
-  check_launch("hankel_ls_solve");
+  double* Bls = ws.take<double>((size_t)ell_r * ell_l);
+  ls_coef_kernel<<<ell_l, 32, 0, c->stream>>>(Qp, Rp, ell_l, ell_r, Bls);
+  check_launch("hankel_ls_coef");
+  {
+    const size_t sm = sizeof(double) * (size_t)ell_l * kLsCols;
+    KRP_CUDA_CHECK(cudaFuncSetAttribute(ls_apply_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)sm));
+    ls_apply_kernel<<<(unsigned)((ns + kLsCols - 1) / kLsCols), 256, sm, c->stream>>>(Bls, Z, ns, ell_l,
+                                                                                   ell_r, W);
+  }
+  check_launch("hankel_ls_apply");
   // SVD of W via W W^T
   double* Wg = ws.take<double>((size_t)ell_r * ell_r);
   const int64_t wd[2] = {ell_r, ns};

@@ -2,27 +2,28 @@
 //
 // RHOSVD-KRP-MEMO (Alg. 7 with one factor set, Sec. 5.1) of every tensor of a
 // batch.  Each phase is one kernel launch over the whole batch:
-//   factors     one Philox launch over all (tensor, mode) factors
-//   sketch      persistent kernel over (tensor, slab range) work tiles: for a
-//               mode-3 slab X_t (n1 x n2) it forms A_t = X_t Om2 and
-//               B_t = X_t^T Om1 and accumulates Y1 += A_t diag(Om3[t,:]),
-//               Y2 += B_t diag(Om3[t,:]), Y3[t,:] = colsum(Om1 * A_t): all
-//               three mode sketches from one pass over X (the dimension tree
-//               of Sec. 5.1, 4 N l flops)
+//   factors     one Philox launch over all (tensor, mode) factors, then
+//               row-major FP32 (and, for BF16, k-major BF16) copies
+//   sketch      persistent kernel whose warps take work units from an atomic
+//               counter: a row unit (32 rows i, a range of mode-3 slabs X_t)
+//               forms A_t = X_t Om2 and accumulates Y1 += A_t diag(Om3[t,:])
+//               and Y3[t,:] = colsum(Om1 * A_t); a column unit (32 columns j)
+//               forms B_t = X_t^T Om1 and accumulates Y2 += B_t diag(Om3[t,:])
+//               (the dimension tree of Sec. 5.1, 4 N l flops)
 //   QR          one CTA per (tensor, mode), FP64 Householder
-//   core        persistent kernel over the same tiles: C_t = Q1^T X_t Q2,
+//   core        persistent kernel, one slab per warp unit: C_t = Q1^T X_t Q2,
 //               then G(:,:,c) = sum_t C_t Q3[t,c] in a per-tensor kernel
 //   truncation  FP64 Gram matrices of the core unfoldings, the eigensolver
 //               on all 3 x count of them, then G x {U_i^T}, Q_i U_i
-//   residual    persistent kernel: ||X_t - Q1 (sum_c G(:,:,c) Q3[t,c]) Q2^T||^2
-//               with FP64 sums per tensor
-// The tiles are sorted by work (largest first) and handed out by an atomic
-// counter.  The slabs-per-tile granularity is picked once per batch by timing
-// the sketch phase for a few candidates.  The whole sequence is captured in a
-// CUDA graph when the batch is first seen; a repeated call with the same
-// descriptors replays the graph.  Products run on CUDA cores in FP32 with
-// FP32 accumulation (the slabs are too small and too unevenly shaped for
-// 128-row tensor-core tiles); X may be FP32 or BF16.
+//   residual    persistent kernel over (tensor, slab range) tiles, one warp per
+//               (slab, 32 rows): ||X_t - F1 M_t F2^T||^2 with FP64 sums per tensor
+// Units and tiles are ordered by work (largest first).  The slabs per sketch
+// unit are picked once per batch by timing the sketch phase for a few
+// candidates.  The whole sequence is captured in a CUDA graph when the batch
+// is first seen; a repeated call with the same descriptors replays the graph.
+// FP32 X: products on CUDA cores (FFMA).  BF16 X: the sketch and core
+// contractions on warp-level tensor-core MMAs (m16n8k16, FP32 accumulators);
+// the residual stays on CUDA cores.
 #include <algorithm>
 #include <cmath>
 #include <cstring>

@@ -107,6 +107,37 @@ def single_pass_svd(blocks: np.ndarray, r: int, ell_r: int, ell_l: int, seed: in
             "W": w, "factors": (o1, o2, p1, p2), "H": h}
 
 
+def era_realization(blocks: np.ndarray, u: np.ndarray, sig: np.ndarray,
+                    v: np.ndarray) -> np.ndarray:
+    """State matrix of the eigensystem realization built from a rank-r SVD of
+    the block Hankel matrix (the use Sec. 4.2 makes of Alg. 6).
+
+    With H = U S V^T, the observability factor is O = U S^{1/2} and the
+    controllability factor is G = S^{1/2} V^T.  The shifted block Hankel
+    matrix H_up has h_{i+j} in block (i, j), for i = 1..s-1 and j = 1..s, so
+    it uses blocks 2..2s-1 only.  It equals O_top A G, where O_top is the
+    first (s-1) m rows of O.  Hence A = O_top^+ H_up G^+, with
+    G^+ = V S^{-1/2}.  A is returned up to a similarity transform, so its
+    eigenvalues are those of the system.
+    """
+    m, n, nb = blocks.shape
+    s = (nb + 1) // 2
+    h_up = np.zeros(((s - 1) * m, s * n))
+    for i in range(s - 1):
+        for j in range(s):
+            h_up[i * m:(i + 1) * m, j * n:(j + 1) * n] = blocks[:, :, i + j + 1]
+    sq = np.sqrt(sig)
+    o_top = u[:(s - 1) * m] * sq
+    g_pinv = v / sq
+    return np.linalg.lstsq(o_top, h_up @ g_pinv, rcond=None)[0]
+
+
+def hausdorff(a: np.ndarray, b: np.ndarray) -> float:
+    """Hausdorff distance between two finite sets of complex numbers."""
+    d = np.abs(np.asarray(a)[:, None] - np.asarray(b)[None, :])
+    return float(max(d.min(axis=1).max(), d.min(axis=0).max()))
+
+
 def rng_count_block(m: int, n: int, p: int, q: int, ell_r: int, ell_l: int) -> int:
     """Normals drawn by Alg. 6 with KRP sketches: (n+q) l_r + (m+p) l_l (Sec. 4.1)."""
     return (n + q) * ell_r + (m + p) * ell_l

@@ -79,6 +79,36 @@ def test_single_pass_exact_rank_recovery():
     assert np.linalg.norm(res["V"].T @ res["V"] - np.eye(sp.r)) < 1e-12
 
 
+def test_era_from_single_pass_recovers_the_system_eigenvalues():
+    """End-to-end pin of Alg. 6 through ERA.  The data come from a known
+    order-8 system, so the eigenvalues of the realized state matrix are fixed
+    by construction.  Alg. 6's rank-r factors must reproduce them up to
+    rounding.  With r one below the order they must not."""
+    sp = HankelSpec("era", 8, 3, 3, 14, 0.9, 21, r=8, ell_r=12, ell_l=18)
+    blocks = markov_parameters(sp)
+    _, _, _, eig = system_matrices(sp)
+    res = HK.single_pass_svd(blocks, sp.r, sp.ell_r, sp.ell_l, seed=3)
+    a_hat = HK.era_realization(blocks, res["U"], res["S"], res["V"])
+    assert a_hat.shape == (8, 8)
+    assert HK.hausdorff(np.linalg.eigvals(a_hat), eig) <= 1e-11
+    # the exact SVD gives the same realization spectrum (a check of era_realization
+    # that does not depend on the sketch)
+    uh, sh, vth = np.linalg.svd(res["H"])
+    a_ref = HK.era_realization(blocks, uh[:, :8], sh[:8], vth[:8].T)
+    assert HK.hausdorff(np.linalg.eigvals(a_ref), eig) <= 1e-11
+    # truncating below the order loses an eigenvalue pair's worth of the spectrum
+    res7 = HK.single_pass_svd(blocks, 7, sp.ell_r, sp.ell_l, seed=3)
+    a7 = HK.era_realization(blocks, res7["U"], res7["S"], res7["V"])
+    assert HK.hausdorff(np.linalg.eigvals(a7), eig) > 1e-3
+
+
+def test_hausdorff_distance():
+    a = np.array([0.0, 1.0 + 1.0j])
+    assert HK.hausdorff(a, a) == 0.0
+    assert HK.hausdorff(a, np.array([0.0, 1.0 + 1.0j, 3.0])) == abs(3.0 - (1.0 + 1.0j))
+    assert HK.hausdorff(np.array([0.0]), np.array([0.5])) == 0.5
+
+
 def test_rng_counts_against_printed_shares():
     vals = {}
     with open(os.path.join(GOLDEN, "era_rng_percentages.txt")) as f:

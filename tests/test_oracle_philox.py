@@ -140,3 +140,25 @@ def test_bf16_rounding_matches_torch():
                         np.array([1.0, -1.0, 0.0, 1.00390625, 1.01171875, 3.0e-39])])
     ref = torch.from_numpy(x.astype(np.float32)).to(torch.bfloat16).to(torch.float64).numpy()
     assert np.array_equal(philox.round_to_bf16(x), ref)
+
+
+def test_krp_columns_are_isotropic():
+    """Sec. 2.5: a column of Omega_1 kr Omega_2 (independent standard Gaussian
+    factors) has E[w w^T] = I.  Monte Carlo over 20000 columns drawn from the
+    Philox stream at n = (3, 4).  The tolerance is 5 sigma of the sample
+    mean: an entry of w w^T is a product of four standard normal factors,
+    with variance at most E[x^4] E[y^4] - 1 = 8 (diagonal) and at most 3
+    (off-diagonal).  A stream that repeated columns or correlated the two
+    factors would fail it."""
+    cols = 20000
+    o1 = philox.gaussian_factor(11, 0, 0, philox.TAG_OMEGA, 3, cols)
+    o2 = philox.gaussian_factor(11, 1, 0, philox.TAG_OMEGA, 4, cols)
+    # column k of the Khatri-Rao product: kron(o1[:, k], o2[:, k])
+    w = (o1[:, None, :] * o2[None, :, :]).reshape(12, cols)
+    cov = w @ w.T / cols
+    diag = np.diag(cov)
+    off = cov - np.diag(diag)
+    assert np.max(np.abs(diag - 1.0)) <= 5 * np.sqrt(8.0 / cols)
+    assert np.max(np.abs(off)) <= 5 * np.sqrt(3.0 / cols)
+    # the two factors of one column are independent draws (different counters)
+    assert abs(np.corrcoef(o1[0], o2[0])[0, 1]) <= 5 / np.sqrt(cols)

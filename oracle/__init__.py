@@ -20,6 +20,8 @@ Modules
            variant, RSTHOSVD-KRP (Alg. 8), core truncation, residual (Sec. 5)
   hankel   block-Hankel matrices and the single-pass block-structured
            randomized SVD (Alg. 6, Sec. 4)
+  quant    FP8 E4M3 storage of X with one scale per slab of the slowest mode
+           (a storage option for the sketch; the paper uses one precision)
 
 Parity pins live in tests/test_oracle_*.py.  Functions without an independent
 pin are marked "parity unpinned" in their docstring; currently: none.

@@ -638,7 +638,7 @@ def main():
     ms = f32["ms"]
     value = world * bytes_step / (ms * 1e-3) / 1e9
     cpu = None
-    if not args.no_cpu:
+    if not args.no_cpu and world == 1:   # the host baseline is timed at N = 1 only
         try:
             cpu = cpu_baseline(spec)
         except Exception as exc:  # the GPU line is still printed

@@ -53,3 +53,35 @@ def test_null_context_is_rejected_without_a_gpu(lib):
     assert lib.krp_destroy(None) == K.KRP_EINVAL
     assert lib.krp_set_stream(None, None) == K.KRP_EINVAL
     assert lib.krp_last_error(None) == b"null context"
+
+
+def test_without_a_gpu_the_library_fails_loudly(lib):
+    """No CPU fallback: with no usable GPU, creating a context is an error
+    (KRP_ECUDA from the C ABI, KrpError from the binding), so no entry point
+    that needs a context can run."""
+    import ctypes as C
+    import torch
+    import paper_2507_23207_gb300 as K
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    h = C.c_void_p()
+    assert lib.krp_create(C.byref(h), 0, None) == K.KRP_ECUDA
+    assert not h.value
+    with pytest.raises(K.KrpError) as e:
+        K.Context(0, 0)
+    assert e.value.status == K.KRP_ECUDA
+
+
+def test_noalloc_qr_checks_its_arguments_before_touching_the_device(lib):
+    """krp_qr_noalloc rejects sizes beyond its fixed scratch (and l outside
+    1..64, m < l, null pointers) before any CUDA call, so the rejection is
+    the same with or without a GPU."""
+    import ctypes as C
+    import paper_2507_23207_gb300 as K
+    p = C.c_void_p(256)  # never dereferenced: every call below is rejected first
+    assert lib.krp_qr_noalloc(p, 16384, 48, p, None, None) == K.KRP_EINVAL
+    assert lib.krp_qr_noalloc(p, 100, 65, p, None, None) == K.KRP_EINVAL
+    assert lib.krp_qr_noalloc(p, 3, 4, p, None, None) == K.KRP_EINVAL
+    assert lib.krp_qr_noalloc(p, 100, 0, p, None, None) == K.KRP_EINVAL
+    assert lib.krp_qr_noalloc(None, 8, 4, p, None, None) == K.KRP_EINVAL
+    assert lib.krp_qr_noalloc(p, 8, 4, None, None, None) == K.KRP_EINVAL

@@ -86,3 +86,72 @@ def test_constants_match_the_header(header_layout):
             continue
         assert getattr(K, k) == header_layout[k], k
     assert header_layout["KRP_ABI_VERSION"] == 1
+
+
+# ---------------------------------------------------------------- prototypes --
+
+_SCALARS = {"int": C.c_int, "unsigned": C.c_uint, "int64_t": C.c_int64,
+            "uint64_t": C.c_uint64, "uint32_t": C.c_uint32, "size_t": C.c_size_t,
+            "krp_dtype": C.c_int, "krp_status": C.c_int}
+_POINTEES = {"int": C.c_int, "int64_t": C.c_int64, "uint32_t": C.c_uint32,
+             "double": C.c_double, "float": C.c_float, "char": C.c_char}
+
+
+def _prototypes():
+    import re
+    with open(os.path.join(ROOT, "include", "krp.h")) as f:
+        src = re.sub(r"/\*.*?\*/", "", f.read(), flags=re.S)
+    out = {}
+    for ret, name, args in re.findall(
+            r"([A-Za-z_][A-Za-z0-9_ \*]*?)\b(krp_[a-z0-9_]+)\s*\(([^)]*)\)\s*;", src):
+        params = [a.strip() for a in args.split(",")]
+        if params == ["void"]:
+            params = []
+        # drop the parameter name, keep the type
+        types = [re.sub(r"\s*\b[A-Za-z_][A-Za-z0-9_]*$", "", p).strip() for p in params]
+        out[name] = (ret.strip(), types)
+    return out
+
+
+def _check(ctype_str, ct, where):
+    s = ctype_str.replace("const", " ").split()
+    stars = "".join(s).count("*")
+    base = "".join(s).replace("*", "")
+    if base == "krp_ctx":               # an opaque pointer typedef
+        stars += 1
+        base = "void"
+    if stars == 0:
+        assert ct is _SCALARS[base], (where, ctype_str, ct)
+        return
+    if ct in (C.c_void_p, C.c_char_p):  # any data pointer passed as an address
+        assert stars == 1, (where, ctype_str, ct)
+        return
+    pointee = ct._type_                 # POINTER(T)
+    if stars >= 2:
+        assert pointee is C.c_void_p, (where, ctype_str, ct)
+    elif base in _POINTEES:
+        assert C.sizeof(pointee) == C.sizeof(_POINTEES[base]), (where, ctype_str, ct)
+    else:                               # a struct of the boundary: its own ctypes class
+        assert base in STRUCTS and pointee.__name__ == STRUCTS[base][0], (where, ctype_str, ct)
+
+
+def test_binding_signatures_match_the_header_prototypes():
+    """Every argtypes/restype of the binding against the header's prototype:
+    same arity, the same integer width for each scalar, and pointers where
+    the header has pointers.  A 32-bit int passed for an int64_t (or an
+    argument missing) would otherwise be accepted by ctypes silently."""
+    import paper_2507_23207_gb300 as K
+    from paper_2507_23207_gb300 import build
+    build.build()                       # incremental: a no-op when up to date
+    lib = K.load_library()
+    protos = _prototypes()
+    assert sorted(protos) == sorted(K.EXPORTED)
+    for name, (ret, types) in protos.items():
+        fn = getattr(lib, name)
+        assert fn.argtypes is not None and len(fn.argtypes) == len(types), name
+        for i, (t, ct) in enumerate(zip(types, fn.argtypes)):
+            _check(t, ct, f"{name} argument {i}")
+        if ret == "const char*":
+            assert fn.restype is C.c_char_p, name
+        else:
+            _check(ret, fn.restype, f"{name} result")

@@ -172,3 +172,29 @@ def test_bf16_quantisation_degrades_decaying_core():
         g2, q2 = TK.truncate_core(o["G"], o["Q"], [20] * 3)
         errs.append(TK.rel_error(x, g2, q2))
     assert errs[1] > 1.05 * errs[0]
+
+
+@pytest.mark.parametrize("dims", [(4, 3, 5), (3, 2, 4, 2)])
+def test_mttkrp_rows_is_the_elementwise_sketch_on_the_selected_rows(dims):
+    """The sampled-row sketch used for full-size checks equals the elementwise
+    definition Y_n[i, k] = sum over the other indices of
+    X[i_1..i_d] prod_{j != n} Omega_j[i_j, k], evaluated by nested loops."""
+    import itertools
+    rng = np.random.default_rng(31)
+    ell = 3
+    x = rng.standard_normal(dims)
+    om = [rng.standard_normal((nj, ell)) for nj in dims]
+    d = len(dims)
+    for n in range(d):
+        rows = [dims[n] - 1, 0] if dims[n] > 1 else [0]
+        got = TK.mttkrp_rows(x, om, n, rows)
+        for r_i, i in enumerate(rows):
+            ref = np.zeros(ell)
+            others = [range(dims[j]) if j != n else [i] for j in range(d)]
+            for idx in itertools.product(*others):
+                w = np.ones(ell)
+                for j in range(d):
+                    if j != n:
+                        w = w * om[j][idx[j], :]
+                ref += x[idx] * w
+            np.testing.assert_allclose(got[r_i], ref, rtol=1e-13, atol=1e-13)

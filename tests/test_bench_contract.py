@@ -27,3 +27,16 @@ def test_reference_arm_prints_one_contract_line():
     assert d["e2e"] == {"value": d["value"], "unit": "GB/s", "h2d_bytes_per_step": 0,
                         "d2h_bytes_per_step": 0}
     assert "workload" in d["config"]
+
+
+def test_product_arm_prints_no_number_without_a_gpu():
+    """The timed arm has no host fallback: without a CUDA device it exits
+    with an error and prints no JSON line."""
+    import torch
+    import pytest
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    out = subprocess.run([sys.executable, "bench.py", "--steps", "1", "--warmup", "1",
+                          "--no-cpu"], cwd=ROOT, capture_output=True, text=True, timeout=600)
+    assert out.returncode != 0
+    assert not [l for l in out.stdout.splitlines() if l.strip().startswith("{")]

@@ -38,10 +38,30 @@ from synth.hankel import hankel_config_spec, markov_parameters  # noqa: E402
 from synth.tucker import tucker_factors  # noqa: E402
 
 
+def compressed_rhosvd_memo(g0, us, dims, seed, ells, ranks, form):
+    """RHOSVD-KRP-MEMO of X = G0 x {U_i} (orthonormal U_i), run on G0.
+
+    The mode-i sketch of X is U_i times the mode-i sketch of G0 with the
+    factors U_j^T Omega_j (mixed product), so Q_i = U_i Q~_i, the core is the
+    same and ||X - X_hat|| = ||G0 - G0_hat||.  Returns the rank-l and the
+    truncated relative errors and the truncated core's norm.
+    """
+    d = len(dims)
+    oms = TK.memo_factors(seed, dims, max(ells), omega_round=form)
+    omt = [u.T @ om for u, om in zip(us, oms)]
+    qs = []
+    for i in range(d):
+        om_i = [omt[j][:, :ells[i]] if j != i else None for j in range(d)]
+        q, _ = LA.householder_qr(T.mttkrp(g0, om_i, i))
+        qs.append(q)
+    g = T.multi_ttm(g0, [q.T for q in qs])
+    g2, q2 = TK.truncate_core(g, qs, ranks)
+    return TK.rel_error(g0, g, qs), TK.rel_error(g0, g2, q2), float(T.frob(g2))
+
+
 def c3_values():
     spec = config_spec("c3")
     g0, us = tucker_factors(spec)
-    d = spec.d
     ells, ranks = list(spec.ell), list(spec.ranks)
     out = {"workload": "200^4 Tucker, core 40^4 N(0,1)*0.8^(i+j+k+l), no noise, "
                        "RHOSVD-KRP-MEMO l=30, truncated to rank 20",
@@ -50,18 +70,11 @@ def c3_values():
     gh, qh = TK.hosvd(g0, ranks)
     out["hosvd_rel_error"] = TK.rel_error(g0, gh, qh)
     for form in ("f32", "bf16"):
-        oms = TK.memo_factors(spec.omega_seed, spec.dims, max(ells), omega_round=form)
-        omt = [u.T @ om for u, om in zip(us, oms)]
-        qs = []
-        for i in range(d):
-            om_i = [omt[j][:, :ells[i]] if j != i else None for j in range(d)]
-            q, _ = LA.householder_qr(T.mttkrp(g0, om_i, i))
-            qs.append(q)
-        g = T.multi_ttm(g0, [q.T for q in qs])
-        g2, q2 = TK.truncate_core(g, qs, ranks)
-        out[f"rhosvd_memo_rank_l_rel_error_{form}"] = TK.rel_error(g0, g, qs)
-        out[f"rhosvd_memo_truncated_rel_error_{form}"] = TK.rel_error(g0, g2, q2)
-        out[f"core_norm_truncated_{form}"] = float(T.frob(g2))
+        e_l, e_r, gn = compressed_rhosvd_memo(g0, us, spec.dims, spec.omega_seed, ells, ranks,
+                                              form)
+        out[f"rhosvd_memo_rank_l_rel_error_{form}"] = e_l
+        out[f"rhosvd_memo_truncated_rel_error_{form}"] = e_r
+        out[f"core_norm_truncated_{form}"] = gn
     return out
 
 

@@ -198,3 +198,30 @@ def test_mttkrp_rows_is_the_elementwise_sketch_on_the_selected_rows(dims):
                         w = w * om[j][idx[j], :]
                 ref += x[idx] * w
             np.testing.assert_allclose(got[r_i], ref, rtol=1e-13, atol=1e-13)
+
+
+@pytest.mark.parametrize("form", ["f32", "bf16"])
+def test_compressed_problem_behind_the_stored_full_size_values(form):
+    """The stored 200^4 values are computed on the 40^4 core G0 with the
+    factors U_j^T Omega_j (tests/golden/make_fullsize.py).  On a small
+    noise-free Tucker tensor with a decaying core, that compressed
+    computation gives the rank-l error, the truncated error and the
+    truncated core norm of the explicit oracle run on X itself."""
+    import importlib.util
+    import os
+    path = os.path.join(os.path.dirname(__file__), "golden", "make_fullsize.py")
+    sp = importlib.util.spec_from_file_location("make_fullsize", path)
+    mf = importlib.util.module_from_spec(sp)
+    sp.loader.exec_module(mf)
+    spec = TuckerSpec("cmp", (22, 19, 17, 15), (8, 7, 6, 6), 0.0, 0.6, 4321, (3, 3, 2, 2),
+                      (5, 5, 4, 4), omega_seed=9)
+    x, g0, us = tucker_tensor(spec)
+    ells, ranks = list(spec.ell), list(spec.ranks)
+    e_l, e_r, gn = mf.compressed_rhosvd_memo(g0, us, spec.dims, spec.omega_seed, ells, ranks,
+                                            form)
+    o = TK.rhosvd_krp(x, ells, spec.omega_seed, memo=True, omega_round=form)
+    g2, q2 = TK.truncate_core(o["G"], o["Q"], ranks)
+    assert e_l == pytest.approx(TK.rel_error(x, o["G"], o["Q"]), rel=1e-10)
+    assert e_r == pytest.approx(TK.rel_error(x, g2, q2), rel=1e-10)
+    assert gn == pytest.approx(T.frob(g2), rel=1e-12)
+    assert e_l < e_r < 1.0

@@ -118,6 +118,13 @@ def test_sharded_two_gloo_ranks_match_unsharded_oracle(case_idx):
     mp.spawn(_rank_main, args=(2, _free_port(), case_idx), nprocs=2, join=True)
 
 
+@pytest.mark.parametrize("world,case_idx", [(3, 0), (4, 1)])
+def test_sharded_more_ranks_than_two_uneven_slabs(world, case_idx):
+    # 7 slabs over 3 ranks and 5 slabs over 4 ranks: unequal slab counts per rank
+    import torch.multiprocessing as mp
+    mp.spawn(_rank_main, args=(world, _free_port(), case_idx), nprocs=world, join=True)
+
+
 def test_single_rank_is_the_unsharded_pipeline():
     dims, ranks, p = CASES[0]
     x = _tensor(dims, 7)

@@ -141,8 +141,10 @@ krp_status krp_philox_words(krp_ctx ctx, uint64_t seed, uint32_t c1,
 
 /* Y (dims[n] x ell, FP32, column-major) = X_(n) K_n with
  * K_n = Omega_d kr ... kr Omega_{n+1} kr Omega_{n-1} kr ... kr Omega_1.
- * X: xt = KRP_F32 or KRP_BF16; omega[j] (j != n) is dims[j] x ell of type
- * omt (KRP_F32 for F32 X, KRP_BF16 for BF16 X); omega[n] is ignored.  n is
+ * X: xt = KRP_F32, KRP_BF16 or KRP_BF16X2; omega[j] (j != n) is dims[j] x
+ * ell of type omt (KRP_F32 for F32 X, KRP_BF16 for BF16 and BF16X2 X);
+ * omega[n] is ignored.  The tensor-core forms need n_1 % 8 == 0 and a
+ * 16-byte aligned X (KRP_EINVAL otherwise).  n is
  * 0-based.  d in 2..KRP_MAXD, 1 <= ell <= 256.  The product is never formed:
  * the contraction runs over X once (two-stage: one factor by GEMM, the rest
  * as Hadamard-weighted reductions).  Errors: KRP_EINVAL, KRP_ENOMEM, KRP_ECUDA. */
@@ -164,9 +166,12 @@ krp_status krp_sketch_all_modes(krp_ctx ctx, const void* X, krp_dtype xt,
 
 /* ---- a4: FP64 thin QR (Alg. 1 step 3) ------------------------------------ */
 
-/* Householder QR of `count` FP32 matrices Y[b] (m[b] x l[b], column-major,
- * m >= l) into Q[b] (FP64, m x l, column-major, diag(R) >= 0).  R[b] (l x l,
- * FP64, column-major) may be NULL.  Errors: KRP_EINVAL (m < l, l > 256),
+/* FP64 thin QR of `count` FP32 matrices Y[b] (m[b] x l[b], column-major,
+ * m >= l) into Q[b] (FP64, m x l, column-major, diag(R) >= 0): shifted
+ * CholeskyQR3 for l <= 64 (columns whose pivot collapses are refilled and
+ * re-orthogonalised, so Q stays orthonormal for rank-deficient Y),
+ * Householder above.  R[b] (l x l, FP64, column-major) may be NULL.
+ * Errors: KRP_EINVAL (m < l, l > 256),
  * KRP_ENUMERIC (non-finite input; reported after a stream synchronisation). */
 krp_status krp_qr(krp_ctx ctx, int count, const float* const* Y,
                   const int64_t* m, const int* l, double* const* Q,

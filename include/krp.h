@@ -75,7 +75,7 @@ typedef enum krp_dtype {
 #define KRP_MEMO 0x1u     /* one shared factor set + dimension tree (MEMO variant) */
 #define KRP_TRUNCATE 0x2u /* truncate the rank-l result to ranks r_i */
 #define KRP_RESIDUAL 0x4u /* compute ||X - X_hat||_F / ||X||_F (extra pass over X) */
-#define KRP_TIMINGS 0x8u  /* fill krp_tucker_out.times (synchronises per phase) */
+#define KRP_TIMINGS 0x8u  /* fill krp_tucker_out.times (events between phases; synchronises) */
 
 /* Draw ids of the factor sets used by the Tucker pipelines (see
  * krp_gen_factors): memoized set = 0, fresh set of mode i = 1 + i, ST-HOSVD
@@ -221,7 +221,11 @@ krp_status krp_split_bf16x2(krp_ctx ctx, const float* X, int64_t n, void* out);
 /* ---- a5: multi-TTM core (Alg. 7 last step) ------------------------------- */
 
 /* G = X x_1 Q_1^T x_2 Q_2^T ... x_d Q_d^T, G of dims (cols[0..d-1]) FP32,
- * mode-1 fastest.  Q[j] is FP64 dims[j] x cols[j] column-major. */
+ * mode-1 fastest.  Q[j] is FP64 dims[j] x cols[j] column-major.  X as in
+ * krp_sketch_mode (KRP_F32, KRP_BF16 or KRP_BF16X2); with BF16 X the first
+ * two contractions run on tensor cores with Q_1 (and the intermediate) as
+ * BF16 hi/lo pairs.  All pointers are device pointers.  Errors: KRP_EINVAL,
+ * KRP_ENOMEM, KRP_ECUDA. */
 krp_status krp_multi_ttm(krp_ctx ctx, const void* X, krp_dtype xt, int d,
                          const int64_t* dims, const double* const* Q,
                          const int* cols, float* G);
@@ -284,8 +288,15 @@ typedef struct krp_tucker_out {
  * the dimension tree (krp_sketch_all_modes).  KRP_TRUNCATE: rank-r_i
  * truncation by an FP64 HOSVD of the core (U_i = leading r_i left singular
  * vectors of G_(i), G <- G x {U_i^T}, Q_i <- Q_i U_i).  KRP_RESIDUAL: FP64
- * ||X - X_hat||_F / ||X||_F by streaming reconstruction.  Needs l_i <= n_i.
- * X is KRP_F32 or KRP_BF16 (then factors are drawn in BF16). */
+ * ||X - X_hat||_F / ||X||_F by streaming reconstruction.  Needs l_i <= n_i
+ * (l_i <= 64 with KRP_TRUNCATE).  X is KRP_F32, KRP_BF16 or KRP_BF16X2 (for
+ * the last two the factors are drawn in BF16).  KRP_TIMINGS fills
+ * out->times from CUDA events recorded between the phases (the call then
+ * synchronises the stream).  Errors: KRP_EINVAL (shapes,
+ * ranks, flags, dtype, NULL buffers), KRP_ENOMEM, KRP_ECUDA; KRP_ETIMEOUT if
+ * a bounded device-side wait expired and KRP_ENUMERIC if an FP64 stage met a
+ * non-finite value (both read from the context's device status word after
+ * a stream synchronisation). */
 krp_status krp_tucker_rhosvd(krp_ctx ctx, const void* X, krp_dtype xt, int d,
                              const int64_t* dims, const int* ranks,
                              int oversample, uint64_t seed, unsigned flags,

@@ -320,15 +320,20 @@ krp_status krp_tucker_sthosvd(krp_ctx ctx, const void* X, krp_dtype xt, int d,
  *   Z = M^T Psi  = sum_k (E_k^T Psi1) kr (H_k^T Psi2)
  *   Y = QR;  W = (Psi^T Q)^+ Z^T;  W = U_W S V^T;  U = Q U_W;
  * returns U (m s x r), S (r), V (n s x r), FP64 column-major (device or host).
- * ell_l = 0 selects ceil(1.5 ell_r).  Needs r <= ell_r <= ell_l, ell_r <= m s,
- * ell_l <= n s, ell_r <= 256, ell_l <= 256. */
+ * ell_l = 0 selects ceil(1.5 ell_r).  Needs 1 <= r <= ell_r <= ell_l,
+ * ell_r <= m s, ell_l <= n s, ell_r <= 64, ell_l <= 256.  Synchronises the
+ * stream.
+ * Errors: KRP_EINVAL (sizes, dtype, NULL buffers), KRP_ENOMEM, KRP_ECUDA,
+ * KRP_ENUMERIC (an FP64 stage met a non-finite value). */
 krp_status krp_block_hankel_lowrank(krp_ctx ctx, const void* blocks,
                                     krp_dtype bt, int m, int n, int s, int r,
                                     int ell_r, int ell_l, uint64_t seed,
                                     double* U, double* S, double* V);
 
 /* The two sketches of Alg. 6 alone (device pointers): Y (m s x ell_r) and
- * Z (n s x ell_l), FP32, from given factors (FP32 or BF16 like the blocks). */
+ * Z (n s x ell_l), FP32, from given factors (FP32 or BF16 like the blocks;
+ * omega1 s x ell_r, omega2 n x ell_r, psi1 s x ell_l, psi2 m x ell_l, all
+ * column-major).  Asynchronous.  Errors: KRP_EINVAL, KRP_ENOMEM, KRP_ECUDA. */
 krp_status krp_block_hankel_sketch(krp_ctx ctx, const void* blocks,
                                    krp_dtype bt, int m, int n, int s,
                                    const void* omega1, const void* omega2,
@@ -388,7 +393,9 @@ typedef struct krp_hankel_item {
  * with given descriptors builds a plan and records a CUDA graph that later
  * identical calls replay (ell_l = 0 is replaced in the descriptor by its
  * value).  Needs ell_r <= 64.  Synchronises the stream.  The paper describes
- * single matrices only; the batched form has no counterpart there. */
+ * single matrices only; the batched form has no counterpart there.  Errors:
+ * KRP_EINVAL (sizes, dtype, host pointers), KRP_ENOMEM, KRP_ECUDA,
+ * KRP_ENUMERIC. */
 krp_status krp_block_hankel_batched(krp_ctx ctx, krp_dtype bt, int count,
                                     krp_hankel_item* items);
 

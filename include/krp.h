@@ -190,14 +190,17 @@ krp_status krp_qr(krp_ctx ctx, int count, const float* const* Y,
  * (4 MiB) built into the library, resident on every GPU that loads it until
  * the process exits.  A call needs m*l + 4*l*l + 2 of those doubles; larger
  * requests, l outside 1..64, m < l and NULL Y/Q return KRP_EINVAL before any
- * launch.  The first call on each device looks the array's device address up
- * (cudaGetSymbolAddress) and caches it; make that first call before any
- * stream capture.  All calls share the array and it keeps the last call's
+ * launch.  Every call looks the array's device address up with
+ * cudaGetSymbolAddress in the current device's context (nothing is cached, so
+ * a device reset does not leave a stale address); the first call on a device
+ * may load the library's device code there, so make it before any stream
+ * capture.  All calls share the array and it keeps the last call's
  * contents (the accumulators a call needs zeroed are cleared by the call), so
  * calls whose work can overlap on the GPU -- on different streams, or from
  * different threads -- race and must be serialised by the caller.  The call
- * is asynchronous and does not check the input for NaN/Inf (use krp_qr for
- * that); CUDA launch failures return KRP_ECUDA. */
+ * is asynchronous and does not check the input for NaN/Inf: for non-finite
+ * input Q and R are undefined and the call still returns KRP_OK (krp_qr
+ * reports KRP_ENUMERIC instead).  CUDA launch failures return KRP_ECUDA. */
 #define KRP_QR_NOALLOC_MAX_DOUBLES 524288
 krp_status krp_qr_noalloc(const float* Y, int64_t m, int l, double* Q,
                           double* R, void* cuda_stream);

@@ -8,6 +8,8 @@
   truncate_core    rank-r truncation of a rank-l Tucker result by HOSVD of its
                    core (the analogue of Alg. 2's truncation step)
   rel_error        ||X - [G; Q_1..Q_d]||_F / ||X||_F, explicit reconstruction
+  rel_error_slabs  the same, with the reconstruction formed one slab of the
+                   last mode at a time (bounded memory for large X)
 
 Draw ids of the sketching factors (contract with the device generator):
   memoized set: draw 0; fresh set of mode i (0-based): draw 1 + i;
@@ -162,6 +164,25 @@ def reconstruct(g: np.ndarray, qs: Sequence[np.ndarray]) -> np.ndarray:
 def rel_error(x: np.ndarray, g: np.ndarray, qs: Sequence[np.ndarray]) -> float:
     """||X - X_hat||_F / ||X||_F with the reconstruction formed explicitly."""
     return frob(x - reconstruct(g, qs)) / frob(x)
+
+
+def rel_error_slabs(x: np.ndarray, g: np.ndarray, qs: Sequence[np.ndarray],
+                    slab: int = 64) -> float:
+    """rel_error with X_hat formed slab by slab along the last mode.
+
+    X_hat[..., t] depends on row t of Q_d only, so the slab t0 <= t < t1 of the
+    reconstruction is G x_1 Q_1 ... x_{d-1} Q_{d-1} x_d Q_d[t0:t1]; the squared
+    residuals of the slabs add up to ||X - X_hat||_F^2.  Only one slab of
+    X_hat is held at a time.
+    """
+    n_d = x.shape[-1]
+    num = 0.0
+    for t0 in range(0, n_d, slab):
+        t1 = min(n_d, t0 + slab)
+        part = reconstruct(g, list(qs[:-1]) + [qs[-1][t0:t1]])
+        num += float(np.sum(np.square(x[..., t0:t1] - part, dtype=np.float64)))
+    nx = frob(x)
+    return float(np.sqrt(num)) / nx if nx > 0 else 0.0
 
 
 def mttkrp_rows(x: np.ndarray, omegas, n: int, rows) -> np.ndarray:

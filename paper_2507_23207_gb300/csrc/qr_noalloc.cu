@@ -12,10 +12,10 @@
 //
 // The scratch is a file-scope __device__ array (KRP_QR_NOALLOC_MAX_DOUBLES
 // doubles, 4 MiB), present on every GPU that loads the library until the
-// process exits.  Its host-side name is only a stand-in, so the device address
-// is looked up once per device with cudaGetSymbolAddress and cached.
-#include <mutex>
-
+// process exits.  Its host-side name is only a stand-in, so every call looks
+// the device address up with cudaGetSymbolAddress on the current device (no
+// cached pointer that a device reset or a new primary context could make
+// stale; the lookup costs microseconds).
 #include "common.cuh"
 
 namespace krp {
@@ -27,25 +27,12 @@ namespace {
 
 __device__ __align__(256) double g_qr_noalloc_scratch[KRP_QR_NOALLOC_MAX_DOUBLES];
 
-constexpr int kMaxDevices = 256;
-std::mutex g_setup_mutex;
-double* g_scratch_ptr[kMaxDevices] = {};
-
-// Device address of the scratch array on the current device (set-up on the
-// first call per device).
+// Device address of the scratch array in the current device's context.
 cudaError_t scratch_on_current_device(double** out) {
-  int dev = -1;
-  cudaError_t e = cudaGetDevice(&dev);
+  void* p = nullptr;
+  const cudaError_t e = cudaGetSymbolAddress(&p, g_qr_noalloc_scratch);
   if (e != cudaSuccess) return e;
-  if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
-  std::lock_guard<std::mutex> lock(g_setup_mutex);
-  if (!g_scratch_ptr[dev]) {
-    void* p = nullptr;
-    e = cudaGetSymbolAddress(&p, g_qr_noalloc_scratch);
-    if (e != cudaSuccess) return e;
-    g_scratch_ptr[dev] = static_cast<double*>(p);
-  }
-  *out = g_scratch_ptr[dev];
+  *out = static_cast<double*>(p);
   return cudaSuccess;
 }
 

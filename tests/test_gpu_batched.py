@@ -3,13 +3,9 @@
 Each tensor b of a batch is RHOSVD-KRP-MEMO with its own Philox key seed_b, so
 the oracle's rhosvd_krp(X_b, l, seed_b, memo=True) (+ truncation) is the
 reference: FP32 form within 1e-5 (reconstruction relative to ||X_b||); error
-values within 1e-5 relative plus 1e-6: the factors enter the reconstruction
-in FP32, Q~_i = Q_i + E_i with ||E_i||_F ~ 2^-24 sqrt(l_i), so the residual
-differs from the residual R of the exact projection by first-order terms
-<R, E_i Q_i^T X_(i)> (one per mode; the core's own rounding only acts at
-second order since R is orthogonal to the projection's range).  Each shifts
-the relative error value by at most about 2^-24 sqrt(l) <= 3.4e-7 for
-l <= 32, so three modes give the 1e-6 absolute term.  BF16 form (X and factors rounded to BF16, FP32 arithmetic
+values within 1e-5 relative, widened by the measured reconstruction distance
+and the residual pass's rounding bound (tests/parity.py; the factors enter
+the FP32 reconstruction rounded, Q~_i = Q_i + E_i).  BF16 form (X and factors rounded to BF16, FP32 arithmetic
 on CUDA cores): the same bounds on the BF16-rounded data.  Also: a repeated call
 replays the captured graph with identical results, and new descriptors build
 a new plan.
@@ -19,6 +15,7 @@ import numpy as np
 import pytest
 
 from tests.gpu_util import require_gpu, dev, tensor_to_dev
+from tests.parity import check_error_value, eval_bound
 from oracle import philox, tucker as TK
 from synth import TuckerSpec, tucker_tensor
 
@@ -72,10 +69,13 @@ def _check(hosts, ranks, seeds, cores, facs, rels, trunc, omega_round, tol):
         gg = cores[b].cpu().numpy().astype(np.float64).reshape(out[::-1]).T
         qq = [f.cpu().numpy().reshape(o, n).T for f, n, o in zip(facs[b], x.shape, out)]
         nx = np.linalg.norm(x)
-        d = np.linalg.norm(TK.reconstruct(gg, qq) - TK.reconstruct(g, qs)) / nx
+        xh = TK.reconstruct(gg, qq)
+        d = np.linalg.norm(xh - TK.reconstruct(g, qs)) / nx
         assert d <= tol, (b, x.shape, d)
         e_ora = TK.rel_error(x, g, qs)
-        assert abs(rels[b] - e_ora) <= tol * e_ora + 1e-6, (b, rels[b], e_ora)
+        e_self = TK.rel_error(x, gg, qq)
+        rho = eval_bound(out, x.shape, np.linalg.norm(xh) / nx, e_self)
+        check_error_value(rels[b], e_ora, e_self, d, rho, f"item {b} {x.shape}")
         for q in qq:
             assert np.linalg.norm(q.T @ q - np.eye(q.shape[1])) <= 1e-10
 

@@ -25,7 +25,9 @@ import numpy as np
 import pytest
 
 from tests.gpu_util import require_gpu, dev, mat_from_dev, empty_mat
-from oracle import hankel as HK, philox
+from tests.parity import (U_BF16_PAIR, U_F32, check_error_value, eval_bound,
+                          projector_distance, recon_distance)
+from oracle import hankel as HK, philox, tucker as TK
 from synth import config_spec, hankel_config_spec, markov_parameters
 
 pytestmark = pytest.mark.gpu
@@ -137,7 +139,9 @@ def test_c3_bf16x2_within_105_of_fp32(ctx, c3_inputs):
     e32 = _rhosvd(ctx, spec, x32)["rel_residual"]
     assert e2 <= 1.05 * e32, (e2, e32)
     e_ora = g["rhosvd_memo_truncated_rel_error_bf16"]
-    assert abs(e2 - e_ora) <= 1e-5 * e_ora + 1e-6, (e2, e_ora)
+    # relative: the pair and the BF16 hi/lo copies of Q_1 and H in the
+    # residual MMAs carry 2^-16 per operand, which moves e by ~1e-5 of itself
+    assert abs(e2 - e_ora) <= 5e-5 * e_ora, (e2, e_ora)
 
 
 # ---- 1024^3 (the bench's FP32 workload): sampled rows of every mode sketch --
@@ -249,3 +253,71 @@ def test_c2_pipeline_properties(ctx, c2_inputs):
         if form == "f32":
             # noise of relative size 1e-4 bounds any rank-32 error from below
             assert 0.9e-4 <= errs[1] <= 5e-4, errs
+
+
+def _host_tensor(t):
+    """A device tensor of torch layout (n_d..n_1) as the FP64 numpy array of
+    dims (n_1..n_d) holding the same values."""
+    import torch
+    return np.asarray(t.to(torch.float64).cpu().numpy().transpose(), order="F")
+
+
+@pytest.mark.parametrize("form", ["f32", "bf16x2", "bf16"])
+def test_c2_pipeline_matches_oracle(ctx, c2_inputs, form):
+    """The bench's timed step (krp_tucker_rhosvd, KRP_MEMO | KRP_TRUNCATE |
+    KRP_RESIDUAL) on the whole 1024^3 workload against the FP64 oracle run
+    on the same values (the FP32 tensor; hi + lo of the BF16 pair; the BF16
+    tensor) with the same rounded factors:
+      P2  ||X_hat_gpu - X_hat_ora||_F / ||X||_F <= 1e-5 (FP32 and hi/lo
+          forms), 5e-5 (BF16: Q_1 enters the core and residual MMAs as a
+          BF16 hi/lo pair, and the one-pass tree accumulates the mode-1 sketch
+          over 2^20 products per row in FP32);
+      P4  rank-32 projectors of every mode within the same bound;
+      P3  error values, 1e-5 relative widened by the measured P2 distance
+          and the residual pass's rounding bound (tests/parity.py), and the
+          value checked against the exact FP64 error of the library's own
+          result.
+    The distances are computed in the span of the two factor sets (no full
+    reconstruction); the error values by reconstruction one slab of the last
+    mode at a time."""
+    import torch
+    import paper_2507_23207_gb300 as K
+    spec, x32, xbf = c2_inputs
+    ranks, ells = list(spec.ranks), list(spec.ell)
+    if form == "f32":
+        x, xh, om_round, tol, unit = x32, _host_tensor(x32), "f32", 1e-5, U_F32
+    elif form == "bf16":
+        x, xh, om_round, tol, unit = xbf, _host_tensor(xbf), "bf16", 5e-5, U_BF16_PAIR
+    else:
+        x = K.krp_split_bf16x2(ctx, x32)
+        n_ = x32.numel()
+        xh = (_host_tensor(x.tensor[:n_].view(x32.shape))
+              + _host_tensor(x.tensor[n_:].view(x32.shape)))
+        om_round, tol, unit = "bf16", 1e-5, U_BF16_PAIR
+    core = torch.empty(int(np.prod(ranks)), dtype=torch.float32, device=dev())
+    facs = [torch.empty(n * r, dtype=torch.float64, device=dev()) for n, r in zip(spec.dims, ranks)]
+    flags = K.KRP_MEMO | K.KRP_TRUNCATE | K.KRP_RESIDUAL
+    res = K.krp_tucker_rhosvd(ctx, x, spec.dims, ranks, spec.oversample, spec.omega_seed, flags,
+                              core, facs)
+    torch.cuda.synchronize()
+    del x
+    torch.cuda.empty_cache()
+    g = core.cpu().numpy().astype(np.float64).reshape(ranks[::-1]).T
+    qs = [f.cpu().numpy().reshape(r, n).T for f, n, r in zip(facs, spec.dims, ranks)]
+    ora = TK.rhosvd_krp(xh, ells, spec.omega_seed, memo=True, omega_round=om_round)
+    g_o, q_o = TK.truncate_core(ora["G"], ora["Q"], ranks)
+    del ora
+    nx = float(np.sqrt(np.sum(np.square(xh))))
+    eta = recon_distance(g, qs, g_o, q_o) / nx
+    assert eta <= tol, (form, "P2", eta)
+    for i, (a, b) in enumerate(zip(qs, q_o)):
+        assert np.linalg.norm(a.T @ a - np.eye(a.shape[1])) <= 1e-10
+        assert projector_distance(a, b) <= tol, (form, "P4", i)
+    e_ora = TK.rel_error_slabs(xh, g_o, q_o)
+    e_self = TK.rel_error_slabs(xh, g, qs)
+    # ||X_hat|| = ||G|| (orthonormal factors)
+    rho = eval_bound(ranks, spec.dims, np.linalg.norm(g) / nx, e_self, unit)
+    check_error_value(res["rel_residual"], e_ora, e_self, eta, rho, form)
+    assert abs(res["x_norm"] - nx) <= 1e-6 * nx
+    print(f"{form}: P2 {eta:.2e}, e_gpu {res['rel_residual']:.6e}, e_self {e_self:.6e}, "
+          f"e_ora {e_ora:.6e}, rho {rho:.2e}")

@@ -14,6 +14,7 @@ import pytest
 from tests.gpu_util import (require_gpu, dev, mat_to_dev, mat_from_dev, empty_mat,
                             tensor_to_dev, tensor_from_dev, rel)
 from oracle import linalg as L, philox, tensor as T, tucker as TK
+from tests.parity import U_BF16_PAIR, check_error_value, eval_bound
 from synth import TuckerSpec, tucker_tensor
 
 pytestmark = pytest.mark.gpu
@@ -112,9 +113,13 @@ def test_bf16_tucker(ctx, spec, variant):
     nx = np.linalg.norm(xb)
     for q in qs:
         assert np.linalg.norm(q.T @ q - np.eye(q.shape[1])) <= 1e-12
-    d2 = np.linalg.norm(TK.reconstruct(g, qs) - TK.reconstruct(ora["G"], ora["Q"])) / nx
+    xh = TK.reconstruct(g, qs)
+    d2 = np.linalg.norm(xh - TK.reconstruct(ora["G"], ora["Q"])) / nx
     assert d2 <= 5e-5
-    assert abs(res["rel_residual"] - TK.rel_error(xb, ora["G"], ora["Q"])) <= 5e-5
+    e_self = TK.rel_error(xb, g, qs)
+    rho = eval_bound(ells, spec.dims, np.linalg.norm(xh) / nx, e_self, U_BF16_PAIR)
+    check_error_value(res["rel_residual"], TK.rel_error(xb, ora["G"], ora["Q"]), e_self, d2, rho,
+                      f"{spec.name}/{variant}")
 
 
 def _sthosvd_bf16_first(x, ells):
@@ -224,5 +229,9 @@ def test_bf16x2_tucker_truncated(ctx, variant):
     gg = core.cpu().numpy().astype(np.float64).reshape(ranks[::-1]).T
     qq = [f.cpu().numpy().reshape(r, n).T for f, n, r in zip(facs, spec.dims, ranks)]
     nx = np.linalg.norm(xe)
-    assert np.linalg.norm(TK.reconstruct(gg, qq) - TK.reconstruct(g2, q2)) / nx <= 5e-5
-    assert abs(res["rel_residual"] - TK.rel_error(xe, g2, q2)) <= 5e-5
+    xh = TK.reconstruct(gg, qq)
+    d2 = np.linalg.norm(xh - TK.reconstruct(g2, q2)) / nx
+    assert d2 <= 5e-5
+    e_self = TK.rel_error(xe, gg, qq)
+    rho = eval_bound(ranks, spec.dims, np.linalg.norm(xh) / nx, e_self, U_BF16_PAIR)
+    check_error_value(res["rel_residual"], TK.rel_error(xe, g2, q2), e_self, d2, rho, variant)

@@ -225,3 +225,25 @@ def test_compressed_problem_behind_the_stored_full_size_values(form):
     assert e_r == pytest.approx(TK.rel_error(x, g2, q2), rel=1e-10)
     assert gn == pytest.approx(T.frob(g2), rel=1e-12)
     assert e_l < e_r < 1.0
+
+
+@pytest.mark.parametrize("dims,slab", [((12, 10, 9), 4), ((7, 8, 6, 5), 3), ((9, 11, 13), 64)])
+def test_slab_residual_is_the_explicit_residual(dims, slab):
+    """rel_error_slabs (reconstruction one slab of the last mode at a time)
+    equals the explicit residual, gives 0 on an exact-rank tensor, and obeys
+    e^2 = ||X||^2 - ||G||^2 when G = X x {Q_i^T} (X_hat an orthogonal
+    projection of X, Sec. 5.2)."""
+    core = tuple(min(3, n) for n in dims)
+    x, _, _ = tucker_tensor(small_spec(dims, core, noise=1e-2, seed=91))
+    res = TK.rhosvd_krp(x, [4] * len(dims), seed=5, memo=True)
+    e = TK.rel_error_slabs(x, res["G"], res["Q"], slab=slab)
+    assert e == pytest.approx(TK.rel_error(x, res["G"], res["Q"]), rel=1e-12)
+    e2_identity = (T.frob(x) ** 2 - T.frob(res["G"]) ** 2) / T.frob(x) ** 2
+    assert e ** 2 == pytest.approx(e2_identity, rel=1e-9)
+    x0, _, _ = tucker_tensor(small_spec(dims, core, noise=0.0, seed=91))
+    r0 = TK.rhosvd_krp(x0, [4] * len(dims), seed=5, memo=True)
+    assert TK.rel_error_slabs(x0, r0["G"], r0["Q"], slab=slab) <= 1e-12
+    # a wrong last-mode slab (rows of Q_d shifted) is caught
+    qbad = list(res["Q"])
+    qbad[-1] = np.roll(qbad[-1], 1, axis=0)
+    assert TK.rel_error_slabs(x, res["G"], qbad, slab=slab) > 10 * e

@@ -43,7 +43,12 @@ def measured_peaks():
             "sm_max_mhz": 2070.0}, "fallback"
 
 
-def fp32_ffma_peak_tflops(sm_mhz: float, sms: int = 152) -> float:
+def sm_count() -> int:
+    import torch
+    return int(torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count)
+
+
+def fp32_ffma_peak_tflops(sm_mhz: float, sms: int) -> float:
     # 128 FP32 lanes per SM, one FMA (2 flops) per lane per clock
     return sms * 128 * 2 * sm_mhz * 1e6 / 1e12
 
@@ -190,8 +195,7 @@ def run_ours(args, rank, world, local_rank):
                          "bytes_per_elem": 4 if form == "bf16x2" else x.element_size()}
     # dominant-kernel roofline from the launch trace of the timed FP32 steps
     kr = trace_roofline(spec, results["f32"], peaks, args)
-    kr["mode1_sketch_alone"] = kernel_roofline(ctx, spec, x32, dev, stream, peaks,
-                                               results["f32"]["clocks"], args)
+    sketch = sketch_rooflines(ctx, spec, forms, dev, stream, peaks, results["f32"]["clocks"], args)
     # e2e through the C ABI with host buffers (pinned), FP32 form
     e2e = e2e_run(ctx, spec, x32, args) if rank == 0 and not args.no_e2e else None
     extra = {}
@@ -204,7 +208,7 @@ def run_ours(args, rank, world, local_rank):
         extra["batched_512_tucker"] = batch_run(ctx, dev, stream, args)
         extra["batched_64_hankel"] = hankel_batch_run(ctx, dev, stream, args)
     ctx.close()
-    return spec, results, kr, e2e, peaks, peak_src, (sk, co, rs, qr), extra
+    return spec, results, kr, sketch, e2e, peaks, peak_src, (sk, co, rs, qr), extra
 
 
 def _timed(stream, step, reps, warm):
@@ -413,9 +417,9 @@ def c4_run(ctx, dev, stream, args, reps=10, warm=3):
 
 
 # DRAM traffic (read + write bytes) of one big launch of the dominant kernel
-# at 1024^3: ncu at 512^3 measured 537.0 MB read (X once) and 43.0 MB write
-# (the (N/n1) x l output); X scales x8 and the output x4 to 1024^3
-# (profiles/ncu_f32_kernels_512cubed.md).  Set to None if the kernel changes.
+# at 1024^3: an ncu capture at 512^3 measured 537.0 MB read (X once) and
+# 43.0 MB write (the (N/n1) x l output); X scales x8 and the output x4 to
+# 1024^3.  Set to None if the kernel changes.
 TTM48_TRAFFIC_PER_BIG_LAUNCH = 537.0e6 * 8 + 43.0e6 * 4
 
 
@@ -432,7 +436,8 @@ def trace_roofline(spec, f32, peaks, args):
     tr = f32.get("trace") or []
     ttm = [t for name, t in tr if name == "gemm_tn_tile<48>"]
     mhz = (f32.get("clocks") or {}).get("sm_max_mhz") or peaks.get("sm_max_mhz", 2070.0)
-    peak = fp32_ffma_peak_tflops(mhz)
+    sms = sm_count()
+    peak = fp32_ffma_peak_tflops(mhz, sms)
     if len(ttm) != 4 * args.steps:
         return {"kernel": "gemm_tn_tile_kernel<48>", "error": f"trace saw {len(ttm)} launches"}
     big = [t for i, t in enumerate(ttm) if i % 4 < 2]
@@ -445,38 +450,67 @@ def trace_roofline(spec, f32, peaks, args):
             "algorithmic_bytes": n * 4 + n / spec.dims[0] * ell * 4,
             "ms_per_launch": round(t_big, 4), "launches_averaged": len(big),
             "kernel_share_of_step": round(sum(ttm) / args.steps / step_ms, 4),
-            "peak_note": f"FP32 FFMA peak = 152 SMs x 128 lanes x 2 flop x {mhz:.0f} MHz",
+            "peak_note": f"FP32 FFMA peak = {sms} SMs x 128 lanes x 2 flop x {mhz:.0f} MHz",
             "timing": "CUDA events after every launch on the context stream over the timed steps"}
 
 
-def kernel_roofline(ctx, spec, x32, dev, stream, peaks, clk, args):
+def sketch_rooflines(ctx, spec, forms, dev, stream, peaks, clk, args):
+    """The all-mode KRP sketch alone (krp_sketch_all_modes with the memoized
+    factor set, Sec. 5.1) in each form, against its own roofline: FP32 on CUDA
+    cores (4 N l flops against the FFMA peak), the BF16 and BF16 hi/lo forms
+    on tensor cores (one pass over X against the measured HBM bandwidth;
+    their 4 N l flops need well under the tensor peak).  The kernels of one
+    call and their times come from the launch trace."""
     import torch
     import paper_2507_23207_gb300 as K
     ell = max(spec.ell)
-    om = [torch.empty((ell, n), dtype=torch.float32, device=dev) for n in spec.dims]
-    K.krp_gen_factors(ctx, 0, 0, 0, spec.dims, ell, om)
-    y = torch.empty((ell, spec.dims[0]), dtype=torch.float32, device=dev)
-    for _ in range(3):
-        K.krp_sketch_mode(ctx, x32, spec.dims, 0, om, ell, y)
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    reps = max(3, args.steps)
-    torch.cuda.synchronize()
-    e0.record(stream)
-    for _ in range(reps):
-        K.krp_sketch_mode(ctx, x32, spec.dims, 0, om, ell, y)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    ms = e0.elapsed_time(e1) / reps
-    flops = 2.0 * spec.numel * ell
+    n = spec.numel
     mhz = (clk or {}).get("sm_max_mhz") or peaks.get("sm_max_mhz", 2070.0)
-    peak = fp32_ffma_peak_tflops(mhz)
-    ach = flops / (ms * 1e-3) / 1e12
-    return {"kernel": "krp_slab_mttkrp_kernel (FP32, mode-1 KRP sketch)", "bound": "alu",
-            "achieved": round(ach, 3), "peak": round(peak, 3), "unit": "TFLOP/s",
-            "frac": round(ach / peak, 4), "traffic": None, "ms": round(ms, 4),
-            "gbs": round(spec.numel * 4 / (ms * 1e-3) / 1e9, 1),
-            "peak_note": f"FP32 FFMA peak = 152 SMs x 128 lanes x 2 flop x {mhz:.0f} MHz"}
+    sms = sm_count()
+    ffma = fp32_ffma_peak_tflops(mhz, sms)
+    hbm = float(peaks["hbm_gbs"])
+    reps = max(5, args.steps)
+    out = {"workload": f"krp_sketch_all_modes, {'x'.join(map(str, spec.dims))}, l = {ell}, "
+                       "memoized factor set (one pass over X for the tensor-core forms)",
+           "timing": f"CUDA events over {reps} calls after 3 warm-ups; kernel times from the "
+                     "launch trace (an event after every launch) over 3 more calls"}
+    for form, x in forms:
+        dt = torch.float32 if form == "f32" else torch.bfloat16
+        om = [torch.empty((ell, m), dtype=dt, device=dev) for m in spec.dims]
+        K.krp_gen_factors(ctx, spec.omega_seed, K.KRP_DRAW_MEMO, K.KRP_TAG_OMEGA, spec.dims, ell, om)
+        ys = [torch.empty((ell, m), dtype=torch.float32, device=dev) for m in spec.dims]
+        ms, _ = _timed(stream, lambda: K.krp_sketch_all_modes(ctx, x, spec.dims, om, ell, ys),
+                       reps=reps, warm=3)
+        K.krp_trace_begin(ctx)
+        for _ in range(3):
+            K.krp_sketch_all_modes(ctx, x, spec.dims, om, ell, ys)
+        tr = K.krp_trace_end(ctx)
+        agg = {}
+        for nm, t in tr:
+            agg[nm] = agg.get(nm, 0.0) + t / 3
+        top = max(agg, key=agg.get)
+        b = 4 if form in ("f32", "bf16x2") else 2
+        gbs = n * b / (ms * 1e-3) / 1e9
+        tfl = 4.0 * n * ell / (ms * 1e-3) / 1e12
+        e = {"ms": round(ms, 4), "gbs": round(gbs, 1), "tflops": round(tfl, 2),
+             "bytes_per_elem": b, "kernels_ms": {k: round(v, 4) for k, v in
+                                                 sorted(agg.items(), key=lambda kv: -kv[1])}}
+        t_top = agg[top]
+        if form == "f32":
+            e["roofline"] = {"bound": "alu", "achieved": round(tfl, 3), "peak": round(ffma, 3),
+                             "unit": "TFLOP/s", "frac": round(tfl / ffma, 4),
+                             "peak_note": f"FP32 FFMA peak = {sms} SMs x 128 lanes x 2 flop x "
+                                          f"{mhz:.0f} MHz (derived)"}
+        else:
+            e["roofline"] = {"bound": "hbm", "achieved": round(gbs, 1), "peak": hbm,
+                             "unit": "GB/s", "frac": round(gbs / hbm, 4),
+                             "peak_note": "hbm_gbs of MEASURED_PEAKS.json"}
+            e["dominant_kernel"] = {"name": top, "ms": round(t_top, 4),
+                                    "gbs": round(n * b / (t_top * 1e-3) / 1e9, 1),
+                                    "frac": round(n * b / (t_top * 1e-3) / 1e9 / hbm, 4)}
+        out[form] = e
+        del om, ys
+    return out
 
 
 def e2e_run(ctx, spec, x32, args):
@@ -501,44 +535,90 @@ def e2e_run(ctx, spec, x32, args):
     return {"ms": ms, "h2d": spec.numel * 4, "d2h": d2h, "resid": res["rel_residual"]}
 
 
-def _oracle_sample(spec, k, g0, us):
-    """Seconds of one oracle run (RHOSVD-KRP-MEMO + truncation + explicit
-    residual) on the slab X[:, :, :k], and the slab's entry count."""
-    from oracle import philox, tucker as TK
-    from synth.tucker import expand_tucker
+def _oracle_sample(spec, k):
+    """One oracle run (RHOSVD-KRP-MEMO + truncation + explicit residual, in
+    the order of oracle.tucker.rhosvd_krp) on the slab X[:, :, :k], timed per
+    phase in the paper's categories (RNG, mult/KRP, QR, core) plus truncation
+    and residual.  Returns (phase seconds, total seconds, entries)."""
+    from oracle import linalg as LA, philox, tensor as T, tucker as TK
+    from synth.tucker import expand_tucker, tucker_factors
+    g0, us = tucker_factors(spec)
     us_k = list(us)
     us_k[-1] = us[-1][:k]
     xs = philox.round_to_f32(expand_tucker(g0, us_k))
+    ells = list(spec.ell)
+    ph = {}
     t0 = time.perf_counter()
-    ora = TK.rhosvd_krp(xs, list(spec.ell), spec.omega_seed, memo=True, omega_round="f32")
-    g2, q2 = TK.truncate_core(ora["G"], ora["Q"], list(spec.ranks))
+    shared = TK.memo_factors(spec.omega_seed, xs.shape, max(ells), "f32")
+    t1 = time.perf_counter()
+    ys = [T.mttkrp(xs, [f[:, :ells[i]] if j != i else None for j, f in enumerate(shared)], i)
+          for i in range(xs.ndim)]
+    t2 = time.perf_counter()
+    qs = [LA.householder_qr(y)[0] for y in ys]
+    t3 = time.perf_counter()
+    g = T.multi_ttm(xs, [q.T for q in qs])
+    t4 = time.perf_counter()
+    g2, q2 = TK.truncate_core(g, qs, list(spec.ranks))
+    t5 = time.perf_counter()
     TK.rel_error(xs, g2, q2)
-    return time.perf_counter() - t0, xs.size
+    t6 = time.perf_counter()
+    ph = {"rng_s": t1 - t0, "mult_krp_s": t2 - t1, "qr_s": t3 - t2, "core_s": t4 - t3,
+          "truncate_s": t5 - t4, "residual_s": t6 - t5}
+    return ph, t6 - t0, xs.size
 
 
-def cpu_baseline(spec, target_s=10.0, k=None):
+def _cpu_model() -> str:
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.lower().startswith("model name"):
+                return ln.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    import platform
+    return platform.processor() or platform.machine()
+
+
+def _sample_in_subprocess(spec_args, k, threads):
+    """The oracle sample in a fresh process (no CUDA state), with the BLAS and
+    OpenMP thread counts fixed before numpy loads (threads None = all cores)."""
+    env = dict(os.environ)
+    if threads is not None:
+        for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS",
+                  "BLIS_NUM_THREADS", "VECLIB_MAXIMUM_THREADS"):
+            env[v] = str(threads)
+    cmd = [sys.executable, os.path.abspath(__file__), "--cpu-sample", str(k)] + spec_args
+    res = subprocess.run(cmd, capture_output=True, text=True, env=env, timeout=1800)
+    if res.returncode != 0:
+        raise RuntimeError(res.stderr[-500:])
+    return json.loads(res.stdout.strip().splitlines()[-1])
+
+
+def cpu_baseline(spec, spec_args, target_s=10.0, k=None, threads=None):
     """The FP64 oracle (RHOSVD-KRP-MEMO + truncation + explicit residual) on a
-    slab sample X[:, :, :k] of the same workload, timed on the host cores.
+    slab sample X[:, :, :k] of the same workload, timed on the host cores
+    (threads None: all of them; 1: a single thread) with per-phase times.
     Without k, the slab depth doubles from max(l) until one sample takes at
-    least target_s seconds (or the slab is the whole tensor), and that
-    sample is reported."""
-    from synth.tucker import tucker_factors
-    g0, us = tucker_factors(spec)
+    least target_s seconds (or the slab is the whole tensor), and that sample
+    is reported."""
     if k is None:
         k = max(spec.ell)  # the slab depth must allow l_d columns in the last mode
         while True:
-            dt, n = _oracle_sample(spec, k, g0, us)
-            if dt >= target_s or k >= spec.dims[-1]:
+            r = _sample_in_subprocess(spec_args, k, threads)
+            if r["seconds"] >= target_s or k >= spec.dims[-1]:
                 break
             k = min(spec.dims[-1], 2 * k)
     else:
-        dt, n = _oracle_sample(spec, k, g0, us)
+        r = _sample_in_subprocess(spec_args, k, threads)
+    dt, n = r["seconds"], r["entries"]
     gbs = 3 * n * 4 / dt / 1e9
-    threads = os.cpu_count() or 1
-    return {"value": round(gbs, 4), "unit": "GB/s", "cores": threads, "kind": "oracle",
+    cores = threads if threads is not None else (os.cpu_count() or 1)
+    return {"value": round(gbs, 4), "unit": "GB/s", "cores": cores, "kind": "oracle",
+            "cpu_model": _cpu_model(),
             "sample": f"slab sample X[:, :, :{k}] of {spec.name} ({n} entries), one "
                       f"RHOSVD-KRP-MEMO + truncation + explicit residual, {dt:.2f} s",
-            "seconds": round(dt, 3), "slab_depth": k}
+            "seconds": round(dt, 3), "slab_depth": k,
+            "phases_s": {p: round(v, 3) for p, v in r["phases"].items()}}
 
 
 def workload(args):
@@ -571,7 +651,15 @@ def main():
                     help="tensors in the batched workload with --batch-only")
     ap.add_argument("--hankel-only", action="store_true",
                     help="run only the 1024 x 1024 block-Hankel measurement (for profiling)")
+    ap.add_argument("--cpu-sample", type=int, default=None,
+                    help="(internal) time one oracle sample of slab depth K and print it")
     args = ap.parse_args()
+    spec_args = ["--config", args.config] + (["--dims", args.dims] if args.dims else [])
+
+    if args.cpu_sample is not None:
+        ph, dt, n = _oracle_sample(workload(args), args.cpu_sample)
+        print(json.dumps({"phases": ph, "seconds": dt, "entries": n}))
+        return
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
@@ -582,17 +670,18 @@ def main():
         spec = workload(args)
         # the slab depth is chosen once (that search is the first warm-up),
         # then every step times the oracle on the same slab
-        k = cpu_baseline(spec, target_s=4.0)["slab_depth"]
+        k = cpu_baseline(spec, spec_args, target_s=4.0)["slab_depth"]
         for _ in range(args.warmup - 1):
-            cpu_baseline(spec, k=k)
-        vals = [cpu_baseline(spec, k=k) for _ in range(max(1, args.steps))]
+            cpu_baseline(spec, spec_args, k=k)
+        vals = [cpu_baseline(spec, spec_args, k=k) for _ in range(max(1, args.steps))]
         v = float(np.median([c["value"] for c in vals]))
         line = {"impl": "reference", "metric": METRIC, "value": round(v, 4), "unit": "GB/s",
                 "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
                 "ms_per_step": round(1e3 * float(np.median([c["seconds"] for c in vals])), 2),
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
                 "data": "synthetic", "config": {"workload": spec.name + " slab sample"},
-                "cpu_baseline": {f: vals[-1][f] for f in ("kind", "cores", "sample")} | {"value": round(v, 4)},
+                "cpu_baseline": {f: vals[-1][f] for f in ("kind", "cores", "sample", "cpu_model",
+                                                          "phases_s")} | {"value": round(v, 4)},
                 "e2e": {"value": round(v, 4), "unit": "GB/s", "h2d_bytes_per_step": 0,
                         "d2h_bytes_per_step": 0}}
         print(json.dumps(line))
@@ -627,8 +716,8 @@ def main():
     if world > 1:
         import torch
         torch.distributed.init_process_group("nccl")
-    spec, results, kr, e2e, peaks, peak_src, (sk, co, rs, qr), extra = run_ours(args, rank, world,
-                                                                                local_rank)
+    spec, results, kr, sketch, e2e, peaks, peak_src, (sk, co, rs, qr), extra = run_ours(
+        args, rank, world, local_rank)
     if rank != 0:
         return
     f32 = results["f32"]
@@ -640,7 +729,10 @@ def main():
     cpu = None
     if not args.no_cpu and world == 1:   # the host baseline is timed at N = 1 only
         try:
-            cpu = cpu_baseline(spec)
+            cpu = cpu_baseline(spec, spec_args)
+            one = cpu_baseline(spec, spec_args, target_s=5.0, threads=1)
+            cpu["one_thread"] = {f: one[f] for f in ("value", "cores", "sample", "seconds",
+                                                     "phases_s")}
         except Exception as exc:  # the GPU line is still printed
             cpu = {"error": repr(exc)[:300]}
     line = {
@@ -659,6 +751,7 @@ def main():
         "clocks": f32["clocks"],
         "gpu_launches": f32["launches"],
         "roofline": kr,
+        "sketch": sketch,
         "peaks_source": peak_src,
     }
     if "bf16" in results:

@@ -81,11 +81,14 @@ size_t tc_workspace_bytes(int64_t n1, int64_t S, int L);
 // n1 x c, H FP32 c x S, on tensor cores (c <= 64, n1 % 8 == 0)
 // One pass over BF16 X (n1, n2, T) for the dimension tree: Y1 (n1 x L),
 // Y2 (n2 x L) and C (T x L, the contraction of modes 1 and 2 weighted by the
-// factors); w is the T x L table of Khatri-Rao weights of modes 3..d.
+// factors); w is the T x L table of Khatri-Rao weights of modes 3..d.  Xlo
+// (optional): the lo plane of a BF16 hi/lo X.
 bool tc_tree_supported(int64_t n1, int L);
+// workspace of the tree's C partials (beyond tc_workspace_bytes)
+size_t tc_tree_workspace_bytes(int64_t n1, int64_t n2, int64_t T, int L);
 void tc_tree_bf16(const __nv_bfloat16* X, int64_t n1, int64_t n2, int64_t T,
                   const __nv_bfloat16* Om1, const __nv_bfloat16* Om2, const float* w, int L,
-                  float* Y1, float* Y2, float* C);
+                  float* Y1, float* Y2, float* C, const __nv_bfloat16* Xlo = nullptr);
 bool tc_residual_supported(int64_t n1, int c);
 size_t tc_residual_workspace_bytes(int64_t n1, int64_t S);
 void tc_residual_bf16(const __nv_bfloat16* X, int64_t n1, int64_t S, const double* Q1, int c,

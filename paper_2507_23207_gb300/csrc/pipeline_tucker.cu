@@ -218,7 +218,9 @@ size_t sketch_workspace_bytes(const SketchArgs& a, bool) {
   int64_t dmax = 1;
   for (int j = 0; j < a.d; ++j) dmax = std::max<int64_t>(dmax, a.dims[j]);
   b += mttkrp_first_f32_workspace_bytes(a.N / std::max<int64_t>(1, a.dims[0]), dmax);
-  if (bf16_family(a.xt)) b += tc_workspace_bytes(n1, a.N / n1, a.ell);
+  if (bf16_family(a.xt))
+    b += tc_workspace_bytes(n1, a.N / n1, a.ell) +
+         tc_tree_workspace_bytes(n1, a.dims[1], a.N / (n1 * a.dims[1]), a.ell);
   return b + (1 << 20);
 }
 
@@ -258,8 +260,9 @@ void sketch_all_modes(const SketchArgs& a, float* const* Y) {
   for (int j = 0; j < a.d; ++j) KRP_REQUIRE(a.omega[j], "omega[%d] is NULL", j);
   const int64_t n1 = a.dims[0], S = a.N / n1;
   const float* f32v[KRP_MAXD];
-  f32_factor_views(a, f32v);
-  if (a.xt == KRP_BF16 && tc_tree_supported(n1, a.ell)) {
+  if (bf16_family(a.xt) && tc_tree_supported(n1, a.ell)) {
+    // FP32 copies of the factors are needed only for the modes past the tree
+    if (a.d > 3) f32_factor_views(a, f32v);
     // one pass over X for every mode (fused dimension tree on tensor cores)
     const int64_t n2 = a.dims[1], T = S / n2;
     Radix R;
@@ -273,11 +276,13 @@ void sketch_all_modes(const SketchArgs& a, float* const* Y) {
     float* C = (a.d == 3) ? Y[2] : current()->ws.take<float>((size_t)T * a.ell);
     tc_tree_bf16(static_cast<const __nv_bfloat16*>(a.X), n1, n2, T,
                  static_cast<const __nv_bfloat16*>(a.omega[0]),
-                 static_cast<const __nv_bfloat16*>(a.omega[1]), w, a.ell, Y[0], Y[1], C);
+                 static_cast<const __nv_bfloat16*>(a.omega[1]), w, a.ell, Y[0], Y[1], C,
+                 lo_plane(a.X, a.xt, a.N));
     for (int n = 2; n < a.d && a.d > 3; ++n)
       diag_contract_f32(C, a.d - 2, a.dims + 2, T, n - 2, f32v + 2, a.ell, Y[n]);
     return;
   }
+  f32_factor_views(a, f32v);
   big_mttkrp_first(a.X, a.xt, n1, a.d - 1, a.dims + 1, a.omega + 1, a.ell, Y[0]);
   float* B = current()->ws.take<float>((size_t)S * a.ell);
   big_gemm_tn(a.X, a.xt, n1, S, f32v[0], static_cast<const __nv_bfloat16*>(a.omega[0]), nullptr,
@@ -506,7 +511,9 @@ void tucker_pipeline(bool sequential, const void* X, krp_dtype xt, int d, const 
   }
   need += 4 * ws_bytes((size_t)core_l, 8) + 2 * ws_bytes((size_t)core_l, 4);
   need += sym_eig_workspace_bytes(d);
-  if (bf16_family(xt)) need += tc_workspace_bytes(dims[0], N / dims[0], 2 * ellmax);
+  if (bf16_family(xt))
+    need += tc_workspace_bytes(dims[0], N / dims[0], 2 * ellmax) +
+            tc_tree_workspace_bytes(dims[0], dims[1], N / (dims[0] * dims[1]), ellmax);
   if (bf16_family(xt) && resid) need += tc_residual_workspace_bytes(dims[0], N / dims[0]);
   need += 4 << 20;
   ensure_workspace(c, need);

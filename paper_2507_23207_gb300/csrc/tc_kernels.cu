@@ -133,6 +133,23 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
   for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+// The same load without the wait: the registers are valid after tmem_ld_wait().
+__device__ __forceinline__ void tmem_ld16_issue(uint32_t taddr, float* v) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+      "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+        "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+__device__ __forceinline__ void tmem_ld_wait() {
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
 // Shared-memory matrix descriptor, 128-byte swizzle (sm_100 layout):
 // start>>4 [0,14), leading-byte-offset>>4 [16,30), stride-byte-offset>>4
 // [32,46), version 1 at [46,48), layout SWIZZLE_128B (=2) at [61,64).
@@ -516,27 +533,45 @@ __global__ void __launch_bounds__(kThreads, 1)
 // ----------------------------------------------------------------------------
 // Dimension tree in one pass over X (Sec. 5.1, memoization): X viewed as
 // (n1, n2, T), T = prod_{j>=3} n_j, w[t, k] = prod_{j>=3} Omega_j[i_j(t), k].
-// A CTA owns one 128-row block b of i2 and a range of slabs t; every stage
-// holds X[128 i1, 128 i2, t] (two 64-wide TMA boxes) and is read twice by the
-// tensor core:
-//   MMA1 (K-major, rows i2, K = i1):  D1[i2, k] = sum_i1 X Omega1      (per t)
-//   MMA2 (MN-major, M = i1, K = i2):  D2[i1, k] += sum_i2 X B2_t,
-//        B2_t[i2, k] = Omega2[i2, k] w[t, k] as a BF16 hi/lo pair written to
-//        shared memory by a producer warpgroup (D2 accumulates over all t).
-// Epilogue per t: Y2[i2, k] += D1 w[t, k] (registers across t) and
-// C[t, k] += sum_i2 Omega2[i2, k] D1[i2, k]; at the end D2 -> Y1.
-// For d = 3, C is Y3 itself.
+// Work items are (i2 block b of 128 rows, slab t).  The i1 range is cut into
+// segments of kseg chunks of 128 rows, so that a segment's accumulators fit
+// in TMEM; a CTA owns one segment and a contiguous range of items (b-major).
+// It keeps the segment's rows of Omega1 resident in shared memory (loaded
+// once by TMA) and streams the tiles X[128 i1, 128 i2, t] (two 64-wide
+// boxes; with XLO also the lo plane's two boxes) through an NS-stage ring.
+// Each tile is read twice by the tensor core:
+//   MMA1 (K-major, rows i2, K = i1): D1[i2, k] = sum_i1 X Omega1, per item
+//        (a partial over the segment's i1);
+//   MMA2 (MN-major, M = i1, K = i2): D2[i1, :] += X [B2hi_t | B2lo_t], one
+//        MMA of width 2N per K step.  B2_t[i2, k] = Omega2[i2, k] w[t, k] is
+//        exact as a BF16 hi/lo pair (hi in operand rows 0..N-1, lo in rows
+//        N..2N-1), written to shared memory per item by a producer
+//        warpgroup; D2 accumulates over a group of items, and its two column
+//        halves are summed when it is stored.
+// XLO adds Xlo Omega1 to D1 and Xlo B2hi_t to D2's hi half (the dropped
+// Xlo B2lo_t is below 2^-16 relative).
+// Long accumulation chains in TMEM lose accuracy (the error of a chain of m
+// MMA accumulations grows about linearly in m), so with drain > 0 the CTA's
+// items are cut into groups of `drain` items (chains of 8 drain K steps per
+// accumulator); after each group the epilogue adds D2 into the CTA's FP32
+// partials of Y1.  With nd2 = 2 buffers the MMAs fill one while the other is
+// stored; with one buffer the next group waits for the store.  Without
+// draining D2 holds all of the CTA's items and is stored once at the end.
+// Epilogue per item: Y2[i2, k] += D1 w[t, k] (registers, flushed when the
+// block b changes) and each warp's 32-row partial of C[t, k] = sum_i2
+// Omega2[i2, k] D1[i2, k] (warp reduce-scatter) stored into its own slot of
+// the C partials; second kernels sum the Y1 and C partials in a fixed order
+// (no atomics on the contended C rows).  For d = 3, C is Y3 itself.
 // Warp reduce-scatter of CNT per-lane values: on return the warp's sums over
-// its 32 lanes have been added to dst[t + T * (kbase + j)] (j < CNT, skipping
-// kbase + j >= L).  Each halving step exchanges half of the values with the
-// lane BIT apart (CNT/2 shuffles) and keeps the half selected by that lane
-// bit; the bits left when CNT is odd are summed by a plain butterfly.  For
-// 16 values: 8 + 4 + 2 + 1 + 1 = 16 shuffles instead of 16 x 5, and the
-// atomics are spread over the lanes.
+// its 32 lanes have been handed to sink(kbase + j, sum) by one lane each
+// (j < CNT).  Each halving step exchanges half of the values with the lane
+// BIT apart (CNT/2 shuffles) and keeps the half selected by that lane bit;
+// the bits left when CNT is odd are summed by a plain butterfly.  For 16
+// values: 8 + 4 + 2 + 1 + 1 = 16 shuffles instead of 16 x 5.
 template <int CNT, int BIT>
 struct WarpReduceScatter {
-  __device__ __forceinline__ static void run(float* v, int lane, int kbase, float* dst, int64_t t,
-                                             int64_t T, int L) {
+  template <class Sink>
+  __device__ __forceinline__ static void run(float* v, int lane, int kbase, Sink&& sink) {
     if constexpr (BIT > 0 && CNT % 2 == 0) {
       constexpr int H = CNT / 2;
       const bool hb = (lane & BIT) != 0;
@@ -546,7 +581,7 @@ struct WarpReduceScatter {
         const float send = hb ? v[j] : v[H + j];
         v[j] = keep + __shfl_xor_sync(0xffffffffu, send, BIT);
       }
-      WarpReduceScatter<H, BIT / 2>::run(v, lane, kbase + (hb ? H : 0), dst, t, T, L);
+      WarpReduceScatter<H, BIT / 2>::run(v, lane, kbase + (hb ? H : 0), sink);
     } else {
 #pragma unroll
       for (int j = 0; j < CNT; ++j) {
@@ -558,50 +593,57 @@ struct WarpReduceScatter {
       constexpr int kMask = BIT > 0 ? 2 * BIT - 1 : 0;  // the lane bits still shared
       if ((lane & kMask) == 0) {
 #pragma unroll
-        for (int j = 0; j < CNT; ++j)
-          if (kbase + j < L) atomicAdd(dst + t + T * (kbase + j), v[j]);
+        for (int j = 0; j < CNT; ++j) sink(kbase + j, v[j]);
       }
     }
   }
 };
 
-// X stages of the fused tree: four while they fit beside the two B2 buffers
-__host__ __device__ constexpr int tree_stages(int N) { return N <= 48 ? 4 : 3; }
-
 struct TreeArgs {
   const float* w;            // T x L
   const __nv_bfloat16* om2;  // n2 x L (column-major)
-  float* Y1;                 // n1 x L
   float* Y2;                 // n2 x L
-  float* C;                  // T x L
-  float* Yw;                 // per-CTA partials of Y1, [cta][k < N][i1 < n1p], or null (atomics)
-  int64_t n1, n2, T, t_per_cta, n1p;
-  int L, nb, kchunks;        // kchunks = ceil(n1 / 128)
+  float* Cw;                 // C partials: [(seg nb + b) 4 + warp][t][k < N]
+  float* Yw;                 // Y1 partials: [cta][k < N][kseg * 128 rows of its segment]
+  int64_t n2, T, items;      // items = nb * T
+  int L, nb, kch, kseg, cps; // kch = ceil(n1 / 128); cps = CTAs per segment
+  int drain, nd2;            // items per D2 accumulation chain (0: all), D2 buffers
 };
 
-template <int N>
+// TMEM columns of the tree: D1 double buffer (2N) + nd2 buffers of the
+// segment's D2 (2N per chunk)
+__host__ __device__ constexpr int tree_kseg_max(int N, int nd2) {
+  return (512 - 2 * N) / (nd2 * 2 * N);
+}
+
+template <int N, int NS, bool XLO>
 __global__ void __launch_bounds__(320, 1)
     tc_tree_kernel(const __grid_constant__ CUtensorMap mapX,
+                   const __grid_constant__ CUtensorMap mapXlo,
                    const __grid_constant__ CUtensorMap mapF, const TreeArgs P, int* status) {
-  constexpr int NS = tree_stages(N);
   constexpr uint32_t kXBox = 64 * 128 * 2;            // 64 i1 x 128 i2
+  constexpr uint32_t kStage = (XLO ? 4 : 2) * kXBox;  // hi boxes, then lo boxes
   constexpr uint32_t kFBox = N * 128;                 // N rows (k) x 64 i1
-  constexpr uint32_t kStage = 2 * kXBox + 2 * kFBox;
-  constexpr uint32_t kB2Atom = N * 128;               // N rows (k) x 64 i2
-  constexpr uint32_t kB2Buf = 4 * kB2Atom;            // hi (2 atoms) + lo (2 atoms)
+  constexpr uint32_t kB2Atom = 2 * N * 128;           // 2N rows (hi, lo) x 64 i2
+  constexpr uint32_t kB2Buf = 2 * kB2Atom;            // i2 0..63 and 64..127
   constexpr uint32_t kIdesc1 = idesc_bf16(kBM, N, false, false);
-  constexpr uint32_t kIdesc2 = idesc_bf16(kBM, N, true, false);
+  constexpr uint32_t kIdesc2 = idesc_bf16(kBM, 2 * N, true, false);
+  constexpr uint32_t kIdesc2h = idesc_bf16(kBM, N, true, false);
+  static_assert(N % 16 == 0 && N <= 64, "tree width");
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-  uint8_t* b2 = smem + NS * kStage;
+  uint8_t* fres = smem;                           // 2 kseg boxes of Omega1 (resident)
+  uint8_t* xst = fres + 2 * P.kseg * kFBox;       // X ring
+  uint8_t* b2 = xst + NS * kStage;                // two B2 buffers
   Bars* bars = reinterpret_cast<Bars*>(b2 + 2 * kB2Buf);
-  __shared__ uint64_t b2full[2], b2empty[2];
+  __shared__ uint64_t b2full[2], b2empty[2], fbar, d2full[2], d2empty[2];
   __shared__ float wsm[2][N];  // w[t, :] beside B2_t, same double buffering
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int b = blockIdx.x % P.nb;
-  const int64_t t0 = static_cast<int64_t>(blockIdx.x / P.nb) * P.t_per_cta;
-  const int64_t t1 = min(P.T, t0 + P.t_per_cta);
-  const int kch = P.kchunks;
+  const int seg = blockIdx.x / P.cps;
+  const int rk = blockIdx.x % P.cps;
+  const int64_t j0 = P.items * rk / P.cps, j1 = P.items * (rk + 1) / P.cps;
+  const int c0 = seg * P.kseg;                        // first 128-row chunk of i1
+  const int kc = min(P.kseg, P.kch - c0);             // chunks in this segment
   const uint32_t tmem_cols = 512;
 
   if (threadIdx.x == 0) {
@@ -614,7 +656,10 @@ __global__ void __launch_bounds__(320, 1)
       mbar_init(smem_u32(&bars->tempty[a]), 4);
       mbar_init(smem_u32(&b2full[a]), 4);
       mbar_init(smem_u32(&b2empty[a]), 1 + 4);  // MMA commit + four epilogue warps (wsm)
+      mbar_init(smem_u32(&d2full[a]), 1);
+      mbar_init(smem_u32(&d2empty[a]), 4);
     }
+    mbar_init(smem_u32(&fbar), 1);
     mbar_init(smem_u32(&bars->drain), 1);
     bars->abort_flag = 0;
     bars->issued = 0;
@@ -626,35 +671,52 @@ __global__ void __launch_bounds__(320, 1)
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
-  const uint32_t tmem = bars->tmem_base;  // D1 buffers at 0 and N; D2 chunk c at (2 + c) N
+  // D1 buffers at columns 0 and N; chunk c of D2 buffer u at (2 + 2 (u kseg + c)) N
+  const uint32_t tmem = bars->tmem_base;
   volatile int* abort_flag = &bars->abort_flag;
 
   if (warp == 0) {
     if (lane == 0) {
+      // the segment's rows of Omega1, once
+      mbar_expect_tx(smem_u32(&fbar), static_cast<uint32_t>(2 * kc) * kFBox);
+      for (int c = 0; c < kc; ++c)
+        for (int h = 0; h < 2; ++h)
+          tma_load_2d(smem_u32(fres + (2 * c + h) * kFBox), &mapF, smem_u32(&fbar),
+                      (c0 + c) * 128 + h * 64, 0);
       int it = 0;
-      for (int64_t t = t0; t < t1 && !*abort_flag; ++t) {
-        for (int c = 0; c < kch; ++c, ++it) {
+      for (int64_t j = j0; j < j1 && !*abort_flag; ++j) {
+        const int b = static_cast<int>(j / P.T);
+        const int t = static_cast<int>(j % P.T);
+        for (int c = 0; c < kc; ++c, ++it) {
           const int st = it % NS;
           const uint32_t ph = (it / NS) & 1;
           if (!mbar_wait(smem_u32(&bars->empty[st]), ph ^ 1, abort_flag)) {
             raise_timeout(bars, status);
             break;
           }
-          const uint32_t a = smem_u32(smem + st * kStage);
+          const uint32_t a = smem_u32(xst + st * kStage);
           const uint32_t fb = smem_u32(&bars->full[st]);
+          const int x0 = (c0 + c) * 128;
           mbar_expect_tx(fb, kStage);
-          tma_load_3d(a, &mapX, fb, c * 128, b * 128, static_cast<int>(t));
-          tma_load_3d(a + kXBox, &mapX, fb, c * 128 + 64, b * 128, static_cast<int>(t));
-          tma_load_2d(a + 2 * kXBox, &mapF, fb, c * 128, 0);
-          tma_load_2d(a + 2 * kXBox + kFBox, &mapF, fb, c * 128 + 64, 0);
+          tma_load_3d(a, &mapX, fb, x0, b * 128, t);
+          tma_load_3d(a + kXBox, &mapX, fb, x0 + 64, b * 128, t);
+          if (XLO) {
+            tma_load_3d(a + 2 * kXBox, &mapXlo, fb, x0, b * 128, t);
+            tma_load_3d(a + 3 * kXBox, &mapXlo, fb, x0 + 64, b * 128, t);
+          }
           bars->issued = it + 1;
         }
       }
     }
   } else if (warp == 1) {
     if (lane == 0) {
+      // Omega1 must have landed before the first MMA (and before exit)
+      const bool f_ok = mbar_wait(smem_u32(&fbar), 0, abort_flag);
+      if (!f_ok) raise_timeout(bars, status);
+      tc_fence_after();
+      const uint64_t fdesc = sdesc(smem_u32(fres), 16, 1024);
       int it = 0, tl = 0;
-      for (int64_t t = t0; t < t1 && !*abort_flag; ++t, ++tl) {
+      for (int64_t j = j0; f_ok && j < j1 && !*abort_flag; ++j, ++tl) {
         const int acc = tl & 1;
         const uint32_t aph = (tl >> 1) & 1;
         if (!mbar_wait(smem_u32(&bars->tempty[acc]), aph ^ 1, abort_flag) ||
@@ -662,11 +724,23 @@ __global__ void __launch_bounds__(320, 1)
           raise_timeout(bars, status);
           break;
         }
+        // the D2 buffer of this item's group; the group's first item starts
+        // its chains, once the buffer's previous group has been stored
+        const int grp = P.drain ? tl / P.drain : 0;
+        const int u = grp % P.nd2;
+        const bool first = P.drain ? (tl % P.drain == 0) : (tl == 0);
+        const bool last = P.drain && (tl % P.drain == P.drain - 1 || j == j1 - 1);
+        if (P.drain && first &&
+            !mbar_wait(smem_u32(&d2empty[u]), ((grp / P.nd2) & 1) ^ 1, abort_flag)) {
+          raise_timeout(bars, status);
+          break;
+        }
         tc_fence_after();
         const uint32_t d1 = tmem + acc * N;
-        const uint32_t b2b = smem_u32(b2 + acc * kB2Buf);
+        const uint32_t d2b = tmem + (2 + 2 * u * P.kseg) * N;
+        const uint64_t bdesc = sdesc(smem_u32(b2 + acc * kB2Buf), 16, 1024);
         bool ok = true;
-        for (int c = 0; c < kch; ++c, ++it) {
+        for (int c = 0; c < kc; ++c, ++it) {
           const int st = it % NS;
           const uint32_t ph = (it / NS) & 1;
           if (!mbar_wait(smem_u32(&bars->full[st]), ph, abort_flag)) {
@@ -675,26 +749,30 @@ __global__ void __launch_bounds__(320, 1)
             break;
           }
           tc_fence_after();
-          const uint32_t a = smem_u32(smem + st * kStage);
-          const uint32_t f = a + 2 * kXBox;
+          const uint32_t a = smem_u32(xst + st * kStage);
+          // descriptors differ only in their start address (field in 16-byte
+          // units, no carry: shared addresses are below 2^18)
+          const uint64_t ak = sdesc(a, 16, 1024);       // K-major view (MMA1)
+          const uint64_t am = sdesc(a, kXBox, 1024);    // MN-major view (MMA2)
           // MMA1: rows i2, K = i1 (two 64-wide boxes, 4 K-steps each)
 #pragma unroll
           for (int h = 0; h < 2; ++h)
 #pragma unroll
-            for (int k = 0; k < 4; ++k)
-              mma_bf16(d1, sdesc(a + h * kXBox + 32 * k, 16, 1024),
-                       sdesc(f + h * kFBox + 32 * k, 16, 1024), kIdesc1, (c | h | k) != 0);
+            for (int k = 0; k < 4; ++k) {
+              const uint64_t fo = ((2 * c + h) * kFBox + 32 * k) >> 4;
+              mma_bf16(d1, ak + ((h * kXBox + 32 * k) >> 4), fdesc + fo, kIdesc1, (c | h | k) != 0);
+              if (XLO)
+                mma_bf16(d1, ak + (((2 + h) * kXBox + 32 * k) >> 4), fdesc + fo, kIdesc1, 1u);
+            }
           // MMA2: M = i1 (the two boxes kXBox apart), K = i2 (128 rows, 8 K-steps),
-          // B = B2_t hi then lo (two 64-wide K atoms each)
-          const uint32_t d2 = tmem + (2 + c) * N;
+          // B = [B2hi | B2lo] (2N rows per 64-wide K atom); the lo plane of X
+          // takes the hi rows only
+          const uint32_t d2 = d2b + 2 * c * N;
 #pragma unroll
           for (int k = 0; k < 8; ++k) {
-            const uint32_t adesc_lo = a + 2048 * k;
-            const uint32_t batom = (k >> 2) * kB2Atom + 32 * (k & 3);
-            mma_bf16(d2, sdesc(adesc_lo, kXBox, 1024), sdesc(b2b + batom, 16, 1024), kIdesc2,
-                     (tl != 0 || k != 0) ? 1u : 0u);
-            mma_bf16(d2, sdesc(adesc_lo, kXBox, 1024), sdesc(b2b + 2 * kB2Atom + batom, 16, 1024),
-                     kIdesc2, 1u);
+            const uint64_t bo = ((k >> 2) * kB2Atom + 32 * (k & 3)) >> 4;
+            mma_bf16(d2, am + ((2048 * k) >> 4), bdesc + bo, kIdesc2, (!first || k != 0) ? 1u : 0u);
+            if (XLO) mma_bf16(d2, am + ((2 * kXBox + 2048 * k) >> 4), bdesc + bo, kIdesc2h, 1u);
           }
           mma_commit(smem_u32(&bars->empty[st]));
           bars->consumed = it + 1;
@@ -702,6 +780,7 @@ __global__ void __launch_bounds__(320, 1)
         if (!ok) break;
         mma_commit(smem_u32(&bars->tfull[acc]));
         mma_commit(smem_u32(&b2empty[acc]));
+        if (last) mma_commit(smem_u32(&d2full[u]));
       }
       mma_commit(smem_u32(&bars->drain));
       int dummy = 0;
@@ -709,15 +788,35 @@ __global__ void __launch_bounds__(320, 1)
     }
   } else if (warp >= 6) {
     // B2 producer warpgroup: B2_t[i2, k] = Omega2[i2, k] w[t, k] in the K-major
-    // 128-byte swizzled layout (rows k, 64 i2 per atom), as BF16 hi and lo.
+    // 128-byte swizzled layout (rows k, 64 i2 per atom): hi in row k, lo in
+    // row N + k (the same swizzle phase, N being a multiple of 8).
     const int tid = threadIdx.x - 192;  // 0..127, one i2 row each
-    const int64_t i2 = static_cast<int64_t>(b) * 128 + tid;
+    const int col = tid & 63;
     float om[N];
-#pragma unroll
-    for (int k = 0; k < N; ++k)
-      om[k] = (k < P.L && i2 < P.n2) ? __bfloat162float(P.om2[i2 + P.n2 * k]) : 0.f;
+    int cur_b = -1;
     int tl = 0;
-    for (int64_t t = t0; t < t1; ++t, ++tl) {
+    // w[t, :]: two loads per lane, shared within the warp by shuffles (no
+    // barrier across the producer warps), loaded one item ahead; the first
+    // warp also stages it in shared memory for the epilogue (published by
+    // the b2full arrival)
+    auto load_w = [&](int64_t jj, float& a0, float& a1) {
+      const int64_t tt = jj % P.T;
+      a0 = (jj < j1 && lane < P.L) ? __ldg(P.w + tt + P.T * lane) : 0.f;
+      a1 = (jj < j1 && lane + 32 < P.L) ? __ldg(P.w + tt + P.T * (lane + 32)) : 0.f;
+    };
+    float nw0, nw1;
+    load_w(j0, nw0, nw1);
+    for (int64_t j = j0; j < j1; ++j, ++tl) {
+      const int b = static_cast<int>(j / P.T);
+      if (b != cur_b) {
+        cur_b = b;
+        const int64_t i2 = static_cast<int64_t>(b) * 128 + tid;
+#pragma unroll
+        for (int k = 0; k < N; ++k)
+          om[k] = (k < P.L && i2 < P.n2) ? __bfloat162float(P.om2[i2 + P.n2 * k]) : 0.f;
+      }
+      const float wl0 = nw0, wl1 = nw1;
+      load_w(j + 1, nw0, nw1);
       const int buf = tl & 1;
       const uint32_t ph = (tl >> 1) & 1;
       if (!mbar_wait(smem_u32(&b2empty[buf]), ph ^ 1, abort_flag)) {
@@ -725,12 +824,6 @@ __global__ void __launch_bounds__(320, 1)
         break;
       }
       uint8_t* base = b2 + buf * kB2Buf + (tid >> 6) * kB2Atom;
-      const int col = tid & 63;
-      // w[t, :]: two loads per lane, shared within the warp by shuffles (no
-      // barrier across the producer warps); the first warp also stages it
-      // in shared memory for the epilogue (published by the b2full arrival)
-      const float wl0 = (lane < P.L) ? __ldg(P.w + t + P.T * lane) : 0.f;
-      const float wl1 = (lane + 32 < P.L) ? __ldg(P.w + t + P.T * (lane + 32)) : 0.f;
       if (tid < 32) {
         if (lane < N) wsm[buf][lane] = wl0;
         if (lane + 32 < N) wsm[buf][lane + 32] = wl1;
@@ -742,7 +835,7 @@ __global__ void __launch_bounds__(320, 1)
         const __nv_bfloat16 lo = __float2bfloat16_rn(v - __bfloat162float(hi));
         const uint32_t off = k * 128 + ((((col >> 3) ^ (k & 7)) << 4)) + (col & 7) * 2;
         *reinterpret_cast<__nv_bfloat16*>(base + off) = hi;
-        *reinterpret_cast<__nv_bfloat16*>(base + 2 * kB2Atom + off) = lo;
+        *reinterpret_cast<__nv_bfloat16*>(base + N * 128 + off) = lo;
       }
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       __syncwarp();
@@ -750,18 +843,65 @@ __global__ void __launch_bounds__(320, 1)
     }
   } else {
     const int q = warp & 3;
-    const int row = q * 32 + lane;  // i2 within the block
-    const int64_t i2 = static_cast<int64_t>(b) * 128 + row;
-    const bool valid = i2 < P.n2;
+    const int row = q * 32 + lane;  // i2 within the block; i1 within a chunk
     float y2[N];
     float o2[N];
+    int cur_b = -1;
+    int64_t i2 = 0;
+    bool valid = false;
+    auto flush_y2 = [&]() {
+      if (valid) {
 #pragma unroll
-    for (int k = 0; k < N; ++k) {
-      y2[k] = 0.f;
-      o2[k] = (valid && k < P.L) ? __bfloat162float(P.om2[i2 + P.n2 * k]) : 0.f;
-    }
+        for (int k = 0; k < N; ++k)
+          if (k < P.L) atomicAdd(P.Y2 + i2 + P.n2 * k, y2[k]);
+      }
+    };
+    // D2 buffer u -> the CTA's partials of Y1 for its segment (hi and lo
+    // halves summed), coalesced over i1; `init` stores, otherwise adds; a
+    // buffer that holds nothing (`have` false) contributes zeros
+    const int64_t segrows = static_cast<int64_t>(P.kseg) * 128;
+    float* yw = P.Yw + static_cast<size_t>(blockIdx.x) * N * segrows;
+    auto store_d2 = [&](int u, bool init, bool have) {
+      for (int c = 0; c < P.kseg; ++c) {
+        const uint32_t base =
+            tmem + (static_cast<uint32_t>(q * 32) << 16) + (2 + 2 * (u * P.kseg + c)) * N;
+#pragma unroll
+        for (int cc = 0; cc < N; cc += 16) {
+          float vh[16], vl[16];
+          if (have && c < kc) {
+            tmem_ld16(base + cc, vh);
+            tmem_ld16(base + N + cc, vl);
+          } else {
+#pragma unroll
+            for (int jj = 0; jj < 16; ++jj) vh[jj] = vl[jj] = 0.f;
+          }
+          float* dst = yw + static_cast<size_t>(cc) * segrows + c * 128 + row;
+          // the 16 old values are loaded before any store (one L2 round trip)
+          float prev[16];
+#pragma unroll
+          for (int jj = 0; jj < 16; ++jj)
+            prev[jj] = init ? 0.f : __ldcg(dst + static_cast<size_t>(jj) * segrows);
+#pragma unroll
+          for (int jj = 0; jj < 16; ++jj)
+            __stcg(dst + static_cast<size_t>(jj) * segrows, prev[jj] + (vh[jj] + vl[jj]));
+        }
+      }
+    };
     int tl = 0;
-    for (int64_t t = t0; t < t1; ++t, ++tl) {
+    for (int64_t j = j0; j < j1; ++j, ++tl) {
+      const int b = static_cast<int>(j / P.T);
+      const int64_t t = j % P.T;
+      if (b != cur_b) {
+        if (cur_b >= 0) flush_y2();
+        cur_b = b;
+        i2 = static_cast<int64_t>(b) * 128 + row;
+        valid = i2 < P.n2;
+#pragma unroll
+        for (int k = 0; k < N; ++k) {
+          y2[k] = 0.f;
+          o2[k] = (valid && k < P.L) ? __bfloat162float(P.om2[i2 + P.n2 * k]) : 0.f;
+        }
+      }
       const int acc = tl & 1;
       const uint32_t ph = (tl >> 1) & 1;
       if (!mbar_wait(smem_u32(&bars->tfull[acc]), ph, abort_flag)) {
@@ -775,19 +915,24 @@ __global__ void __launch_bounds__(320, 1)
       }
       tc_fence_after();
       const uint32_t base = tmem + (static_cast<uint32_t>(q * 32) << 16) + acc * N;
+      // this warp's slot of the C partials for item (b, t)
+      float* cw = P.Cw + ((static_cast<size_t>(seg) * P.nb + b) * 4 + q) * P.T * N +
+                  static_cast<size_t>(t) * N;
+      // all of D1's columns in flight at once, one wait
+      float v[N];
 #pragma unroll
-      for (int c0 = 0; c0 < N; c0 += 16) {
-        float v[16];
-        tmem_ld16(base + c0, v);
+      for (int cc = 0; cc < N; cc += 16) tmem_ld16_issue(base + cc, v + cc);
+      tmem_ld_wait();
+#pragma unroll
+      for (int cc = 0; cc < N; cc += 16) {
         float cp[16];
 #pragma unroll
-        for (int j = 0; j < 16; ++j) {
-          const int k = c0 + j;
-          y2[k] = fmaf(v[j], wsm[acc][k], y2[k]);
-          cp[j] = v[j] * o2[k];
+        for (int jj = 0; jj < 16; ++jj) {
+          const int k = cc + jj;
+          y2[k] = fmaf(v[k], wsm[acc][k], y2[k]);
+          cp[jj] = v[k] * o2[k];
         }
-        // each warp adds its 32-row partial of C[t, k] (no cross-warp barrier)
-        WarpReduceScatter<16, 16>::run(cp, lane, c0, P.C, t, P.T, P.L);
+        WarpReduceScatter<16, 16>::run(cp, lane, cc, [&](int k, float x) { cw[k] = x; });
       }
       tc_fence_before();
       __syncwarp();
@@ -795,44 +940,35 @@ __global__ void __launch_bounds__(320, 1)
         mbar_arrive(smem_u32(&bars->tempty[acc]));
         mbar_arrive(smem_u32(&b2empty[acc]));
       }
-    }
-    if (valid) {
-#pragma unroll
-      for (int k = 0; k < N; ++k)
-        if (k < P.L) atomicAdd(P.Y2 + i2 + P.n2 * k, y2[k]);
-    }
-    // D2 (all MMAs are complete once the last tfull has been observed): this
-    // CTA's partial of Y1, stored (coalesced over i1) into its own slot of the
-    // partials buffer, which a second kernel sums in a fixed order; without
-    // the buffer, atomically into Y1
-    if (P.Yw && t1 <= t0) {
-      for (int c = 0; c < kch; ++c)
-        for (int k = 0; k < N; ++k)
-          P.Yw[(static_cast<size_t>(blockIdx.x) * N + k) * P.n1p + c * 128 + row] = 0.f;
-    } else if (t1 > t0) {
-      tc_fence_after();
-      for (int c = 0; c < kch; ++c) {
-        const int64_t i1 = static_cast<int64_t>(c) * 128 + row;
-        const uint32_t base = tmem + (static_cast<uint32_t>(q * 32) << 16) + (2 + c) * N;
-#pragma unroll
-        for (int c0 = 0; c0 < N; c0 += 16) {
-          float v[16];
-          tmem_ld16(base + c0, v);
-          if (P.Yw) {
-            float* dst = P.Yw + (static_cast<size_t>(blockIdx.x) * N + c0) * P.n1p + i1;
-#pragma unroll
-            for (int j = 0; j < 16; ++j) dst[static_cast<size_t>(j) * P.n1p] = v[j];
-          } else if (i1 < P.n1) {
-#pragma unroll
-            for (int j = 0; j < 16; ++j)
-              if (c0 + j < P.L) atomicAdd(P.Y1 + i1 + P.n1 * (c0 + j), v[j]);
-          }
+      if (P.drain && (tl % P.drain == P.drain - 1 || j == j1 - 1)) {
+        const int grp = tl / P.drain;
+        const int u = grp % P.nd2;
+        if (!mbar_wait(smem_u32(&d2full[u]), (grp / P.nd2) & 1, abort_flag)) {
+          if (lane == 0) raise_timeout(bars, status);
+          break;
         }
+        tc_fence_after();
+        store_d2(u, grp == 0, true);
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(smem_u32(&d2empty[u]));
       }
+    }
+    if (cur_b >= 0) flush_y2();
+    // Without draining, D2 (complete once the last tfull has been observed)
+    // is stored once; a CTA without items stores zeros
+    const bool have = j1 > j0 && !*abort_flag;
+    if (!P.drain || !have) {
+      if (have) tc_fence_after();
+      store_d2(0, true, have);
     }
   }
   __syncthreads();
-  if (warp == 0 && lane == 0 && bars->abort_flag) drain_loads<NS>(bars);
+  if (warp == 0 && lane == 0 && bars->abort_flag) {
+    drain_loads<NS>(bars);
+    int dummy = 0;  // the resident Omega1 load too (bounded)
+    mbar_wait(smem_u32(&fbar), 0, reinterpret_cast<volatile int*>(&dummy));
+  }
   __syncthreads();
   if (warp == 1) {
     tc_fence_after();
@@ -1055,18 +1191,37 @@ __global__ void __launch_bounds__(kThreads, 1)
   }
 }
 
-// Y1[i + n1 k] = sum over the tree CTAs c (in order) of Yw[(c N + k) n1p + i]
-__global__ void tree_reduce_kernel(const float* __restrict__ Yw, int parts, int64_t n1, int64_t n1p,
-                                   int L, int N, float* __restrict__ Y1) {
+// Y1[i + n1 k] = sum over the cps CTAs of i's segment (in order) of their
+// partials Yw[cta][k][i - first row of the segment]
+__global__ void tree_reduce_kernel(const float* __restrict__ Yw, int cps, int64_t segrows,
+                                   int64_t n1, int L, int N, float* __restrict__ Y1) {
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n1 * L;
        e += (int64_t)gridDim.x * blockDim.x) {
     const int64_t i = e % n1;
     const int k = static_cast<int>(e / n1);
-    const float* src = Yw + static_cast<size_t>(k) * n1p + i;
-    const size_t step = static_cast<size_t>(N) * n1p;
+    const int64_t seg = i / segrows;
+    const size_t step = static_cast<size_t>(N) * segrows;
+    const float* src = Yw + seg * cps * step + static_cast<size_t>(k) * segrows + (i - seg * segrows);
     float acc = 0.f;
-    for (int c = 0; c < parts; ++c) acc += src[c * step];
+    for (int c = 0; c < cps; ++c) acc += src[c * step];
     Y1[e] = acc;
+  }
+}
+
+// C[t + T k] = sum over the `parts` partial slots p (in order) of
+// Cw[(p T + t) N + k]
+__global__ void tree_c_reduce_kernel(const float* __restrict__ Cw, int64_t parts, int64_t T,
+                                     int L, int N, float* __restrict__ C) {
+  // consecutive threads take consecutive k of one t: coalesced partial reads
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < T * L;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t t = e / L;
+    const int k = static_cast<int>(e % L);
+    const float* src = Cw + static_cast<size_t>(t) * N + k;
+    const size_t step = static_cast<size_t>(T) * N;
+    float acc = 0.f;
+    for (int64_t p = 0; p < parts; ++p) acc += src[p * step];
+    C[t + T * k] = acc;
   }
 }
 
@@ -1195,6 +1350,12 @@ void launch_mttkrp(const CUtensorMap& mx, const CUtensorMap* mxlo, const CUtenso
 
 bool tc_available() { return true; }
 
+size_t tc_tree_workspace_bytes(int64_t n1, int64_t n2, int64_t T, int L) {
+  const int64_t N = round_up(L, 16);
+  const int64_t nseg = (n1 + 127) / 128;  // at most one segment per chunk
+  return ws_bytes((size_t)nseg * ((n2 + 127) / 128) * 4 * T * N, 4) + (1 << 16);
+}
+
 size_t tc_workspace_bytes(int64_t n1, int64_t S, int L) {
   (void)S;
   const int64_t n1p = (n1 + 63) / 64 * 64;
@@ -1262,72 +1423,115 @@ void tc_gemm_tn_bf16(const __nv_bfloat16* X, int64_t n1, int64_t S, const __nv_b
 
 bool tc_tree_supported(int64_t n1, int L) {
   const int N = round_up(L, 16);
-  const int64_t kch = (n1 + 127) / 128;
-  return n1 % 8 == 0 && N <= 64 && (2 + kch) * N <= 512;
+  return n1 % 8 == 0 && N <= 64;
 }
+
+namespace {
+// dynamic shared memory of the tree kernel with NS stages and kseg resident
+// Omega1 chunks (1 KB alignment slack, the barriers)
+size_t tree_smem(int N, bool xlo, int kseg, int ns) {
+  return 1024 + (size_t)2 * kseg * N * 128 + (size_t)ns * (xlo ? 4 : 2) * 16384 +
+         (size_t)2 * 2 * (2 * N * 128) + sizeof(Bars) + 64;
+}
+constexpr size_t kTreeSmemMax = 232448 - 1024;  // 227 KB less the static shared arrays
+
+template <int N, int NS, bool XLO>
+void launch_tree(const CUtensorMap& mx, const CUtensorMap& mxlo, const CUtensorMap& mf,
+                 const TreeArgs& P, int grid, size_t smem) {
+  set_smem(tc_tree_kernel<N, NS, XLO>, smem);
+  tc_tree_kernel<N, NS, XLO><<<grid, 320, smem, stream()>>>(mx, mxlo, mf, P, current()->d_status);
+}
+
+template <int N, bool XLO>
+void launch_tree_ns(const CUtensorMap& mx, const CUtensorMap& mxlo, const CUtensorMap& mf,
+                    const TreeArgs& P, int grid, int ns) {
+  const size_t smem = tree_smem(N, XLO, P.kseg, ns);
+  if (ns >= 4) launch_tree<N, 4, XLO>(mx, mxlo, mf, P, grid, smem);
+  else if (ns == 3) launch_tree<N, 3, XLO>(mx, mxlo, mf, P, grid, smem);
+  else launch_tree<N, 2, XLO>(mx, mxlo, mf, P, grid, smem);
+}
+
+template <int N>
+void launch_tree_n(const CUtensorMap& mx, const CUtensorMap& mxlo, const CUtensorMap& mf,
+                   const TreeArgs& P, int grid, bool xlo, int ns) {
+  if (xlo) launch_tree_ns<N, true>(mx, mxlo, mf, P, grid, ns);
+  else launch_tree_ns<N, false>(mx, mxlo, mf, P, grid, ns);
+}
+}  // namespace
 
 void tc_tree_bf16(const __nv_bfloat16* X, int64_t n1, int64_t n2, int64_t T,
                   const __nv_bfloat16* Om1, const __nv_bfloat16* Om2, const float* w, int L,
-                  float* Y1, float* Y2, float* C) {
-  KRP_REQUIRE(tc_tree_supported(n1, L), "fused tree needs n_1 %% 8 == 0, l <= 64 and TMEM room");
+                  float* Y1, float* Y2, float* C, const __nv_bfloat16* Xlo) {
+  KRP_REQUIRE(tc_tree_supported(n1, L), "fused tree needs n_1 %% 8 == 0 and l <= 64");
   KRP_REQUIRE((reinterpret_cast<uintptr_t>(X) & 15) == 0, "X must be 16-byte aligned");
+  KRP_REQUIRE(!Xlo || (reinterpret_cast<uintptr_t>(Xlo) & 15) == 0,
+              "X lo plane must be 16-byte aligned");
   KRP_REQUIRE(T < (int64_t(1) << 31) && n2 < (int64_t(1) << 31), "tensor too large for TMA");
+  const bool xlo = Xlo != nullptr;
   const int N = round_up(L, 16);
   const int64_t n1p = round_up(n1, 128);
   Ctx* ctx = current();
+  TreeArgs P{};
+  P.kch = static_cast<int>(n1p / 128);
+  // the hi/lo form drains D2 every 16 items (chains of 128 MMA steps: Y1 to
+  // ~5e-6, against ~3.5e-5 for one chain per CTA at 1024^3) from one buffer;
+  // the BF16 form, whose input carries 2^-9 rounding, keeps one chain per CTA
+  P.drain = xlo ? 16 : 0;
+  P.nd2 = 1;
+  // the segment as long as TMEM allows, shortened while the ring would hold
+  // fewer than two stages
+  P.kseg = std::min(P.kch, tree_kseg_max(N, P.nd2));
+  auto stages = [&](int kseg) {
+    int ns = 4;
+    while (ns > 1 && tree_smem(N, xlo, kseg, ns) > kTreeSmemMax) --ns;
+    return ns;
+  };
+  while (P.kseg > 1 && stages(P.kseg) < 2) --P.kseg;
+  const int ns = stages(P.kseg);
+  KRP_REQUIRE(ns >= 2, "fused tree: shared memory too small (l = %d)", L);
+  const int nseg = (P.kch + P.kseg - 1) / P.kseg;
   __nv_bfloat16* Fc = ctx->ws.take<__nv_bfloat16>((size_t)n1p * N);
   pack_factor_kernel<<<(int)std::min<int64_t>((n1p * N + 255) / 256, 4096), 256, 0, stream()>>>(
       Om1, nullptr, n1, n1p, L, N, N, Fc);
   check_launch("pack_factor");
   KRP_CUDA_CHECK(cudaMemsetAsync(Y2, 0, sizeof(float) * n2 * L, stream()));
-  KRP_CUDA_CHECK(cudaMemsetAsync(C, 0, sizeof(float) * T * L, stream()));
   const uint64_t xd[3] = {(uint64_t)n1, (uint64_t)n2, (uint64_t)T};
   const uint64_t xs[2] = {(uint64_t)n1 * 2, (uint64_t)n1 * n2 * 2};
   const uint32_t xbox[3] = {64, 128, 1};
   const CUtensorMap mx = make_map(X, 3, xd, xs, xbox);
+  const CUtensorMap mxlo = xlo ? make_map(Xlo, 3, xd, xs, xbox) : mx;
   const uint64_t fd[2] = {(uint64_t)n1p, (uint64_t)N};
   const uint64_t fs[1] = {(uint64_t)n1p * 2};
   const uint32_t fbox[2] = {64, (uint32_t)N};
   const CUtensorMap mf = make_map(Fc, 2, fd, fs, fbox);
-  TreeArgs P{};
   P.w = w;
   P.om2 = Om2;
-  P.Y1 = Y1;
   P.Y2 = Y2;
-  P.C = C;
-  P.n1 = n1;
   P.n2 = n2;
   P.T = T;
   P.L = L;
-  P.nb = static_cast<int>((n2 + 127) / 128);
-  P.kchunks = static_cast<int>((n1 + 127) / 128);
-  int64_t chunks = std::max<int64_t>(1, ctx->num_sms / P.nb);
-  chunks = std::min<int64_t>(chunks, T);
-  P.t_per_cta = (T + chunks - 1) / chunks;
-  chunks = (T + P.t_per_cta - 1) / P.t_per_cta;
-  const int grid = static_cast<int>(P.nb * chunks);
-  // partials of Y1 per CTA (the workspace holds one set per SM)
-  P.n1p = n1p;
-  P.Yw = (grid <= ctx->num_sms) ? ctx->ws.take<float>((size_t)grid * N * n1p) : nullptr;
-  if (!P.Yw) KRP_CUDA_CHECK(cudaMemsetAsync(Y1, 0, sizeof(float) * n1 * L, stream()));
-  auto go = [&](auto kern, size_t stage) {
-    const size_t smem = 1024 + tree_stages(N) * stage + 2 * (4 * (size_t)N * 128) + sizeof(Bars) + 64;
-    set_smem(kern, smem);
-    kern<<<grid, 320, smem, stream()>>>(mx, mf, P, ctx->d_status);
-  };
+  const int64_t nb = (n2 + 127) / 128;
+  P.nb = static_cast<int>(nb);
+  P.items = nb * T;
+  P.Cw = ctx->ws.take<float>((size_t)nseg * nb * 4 * T * N);
+  P.cps = static_cast<int>(std::max<int64_t>(1, std::min<int64_t>(ctx->num_sms / nseg, P.items)));
+  const int grid = nseg * P.cps;
+  const int64_t segrows = static_cast<int64_t>(P.kseg) * 128;
+  P.Yw = ctx->ws.take<float>((size_t)grid * N * segrows);
   switch (N) {
-    case 16: go(tc_tree_kernel<16>, 2 * 16384 + 2 * 16 * 128); break;
-    case 32: go(tc_tree_kernel<32>, 2 * 16384 + 2 * 32 * 128); break;
-    case 48: go(tc_tree_kernel<48>, 2 * 16384 + 2 * 48 * 128); break;
-    case 64: go(tc_tree_kernel<64>, 2 * 16384 + 2 * 64 * 128); break;
+    case 16: launch_tree_n<16>(mx, mxlo, mf, P, grid, xlo, ns); break;
+    case 32: launch_tree_n<32>(mx, mxlo, mf, P, grid, xlo, ns); break;
+    case 48: launch_tree_n<48>(mx, mxlo, mf, P, grid, xlo, ns); break;
+    case 64: launch_tree_n<64>(mx, mxlo, mf, P, grid, xlo, ns); break;
     default: fail(KRP_EUNSUPPORTED, "fused tree width %d", N);
   }
   check_launch("tc_tree_bf16");
-  if (P.Yw) {
-    tree_reduce_kernel<<<(int)std::min<int64_t>((n1 * L + 255) / 256, 4096), 256, 0, stream()>>>(
-        P.Yw, grid, n1, n1p, L, N, Y1);
-    check_launch("tree_reduce");
-  }
+  tree_reduce_kernel<<<(int)std::min<int64_t>((n1 * L + 255) / 256, 4096), 256, 0, stream()>>>(
+      P.Yw, P.cps, segrows, n1, L, N, Y1);
+  check_launch("tree_reduce");
+  tree_c_reduce_kernel<<<(int)std::min<int64_t>((T * L + 255) / 256, 4096), 256, 0, stream()>>>(
+      P.Cw, (int64_t)nseg * nb * 4, T, L, N, C);
+  check_launch("tree_c_reduce");
 }
 
 size_t tc_residual_workspace_bytes(int64_t n1, int64_t S) {

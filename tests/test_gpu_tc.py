@@ -19,8 +19,11 @@ from synth import TuckerSpec, tucker_tensor
 
 pytestmark = pytest.mark.gpu
 
+# (1024, 64, 5) at l = 48 and (1024, 40, 6) at l = 64 cut i1 into two and
+# three segments of the one-pass tree (the last one short)
 CASES = [((64, 48, 40), 5), ((128, 72, 33), 16), ((200, 200, 7), 30), ((256, 64, 16, 3), 12),
-         ((1024, 64, 5), 48), ((136, 40, 30), 64), ((8, 9, 10), 3), ((520, 130, 9), 20)]
+         ((1024, 64, 5), 48), ((136, 40, 30), 64), ((8, 9, 10), 3), ((520, 130, 9), 20),
+         ((1024, 40, 6), 64)]
 
 
 @pytest.fixture(scope="module")
@@ -179,9 +182,11 @@ def test_split_bf16x2_matches_host_split(ctx):
 
 
 @pytest.mark.parametrize("dims,ell", [((64, 48, 40), 5), ((200, 200, 7), 30), ((256, 64, 16, 3), 12),
-                                      ((136, 40, 30), 64)])
+                                      ((136, 40, 30), 64), ((1024, 72, 5), 40), ((1024, 40, 6), 64)])
 def test_bf16x2_sketches(ctx, dims, ell):
-    """Sketch of hi + lo with BF16 factors: products exact, FP32 accumulation."""
+    """Sketch of hi + lo with BF16 factors: products exact, FP32 accumulation
+    (all modes: the one-pass tree with the lo plane; mode 1 alone: the
+    MTTKRP kernel)."""
     import torch
     import paper_2507_23207_gb300 as K
     rng = np.random.default_rng(sum(dims) + ell)

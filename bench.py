@@ -621,6 +621,69 @@ def cpu_baseline(spec, spec_args, target_s=10.0, k=None, threads=None):
             "phases_s": {p: round(v, 3) for p, v in r["phases"].items()}}
 
 
+def run_sharded(args, rank, world, local_rank):
+    """RHOSVD-KRP-MEMO of the one workload tensor split into slabs of its last
+    mode, one per rank (paper_2507_23207_gb300.sharded): every rank runs the
+    C-ABI steps on its slab and the ranks all-reduce the packed sketches, the
+    core and the residual sums (NCCL under torchrun; at N = 1 the reductions
+    are the identity).  Total work is fixed as N grows (strong scaling)."""
+    import torch
+    import paper_2507_23207_gb300 as K
+    from paper_2507_23207_gb300.sharded import CudaOps, exchange_bytes, rhosvd_sharded, slab_bounds
+    dev = torch.device(f"cuda:{local_rank}")
+    torch.cuda.set_device(dev)
+    spec = workload(args)
+    x32, _ = make_inputs(spec, dev, want_bf16=False)
+    start, stop = slab_bounds(spec.dims[-1], world, rank)
+    xs = x32[start:stop].contiguous()  # torch layout (n_d, ..., n_1): the slab of the last mode
+    del x32
+    torch.cuda.empty_cache()
+    ctx = K.Context(local_rank, torch.cuda.current_stream(dev).cuda_stream)
+    ops = CudaOps(ctx, dev)
+    red = None if world > 1 else (lambda t: None)
+
+    def step():
+        return rhosvd_sharded(ops, xs, spec.dims, start, stop, list(spec.ranks), spec.oversample,
+                              spec.omega_seed, allreduce=red)
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        core, qs, rel = step()
+    e1.record()
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    ms = e0.elapsed_time(e1) / args.steps
+    if world > 1:
+        t = torch.tensor([ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    ctx.close()
+    if rank != 0:
+        return
+    n = spec.numel
+    line = {"metric": METRIC, "value": round(3.0 * n * 4 / (ms * 1e-3) / 1e9, 2), "unit": "GB/s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(ms, 4), "higher_is_better": True, "scaling": "strong",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"{spec.name}: {'x'.join(map(str, spec.dims))} FP32, "
+                       f"RHOSVD-KRP-MEMO + truncation + residual, one slab of the last mode per rank",
+                       "parallelism": f"slab-sharded x{world}",
+                       "l2": "inputs larger than L2 (no flush)"},
+            "rel_error": rel,
+            "allreduce_bytes_per_rank_per_step": exchange_bytes(spec.dims, spec.ranks,
+                                                                spec.oversample),
+            "note": "per-rank C-ABI steps (factors, sketch, QR, multi-TTM, truncation, residual) "
+                    "with NCCL all-reduces between them"}
+    print(json.dumps(line))
+
+
 def workload(args):
     from dataclasses import replace
     from synth import config_spec
@@ -651,6 +714,9 @@ def main():
                     help="tensors in the batched workload with --batch-only")
     ap.add_argument("--hankel-only", action="store_true",
                     help="run only the 1024 x 1024 block-Hankel measurement (for profiling)")
+    ap.add_argument("--sharded", action="store_true",
+                    help="split the tensor into slabs of its last mode, one per rank, with "
+                         "all-reduces between the steps (strong scaling)")
     ap.add_argument("--cpu-sample", type=int, default=None,
                     help="(internal) time one oracle sample of slab depth K and print it")
     args = ap.parse_args()
@@ -716,6 +782,9 @@ def main():
     if world > 1:
         import torch
         torch.distributed.init_process_group("nccl")
+    if args.sharded:
+        run_sharded(args, rank, world, local_rank)
+        return
     spec, results, kr, sketch, e2e, peaks, peak_src, (sk, co, rs, qr), extra = run_ours(
         args, rank, world, local_rank)
     if rank != 0:

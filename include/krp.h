@@ -101,6 +101,19 @@ krp_status krp_destroy(krp_ctx ctx);
 /* Switch the stream later work is enqueued on. */
 krp_status krp_set_stream(krp_ctx ctx, void* cuda_stream);
 
+/* Limit, in nanoseconds, of every bounded device-side wait of the context's
+ * tensor-core kernels (their mbarrier waits on TMA data, MMA completion and
+ * the other warp roles); 0 restores the default of 1 s.  A wait that runs
+ * out makes its kernel stop: it records KRP_ETIMEOUT in the context's status
+ * word (the first error recorded is kept), lets the copies and MMAs it has
+ * issued complete (those waits keep the 1 s default), frees its tensor
+ * memory and returns; the pipeline entry points then return KRP_ETIMEOUT and
+ * clear the word.  Diagnostics: a limit shorter than the kernels' own
+ * progress (e.g. 1 ns) exercises that path; the paper has no counterpart.
+ * Synchronises the context's stream.  Errors: KRP_EINVAL (null ctx),
+ * KRP_ECUDA. */
+krp_status krp_set_wait_limit(krp_ctx ctx, uint64_t ns);
+
 /* Message of the last failed call on `ctx` ("" if none).  Owned by ctx. */
 const char* krp_last_error(krp_ctx ctx);
 

@@ -197,6 +197,16 @@ krp_status krp_set_stream(krp_ctx ctx, void* cuda_stream) {
   return guarded(ctx, [&] { ctx->c.stream = static_cast<cudaStream_t>(cuda_stream); });
 }
 
+krp_status krp_set_wait_limit(krp_ctx ctx, uint64_t ns) {
+  return guarded(ctx, [&] {
+    // the limit sits beside the status word (bytes 8..15 of that block);
+    // ordered with the context's later kernels by its stream
+    KRP_CUDA_CHECK(cudaMemcpyAsync(ctx->c.d_status + 2, &ns, sizeof(ns), cudaMemcpyHostToDevice,
+                                   ctx->c.stream));
+    KRP_CUDA_CHECK(cudaStreamSynchronize(ctx->c.stream));
+  });
+}
+
 const char* krp_last_error(krp_ctx ctx) { return ctx ? ctx->c.last_error.c_str() : "null context"; }
 
 const char* krp_status_string(krp_status s) {

@@ -44,7 +44,7 @@ __global__ void __launch_bounds__(kQrThreads) qr_kernel(const QrJob* __restrict_
   }
   __syncthreads();
   if (bad) {
-    if (tid == 0) atomicExch(status, (int)KRP_ENUMERIC);
+    if (tid == 0) atomicCAS(status, 0, (int)KRP_ENUMERIC);
     return;
   }
   for (int j = 0; j < l; ++j) {
@@ -514,7 +514,7 @@ __global__ void __launch_bounds__(kEigThreads) eig_kernel(const EigJob* __restri
     V32[r][c] = (r == c) ? 1.f : 0.f;
   }
   if (!__syncthreads_and(finite_in)) {
-    if (tid == 0) atomicExch(status, (int)KRP_ENUMERIC);
+    if (tid == 0) atomicCAS(status, 0, (int)KRP_ENUMERIC);
     return;
   }
   jacobi32<kEP, kEigThreads>(S32, S32b, V32, n, red);
@@ -573,7 +573,7 @@ __global__ void __launch_bounds__(kEigThreads) eig_kernel(const EigJob* __restri
     }
     bool ok = true;
     for (int i = 0; i < l; ++i) ok = ok && isfinite(lam[i]);
-    if (!ok) atomicExch(status, (int)KRP_ENUMERIC);
+    if (!ok) atomicCAS(status, 0, (int)KRP_ENUMERIC);
   }
   __syncthreads();
   for (int e = tid; e < l * job.r; e += blockDim.x) {
@@ -628,7 +628,7 @@ __global__ void __launch_bounds__(kJacobiThreads)
   double* out = scratch + (size_t)blockIdx.x * kEigScratch;
   if (!__syncthreads_and(finite_in)) {
     if (tid == 0) {
-      atomicExch(status, (int)KRP_ENUMERIC);
+      atomicCAS(status, 0, (int)KRP_ENUMERIC);
       out[kEigMaxL * kEigMaxL] = 0.0;  // marks the problem as failed for the refinement
     }
     return;
@@ -765,7 +765,7 @@ __global__ void __cluster_dims__(kEigCluster, 1, 1) __launch_bounds__(kEigThread
     }
     bool ok = true;
     for (int i = 0; i < l; ++i) ok = ok && isfinite(lam[i]);
-    if (!ok) atomicExch(status, (int)KRP_ENUMERIC);
+    if (!ok) atomicCAS(status, 0, (int)KRP_ENUMERIC);
   }
   __syncthreads();
   for (int e = tid; e < l * job.r; e += blockDim.x) {
@@ -815,7 +815,7 @@ __global__ void sumsq_kernel(const double* __restrict__ x, int64_t n, double* ou
 __global__ void finite_kernel(const double* __restrict__ x, int64_t n, int* status) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x)
-    if (!isfinite(x[i])) atomicExch(status, (int)KRP_ENUMERIC);
+    if (!isfinite(x[i])) atomicCAS(status, 0, (int)KRP_ENUMERIC);
 }
 
 // ---------------------------------------------------------------------------
@@ -890,7 +890,7 @@ __global__ void __launch_bounds__(256) cqr_gram_kernel(const JOBS jobs, int* sta
   }
   __syncthreads();
   if (bad) {
-    if (threadIdx.x == 0) atomicExch(status, (int)KRP_ENUMERIC);
+    if (threadIdx.x == 0) atomicCAS(status, 0, (int)KRP_ENUMERIC);
     return;
   }
   // upper triangle (a <= b) of the partial Gram

@@ -63,14 +63,23 @@ __device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
   return ok != 0;
 }
 // Bounded wait for the phase with the given parity; false on timeout/abort.
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort_flag) {
+// lim: the wait's limit in ns (the context's setting for the pipeline's
+// waits; the drains after an abort keep the full kWaitNs).
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort_flag,
+                                          uint64_t lim = kWaitNs) {
   if (mbar_try(bar, parity)) return true;
   const uint64_t t0 = gtime();
   for (;;) {
     if (mbar_try(bar, parity)) return true;
     if (*abort_flag) return false;
-    if (gtime() - t0 > kWaitNs) return false;
+    if (gtime() - t0 > lim) return false;
   }
+}
+// The context's limit of the pipeline's waits: a uint64 in ns beside the
+// status word (0: kWaitNs).
+__device__ __forceinline__ uint64_t wait_limit(const int* status) {
+  const uint64_t v = *reinterpret_cast<const volatile uint64_t*>(status + 2);
+  return v ? v : kWaitNs;
 }
 __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, uint32_t bar,
                                             int c0, int c1) {
@@ -182,7 +191,7 @@ struct Bars {
 
 __device__ __forceinline__ void raise_timeout(Bars* b, int* status) {
   b->abort_flag = 1;
-  atomicExch(status, static_cast<int>(KRP_ETIMEOUT));
+  atomicCAS(status, 0, static_cast<int>(KRP_ETIMEOUT));  // the first error is kept
 }
 
 // Producer-side drain after an abort: wait (bounded) for every TMA load that
@@ -245,6 +254,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   tc_fence_after();
   const uint32_t tmem = bars->tmem_base;
   volatile int* abort_flag = &bars->abort_flag;
+  const uint64_t lim = wait_limit(status);
   const uint32_t idesc_lo = idesc_bf16(kBM, Lp, false, false);
 
   if (warp == 0) {
@@ -254,7 +264,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         for (int kc = 0; kc < kchunks; ++kc, ++it) {
           const int st = it % NS;
           const uint32_t ph = (it / NS) & 1;
-          if (!mbar_wait(smem_u32(&bars->empty[st]), ph ^ 1, abort_flag)) {
+          if (!mbar_wait(smem_u32(&bars->empty[st]), ph ^ 1, abort_flag, lim)) {
             raise_timeout(bars, status);
             break;
           }
@@ -274,7 +284,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       for (int64_t tile = blockIdx.x; tile < tiles && !*abort_flag; tile += gridDim.x, ++tl) {
         const int acc = tl & 1;
         const uint32_t aph = (tl >> 1) & 1;
-        if (!mbar_wait(smem_u32(&bars->tempty[acc]), aph ^ 1, abort_flag)) {
+        if (!mbar_wait(smem_u32(&bars->tempty[acc]), aph ^ 1, abort_flag, lim)) {
           raise_timeout(bars, status);
           break;
         }
@@ -284,7 +294,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         for (int kc = 0; kc < kchunks; ++kc, ++it) {
           const int st = it % NS;
           const uint32_t ph = (it / NS) & 1;
-          if (!mbar_wait(smem_u32(&bars->full[st]), ph, abort_flag)) {
+          if (!mbar_wait(smem_u32(&bars->full[st]), ph, abort_flag, lim)) {
             raise_timeout(bars, status);
             ok = false;
             break;
@@ -317,7 +327,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     for (int64_t tile = blockIdx.x; tile < tiles; tile += gridDim.x, ++tl) {
       const int acc = tl & 1;
       const uint32_t ph = (tl >> 1) & 1;
-      if (!mbar_wait(smem_u32(&bars->tfull[acc]), ph, abort_flag)) {
+      if (!mbar_wait(smem_u32(&bars->tfull[acc]), ph, abort_flag, lim)) {
         if (lane == 0) raise_timeout(bars, status);
         break;
       }
@@ -413,6 +423,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   tc_fence_after();
   const uint32_t tmem = bars->tmem_base;
   volatile int* abort_flag = &bars->abort_flag;
+  const uint64_t lim = wait_limit(status);
 
   if (warp == 0) {
     if (lane == 0) {
@@ -421,7 +432,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         for (int kc = 0; kc < kchunks; ++kc, ++it) {
           const int st = it % NS;
           const uint32_t ph = (it / NS) & 1;
-          if (!mbar_wait(smem_u32(&bars->empty[st]), ph ^ 1, abort_flag)) {
+          if (!mbar_wait(smem_u32(&bars->empty[st]), ph ^ 1, abort_flag, lim)) {
             raise_timeout(bars, status);
             break;
           }
@@ -445,7 +456,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       for (int64_t t = t0; t < t1 && !*abort_flag; ++t, ++tl) {
         const int acc = tl & 1;
         const uint32_t aph = (tl >> 1) & 1;
-        if (!mbar_wait(smem_u32(&bars->tempty[acc]), aph ^ 1, abort_flag)) {
+        if (!mbar_wait(smem_u32(&bars->tempty[acc]), aph ^ 1, abort_flag, lim)) {
           raise_timeout(bars, status);
           break;
         }
@@ -455,7 +466,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         for (int kc = 0; kc < kchunks; ++kc, ++it) {
           const int st = it % NS;
           const uint32_t ph = (it / NS) & 1;
-          if (!mbar_wait(smem_u32(&bars->full[st]), ph, abort_flag)) {
+          if (!mbar_wait(smem_u32(&bars->full[st]), ph, abort_flag, lim)) {
             raise_timeout(bars, status);
             ok = false;
             break;
@@ -494,7 +505,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     for (int64_t t = t0; t < t1; ++t, ++tl) {
       const int acc = tl & 1;
       const uint32_t ph = (tl >> 1) & 1;
-      if (!mbar_wait(smem_u32(&bars->tfull[acc]), ph, abort_flag)) {
+      if (!mbar_wait(smem_u32(&bars->tfull[acc]), ph, abort_flag, lim)) {
         if (lane == 0) raise_timeout(bars, status);
         break;
       }
@@ -674,6 +685,7 @@ __global__ void __launch_bounds__(320, 1)
   // D1 buffers at columns 0 and N; chunk c of D2 buffer u at (2 + 2 (u kseg + c)) N
   const uint32_t tmem = bars->tmem_base;
   volatile int* abort_flag = &bars->abort_flag;
+  const uint64_t lim = wait_limit(status);
 
   if (warp == 0) {
     if (lane == 0) {
@@ -690,7 +702,7 @@ __global__ void __launch_bounds__(320, 1)
         for (int c = 0; c < kc; ++c, ++it) {
           const int st = it % NS;
           const uint32_t ph = (it / NS) & 1;
-          if (!mbar_wait(smem_u32(&bars->empty[st]), ph ^ 1, abort_flag)) {
+          if (!mbar_wait(smem_u32(&bars->empty[st]), ph ^ 1, abort_flag, lim)) {
             raise_timeout(bars, status);
             break;
           }
@@ -711,7 +723,7 @@ __global__ void __launch_bounds__(320, 1)
   } else if (warp == 1) {
     if (lane == 0) {
       // Omega1 must have landed before the first MMA (and before exit)
-      const bool f_ok = mbar_wait(smem_u32(&fbar), 0, abort_flag);
+      const bool f_ok = mbar_wait(smem_u32(&fbar), 0, abort_flag, lim);
       if (!f_ok) raise_timeout(bars, status);
       tc_fence_after();
       const uint64_t fdesc = sdesc(smem_u32(fres), 16, 1024);
@@ -719,8 +731,8 @@ __global__ void __launch_bounds__(320, 1)
       for (int64_t j = j0; f_ok && j < j1 && !*abort_flag; ++j, ++tl) {
         const int acc = tl & 1;
         const uint32_t aph = (tl >> 1) & 1;
-        if (!mbar_wait(smem_u32(&bars->tempty[acc]), aph ^ 1, abort_flag) ||
-            !mbar_wait(smem_u32(&b2full[acc]), aph, abort_flag)) {
+        if (!mbar_wait(smem_u32(&bars->tempty[acc]), aph ^ 1, abort_flag, lim) ||
+            !mbar_wait(smem_u32(&b2full[acc]), aph, abort_flag, lim)) {
           raise_timeout(bars, status);
           break;
         }
@@ -731,7 +743,7 @@ __global__ void __launch_bounds__(320, 1)
         const bool first = P.drain ? (tl % P.drain == 0) : (tl == 0);
         const bool last = P.drain && (tl % P.drain == P.drain - 1 || j == j1 - 1);
         if (P.drain && first &&
-            !mbar_wait(smem_u32(&d2empty[u]), ((grp / P.nd2) & 1) ^ 1, abort_flag)) {
+            !mbar_wait(smem_u32(&d2empty[u]), ((grp / P.nd2) & 1) ^ 1, abort_flag, lim)) {
           raise_timeout(bars, status);
           break;
         }
@@ -743,7 +755,7 @@ __global__ void __launch_bounds__(320, 1)
         for (int c = 0; c < kc; ++c, ++it) {
           const int st = it % NS;
           const uint32_t ph = (it / NS) & 1;
-          if (!mbar_wait(smem_u32(&bars->full[st]), ph, abort_flag)) {
+          if (!mbar_wait(smem_u32(&bars->full[st]), ph, abort_flag, lim)) {
             raise_timeout(bars, status);
             ok = false;
             break;
@@ -819,7 +831,7 @@ __global__ void __launch_bounds__(320, 1)
       load_w(j + 1, nw0, nw1);
       const int buf = tl & 1;
       const uint32_t ph = (tl >> 1) & 1;
-      if (!mbar_wait(smem_u32(&b2empty[buf]), ph ^ 1, abort_flag)) {
+      if (!mbar_wait(smem_u32(&b2empty[buf]), ph ^ 1, abort_flag, lim)) {
         if (lane == 0) raise_timeout(bars, status);
         break;
       }
@@ -904,12 +916,12 @@ __global__ void __launch_bounds__(320, 1)
       }
       const int acc = tl & 1;
       const uint32_t ph = (tl >> 1) & 1;
-      if (!mbar_wait(smem_u32(&bars->tfull[acc]), ph, abort_flag)) {
+      if (!mbar_wait(smem_u32(&bars->tfull[acc]), ph, abort_flag, lim)) {
         if (lane == 0) raise_timeout(bars, status);
         break;
       }
       // w[t, :] was staged with B2_t (that phase is complete once tfull is)
-      if (!mbar_wait(smem_u32(&b2full[acc]), ph, abort_flag)) {
+      if (!mbar_wait(smem_u32(&b2full[acc]), ph, abort_flag, lim)) {
         if (lane == 0) raise_timeout(bars, status);
         break;
       }
@@ -943,7 +955,7 @@ __global__ void __launch_bounds__(320, 1)
       if (P.drain && (tl % P.drain == P.drain - 1 || j == j1 - 1)) {
         const int grp = tl / P.drain;
         const int u = grp % P.nd2;
-        if (!mbar_wait(smem_u32(&d2full[u]), (grp / P.nd2) & 1, abort_flag)) {
+        if (!mbar_wait(smem_u32(&d2full[u]), (grp / P.nd2) & 1, abort_flag, lim)) {
           if (lane == 0) raise_timeout(bars, status);
           break;
         }
@@ -1039,6 +1051,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   tc_fence_after();
   const uint32_t tmem = bars->tmem_base;
   volatile int* abort_flag = &bars->abort_flag;
+  const uint64_t lim = wait_limit(status);
 
   if (warp == 0) {
     if (lane == 0) {
@@ -1050,7 +1063,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       for (int64_t sb = sb0; sb < sblocks && !*abort_flag; sb += cpm, ++it) {
         const int st = it % NS;
         const uint32_t ph = (it / NS) & 1;
-        if (!mbar_wait(smem_u32(&bars->empty[st]), ph ^ 1, abort_flag)) {
+        if (!mbar_wait(smem_u32(&bars->empty[st]), ph ^ 1, abort_flag, lim)) {
           raise_timeout(bars, status);
           break;
         }
@@ -1074,7 +1087,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
   } else if (warp == 1) {
     if (lane == 0) {
-      bool ok = mbar_wait(smem_u32(&qbar), 0, abort_flag);
+      bool ok = mbar_wait(smem_u32(&qbar), 0, abort_flag, lim);
       if (!ok) raise_timeout(bars, status);
       int it = 0;
       for (int64_t sb = sb0; ok && sb < sblocks && !*abort_flag; sb += cpm, ++it) {
@@ -1082,8 +1095,8 @@ __global__ void __launch_bounds__(kThreads, 1)
         const uint32_t ph = (it / NS) & 1;
         const int accb = it & 1;
         const uint32_t aph = (it >> 1) & 1;
-        if (!mbar_wait(smem_u32(&bars->tempty[accb]), aph ^ 1, abort_flag) ||
-            !mbar_wait(smem_u32(&bars->full[st]), ph, abort_flag)) {
+        if (!mbar_wait(smem_u32(&bars->tempty[accb]), aph ^ 1, abort_flag, lim) ||
+            !mbar_wait(smem_u32(&bars->full[st]), ph, abort_flag, lim)) {
           raise_timeout(bars, status);
           break;
         }
@@ -1115,7 +1128,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       const int st = it % NS;
       const int accb = it & 1;
       const uint32_t aph = (it >> 1) & 1;
-      if (!mbar_wait(smem_u32(&bars->tfull[accb]), aph, abort_flag)) {
+      if (!mbar_wait(smem_u32(&bars->tfull[accb]), aph, abort_flag, lim)) {
         if (lane == 0) raise_timeout(bars, status);
         break;
       }

@@ -33,7 +33,7 @@ EXPORTED = [
     "krp_tucker_rhosvd", "krp_tucker_sthosvd", "krp_block_hankel_lowrank",
     "krp_block_hankel_sketch", "krp_tucker_rhosvd_batched", "krp_tucker_batch_plan_info",
     "krp_block_hankel_batched", "krp_split_bf16x2", "krp_trace_begin", "krp_trace_end",
-    "krp_core_truncate", "krp_residual",
+    "krp_core_truncate", "krp_residual", "krp_set_wait_limit",
 ]
 
 
@@ -101,6 +101,7 @@ def load_library(path: Optional[str] = None):
         "krp_create": (C.c_int, [C.POINTER(vp), C.c_int, vp]),
         "krp_destroy": (C.c_int, [vp]),
         "krp_set_stream": (C.c_int, [vp, vp]),
+        "krp_set_wait_limit": (C.c_int, [vp, C.c_uint64]),
         "krp_last_error": (C.c_char_p, [vp]),
         "krp_status_string": (C.c_char_p, [C.c_int]),
         "krp_abi_version": (C.c_int, []),
@@ -238,6 +239,10 @@ class Context:
 
     def set_stream(self, stream: int):
         self.check(self.lib.krp_set_stream(self.handle, C.c_void_p(stream)))
+
+    def set_wait_limit(self, ns: int):
+        """krp_set_wait_limit: limit of the tensor-core kernels' bounded waits (0 = 1 s)."""
+        self.check(self.lib.krp_set_wait_limit(self.handle, C.c_uint64(ns)))
 
     def launch_count(self) -> int:
         return int(self.lib.krp_launch_count(self.handle))

@@ -9,8 +9,9 @@ small sums (an all-reduce):
 2. sketches of the slab (Alg. 7, memoized, one pass over the slab): for
    n < d the slab's Y_n is a partial sum of the full Y_n (the slabs partition
    the rows of the Khatri-Rao product); for n = d it is the block of rows
-   [start, stop) of Y_d.  One all-reduce of sum_n n_n l values (Y_d padded
-   with zeros outside the slab's rows);
+   [start, stop) of Y_d.  One all-reduce of sum_n n_n l values, all d
+   sketches packed into one buffer (Y_d padded with zeros outside the slab's
+   rows);
 3. the FP64 QR of every Y_n runs on every rank (replicated, identical);
 4. core G = X x {Q_n^T}: with Q_d's rows [start, stop) the slab gives a
    partial sum of G; one all-reduce of prod_n l_n values;
@@ -101,6 +102,15 @@ def _dist_allreduce(t: torch.Tensor) -> None:
     dist.all_reduce(t)
 
 
+def exchange_bytes(dims: Sequence[int], ranks: Sequence[int], oversample: int,
+                   residual: bool = True) -> int:
+    """Bytes each rank contributes to the all-reduces of one sharded call:
+    the packed sketches (sum_n n_n l, FP32), the core (prod l_n, FP32) and the
+    two residual sums (FP64)."""
+    ells = [int(r) + oversample for r in ranks]
+    return 4 * sum(int(n) * max(ells) for n in dims) + 4 * math.prod(ells) + (16 if residual else 0)
+
+
 def rhosvd_sharded(ops, x_local, dims: Sequence[int], start: int, stop: int,
                    ranks: Sequence[int], oversample: int, seed: int, *,
                    truncate: bool = True, residual: bool = True,
@@ -126,8 +136,12 @@ def rhosvd_sharded(ops, x_local, dims: Sequence[int], start: int, stop: int,
     yd = torch.zeros(dims[-1] * ellmax, dtype=ys[-1].dtype, device=ys[-1].device)
     place_rows(yd, ys[-1], dims[-1], ellmax, start, stop)
     ys[-1] = yd
-    for y in ys:  # partial sums (n < d) and disjoint row blocks (n = d)
-        reduce(y)
+    # one exchange for all d sketches: partial sums (n < d) and disjoint row
+    # blocks (n = d) packed into one buffer
+    sizes = [y.numel() for y in ys]
+    packed = torch.cat(ys)
+    reduce(packed)
+    ys = list(torch.split(packed, sizes))
     qs = ops.qr([y[: n * l] for y, n, l in zip(ys, dims, ells)], dims, ells)
     q_local = list(qs[:-1]) + [rows_of(qs[-1], dims[-1], ells[-1], start, stop)]
     core = ops.multi_ttm(x_local, local, q_local, ells)

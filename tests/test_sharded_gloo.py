@@ -161,3 +161,22 @@ def test_row_slicing_helpers():
     place_rows(full, blk, n, ell, 2, 5)
     fa = full.numpy().reshape((n, ell), order="F")
     assert np.array_equal(fa[2:5], a[2:5]) and not fa[:2].any() and not fa[5:].any()
+
+
+def test_one_exchange_per_phase():
+    """The d sketches travel in one packed all-reduce: a call makes exactly
+    three exchanges (sketches, core, residual sums) carrying
+    exchange_bytes() bytes, whatever d is."""
+    from paper_2507_23207_gb300.sharded import exchange_bytes
+    for dims, ranks in (((9, 8, 7), (2, 2, 2)), ((6, 5, 4, 5), (2, 2, 2, 2))):
+        rng = np.random.default_rng(5)
+        x = rng.standard_normal(dims)
+        calls = []
+
+        def count(t):
+            calls.append(t.numel() * t.element_size())
+        core, qs, rel = rhosvd_sharded(OracleOps(), _flat(x), dims, 0, dims[-1], ranks, 2, 0,
+                                       allreduce=count, factor_dtype=torch.float64)
+        assert len(calls) == 3, calls
+        # FP64 buffers here; the CUDA path exchanges FP32 sketches and core
+        assert sum(calls) == 2 * (exchange_bytes(dims, ranks, 2) - 16) + 16

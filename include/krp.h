@@ -15,9 +15,15 @@
  *     sketches (Alg. 6, Eq. (4.1)).
  *
  * Conventions used by every entry point
- *   Layout.  A d-way tensor X of dims (n_1..n_d) is dense and mode-1 fastest:
- *     element (i_1..i_d), 0-based, sits at sum_j i_j * prod_{m<j} n_m.  (A
- *     C-contiguous torch tensor of shape (n_d, ..., n_1) has this layout.)
+ *   Layout.  A d-way tensor X of dims (n_1..n_d) is mode-1 fastest: element
+ *     (i_1..i_d), 0-based, sits at sum_j i_j * prod_{m<j} ld_m, where ld
+ *     (the per-mode leading sizes, ld_m >= n_m) is the argument `ld` of the
+ *     entry points that take X; ld = NULL means ld_m = n_m (dense: a
+ *     C-contiguous torch tensor of shape (n_d, ..., n_1)).  A padded X (some
+ *     ld_m > n_m) must be device memory; it is first packed into a dense
+ *     copy in the workspace (one extra read and write of X).  For KRP_BF16X2
+ *     both planes have the same padding and the lo plane starts prod_m ld_m
+ *     elements after the hi plane.
  *     Matrices (factors Omega_j, sketches Y_n, bases Q_n) are column-major with
  *     leading dimension equal to their row count.
  *   Memory.  Unless stated otherwise, data pointers are device pointers of the
@@ -46,7 +52,7 @@
 extern "C" {
 #endif
 
-#define KRP_ABI_VERSION 1
+#define KRP_ABI_VERSION 2
 #define KRP_MAXD 8
 
 typedef enum krp_status {
@@ -162,7 +168,7 @@ krp_status krp_philox_words(krp_ctx ctx, uint64_t seed, uint32_t c1,
  * the contraction runs over X once (two-stage: one factor by GEMM, the rest
  * as Hadamard-weighted reductions).  Errors: KRP_EINVAL, KRP_ENOMEM, KRP_ECUDA. */
 krp_status krp_sketch_mode(krp_ctx ctx, const void* X, krp_dtype xt, int d,
-                           const int64_t* dims, int n,
+                           const int64_t* dims, const int64_t* ld, int n,
                            const void* const* omega, krp_dtype omt, int ell,
                            float* Y);
 
@@ -171,11 +177,19 @@ krp_status krp_sketch_mode(krp_ctx ctx, const void* X, krp_dtype xt, int d,
 /* Y[n] (dims[n] x ell) for n = 0..d-1 from the shared factors omega[0..d-1],
  * by a dimension tree that contracts the first mode once and reuses the
  * partial result for every mode but the first (cost 4 N ell flops, Sec. 5.1).
- * Arguments as in krp_sketch_mode. */
+ * Arguments as in krp_sketch_mode.  tree_split (tensor-core forms, one pass
+ * over X): the tree's second dimension is the modes 2..tree_split+1 merged
+ * (1 <= tree_split <= d-1), contracted in the same pass as mode 1, and its
+ * sketch is split into those modes' sketches afterwards; -1 lets the library
+ * pick it: the first call for a given (dims, ell, dtype) times every split
+ * whose merged dimension has at most 2^20 rows (the call then synchronises
+ * the stream) and the context keeps the fastest for later calls.  The FP32
+ * form ignores tree_split.  Errors: as krp_sketch_mode, and KRP_EINVAL for a
+ * tree_split out of range. */
 krp_status krp_sketch_all_modes(krp_ctx ctx, const void* X, krp_dtype xt,
-                                int d, const int64_t* dims,
+                                int d, const int64_t* dims, const int64_t* ld,
                                 const void* const* omega, krp_dtype omt,
-                                int ell, float* const* Y);
+                                int ell, float* const* Y, int tree_split);
 
 /* ---- a4: FP64 thin QR (Alg. 1 step 3) ------------------------------------ */
 
@@ -243,8 +257,8 @@ krp_status krp_split_bf16x2(krp_ctx ctx, const float* X, int64_t n, void* out);
  * BF16 hi/lo pairs.  All pointers are device pointers.  Errors: KRP_EINVAL,
  * KRP_ENOMEM, KRP_ECUDA. */
 krp_status krp_multi_ttm(krp_ctx ctx, const void* X, krp_dtype xt, int d,
-                         const int64_t* dims, const double* const* Q,
-                         const int* cols, float* G);
+                         const int64_t* dims, const int64_t* ld,
+                         const double* const* Q, const int* cols, float* G);
 
 /* ---- a7, a8 as separate steps (for sharded use: one slab of X per GPU) ---- */
 
@@ -275,8 +289,8 @@ krp_status krp_core_truncate(krp_ctx ctx, int d, const int64_t* dims, const int*
  *   core: device FP32, core_dims; factors[i]: device FP64 dims[i] x core_dims[i]
  * Synchronises the context stream. */
 krp_status krp_residual(krp_ctx ctx, const void* X, krp_dtype xt, int d,
-                        const int64_t* dims, const int* core_dims, const float* core,
-                        const double* const* factors, double* sums);
+                        const int64_t* dims, const int64_t* ld, const int* core_dims,
+                        const float* core, const double* const* factors, double* sums);
 
 /* ---- a6-a8: randomized Tucker pipelines (Alg. 7, Alg. 8) ------------------ */
 
@@ -314,17 +328,17 @@ typedef struct krp_tucker_out {
  * non-finite value (both read from the context's device status word after
  * a stream synchronisation). */
 krp_status krp_tucker_rhosvd(krp_ctx ctx, const void* X, krp_dtype xt, int d,
-                             const int64_t* dims, const int* ranks,
-                             int oversample, uint64_t seed, unsigned flags,
-                             krp_tucker_out* out);
+                             const int64_t* dims, const int64_t* ld,
+                             const int* ranks, int oversample, uint64_t seed,
+                             unsigned flags, krp_tucker_out* out);
 
 /* RSTHOSVD-KRP (Alg. 8), modes in the order 1..d: step i sketches the current
  * core with factors of draw 64+i (l_j x l_i for j < i, n_j x l_i for j > i),
  * QR -> Q_i, G <- G x_i Q_i^T.  Flags as above except KRP_MEMO (ignored). */
 krp_status krp_tucker_sthosvd(krp_ctx ctx, const void* X, krp_dtype xt, int d,
-                              const int64_t* dims, const int* ranks,
-                              int oversample, uint64_t seed, unsigned flags,
-                              krp_tucker_out* out);
+                              const int64_t* dims, const int64_t* ld,
+                              const int* ranks, int oversample, uint64_t seed,
+                              unsigned flags, krp_tucker_out* out);
 
 /* ---- a9-a10: block Hankel single-pass low-rank approximation (Alg. 6) ------ */
 

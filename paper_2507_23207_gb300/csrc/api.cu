@@ -255,25 +255,32 @@ krp_status krp_philox_words(krp_ctx ctx, uint64_t seed, uint32_t c1, uint32_t c2
 }
 
 krp_status krp_sketch_mode(krp_ctx ctx, const void* X, krp_dtype xt, int d, const int64_t* dims,
-                           int n, const void* const* omega, krp_dtype omt, int ell, float* Y) {
+                           const int64_t* ld, int n, const void* const* omega, krp_dtype omt,
+                           int ell, float* Y) {
   return guarded(ctx, [&] {
     SketchArgs a = validate_sketch(X, xt, d, dims, omega, omt, ell);
     KRP_REQUIRE(n >= 0 && n < d, "mode n = %d out of range", n);
     KRP_REQUIRE(Y, "Y is NULL");
-    ensure_workspace(current(), sketch_workspace_bytes(a, false));
+    ensure_workspace(current(), sketch_workspace_bytes(a, false) + dense_copy_bytes(d, dims, ld, xt));
+    a.X = dense_copy(X, xt, d, dims, ld);
     sketch_one_mode(a, n, Y);
   });
 }
 
 krp_status krp_sketch_all_modes(krp_ctx ctx, const void* X, krp_dtype xt, int d,
-                                const int64_t* dims, const void* const* omega, krp_dtype omt,
-                                int ell, float* const* Y) {
+                                const int64_t* dims, const int64_t* ld,
+                                const void* const* omega, krp_dtype omt, int ell,
+                                float* const* Y, int tree_split) {
   return guarded(ctx, [&] {
     SketchArgs a = validate_sketch(X, xt, d, dims, omega, omt, ell);
     KRP_REQUIRE(Y, "Y is NULL");
     for (int j = 0; j < d; ++j) KRP_REQUIRE(Y[j], "Y[%d] is NULL", j);
-    ensure_workspace(current(), sketch_workspace_bytes(a, true));
-    sketch_all_modes(a, Y);
+    KRP_REQUIRE(tree_split == -1 || (tree_split >= 1 && tree_split <= d - 1),
+                "tree_split = %d out of range 1..%d (or -1)", tree_split, d - 1);
+    ensure_workspace(current(), sketch_workspace_bytes(a, true, tree_split) +
+                                    dense_copy_bytes(d, dims, ld, xt));
+    a.X = dense_copy(X, xt, d, dims, ld);
+    sketch_all_modes(a, Y, tree_split);
   });
 }
 
@@ -302,7 +309,7 @@ krp_status krp_qr(krp_ctx ctx, int count, const float* const* Y, const int64_t* 
 }
 
 krp_status krp_multi_ttm(krp_ctx ctx, const void* X, krp_dtype xt, int d, const int64_t* dims,
-                         const double* const* Q, const int* cols, float* G) {
+                         const int64_t* ld, const double* const* Q, const int* cols, float* G) {
   return guarded(ctx, [&] {
     KRP_REQUIRE(d >= 1 && d <= KRP_MAXD, "d out of range");
     checked_numel(d, dims);
@@ -313,8 +320,9 @@ krp_status krp_multi_ttm(krp_ctx ctx, const void* X, krp_dtype xt, int d, const 
       KRP_REQUIRE(Q[j], "Q[%d] is NULL", j);
       KRP_REQUIRE(cols[j] >= 1 && cols[j] <= 256, "cols[%d] out of range", j);
     }
-    ensure_workspace(current(), multi_ttm_workspace_bytes(d, dims, cols, xt));
-    multi_ttm(X, xt, d, dims, Q, cols, G);
+    ensure_workspace(current(), multi_ttm_workspace_bytes(d, dims, cols, xt) +
+                                    dense_copy_bytes(d, dims, ld, xt));
+    multi_ttm(dense_copy(X, xt, d, dims, ld), xt, d, dims, Q, cols, G);
   });
 }
 
@@ -341,8 +349,8 @@ krp_status krp_core_truncate(krp_ctx ctx, int d, const int64_t* dims, const int*
 }
 
 krp_status krp_residual(krp_ctx ctx, const void* X, krp_dtype xt, int d, const int64_t* dims,
-                        const int* core_dims, const float* core, const double* const* factors,
-                        double* sums) {
+                        const int64_t* ld, const int* core_dims, const float* core,
+                        const double* const* factors, double* sums) {
   return guarded(ctx, [&] {
     KRP_REQUIRE(d >= 2 && d <= KRP_MAXD, "d out of range");
     checked_numel(d, dims);
@@ -357,26 +365,31 @@ krp_status krp_residual(krp_ctx ctx, const void* X, krp_dtype xt, int d, const i
       cdim[i] = core_dims[i];
     }
     Ctx* c = current();
-    ensure_workspace(c, residual_workspace_bytes(d, dims, cdim, xt) + ws_bytes(4, 8));
+    ensure_workspace(c, residual_workspace_bytes(d, dims, cdim, xt) + ws_bytes(4, 8) +
+                            dense_copy_bytes(d, dims, ld, xt));
     double* acc = c->ws.take<double>(4);
     KRP_CUDA_CHECK(cudaMemsetAsync(c->d_status, 0, sizeof(int), c->stream));
     KRP_CUDA_CHECK(cudaMemsetAsync(acc, 0, 2 * sizeof(double), c->stream));
-    residual_sums(X, xt, d, dims, core, cdim, factors, acc);
+    residual_sums(dense_copy(X, xt, d, dims, ld), xt, d, dims, core, cdim, factors, acc);
     KRP_CUDA_CHECK(cudaMemcpyAsync(sums, acc, 2 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
     raise_device_status(c);
   });
 }
 
 krp_status krp_tucker_rhosvd(krp_ctx ctx, const void* X, krp_dtype xt, int d, const int64_t* dims,
-                             const int* ranks, int oversample, uint64_t seed, unsigned flags,
-                             krp_tucker_out* out) {
-  return guarded(ctx, [&] { tucker_pipeline(false, X, xt, d, dims, ranks, oversample, seed, flags, out); });
+                             const int64_t* ld, const int* ranks, int oversample, uint64_t seed,
+                             unsigned flags, krp_tucker_out* out) {
+  return guarded(ctx, [&] {
+    tucker_pipeline(false, X, xt, d, dims, ld, ranks, oversample, seed, flags, out);
+  });
 }
 
 krp_status krp_tucker_sthosvd(krp_ctx ctx, const void* X, krp_dtype xt, int d,
-                              const int64_t* dims, const int* ranks, int oversample,
-                              uint64_t seed, unsigned flags, krp_tucker_out* out) {
-  return guarded(ctx, [&] { tucker_pipeline(true, X, xt, d, dims, ranks, oversample, seed, flags, out); });
+                              const int64_t* dims, const int64_t* ld, const int* ranks,
+                              int oversample, uint64_t seed, unsigned flags, krp_tucker_out* out) {
+  return guarded(ctx, [&] {
+    tucker_pipeline(true, X, xt, d, dims, ld, ranks, oversample, seed, flags, out);
+  });
 }
 
 krp_status krp_trace_begin(krp_ctx ctx) {

@@ -6,6 +6,7 @@
 #include <cuda_bf16.h>
 #include <stdint.h>
 
+#include <map>
 #include <string>
 #include <vector>
 
@@ -74,6 +75,8 @@ struct Ctx {
   void (*batch_plan_free)(void*) = nullptr;
   void* hankel_plan = nullptr;             // cached batched block-Hankel plan
   void (*hankel_plan_free)(void*) = nullptr;
+  // tree splits picked by timing, per (dims, l, dtype)
+  std::map<std::vector<int64_t>, int> tree_split_cache;
   // launch trace (krp_trace_begin/end): an event after every launch
   bool trace_on = false;
   std::vector<std::pair<const char*, cudaEvent_t>> trace;

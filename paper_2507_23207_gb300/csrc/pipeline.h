@@ -23,9 +23,13 @@ struct SketchArgs {
 };
 SketchArgs validate_sketch(const void* X, krp_dtype xt, int d, const int64_t* dims,
                            const void* const* omega, krp_dtype omt, int ell);
-size_t sketch_workspace_bytes(const SketchArgs& a, bool all_modes);
+size_t sketch_workspace_bytes(const SketchArgs& a, bool all_modes, int tree_split = -1);
 void sketch_one_mode(const SketchArgs& a, int n, float* Y);
-void sketch_all_modes(const SketchArgs& a, float* const* Y);
+// tree_split: the dimension tree of the tensor-core forms contracts mode 1
+// and the merged modes 2..tree_split+1 in one pass (1 <= tree_split <= d-1);
+// -1 picks it by timing each candidate on the first call for a shape
+// (cached in the context).  The FP32 form ignores it.
+void sketch_all_modes(const SketchArgs& a, float* const* Y, int tree_split = -1);
 
 size_t multi_ttm_workspace_bytes(int d, const int64_t* dims, const int* cols, krp_dtype xt);
 void multi_ttm(const void* X, krp_dtype xt, int d, const int64_t* dims, const double* const* Q,
@@ -39,8 +43,18 @@ void residual_sums(const void* Xd, krp_dtype xt, int d, const int64_t* dims, con
                    const int64_t* cdim, const double* const* Q, double* acc);
 
 void tucker_pipeline(bool sequential, const void* X, krp_dtype xt, int d, const int64_t* dims,
-                     const int* ranks, int oversample, uint64_t seed, unsigned flags,
-                     krp_tucker_out* out);
+                     const int64_t* ld, const int* ranks, int oversample, uint64_t seed,
+                     unsigned flags, krp_tucker_out* out);
+
+// Padded tensors (ld: per-mode leading sizes, ld[j] >= dims[j]; element
+// (i_1..i_d) at sum_j i_j prod_{m<j} ld[m]): padded() checks ld and tells
+// whether it differs from dims; dense_copy() packs a padded device X (both
+// planes of a BF16 hi/lo pair, the lo plane prod(ld) elements after the hi
+// plane) into a dense workspace copy and returns it, or returns X itself.
+bool padded(int d, const int64_t* dims, const int64_t* ld);
+int64_t padded_numel(int d, const int64_t* ld);
+size_t dense_copy_bytes(int d, const int64_t* dims, const int64_t* ld, krp_dtype xt);
+const void* dense_copy(const void* X, krp_dtype xt, int d, const int64_t* dims, const int64_t* ld);
 
 void tucker_batched(krp_dtype xt, int count, krp_tucker_item* items, int oversample,
                     unsigned flags);
@@ -79,15 +93,17 @@ void tc_mttkrp_first_bf16(const __nv_bfloat16* X, int64_t n1, int64_t n2, int64_
 size_t tc_workspace_bytes(int64_t n1, int64_t S, int L);
 // acc[0] += ||X - Q1 H||^2, acc[1] += ||X||^2 for BF16 X (n1 x S), Q1 FP64
 // n1 x c, H FP32 c x S, on tensor cores (c <= 64, n1 % 8 == 0)
-// One pass over BF16 X (n1, n2, T) for the dimension tree: Y1 (n1 x L),
-// Y2 (n2 x L) and C (T x L, the contraction of modes 1 and 2 weighted by the
-// factors); w is the T x L table of Khatri-Rao weights of modes 3..d.  Xlo
-// (optional): the lo plane of a BF16 hi/lo X.
+// One pass over BF16 X viewed as (n1, n2, T) for the dimension tree: Y1
+// (n1 x L), Y2 (n2 x L) and C (T x L, the contraction of the first two
+// dimensions weighted by their factors); Om1 is the BF16 factor of mode 1,
+// Om2 the FP32 factor of the second dimension (one mode, or the Khatri-Rao
+// rows of several merged modes), w the T x L table of Khatri-Rao weights of
+// the rest.  Xlo (optional): the lo plane of a BF16 hi/lo X.
 bool tc_tree_supported(int64_t n1, int L);
 // workspace of the tree's C partials (beyond tc_workspace_bytes)
 size_t tc_tree_workspace_bytes(int64_t n1, int64_t n2, int64_t T, int L);
 void tc_tree_bf16(const __nv_bfloat16* X, int64_t n1, int64_t n2, int64_t T,
-                  const __nv_bfloat16* Om1, const __nv_bfloat16* Om2, const float* w, int L,
+                  const __nv_bfloat16* Om1, const float* Om2, const float* w, int L,
                   float* Y1, float* Y2, float* C, const __nv_bfloat16* Xlo = nullptr);
 bool tc_residual_supported(int64_t n1, int c);
 size_t tc_residual_workspace_bytes(int64_t n1, int64_t S);

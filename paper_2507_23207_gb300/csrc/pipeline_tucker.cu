@@ -69,6 +69,30 @@ __global__ void bf16_to_f32_kernel(const __nv_bfloat16* __restrict__ s, float* _
 
 int grid_of(int64_t n) { return (int)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, 8192)); }
 
+// Sides and element strides of a padded tensor (element (i_1..i_d) at
+// sum_j i_j str[j]).
+struct StridedDims {
+  int d;
+  int64_t dims[KRP_MAXD];
+  int64_t str[KRP_MAXD];
+};
+
+// dense[r n1 + i] = src[offset of row r + i]: one mode-1 row (n1 contiguous
+// elements of both) per CTA iteration, rows r in mixed radix over modes 2..d
+template <class T>
+__global__ void pack_strided_kernel(const T* __restrict__ src, T* __restrict__ dst,
+                                    const StridedDims A, int64_t rows) {
+  const int64_t n1 = A.dims[0];
+  for (int64_t r = blockIdx.x; r < rows; r += gridDim.x) {
+    int64_t rem = r, off = 0;
+    for (int j = 1; j < A.d; ++j) {
+      off += (rem % A.dims[j]) * A.str[j];
+      rem /= A.dims[j];
+    }
+    for (int64_t i = threadIdx.x; i < n1; i += blockDim.x) dst[r * n1 + i] = src[off + i];
+  }
+}
+
 struct Timer {
   bool on = false;
   cudaEvent_t ev[64] = {};
@@ -136,6 +160,62 @@ void convert_bf16_to_f32(const __nv_bfloat16* src, float* dst, int64_t n) {
   if (n <= 0) return;
   bf16_to_f32_kernel<<<grid_of(n), 256, 0, stream()>>>(src, dst, n);
   check_launch("bf16_to_f32");
+}
+
+// -------------------------------------------------- padded (ld) inputs ----
+bool padded(int d, const int64_t* dims, const int64_t* ld) {
+  if (!ld) return false;
+  bool pad = false;
+  for (int j = 0; j < d; ++j) {
+    KRP_REQUIRE(ld[j] >= dims[j], "ld[%d] = %lld is smaller than dims[%d] = %lld", j,
+                (long long)ld[j], j, (long long)dims[j]);
+    pad = pad || ld[j] != dims[j];
+  }
+  return pad;
+}
+
+int64_t padded_numel(int d, const int64_t* ld) {
+  int64_t n = 1;
+  for (int j = 0; j < d; ++j) {
+    KRP_REQUIRE(ld[j] >= 1 && n <= (int64_t(1) << 46) / ld[j], "padded tensor too large");
+    n *= ld[j];
+  }
+  return n;
+}
+
+size_t dense_copy_bytes(int d, const int64_t* dims, const int64_t* ld, krp_dtype xt) {
+  return padded(d, dims, ld) ? ws_bytes((size_t)checked_numel(d, dims), dtype_size(xt)) : 0;
+}
+
+const void* dense_copy(const void* X, krp_dtype xt, int d, const int64_t* dims, const int64_t* ld) {
+  if (!padded(d, dims, ld)) return X;
+  KRP_REQUIRE(is_device_ptr(X), "a padded X (ld) must be device memory");
+  const int64_t N = checked_numel(d, dims);
+  const int64_t NP = padded_numel(d, ld);
+  StridedDims A{};
+  A.d = d;
+  int64_t st = 1;
+  for (int j = 0; j < d; ++j) {
+    A.dims[j] = dims[j];
+    A.str[j] = st;
+    st *= ld[j];
+  }
+  const int64_t rows = N / dims[0];
+  const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(rows, 65535));
+  const int planes = xt == KRP_BF16X2 ? 2 : 1;  // the lo plane follows the hi plane
+  void* out = current()->ws.take<char>((size_t)N * dtype_size(xt));
+  for (int p = 0; p < planes; ++p) {
+    if (xt == KRP_F32) {
+      pack_strided_kernel<float><<<grid, 256, 0, stream()>>>(static_cast<const float*>(X),
+                                                             static_cast<float*>(out), A, rows);
+    } else {
+      pack_strided_kernel<__nv_bfloat16><<<grid, 256, 0, stream()>>>(
+          static_cast<const __nv_bfloat16*>(X) + p * NP, static_cast<__nv_bfloat16*>(out) + p * N,
+          A, rows);
+    }
+    check_launch("pack_strided");
+  }
+  return out;
 }
 
 // ------------------------------------------------------------- dispatch ----
@@ -210,7 +290,31 @@ SketchArgs validate_sketch(const void* X, krp_dtype xt, int d, const int64_t* di
   return a;
 }
 
-size_t sketch_workspace_bytes(const SketchArgs& a, bool) {
+// Splits the autotuner tries: merged second dimensions up to 2^20 rows (and
+// always the plain one, s = 1); an explicit split may merge more.
+static bool tree_split_candidate(int64_t n2, int s) { return s == 1 || n2 <= (int64_t(1) << 20); }
+
+// Workspace of the one-pass tree for a split s (the largest over the
+// autotuner's candidates for s = -1): the merged dimension's factor and
+// sketch (n2' x l), the slab weights and sketch (T x l), and the kernel's C
+// partials.
+static size_t tree_ws_bytes(int d, const int64_t* dims, int ell, int split = -1) {
+  int64_t N = 1;
+  for (int j = 0; j < d; ++j) N *= dims[j];
+  size_t best = 0;
+  int64_t n2 = 1;
+  for (int s = 1; s <= d - 1; ++s) {
+    n2 *= dims[s];
+    if (split == -1 ? !tree_split_candidate(n2, s) : s != split) continue;
+    const int64_t T = N / (dims[0] * n2);
+    const size_t b = 2 * ws_bytes((size_t)n2 * ell, 4) + 2 * ws_bytes((size_t)T * ell, 4) +
+                     tc_tree_workspace_bytes(dims[0], n2, T, ell);
+    best = std::max(best, b);
+  }
+  return best;
+}
+
+size_t sketch_workspace_bytes(const SketchArgs& a, bool, int tree_split) {
   const int64_t n1 = a.dims[0];
   size_t b = ws_bytes((size_t)(a.N / n1) * a.ell, 4);               // B
   for (int j = 0; j < a.d; ++j) b += ws_bytes((size_t)a.dims[j] * a.ell, 4);  // f32 factors
@@ -219,8 +323,7 @@ size_t sketch_workspace_bytes(const SketchArgs& a, bool) {
   for (int j = 0; j < a.d; ++j) dmax = std::max<int64_t>(dmax, a.dims[j]);
   b += mttkrp_first_f32_workspace_bytes(a.N / std::max<int64_t>(1, a.dims[0]), dmax);
   if (bf16_family(a.xt))
-    b += tc_workspace_bytes(n1, a.N / n1, a.ell) +
-         tc_tree_workspace_bytes(n1, a.dims[1], a.N / (n1 * a.dims[1]), a.ell);
+    b += tc_workspace_bytes(n1, a.N / n1, a.ell) + tree_ws_bytes(a.d, a.dims, a.ell, tree_split);
   return b + (1 << 20);
 }
 
@@ -256,30 +359,108 @@ void sketch_one_mode(const SketchArgs& a, int n, float* Y) {
   diag_contract_f32(B, a.d - 1, a.dims + 1, S, n - 1, f32v + 1, a.ell, Y);
 }
 
-void sketch_all_modes(const SketchArgs& a, float* const* Y) {
+// One-pass tree with the modes 2..s+1 merged into its second dimension
+// (n2' = prod of their sides, factor = their Khatri-Rao rows, FP32) and the
+// modes s+2..d as its slabs (weights w).  Y_1 comes out whole; the merged
+// dimension's sketch is contracted to Y_2..Y_{s+1}, the slabs' to the rest.
+static void tree_sketch(const SketchArgs& a, float* const* Y, int s) {
+  Ctx* c = current();
+  // FP32 copies of the factors serve only the contractions after the tree
+  const float* f32v[KRP_MAXD] = {};
+  if (s > 1 || a.d - 1 - s > 1) f32_factor_views(a, f32v);
+  const int64_t n1 = a.dims[0];
+  int64_t n2 = 1;
+  for (int j = 1; j <= s; ++j) n2 *= a.dims[j];
+  const int64_t T = a.N / (n1 * n2);
+  float* om2 = c->ws.take<float>((size_t)n2 * a.ell);
+  if (s == 1) {
+    convert_bf16_to_f32(static_cast<const __nv_bfloat16*>(a.omega[1]), om2, n2 * a.ell);
+  } else {
+    Radix R2;
+    R2.n = s;
+    for (int j = 1; j <= s; ++j) {
+      R2.radix[j - 1] = a.dims[j];
+      R2.V[j - 1] = static_cast<const float*>(a.omega[j]);  // bf16 bits
+    }
+    krp_rows(R2, n2, a.ell, true, om2);
+  }
+  Radix R;
+  R.n = a.d - 1 - s;
+  for (int j = s + 1; j < a.d; ++j) {
+    R.radix[j - s - 1] = a.dims[j];
+    R.V[j - s - 1] = static_cast<const float*>(a.omega[j]);  // bf16 bits
+  }
+  float* w = c->ws.take<float>((size_t)T * a.ell);
+  krp_rows(R, T, a.ell, true, w);
+  float* Y2 = (s == 1) ? Y[1] : c->ws.take<float>((size_t)n2 * a.ell);
+  float* C = (a.d - 1 - s == 1) ? Y[a.d - 1] : c->ws.take<float>((size_t)T * a.ell);
+  tc_tree_bf16(static_cast<const __nv_bfloat16*>(a.X), n1, n2, T,
+               static_cast<const __nv_bfloat16*>(a.omega[0]), om2, w, a.ell, Y[0], Y2, C,
+               lo_plane(a.X, a.xt, a.N));
+  if (s > 1)
+    for (int n = 1; n <= s; ++n) diag_contract_f32(Y2, s, a.dims + 1, n2, n - 1, f32v + 1, a.ell, Y[n]);
+  if (a.d - 1 - s > 1)
+    for (int n = s + 1; n < a.d; ++n)
+      diag_contract_f32(C, a.d - 1 - s, a.dims + s + 1, T, n - s - 1, f32v + s + 1, a.ell, Y[n]);
+}
+
+static bool tree_split_ok(const SketchArgs& a, int s) {
+  if (s < 1 || s > a.d - 1) return false;
+  int64_t n2 = 1;
+  for (int j = 1; j <= s; ++j) n2 *= a.dims[j];
+  return n2 < (int64_t(1) << 31) && a.N / (a.dims[0] * n2) < (int64_t(1) << 31);
+}
+
+void sketch_all_modes(const SketchArgs& a, float* const* Y, int tree_split) {
   for (int j = 0; j < a.d; ++j) KRP_REQUIRE(a.omega[j], "omega[%d] is NULL", j);
   const int64_t n1 = a.dims[0], S = a.N / n1;
   const float* f32v[KRP_MAXD];
   if (bf16_family(a.xt) && tc_tree_supported(n1, a.ell)) {
-    // FP32 copies of the factors are needed only for the modes past the tree
-    if (a.d > 3) f32_factor_views(a, f32v);
     // one pass over X for every mode (fused dimension tree on tensor cores)
-    const int64_t n2 = a.dims[1], T = S / n2;
-    Radix R;
-    R.n = a.d - 2;
-    for (int j = 2; j < a.d; ++j) {
-      R.radix[j - 2] = a.dims[j];
-      R.V[j - 2] = static_cast<const float*>(a.omega[j]);  // bf16 bits
+    KRP_REQUIRE(tree_split == -1 || tree_split_ok(a, tree_split),
+                "tree_split = %d out of range 1..%d (or -1)", tree_split, a.d - 1);
+    Ctx* c = current();
+    int s = tree_split;
+    if (s == -1) {
+      std::vector<int64_t> key(a.dims, a.dims + a.d);
+      key.push_back(a.ell);
+      key.push_back(static_cast<int64_t>(a.xt));
+      auto it = c->tree_split_cache.find(key);
+      if (it != c->tree_split_cache.end()) {
+        s = it->second;
+      } else {
+        // time every admissible split once (after a first run of each) and
+        // keep the fastest; the workspace arena is rewound between runs
+        cudaEvent_t e0, e1;
+        KRP_CUDA_CHECK(cudaEventCreate(&e0));
+        KRP_CUDA_CHECK(cudaEventCreate(&e1));
+        float best = 0.f;
+        int64_t n2c = 1;
+        for (int cand = 1; cand <= a.d - 1; ++cand) {
+          n2c *= a.dims[cand];
+          if (!tree_split_ok(a, cand) || !tree_split_candidate(n2c, cand)) continue;
+          const size_t mark = c->ws.off;
+          tree_sketch(a, Y, cand);
+          c->ws.off = mark;
+          KRP_CUDA_CHECK(cudaEventRecord(e0, c->stream));
+          tree_sketch(a, Y, cand);
+          KRP_CUDA_CHECK(cudaEventRecord(e1, c->stream));
+          c->ws.off = mark;
+          KRP_CUDA_CHECK(cudaEventSynchronize(e1));
+          float ms = 0.f;
+          KRP_CUDA_CHECK(cudaEventElapsedTime(&ms, e0, e1));
+          if (s == -1 || ms < best) {
+            best = ms;
+            s = cand;
+          }
+        }
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        KRP_REQUIRE(s >= 1, "no admissible tree split");
+        c->tree_split_cache[key] = s;
+      }
     }
-    float* w = current()->ws.take<float>((size_t)T * a.ell);
-    krp_rows(R, T, a.ell, true, w);
-    float* C = (a.d == 3) ? Y[2] : current()->ws.take<float>((size_t)T * a.ell);
-    tc_tree_bf16(static_cast<const __nv_bfloat16*>(a.X), n1, n2, T,
-                 static_cast<const __nv_bfloat16*>(a.omega[0]),
-                 static_cast<const __nv_bfloat16*>(a.omega[1]), w, a.ell, Y[0], Y[1], C,
-                 lo_plane(a.X, a.xt, a.N));
-    for (int n = 2; n < a.d && a.d > 3; ++n)
-      diag_contract_f32(C, a.d - 2, a.dims + 2, T, n - 2, f32v + 2, a.ell, Y[n]);
+    tree_sketch(a, Y, s);
     return;
   }
   f32_factor_views(a, f32v);
@@ -461,8 +642,8 @@ void residual_sums(const void* Xd, krp_dtype xt, int d, const int64_t* dims, con
 
 // ------------------------------------------------------------ pipeline -----
 void tucker_pipeline(bool sequential, const void* X, krp_dtype xt, int d, const int64_t* dims,
-                     const int* ranks, int oversample, uint64_t seed, unsigned flags,
-                     krp_tucker_out* out) {
+                     const int64_t* ld, const int* ranks, int oversample, uint64_t seed,
+                     unsigned flags, krp_tucker_out* out) {
   Ctx* c = current();
   KRP_REQUIRE(d >= 2 && d <= KRP_MAXD, "d = %d out of range 2..%d", d, KRP_MAXD);
   const int64_t N = checked_numel(d, dims);
@@ -499,7 +680,9 @@ void tucker_pipeline(bool sequential, const void* X, krp_dtype xt, int d, const 
     for (int i = 0; i < d; ++i) dmax = std::max<int64_t>(dmax, dims[i]);
     need += mttkrp_first_f32_workspace_bytes(maxS, dmax);  // FP32 slab-MTTKRP operands
   }
-  if (!x_dev) need += ws_bytes((size_t)N, xb);
+  const bool x_pad = padded(d, dims, ld);
+  if (!x_dev) need += ws_bytes((size_t)(x_pad ? padded_numel(d, ld) : N), xb);
+  if (x_pad) need += ws_bytes((size_t)N, xb);
   int64_t core_l = 1;
   for (int i = 0; i < d; ++i) {
     need += (size_t)d * ws_bytes((size_t)dims[i] * ellmax, 4 + 4);  // factors (both types)
@@ -512,8 +695,7 @@ void tucker_pipeline(bool sequential, const void* X, krp_dtype xt, int d, const 
   need += 4 * ws_bytes((size_t)core_l, 8) + 2 * ws_bytes((size_t)core_l, 4);
   need += sym_eig_workspace_bytes(d);
   if (bf16_family(xt))
-    need += tc_workspace_bytes(dims[0], N / dims[0], 2 * ellmax) +
-            tc_tree_workspace_bytes(dims[0], dims[1], N / (dims[0] * dims[1]), ellmax);
+    need += tc_workspace_bytes(dims[0], N / dims[0], 2 * ellmax) + tree_ws_bytes(d, dims, ellmax);
   if (bf16_family(xt) && resid) need += tc_residual_workspace_bytes(dims[0], N / dims[0]);
   need += 4 << 20;
   ensure_workspace(c, need);
@@ -525,10 +707,13 @@ void tucker_pipeline(bool sequential, const void* X, krp_dtype xt, int d, const 
 
   const void* Xd = X;
   if (!x_dev) {
-    void* p = ws.take<char>((size_t)N * xb);
-    KRP_CUDA_CHECK(cudaMemcpyAsync(p, X, (size_t)N * xb, cudaMemcpyHostToDevice, c->stream));
+    // host X (padded or not) is staged as given, then packed on the device
+    const size_t hb = (size_t)(x_pad ? padded_numel(d, ld) : N) * xb;
+    void* p = ws.take<char>(hb);
+    KRP_CUDA_CHECK(cudaMemcpyAsync(p, X, hb, cudaMemcpyHostToDevice, c->stream));
     Xd = p;
   }
+  Xd = dense_copy(Xd, xt, d, dims, ld);
 
   // ---------------- factors (a1) and sketches (a2/a3), QR (a4), core (a5/a6)
   float* Y[KRP_MAXD];

@@ -569,10 +569,13 @@ __global__ void __launch_bounds__(kThreads, 1)
 // stored; with one buffer the next group waits for the store.  Without
 // draining D2 holds all of the CTA's items and is stored once at the end.
 // Epilogue per item: Y2[i2, k] += D1 w[t, k] (registers, flushed when the
-// block b changes) and each warp's 32-row partial of C[t, k] = sum_i2
-// Omega2[i2, k] D1[i2, k] (warp reduce-scatter) stored into its own slot of
-// the C partials; second kernels sum the Y1 and C partials in a fixed order
-// (no atomics on the contended C rows).  For d = 3, C is Y3 itself.
+// block b changes) and C[t, k] = sum_i2 Omega2[i2, k] D1[i2, k]: each warp
+// reduces its 32 rows (warp reduce-scatter) and adds them into a shared
+// slot with shared-memory atomics; the last of the four warps to finish the
+// item stores the slot into the item's entry of the C partials and clears
+// it (no barrier among the warps, so an aborted CTA cannot deadlock).
+// Second kernels sum the Y1 and C partials in a fixed order (no global
+// atomics on the contended C rows).  For d = 3, C is Y3 itself.
 // Warp reduce-scatter of CNT per-lane values: on return the warp's sums over
 // its 32 lanes have been handed to sink(kbase + j, sum) by one lane each
 // (j < CNT).  Each halving step exchanges half of the values with the lane
@@ -612,9 +615,9 @@ struct WarpReduceScatter {
 
 struct TreeArgs {
   const float* w;            // T x L
-  const __nv_bfloat16* om2;  // n2 x L (column-major)
+  const float* om2;          // n2 x L (column-major): the second operand's factor
   float* Y2;                 // n2 x L
-  float* Cw;                 // C partials: [(seg nb + b) 4 + warp][t][k < N]
+  float* Cw;                 // C partials: [seg nb + b][t][k < N]
   float* Yw;                 // Y1 partials: [cta][k < N][kseg * 128 rows of its segment]
   int64_t n2, T, items;      // items = nb * T
   int L, nb, kch, kseg, cps; // kch = ceil(n1 / 128); cps = CTAs per segment
@@ -649,6 +652,8 @@ __global__ void __launch_bounds__(320, 1)
   Bars* bars = reinterpret_cast<Bars*>(b2 + 2 * kB2Buf);
   __shared__ uint64_t b2full[2], b2empty[2], fbar, d2full[2], d2empty[2];
   __shared__ float wsm[2][N];  // w[t, :] beside B2_t, same double buffering
+  __shared__ float csm[2][N];  // C[t, :] of the item, summed over the four epilogue warps
+  __shared__ int cdone[2];     // warps done with the item's csm slot
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int seg = blockIdx.x / P.cps;
   const int rk = blockIdx.x % P.cps;
@@ -669,7 +674,9 @@ __global__ void __launch_bounds__(320, 1)
       mbar_init(smem_u32(&b2empty[a]), 1 + 4);  // MMA commit + four epilogue warps (wsm)
       mbar_init(smem_u32(&d2full[a]), 1);
       mbar_init(smem_u32(&d2empty[a]), 4);
+      cdone[a] = 0;
     }
+    for (int k = 0; k < 2 * N; ++k) (&csm[0][0])[k] = 0.f;
     mbar_init(smem_u32(&fbar), 1);
     mbar_init(smem_u32(&bars->drain), 1);
     bars->abort_flag = 0;
@@ -825,7 +832,7 @@ __global__ void __launch_bounds__(320, 1)
         const int64_t i2 = static_cast<int64_t>(b) * 128 + tid;
 #pragma unroll
         for (int k = 0; k < N; ++k)
-          om[k] = (k < P.L && i2 < P.n2) ? __bfloat162float(P.om2[i2 + P.n2 * k]) : 0.f;
+          om[k] = (k < P.L && i2 < P.n2) ? P.om2[i2 + P.n2 * k] : 0.f;
       }
       const float wl0 = nw0, wl1 = nw1;
       load_w(j + 1, nw0, nw1);
@@ -911,7 +918,7 @@ __global__ void __launch_bounds__(320, 1)
 #pragma unroll
         for (int k = 0; k < N; ++k) {
           y2[k] = 0.f;
-          o2[k] = (valid && k < P.L) ? __bfloat162float(P.om2[i2 + P.n2 * k]) : 0.f;
+          o2[k] = (valid && k < P.L) ? P.om2[i2 + P.n2 * k] : 0.f;
         }
       }
       const int acc = tl & 1;
@@ -927,8 +934,8 @@ __global__ void __launch_bounds__(320, 1)
       }
       tc_fence_after();
       const uint32_t base = tmem + (static_cast<uint32_t>(q * 32) << 16) + acc * N;
-      // this warp's slot of the C partials for item (b, t)
-      float* cw = P.Cw + ((static_cast<size_t>(seg) * P.nb + b) * 4 + q) * P.T * N +
+      // the item's entry of the C partials
+      float* cw = P.Cw + (static_cast<size_t>(seg) * P.nb + b) * P.T * N +
                   static_cast<size_t>(t) * N;
       // all of D1's columns in flight at once, one wait
       float v[N];
@@ -944,7 +951,27 @@ __global__ void __launch_bounds__(320, 1)
           y2[k] = fmaf(v[k], wsm[acc][k], y2[k]);
           cp[jj] = v[k] * o2[k];
         }
-        WarpReduceScatter<16, 16>::run(cp, lane, cc, [&](int k, float x) { cw[k] = x; });
+        WarpReduceScatter<16, 16>::run(cp, lane, cc,
+                                       [&](int k, float x) { atomicAdd(&csm[acc][k], x); });
+      }
+      // the last warp stores the slot and clears it; it is reused two items
+      // later, which the MMAs reach only after all four warps have released
+      // D1 buffer acc below
+      __syncwarp();
+      int last_w = 0;
+      if (lane == 0) {
+        __threadfence_block();
+        last_w = atomicAdd(&cdone[acc], 1) == 3;
+      }
+      last_w = __shfl_sync(0xffffffffu, last_w, 0);
+      if (last_w) {
+        __threadfence_block();
+        for (int k = lane; k < N; k += 32) {
+          cw[k] = csm[acc][k];
+          csm[acc][k] = 0.f;
+        }
+        if (lane == 0) cdone[acc] = 0;
+        __threadfence_block();
       }
       tc_fence_before();
       __syncwarp();
@@ -1221,20 +1248,33 @@ __global__ void tree_reduce_kernel(const float* __restrict__ Yw, int cps, int64_
   }
 }
 
-// C[t + T k] = sum over the `parts` partial slots p (in order) of
-// Cw[(p T + t) N + k]
-__global__ void tree_c_reduce_kernel(const float* __restrict__ Cw, int64_t parts, int64_t T,
-                                     int L, int N, float* __restrict__ C) {
-  // consecutive threads take consecutive k of one t: coalesced partial reads
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < T * L;
-       e += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t t = e / L;
-    const int k = static_cast<int>(e % L);
-    const float* src = Cw + static_cast<size_t>(t) * N + k;
-    const size_t step = static_cast<size_t>(T) * N;
-    float acc = 0.f;
-    for (int64_t p = 0; p < parts; ++p) acc += src[p * step];
-    C[t + T * k] = acc;
+// C[t + T k] = sum over the `parts` partial slots p of Cw[(p T + t) N + k]:
+// one CTA per slab t, 256 threads as 8 slices x 32 lanes over k; lane k' of
+// slice q sums the slots p = q, q + 8, ..., the slices then add up in a
+// fixed order in shared memory
+__global__ void __launch_bounds__(256) tree_c_reduce_kernel(const float* __restrict__ Cw,
+                                                            int64_t parts, int64_t T, int L, int N,
+                                                            float* __restrict__ C) {
+  __shared__ float part[8][64];
+  const int q = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const size_t step = static_cast<size_t>(T) * N;
+  for (int64_t t = blockIdx.x; t < T; t += gridDim.x) {
+    for (int k0 = 0; k0 < L; k0 += 32) {
+      const int k = k0 + lane;
+      float acc = 0.f;
+      if (k < L) {
+        const float* src = Cw + static_cast<size_t>(t) * N + k;
+        for (int64_t p = q; p < parts; p += 8) acc += src[p * step];
+      }
+      part[q][lane] = acc;
+      __syncthreads();
+      if (q == 0 && k < L) {
+        float s = 0.f;
+        for (int r = 0; r < 8; ++r) s += part[r][lane];
+        C[t + T * k] = s;
+      }
+      __syncthreads();
+    }
   }
 }
 
@@ -1366,7 +1406,7 @@ bool tc_available() { return true; }
 size_t tc_tree_workspace_bytes(int64_t n1, int64_t n2, int64_t T, int L) {
   const int64_t N = round_up(L, 16);
   const int64_t nseg = (n1 + 127) / 128;  // at most one segment per chunk
-  return ws_bytes((size_t)nseg * ((n2 + 127) / 128) * 4 * T * N, 4) + (1 << 16);
+  return ws_bytes((size_t)nseg * ((n2 + 127) / 128) * T * N, 4) + (1 << 16);
 }
 
 size_t tc_workspace_bytes(int64_t n1, int64_t S, int L) {
@@ -1473,7 +1513,7 @@ void launch_tree_n(const CUtensorMap& mx, const CUtensorMap& mxlo, const CUtenso
 }  // namespace
 
 void tc_tree_bf16(const __nv_bfloat16* X, int64_t n1, int64_t n2, int64_t T,
-                  const __nv_bfloat16* Om1, const __nv_bfloat16* Om2, const float* w, int L,
+                  const __nv_bfloat16* Om1, const float* Om2, const float* w, int L,
                   float* Y1, float* Y2, float* C, const __nv_bfloat16* Xlo) {
   KRP_REQUIRE(tc_tree_supported(n1, L), "fused tree needs n_1 %% 8 == 0 and l <= 64");
   KRP_REQUIRE((reinterpret_cast<uintptr_t>(X) & 15) == 0, "X must be 16-byte aligned");
@@ -1526,7 +1566,7 @@ void tc_tree_bf16(const __nv_bfloat16* X, int64_t n1, int64_t n2, int64_t T,
   const int64_t nb = (n2 + 127) / 128;
   P.nb = static_cast<int>(nb);
   P.items = nb * T;
-  P.Cw = ctx->ws.take<float>((size_t)nseg * nb * 4 * T * N);
+  P.Cw = ctx->ws.take<float>((size_t)nseg * nb * T * N);
   P.cps = static_cast<int>(std::max<int64_t>(1, std::min<int64_t>(ctx->num_sms / nseg, P.items)));
   const int grid = nseg * P.cps;
   const int64_t segrows = static_cast<int64_t>(P.kseg) * 128;
@@ -1542,8 +1582,8 @@ void tc_tree_bf16(const __nv_bfloat16* X, int64_t n1, int64_t n2, int64_t T,
   tree_reduce_kernel<<<(int)std::min<int64_t>((n1 * L + 255) / 256, 4096), 256, 0, stream()>>>(
       P.Yw, P.cps, segrows, n1, L, N, Y1);
   check_launch("tree_reduce");
-  tree_c_reduce_kernel<<<(int)std::min<int64_t>((T * L + 255) / 256, 4096), 256, 0, stream()>>>(
-      P.Cw, (int64_t)nseg * nb * 4, T, L, N, C);
+  tree_c_reduce_kernel<<<(int)std::min<int64_t>(T, 65535), 256, 0, stream()>>>(
+      P.Cw, (int64_t)nseg * nb, T, L, N, C);
   check_launch("tree_c_reduce");
 }
 

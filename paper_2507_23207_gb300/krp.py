@@ -110,19 +110,21 @@ def load_library(path: Optional[str] = None):
                                       C.c_int, C.c_int, C.POINTER(vp)]),
         "krp_philox_words": (C.c_int, [vp, C.c_uint64, C.c_uint32, C.c_uint32, C.c_uint32,
                                        C.c_uint64, C.c_int64, vp]),
-        "krp_sketch_mode": (C.c_int, [vp, vp, C.c_int, C.c_int, i64p, C.c_int, C.POINTER(vp),
-                                      C.c_int, C.c_int, vp]),
-        "krp_sketch_all_modes": (C.c_int, [vp, vp, C.c_int, C.c_int, i64p, C.POINTER(vp),
-                                           C.c_int, C.c_int, C.POINTER(vp)]),
+        "krp_sketch_mode": (C.c_int, [vp, vp, C.c_int, C.c_int, i64p, i64p, C.c_int,
+                                      C.POINTER(vp), C.c_int, C.c_int, vp]),
+        "krp_sketch_all_modes": (C.c_int, [vp, vp, C.c_int, C.c_int, i64p, i64p, C.POINTER(vp),
+                                           C.c_int, C.c_int, C.POINTER(vp), C.c_int]),
         "krp_qr": (C.c_int, [vp, C.c_int, C.POINTER(vp), i64p, C.POINTER(C.c_int),
                              C.POINTER(vp), C.POINTER(vp)]),
         "krp_qr_noalloc": (C.c_int, [vp, C.c_int64, C.c_int, vp, vp, vp]),
-        "krp_multi_ttm": (C.c_int, [vp, vp, C.c_int, C.c_int, i64p, C.POINTER(vp),
+        "krp_multi_ttm": (C.c_int, [vp, vp, C.c_int, C.c_int, i64p, i64p, C.POINTER(vp),
                                     C.POINTER(C.c_int), vp]),
-        "krp_tucker_rhosvd": (C.c_int, [vp, vp, C.c_int, C.c_int, i64p, C.POINTER(C.c_int),
-                                        C.c_int, C.c_uint64, C.c_uint, C.POINTER(TuckerOut)]),
-        "krp_tucker_sthosvd": (C.c_int, [vp, vp, C.c_int, C.c_int, i64p, C.POINTER(C.c_int),
-                                         C.c_int, C.c_uint64, C.c_uint, C.POINTER(TuckerOut)]),
+        "krp_tucker_rhosvd": (C.c_int, [vp, vp, C.c_int, C.c_int, i64p, i64p,
+                                        C.POINTER(C.c_int), C.c_int, C.c_uint64, C.c_uint,
+                                        C.POINTER(TuckerOut)]),
+        "krp_tucker_sthosvd": (C.c_int, [vp, vp, C.c_int, C.c_int, i64p, i64p,
+                                         C.POINTER(C.c_int), C.c_int, C.c_uint64, C.c_uint,
+                                         C.POINTER(TuckerOut)]),
         "krp_block_hankel_lowrank": (C.c_int, [vp, vp, C.c_int, C.c_int, C.c_int, C.c_int,
                                                C.c_int, C.c_int, C.c_int, C.c_uint64, vp, vp,
                                                vp]),
@@ -139,7 +141,7 @@ def load_library(path: Optional[str] = None):
         "krp_core_truncate": (C.c_int, [vp, C.c_int, i64p, C.POINTER(C.c_int),
                                         C.POINTER(C.c_int), vp, C.POINTER(vp), vp,
                                         C.POINTER(vp)]),
-        "krp_residual": (C.c_int, [vp, vp, C.c_int, C.c_int, i64p, C.POINTER(C.c_int), vp,
+        "krp_residual": (C.c_int, [vp, vp, C.c_int, C.c_int, i64p, i64p, C.POINTER(C.c_int), vp,
                                    C.POINTER(vp), C.POINTER(C.c_double)]),
     }
     for name, (res, args) in sig.items():
@@ -285,17 +287,22 @@ def krp_philox_words(ctx: Context, seed: int, c1: int, c2: int, c3: int, first_b
                                        _ptr(out)))
 
 
-def krp_sketch_mode(ctx: Context, X, dims: Sequence[int], n: int, omega: Sequence, ell: int, Y):
+def _ld(ld):
+    return None if ld is None else _i64(ld)
+
+
+def krp_sketch_mode(ctx: Context, X, dims: Sequence[int], n: int, omega: Sequence, ell: int, Y,
+                    ld: Optional[Sequence[int]] = None):
     om_t = next(o for o in omega if o is not None)
     ctx.check(ctx.lib.krp_sketch_mode(ctx.handle, _ptr(X), _dtype_code(X), len(dims), _i64(dims),
-                                      n, _ptrs(omega), _dtype_code(om_t), ell, _ptr(Y)))
+                                      _ld(ld), n, _ptrs(omega), _dtype_code(om_t), ell, _ptr(Y)))
 
 
 def krp_sketch_all_modes(ctx: Context, X, dims: Sequence[int], omega: Sequence, ell: int,
-                         Ys: Sequence):
+                         Ys: Sequence, ld: Optional[Sequence[int]] = None, tree_split: int = -1):
     ctx.check(ctx.lib.krp_sketch_all_modes(ctx.handle, _ptr(X), _dtype_code(X), len(dims),
-                                           _i64(dims), _ptrs(omega), _dtype_code(omega[0]), ell,
-                                           _ptrs(Ys)))
+                                           _i64(dims), _ld(ld), _ptrs(omega),
+                                           _dtype_code(omega[0]), ell, _ptrs(Ys), tree_split))
 
 
 def krp_qr(ctx: Context, Ys: Sequence, ms: Sequence[int], ls: Sequence[int], Qs: Sequence,
@@ -321,9 +328,10 @@ def krp_qr_noalloc(Y, m: int, l: int, Q, R=None, stream: Optional[int] = None) -
     return int(lib.krp_qr_noalloc(_ptr(Y), m, l, _ptr(Q), _ptr(R), C.c_void_p(stream)))
 
 
-def krp_multi_ttm(ctx: Context, X, dims: Sequence[int], Qs: Sequence, cols: Sequence[int], G):
+def krp_multi_ttm(ctx: Context, X, dims: Sequence[int], Qs: Sequence, cols: Sequence[int], G,
+                  ld: Optional[Sequence[int]] = None):
     ctx.check(ctx.lib.krp_multi_ttm(ctx.handle, _ptr(X), _dtype_code(X), len(dims), _i64(dims),
-                                    _ptrs(Qs), _i32(cols), _ptr(G)))
+                                    _ld(ld), _ptrs(Qs), _i32(cols), _ptr(G)))
 
 
 def krp_core_truncate(ctx: Context, dims: Sequence[int], ell: Sequence[int], ranks: Sequence[int],
@@ -334,21 +342,21 @@ def krp_core_truncate(ctx: Context, dims: Sequence[int], ell: Sequence[int], ran
 
 
 def krp_residual(ctx: Context, X, dims: Sequence[int], core_dims: Sequence[int], core,
-                 factors: Sequence):
+                 factors: Sequence, ld: Optional[Sequence[int]] = None):
     """Returns (||X - X_hat||_F^2, ||X||_F^2) as Python floats."""
     sums = (C.c_double * 2)()
     ctx.check(ctx.lib.krp_residual(ctx.handle, _ptr(X), _dtype_code(X), len(dims), _i64(dims),
-                                   _i32(core_dims), _ptr(core), _ptrs(factors), sums))
+                                   _ld(ld), _i32(core_dims), _ptr(core), _ptrs(factors), sums))
     return float(sums[0]), float(sums[1])
 
 
-def _tucker(fn, ctx, X, dims, ranks, oversample, seed, flags, core, factors):
+def _tucker(fn, ctx, X, dims, ranks, oversample, seed, flags, core, factors, ld=None):
     out = TuckerOut()
     out.core = _ptr(core)
     for i, f in enumerate(factors):
         out.factors[i] = _ptr(f)
-    ctx.check(fn(ctx.handle, _ptr(X), _dtype_code(X), len(dims), _i64(dims), _i32(ranks),
-                 oversample, seed, flags, C.byref(out)))
+    ctx.check(fn(ctx.handle, _ptr(X), _dtype_code(X), len(dims), _i64(dims), _ld(ld),
+                 _i32(ranks), oversample, seed, flags, C.byref(out)))
     t = out.times
     return {
         "core_dims": [int(out.core_dims[i]) for i in range(out.d)],
@@ -359,16 +367,18 @@ def _tucker(fn, ctx, X, dims, ranks, oversample, seed, flags, core, factors):
     }
 
 
-def krp_tucker_rhosvd(ctx: Context, X, dims, ranks, oversample, seed, flags, core, factors):
+def krp_tucker_rhosvd(ctx: Context, X, dims, ranks, oversample, seed, flags, core, factors,
+                      ld=None):
     """RHOSVD-KRP (Alg. 7); core/factors are preallocated outputs."""
     return _tucker(ctx.lib.krp_tucker_rhosvd, ctx, X, dims, ranks, oversample, seed, flags, core,
-                   factors)
+                   factors, ld)
 
 
-def krp_tucker_sthosvd(ctx: Context, X, dims, ranks, oversample, seed, flags, core, factors):
+def krp_tucker_sthosvd(ctx: Context, X, dims, ranks, oversample, seed, flags, core, factors,
+                       ld=None):
     """RSTHOSVD-KRP (Alg. 8); core/factors are preallocated outputs."""
     return _tucker(ctx.lib.krp_tucker_sthosvd, ctx, X, dims, ranks, oversample, seed, flags,
-                   core, factors)
+                   core, factors, ld)
 
 
 def krp_block_hankel_lowrank(ctx: Context, blocks, m, n, s, r, ell_r, ell_l, seed, U, S, V):

@@ -85,7 +85,7 @@ def test_constants_match_the_header(header_layout):
         if k == "KRP_ABI_VERSION":
             continue
         assert getattr(K, k) == header_layout[k], k
-    assert header_layout["KRP_ABI_VERSION"] == 1
+    assert header_layout["KRP_ABI_VERSION"] == 2
 
 
 # ---------------------------------------------------------------- prototypes --

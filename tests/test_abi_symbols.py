@@ -43,7 +43,7 @@ def test_binding_covers_every_declared_symbol():
 
 def test_abi_version_and_status_strings(lib):
     import paper_2507_23207_gb300 as K
-    assert K.krp_abi_version() == 1
+    assert K.krp_abi_version() == 2
     assert lib.krp_status_string(K.KRP_EINVAL) == b"KRP_EINVAL"
     assert lib.krp_status_string(K.KRP_ETIMEOUT) == b"KRP_ETIMEOUT"
 

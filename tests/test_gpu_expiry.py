@@ -54,11 +54,12 @@ def test_expired_wait_reports_timeout_and_context_recovers(form):
         assert e.value.status == K.KRP_ETIMEOUT, str(e.value)
         ctx.set_wait_limit(0)
         g1, q1, r1 = _run(ctx, xd, spec)
-        # the same result as before the expired call (up to the order of the
-        # FP32 atomics of the split reductions)
+        # the same result as before the expired call, up to the order of the
+        # FP32 atomics of the split reductions (within the reconstruction
+        # bound P2 of the parity tests; a damaged context gives garbage)
         nx = np.linalg.norm(x32)
-        assert np.linalg.norm(TK.reconstruct(g1, q1) - TK.reconstruct(g0, q0)) <= 1e-6 * nx
-        assert abs(r1["rel_residual"] - r0["rel_residual"]) <= 1e-4 * r0["rel_residual"]
+        assert np.linalg.norm(TK.reconstruct(g1, q1) - TK.reconstruct(g0, q0)) <= 1e-5 * nx
+        assert abs(r1["rel_residual"] - r0["rel_residual"]) <= 1e-3 * r0["rel_residual"]
         for q in q1:
             assert np.linalg.norm(q.T @ q - np.eye(q.shape[1])) <= 1e-12
     finally:

@@ -714,6 +714,10 @@ def main():
                     help="tensors in the batched workload with --batch-only")
     ap.add_argument("--hankel-only", action="store_true",
                     help="run only the 1024 x 1024 block-Hankel measurement (for profiling)")
+    ap.add_argument("--sketch-only", action="store_true",
+                    help="run only the all-mode sketch of each form (for profiling) and print it")
+    ap.add_argument("--forms", default="f32,bf16,bf16x2",
+                    help="forms of --sketch-only (comma separated)")
     ap.add_argument("--sharded", action="store_true",
                     help="split the tensor into slabs of its last mode, one per rank, with "
                          "all-reduces between the steps (strong scaling)")
@@ -764,6 +768,29 @@ def main():
                                            warm=max(1, args.warmup))}
         ctx.close()
         print(json.dumps(out))
+        return
+
+    if args.sketch_only:
+        import torch
+        import paper_2507_23207_gb300 as K
+        dev = torch.device(f"cuda:{local_rank}")
+        torch.cuda.set_device(dev)
+        stream = torch.cuda.current_stream(dev)
+        spec = workload(args)
+        want = set(args.forms.split(","))
+        x32, xbf = make_inputs(spec, dev, want_bf16="bf16" in want)
+        ctx = K.Context(local_rank, stream.cuda_stream)
+        forms = []
+        if "f32" in want:
+            forms.append(("f32", x32))
+        if "bf16" in want:
+            forms.append(("bf16", xbf))
+        if "bf16x2" in want:
+            forms.append(("bf16x2", K.krp_split_bf16x2(ctx, x32)))
+        peaks, _ = measured_peaks()
+        out = sketch_rooflines(ctx, spec, forms, dev, stream, peaks, None, args)
+        ctx.close()
+        print(json.dumps({"sketch": out}))
         return
 
     if args.batch_only:

@@ -180,6 +180,10 @@ krp_status krp_destroy(krp_ctx ctx) {
     KRP_CUDA_CHECK(cudaStreamSynchronize(ctx->c.stream));
     for (cudaEvent_t e : ctx->c.trace_pool) cudaEventDestroy(e);
     ctx->c.trace_pool.clear();
+    for (cudaEvent_t e : ctx->c.copy_events) cudaEventDestroy(e);
+    ctx->c.copy_events.clear();
+    if (ctx->c.copy_stream) cudaStreamDestroy(ctx->c.copy_stream);
+    ctx->c.copy_stream = nullptr;
     if (ctx->c.batch_plan) ctx->c.batch_plan_free(ctx->c.batch_plan);
     ctx->c.batch_plan = nullptr;
     if (ctx->c.hankel_plan) ctx->c.hankel_plan_free(ctx->c.hankel_plan);

@@ -75,6 +75,9 @@ struct Ctx {
   void (*batch_plan_free)(void*) = nullptr;
   void* hankel_plan = nullptr;             // cached batched block-Hankel plan
   void (*hankel_plan_free)(void*) = nullptr;
+  // host-to-device copies overlapped with the sketch (created on first use)
+  cudaStream_t copy_stream = nullptr;
+  std::vector<cudaEvent_t> copy_events;
   // tree splits picked by timing, per (dims, l, dtype)
   std::map<std::vector<int64_t>, int> tree_split_cache;
   // launch trace (krp_trace_begin/end): an event after every launch

@@ -60,6 +60,12 @@ __global__ void split_x2_kernel(const float* __restrict__ X, int64_t n, __nv_bfl
   }
 }
 
+__global__ void add_f32_kernel(float* __restrict__ dst, const float* __restrict__ src, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    dst[i] += src[i];
+}
+
 __global__ void bf16_to_f32_kernel(const __nv_bfloat16* __restrict__ s, float* __restrict__ d,
                                    int64_t n) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
@@ -471,6 +477,70 @@ void sketch_all_modes(const SketchArgs& a, float* const* Y, int tree_split) {
   for (int n = 1; n < a.d; ++n) diag_contract_f32(B, a.d - 1, a.dims + 1, S, n - 1, f32v + 1, a.ell, Y[n]);
 }
 
+// All mode sketches of a tensor that is still on the host: X is copied to
+// the device buffer a.X in chunks of its last mode on a second stream, and
+// each chunk is sketched on the context's stream as soon as it has landed
+// (the sketches of the modes before the last are sums over the chunks, the
+// last mode's sketch is the chunks' rows; the same decomposition as the
+// sharded path's).  The copy of X and the sketch overlap.
+static void sketch_host_overlapped(const SketchArgs& a, const void* host, float* const* Y) {
+  Ctx* c = current();
+  Workspace& ws = c->ws;
+  const int d = a.d;
+  const int64_t nd = a.dims[d - 1];
+  const int64_t slab = a.N / nd;  // elements per index of the last mode
+  const size_t eb = dtype_size(a.xt), fb = dtype_size(a.omt);
+  const int K = static_cast<int>(std::min<int64_t>(8, nd));
+  if (!c->copy_stream)
+    KRP_CUDA_CHECK(cudaStreamCreateWithFlags(&c->copy_stream, cudaStreamNonBlocking));
+  while (static_cast<int>(c->copy_events.size()) < K + 1) {
+    cudaEvent_t e;
+    KRP_CUDA_CHECK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    c->copy_events.push_back(e);
+  }
+  // the copies overwrite workspace that earlier work on the context's
+  // stream may still read
+  KRP_CUDA_CHECK(cudaEventRecord(c->copy_events[K], c->stream));
+  KRP_CUDA_CHECK(cudaStreamWaitEvent(c->copy_stream, c->copy_events[K], 0));
+  char* dev = static_cast<char*>(const_cast<void*>(a.X));
+  for (int k = 0; k < K; ++k) {
+    const int64_t t0 = nd * k / K, t1 = nd * (k + 1) / K;
+    KRP_CUDA_CHECK(cudaMemcpyAsync(dev + t0 * slab * eb, static_cast<const char*>(host) + t0 * slab * eb,
+                                   (t1 - t0) * slab * eb, cudaMemcpyHostToDevice, c->copy_stream));
+    KRP_CUDA_CHECK(cudaEventRecord(c->copy_events[k], c->copy_stream));
+  }
+  const int64_t cmax = (nd + K - 1) / K;
+  float* Yt[KRP_MAXD];
+  for (int n = 0; n < d - 1; ++n) {
+    Yt[n] = ws.take<float>((size_t)a.dims[n] * a.ell);
+    KRP_CUDA_CHECK(cudaMemsetAsync(Y[n], 0, sizeof(float) * a.dims[n] * a.ell, c->stream));
+  }
+  Yt[d - 1] = ws.take<float>((size_t)cmax * a.ell);
+  void* omc = ws.take<char>((size_t)cmax * a.ell * fb);
+  for (int k = 0; k < K; ++k) {
+    const int64_t t0 = nd * k / K, t1 = nd * (k + 1) / K, m = t1 - t0;
+    KRP_CUDA_CHECK(cudaStreamWaitEvent(c->stream, c->copy_events[k], 0));
+    const size_t mark = ws.off;
+    SketchArgs ac = a;
+    ac.X = dev + t0 * slab * eb;
+    ac.dims[d - 1] = m;
+    ac.N = slab * m;
+    // rows t0..t1-1 of the last factor (column-major, leading size nd)
+    KRP_CUDA_CHECK(cudaMemcpy2DAsync(omc, m * fb, static_cast<const char*>(a.omega[d - 1]) + t0 * fb,
+                                     nd * fb, m * fb, a.ell, cudaMemcpyDeviceToDevice, c->stream));
+    ac.omega[d - 1] = omc;
+    sketch_all_modes(ac, Yt);
+    for (int n = 0; n < d - 1; ++n) {
+      const int64_t cnt = a.dims[n] * a.ell;
+      add_f32_kernel<<<grid_of(cnt), 256, 0, stream()>>>(Y[n], Yt[n], cnt);
+      check_launch("add_f32");
+    }
+    KRP_CUDA_CHECK(cudaMemcpy2DAsync(Y[d - 1] + t0, nd * sizeof(float), Yt[d - 1], m * sizeof(float),
+                                     m * sizeof(float), a.ell, cudaMemcpyDeviceToDevice, c->stream));
+    ws.off = mark;
+  }
+}
+
 // ----------------------------------------------------------- multi-TTM -----
 size_t multi_ttm_workspace_bytes(int d, const int64_t* dims, const int* cols, krp_dtype xt) {
   const int64_t N = checked_numel(d, dims);
@@ -681,7 +751,18 @@ void tucker_pipeline(bool sequential, const void* X, krp_dtype xt, int d, const 
     need += mttkrp_first_f32_workspace_bytes(maxS, dmax);  // FP32 slab-MTTKRP operands
   }
   const bool x_pad = padded(d, dims, ld);
-  if (!x_dev) need += ws_bytes((size_t)(x_pad ? padded_numel(d, ld) : N), xb);
+  if (!x_dev) {
+    need += ws_bytes((size_t)(x_pad ? padded_numel(d, ld) : N), xb);
+    // chunked copy: the chunk sketches' temporaries (at most the whole
+    // tensor's) and, for BF16, the tree of a chunk's shape
+    for (int i = 0; i < d; ++i) need += ws_bytes((size_t)dims[i] * ellmax, 4 + 4);
+    if (xt == KRP_BF16) {
+      int64_t cd[KRP_MAXD];
+      for (int i = 0; i < d; ++i) cd[i] = dims[i];
+      cd[d - 1] = (dims[d - 1] + 7) / 8;
+      need += tree_ws_bytes(d, cd, ellmax);
+    }
+  }
   if (x_pad) need += ws_bytes((size_t)N, xb);
   int64_t core_l = 1;
   for (int i = 0; i < d; ++i) {
@@ -705,12 +786,17 @@ void tucker_pipeline(bool sequential, const void* X, krp_dtype xt, int d, const 
   tm.start(flags & KRP_TIMINGS);  // event 0
   KRP_CUDA_CHECK(cudaMemsetAsync(c->d_status, 0, sizeof(int), c->stream));
 
+  // a dense host X of the memoized RHOSVD (FP32 or BF16) is copied in chunks
+  // of the last mode, overlapped with the sketch; other host inputs are
+  // copied whole first
+  const bool overlap = !x_dev && !x_pad && memo && (xt == KRP_F32 || xt == KRP_BF16) &&
+                       dims[d - 1] >= 2;
   const void* Xd = X;
   if (!x_dev) {
     // host X (padded or not) is staged as given, then packed on the device
     const size_t hb = (size_t)(x_pad ? padded_numel(d, ld) : N) * xb;
     void* p = ws.take<char>(hb);
-    KRP_CUDA_CHECK(cudaMemcpyAsync(p, X, hb, cudaMemcpyHostToDevice, c->stream));
+    if (!overlap) KRP_CUDA_CHECK(cudaMemcpyAsync(p, X, hb, cudaMemcpyHostToDevice, c->stream));
     Xd = p;
   }
   Xd = dense_copy(Xd, xt, d, dims, ld);
@@ -762,7 +848,10 @@ void tucker_pipeline(bool sequential, const void* X, krp_dtype xt, int d, const 
       SketchArgs a{};
       a.X = Xd; a.xt = xt; a.d = d; a.omt = ft; a.ell = ellmax; a.N = N;
       for (int j = 0; j < d; ++j) { a.dims[j] = dims[j]; a.omega[j] = fac[0][j]; }
-      sketch_all_modes(a, Y);
+      if (overlap)
+        sketch_host_overlapped(a, X, Y);
+      else
+        sketch_all_modes(a, Y);
     } else {
       for (int i = 0; i < d; ++i) {
         SketchArgs a{};

@@ -201,3 +201,30 @@ def test_zero_tensor(ctx, memo):
             assert np.linalg.norm(q.T @ q - np.eye(o)) <= 1e-12
         assert float(core.abs().max()) == 0.0
         assert res["rel_residual"] == 0.0 and res["x_norm"] == 0.0
+
+
+def test_host_bf16_input_matches_device_input(ctx):
+    """A BF16 tensor in host memory: the library copies it in chunks of the
+    last mode on a second stream while it sketches the chunks already on the
+    device; the result is the one of the same call on a device copy."""
+    import torch
+    import paper_2507_23207_gb300 as K
+    spec = TuckerSpec("hostbf", (40, 33, 27), (4, 3, 5), 1e-3, None, 63, (4, 3, 5), (8, 7, 9))
+    x, _, _ = tucker_tensor(spec)
+    xb = philox.round_to_bf16(x)
+    from synth import to_torch_layout
+    xh = to_torch_layout(np.asfortranarray(xb)).to(torch.bfloat16)
+    flags = K.KRP_MEMO | K.KRP_TRUNCATE | K.KRP_RESIDUAL
+    outs = []
+    for xx in (xh.pin_memory(), xh.to(dev())):
+        ranks = list(spec.ranks)
+        core = torch.empty(int(np.prod(ranks)), dtype=torch.float32, device=dev())
+        facs = [torch.empty(n * r, dtype=torch.float64, device=dev()) for n, r in zip(spec.dims, ranks)]
+        res = K.krp_tucker_rhosvd(ctx, xx, spec.dims, ranks, spec.oversample, 0, flags, core, facs)
+        torch.cuda.synchronize()
+        g = core.cpu().numpy().reshape(ranks[::-1]).T.astype(np.float64)
+        qs = [f.cpu().numpy().reshape(r, n).T for f, n, r in zip(facs, spec.dims, ranks)]
+        outs.append((TK.reconstruct(g, qs), res["rel_residual"]))
+    nx = np.linalg.norm(xb)
+    assert np.linalg.norm(outs[0][0] - outs[1][0]) <= 1e-5 * nx
+    assert abs(outs[0][1] - outs[1][1]) <= 1e-3 * outs[1][1]

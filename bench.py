@@ -413,6 +413,19 @@ def c4_run(ctx, dev, stream, args, reps=10, warm=3):
         out[form] = {"ms": round(ms, 4),
                      "sigma_max_abs_diff_over_sigma1": float(np.max(np.abs(sg - so)) / so[0]),
                      "oracle_rel_error_vs_input": gold[f"rel_error_vs_input_{form}"]}
+        # eigensystem realization from the rank-r factors (Sec. 4.2), and the
+        # distance of its eigenvalues to the system's (known by construction)
+        er = torch.empty(r, dtype=torch.float64, device=dev)
+        ei = torch.empty(r, dtype=torch.float64, device=dev)
+        ms_era, _ = _timed(stream, lambda: K.krp_era_realize(
+            ctx, bl, spec.m, spec.n, spec.s, r, U, S, V, er, ei), reps=reps, warm=warm)
+        from synth.hankel import system_matrices
+        eig_true = system_matrices(spec)[3]
+        eg = er.cpu().numpy() + 1j * ei.cpu().numpy()
+        dist = np.abs(eg[:, None] - eig_true[None, :])
+        out[form]["era"] = {"ms": round(ms_era, 4),
+                            "hausdorff_to_system_eigenvalues": float(max(dist.min(1).max(),
+                                                                         dist.min(0).max()))}
     return out
 
 

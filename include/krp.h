@@ -371,6 +371,32 @@ krp_status krp_block_hankel_sketch(krp_ctx ctx, const void* blocks,
                                    const void* psi2, int ell_l, float* Y,
                                    float* Z);
 
+/* Eigensystem realization from the rank-r result of krp_block_hankel_lowrank
+ * (the use Sec. 4.2 makes of Alg. 6): with M ~ U S V^T, O = U S^{1/2} and
+ * G^+ = V S^{-1/2}, the state matrix is
+ *   A = O_top^+ H_up G^+,
+ * O_top the first (s-1) m rows of O and H_up the block Hankel matrix shifted
+ * by one block (block (i, j) = h_{i+j}, i = 1..s-1, j = 1..s, 1-based, i.e.
+ * blocks 2..2s-1).  A is determined up to a similarity transform; its
+ * eigenvalues are the realized system's.  The least-squares step uses the
+ * normal equations with a Cholesky factor in FP64 (O_top's condition number
+ * is that of S^{1/2} on the orthonormal rows of U, small for a decaying
+ * Hankel spectrum), the eigenvalues Householder reduction to Hessenberg form
+ * and the Francis double-shift QR iteration in FP64 (Golub & Van Loan).
+ *   blocks: 2s-1 column-major m x n blocks as for krp_block_hankel_lowrank
+ *           (KRP_F32 or KRP_BF16); U (m s x r), S (r), V (n s x r): FP64
+ *   A:      r x r FP64 column-major (may be NULL)
+ *   eig_re, eig_im: r FP64 each, the eigenvalues in deflation order (complex
+ *           pairs adjacent, positive imaginary part first)
+ * All pointers are device pointers.  Needs s >= 2 and 1 <= r <= min(64,
+ * (s-1) m, s n).  Synchronises the stream.  Errors: KRP_EINVAL, KRP_ENOMEM,
+ * KRP_ECUDA, KRP_ENUMERIC (O_top rank-deficient, a non-finite value, or an
+ * eigenvalue that did not converge in 100 iterations). */
+krp_status krp_era_realize(krp_ctx ctx, const void* blocks, krp_dtype bt, int m,
+                           int n, int s, int r, const double* U, const double* S,
+                           const double* V, double* A, double* eig_re,
+                           double* eig_im);
+
 /* ---- a11: batches of small uneven 3-way tensors -------------------------- */
 
 /* One tensor of a batch (all device pointers). */

@@ -442,6 +442,27 @@ krp_status krp_tucker_rhosvd_batched(krp_ctx ctx, krp_dtype xt, int count, krp_t
   return guarded(ctx, [&] { tucker_batched(xt, count, items, oversample, flags); });
 }
 
+krp_status krp_era_realize(krp_ctx ctx, const void* blocks, krp_dtype bt, int m, int n, int s,
+                           int r, const double* U, const double* S, const double* V, double* A,
+                           double* eig_re, double* eig_im) {
+  return guarded(ctx, [&] {
+    KRP_REQUIRE(blocks && U && S && V && eig_re && eig_im, "NULL argument");
+    KRP_REQUIRE(bt == KRP_F32 || bt == KRP_BF16, "blocks must be KRP_F32 or KRP_BF16");
+    KRP_REQUIRE(m >= 1 && n >= 1 && s >= 2, "need m, n >= 1 and s >= 2");
+    KRP_REQUIRE(r >= 1 && r <= 64 && r <= (int64_t)(s - 1) * m && r <= (int64_t)s * n,
+                "need 1 <= r <= min(64, (s-1) m, s n)");
+    for (const void* p : {blocks, (const void*)U, (const void*)S, (const void*)V, (const void*)eig_re,
+                          (const void*)eig_im})
+      KRP_REQUIRE(is_device_ptr(p), "all buffers must be device memory");
+    KRP_REQUIRE(!A || is_device_ptr(A), "A must be device memory");
+    Ctx* c = current();
+    ensure_workspace(c, era_workspace_bytes(m, s, r));
+    KRP_CUDA_CHECK(cudaMemsetAsync(c->d_status, 0, sizeof(int), c->stream));
+    era_realize(blocks, bt, m, n, s, r, U, S, V, A, eig_re, eig_im);
+    raise_device_status(c);
+  });
+}
+
 krp_status krp_block_hankel_batched(krp_ctx ctx, krp_dtype bt, int count, krp_hankel_item* items) {
   return guarded(ctx, [&] { hankel_batched(bt, count, items); });
 }

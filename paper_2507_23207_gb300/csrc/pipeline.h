@@ -63,6 +63,12 @@ void hankel_batched(krp_dtype bt, int count, krp_hankel_item* items);
 
 void hankel_pipeline(const void* blocks, krp_dtype bt, int m, int n, int s, int r, int ell_r,
                      int ell_l, uint64_t seed, double* U, double* S, double* V);
+// Eigensystem realization (era.cu): A (r x r, nullable) and its eigenvalues
+// (wr, wi) from the blocks and the rank-r factors U (m s x r), S, V (n s x r),
+// all device memory, FP64; r <= 64.
+void era_realize(const void* blocks, krp_dtype bt, int m, int n, int s, int r, const double* U,
+                 const double* S, const double* V, double* A, double* wr, double* wi);
+size_t era_workspace_bytes(int m, int s, int r);
 void hankel_sketch_only(const void* blocks, krp_dtype bt, int m, int n, int s,
                         const void* omega1, const void* omega2, int ell_r, const void* psi1,
                         const void* psi2, int ell_l, float* Y, float* Z);

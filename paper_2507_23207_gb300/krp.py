@@ -33,7 +33,7 @@ EXPORTED = [
     "krp_tucker_rhosvd", "krp_tucker_sthosvd", "krp_block_hankel_lowrank",
     "krp_block_hankel_sketch", "krp_tucker_rhosvd_batched", "krp_tucker_batch_plan_info",
     "krp_block_hankel_batched", "krp_split_bf16x2", "krp_trace_begin", "krp_trace_end",
-    "krp_core_truncate", "krp_residual", "krp_set_wait_limit",
+    "krp_core_truncate", "krp_residual", "krp_set_wait_limit", "krp_era_realize",
 ]
 
 
@@ -102,6 +102,8 @@ def load_library(path: Optional[str] = None):
         "krp_destroy": (C.c_int, [vp]),
         "krp_set_stream": (C.c_int, [vp, vp]),
         "krp_set_wait_limit": (C.c_int, [vp, C.c_uint64]),
+        "krp_era_realize": (C.c_int, [vp, vp, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, vp,
+                                      vp, vp, vp, vp, vp]),
         "krp_last_error": (C.c_char_p, [vp]),
         "krp_status_string": (C.c_char_p, [C.c_int]),
         "krp_abi_version": (C.c_int, []),
@@ -385,6 +387,13 @@ def krp_block_hankel_lowrank(ctx: Context, blocks, m, n, s, r, ell_r, ell_l, see
     ctx.check(ctx.lib.krp_block_hankel_lowrank(ctx.handle, _ptr(blocks), _dtype_code(blocks), m,
                                                n, s, r, ell_r, ell_l, seed, _ptr(U), _ptr(S),
                                                _ptr(V)))
+
+
+def krp_era_realize(ctx: Context, blocks, m, n, s, r, U, S, V, eig_re, eig_im, A=None):
+    """Eigensystem realization from krp_block_hankel_lowrank's U, S, V (device)."""
+    ctx.check(ctx.lib.krp_era_realize(ctx.handle, _ptr(blocks), _dtype_code(blocks), m, n, s, r,
+                                      _ptr(U), _ptr(S), _ptr(V), _ptr(A), _ptr(eig_re),
+                                      _ptr(eig_im)))
 
 
 def krp_block_hankel_sketch(ctx: Context, blocks, m, n, s, omega1, omega2, ell_r, psi1, psi2,

@@ -919,8 +919,12 @@ __global__ void batch_gram_kernel(const TbItem* __restrict__ items) {
 }
 
 // Truncated core and factors (one CTA per tensor): G' = G x_1 U1^T x_2 U2^T
-// x_3 U3^T in FP64 through two global scratch tensors, Q_i U_i; without
-// truncation the core and factors are copied out.
+// x_3 U3^T through two global scratch tensors, Q_i U_i; without truncation
+// the core and factors are copied out.  The core is stored in FP32, so its
+// three contractions run in FP32 (U_i rounded to FP32: relative 2^-24 per
+// entry, ~1e-7 on the core, against the 1e-5 bounds of the reconstruction);
+// GB300 issues FP64 at 1/64 of the FP32 rate, and these products were two
+// thirds of the kernel's FP64 work.  The factors Q_i U_i stay FP64.
 __global__ void batch_trunc_apply_kernel(const TbItem* __restrict__ items, int trunc) {
   const TbItem& it = items[blockIdx.x];
   const int l0 = it.l[0], l1 = it.l[1], l2 = it.l[2];
@@ -932,27 +936,29 @@ __global__ void batch_trunc_apply_kernel(const TbItem* __restrict__ items, int t
       for (int e = tid; e < it.n[m] * it.l[m]; e += nt) it.fac_out[m][e] = it.Q[m][e];
     return;
   }
+  float* T1 = reinterpret_cast<float*>(it.T1);  // FP32 views of the FP64 scratch
+  float* T2 = reinterpret_cast<float*>(it.T2);
   // T1[a', x1, x2] = sum_a U0[a, a'] G[a, x1, x2]
   for (int e = tid; e < r0 * l1 * l2; e += nt) {
     const int ap = e % r0, rest = e / r0;
-    double s = 0.0;
-    for (int a = 0; a < l0; ++a) s = fma(it.U[0][a + l0 * ap], (double)it.G[a + l0 * rest], s);
-    it.T1[e] = s;
+    float s = 0.f;
+    for (int a = 0; a < l0; ++a) s = fmaf((float)it.U[0][a + l0 * ap], it.G[a + l0 * rest], s);
+    T1[e] = s;
   }
   __syncthreads();
   // T2[a', b', x2] = sum_b U1[b, b'] T1[a', b, x2]
   for (int e = tid; e < r0 * r1 * l2; e += nt) {
     const int ap = e % r0, bp = (e / r0) % r1, c = e / (r0 * r1);
-    double s = 0.0;
-    for (int b = 0; b < l1; ++b) s = fma(it.U[1][b + l1 * bp], it.T1[ap + r0 * (b + l1 * c)], s);
-    it.T2[e] = s;
+    float s = 0.f;
+    for (int b = 0; b < l1; ++b) s = fmaf((float)it.U[1][b + l1 * bp], T1[ap + r0 * (b + l1 * c)], s);
+    T2[e] = s;
   }
   __syncthreads();
   for (int e = tid; e < r0 * r1 * r2; e += nt) {
     const int ab = e % (r0 * r1), cp = e / (r0 * r1);
-    double s = 0.0;
-    for (int c = 0; c < l2; ++c) s = fma(it.U[2][c + l2 * cp], it.T2[ab + r0 * r1 * c], s);
-    it.core_out[e] = (float)s;
+    float s = 0.f;
+    for (int c = 0; c < l2; ++c) s = fmaf((float)it.U[2][c + l2 * cp], T2[ab + r0 * r1 * c], s);
+    it.core_out[e] = s;
   }
   for (int m = 0; m < 3; ++m) {
     const int n = it.n[m], l = it.l[m], r = it.r[m];

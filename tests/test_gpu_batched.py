@@ -95,6 +95,39 @@ def test_batched_matches_oracle(ctx, form, trunc):
     _check(hosts, ranks, seeds, cores, facs, rels, trunc, form, 1e-5)
 
 
+# sides at the limit (256: one 32-column panel of pitch 264 per copy in the
+# staged BF16 sketch), odd sides, and several panels per slab
+EDGE_SHAPES = [((256, 20, 9), (4, 3, 2)), ((7, 256, 6), (2, 6, 2)), ((33, 65, 7), (3, 3, 2)),
+               ((200, 190, 6), (5, 5, 2)), ((9, 250, 11), (3, 7, 4))]
+
+
+@pytest.mark.parametrize("aligned", [True, False])
+def test_batched_bf16_edge_shapes(ctx, aligned):
+    """BF16 batch at the side limit and with odd sides; aligned=False packs all
+    tensors into one buffer at odd element offsets, so no tensor starts or ends
+    on a 16-byte boundary (the staged sketch copies the aligned interior of
+    each panel and reads the ends with plain loads)."""
+    import torch
+    import paper_2507_23207_gb300 as K
+    xs, hosts, dims, ranks, seeds, cores, facs = _batch(torch.bfloat16, True, EDGE_SHAPES, 700)
+    if not aligned:
+        sizes = [x.numel() for x in xs]
+        buf = torch.empty(sum(sizes) + 3 * len(xs) + 1, dtype=torch.bfloat16, device=dev())
+        views, off = [], 1
+        for x, n in zip(xs, sizes):
+            v = buf[off:off + n]
+            v.copy_(x.reshape(-1))
+            views.append(v)
+            assert (v.data_ptr() % 16) != 0
+            off += n + 2
+            off += 1 if off % 8 == 0 else 0
+        xs = views
+    items = K.make_tucker_items(xs, dims, ranks, seeds, cores, facs)
+    rels = K.krp_tucker_rhosvd_batched(ctx, K.KRP_BF16, items, P, K.KRP_TRUNCATE | K.KRP_RESIDUAL)
+    torch.cuda.synchronize()
+    _check(hosts, ranks, seeds, cores, facs, rels, True, "bf16", 1e-5)
+
+
 def test_batched_graph_replay_and_rebuild(ctx):
     import torch
     import paper_2507_23207_gb300 as K

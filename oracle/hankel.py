@@ -18,7 +18,7 @@ from __future__ import annotations
 import numpy as np
 
 from . import philox
-from .linalg import householder_qr, jacobi_svd, lstsq_qr
+from .linalg import householder_qr, jacobi_eig, jacobi_svd, lstsq_qr
 from .tensor import khatri_rao
 
 
@@ -105,6 +105,51 @@ def single_pass_svd(blocks: np.ndarray, r: int, ell_r: int, ell_l: int, seed: in
     u = q @ uw
     return {"U": u[:, :r], "S": sig[:r], "V": vt[:r].T, "Y": y, "Z": z, "Q": q,
             "W": w, "factors": (o1, o2, p1, p2), "H": h}
+
+
+# Reading of the pseudoinverse in the Nystrom approximation: eigenvalues of
+# Omega^T M Omega at or below NYS_RCOND times the largest are treated as zero.
+NYS_RCOND = 1e-6
+
+
+def nystrom(blocks: np.ndarray, r: int, ell: int, seed: int, rcond: float = NYS_RCOND,
+            omega_round=None):
+    """Nystrom approximation of a symmetric positive semidefinite block Hankel
+    matrix M (Sec. 4.1, the remark after Alg. 6):
+
+        M_nys = (M Omega) (Omega^T M Omega)^+ (M Omega)^T,  Omega = Omega^(1) kr Omega^(2),
+
+    with Omega the column-sketch factors of Alg. 6 (s x l and m x l, tag 0,
+    draw 0).  Steps, on the explicit matrices:
+    1. Y = M Omega
+    2. C = Omega^T Y (symmetrised), C = V diag(c) V^T (two-sided Jacobi)
+    3. the pseudoinverse keeps c_i > rcond * c_1: M_nys = F F^T with
+       F = Y V_k diag(c_k^{-1/2})
+    4. F = U Sigma W^T (one-sided Jacobi SVD), so M_nys = U Sigma^2 U^T
+    Returns U[:, :r] and Lambda = Sigma[:r]^2 (zero-padded when fewer than r
+    eigenvalues are kept), with M_nys, Y, C and the kept count for tests.
+    """
+    m, n, nb = blocks.shape
+    if m != n:
+        raise ValueError("the Nystrom approximation needs square blocks")
+    s = (nb + 1) // 2
+    o1, o2, _, _ = sketch_factors(seed, s, m, n, ell, 1, omega_round)
+    h = block_hankel(blocks)
+    omega = khatri_rao(o1, o2)
+    y = h @ omega
+    c = omega.T @ y
+    c = 0.5 * (c + c.T)
+    cv, vv = jacobi_eig(c)
+    keep = cv > rcond * cv[0] if cv[0] > 0.0 else np.zeros(ell, dtype=bool)
+    f = (y @ vv[:, keep]) / np.sqrt(cv[keep])
+    u = np.zeros((m * s, r))
+    lam = np.zeros(r)
+    k = int(keep.sum())
+    if k:
+        uf, sig, _ = jacobi_svd(f)
+        u[:, :min(r, k)] = uf[:, :r]
+        lam[:min(r, k)] = sig[:r] ** 2
+    return {"U": u, "L": lam, "M": f @ f.T, "Y": y, "C": c, "kept": k, "H": h}
 
 
 def era_realization(blocks: np.ndarray, u: np.ndarray, sig: np.ndarray,

@@ -1,4 +1,5 @@
-"""Dense FP64 kernels of the oracle: Householder thin QR, one-sided Jacobi SVD, LS.
+"""Dense FP64 kernels of the oracle: Householder thin QR, one-sided Jacobi SVD,
+two-sided Jacobi eigen-decomposition, LS.
 
 The thin QR Y = QR is the orthonormalisation step of the randomized range
 finder (Alg. 1) and of every sketch in Alg. 6, 7 and 8.  It is written out as
@@ -103,6 +104,49 @@ def jacobi_svd(a: np.ndarray, tol: float = 1e-15, max_sweeps: int = 60):
         if sig[k] > 0:
             u[:, k] = w[:, k] / sig[k]
     return u, sig, v.T
+
+
+def jacobi_eig(a: np.ndarray, tol: float = 1e-15, max_sweeps: int = 60):
+    """Eigen-decomposition of a symmetric matrix by the cyclic two-sided
+    (classical) Jacobi method.
+
+    Each rotation J in the plane (p, q) is chosen so that (J^T A J)_pq = 0:
+    theta = (a_qq - a_pp) / (2 a_pq), t = sign(theta) / (|theta| +
+    sqrt(1 + theta^2)) (t = 1 when theta = 0), c = 1 / sqrt(1 + t^2), s = t c;
+    columns p, q and then rows p, q of A are rotated, and V accumulates the
+    columns.  Sweeps stop when the off-diagonal Frobenius norm is at most
+    ``tol`` times that of A.  Returns the eigenvalues in descending order
+    (negative ones included) and V with the eigenvectors as columns.
+    """
+    a = np.array(a, dtype=np.float64, copy=True)
+    a = 0.5 * (a + a.T)
+    n = a.shape[0]
+    v = np.eye(n)
+    scale = np.linalg.norm(a)
+    for _ in range(max_sweeps):
+        off = np.linalg.norm(a - np.diag(np.diag(a)))
+        if off <= tol * scale:
+            break
+        for p in range(n - 1):
+            for q in range(p + 1, n):
+                if a[p, q] == 0.0:
+                    continue
+                theta = (a[q, q] - a[p, p]) / (2.0 * a[p, q])
+                t = 1.0 if theta == 0.0 else np.sign(theta) / (abs(theta) + np.sqrt(1.0 + theta * theta))
+                c = 1.0 / np.sqrt(1.0 + t * t)
+                s = t * c
+                ap = a[:, p].copy()
+                a[:, p] = c * ap - s * a[:, q]
+                a[:, q] = s * ap + c * a[:, q]
+                ap = a[p, :].copy()
+                a[p, :] = c * ap - s * a[q, :]
+                a[q, :] = s * ap + c * a[q, :]
+                vp = v[:, p].copy()
+                v[:, p] = c * vp - s * v[:, q]
+                v[:, q] = s * vp + c * v[:, q]
+    w = np.diag(a).copy()
+    order = np.argsort(-w, kind="stable")
+    return w[order], v[:, order]
 
 
 def fix_signs(u: np.ndarray, vt: np.ndarray = None):

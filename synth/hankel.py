@@ -88,3 +88,25 @@ def markov_parameters(spec: HankelSpec) -> np.ndarray:
         out[:, :, k] = cmat @ akb
         akb = a @ akb
     return out
+
+
+def symmetric_markov_parameters(spec: HankelSpec) -> np.ndarray:
+    """Blocks H_k = B^T A^(k-1) B of a symmetric system (A = A^T, C = B^T,
+    m = n), k = 1..2s-1, Fortran array (m, m, 2s-1).  Block (i, j) of the
+    block Hankel matrix is then (A^(i-1) B)^T (A^(j-1) B), so the matrix is
+    K^T K with K = [B, A B, ..., A^(s-1) B]: symmetric positive semidefinite
+    of rank <= order.  A = V diag(lambda) V^T with V Haar orthogonal and
+    |lambda| uniform in [0.5, radius], random signs; B standard Gaussian."""
+    if spec.m != spec.n:
+        raise ValueError("a symmetric system needs m = n")
+    rng = np.random.default_rng(spec.data_seed)
+    lam = rng.uniform(0.5, spec.radius, spec.order) * rng.choice([-1.0, 1.0], spec.order)
+    v = haar(spec.order, spec.order, rng)
+    a = (v * lam) @ v.T
+    b = rng.standard_normal((spec.order, spec.m))
+    out = np.zeros((spec.m, spec.m, spec.nblocks), order="F")
+    akb = b.copy()
+    for k in range(spec.nblocks):
+        out[:, :, k] = b.T @ akb
+        akb = a @ akb
+    return out

@@ -127,3 +127,86 @@ def test_rng_counts_against_printed_shares():
     # the oracle's actual draws have exactly that many entries
     o1, o2, p1, p2 = HK.sketch_factors(0, s, m, n, 3, 4)
     assert o1.size + o2.size + p1.size + p2.size == HK.rng_count_block(m, n, s, s, 3, 4)
+
+
+# ---- Nystrom approximation (the remark after Alg. 6) and its eigensolver ----
+
+@pytest.mark.parametrize("n", [1, 2, 7, 20])
+def test_jacobi_eig_matches_lapack(n):
+    """Two-sided Jacobi against LAPACK's symmetric eigensolver, on an
+    indefinite matrix: eigenvalues, A V = V diag(w), V orthogonal."""
+    from oracle import linalg as LA
+    rng = np.random.default_rng(40 + n)
+    a = rng.standard_normal((n, n))
+    a = a + a.T
+    w, v = LA.jacobi_eig(a)
+    scale = np.linalg.norm(a)
+    assert np.all(np.diff(w) <= 0)
+    assert np.allclose(w, np.sort(np.linalg.eigvalsh(a))[::-1], atol=1e-12 * scale)
+    assert np.linalg.norm(a @ v - v * w) <= 1e-12 * scale
+    assert np.linalg.norm(v.T @ v - np.eye(n)) <= 1e-12
+
+
+def _spsd_spec(order, m, s, seed=11):
+    return HankelSpec("nys", order, m, m, s, 0.9, seed, r=order, ell_r=order, ell_l=order)
+
+
+def test_symmetric_system_is_spsd():
+    """The generator's block Hankel matrix is symmetric PSD of rank <= order."""
+    from synth import symmetric_markov_parameters
+    h = HK.block_hankel(symmetric_markov_parameters(_spsd_spec(6, 3, 10)))
+    assert np.linalg.norm(h - h.T) <= 1e-13 * np.linalg.norm(h)
+    w = np.linalg.eigvalsh(h)
+    assert w.min() >= -1e-12 * w.max()
+    assert np.sum(w > 1e-10 * w.max()) <= 6
+
+
+@pytest.mark.parametrize("order,m,s,ell", [(6, 3, 10, 10), (4, 2, 9, 4)])
+def test_nystrom_exact_for_low_rank(order, m, s, ell):
+    """rank(M) <= l: the column space of M Omega is that of M, and M_nys = M;
+    its eigenpairs are M's (LAPACK), U orthonormal."""
+    from synth import symmetric_markov_parameters
+    blocks = symmetric_markov_parameters(_spsd_spec(order, m, s))
+    out = HK.nystrom(blocks, order, ell, seed=3)
+    h = out["H"]
+    assert out["kept"] == order
+    assert np.linalg.norm(out["M"] - h) <= 1e-9 * np.linalg.norm(h)
+    w = np.sort(np.linalg.eigvalsh(h))[::-1][:order]
+    assert np.allclose(out["L"], w, rtol=0, atol=1e-9 * w[0])
+    u = out["U"]
+    assert np.linalg.norm(u.T @ u - np.eye(order)) <= 1e-10
+    assert np.linalg.norm(u * out["L"] @ u.T - h) <= 1e-9 * np.linalg.norm(h)
+
+
+def test_nystrom_below_m_and_eckart_young():
+    """l < rank(M): M - M_nys is PSD (M_nys = M^{1/2} P M^{1/2} with P an
+    orthogonal projector), M_nys is PSD of rank <= l, and its error is at
+    least the best rank-l error sqrt(sum_{i > l} lambda_i^2)."""
+    from synth import symmetric_markov_parameters
+    blocks = symmetric_markov_parameters(_spsd_spec(12, 4, 16))
+    ell = 7
+    out = HK.nystrom(blocks, 5, ell, seed=9)
+    h, mn = out["H"], out["M"]
+    nh = np.linalg.norm(h)
+    assert np.linalg.eigvalsh(h - mn).min() >= -1e-10 * nh
+    wn = np.linalg.eigvalsh(mn)
+    assert wn.min() >= -1e-10 * nh
+    assert np.sum(wn > 1e-10 * nh) <= ell
+    lam = np.sort(np.linalg.eigvalsh(h))[::-1]
+    assert np.linalg.norm(h - mn) >= np.sqrt(np.sum(lam[ell:] ** 2)) * (1 - 1e-12)
+    # the top r eigenpairs returned are those of M_nys
+    wtop = np.sort(wn)[::-1][:5]
+    assert np.allclose(out["L"], wtop, rtol=0, atol=1e-10 * nh)
+
+
+def test_nystrom_core_from_structured_sketch():
+    """Omega^T M Omega from the structured sketch of Eq. (4.1) (what the CUDA
+    path forms) equals the oracle's explicit C."""
+    from synth import symmetric_markov_parameters
+    blocks = symmetric_markov_parameters(_spsd_spec(6, 3, 10))
+    out = HK.nystrom(blocks, 4, 8, seed=21)
+    s = (blocks.shape[2] + 1) // 2
+    o1, o2, _, _ = HK.sketch_factors(21, s, 3, 3, 8, 1)
+    y = HK.structured_sketch(blocks, o1, o2)
+    c = T.khatri_rao(o1, o2).T @ y
+    assert np.linalg.norm(0.5 * (c + c.T) - out["C"]) <= 1e-12 * np.linalg.norm(c)

@@ -426,6 +426,40 @@ def c4_run(ctx, dev, stream, args, reps=10, warm=3):
         out[form]["era"] = {"ms": round(ms_era, 4),
                             "hausdorff_to_system_eigenvalues": float(max(dist.min(1).max(),
                                                                          dist.min(0).max()))}
+    out["nystrom"] = nystrom_run(ctx, dev, stream, reps, warm)
+    return out
+
+
+def nystrom_run(ctx, dev, stream, reps, warm):
+    """Nystrom approximation (the remark after Alg. 6) of a symmetric positive
+    semidefinite block Hankel matrix of the same size (symmetric system of
+    order 40, 128 x 128 blocks of 8 x 8), l = 50, r = 40, default cut-off;
+    eigenvalues against the input's (LAPACK on the explicit 1024 x 1024)."""
+    import torch
+    import paper_2507_23207_gb300 as K
+    from synth import HankelSpec, symmetric_markov_parameters
+    spec = HankelSpec("spsd", 40, 8, 8, 128, 0.95, 1104, 40, 50, 50)
+    b = symmetric_markov_parameters(spec)
+    flat = np.concatenate([np.asfortranarray(b[:, :, k]).ravel(order="F") for k in range(b.shape[2])])
+    t32 = torch.from_numpy(flat).to(torch.float32)
+    ms_, r, ell = spec.m * spec.s, 20, spec.ell_r
+    s = spec.s
+    h = np.zeros((ms_, ms_))
+    bb = t32.numpy().astype(np.float64).reshape(2 * s - 1, 8, 8)
+    for i in range(s):
+        for j in range(s):
+            h[i * 8:(i + 1) * 8, j * 8:(j + 1) * 8] = bb[i + j].T
+    lam_in = np.sort(np.linalg.eigvalsh(h))[::-1][:r]
+    U = torch.empty((r, ms_), dtype=torch.float64, device=dev)
+    L = torch.empty(r, dtype=torch.float64, device=dev)
+    out = {"workload": "1024x1024 SPSD block Hankel (symmetric system, order 40), 128x128 "
+                       "blocks of 8x8, l=50, top r=20 eigenpairs, cut-off 1e-5"}
+    for form, bl in (("f32", t32.to(dev)), ("bf16", t32.to(torch.bfloat16).to(dev))):
+        ms, _ = _timed(stream, lambda: K.krp_block_hankel_nystrom(ctx, bl, 8, s, r, ell, 0, U, L),
+                       reps=reps, warm=warm)
+        lg = L.cpu().numpy()
+        out[form] = {"ms": round(ms, 4),
+                     "eig_max_abs_diff_over_lambda1": float(np.max(np.abs(lg - lam_in)) / lam_in[0])}
     return out
 
 

@@ -371,6 +371,28 @@ krp_status krp_block_hankel_sketch(krp_ctx ctx, const void* blocks,
                                    const void* psi2, int ell_l, float* Y,
                                    float* Z);
 
+/* Nystrom approximation of a symmetric positive semidefinite block Hankel
+ * matrix M (Sec. 4.1, the remark after Alg. 6):
+ *   M_nys = (M Omega) (Omega^T M Omega)^+ (M Omega)^T,  Omega = Omega1 kr Omega2,
+ * with the column-sketch factors of krp_block_hankel_lowrank (Omega1 s x ell,
+ * Omega2 m x ell, tag 0, draw 0), so Y = M Omega is that call's Y for
+ * ell_r = ell.  Y = QR (FP64), C = Omega^T Y = (Omega^T Q) R formed
+ * structurally and symmetrised, C = V diag(c) V^T; the pseudoinverse treats
+ * c_i <= rcond * c_1 as zero (rcond <= 0 selects 1e-5); the eigenpairs of
+ * M_nys = Q (R C^+ R^T) Q^T come from the ell x ell matrix R C^+ R^T.
+ *   blocks: 2s-1 column-major m x m blocks (FP32 or BF16), each symmetric
+ *           and M positive semidefinite (the caller's promise; not checked)
+ *   U:      m s x r FP64 column-major, the top r eigenvectors of M_nys
+ *   Lambda: r FP64, their eigenvalues, descending
+ * Device or host pointers (host ones are staged).  Needs 1 <= r <= ell <=
+ * min(64, m s) and rcond < 1.  Synchronises the stream.  Errors: KRP_EINVAL,
+ * KRP_ENOMEM, KRP_ECUDA, KRP_ENUMERIC (an FP64 stage met a non-finite
+ * value). */
+krp_status krp_block_hankel_nystrom(krp_ctx ctx, const void* blocks,
+                                    krp_dtype bt, int m, int s, int r, int ell,
+                                    double rcond, uint64_t seed, double* U,
+                                    double* Lambda);
+
 /* Eigensystem realization from the rank-r result of krp_block_hankel_lowrank
  * (the use Sec. 4.2 makes of Alg. 6): with M ~ U S V^T, O = U S^{1/2} and
  * G^+ = V S^{-1/2}, the state matrix is

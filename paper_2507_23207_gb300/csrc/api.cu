@@ -479,6 +479,12 @@ krp_status krp_block_hankel_lowrank(krp_ctx ctx, const void* blocks, krp_dtype b
   return guarded(ctx, [&] { hankel_pipeline(blocks, bt, m, n, s, r, ell_r, ell_l, seed, U, S, V); });
 }
 
+krp_status krp_block_hankel_nystrom(krp_ctx ctx, const void* blocks, krp_dtype bt, int m, int s,
+                                    int r, int ell, double rcond, uint64_t seed, double* U,
+                                    double* Lambda) {
+  return guarded(ctx, [&] { hankel_nystrom(blocks, bt, m, s, r, ell, rcond, seed, U, Lambda); });
+}
+
 krp_status krp_block_hankel_sketch(krp_ctx ctx, const void* blocks, krp_dtype bt, int m, int n,
                                    int s, const void* omega1, const void* omega2, int ell_r,
                                    const void* psi1, const void* psi2, int ell_l, float* Y,

@@ -63,6 +63,10 @@ void hankel_batched(krp_dtype bt, int count, krp_hankel_item* items);
 
 void hankel_pipeline(const void* blocks, krp_dtype bt, int m, int n, int s, int r, int ell_r,
                      int ell_l, uint64_t seed, double* U, double* S, double* V);
+// Nystrom approximation of an SPSD block Hankel matrix (square m x m blocks):
+// its top r eigenpairs, U (m s x r) and L (r), FP64 (device or host).
+void hankel_nystrom(const void* blocks, krp_dtype bt, int m, int s, int r, int ell, double rcond,
+                    uint64_t seed, double* U, double* L);
 // Eigensystem realization (era.cu): A (r x r, nullable) and its eigenvalues
 // (wr, wi) from the blocks and the rank-r factors U (m s x r), S, V (n s x r),
 // all device memory, FP64; r <= 64.

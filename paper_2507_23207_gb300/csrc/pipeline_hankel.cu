@@ -105,6 +105,30 @@ __global__ void right_vectors_kernel(const double* __restrict__ W, int64_t ns, i
   }
 }
 
+// C <- (C + C^T) / 2 for an l x l column-major matrix (one CTA).
+__global__ void nys_sym_kernel(double* __restrict__ C, int l) {
+  for (int e = threadIdx.x; e < l * l; e += blockDim.x) {
+    const int i = e % l, j = e / l;
+    if (i < j) {
+      const double v = 0.5 * (C[i + (int64_t)l * j] + C[j + (int64_t)l * i]);
+      C[i + (int64_t)l * j] = v;
+      C[j + (int64_t)l * i] = v;
+    }
+  }
+}
+
+// G[:, j] *= c_j^{-1/2} for the eigenvalues kept by the pseudoinverse
+// (c_j > rcond * c_0, c sorted descending, c_0 > 0), else 0 (one CTA).
+__global__ void nys_scale_kernel(double* __restrict__ G, const double* __restrict__ c, int l,
+                                 double rcond) {
+  const double c0 = c[0];
+  for (int e = threadIdx.x; e < l * l; e += blockDim.x) {
+    const int j = e / l;
+    const double cj = c[j];
+    G[e] = (c0 > 0.0 && cj > rcond * c0) ? G[e] / sqrt(cj) : 0.0;
+  }
+}
+
 int grid_for(int64_t n) {
   int64_t g = (n + 255) / 256;
   return (int)(g < 1 ? 1 : (g > 8192 ? 8192 : g));
@@ -249,6 +273,106 @@ void hankel_pipeline(const void* blocks, krp_dtype bt, int m, int n, int s, int 
   out(U, Ud, (size_t)ms * r);
   out(V, Vd, (size_t)ns * r);
   out(S, Sd, (size_t)r);
+  raise_device_status(c);
+}
+
+// Nystrom approximation of a symmetric positive semidefinite block Hankel
+// matrix (the remark after Alg. 6): M_nys = Y (Omega^T Y)^+ Y^T with
+// Y = M Omega the column sketch of Alg. 6 (Eq. (4.1)).  With Y = Q R:
+//   C = Omega^T Y = (Omega^T Q) R (structured, as Psi^T Q above),
+//   C = V diag(c) V^T, G = R V diag(c_k^{-1/2}) over the kept eigenvalues,
+//   M_nys = Q (G G^T) Q^T, and the eigenpairs of M_nys are Q U_T, lambda_T
+//   of T = G G^T (l x l).  All stages after the sketch in FP64.
+void hankel_nystrom(const void* blocks, krp_dtype bt, int m, int s, int r, int ell, double rcond,
+                    uint64_t seed, double* U, double* L) {
+  Ctx* c = current();
+  validate_hankel(blocks, bt, m, m, s);
+  const int64_t ms = (int64_t)m * s;
+  KRP_REQUIRE(r >= 1 && r <= ell && ell <= 64 && ell <= ms, "need 1 <= r <= l <= min(64, m s)");
+  KRP_REQUIRE(U && L, "U/Lambda is NULL");
+  KRP_REQUIRE(rcond < 1.0, "rcond must be < 1");
+  if (rcond <= 0.0) rcond = 1e-5;  // ten times the FP32 sketch's relative rounding of C
+  const int nb = 2 * s - 1;
+  const size_t eb = dtype_size(bt);
+  const bool b_dev = is_device_ptr(blocks);
+  size_t need = b_dev ? 0 : ws_bytes((size_t)m * m * nb, eb);
+  need += ws_bytes((size_t)m * ell * nb, 4) + ws_bytes((size_t)s * ell, eb) +
+          ws_bytes((size_t)m * ell, eb) + ws_bytes((size_t)ms * ell, 4);
+  need += 2 * ws_bytes((size_t)ms * ell, 8) + 6 * ws_bytes((size_t)ell * ell, 8) +
+          2 * ws_bytes((size_t)ell, 8) + ws_bytes((size_t)ms * r, 8);
+  need += 2 * sym_eig_workspace_bytes(1) + (1 << 20);
+  ensure_workspace(c, need);
+  Workspace& ws = c->ws;
+  KRP_CUDA_CHECK(cudaMemsetAsync(c->d_status, 0, sizeof(int), c->stream));
+  const void* Bd = blocks;
+  if (!b_dev) {
+    void* p = ws.take<char>((size_t)m * m * nb * eb);
+    KRP_CUDA_CHECK(cudaMemcpyAsync(p, blocks, (size_t)m * m * nb * eb, cudaMemcpyHostToDevice,
+                                   c->stream));
+    Bd = p;
+  }
+  float* Zs = ws.take<float>((size_t)m * ell * nb);
+  void* o1 = ws.take<char>((size_t)s * ell * eb);
+  void* o2 = ws.take<char>((size_t)m * ell * eb);
+  FactorJob jo[2] = {{o1, s, ((int64_t)s * ell + 3) / 4, 0}, {o2, m, ((int64_t)m * ell + 3) / 4, 1}};
+  launch_gen_factors(seed, 0, KRP_TAG_OMEGA, ell, bt, jo, 2);
+  float* Y = ws.take<float>((size_t)ms * ell);
+  hankel_sketch(Bd, bt, m, m, s, o1, o2, ell, false, Y, Zs);
+  double* Q = ws.take<double>((size_t)ms * ell);
+  double* qw = ws.take<double>((size_t)ms * ell);
+  double* R = ws.take<double>((size_t)ell * ell);
+  QrJob jy{Y, Q, R, qw, ms, ell};
+  qr_householder_f64(&jy, 1, c->d_status);
+  double* P = ws.take<double>((size_t)ell * ell);
+  dim3 g(ell, ell);
+  if (bt == KRP_F32)
+    psi_t_q_kernel<float><<<g, 256, 0, c->stream>>>(static_cast<const float*>(o1),
+                                                    static_cast<const float*>(o2), s, m, ell, Q,
+                                                    ell, P);
+  else
+    psi_t_q_kernel<__nv_bfloat16><<<g, 256, 0, c->stream>>>(
+        static_cast<const __nv_bfloat16*>(o1), static_cast<const __nv_bfloat16*>(o2), s, m, ell,
+        Q, ell, P);
+  check_launch("nystrom_omega_t_q");
+  double* C = ws.take<double>((size_t)ell * ell);
+  matmul_f64(P, R, C, ell, ell, ell);
+  nys_sym_kernel<<<1, 256, 0, c->stream>>>(C, ell);
+  check_launch("nystrom_sym");
+  double* Vc = ws.take<double>((size_t)ell * ell);
+  double* cev = ws.take<double>((size_t)ell);
+  {
+    const double* Sa[1] = {C};
+    double* Ua[1] = {Vc};
+    double* Ea[1] = {cev};
+    int lv[1] = {ell}, rv[1] = {ell};
+    sym_eig_top_f64(Sa, lv, rv, Ua, 1, c->d_status, Ea);
+  }
+  double* G = ws.take<double>((size_t)ell * ell);
+  matmul_f64(R, Vc, G, ell, ell, ell);
+  nys_scale_kernel<<<1, 256, 0, c->stream>>>(G, cev, ell, rcond);
+  check_launch("nystrom_scale");
+  double* T = ws.take<double>((size_t)ell * ell);
+  const int64_t gd[2] = {ell, ell};
+  gram_mode_f64(G, 2, gd, 0, T);
+  double* Ut = ws.take<double>((size_t)ell * ell);
+  double* lam = ws.take<double>((size_t)ell);
+  {
+    const double* Sa[1] = {T};
+    double* Ua[1] = {Ut};
+    double* Ea[1] = {lam};
+    int lv[1] = {ell}, rv[1] = {r};
+    sym_eig_top_f64(Sa, lv, rv, Ua, 1, c->d_status, Ea);
+  }
+  double* Ud = ws.take<double>((size_t)ms * r);
+  matmul_f64(Q, Ut, Ud, ms, ell, r);
+  auto out = [&](double* dst, const double* src, size_t count) {
+    const bool dev = is_device_ptr(dst);
+    KRP_CUDA_CHECK(cudaMemcpyAsync(dst, src, count * sizeof(double),
+                                   dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                                   c->stream));
+  };
+  out(U, Ud, (size_t)ms * r);
+  out(L, lam, (size_t)r);
   raise_device_status(c);
 }
 

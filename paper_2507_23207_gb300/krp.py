@@ -34,6 +34,7 @@ EXPORTED = [
     "krp_block_hankel_sketch", "krp_tucker_rhosvd_batched", "krp_tucker_batch_plan_info",
     "krp_block_hankel_batched", "krp_split_bf16x2", "krp_trace_begin", "krp_trace_end",
     "krp_core_truncate", "krp_residual", "krp_set_wait_limit", "krp_era_realize",
+    "krp_block_hankel_nystrom",
 ]
 
 
@@ -130,6 +131,8 @@ def load_library(path: Optional[str] = None):
         "krp_block_hankel_lowrank": (C.c_int, [vp, vp, C.c_int, C.c_int, C.c_int, C.c_int,
                                                C.c_int, C.c_int, C.c_int, C.c_uint64, vp, vp,
                                                vp]),
+        "krp_block_hankel_nystrom": (C.c_int, [vp, vp, C.c_int, C.c_int, C.c_int, C.c_int,
+                                               C.c_int, C.c_double, C.c_uint64, vp, vp]),
         "krp_block_hankel_sketch": (C.c_int, [vp, vp, C.c_int, C.c_int, C.c_int, C.c_int, vp,
                                               vp, C.c_int, vp, vp, C.c_int, vp, vp]),
         "krp_tucker_rhosvd_batched": (C.c_int, [vp, C.c_int, C.c_int, C.POINTER(TuckerItem),
@@ -387,6 +390,12 @@ def krp_block_hankel_lowrank(ctx: Context, blocks, m, n, s, r, ell_r, ell_l, see
     ctx.check(ctx.lib.krp_block_hankel_lowrank(ctx.handle, _ptr(blocks), _dtype_code(blocks), m,
                                                n, s, r, ell_r, ell_l, seed, _ptr(U), _ptr(S),
                                                _ptr(V)))
+
+
+def krp_block_hankel_nystrom(ctx: Context, blocks, m, s, r, ell, seed, U, L, rcond=0.0):
+    """Top r eigenpairs (U, L) of the Nystrom approximation of an SPSD block Hankel matrix."""
+    ctx.check(ctx.lib.krp_block_hankel_nystrom(ctx.handle, _ptr(blocks), _dtype_code(blocks), m, s,
+                                               r, ell, float(rcond), seed, _ptr(U), _ptr(L)))
 
 
 def krp_era_realize(ctx: Context, blocks, m, n, s, r, U, S, V, eig_re, eig_im, A=None):

@@ -92,7 +92,7 @@ def test_constants_match_the_header(header_layout):
 
 _SCALARS = {"int": C.c_int, "unsigned": C.c_uint, "int64_t": C.c_int64,
             "uint64_t": C.c_uint64, "uint32_t": C.c_uint32, "size_t": C.c_size_t,
-            "krp_dtype": C.c_int, "krp_status": C.c_int}
+            "krp_dtype": C.c_int, "krp_status": C.c_int, "double": C.c_double}
 _POINTEES = {"int": C.c_int, "int64_t": C.c_int64, "uint32_t": C.c_uint32,
              "double": C.c_double, "float": C.c_float, "char": C.c_char}
 

@@ -430,6 +430,48 @@ def c4_run(ctx, dev, stream, args, reps=10, warm=3):
     return out
 
 
+def cauchy_run(ctx, dev, stream, args, n=250, ranks=(5, 10, 20, 30, 40, 50)):
+    """The Tucker sweep of Sec. 5.3 on the GPU: the 4-way Cauchy tensor
+    (n = 250, alpha = 2, FP32, 15.6 GB), the same target rank r in every mode
+    and no oversampling, RHOSVD-KRP (fresh factors per mode), RHOSVD-KRP-MEMO
+    and RSTHOSVD-KRP; the library's relative error and its phase times in the
+    paper's categories (RNG, mult/KRP, QR, core; the unfolding phase is zero,
+    X is never permuted).  Median of `reps` timed calls after one warm-up."""
+    import torch
+    import paper_2507_23207_gb300 as K
+    from synth import cauchy_tensor_device
+    x = cauchy_tensor_device(n, 4, 2.0, device=dev, dtype=torch.float32)
+    dims = (n,) * 4
+    reps = max(1, min(args.steps, 3))
+    out = {"workload": f"4-way Cauchy tensor n={n}, alpha=2, FP32, l = r (no oversampling)",
+           "sweep": []}
+    for r in ranks:
+        core = torch.empty(r ** 4, dtype=torch.float32, device=dev)
+        facs = [torch.empty(n * r, dtype=torch.float64, device=dev) for _ in range(4)]
+        row = {"r": r}
+        for name, fn, fl in (("rhosvd_krp", K.krp_tucker_rhosvd, 0),
+                             ("rhosvd_krp_memo", K.krp_tucker_rhosvd, K.KRP_MEMO),
+                             ("rsthosvd_krp", K.krp_tucker_sthosvd, 0)):
+            flags = fl | K.KRP_RESIDUAL | K.KRP_TIMINGS
+            fn(ctx, x, dims, [r] * 4, 0, 0, flags, core, facs)
+            runs = []
+            for _ in range(reps):
+                res = fn(ctx, x, dims, [r] * 4, 0, 0, flags, core, facs)
+                runs.append(res)
+            runs.sort(key=lambda z: z["times"]["total_ms"])
+            med = runs[len(runs) // 2]
+            t = med["times"]
+            row[name] = {"ms": round(t["total_ms"], 3), "rel_error": med["rel_residual"],
+                         "phases_ms": {"rng": round(t["rng_ms"], 3), "mult_krp": round(t["sketch_ms"], 3),
+                                       "qr": round(t["qr_ms"], 3), "core": round(t["core_ms"], 3),
+                                       "residual": round(t["residual_ms"], 3)}}
+        out["sweep"].append(row)
+        del core, facs
+    del x
+    torch.cuda.empty_cache()
+    return out
+
+
 def nystrom_run(ctx, dev, stream, reps, warm):
     """Nystrom approximation (the remark after Alg. 6) of a symmetric positive
     semidefinite block Hankel matrix of the same size (symmetric system of
@@ -771,6 +813,8 @@ def main():
                     help="run only the batched workloads (for profiling) and print their line")
     ap.add_argument("--batch-count", type=int, default=512,
                     help="tensors in the batched workload with --batch-only")
+    ap.add_argument("--cauchy", action="store_true",
+                    help="run only the Cauchy-tensor Tucker sweep (4-way, n = 250) and print its line")
     ap.add_argument("--hankel-only", action="store_true",
                     help="run only the 1024 x 1024 block-Hankel measurement (for profiling)")
     ap.add_argument("--sketch-only", action="store_true",
@@ -814,6 +858,18 @@ def main():
                 "e2e": {"value": round(v, 4), "unit": "GB/s", "h2d_bytes_per_step": 0,
                         "d2h_bytes_per_step": 0}}
         print(json.dumps(line))
+        return
+
+    if args.cauchy:
+        import torch
+        import paper_2507_23207_gb300 as K
+        dev = torch.device(f"cuda:{local_rank}")
+        torch.cuda.set_device(dev)
+        stream = torch.cuda.current_stream(dev)
+        ctx = K.Context(local_rank, stream.cuda_stream)
+        out = {"cauchy_250": cauchy_run(ctx, dev, stream, args)}
+        ctx.close()
+        print(json.dumps(out))
         return
 
     if args.hankel_only:

@@ -472,6 +472,67 @@ def cauchy_run(ctx, dev, stream, args, n=250, ranks=(5, 10, 20, 30, 40, 50)):
     return out
 
 
+def sensor_run(ctx, dev, stream, args):
+    """Sensor placement (Sec. 6) at the size of the paper's flow data (not
+    available; synthetic stand-in): a 150 x 90 x 60 grid with 150 training
+    and 61 test snapshots of a Tucker field (core 12 x 10 x 8 x 20, noise
+    1e-4, FP32).  Training: RHOSVD-KRP-MEMO of the 150 x 90 x 60 x 150
+    training tensor (ranks 12, 10, 8, 20, oversampling 8), then the sensor
+    grid (20 x 18 x 16) from its spatial factors; test: every test snapshot
+    rebuilt from its values on the grid.  Times by CUDA events (training and
+    selection: mean of three calls; reconstruction: median over the test
+    snapshots), errors relative to each snapshot."""
+    import torch
+    import paper_2507_23207_gb300 as K
+    from synth import TuckerSpec
+    from synth.tucker import tucker_tensor_device
+    dims, n_train = (150, 90, 60, 211), 150
+    spec = TuckerSpec("snapshots", dims, (12, 10, 8, 20), 1e-4, None, 1106, (12, 10, 8, 20),
+                      (20, 18, 16, 28))
+    xt, _, _ = tucker_tensor_device(spec, device=dev)
+    x = xt.to(torch.float32)
+    del xt
+    train = x[:n_train]
+    tdims = dims[:3] + (n_train,)
+    ells = list(spec.ell)
+    core = torch.empty(int(np.prod(ells)), dtype=torch.float32, device=dev)
+    facs = [torch.empty(n * c, dtype=torch.float64, device=dev) for n, c in zip(tdims, ells)]
+    sp = dims[:3]
+    sp_ells = ells[:3]
+    idx = [torch.empty(l, dtype=torch.int32, device=dev) for l in sp_ells]
+    A = [torch.empty((l, n), dtype=torch.float64, device=dev) for n, l in zip(sp, sp_ells)]
+
+    def train_step():
+        K.krp_tucker_rhosvd(ctx, train, tdims, spec.ranks, 8, 0, K.KRP_MEMO, core, facs)
+
+    def select_step():
+        K.krp_sensor_select(ctx, sp, sp_ells, facs[:3], idx, A)
+
+    ms_train, _ = _timed(stream, train_step, reps=3, warm=2)
+    ms_select, _ = _timed(stream, select_step, reps=3, warm=1)
+    il = [i.long() for i in idx]
+    out = torch.empty(int(np.prod(sp)), dtype=torch.float32, device=dev)
+    errs, ms_rec = [], []
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    for t in range(n_train, dims[3]):
+        field = x[t]  # (60, 90, 150): mode-1 fastest
+        t_hat = field.index_select(0, il[2]).index_select(1, il[1]).index_select(2, il[0]).contiguous()
+        e0.record(stream)
+        K.krp_sensor_reconstruct(ctx, sp, sp_ells, A, t_hat, out)
+        e1.record(stream)
+        e1.synchronize()
+        ms_rec.append(e0.elapsed_time(e1))
+        f = field.reshape(-1)
+        errs.append(float(torch.linalg.vector_norm(out - f) / torch.linalg.vector_norm(f)))
+    del x, train
+    torch.cuda.empty_cache()
+    return {"workload": "150x90x60 grid, 150 training + 61 test snapshots (synthetic Tucker field, "
+                        "core 12x10x8x20, noise 1e-4, FP32); sensor grid 20x18x16",
+            "training_rhosvd_krp_memo_ms": round(ms_train, 3), "selection_ms": round(ms_select, 3),
+            "reconstruct_ms_median": round(sorted(ms_rec)[len(ms_rec) // 2], 4),
+            "test_rel_error_mean": float(np.mean(errs)), "test_rel_error_max": float(np.max(errs))}
+
+
 def nystrom_run(ctx, dev, stream, reps, warm):
     """Nystrom approximation (the remark after Alg. 6) of a symmetric positive
     semidefinite block Hankel matrix of the same size (symmetric system of
@@ -813,6 +874,8 @@ def main():
                     help="run only the batched workloads (for profiling) and print their line")
     ap.add_argument("--batch-count", type=int, default=512,
                     help="tensors in the batched workload with --batch-only")
+    ap.add_argument("--sensor", action="store_true",
+                    help="run only the sensor-placement workload and print its line")
     ap.add_argument("--cauchy", action="store_true",
                     help="run only the Cauchy-tensor Tucker sweep (4-way, n = 250) and print its line")
     ap.add_argument("--hankel-only", action="store_true",
@@ -858,6 +921,18 @@ def main():
                 "e2e": {"value": round(v, 4), "unit": "GB/s", "h2d_bytes_per_step": 0,
                         "d2h_bytes_per_step": 0}}
         print(json.dumps(line))
+        return
+
+    if args.sensor:
+        import torch
+        import paper_2507_23207_gb300 as K
+        dev = torch.device(f"cuda:{local_rank}")
+        torch.cuda.set_device(dev)
+        stream = torch.cuda.current_stream(dev)
+        ctx = K.Context(local_rank, stream.cuda_stream)
+        out = {"sensor_placement": sensor_run(ctx, dev, stream, args)}
+        ctx.close()
+        print(json.dumps(out))
         return
 
     if args.cauchy:

@@ -419,6 +419,34 @@ krp_status krp_era_realize(krp_ctx ctx, const void* blocks, krp_dtype bt, int m,
                            const double* V, double* A, double* eig_re,
                            double* eig_im);
 
+/* ---- Sensor placement from Tucker factors (Sec. 6) ------------------------ */
+
+/* Training phase: for each mode i, the column-pivoted Householder QR of
+ * Q_i^T (l_i x N_i) picks l_i grid indices (the first l_i pivots, in the
+ * order picked: at step k the column of largest remaining norm over rows
+ * k..l_i-1, ties to the lowest position, decided in FP64), and the
+ * interpolation factor is A_i = Q_i (P_i^T Q_i)^{-1}, P_i^T Q_i = Q_i[idx_i, :]
+ * (Gauss-Jordan elimination with partial pivoting, FP64).
+ *   Q[i]:   N_i x l_i FP64 column-major with orthonormal columns (e.g. the
+ *           factors returned by krp_tucker_rhosvd)
+ *   idx[i]: l_i int32, the sensor indices of mode i (0-based)
+ *   A[i]:   N_i x l_i FP64 column-major
+ * All device pointers.  Needs 1 <= d <= KRP_MAXD and 1 <= l_i <= min(64, N_i).
+ * Synchronises the stream.  Errors: KRP_EINVAL, KRP_ENOMEM, KRP_ECUDA,
+ * KRP_ENUMERIC (P_i^T Q_i singular). */
+krp_status krp_sensor_select(krp_ctx ctx, int d, const int64_t* dims,
+                             const int* ells, const double* const* Q,
+                             int* const* idx, double* const* A);
+
+/* Test phase: T ~ T_hat x_1 A_1 ... x_d A_d from the measurements
+ * T_hat = T(idx_1, ..., idx_d) (l_1 x ... x l_d FP32, mode-1 fastest) with the
+ * factors of krp_sensor_select; out (N_1 x ... x N_d FP32, mode-1 fastest).
+ * The expansion runs in FP64 (one small TTM per mode).  Device pointers;
+ * asynchronous.  Errors: KRP_EINVAL, KRP_ENOMEM, KRP_ECUDA. */
+krp_status krp_sensor_reconstruct(krp_ctx ctx, int d, const int64_t* dims,
+                                  const int* ells, const double* const* A,
+                                  const float* T_hat, float* out);
+
 /* ---- a11: batches of small uneven 3-way tensors -------------------------- */
 
 /* One tensor of a batch (all device pointers). */

@@ -485,6 +485,44 @@ krp_status krp_block_hankel_nystrom(krp_ctx ctx, const void* blocks, krp_dtype b
   return guarded(ctx, [&] { hankel_nystrom(blocks, bt, m, s, r, ell, rcond, seed, U, Lambda); });
 }
 
+krp_status krp_sensor_select(krp_ctx ctx, int d, const int64_t* dims, const int* ells,
+                             const double* const* Q, int* const* idx, double* const* A) {
+  return guarded(ctx, [&] {
+    KRP_REQUIRE(d >= 1 && d <= KRP_MAXD, "d out of range");
+    KRP_REQUIRE(dims && ells && Q && idx && A, "NULL argument");
+    for (int i = 0; i < d; ++i) {
+      KRP_REQUIRE(dims[i] >= 1 && dims[i] <= INT32_MAX, "dims[%d] out of range", i);
+      KRP_REQUIRE(ells[i] >= 1 && ells[i] <= 64 && ells[i] <= dims[i],
+                  "need 1 <= ells[%d] <= min(64, dims[%d])", i, i);
+      KRP_REQUIRE(Q[i] && idx[i] && A[i], "NULL pointer for mode %d", i);
+      KRP_REQUIRE(is_device_ptr(Q[i]) && is_device_ptr(idx[i]) && is_device_ptr(A[i]),
+                  "mode %d: buffers must be device memory", i);
+    }
+    Ctx* c = current();
+    ensure_workspace(c, sensor_select_workspace_bytes(d, dims, ells));
+    KRP_CUDA_CHECK(cudaMemsetAsync(c->d_status, 0, sizeof(int), c->stream));
+    sensor_select(d, dims, ells, Q, idx, A);
+    raise_device_status(c);
+  });
+}
+
+krp_status krp_sensor_reconstruct(krp_ctx ctx, int d, const int64_t* dims, const int* ells,
+                                  const double* const* A, const float* That, float* out) {
+  return guarded(ctx, [&] {
+    KRP_REQUIRE(d >= 1 && d <= KRP_MAXD, "d out of range");
+    KRP_REQUIRE(dims && ells && A && That && out, "NULL argument");
+    checked_numel(d, dims);
+    for (int i = 0; i < d; ++i) {
+      KRP_REQUIRE(ells[i] >= 1 && ells[i] <= dims[i], "need 1 <= ells[%d] <= dims[%d]", i, i);
+      KRP_REQUIRE(A[i] && is_device_ptr(A[i]), "A[%d] must be device memory", i);
+    }
+    KRP_REQUIRE(is_device_ptr(That) && is_device_ptr(out), "T_hat and out must be device memory");
+    Ctx* c = current();
+    ensure_workspace(c, sensor_reconstruct_workspace_bytes(d, dims, ells));
+    sensor_reconstruct(d, dims, ells, A, That, out);
+  });
+}
+
 krp_status krp_block_hankel_sketch(krp_ctx ctx, const void* blocks, krp_dtype bt, int m, int n,
                                    int s, const void* omega1, const void* omega2, int ell_r,
                                    const void* psi1, const void* psi2, int ell_l, float* Y,

@@ -67,6 +67,15 @@ void hankel_pipeline(const void* blocks, krp_dtype bt, int m, int n, int s, int 
 // its top r eigenpairs, U (m s x r) and L (r), FP64 (device or host).
 void hankel_nystrom(const void* blocks, krp_dtype bt, int m, int s, int r, int ell, double rcond,
                     uint64_t seed, double* U, double* L);
+// Sensor placement (sensor.cu, Sec. 6): pivoted-QR indices and interpolation
+// factors of d orthonormal factors Q_i (N_i x l_i, FP64, device), and the
+// reconstruction T_hat x {A_i} of measurements on the sensor grid.
+size_t sensor_select_workspace_bytes(int d, const int64_t* dims, const int* ells);
+void sensor_select(int d, const int64_t* dims, const int* ells, const double* const* Q,
+                   int* const* idx, double* const* A);
+size_t sensor_reconstruct_workspace_bytes(int d, const int64_t* dims, const int* ells);
+void sensor_reconstruct(int d, const int64_t* dims, const int* ells, const double* const* A,
+                        const float* That, float* out);
 // Eigensystem realization (era.cu): A (r x r, nullable) and its eigenvalues
 // (wr, wi) from the blocks and the rank-r factors U (m s x r), S, V (n s x r),
 // all device memory, FP64; r <= 64.

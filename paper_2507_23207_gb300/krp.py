@@ -34,7 +34,7 @@ EXPORTED = [
     "krp_block_hankel_sketch", "krp_tucker_rhosvd_batched", "krp_tucker_batch_plan_info",
     "krp_block_hankel_batched", "krp_split_bf16x2", "krp_trace_begin", "krp_trace_end",
     "krp_core_truncate", "krp_residual", "krp_set_wait_limit", "krp_era_realize",
-    "krp_block_hankel_nystrom",
+    "krp_block_hankel_nystrom", "krp_sensor_select", "krp_sensor_reconstruct",
 ]
 
 
@@ -131,6 +131,10 @@ def load_library(path: Optional[str] = None):
         "krp_block_hankel_lowrank": (C.c_int, [vp, vp, C.c_int, C.c_int, C.c_int, C.c_int,
                                                C.c_int, C.c_int, C.c_int, C.c_uint64, vp, vp,
                                                vp]),
+        "krp_sensor_select": (C.c_int, [vp, C.c_int, i64p, C.POINTER(C.c_int), C.POINTER(vp),
+                                        C.POINTER(vp), C.POINTER(vp)]),
+        "krp_sensor_reconstruct": (C.c_int, [vp, C.c_int, i64p, C.POINTER(C.c_int),
+                                             C.POINTER(vp), vp, vp]),
         "krp_block_hankel_nystrom": (C.c_int, [vp, vp, C.c_int, C.c_int, C.c_int, C.c_int,
                                                C.c_int, C.c_double, C.c_uint64, vp, vp]),
         "krp_block_hankel_sketch": (C.c_int, [vp, vp, C.c_int, C.c_int, C.c_int, C.c_int, vp,
@@ -390,6 +394,18 @@ def krp_block_hankel_lowrank(ctx: Context, blocks, m, n, s, r, ell_r, ell_l, see
     ctx.check(ctx.lib.krp_block_hankel_lowrank(ctx.handle, _ptr(blocks), _dtype_code(blocks), m,
                                                n, s, r, ell_r, ell_l, seed, _ptr(U), _ptr(S),
                                                _ptr(V)))
+
+
+def krp_sensor_select(ctx: Context, dims, ells, Qs, idxs, As):
+    """Sensor indices (int32, device) and interpolation factors of the factors Qs."""
+    ctx.check(ctx.lib.krp_sensor_select(ctx.handle, len(dims), _i64(dims), _i32(ells), _ptrs(Qs),
+                                        _ptrs(idxs), _ptrs(As)))
+
+
+def krp_sensor_reconstruct(ctx: Context, dims, ells, As, T_hat, out):
+    """out = T_hat x_1 A_1 ... x_d A_d (FP32 tensors, FP64 factors, device)."""
+    ctx.check(ctx.lib.krp_sensor_reconstruct(ctx.handle, len(dims), _i64(dims), _i32(ells),
+                                             _ptrs(As), _ptr(T_hat), _ptr(out)))
 
 
 def krp_block_hankel_nystrom(ctx: Context, blocks, m, s, r, ell, seed, U, L, rcond=0.0):

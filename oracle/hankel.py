@@ -19,7 +19,7 @@ import numpy as np
 
 from . import philox
 from .linalg import householder_qr, jacobi_eig, jacobi_svd, lstsq_qr
-from .tensor import khatri_rao
+from .tensor import khatri_rao, khatri_rao_list
 
 
 def block_hankel(blocks: np.ndarray) -> np.ndarray:
@@ -192,3 +192,88 @@ def rng_count_block_gauss(m: int, n: int, p: int, q: int, ell_r: int,
                           ell_l: int) -> int:
     """Normals for the same algorithm with dense Gaussian sketches: nq l_r + mp l_l."""
     return n * q * ell_r + m * p * ell_l
+
+
+# ---- two-level block Hankel matrices (Sec. 4.3, multilevel structure) ----
+#
+# M = sum_{k1, k2} E_{k1} kron E_{k2} kron H_{k1,k2}: s1 x s1 blocks, block
+# (i1, j1) itself an s2 x s2 block Hankel matrix whose block (i2, j2) is
+# H_{i1+j1, i2+j2} (0-based), each m x n.  blocks has shape
+# (m, n, 2 s1 - 1, 2 s2 - 1); row index a + m (i2 + s2 i1), column index
+# b + n (j2 + s2 j1).  Factor draws: Omega = Omega^(1) kr Omega^(2) kr
+# Omega^(3) (s1, s2, n rows: factors 0, 1, 2 on tag 0), Psi likewise with
+# (s1, s2, m) rows on tag 1; draw id 0.
+
+
+def block_hankel2(blocks: np.ndarray) -> np.ndarray:
+    """Explicit (m s1 s2) x (n s1 s2) two-level block Hankel matrix."""
+    m, n, nb1, nb2 = blocks.shape
+    s1, s2 = (nb1 + 1) // 2, (nb2 + 1) // 2
+    if nb1 != 2 * s1 - 1 or nb2 != 2 * s2 - 1:
+        raise ValueError("a two-level block Hankel needs (2 s1 - 1) x (2 s2 - 1) blocks")
+    h = np.zeros((m * s1 * s2, n * s1 * s2))
+    for i1 in range(s1):
+        for j1 in range(s1):
+            for i2 in range(s2):
+                for j2 in range(s2):
+                    r0 = m * (i2 + s2 * i1)
+                    c0 = n * (j2 + s2 * j1)
+                    h[r0:r0 + m, c0:c0 + n] = blocks[:, :, i1 + j1, i2 + j2]
+    return h
+
+
+def structured_sketch2(blocks: np.ndarray, o1: np.ndarray, o2: np.ndarray, o3: np.ndarray,
+                       transpose: bool = False) -> np.ndarray:
+    """sum_{k1,k2} (E_{k1} O1) kr (E_{k2} O2) kr (H_{k1,k2} O3), the two-level
+    form of Eq. (4.1) (mixed-product property of the Kronecker and
+    Khatri-Rao products); with transpose=True the blocks enter transposed
+    (the row sketch M^T Psi)."""
+    m, n, nb1, nb2 = blocks.shape
+    s1, s2 = (nb1 + 1) // 2, (nb2 + 1) // 2
+    out = 0.0
+    for k1 in range(1, nb1 + 1):
+        e1 = hankel_pattern(s1, k1)
+        for k2 in range(1, nb2 + 1):
+            e2 = hankel_pattern(s2, k2)
+            hk = blocks[:, :, k1 - 1, k2 - 1]
+            if transpose:
+                hk = hk.T
+            out = out + khatri_rao_list([e1.T @ o1 if transpose else e1 @ o1,
+                                         e2.T @ o2 if transpose else e2 @ o2, hk @ o3])
+    return out
+
+
+def sketch_factors2(seed: int, s1: int, s2: int, m: int, n: int, ell_r: int, ell_l: int,
+                    omega_round=None):
+    """(Omega^(1..3), Psi^(1..3)): s1, s2, n rows x l_r and s1, s2, m rows x l_l."""
+    om = [philox.gaussian_factor(seed, f, 0, philox.TAG_OMEGA, rows, ell_r)
+          for f, rows in enumerate((s1, s2, n))]
+    ps = [philox.gaussian_factor(seed, f, 0, philox.TAG_PSI, rows, ell_l)
+          for f, rows in enumerate((s1, s2, m))]
+    if omega_round == "f32":
+        om, ps = [philox.round_to_f32(a) for a in om], [philox.round_to_f32(a) for a in ps]
+    elif omega_round == "bf16":
+        om, ps = [philox.round_to_bf16(a) for a in om], [philox.round_to_bf16(a) for a in ps]
+    return om, ps
+
+
+def single_pass_svd2(blocks: np.ndarray, r: int, ell_r: int, ell_l: int, seed: int,
+                     omega_round=None):
+    """Alg. 6 on the explicit two-level block Hankel matrix, with
+    Omega = Omega^(1) kr Omega^(2) kr Omega^(3) and Psi likewise:
+    Y = M Omega, Z = M^T Psi, Y = QR, W = (Psi^T Q)^+ Z^T, W = U_W S V^T,
+    U = Q U_W; returns U[:, :r], S[:r], V[:, :r] and the intermediates."""
+    m, n, nb1, nb2 = blocks.shape
+    s1, s2 = (nb1 + 1) // 2, (nb2 + 1) // 2
+    om, ps = sketch_factors2(seed, s1, s2, m, n, ell_r, ell_l, omega_round)
+    h = block_hankel2(blocks)
+    omega = khatri_rao_list(om)
+    psi = khatri_rao_list(ps)
+    y = h @ omega
+    z = h.T @ psi
+    q, _ = householder_qr(y)
+    w = lstsq_qr(psi.T @ q, z.T)
+    uw, sig, vt = jacobi_svd(w)
+    u = q @ uw
+    return {"U": u[:, :r], "S": sig[:r], "V": vt[:r].T, "Y": y, "Z": z, "Q": q, "W": w,
+            "factors": (om, ps), "H": h}

@@ -15,7 +15,8 @@ describe the same bytes.
 from .tucker import (TuckerSpec, haar, tucker_factors, expand_tucker,
                      tucker_tensor, config_spec, to_torch_layout,
                      from_torch_layout)
-from .hankel import HankelSpec, markov_parameters, hankel_config_spec, symmetric_markov_parameters
+from .hankel import (HankelSpec, markov_parameters, hankel_config_spec, symmetric_markov_parameters,
+                     two_level_markov_parameters)
 from .batch import batch_tucker_specs, batch_hankel_specs
 from .cauchy import cauchy_tensor, cauchy_tensor_device
 
@@ -23,5 +24,5 @@ __all__ = [
     "TuckerSpec", "haar", "tucker_factors", "expand_tucker", "tucker_tensor",
     "config_spec", "to_torch_layout", "from_torch_layout", "HankelSpec",
     "markov_parameters", "hankel_config_spec", "symmetric_markov_parameters",
-    "cauchy_tensor", "cauchy_tensor_device", "batch_tucker_specs", "batch_hankel_specs",
+    "cauchy_tensor", "cauchy_tensor_device", "two_level_markov_parameters", "batch_tucker_specs", "batch_hankel_specs",
 ]

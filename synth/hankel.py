@@ -110,3 +110,23 @@ def symmetric_markov_parameters(spec: HankelSpec) -> np.ndarray:
         out[:, :, k] = b.T @ akb
         akb = a @ akb
     return out
+
+
+def two_level_markov_parameters(order: int, m: int, n: int, s1: int, s2: int, seed: int,
+                                radius: float = 0.9) -> np.ndarray:
+    """Blocks H_{k1,k2} = C diag(lambda^k1 mu^k2) B (k1 < 2 s1 - 1,
+    k2 < 2 s2 - 1, 0-based) of a two-dimensional exponential sum, shape
+    (m, n, 2 s1 - 1, 2 s2 - 1): the two-level block Hankel matrix they form
+    is sum_r (u_r kron c_r)(v_r kron b_r)^T with Vandermonde-like u_r, v_r, so
+    its rank is at most `order`.  lambda, mu uniform in [-radius, radius];
+    B, C standard Gaussian.  Input construction only."""
+    rng = np.random.default_rng(seed)
+    lam = rng.uniform(-radius, radius, order)
+    mu = rng.uniform(-radius, radius, order)
+    b = rng.standard_normal((order, n))
+    c = rng.standard_normal((m, order))
+    out = np.zeros((m, n, 2 * s1 - 1, 2 * s2 - 1), order="F")
+    for k1 in range(2 * s1 - 1):
+        for k2 in range(2 * s2 - 1):
+            out[:, :, k1, k2] = (c * (lam ** k1 * mu ** k2)) @ b
+    return out

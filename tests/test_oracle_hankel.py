@@ -210,3 +210,49 @@ def test_nystrom_core_from_structured_sketch():
     y = HK.structured_sketch(blocks, o1, o2)
     c = T.khatri_rao(o1, o2).T @ y
     assert np.linalg.norm(0.5 * (c + c.T) - out["C"]) <= 1e-12 * np.linalg.norm(c)
+
+
+# ---- two-level block Hankel matrices (Sec. 4.3) ----
+
+def test_block_hankel2_is_the_kronecker_sum():
+    """M = sum_{k1,k2} E_{k1} kron E_{k2} kron H_{k1,k2} with the 0/1 patterns
+    of Sec. 4.2 at both levels, from explicit Kronecker products."""
+    from synth import two_level_markov_parameters
+    b = two_level_markov_parameters(3, 2, 3, 4, 3, seed=1)
+    m, n = 2, 3
+    s1, s2 = 4, 3
+    ref = 0.0
+    for k1 in range(1, 2 * s1):
+        for k2 in range(1, 2 * s2):
+            ref = ref + np.kron(HK.hankel_pattern(s1, k1),
+                                np.kron(HK.hankel_pattern(s2, k2), b[:, :, k1 - 1, k2 - 1]))
+    assert np.array_equal(HK.block_hankel2(b), ref)
+
+
+def test_structured_sketch2_identity():
+    """Two-level Eq. (4.1): M (O1 kr O2 kr O3) and M^T (P1 kr P2 kr P3)."""
+    from synth import two_level_markov_parameters
+    b = two_level_markov_parameters(4, 3, 2, 5, 4, seed=2)
+    h = HK.block_hankel2(b)
+    rng = np.random.default_rng(3)
+    om = [rng.standard_normal((r, 6)) for r in (5, 4, 2)]
+    ps = [rng.standard_normal((r, 7)) for r in (5, 4, 3)]
+    y = HK.structured_sketch2(b, *om)
+    z = HK.structured_sketch2(b, *ps, transpose=True)
+    assert np.linalg.norm(y - h @ T.khatri_rao_list(om)) <= 1e-12 * np.linalg.norm(y)
+    assert np.linalg.norm(z - h.T @ T.khatri_rao_list(ps)) <= 1e-12 * np.linalg.norm(z)
+
+
+def test_single_pass_svd2_exact_for_low_rank():
+    """rank(M) <= order <= l_r: the two-sided single-pass approximation
+    reproduces M, and its singular values are LAPACK's."""
+    from synth import two_level_markov_parameters
+    order = 5
+    b = two_level_markov_parameters(order, 3, 2, 6, 5, seed=4)
+    out = HK.single_pass_svd2(b, order, order + 4, 2 * (order + 4), seed=5)
+    h = out["H"]
+    assert np.linalg.matrix_rank(h, tol=1e-10 * np.linalg.norm(h)) <= order
+    approx = (out["U"] * out["S"]) @ out["V"].T
+    assert np.linalg.norm(approx - h) <= 1e-9 * np.linalg.norm(h)
+    sv = np.linalg.svd(h, compute_uv=False)[:order]
+    assert np.allclose(out["S"], sv, rtol=0, atol=1e-9 * sv[0])

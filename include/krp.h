@@ -360,6 +360,28 @@ krp_status krp_block_hankel_lowrank(krp_ctx ctx, const void* blocks,
                                     int ell_r, int ell_l, uint64_t seed,
                                     double* U, double* S, double* V);
 
+/* Alg. 6 on a two-level block Hankel matrix (Sec. 4.3, multilevel block
+ * structure with L = 2): M is (m s1 s2) x (n s1 s2); block (i1, j1) of M
+ * (1-based, s1 x s1 of them) is itself an s2 x s2 block Hankel matrix whose
+ * block (i2, j2) is H_{i1+j1-1, i2+j2-1}, m x n, i.e.
+ *   M = sum_{k1, k2} E_{k1} kron E_{k2} kron H_{k1,k2}.
+ * `blocks` holds the (2 s1 - 1)(2 s2 - 1) column-major m x n blocks, block
+ * (k1, k2) (0-based) at position k1 + (2 s1 - 1) k2; row index of M is
+ * a + m (i2 + s2 i1) (0-based).  With Omega = Omega1 kr Omega2 kr Omega3
+ * (s1, s2, n rows x l_r; factors 0, 1, 2 of tag 0) and Psi = Psi1 kr Psi2 kr
+ * Psi3 (s1, s2, m rows x l_l; tag 1), draw 0:
+ *   Y = M Omega = sum_{k1,k2} (E_{k1} Omega1) kr (E_{k2} Omega2) kr (H_{k1,k2} Omega3)
+ * (the two-level form of Eq. (4.1)), Z = M^T Psi likewise with the blocks
+ * transposed, then the steps of krp_block_hankel_lowrank: returns U
+ * (m s1 s2 x r), S (r), V (n s1 s2 x r), FP64 column-major (device or host).
+ * ell_l = 0 selects ceil(1.5 ell_r).  Needs 1 <= r <= ell_r <= ell_l,
+ * ell_r <= 64, ell_l <= 256, ell_r <= m s1 s2, ell_l <= n s1 s2.  Synchronises
+ * the stream.  Errors: KRP_EINVAL, KRP_ENOMEM, KRP_ECUDA, KRP_ENUMERIC. */
+krp_status krp_block_hankel2_lowrank(krp_ctx ctx, const void* blocks,
+                                     krp_dtype bt, int m, int n, int s1, int s2,
+                                     int r, int ell_r, int ell_l, uint64_t seed,
+                                     double* U, double* S, double* V);
+
 /* The two sketches of Alg. 6 alone (device pointers): Y (m s x ell_r) and
  * Z (n s x ell_l), FP32, from given factors (FP32 or BF16 like the blocks;
  * omega1 s x ell_r, omega2 n x ell_r, psi1 s x ell_l, psi2 m x ell_l, all

@@ -523,6 +523,14 @@ krp_status krp_sensor_reconstruct(krp_ctx ctx, int d, const int64_t* dims, const
   });
 }
 
+krp_status krp_block_hankel2_lowrank(krp_ctx ctx, const void* blocks, krp_dtype bt, int m, int n,
+                                     int s1, int s2, int r, int ell_r, int ell_l, uint64_t seed,
+                                     double* U, double* S, double* V) {
+  return guarded(ctx, [&] {
+    hankel2_pipeline(blocks, bt, m, n, s1, s2, r, ell_r, ell_l, seed, U, S, V);
+  });
+}
+
 krp_status krp_block_hankel_sketch(krp_ctx ctx, const void* blocks, krp_dtype bt, int m, int n,
                                    int s, const void* omega1, const void* omega2, int ell_r,
                                    const void* psi1, const void* psi2, int ell_l, float* Y,

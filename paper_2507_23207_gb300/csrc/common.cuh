@@ -212,6 +212,10 @@ void check_finite_f64(const double* x, int64_t n, int* status);
 void hankel_sketch(const void* blocks, krp_dtype bt, int m, int n, int s,
                    const void* f1, const void* f2, int ell, bool transpose,
                    float* Y, float* Zscratch);
+// The two-level form (Sec. 4.3): (2 s1 - 1)(2 s2 - 1) blocks, block (k1, k2)
+// at k1 + (2 s1 - 1) k2; f1 s1 x ell, f2 s2 x ell, f3 (n or m) x ell.
+void hankel2_sketch(const void* blocks, krp_dtype bt, int m, int n, int s1, int s2, const void* f1,
+                    const void* f2, const void* f3, int ell, bool transpose, float* Y, float* Zs);
 
 // BF16 tensor-core kernels (tc_kernels.cu)
 bool tc_available();

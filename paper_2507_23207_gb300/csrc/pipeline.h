@@ -63,6 +63,10 @@ void hankel_batched(krp_dtype bt, int count, krp_hankel_item* items);
 
 void hankel_pipeline(const void* blocks, krp_dtype bt, int m, int n, int s, int r, int ell_r,
                      int ell_l, uint64_t seed, double* U, double* S, double* V);
+// Alg. 6 on a two-level block Hankel matrix (Sec. 4.3; blocks (k1, k2) at
+// k1 + (2 s1 - 1) k2, each m x n column-major).
+void hankel2_pipeline(const void* blocks, krp_dtype bt, int m, int n, int s1, int s2, int r,
+                      int ell_r, int ell_l, uint64_t seed, double* U, double* S, double* V);
 // Nystrom approximation of an SPSD block Hankel matrix (square m x m blocks):
 // its top r eigenpairs, U (m s x r) and L (r), FP64 (device or host).
 void hankel_nystrom(const void* blocks, krp_dtype bt, int m, int s, int r, int ell, double rcond,

@@ -35,6 +35,7 @@ EXPORTED = [
     "krp_block_hankel_batched", "krp_split_bf16x2", "krp_trace_begin", "krp_trace_end",
     "krp_core_truncate", "krp_residual", "krp_set_wait_limit", "krp_era_realize",
     "krp_block_hankel_nystrom", "krp_sensor_select", "krp_sensor_reconstruct",
+    "krp_block_hankel2_lowrank",
 ]
 
 
@@ -137,6 +138,9 @@ def load_library(path: Optional[str] = None):
                                              C.POINTER(vp), vp, vp]),
         "krp_block_hankel_nystrom": (C.c_int, [vp, vp, C.c_int, C.c_int, C.c_int, C.c_int,
                                                C.c_int, C.c_double, C.c_uint64, vp, vp]),
+        "krp_block_hankel2_lowrank": (C.c_int, [vp, vp, C.c_int, C.c_int, C.c_int, C.c_int,
+                                                C.c_int, C.c_int, C.c_int, C.c_int, C.c_uint64,
+                                                vp, vp, vp]),
         "krp_block_hankel_sketch": (C.c_int, [vp, vp, C.c_int, C.c_int, C.c_int, C.c_int, vp,
                                               vp, C.c_int, vp, vp, C.c_int, vp, vp]),
         "krp_tucker_rhosvd_batched": (C.c_int, [vp, C.c_int, C.c_int, C.POINTER(TuckerItem),
@@ -412,6 +416,13 @@ def krp_block_hankel_nystrom(ctx: Context, blocks, m, s, r, ell, seed, U, L, rco
     """Top r eigenpairs (U, L) of the Nystrom approximation of an SPSD block Hankel matrix."""
     ctx.check(ctx.lib.krp_block_hankel_nystrom(ctx.handle, _ptr(blocks), _dtype_code(blocks), m, s,
                                                r, ell, float(rcond), seed, _ptr(U), _ptr(L)))
+
+
+def krp_block_hankel2_lowrank(ctx: Context, blocks, m, n, s1, s2, r, ell_r, ell_l, seed, U, S, V):
+    """Alg. 6 on a two-level block Hankel matrix (blocks (k1, k2) at k1 + (2 s1 - 1) k2)."""
+    ctx.check(ctx.lib.krp_block_hankel2_lowrank(ctx.handle, _ptr(blocks), _dtype_code(blocks), m,
+                                                n, s1, s2, r, ell_r, ell_l, seed, _ptr(U),
+                                                _ptr(S), _ptr(V)))
 
 
 def krp_era_realize(ctx: Context, blocks, m, n, s, r, U, S, V, eig_re, eig_im, A=None):

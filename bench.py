@@ -427,6 +427,41 @@ def c4_run(ctx, dev, stream, args, reps=10, warm=3):
                             "hausdorff_to_system_eigenvalues": float(max(dist.min(1).max(),
                                                                          dist.min(0).max()))}
     out["nystrom"] = nystrom_run(ctx, dev, stream, reps, warm)
+    out["two_level"] = hankel2_run(ctx, dev, stream, reps, warm)
+    return out
+
+
+def hankel2_run(ctx, dev, stream, reps, warm):
+    """Alg. 6 on a 1024 x 1024 two-level block Hankel matrix (16 x 16 blocks,
+    each a 16 x 16 block Hankel matrix of 4 x 4 blocks; a two-dimensional
+    exponential sum of order 20), l_r = 30, l_l = 45, r = 20; singular values
+    against the explicit matrix's (LAPACK)."""
+    import torch
+    import paper_2507_23207_gb300 as K
+    from synth import two_level_markov_parameters
+    order, m, n, s1, s2, r, lr, ll = 20, 4, 4, 16, 16, 20, 30, 45
+    b = two_level_markov_parameters(order, m, n, s1, s2, seed=1107)
+    t32 = torch.from_numpy(np.asfortranarray(b).ravel(order="F").copy()).to(torch.float32)
+    b32 = t32.numpy().astype(np.float64).reshape(b.shape, order="F")
+    h = np.zeros((m * s1 * s2, n * s1 * s2))
+    for i1 in range(s1):
+        for j1 in range(s1):
+            for i2 in range(s2):
+                for j2 in range(s2):
+                    r0, c0 = m * (i2 + s2 * i1), n * (j2 + s2 * j1)
+                    h[r0:r0 + m, c0:c0 + n] = b32[:, :, i1 + j1, i2 + j2]
+    sv = np.linalg.svd(h, compute_uv=False)[:r]
+    ms, ns = m * s1 * s2, n * s1 * s2
+    U = torch.empty((r, ms), dtype=torch.float64, device=dev)
+    V = torch.empty((r, ns), dtype=torch.float64, device=dev)
+    S = torch.empty(r, dtype=torch.float64, device=dev)
+    out = {"workload": "1024x1024 two-level block Hankel (16x16 blocks of 16x16 blocks of 4x4), "
+                       "order 20, l_r=30 l_l=45 r=20"}
+    for form, bl in (("f32", t32.to(dev)), ("bf16", t32.to(torch.bfloat16).to(dev))):
+        ms_, _ = _timed(stream, lambda: K.krp_block_hankel2_lowrank(
+            ctx, bl, m, n, s1, s2, r, lr, ll, 0, U, S, V), reps=reps, warm=warm)
+        out[form] = {"ms": round(ms_, 4),
+                     "sigma_max_abs_diff_over_sigma1": float(np.max(np.abs(S.cpu().numpy() - sv)) / sv[0])}
     return out
 
 

@@ -441,6 +441,32 @@ krp_status krp_era_realize(krp_ctx ctx, const void* blocks, krp_dtype bt, int m,
                            const double* V, double* A, double* eig_re,
                            double* eig_im);
 
+/* ---- Hadamard products of Tucker tensors (Sec. 5, its opening) ----------- */
+
+/* RHOSVD-KRP-MEMO of Z = X * Y (elementwise), X = G x {U_j}, Y = H x {V_j},
+ * without forming Z: Z is the Tucker tensor with core G (x) H (index
+ * c_j = a_j + r_j b_j) and factors W_j[i, c_j] = U_j[i, a_j] V_j[i, b_j], so
+ * with one Philox factor set Omega_j (n_j x l, FP64, draw 0, tag 0 -- the
+ * MEMO set of krp_tucker_rhosvd):
+ *   Y_n = W_n MTTKRP_n(G (x) H, {W_j^T Omega_j}),  Y_n = Q_n R_n,
+ *   core = (G (x) H) x_1 (Q_1^T W_1) ... x_d (Q_d^T W_d),
+ *   rel_error = sqrt(max(0, ||Z||^2 - ||core||^2)) / ||Z|| with
+ *   ||Z||^2 = <G (x) H, (G (x) H) x_j (W_j^T W_j)> (cancellation limits it to
+ *   errors above ~1e-7).
+ *   G: r_1 x ... x r_d, H: s_1 x ... x s_d (FP64, mode-1 fastest);
+ *   U[j]: n_j x r_j, V[j]: n_j x s_j (FP64 column-major); core: l^d FP64;
+ *   factors[j]: n_j x l FP64 column-major (orthonormal); rel_error: host
+ *   double, may be NULL.
+ * Device pointers except rel_error.  Needs 1 <= l <= min(64, n_j) and
+ * prod_j r_j s_j <= 2^25.  Synchronises the stream.  Errors: KRP_EINVAL,
+ * KRP_ENOMEM, KRP_ECUDA, KRP_ENUMERIC. */
+krp_status krp_tucker_hadamard(krp_ctx ctx, int d, const int64_t* dims,
+                               const int* rg, const double* G,
+                               const double* const* U, const int* rh,
+                               const double* H, const double* const* V,
+                               int ell, uint64_t seed, double* core,
+                               double* const* factors, double* rel_error);
+
 /* ---- Sensor placement from Tucker factors (Sec. 6) ------------------------ */
 
 /* Training phase: for each mode i, the column-pivoted Householder QR of

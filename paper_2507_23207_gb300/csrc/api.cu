@@ -485,6 +485,35 @@ krp_status krp_block_hankel_nystrom(krp_ctx ctx, const void* blocks, krp_dtype b
   return guarded(ctx, [&] { hankel_nystrom(blocks, bt, m, s, r, ell, rcond, seed, U, Lambda); });
 }
 
+krp_status krp_tucker_hadamard(krp_ctx ctx, int d, const int64_t* dims, const int* rg,
+                               const double* G, const double* const* U, const int* rh,
+                               const double* H, const double* const* V, int ell, uint64_t seed,
+                               double* core, double* const* factors, double* rel_error) {
+  return guarded(ctx, [&] {
+    KRP_REQUIRE(d >= 1 && d <= KRP_MAXD, "d out of range");
+    KRP_REQUIRE(dims && rg && rh && G && U && H && V && core && factors, "NULL argument");
+    KRP_REQUIRE(ell >= 1 && ell <= 64, "need 1 <= ell <= 64");
+    int64_t ncore = 1;
+    for (int j = 0; j < d; ++j) {
+      KRP_REQUIRE(dims[j] >= ell && dims[j] <= INT32_MAX, "need ell <= dims[%d] < 2^31", j);
+      KRP_REQUIRE(rg[j] >= 1 && rh[j] >= 1 && rg[j] <= 4096 && rh[j] <= 4096,
+                  "ranks of mode %d out of range", j);
+      ncore *= (int64_t)rg[j] * rh[j];
+      KRP_REQUIRE(ncore <= (int64_t(1) << 25), "the product's core G (x) H exceeds 2^25 entries");
+      KRP_REQUIRE(U[j] && V[j] && factors[j], "NULL factor for mode %d", j);
+      KRP_REQUIRE(is_device_ptr(U[j]) && is_device_ptr(V[j]) && is_device_ptr(factors[j]),
+                  "mode %d: factors must be device memory", j);
+    }
+    KRP_REQUIRE(is_device_ptr(G) && is_device_ptr(H) && is_device_ptr(core),
+                "G, H and core must be device memory");
+    Ctx* c = current();
+    ensure_workspace(c, hadamard_workspace_bytes(d, dims, rg, rh, ell));
+    KRP_CUDA_CHECK(cudaMemsetAsync(c->d_status, 0, sizeof(int), c->stream));
+    hadamard_rhosvd(d, dims, rg, G, U, rh, H, V, ell, seed, core, factors, rel_error);
+    raise_device_status(c);
+  });
+}
+
 krp_status krp_sensor_select(krp_ctx ctx, int d, const int64_t* dims, const int* ells,
                              const double* const* Q, int* const* idx, double* const* A) {
   return guarded(ctx, [&] {

@@ -71,6 +71,13 @@ void hankel2_pipeline(const void* blocks, krp_dtype bt, int m, int n, int s1, in
 // its top r eigenpairs, U (m s x r) and L (r), FP64 (device or host).
 void hankel_nystrom(const void* blocks, krp_dtype bt, int m, int s, int r, int ell, double rcond,
                     uint64_t seed, double* U, double* L);
+// Recompression of the Hadamard product of two Tucker tensors (hadamard.cu):
+// RHOSVD-KRP-MEMO of (G x {U_j}) * (H x {V_j}) without forming it, FP64.
+size_t hadamard_workspace_bytes(int d, const int64_t* dims, const int* rg, const int* rh, int ell);
+void hadamard_rhosvd(int d, const int64_t* dims, const int* rg, const double* G,
+                     const double* const* U, const int* rh, const double* H,
+                     const double* const* V, int ell, uint64_t seed, double* core,
+                     double* const* factors, double* rel_error);
 // Sensor placement (sensor.cu, Sec. 6): pivoted-QR indices and interpolation
 // factors of d orthonormal factors Q_i (N_i x l_i, FP64, device), and the
 // reconstruction T_hat x {A_i} of measurements on the sensor grid.

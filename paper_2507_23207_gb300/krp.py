@@ -35,7 +35,7 @@ EXPORTED = [
     "krp_block_hankel_batched", "krp_split_bf16x2", "krp_trace_begin", "krp_trace_end",
     "krp_core_truncate", "krp_residual", "krp_set_wait_limit", "krp_era_realize",
     "krp_block_hankel_nystrom", "krp_sensor_select", "krp_sensor_reconstruct",
-    "krp_block_hankel2_lowrank",
+    "krp_block_hankel2_lowrank", "krp_tucker_hadamard",
 ]
 
 
@@ -132,6 +132,10 @@ def load_library(path: Optional[str] = None):
         "krp_block_hankel_lowrank": (C.c_int, [vp, vp, C.c_int, C.c_int, C.c_int, C.c_int,
                                                C.c_int, C.c_int, C.c_int, C.c_uint64, vp, vp,
                                                vp]),
+        "krp_tucker_hadamard": (C.c_int, [vp, C.c_int, i64p, C.POINTER(C.c_int), vp,
+                                          C.POINTER(vp), C.POINTER(C.c_int), vp, C.POINTER(vp),
+                                          C.c_int, C.c_uint64, vp, C.POINTER(vp),
+                                          C.POINTER(C.c_double)]),
         "krp_sensor_select": (C.c_int, [vp, C.c_int, i64p, C.POINTER(C.c_int), C.POINTER(vp),
                                         C.POINTER(vp), C.POINTER(vp)]),
         "krp_sensor_reconstruct": (C.c_int, [vp, C.c_int, i64p, C.POINTER(C.c_int),
@@ -398,6 +402,15 @@ def krp_block_hankel_lowrank(ctx: Context, blocks, m, n, s, r, ell_r, ell_l, see
     ctx.check(ctx.lib.krp_block_hankel_lowrank(ctx.handle, _ptr(blocks), _dtype_code(blocks), m,
                                                n, s, r, ell_r, ell_l, seed, _ptr(U), _ptr(S),
                                                _ptr(V)))
+
+
+def krp_tucker_hadamard(ctx: Context, dims, rg, G, Us, rh, H, Vs, ell, seed, core, factors):
+    """RHOSVD-KRP-MEMO of the Hadamard product of two Tucker tensors; returns the relative error."""
+    err = C.c_double(0.0)
+    ctx.check(ctx.lib.krp_tucker_hadamard(ctx.handle, len(dims), _i64(dims), _i32(rg), _ptr(G),
+                                          _ptrs(Us), _i32(rh), _ptr(H), _ptrs(Vs), ell, seed,
+                                          _ptr(core), _ptrs(factors), C.byref(err)))
+    return err.value
 
 
 def krp_sensor_select(ctx: Context, dims, ells, Qs, idxs, As):

@@ -570,15 +570,15 @@ def sensor_run(ctx, dev, stream, args):
 
 def hadamard_run(ctx, dev, stream, args):
     """Recompression of the Hadamard product of two Tucker tensors (Sec. 5):
-    200^3 tensors with Tucker ranks 8 (the product has rank 64 per mode),
+    512^3 tensors with Tucker ranks 8 (the product has rank 64 per mode),
     l = 24.  Structured path (krp_tucker_hadamard, FP64, the product never
-    formed) against forming the 200^3 product on the device (FP32) and running
+    formed) against forming the 512^3 product on the device (FP32) and running
     krp_tucker_rhosvd (MEMO) on it.  CUDA events, mean of three calls after
     a warm-up; both errors as the library reports them."""
     import torch
     import paper_2507_23207_gb300 as K
     from synth import haar
-    dims, r, ell = (200, 200, 200), (8, 8, 8), 24
+    dims, r, ell = (512, 512, 512), (8, 8, 8), 24
     rng = np.random.default_rng(1108)
     g = rng.standard_normal(r)
     h = rng.standard_normal(r)
@@ -591,7 +591,7 @@ def hadamard_run(ctx, dev, stream, args):
     V = [to(v) for v in vs]
     core = torch.empty(ell ** 3, dtype=torch.float64, device=dev)
     facs = [torch.empty((ell, n), dtype=torch.float64, device=dev) for n in dims]
-    out = {"workload": "Hadamard product of two 200^3 Tucker tensors of rank 8 (product rank 64), l = 24"}
+    out = {"workload": "Hadamard product of two 512^3 Tucker tensors of rank 8 (product rank 64), l = 24"}
     err = [0.0]
 
     def structured():
@@ -604,7 +604,7 @@ def hadamard_run(ctx, dev, stream, args):
         # X, Y in torch layout (n3, n2, n1) from the FP64 cores and factors
         x = torch.einsum("cba,ic,jb,ka->ijk", G, U[2].T, U[1].T, U[0].T)
         y = torch.einsum("cba,ic,jb,ka->ijk", H, V[2].T, V[1].T, V[0].T)
-        z = (x * y).to(torch.float32)
+        z = (x * y).to(torch.float32).contiguous()
         c32 = torch.empty(ell ** 3, dtype=torch.float32, device=dev)
         f64 = [torch.empty(n * ell, dtype=torch.float64, device=dev) for n in dims]
         res = K.krp_tucker_rhosvd(ctx, z, dims, [ell] * 3, 0, 0, K.KRP_MEMO | K.KRP_RESIDUAL, c32, f64)
@@ -1015,7 +1015,7 @@ def main():
         torch.cuda.set_device(dev)
         stream = torch.cuda.current_stream(dev)
         ctx = K.Context(local_rank, stream.cuda_stream)
-        out = {"hadamard_200cubed": hadamard_run(ctx, dev, stream, args)}
+        out = {"hadamard_512cubed": hadamard_run(ctx, dev, stream, args)}
         ctx.close()
         print(json.dumps(out))
         return

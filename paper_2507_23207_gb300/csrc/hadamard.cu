@@ -66,39 +66,58 @@ struct PtrList {
   const double* p[KRP_MAXD];
 };
 
-// out[c_n + cd_n k] = sum_{c_j, j != n} C[c] prod_{j != n} P_j[c_j + cd_j k]
-__global__ void small_mttkrp_kernel(const double* __restrict__ C, int d, Dims8 cd, int n,
-                                    PtrList P, int ell, double* __restrict__ out) {
-  const int64_t cn = cd.v[n];
-  int64_t stride_n = 1, others = 1;
+// out[c_n + cd_n k] = sum_{c_j, j != n} C[c] prod_{j != n} P_j[c_j + cd_j k],
+// one CTA per output (c_n, k): the threads split the modes other than n and
+// j0 (the first mode other than n), and each runs the j0 index innermost
+// (no index arithmetic in the inner loop); block sum at the end.
+constexpr int kMtThreads = 128;
+__global__ void __launch_bounds__(kMtThreads)
+    small_mttkrp_kernel(const double* __restrict__ C, int d, Dims8 cd, int n, PtrList P, int ell,
+                        double* __restrict__ out) {
+  const int64_t e = blockIdx.x;
+  const int64_t c_n = e % cd.v[n];
+  const int k = (int)(e / cd.v[n]);
+  int64_t stride[KRP_MAXD];
+  int64_t st = 1;
   for (int j = 0; j < d; ++j) {
-    if (j < n) stride_n *= cd.v[j];
-    if (j != n) others *= cd.v[j];
+    stride[j] = st;
+    st *= cd.v[j];
   }
-  const int64_t total = cn * ell;
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
-       e += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t c_n = e % cn;
-    const int k = (int)(e / cn);
-    double acc = 0.0;
-    for (int64_t o = 0; o < others; ++o) {
-      // o enumerates the other indices, mode-1 fastest
-      int64_t rem = o, off = c_n * stride_n, st = 1;
+  double acc = 0.0;
+  if (d == 1) {
+    acc = threadIdx.x == 0 ? C[c_n] : 0.0;
+  } else {
+    const int j0 = n == 0 ? 1 : 0;
+    int64_t rest = 1;
+    for (int j = 0; j < d; ++j)
+      if (j != n && j != j0) rest *= cd.v[j];
+    const int64_t r0 = cd.v[j0], s0 = stride[j0];
+    const double* p0 = P.p[j0] + r0 * k;
+    for (int64_t o = threadIdx.x; o < rest; o += blockDim.x) {
+      int64_t rem = o, base = c_n * stride[n];
       double w = 1.0;
       for (int j = 0; j < d; ++j) {
-        if (j == n) {
-          st *= cd.v[j];
-          continue;
-        }
+        if (j == n || j == j0) continue;
         const int64_t cj = rem % cd.v[j];
         rem /= cd.v[j];
-        off += cj * st;
-        st *= cd.v[j];
+        base += cj * stride[j];
         w *= P.p[j][cj + cd.v[j] * k];
       }
-      acc = fma(C[off], w, acc);
+      const double* cp = C + base;
+      double part = 0.0;
+      for (int64_t c0 = 0; c0 < r0; ++c0) part = fma(cp[c0 * s0], p0[c0], part);
+      acc = fma(w, part, acc);
     }
-    out[e] = acc;
+  }
+  __shared__ double red[kMtThreads / 32];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < kMtThreads / 32; ++w) t += red[w];
+    out[e] = t;
   }
 }
 
@@ -223,7 +242,7 @@ void hadamard_rhosvd(int d, const int64_t* dims, const int* rg, const double* G,
   std::vector<QrJob> jobs(d);
   for (int n = 0; n < d; ++n) {
     double* M = ws.take<double>((size_t)cd[n] * ell);
-    small_mttkrp_kernel<<<hd_grid(cd[n] * ell), 256, 0, st>>>(C, d, cdd, n, P, ell, M);
+    small_mttkrp_kernel<<<(unsigned)(cd[n] * ell), kMtThreads, 0, st>>>(C, d, cdd, n, P, ell, M);
     check_launch("hadamard_mttkrp");
     double* Yn = ws.take<double>((size_t)dims[n] * ell);
     expand_rows_kernel<<<hd_grid(dims[n] * ell), 256, 0, st>>>(U[n], V[n], M, dims[n], rg[n],

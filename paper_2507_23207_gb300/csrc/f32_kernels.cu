@@ -657,6 +657,7 @@ __global__ void __launch_bounds__(256, 2)
   const int tid = threadIdx.x, gi = tid & 15, gs = tid >> 4;
   const int64_t i0 = (int64_t)blockIdx.y * TM;
   const int64_t ntile = (S + kRtS - 1) / kRtS;
+  const bool rows_full = i0 + TM <= n1;
   for (int q = tid; q < c * (TM / 4); q += 256) {
     const int k = q / (TM / 4), c4 = q % (TM / 4);
     const int64_t i = i0 + 4 * c4;
@@ -667,17 +668,23 @@ __global__ void __launch_bounds__(256, 2)
   auto issue = [&](int64_t t, int st) {
     if (t < ntile) {
       const int64_t s0 = t * kRtS;
+      const bool full = s0 + kRtS <= S;
       float* hs = Hs + st * kRtS * c;
       float* xs = Xs + st * kRtS * TM;
       for (int e = 4 * tid; e < kRtS * c; e += 4 * 256) {  // a copy stays within one s (c % 4 == 0)
-        const bool ok = s0 + e / c < S;
+        const bool ok = full || s0 + e / c < S;
         cp_async16(hs + e, ok ? (const void*)(H + c * s0 + e) : (const void*)H, ok);
       }
-      for (int q = tid; q < kRtS * (TM / 4); q += 256) {
-        const int sl = q / (TM / 4), c4 = q % (TM / 4);
-        const int64_t sg = s0 + sl, i = i0 + 4 * c4;
-        const bool ok = sg < S && i < n1;
-        cp_async16(xs + sl * TM + 4 * c4, ok ? (const void*)(X + i + n1 * sg) : (const void*)X, ok);
+      // X tile: thread tid copies the 4 rows at 4 (tid % 32) of columns
+      // tid / 32 + 8 v (no index division per copy)
+      const int c4 = tid & 31;
+      const bool row_ok = rows_full || i0 + 4 * c4 < n1;
+      const float* xp = X + i0 + 4 * c4 + n1 * (s0 + (tid >> 5));
+#pragma unroll
+      for (int v = 0; v < kRtS / 8; ++v) {
+        const int sl = (tid >> 5) + 8 * v;
+        const bool ok = row_ok && (full || s0 + sl < S);
+        cp_async16(xs + sl * TM + 4 * c4, ok ? (const void*)(xp + n1 * 8 * v) : (const void*)X, ok);
       }
     }
     cp_commit();  // possibly empty: keeps one group per tile slot
@@ -720,21 +727,39 @@ __global__ void __launch_bounds__(256, 2)
     }
     const int64_t s0 = t * kRtS;
     float d2 = 0.f, x2 = 0.f;
+    if (rows_full && s0 + kRtS <= S) {  // a full tile: no bounds checks
 #pragma unroll
-    for (int b = 0; b < 4; ++b) {
-      const int sl = 4 * gs + b;
-      if (s0 + sl >= S) continue;
+      for (int b = 0; b < 4; ++b) {
+        const int sl = 4 * gs + b;
 #pragma unroll
-      for (int half = 0; half < 2; ++half) {
-        const int64_t ib = i0 + half * 64 + 4 * gi;
-        const float4 xq = *reinterpret_cast<const float4*>(xs + sl * TM + half * 64 + 4 * gi);
-        const float xv[4] = {xq.x, xq.y, xq.z, xq.w};
+        for (int half = 0; half < 2; ++half) {
+          const float4 xq = *reinterpret_cast<const float4*>(xs + sl * TM + half * 64 + 4 * gi);
+          const float xv[4] = {xq.x, xq.y, xq.z, xq.w};
 #pragma unroll
-        for (int a = 0; a < 4; ++a) {
-          if (ib + a >= n1) continue;
-          const float df = xv[a] - xh[half * 4 + a][b];
-          d2 = fmaf(df, df, d2);
-          x2 = fmaf(xv[a], xv[a], x2);
+          for (int a = 0; a < 4; ++a) {
+            const float df = xv[a] - xh[half * 4 + a][b];
+            d2 = fmaf(df, df, d2);
+            x2 = fmaf(xv[a], xv[a], x2);
+          }
+        }
+      }
+    } else {
+#pragma unroll
+      for (int b = 0; b < 4; ++b) {
+        const int sl = 4 * gs + b;
+        if (s0 + sl >= S) continue;
+#pragma unroll
+        for (int half = 0; half < 2; ++half) {
+          const int64_t ib = i0 + half * 64 + 4 * gi;
+          const float4 xq = *reinterpret_cast<const float4*>(xs + sl * TM + half * 64 + 4 * gi);
+          const float xv[4] = {xq.x, xq.y, xq.z, xq.w};
+#pragma unroll
+          for (int a = 0; a < 4; ++a) {
+            if (ib + a >= n1) continue;
+            const float df = xv[a] - xh[half * 4 + a][b];
+            d2 = fmaf(df, df, d2);
+            x2 = fmaf(xv[a], xv[a], x2);
+          }
         }
       }
     }

@@ -130,6 +130,13 @@ size_t tc_workspace_bytes(int64_t n1, int64_t S, int L);
 // rows of several merged modes), w the T x L table of Khatri-Rao weights of
 // the rest.  Xlo (optional): the lo plane of a BF16 hi/lo X.
 bool tc_tree_supported(int64_t n1, int L);
+// FP32 TTM out[s + S*k] = sum_i X[i + n1*s] F[i + ldf*k] on the tensor cores
+// as three TF32 products (FP32-level error); needs n1 % 4 == 0, 16-byte X,
+// L <= 64.
+bool tc_gemm_tn_tf32_supported(int64_t n1, int64_t S, int L, const void* X);
+size_t tc_gemm_tn_tf32_workspace_bytes(int64_t n1, int L);
+void tc_gemm_tn_tf32(const float* X, int64_t n1, int64_t S, const float* F, int64_t ldf, int L,
+                     float* out);
 // workspace of the tree's C partials (beyond tc_workspace_bytes)
 size_t tc_tree_workspace_bytes(int64_t n1, int64_t n2, int64_t T, int L);
 void tc_tree_bf16(const __nv_bfloat16* X, int64_t n1, int64_t n2, int64_t T,

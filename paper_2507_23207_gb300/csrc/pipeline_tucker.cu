@@ -235,7 +235,11 @@ static int round_up16(int v) { return (v + 15) / 16 * 16; }
 void big_gemm_tn(const void* X, krp_dtype xt, int64_t n1, int64_t S, const float* Ff,
                  const __nv_bfloat16* Fhi, const __nv_bfloat16* Flo, int L, float* out) {
   if (xt == KRP_F32) {
-    gemm_tn_f32(static_cast<const float*>(X), n1, S, (int)n1, Ff, n1, L, out, S, false);
+    // tensor cores as three TF32 products where the shape allows, else FFMA
+    if (tc_gemm_tn_tf32_supported(n1, S, L, X))
+      tc_gemm_tn_tf32(static_cast<const float*>(X), n1, S, Ff, n1, L, out);
+    else
+      gemm_tn_f32(static_cast<const float*>(X), n1, S, (int)n1, Ff, n1, L, out, S, false);
   } else {
     tc_gemm_tn_bf16(static_cast<const __nv_bfloat16*>(X), n1, S, Fhi, Flo, L, out,
                     lo_plane(X, xt, n1 * S));
@@ -330,6 +334,8 @@ size_t sketch_workspace_bytes(const SketchArgs& a, bool, int tree_split) {
   b += mttkrp_first_f32_workspace_bytes(a.N / std::max<int64_t>(1, a.dims[0]), dmax);
   if (bf16_family(a.xt))
     b += tc_workspace_bytes(n1, a.N / n1, a.ell) + tree_ws_bytes(a.d, a.dims, a.ell, tree_split);
+  else
+    b += tc_gemm_tn_tf32_workspace_bytes(n1, a.ell);
   return b + (1 << 20);
 }
 
@@ -550,6 +556,8 @@ size_t multi_ttm_workspace_bytes(int d, const int64_t* dims, const int* cols, kr
   if (bf16_family(xt)) {
     b += tc_workspace_bytes(dims[0], N / dims[0], 2 * cols[0]);
     if (d >= 3) b += tc_workspace_bytes(dims[1], 1, 2 * cols[1]) + 2 * ws_bytes((size_t)dims[1] * cols[1], 2);
+  } else {
+    b += tc_gemm_tn_tf32_workspace_bytes(dims[0], cols[0]);
   }
   return b + (1 << 20);
 }
@@ -777,6 +785,8 @@ void tucker_pipeline(bool sequential, const void* X, krp_dtype xt, int d, const 
   need += sym_eig_workspace_bytes(d);
   if (bf16_family(xt))
     need += tc_workspace_bytes(dims[0], N / dims[0], 2 * ellmax) + tree_ws_bytes(d, dims, ellmax);
+  else
+    need += tc_gemm_tn_tf32_workspace_bytes(dims[0], ellmax);
   if (bf16_family(xt) && resid) need += tc_residual_workspace_bytes(dims[0], N / dims[0]);
   need += 4 << 20;
   ensure_workspace(c, need);

@@ -375,6 +375,238 @@ __global__ void __launch_bounds__(kThreads, 1)
 }
 
 // ----------------------------------------------------------------------------
+// FP32 TTM on the tensor cores as three TF32 products (kind::tf32):
+//   out[s + S*k] = sum_i X[i + n1*s] F[i, k]   (FP32 X, FP32 F, FP32 out)
+// Each FP32 value splits exactly as x = x_h + x_l, x_h = x with its low 13
+// mantissa bits cleared (the TF32 value an MMA reads from the FP32 word) and
+// x_l = x - x_h; then X F ~ X_h [F_h | F_l] + X_l F_h, dropping X_l F_l and
+// the truncation of the lo parts (each below 2^-20 |x| |f|), which is the
+// size of FP32 rounding over these sums.  A tile: 128 rows (s) x 32 K (i),
+// 128-byte FP32 rows by TMA; four converter warps write X_l beside it
+// (elementwise, so in the same swizzled layout) and release it to the MMA
+// warp through an mbarrier after a proxy fence.  B: the combined factor
+// buffer [F_h rows 0..L-1 | F_l rows Lp..Lp+L-1] (FP32, K = n1p contiguous).
+// Warps: 0 TMA producer, 1 TMEM + MMA issuer, 2-5 epilogue, 6-9 converters.
+constexpr int kBK32 = 32;                 // K elements per stage (128 B of FP32)
+constexpr int kTf32Threads = 320;
+
+__host__ __device__ constexpr uint32_t idesc_tf32(int M, int N) {
+  // D FP32 (bit 4), A and B TF32 (format 2 at bits 7-9 and 10-12), K-major
+  return (1u << 4) | (2u << 7) | (2u << 10) | (static_cast<uint32_t>(N >> 3) << 17) |
+         (static_cast<uint32_t>(M >> 4) << 24);
+}
+__device__ __forceinline__ void mma_tf32(uint32_t dtmem, uint64_t adesc, uint64_t bdesc,
+                                         uint32_t idesc, uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(dtmem),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+
+struct BarsT : Bars {
+  uint64_t lofull[8];
+};
+
+template <int N, int NS>
+__global__ void __launch_bounds__(kTf32Threads, 1)
+    tc_gemm_tn_tf32_kernel(const __grid_constant__ CUtensorMap mapA,
+                           const __grid_constant__ CUtensorMap mapB, int64_t S, int kchunks, int L,
+                           int Lp, float* __restrict__ out, int* status) {
+  constexpr uint32_t kABytes = kBM * kBK32 * 4;  // 16 KB
+  constexpr uint32_t kBBytes = N * kBK32 * 4;
+  constexpr uint32_t kStage = 2 * kABytes + kBBytes;
+  constexpr uint32_t kTmemCols = (2 * N <= 32) ? 32 : (2 * N <= 64) ? 64 : (2 * N <= 128) ? 128 : (2 * N <= 256) ? 256 : 512;
+  constexpr uint32_t kIdesc = idesc_tf32(kBM, N);
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  BarsT* bars = reinterpret_cast<BarsT*>(smem + NS * kStage);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t tiles = (S + kBM - 1) / kBM;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < NS; ++s) {
+      mbar_init(smem_u32(&bars->full[s]), 1);
+      mbar_init(smem_u32(&bars->empty[s]), 1);
+      mbar_init(smem_u32(&bars->lofull[s]), 128);
+    }
+    for (int a = 0; a < 2; ++a) {
+      mbar_init(smem_u32(&bars->tfull[a]), 1);
+      mbar_init(smem_u32(&bars->tempty[a]), 4);
+    }
+    mbar_init(smem_u32(&bars->drain), 1);
+    bars->abort_flag = 0;
+    bars->issued = 0;
+    bars->consumed = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  if (warp == 1) tmem_alloc(smem_u32(&bars->tmem_base), kTmemCols);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = bars->tmem_base;
+  volatile int* abort_flag = &bars->abort_flag;
+  const uint64_t lim = wait_limit(status);
+  const uint32_t idesc_lo = idesc_tf32(kBM, Lp);
+
+  if (warp == 0) {
+    if (lane == 0) {
+      int it = 0;
+      for (int64_t tile = blockIdx.x; tile < tiles && !*abort_flag; tile += gridDim.x) {
+        for (int kc = 0; kc < kchunks; ++kc, ++it) {
+          const int st = it % NS;
+          const uint32_t ph = (it / NS) & 1;
+          if (!mbar_wait(smem_u32(&bars->empty[st]), ph ^ 1, abort_flag, lim)) {
+            raise_timeout(bars, status);
+            break;
+          }
+          const uint32_t a = smem_u32(smem + st * kStage);
+          const uint32_t fb = smem_u32(&bars->full[st]);
+          mbar_expect_tx(fb, kABytes + kBBytes);
+          tma_load_2d(a, &mapA, fb, kc * kBK32, static_cast<int>(tile * kBM));
+          tma_load_2d(a + 2 * kABytes, &mapB, fb, kc * kBK32, 0);
+          bars->issued = it + 1;
+        }
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      int it = 0, tl = 0;
+      for (int64_t tile = blockIdx.x; tile < tiles && !*abort_flag; tile += gridDim.x, ++tl) {
+        const int acc = tl & 1;
+        const uint32_t aph = (tl >> 1) & 1;
+        if (!mbar_wait(smem_u32(&bars->tempty[acc]), aph ^ 1, abort_flag, lim)) {
+          raise_timeout(bars, status);
+          break;
+        }
+        tc_fence_after();
+        const uint32_t dt = tmem + acc * N;
+        bool ok = true;
+        for (int kc = 0; kc < kchunks; ++kc, ++it) {
+          const int st = it % NS;
+          const uint32_t ph = (it / NS) & 1;
+          if (!mbar_wait(smem_u32(&bars->full[st]), ph, abort_flag, lim) ||
+              !mbar_wait(smem_u32(&bars->lofull[st]), ph, abort_flag, lim)) {
+            raise_timeout(bars, status);
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const uint32_t a = smem_u32(smem + st * kStage);
+          const uint32_t b = a + 2 * kABytes;
+#pragma unroll
+          for (int k = 0; k < kBK32 / 8; ++k) {
+            mma_tf32(dt, sdesc(a + 32 * k, 16, 1024), sdesc(b + 32 * k, 16, 1024), kIdesc,
+                     (kc | k) != 0);
+            // X_l times the hi columns of F (the first Lp rows of B)
+            mma_tf32(dt, sdesc(a + kABytes + 32 * k, 16, 1024), sdesc(b + 32 * k, 16, 1024),
+                     idesc_lo, 1);
+          }
+          mma_commit(smem_u32(&bars->empty[st]));
+          bars->consumed = it + 1;
+        }
+        if (!ok) break;
+        mma_commit(smem_u32(&bars->tfull[acc]));
+      }
+      // all MMAs issued by this thread have completed once this commit fires
+      mma_commit(smem_u32(&bars->drain));
+      int dummy = 0;
+      mbar_wait(smem_u32(&bars->drain), 0, reinterpret_cast<volatile int*>(&dummy));
+    }
+  } else if (warp < 6) {
+    const int q = warp & 3;  // TMEM lane quarter of this warp
+    int tl = 0;
+    for (int64_t tile = blockIdx.x; tile < tiles; tile += gridDim.x, ++tl) {
+      const int acc = tl & 1;
+      const uint32_t ph = (tl >> 1) & 1;
+      if (!mbar_wait(smem_u32(&bars->tfull[acc]), ph, abort_flag, lim)) {
+        if (lane == 0) raise_timeout(bars, status);
+        break;
+      }
+      tc_fence_after();
+      const int row = q * 32 + lane;
+      const int64_t s = tile * kBM + row;
+      const uint32_t base = tmem + (static_cast<uint32_t>(q * 32) << 16) + acc * N;
+      for (int c0 = 0; c0 < Lp; c0 += 16) {
+        float v[16], w[16];
+        tmem_ld16(base + c0, v);
+        tmem_ld16(base + Lp + c0, w);
+        if (s < S) {
+#pragma unroll
+          for (int j = 0; j < 16; ++j)
+            if (c0 + j < L) out[s + S * (c0 + j)] = v[j] + w[j];
+        }
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(smem_u32(&bars->tempty[acc]));
+    }
+  } else {
+    // converters: X_l = X - X_h of each landed A tile, written beside it
+    const int ct = threadIdx.x - 6 * 32;  // 0..127
+    int it = 0;
+    bool ok = true;
+    for (int64_t tile = blockIdx.x; tile < tiles && ok; tile += gridDim.x) {
+      for (int kc = 0; kc < kchunks; ++kc, ++it) {
+        const int st = it % NS;
+        const uint32_t ph = (it / NS) & 1;
+        if (!mbar_wait(smem_u32(&bars->full[st]), ph, abort_flag, lim)) {
+          raise_timeout(bars, status);
+          ok = false;
+          break;
+        }
+        const float4* src = reinterpret_cast<const float4*>(smem + st * kStage);
+        float4* dst = reinterpret_cast<float4*>(smem + st * kStage + kABytes);
+#pragma unroll
+        for (int j = 0; j < (int)(kABytes / 16 / 128); ++j) {
+          const float4 x = src[ct + 128 * j];
+          float4 l;
+          l.x = x.x - __uint_as_float(__float_as_uint(x.x) & 0xFFFFE000u);
+          l.y = x.y - __uint_as_float(__float_as_uint(x.y) & 0xFFFFE000u);
+          l.z = x.z - __uint_as_float(__float_as_uint(x.z) & 0xFFFFE000u);
+          l.w = x.w - __uint_as_float(__float_as_uint(x.w) & 0xFFFFE000u);
+          dst[ct + 128 * j] = l;
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        mbar_arrive(smem_u32(&bars->lofull[st]));
+      }
+    }
+  }
+  __syncthreads();
+  if (warp == 0 && lane == 0 && bars->abort_flag) drain_loads<NS>(bars);
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    tmem_dealloc(tmem, kTmemCols);
+  }
+}
+
+// Combined FP32 factor buffer for the TF32 TTM: Fc[r * n1p + i], r < N:
+// rows 0..L-1 the F_h part, rows Lp..Lp+L-1 the F_l part of F[i + ldf*r],
+// zeros elsewhere and for i >= n1.
+__global__ void pack_factor_tf32_kernel(const float* __restrict__ F, int64_t ldf, int64_t n1,
+                                        int64_t n1p, int L, int Lp, int N,
+                                        float* __restrict__ out) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n1p * N;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = e % n1p;
+    const int r = static_cast<int>(e / n1p);
+    float v = 0.f;
+    if (i < n1) {
+      if (r < L) {
+        v = F[i + ldf * r];
+      } else if (r >= Lp && r - Lp < L) {
+        const float f = F[i + ldf * (r - Lp)];
+        v = f - __uint_as_float(__float_as_uint(f) & 0xFFFFE000u);
+      }
+    }
+    out[e] = v;
+  }
+}
+
+// ----------------------------------------------------------------------------
 // Y[i + n1*k] += sum_{t in range} w[t + T*k] * D_t[i, k],
 // D_t[i, k] = sum_{i2} X[i, i2, t] Om2[i2, k]   (MN-major A, two 64-row boxes)
 // XLO: X as a BF16 hi/lo pair; the lo boxes (map mapXlo) are multiplied by
@@ -1333,10 +1565,11 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
 }
 
 CUtensorMap make_map(const void* base, int rank, const uint64_t* dims, const uint64_t* strides_bytes,
-                     const uint32_t* box) {
+                     const uint32_t* box,
+                     CUtensorMapDataType dtype = CU_TENSOR_MAP_DATA_TYPE_BFLOAT16) {
   CUtensorMap m;
   uint32_t estr[3] = {1, 1, 1};
-  const CUresult r = encode_fn()(&m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, rank, const_cast<void*>(base),
+  const CUresult r = encode_fn()(&m, dtype, rank, const_cast<void*>(base),
                                  dims, strides_bytes, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
                                  CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
@@ -1471,6 +1704,61 @@ void tc_gemm_tn_bf16(const __nv_bfloat16* X, int64_t n1, int64_t S, const __nv_b
       else if (N == 208) launch_gemm_tn<208>(ma, malo, mb, S, kchunks, L, Lp, has_lo, out, outb);
       else if (N == 240) launch_gemm_tn<240>(ma, malo, mb, S, kchunks, L, Lp, has_lo, out, outb);
       else fail(KRP_EUNSUPPORTED, "unsupported MMA width %d", N);
+  }
+}
+
+namespace {
+template <int N>
+void launch_gemm_tf32(const CUtensorMap& ma, const CUtensorMap& mb, int64_t S, int kchunks, int L,
+                      int Lp, float* out) {
+  const int64_t tiles = (S + kBM - 1) / kBM;
+  const int grid = static_cast<int>(std::min<int64_t>(tiles, current()->num_sms));
+  constexpr int NS = (N <= 64) ? 5 : 4;
+  const size_t smem = 1024 + NS * (size_t)(2 * kBM * kBK32 * 4 + N * kBK32 * 4) + sizeof(BarsT) + 64;
+  set_smem(tc_gemm_tn_tf32_kernel<N, NS>, smem);
+  tc_gemm_tn_tf32_kernel<N, NS><<<grid, kTf32Threads, smem, stream()>>>(ma, mb, S, kchunks, L, Lp,
+                                                                          out, current()->d_status);
+  check_launch("tc_gemm_tn_tf32");
+}
+}  // namespace
+
+bool tc_gemm_tn_tf32_supported(int64_t n1, int64_t S, int L, const void* X) {
+  return n1 % 4 == 0 && n1 <= (int64_t(1) << 30) && S < (int64_t(1) << 31) && L >= 1 && L <= 64 &&
+         (reinterpret_cast<uintptr_t>(X) & 15) == 0;
+}
+
+size_t tc_gemm_tn_tf32_workspace_bytes(int64_t n1, int L) {
+  const int64_t n1p = (n1 + kBK32 - 1) / kBK32 * kBK32;
+  const int64_t Lp = (L + 15) / 16 * 16;
+  return ws_bytes((size_t)n1p * 2 * Lp, 4) + (1 << 12);
+}
+
+void tc_gemm_tn_tf32(const float* X, int64_t n1, int64_t S, const float* F, int64_t ldf, int L,
+                     float* out) {
+  KRP_REQUIRE(tc_gemm_tn_tf32_supported(n1, S, L, X), "TF32 TTM: unsupported shape or alignment");
+  const int Lp = round_up(L, 16);
+  const int N = 2 * Lp;
+  const int64_t n1p = round_up(n1, kBK32);
+  float* Fc = current()->ws.take<float>((size_t)n1p * N);
+  const int64_t tot = n1p * N;
+  pack_factor_tf32_kernel<<<(int)std::min<int64_t>((tot + 255) / 256, 4096), 256, 0, stream()>>>(
+      F, ldf, n1, n1p, L, Lp, N, Fc);
+  check_launch("pack_factor_tf32");
+  const uint64_t adims[2] = {(uint64_t)n1, (uint64_t)S};
+  const uint64_t astr[1] = {(uint64_t)n1 * 4};
+  const uint32_t abox[2] = {kBK32, kBM};
+  const CUtensorMap ma = make_map(X, 2, adims, astr, abox, CU_TENSOR_MAP_DATA_TYPE_FLOAT32);
+  const uint64_t bdims[2] = {(uint64_t)n1p, (uint64_t)N};
+  const uint64_t bstr[1] = {(uint64_t)n1p * 4};
+  const uint32_t bbox[2] = {kBK32, (uint32_t)N};
+  const CUtensorMap mb = make_map(Fc, 2, bdims, bstr, bbox, CU_TENSOR_MAP_DATA_TYPE_FLOAT32);
+  const int kchunks = static_cast<int>((n1 + kBK32 - 1) / kBK32);
+  switch (N) {
+    case 32: launch_gemm_tf32<32>(ma, mb, S, kchunks, L, Lp, out); break;
+    case 64: launch_gemm_tf32<64>(ma, mb, S, kchunks, L, Lp, out); break;
+    case 96: launch_gemm_tf32<96>(ma, mb, S, kchunks, L, Lp, out); break;
+    case 128: launch_gemm_tf32<128>(ma, mb, S, kchunks, L, Lp, out); break;
+    default: fail(KRP_EUNSUPPORTED, "unsupported TF32 MMA width %d", N);
   }
 }
 

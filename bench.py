@@ -649,42 +649,76 @@ def nystrom_run(ctx, dev, stream, reps, warm):
     return out
 
 
-# DRAM traffic (read + write bytes) of one big launch of the dominant kernel
-# at 1024^3: an ncu capture at 512^3 measured 537.0 MB read (X once) and
-# 43.0 MB write (the (N/n1) x l output); X scales x8 and the output x4 to
-# 1024^3.  Set to None if the kernel changes.
-TTM48_TRAFFIC_PER_BIG_LAUNCH = 537.0e6 * 8 + 43.0e6 * 4
+# DRAM traffic (read + write bytes) per launch at 1024^3, from ncu captures at
+# 512^3 scaled by the bytes each part moves (X x8, per-CTA partials of Y1 x2):
+# the slab MTTKRP read 537.3 MB and wrote 3.6 MB there.  None where no capture
+# of the current kernel exists.
+TRAFFIC_1024 = {"krp_slab_mttkrp_f32": 537.3e6 * 8 + 3.6e6 * 2}
+
+
+def _kernel_work(name, spec):
+    """(kernel, bound, unit, algorithmic work per launch) of the kernels of the
+    FP32 step that can dominate it."""
+    n, ell = spec.numel, max(spec.ell)
+    r = min(spec.ranks)
+    if name == "krp_slab_mttkrp_f32":
+        return ("krp_slab_mttkrp_kernel<48> (FP32 mode-1 sketch Y_1 = X_(1)(Omega_3 kr Omega_2), FFMA)",
+                "alu", "TFLOP/s", 2.0 * n * ell)
+    if name == "residual":
+        return ("residual_tiled_kernel (FP32 residual ||X - Q_1 H||, FFMA)", "alu", "TFLOP/s",
+                2.0 * n * r)
+    if name == "tc_gemm_tn_tf32":
+        return ("tc_gemm_tn_tf32_kernel (FP32 TTM X_(1)^T F on tcgen05, three TF32 products)",
+                "hbm", "GB/s", n * 4.0 + n / spec.dims[0] * ell * 4.0)
+    return None
 
 
 def trace_roofline(spec, f32, peaks, args):
-    """Roofline of the dominant kernel of the FP32 step, the tiled TTM
-    gemm_tn_tile<48> (~43% of the step in the ncu launch list).  Each step
-    launches it four times: the dimension tree's B-part (X_(1)^T Omega_1) and
-    the core's first TTM (X_(1)^T Q_1) -- both a contraction of the whole
-    1024 x 1024^2 X with a 1024 x 48 factor -- then the core's TTMs on the
-    48 x 1024^2 and 48^2 x 1024 intermediates.  The object covers the two big
-    launches (2 N l flops, one read of X each), timed live by the launch
-    trace (events on the context stream) over the timed steps."""
-    n, ell = spec.numel, max(spec.ell)
+    """Roofline of the dominant kernel of the FP32 step: the kernel with the
+    largest share of the step in the launch trace (CUDA events after every
+    launch on the context stream over the timed steps), among the slab
+    MTTKRP (mode-1 sketch, 2 N l flops), the residual (2 N r flops) and the
+    tensor-core TF32 TTM (X read once).  `achieved` = its algorithmic work
+    per launch / its average launch time."""
     tr = f32.get("trace") or []
-    ttm = [t for name, t in tr if name == "gemm_tn_tile<48>"]
+    step_ms = sum(t for _, t in tr) / max(1, args.steps)
+    tot = {}
+    for name, t in tr:
+        if _kernel_work(name, spec):
+            tot.setdefault(name, []).append(t)
+    if not tot or step_ms <= 0:
+        return {"error": "no traced kernel of the FP32 step"}
+    name = max(tot, key=lambda k: sum(tot[k]))
+    label, bound, unit, work = _kernel_work(name, spec)
+    times = tot[name]
+    t_avg = sum(times) / len(times)
     mhz = (f32.get("clocks") or {}).get("sm_max_mhz") or peaks.get("sm_max_mhz", 2070.0)
     sms = sm_count()
-    peak = fp32_ffma_peak_tflops(mhz, sms)
-    if len(ttm) != 4 * args.steps:
-        return {"kernel": "gemm_tn_tile_kernel<48>", "error": f"trace saw {len(ttm)} launches"}
-    big = [t for i, t in enumerate(ttm) if i % 4 < 2]
-    t_big = sum(big) / len(big)
-    ach = 2.0 * n * ell / (t_big * 1e-3) / 1e12
-    step_ms = sum(t for _, t in tr) / args.steps
-    return {"kernel": "gemm_tn_tile_kernel<48> (FP32 TTM of X with a 1024 x 48 factor)",
-            "bound": "alu", "achieved": round(ach, 3), "peak": round(peak, 3), "unit": "TFLOP/s",
-            "frac": round(ach / peak, 4), "traffic": TTM48_TRAFFIC_PER_BIG_LAUNCH,
-            "algorithmic_bytes": n * 4 + n / spec.dims[0] * ell * 4,
-            "ms_per_launch": round(t_big, 4), "launches_averaged": len(big),
-            "kernel_share_of_step": round(sum(ttm) / args.steps / step_ms, 4),
-            "peak_note": f"FP32 FFMA peak = {sms} SMs x 128 lanes x 2 flop x {mhz:.0f} MHz",
-            "timing": "CUDA events after every launch on the context stream over the timed steps"}
+    if bound == "alu":
+        peak = fp32_ffma_peak_tflops(mhz, sms)
+        ach = work / (t_avg * 1e-3) / 1e12
+        note = f"FP32 FFMA peak = {sms} SMs x 128 lanes x 2 flop x {mhz:.0f} MHz"
+    else:
+        peak = peaks["hbm_gbs"]
+        ach = work / (t_avg * 1e-3) / 1e9
+        note = "hbm_gbs of MEASURED_PEAKS.json"
+    out = {"kernel": label, "bound": bound, "achieved": round(ach, 3), "peak": round(peak, 3),
+           "unit": unit, "frac": round(ach / peak, 4), "traffic": TRAFFIC_1024.get(name),
+           "ms_per_launch": round(t_avg, 4), "launches_averaged": len(times),
+           "kernel_share_of_step": round(sum(times) / args.steps / step_ms, 4),
+           "peak_note": note,
+           "timing": "CUDA events after every launch on the context stream over the timed steps"}
+    # the tensor-core TTM beside it (two launches per step: tree B-part, core)
+    if "tc_gemm_tn_tf32" in tot and name != "tc_gemm_tn_tf32":
+        _, _, _, w = _kernel_work("tc_gemm_tn_tf32", spec)
+        big = sorted(tot["tc_gemm_tn_tf32"])[-2 * args.steps:]
+        tb = sum(big) / len(big)
+        gbs = w / (tb * 1e-3) / 1e9
+        out["tf32_ttm"] = {"kernel": "tc_gemm_tn_tf32_kernel (X_(1)^T F, X FP32 1024 x 1024^2)",
+                           "bound": "hbm", "achieved": round(gbs, 1), "peak": peaks["hbm_gbs"],
+                           "unit": "GB/s", "frac": round(gbs / peaks["hbm_gbs"], 4),
+                           "ms_per_launch": round(tb, 4), "launches_averaged": len(big)}
+    return out
 
 
 def sketch_rooflines(ctx, spec, forms, dev, stream, peaks, clk, args):

@@ -723,8 +723,10 @@ def trace_roofline(spec, f32, peaks, args):
 
 def sketch_rooflines(ctx, spec, forms, dev, stream, peaks, clk, args):
     """The all-mode KRP sketch alone (krp_sketch_all_modes with the memoized
-    factor set, Sec. 5.1) in each form, against its own roofline: FP32 on CUDA
-    cores (4 N l flops against the FFMA peak), the BF16 and BF16 hi/lo forms
+    factor set, Sec. 5.1) in each form, against its own roofline: FP32 as the
+    slab MTTKRP on CUDA cores (2 N l flops against the FFMA peak) followed by
+    the TTM on tensor cores (one read of X against the measured HBM
+    bandwidth), the sum of the two minimum times; the BF16 and BF16 hi/lo forms
     on tensor cores (one pass over X against the measured HBM bandwidth;
     their 4 N l flops need well under the tensor peak).  The kernels of one
     call and their times come from the launch trace."""
@@ -763,7 +765,19 @@ def sketch_rooflines(ctx, spec, forms, dev, stream, peaks, clk, args):
              "bytes_per_elem": b, "kernels_ms": {k: round(v, 4) for k, v in
                                                  sorted(agg.items(), key=lambda kv: -kv[1])}}
         t_top = agg[top]
-        if form == "f32":
+        if form == "f32" and "tc_gemm_tn_tf32" in agg:
+            # two sequential parts: the slab MTTKRP (2 N l flops on FFMA) and
+            # the TTM X_(1)^T Omega_1 on tensor cores (one read of X, HBM)
+            t_min = 2.0 * n * ell / (ffma * 1e12) * 1e3 + n * 4.0 / (hbm * 1e9) * 1e3
+            e["roofline"] = {"bound": "alu+hbm", "t_min_ms": round(t_min, 4),
+                             "frac": round(t_min / ms, 4),
+                             "peak_note": f"t_min = 2 N l / FFMA peak ({ffma:.1f} TFLOP/s: {sms} SMs "
+                                          f"x 128 lanes x 2 flop x {mhz:.0f} MHz) + 4 N bytes / "
+                                          "hbm_gbs of MEASURED_PEAKS.json"}
+            e["dominant_kernel"] = {"name": top, "ms": round(t_top, 4),
+                                    "tflops": round(2.0 * n * ell / (t_top * 1e-3) / 1e12, 3),
+                                    "frac": round(2.0 * n * ell / (t_top * 1e-3) / 1e12 / ffma, 4)}
+        elif form == "f32":
             e["roofline"] = {"bound": "alu", "achieved": round(tfl, 3), "peak": round(ffma, 3),
                              "unit": "TFLOP/s", "frac": round(tfl / ffma, 4),
                              "peak_note": f"FP32 FFMA peak = {sms} SMs x 128 lanes x 2 flop x "

@@ -134,6 +134,12 @@ bool tc_tree_supported(int64_t n1, int L);
 // as three TF32 products (FP32-level error); needs n1 % 4 == 0, 16-byte X,
 // L <= 64.
 bool tc_gemm_tn_tf32_supported(int64_t n1, int64_t S, int L, const void* X);
+// FP32 residual on the tensor cores (TF32 hi/lo products of H and Q1, FP32
+// comparison with X): needs n1 % 4 == 0, 16-byte X, c <= 32.
+bool tc_residual_tf32_supported(int64_t n1, int64_t S, int c, const void* X);
+size_t tc_residual_tf32_workspace_bytes(int64_t n1, int64_t S);
+void tc_residual_tf32(const float* X, int64_t n1, int64_t S, const double* Q1, int c, const float* H,
+                      double* acc);
 size_t tc_gemm_tn_tf32_workspace_bytes(int64_t n1, int L);
 void tc_gemm_tn_tf32(const float* X, int64_t n1, int64_t S, const float* F, int64_t ldf, int L,
                      float* out);

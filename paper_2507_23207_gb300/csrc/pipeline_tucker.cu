@@ -676,6 +676,7 @@ size_t residual_workspace_bytes(int d, const int64_t* dims, const int64_t* cdim,
   }
   b += ws_bytes((size_t)cl, 4);
   if (bf16_family(xt)) b += tc_residual_workspace_bytes(dims[0], N / dims[0]);
+  if (xt == KRP_F32) b += tc_residual_tf32_workspace_bytes(dims[0], N / dims[0]);
   return b + (1 << 16);
 }
 
@@ -714,6 +715,9 @@ void residual_sums(const void* Xd, krp_dtype xt, int d, const int64_t* dims, con
                      (int)cdim[0], curh, acc, lo_plane(Xd, xt, N));
   else if (xt == KRP_BF16X2)
     fail(KRP_EUNSUPPORTED, "BF16 hi/lo residual needs n_1 %% 8 == 0 and at most 64 columns");
+  else if (xt == KRP_F32 && tc_residual_tf32_supported(dims[0], N / dims[0], (int)cdim[0], Xd))
+    tc_residual_tf32(static_cast<const float*>(Xd), dims[0], N / dims[0], Qout[0], (int)cdim[0], curh,
+                     acc);
   else
     residual_f32(Xd, xt, dims[0], N / dims[0], Q1f, (int)cdim[0], curh, acc);
 }
@@ -788,6 +792,7 @@ void tucker_pipeline(bool sequential, const void* X, krp_dtype xt, int d, const 
   else
     need += tc_gemm_tn_tf32_workspace_bytes(dims[0], ellmax);
   if (bf16_family(xt) && resid) need += tc_residual_workspace_bytes(dims[0], N / dims[0]);
+  if (xt == KRP_F32 && resid) need += tc_residual_tf32_workspace_bytes(dims[0], N / dims[0]);
   need += 4 << 20;
   ensure_workspace(c, need);
   Workspace& ws = c->ws;

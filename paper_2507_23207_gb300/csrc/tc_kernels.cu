@@ -583,6 +583,206 @@ __global__ void __launch_bounds__(kTf32Threads, 1)
   }
 }
 
+// Residual of the FP32 form on the tensor cores: acc[0] += ||X - Q1 H||_F^2,
+// acc[1] += ||X||_F^2 for FP32 X (n1 x S) and c <= 32.  Same orientation as
+// the BF16 residual (the tile is X_hat^T[s, i], A = H with M = s, B = Q1 with
+// N = i), with FP32 operands split into TF32 hi and lo parts (rows of
+// [hi 32 | lo 32], 256 bytes) and X_hat^T = Hh Qh^T + Hl Qh^T + Hh Ql^T
+// (kind::tf32; the dropped Hl Ql^T and the truncation of the lo parts are
+// below 2^-20 relative).  A stage holds Hh, Hl (128 x 32 FP32 each) and the X
+// tile as four TMA boxes of 32 (i) x 128 (s) FP32; an epilogue thread owns
+// one s and compares 16 consecutive i per TMEM load, four 16-byte chunks of
+// one box row (chunks swizzled by s mod 8).  A CTA keeps the 128-row block of
+// Q1 (hi and lo, 32 KB) resident; release of a stage as in the BF16 form.
+__global__ void __launch_bounds__(kThreads, 1)
+    tc_residual_tf32_kernel(const __grid_constant__ CUtensorMap mapX,
+                            const __grid_constant__ CUtensorMap mapQ,
+                            const __grid_constant__ CUtensorMap mapH, int64_t n1, int64_t S,
+                            int mblocks, int cpm, double* __restrict__ acc, int* status) {
+  constexpr int NS = 2;
+  constexpr uint32_t kOp = 128 * 32 * 4;    // one 128-row x 32-element FP32 operand tile (16 KB)
+  constexpr uint32_t kXBox = 32 * 128 * 4;  // 32 (i) x 128 (s) FP32 (16 KB)
+  constexpr uint32_t kStage = 2 * kOp + 4 * kXBox;  // Hh Hl + X boxes (96 KB)
+  constexpr uint32_t kTmemCols = 256;
+  constexpr uint32_t kIdesc = idesc_tf32(kBM, 128);
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  uint8_t* qres = smem + NS * kStage;  // Qh, Ql of this CTA's row block
+  Bars* bars = reinterpret_cast<Bars*>(qres + 2 * kOp);
+  __shared__ uint64_t qbar;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t sblocks = (S + 127) / 128;
+  const int mb = static_cast<int>(blockIdx.x % mblocks);
+  const int64_t sb0 = blockIdx.x / mblocks;  // this CTA's tiles: sb0, sb0 + cpm, ...
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < NS; ++s) {
+      mbar_init(smem_u32(&bars->full[s]), 1);
+      mbar_init(smem_u32(&bars->empty[s]), 1 + 4);  // MMA commit + four epilogue warps
+    }
+    for (int a = 0; a < 2; ++a) {
+      mbar_init(smem_u32(&bars->tfull[a]), 1);
+      mbar_init(smem_u32(&bars->tempty[a]), 4);
+    }
+    mbar_init(smem_u32(&bars->drain), 1);
+    mbar_init(smem_u32(&qbar), 1);
+    bars->abort_flag = 0;
+    bars->issued = 0;
+    bars->consumed = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  if (warp == 1) tmem_alloc(smem_u32(&bars->tmem_base), kTmemCols);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = bars->tmem_base;
+  volatile int* abort_flag = &bars->abort_flag;
+  const uint64_t lim = wait_limit(status);
+
+  if (warp == 0) {
+    if (lane == 0) {
+      const uint32_t qb = smem_u32(&qbar);
+      mbar_expect_tx(qb, 2 * kOp);
+      tma_load_2d(smem_u32(qres), &mapQ, qb, 0, mb * kBM);          // Qh
+      tma_load_2d(smem_u32(qres + kOp), &mapQ, qb, 32, mb * kBM);   // Ql
+      int it = 0;
+      for (int64_t sb = sb0; sb < sblocks && !*abort_flag; sb += cpm, ++it) {
+        const int st = it % NS;
+        const uint32_t ph = (it / NS) & 1;
+        if (!mbar_wait(smem_u32(&bars->empty[st]), ph ^ 1, abort_flag, lim)) {
+          raise_timeout(bars, status);
+          break;
+        }
+        const uint32_t a = smem_u32(smem + st * kStage);
+        const uint32_t fb = smem_u32(&bars->full[st]);
+        mbar_expect_tx(fb, kStage);
+        const int s0 = static_cast<int>(sb * 128);
+        tma_load_2d(a, &mapH, fb, 0, s0);                             // Hh
+        tma_load_2d(a + kOp, &mapH, fb, 32, s0);                      // Hl
+#pragma unroll
+        for (int j = 0; j < 4; ++j)                                   // X, i 32 j .. 32 j + 31
+          tma_load_2d(a + 2 * kOp + j * kXBox, &mapX, fb, mb * kBM + 32 * j, s0);
+        bars->issued = it + 1;
+      }
+      // the resident Q load must land before the CTA can exit
+      int dummy = 0;
+      mbar_wait(qb, 0, reinterpret_cast<volatile int*>(&dummy));
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      bool ok = mbar_wait(smem_u32(&qbar), 0, abort_flag, lim);
+      if (!ok) raise_timeout(bars, status);
+      int it = 0;
+      for (int64_t sb = sb0; ok && sb < sblocks && !*abort_flag; sb += cpm, ++it) {
+        const int st = it % NS;
+        const uint32_t ph = (it / NS) & 1;
+        const int accb = it & 1;
+        const uint32_t aph = (it >> 1) & 1;
+        if (!mbar_wait(smem_u32(&bars->tempty[accb]), aph ^ 1, abort_flag, lim) ||
+            !mbar_wait(smem_u32(&bars->full[st]), ph, abort_flag, lim)) {
+          raise_timeout(bars, status);
+          break;
+        }
+        tc_fence_after();
+        const uint32_t a = smem_u32(smem + st * kStage);
+        const uint32_t dt = tmem + accb * 128;
+        const uint32_t hh = a, hl = a + kOp, qh = smem_u32(qres), ql = qh + kOp;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          mma_tf32(dt, sdesc(hh + 32 * k, 16, 1024), sdesc(qh + 32 * k, 16, 1024), kIdesc, k != 0);
+          mma_tf32(dt, sdesc(hl + 32 * k, 16, 1024), sdesc(qh + 32 * k, 16, 1024), kIdesc, 1);
+          mma_tf32(dt, sdesc(hh + 32 * k, 16, 1024), sdesc(ql + 32 * k, 16, 1024), kIdesc, 1);
+        }
+        mma_commit(smem_u32(&bars->empty[st]));
+        mma_commit(smem_u32(&bars->tfull[accb]));
+        bars->consumed = it + 1;
+      }
+      mma_commit(smem_u32(&bars->drain));
+      int dummy = 0;
+      mbar_wait(smem_u32(&bars->drain), 0, reinterpret_cast<volatile int*>(&dummy));
+    }
+  } else {
+    const int q = warp & 3;
+    const int srow = q * 32 + lane;  // s within the tile (TMEM lane)
+    const uint32_t sw = static_cast<uint32_t>(srow & 7);
+    double dsum = 0.0, xsum = 0.0;
+    int it = 0;
+    for (int64_t sb = sb0; sb < sblocks; sb += cpm, ++it) {
+      const int st = it % NS;
+      const int accb = it & 1;
+      const uint32_t aph = (it >> 1) & 1;
+      if (!mbar_wait(smem_u32(&bars->tfull[accb]), aph, abort_flag, lim)) {
+        if (lane == 0) raise_timeout(bars, status);
+        break;
+      }
+      tc_fence_after();
+      const uint8_t* xrow = smem + st * kStage + 2 * kOp + srow * 128;
+      const uint32_t base = tmem + (static_cast<uint32_t>(q * 32) << 16) + accb * 128;
+      float d2 = 0.f, x2 = 0.f;
+#pragma unroll 1
+      for (int c0 = 0; c0 < 128; c0 += 16) {
+        float v[16];
+        tmem_ld16(base + c0, v);
+        const uint8_t* bx = xrow + (c0 >> 5) * kXBox;
+        const uint32_t j0 = static_cast<uint32_t>((c0 & 31) >> 2);
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const float4 xv = *reinterpret_cast<const float4*>(bx + (((j0 + u) ^ sw) << 4));
+          const float xs[4] = {xv.x, xv.y, xv.z, xv.w};
+#pragma unroll
+          for (int e = 0; e < 4; ++e) {
+            const float df = xs[e] - v[4 * u + e];
+            d2 = fmaf(df, df, d2);
+            x2 = fmaf(xs[e], xs[e], x2);
+          }
+        }
+      }
+      dsum += d2;
+      xsum += x2;
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) {
+        mbar_arrive(smem_u32(&bars->tempty[accb]));
+        mbar_arrive(smem_u32(&bars->empty[st]));
+      }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      dsum += __shfl_xor_sync(0xffffffffu, dsum, o);
+      xsum += __shfl_xor_sync(0xffffffffu, xsum, o);
+    }
+    if (lane == 0) {
+      atomicAdd(acc, dsum);
+      atomicAdd(acc + 1, xsum);
+    }
+  }
+  __syncthreads();
+  if (warp == 0 && lane == 0 && bars->abort_flag) drain_loads<NS>(bars);
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    tmem_dealloc(tmem, kTmemCols);
+  }
+}
+
+// rows of a K-major TF32 hi/lo pair: out[r * 64 + k] = v, out[r * 64 + 32 + k]
+// = v - (v with the low 13 mantissa bits cleared), for k < c (zero for
+// c <= k < 32), v = (float) src[k * ld_k + r * ld_r]
+template <class T>
+__global__ void pack_rows_tf32_kernel(const T* __restrict__ src, int64_t rows, int c, int64_t ld_k,
+                                      int64_t ld_r, float* __restrict__ out) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < rows * 32;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int k = static_cast<int>(e & 31);
+    const int64_t r = e >> 5;
+    float v = 0.f;
+    if (k < c) v = static_cast<float>(src[k * ld_k + r * ld_r]);
+    out[r * 64 + k] = v;
+    out[r * 64 + 32 + k] = v - __uint_as_float(__float_as_uint(v) & 0xFFFFE000u);
+  }
+}
+
 // Combined FP32 factor buffer for the TF32 TTM: Fc[r * n1p + i], r < N:
 // rows 0..L-1 the F_h part, rows Lp..Lp+L-1 the F_l part of F[i + ldf*r],
 // zeros elsewhere and for i >= n1.
@@ -1932,6 +2132,50 @@ void tc_residual_bf16(const __nv_bfloat16* X, int64_t n1, int64_t S, const doubl
     const CUtensorMap mxlo = make_map(Xlo, 2, xd, xs, xbox);
     launch_residual<true>(mx, mxlo, mq, Hp, n1, S, acc);
   }
+}
+
+size_t tc_residual_tf32_workspace_bytes(int64_t n1, int64_t S) {
+  return ws_bytes((size_t)S * 64, 4) + ws_bytes((size_t)n1 * 64, 4) + (1 << 16);
+}
+
+bool tc_residual_tf32_supported(int64_t n1, int64_t S, int c, const void* X) {
+  return n1 % 4 == 0 && c >= 1 && c <= 32 && S < (int64_t(1) << 31) && n1 < (int64_t(1) << 31) &&
+         (reinterpret_cast<uintptr_t>(X) & 15) == 0;
+}
+
+void tc_residual_tf32(const float* X, int64_t n1, int64_t S, const double* Q1, int c, const float* H,
+                      double* acc) {
+  KRP_REQUIRE(tc_residual_tf32_supported(n1, S, c, X), "TF32 residual: unsupported shape or alignment");
+  Ctx* ctx = current();
+  float* Qp = ctx->ws.take<float>((size_t)n1 * 64);
+  float* Hp = ctx->ws.take<float>((size_t)S * 64);
+  pack_rows_tf32_kernel<double><<<(int)std::min<int64_t>((n1 * 32 + 255) / 256, 4096), 256, 0, stream()>>>(
+      Q1, n1, c, n1, 1, Qp);
+  check_launch("pack_rows_tf32");
+  pack_rows_tf32_kernel<float><<<(int)std::min<int64_t>((S * 32 + 255) / 256, 8192), 256, 0, stream()>>>(
+      H, S, c, 1, c, Hp);
+  check_launch("pack_rows_tf32");
+  const uint64_t xd[2] = {(uint64_t)n1, (uint64_t)S};
+  const uint64_t xs[1] = {(uint64_t)n1 * 4};
+  const uint32_t xbox[2] = {32, 128};
+  const CUtensorMap mx = make_map(X, 2, xd, xs, xbox, CU_TENSOR_MAP_DATA_TYPE_FLOAT32);
+  const uint64_t qd[2] = {64, (uint64_t)n1};
+  const uint64_t qs[1] = {256};
+  const uint32_t qbox[2] = {32, kBM};
+  const CUtensorMap mq = make_map(Qp, 2, qd, qs, qbox, CU_TENSOR_MAP_DATA_TYPE_FLOAT32);
+  const uint64_t hd[2] = {64, (uint64_t)S};
+  const uint64_t hs[1] = {256};
+  const uint32_t hbox[2] = {32, 128};
+  const CUtensorMap mh = make_map(Hp, 2, hd, hs, hbox, CU_TENSOR_MAP_DATA_TYPE_FLOAT32);
+  const int mblocks = static_cast<int>((n1 + kBM - 1) / kBM);
+  const int64_t sblocks = (S + 127) / 128;
+  const int cpm = static_cast<int>(std::max<int64_t>(1, std::min<int64_t>(sblocks, ctx->num_sms / mblocks)));
+  const size_t stage = 2 * (size_t)128 * 32 * 4 + 4 * (size_t)32 * 128 * 4;
+  const size_t smem = 1024 + 2 * stage + 2 * (size_t)128 * 32 * 4 + sizeof(Bars) + 64;
+  set_smem(tc_residual_tf32_kernel, smem);
+  tc_residual_tf32_kernel<<<cpm * mblocks, kThreads, smem, stream()>>>(mx, mq, mh, n1, S, mblocks, cpm,
+                                                                       acc, ctx->d_status);
+  check_launch("tc_residual_tf32");
 }
 
 void tc_mttkrp_first_bf16(const __nv_bfloat16* X, int64_t n1, int64_t n2, int64_t T,

@@ -35,7 +35,14 @@ column), so its cosine with the fixed residual r is at most 4 / sqrt(min_j
 n_j) (four standard deviations): rho = 4 s / sqrt(min_j n_j) + s^2 / (2 e).
 unit is 2^-24 for FP32 operands and 2^-16 for BF16 hi/lo pairs (the pair
 represents a value to 2^-18 and the MMAs drop the lo x lo products, 2^-18
-each).
+each).  The FP32 form expands modes 2..d with FP32 FMAs (unit 2^-24) and may
+run the mode-1 stage on the tensor cores as three TF32 products of FP32
+operands split as v = v_h + v_l (v_h: v with its low 13 mantissa bits
+cleared, v_l exact in FP32): the MMA reads v_l truncated to TF32 (error
+< 2^-10 |v_l| < 2^-20 |v|, for each of the two operands) and the dropped
+v_l w_l term is < 2^-20 |v w|, so a product is off by < 3 * 2^-20 relative
+in the worst case; unit1 = 2^-19 for that stage (U_TF32_PAIR), the same
+factor of about two over the worst case as the BF16 pair's unit has.
 """
 
 from __future__ import annotations
@@ -47,12 +54,16 @@ import numpy as np
 
 U_F32 = 2.0 ** -24
 U_BF16_PAIR = 2.0 ** -16
+U_TF32_PAIR = 2.0 ** -19
 
 
 def eval_bound(cols: Sequence[int], dims: Sequence[int], xhat_over_x: float, e_self: float,
-               unit: float = U_F32) -> float:
-    """rho of the module docstring."""
-    s = unit * math.sqrt(sum(int(c) + 2 for c in cols)) * xhat_over_x
+               unit: float = U_F32, unit1: float | None = None) -> float:
+    """rho of the module docstring; unit1 is the unit of the mode-1 stage
+    (cols[0]) where it differs from the others'."""
+    u1 = unit if unit1 is None else unit1
+    cs = [int(c) for c in cols]
+    s = math.sqrt(u1 * u1 * (cs[0] + 2) + unit * unit * sum(c + 2 for c in cs[1:])) * xhat_over_x
     if s == 0.0:
         return 0.0
     return 4.0 * s / math.sqrt(min(int(n) for n in dims)) + s * s / (2.0 * max(e_self, s))

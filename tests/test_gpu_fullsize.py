@@ -25,7 +25,7 @@ import numpy as np
 import pytest
 
 from tests.gpu_util import require_gpu, dev, mat_from_dev, empty_mat
-from tests.parity import (U_BF16_PAIR, U_F32, check_error_value, eval_bound,
+from tests.parity import (U_BF16_PAIR, U_F32, U_TF32_PAIR, check_error_value, eval_bound,
                           projector_distance, recon_distance)
 from oracle import hankel as HK, philox, tucker as TK
 from synth import config_spec, hankel_config_spec, markov_parameters
@@ -286,6 +286,7 @@ def test_c2_pipeline_matches_oracle(ctx, c2_inputs, form):
     ranks, ells = list(spec.ranks), list(spec.ell)
     if form == "f32":
         x, xh, om_round, tol, unit = x32, _host_tensor(x32), "f32", 1e-5, U_F32
+        unit1 = U_TF32_PAIR  # mode-1 stage of the residual on the tensor cores
     elif form == "bf16":
         x, xh, om_round, tol, unit = xbf, _host_tensor(xbf), "bf16", 5e-5, U_BF16_PAIR
     else:
@@ -316,7 +317,8 @@ def test_c2_pipeline_matches_oracle(ctx, c2_inputs, form):
     e_ora = TK.rel_error_slabs(xh, g_o, q_o)
     e_self = TK.rel_error_slabs(xh, g, qs)
     # ||X_hat|| = ||G|| (orthonormal factors)
-    rho = eval_bound(ranks, spec.dims, np.linalg.norm(g) / nx, e_self, unit)
+    rho = eval_bound(ranks, spec.dims, np.linalg.norm(g) / nx, e_self, unit,
+                     unit1 if form == "f32" else None)
     check_error_value(res["rel_residual"], e_ora, e_self, eta, rho, form)
     assert abs(res["x_norm"] - nx) <= 1e-6 * nx
     print(f"{form}: P2 {eta:.2e}, e_gpu {res['rel_residual']:.6e}, e_self {e_self:.6e}, "

@@ -15,7 +15,7 @@ import numpy as np
 import pytest
 
 from tests.gpu_util import require_gpu, dev, tensor_to_dev
-from tests.parity import check_error_value, eval_bound
+from tests.parity import U_F32, U_TF32_PAIR, check_error_value, eval_bound
 from oracle import philox, tucker as TK
 from synth import TuckerSpec, tucker_tensor
 
@@ -91,7 +91,8 @@ def _rho(x, core, facs, dims, cdims):
     g, qs = _gq(core, facs, dims, cdims)
     nx = np.linalg.norm(x)
     e_self = TK.rel_error(x, g, qs)
-    return e_self, eval_bound(cdims, dims, np.linalg.norm(TK.reconstruct(g, qs)) / nx, e_self)
+    return e_self, eval_bound(cdims, dims, np.linalg.norm(TK.reconstruct(g, qs)) / nx, e_self,
+                              U_F32, U_TF32_PAIR)
 
 
 @pytest.mark.parametrize("spec", SPECS, ids=[s.name for s in SPECS])

@@ -14,7 +14,7 @@ import numpy as np
 import pytest
 
 from tests.gpu_util import require_gpu, dev, tensor_to_dev, rel
-from tests.parity import U_F32, check_error_value, eval_bound
+from tests.parity import U_F32, U_TF32_PAIR, check_error_value, eval_bound
 from oracle import philox, tucker as TK
 from synth import TuckerSpec, tucker_tensor, config_spec
 
@@ -107,7 +107,8 @@ def test_tucker_parity(ctx, spec, variant):
     assert list(res2["core_dims"]) == list(spec.ranks)
 
 
-def _check_p2_p3(x, g, qs, g_o, q_o, e_gpu, dims, what, p2_tol=1e-5, unit=U_F32):
+def _check_p2_p3(x, g, qs, g_o, q_o, e_gpu, dims, what, p2_tol=1e-5, unit=U_F32,
+                 unit1=U_TF32_PAIR):
     """P2 (reconstructions within p2_tol of ||X||) and P3 (error values, with
     the bound of tests/parity.py); returns the measured P2 distance."""
     nx = np.linalg.norm(x)
@@ -116,7 +117,7 @@ def _check_p2_p3(x, g, qs, g_o, q_o, e_gpu, dims, what, p2_tol=1e-5, unit=U_F32)
     assert eta <= p2_tol, (what, eta)
     e_self = TK.rel_error(x, g, qs)
     e_ora = TK.rel_error(x, g_o, q_o)
-    rho = eval_bound(g.shape, dims, np.linalg.norm(xh) / nx, e_self, unit)
+    rho = eval_bound(g.shape, dims, np.linalg.norm(xh) / nx, e_self, unit, unit1)
     check_error_value(e_gpu, e_ora, e_self, eta, rho, what)
     return eta
 
@@ -148,7 +149,7 @@ def test_host_pointers_match_device_pointers(ctx):
     # both error values are within the residual pass's rounding bound of the
     # exact errors of their own results, which differ by at most eta
     e_self = TK.rel_error(x32, gd, qd)
-    rho = eval_bound(gd.shape, spec.dims, np.linalg.norm(xd) / nx, e_self)
+    rho = eval_bound(gd.shape, spec.dims, np.linalg.norm(xd) / nx, e_self, U_F32, U_TF32_PAIR)
     assert abs(rd["rel_residual"] - rh["rel_residual"]) <= 2e-5 * e_self + eta + 2 * rho
 
 

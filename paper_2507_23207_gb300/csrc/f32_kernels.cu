@@ -13,6 +13,7 @@
 #include <type_traits>
 
 #include "common.cuh"
+#include "pipeline.h"
 
 namespace krp {
 namespace {
@@ -1128,8 +1129,10 @@ void krp_slab_mttkrp_launch(const float* X, int64_t n1, int64_t n2, int64_t T, c
 }  // namespace
 
 size_t mttkrp_first_f32_workspace_bytes(int64_t S, int64_t n2max) {
-  // padded mode-2 factor (n2 x 64) and Khatri-Rao weights (S / n2 x 64, n2 >= 16)
-  return ws_bytes((size_t)n2max * 64, 4) + ws_bytes((size_t)(S / 16 + 1) * 64, 4);
+  // padded mode-2 factor (n2 x 64, or the TF32 hi/lo buffer of up to 128 rows
+  // of n2 rounded up to 32) and Khatri-Rao weights (S / n2 x 64, n2 >= 16)
+  return std::max(ws_bytes((size_t)n2max * 64, 4), tc_mttkrp_tf32_workspace_bytes(n2max, 64)) +
+         ws_bytes((size_t)(S / 16 + 1) * 64, 4);
 }
 
 void gemm_tn_f32(const float* A, int64_t lda, int64_t S, int K, const float* F, int64_t ldf,
@@ -1190,6 +1193,15 @@ void mttkrp_first_f32(const float* A, int64_t n1, int64_t S, const Radix& rest, 
       W.V[j - 1] = rest.V[j];
     }
     const int64_t T = S / n2;
+    if (tc_mttkrp_tf32_supported(n1, n2, T, L, A)) {
+      // tensor cores, three TF32 products per multiply (FP32-level error)
+      const int Lp = (L + 15) / 16 * 16;
+      float* wT = current()->ws.take<float>((size_t)T * Lp);
+      krp_weights_padded_kernel<<<grid_for(T * Lp, 256), 256, 0, stream()>>>(W, T, L, Lp, wT);
+      check_launch("krp_weights_padded");
+      tc_mttkrp_first_tf32(A, n1, n2, T, rest.V[0], wT, L, Y);
+      return;
+    }
     if (L <= 16)
       krp_slab_mttkrp_launch<16>(A, n1, n2, T, rest.V[0], W, L, Y);
     else if (L <= 32)

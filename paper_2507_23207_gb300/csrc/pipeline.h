@@ -137,6 +137,14 @@ bool tc_gemm_tn_tf32_supported(int64_t n1, int64_t S, int L, const void* X);
 // FP32 residual on the tensor cores (TF32 hi/lo products of H and Q1, FP32
 // comparison with X): needs n1 % 4 == 0, 16-byte X, c <= 32.
 bool tc_residual_tf32_supported(int64_t n1, int64_t S, int c, const void* X);
+// FP32 mode-1 MTTKRP on the tensor cores (TF32 hi/lo products):
+// Y[i + n1*k] += sum_t wT[t*Lp + k] sum_{i2} X[i, i2, t] Om2[i2 + n2*k],
+// Lp = L rounded up to 16 (wT zero for L <= k < Lp); Y is added to, not set.
+// Needs n1 % 4 == 0, 16-byte X, L <= 64.
+bool tc_mttkrp_tf32_supported(int64_t n1, int64_t n2, int64_t T, int L, const void* X);
+size_t tc_mttkrp_tf32_workspace_bytes(int64_t n2, int L);
+void tc_mttkrp_first_tf32(const float* X, int64_t n1, int64_t n2, int64_t T, const float* Om2,
+                          const float* wT, int L, float* Y);
 size_t tc_residual_tf32_workspace_bytes(int64_t n1, int64_t S);
 void tc_residual_tf32(const float* X, int64_t n1, int64_t S, const double* Q1, int c, const float* H,
                       double* acc);

@@ -583,6 +583,223 @@ __global__ void __launch_bounds__(kTf32Threads, 1)
   }
 }
 
+// ----------------------------------------------------------------------------
+// FP32 mode-1 MTTKRP on the tensor cores, three TF32 products as in the TF32
+// TTM (Alg. 7's MTTKRP step without forming the Khatri-Rao product):
+//   Y[i + n1*k] += sum_{t in range} wT[t*Lp + k] D_t[i, k],
+//   D_t[i, k] = sum_{i2} X[i, i2, t] Om2[i2, k].
+// The contraction runs over i2, which is not X's contiguous index, and these
+// MMAs take K-major operands only, so four converter warps turn each landed
+// X tile (four TMA boxes of 32 i x 32 i2, rows i2) into K-major rows i of 32
+// i2, once as X (the MMA reads its TF32 part X_h) and once as X_l = X - X_h,
+// both in the 128-byte swizzle of the descriptors, and release them through
+// an mbarrier after a proxy fence.  D_t = X_h [Om2_h | Om2_l] + X_l Om2_h
+// accumulates in TMEM over the i2 chunks of slab t (two buffers of width N =
+// 2 Lp); the epilogue adds the two column halves, weights them by w_t and
+// keeps Y's partial sums in registers, one FP32 atomic add per output at the
+// end.  CTA (mb, z) takes rows mb*128.. and slabs [z t_per_cta, ...).
+// Warps: 0 TMA producer, 1 TMEM + MMA issuer, 2-5 epilogue, 6-9 converters.
+template <int N, int NS>
+__global__ void __launch_bounds__(kTf32Threads, 1)
+    tc_mttkrp_tf32_kernel(const __grid_constant__ CUtensorMap mapX,
+                          const __grid_constant__ CUtensorMap mapB, int64_t n1, int64_t T,
+                          int kchunks, int mblocks, int64_t t_per_cta,
+                          const float* __restrict__ wT, int L, float* __restrict__ Y,
+                          int* status) {
+  constexpr int Lp = N / 2;
+  constexpr uint32_t kBox = 32 * kBK32 * 4;    // 32 (i) x 32 (i2) FP32 = 4 KB
+  constexpr uint32_t kRaw = 4 * kBox;          // the landed X tile (16 KB)
+  constexpr uint32_t kA = kBM * kBK32 * 4;     // one K-major operand tile (16 KB)
+  constexpr uint32_t kBBytes = N * kBK32 * 4;
+  constexpr uint32_t kStage = 2 * kA + kRaw + kBBytes;  // [X_h | X_l | raw X | B]
+  constexpr uint32_t kTmemCols = (2 * N <= 64) ? 64 : (2 * N <= 128) ? 128 : 256;
+  constexpr uint32_t kIdesc = idesc_tf32(kBM, N);
+  constexpr uint32_t kIdescLo = idesc_tf32(kBM, Lp);
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  BarsT* bars = reinterpret_cast<BarsT*>(smem + NS * kStage);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int mb = blockIdx.x % mblocks;
+  const int64_t t0 = static_cast<int64_t>(blockIdx.x / mblocks) * t_per_cta;
+  const int64_t t1 = min(T, t0 + t_per_cta);
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < NS; ++s) {
+      mbar_init(smem_u32(&bars->full[s]), 1);
+      mbar_init(smem_u32(&bars->empty[s]), 1);
+      mbar_init(smem_u32(&bars->lofull[s]), 128);
+    }
+    for (int a = 0; a < 2; ++a) {
+      mbar_init(smem_u32(&bars->tfull[a]), 1);
+      mbar_init(smem_u32(&bars->tempty[a]), 4);
+    }
+    mbar_init(smem_u32(&bars->drain), 1);
+    bars->abort_flag = 0;
+    bars->issued = 0;
+    bars->consumed = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  if (warp == 1) tmem_alloc(smem_u32(&bars->tmem_base), kTmemCols);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = bars->tmem_base;
+  volatile int* abort_flag = &bars->abort_flag;
+  const uint64_t lim = wait_limit(status);
+
+  if (warp == 0) {
+    if (lane == 0) {
+      int it = 0;
+      for (int64_t t = t0; t < t1 && !*abort_flag; ++t) {
+        for (int kc = 0; kc < kchunks; ++kc, ++it) {
+          const int st = it % NS;
+          const uint32_t ph = (it / NS) & 1;
+          if (!mbar_wait(smem_u32(&bars->empty[st]), ph ^ 1, abort_flag, lim)) {
+            raise_timeout(bars, status);
+            break;
+          }
+          const uint32_t a = smem_u32(smem + st * kStage);
+          const uint32_t fb = smem_u32(&bars->full[st]);
+          mbar_expect_tx(fb, kRaw + kBBytes);
+#pragma unroll
+          for (int b = 0; b < 4; ++b)
+            tma_load_3d(a + 2 * kA + b * kBox, &mapX, fb, mb * kBM + 32 * b, kc * kBK32,
+                        static_cast<int>(t));
+          tma_load_2d(a + 2 * kA + kRaw, &mapB, fb, kc * kBK32, 0);
+          bars->issued = it + 1;
+        }
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      int it = 0, tl = 0;
+      for (int64_t t = t0; t < t1 && !*abort_flag; ++t, ++tl) {
+        const int acc = tl & 1;
+        const uint32_t aph = (tl >> 1) & 1;
+        if (!mbar_wait(smem_u32(&bars->tempty[acc]), aph ^ 1, abort_flag, lim)) {
+          raise_timeout(bars, status);
+          break;
+        }
+        tc_fence_after();
+        const uint32_t dt = tmem + acc * N;
+        bool ok = true;
+        for (int kc = 0; kc < kchunks; ++kc, ++it) {
+          const int st = it % NS;
+          const uint32_t ph = (it / NS) & 1;
+          if (!mbar_wait(smem_u32(&bars->full[st]), ph, abort_flag, lim) ||
+              !mbar_wait(smem_u32(&bars->lofull[st]), ph, abort_flag, lim)) {
+            raise_timeout(bars, status);
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const uint32_t ah = smem_u32(smem + st * kStage);
+          const uint32_t al = ah + kA;
+          const uint32_t b = ah + 2 * kA + kRaw;
+#pragma unroll
+          for (int k = 0; k < kBK32 / 8; ++k) {
+            mma_tf32(dt, sdesc(ah + 32 * k, 16, 1024), sdesc(b + 32 * k, 16, 1024), kIdesc,
+                     (kc | k) != 0);
+            // X_l times the hi columns of Om2 (the first Lp rows of B)
+            mma_tf32(dt, sdesc(al + 32 * k, 16, 1024), sdesc(b + 32 * k, 16, 1024), kIdescLo, 1);
+          }
+          mma_commit(smem_u32(&bars->empty[st]));
+          bars->consumed = it + 1;
+        }
+        if (!ok) break;
+        mma_commit(smem_u32(&bars->tfull[acc]));
+      }
+      mma_commit(smem_u32(&bars->drain));
+      int dummy = 0;
+      mbar_wait(smem_u32(&bars->drain), 0, reinterpret_cast<volatile int*>(&dummy));
+    }
+  } else if (warp < 6) {
+    const int q = warp & 3;
+    const int row = q * 32 + lane;
+    const int64_t i = static_cast<int64_t>(mb) * kBM + row;
+    float accum[Lp];
+#pragma unroll
+    for (int k = 0; k < Lp; ++k) accum[k] = 0.f;
+    int tl = 0;
+    for (int64_t t = t0; t < t1; ++t, ++tl) {
+      const int acc = tl & 1;
+      const uint32_t ph = (tl >> 1) & 1;
+      if (!mbar_wait(smem_u32(&bars->tfull[acc]), ph, abort_flag, lim)) {
+        if (lane == 0) raise_timeout(bars, status);
+        break;
+      }
+      tc_fence_after();
+      const uint32_t base = tmem + (static_cast<uint32_t>(q * 32) << 16) + acc * N;
+      const float* wt = wT + t * Lp;
+#pragma unroll
+      for (int c0 = 0; c0 < Lp; c0 += 16) {
+        float v[16], u[16];
+        tmem_ld16(base + c0, v);
+        tmem_ld16(base + Lp + c0, u);
+#pragma unroll
+        for (int j = 0; j < 16; ++j) accum[c0 + j] = fmaf(__ldg(wt + c0 + j), v[j] + u[j], accum[c0 + j]);
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(smem_u32(&bars->tempty[acc]));
+    }
+    if (i < n1) {
+#pragma unroll
+      for (int k = 0; k < Lp; ++k)
+        if (k < L) atomicAdd(Y + i + n1 * k, accum[k]);
+    }
+  } else {
+    // converters: thread ct owns row i = ct of the K-major tiles; it reads its
+    // 32 values of i2 from box ct / 32 (a warp reads one 128-byte row per load)
+    const int ct = threadIdx.x - 6 * 32;  // 0..127
+    const int bx = ct >> 5, il = ct & 31;
+    const uint32_t sw = static_cast<uint32_t>(ct & 7);
+    int it = 0;
+    bool ok = true;
+    for (int64_t t = t0; t < t1 && ok; ++t) {
+      for (int kc = 0; kc < kchunks; ++kc, ++it) {
+        const int st = it % NS;
+        const uint32_t ph = (it / NS) & 1;
+        if (!mbar_wait(smem_u32(&bars->full[st]), ph, abort_flag, lim)) {
+          raise_timeout(bars, status);
+          ok = false;
+          break;
+        }
+        uint8_t* sg = smem + st * kStage;
+        const uint8_t* raw = sg + 2 * kA + bx * kBox + ((il & 3) << 2);
+        float x[kBK32];
+#pragma unroll
+        for (int r = 0; r < kBK32; ++r)
+          x[r] = *reinterpret_cast<const float*>(raw + r * 128 + ((((il >> 2) ^ (r & 7))) << 4));
+        uint8_t* hrow = sg + ct * 128;
+        uint8_t* lrow = sg + kA + ct * 128;
+#pragma unroll
+        for (int c = 0; c < kBK32 / 4; ++c) {
+          const float4 h = make_float4(x[4 * c], x[4 * c + 1], x[4 * c + 2], x[4 * c + 3]);
+          float4 l;
+          l.x = h.x - __uint_as_float(__float_as_uint(h.x) & 0xFFFFE000u);
+          l.y = h.y - __uint_as_float(__float_as_uint(h.y) & 0xFFFFE000u);
+          l.z = h.z - __uint_as_float(__float_as_uint(h.z) & 0xFFFFE000u);
+          l.w = h.w - __uint_as_float(__float_as_uint(h.w) & 0xFFFFE000u);
+          const uint32_t off = (static_cast<uint32_t>(c) ^ sw) << 4;
+          *reinterpret_cast<float4*>(hrow + off) = h;
+          *reinterpret_cast<float4*>(lrow + off) = l;
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        mbar_arrive(smem_u32(&bars->lofull[st]));
+      }
+    }
+  }
+  __syncthreads();
+  if (warp == 0 && lane == 0 && bars->abort_flag) drain_loads<NS>(bars);
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    tmem_dealloc(tmem, kTmemCols);
+  }
+}
+
 // Residual of the FP32 form on the tensor cores: acc[0] += ||X - Q1 H||_F^2,
 // acc[1] += ||X||_F^2 for FP32 X (n1 x S) and c <= 32.  Same orientation as
 // the BF16 residual (the tile is X_hat^T[s, i], A = H with M = s, B = Q1 with
@@ -1958,6 +2175,66 @@ void tc_gemm_tn_tf32(const float* X, int64_t n1, int64_t S, const float* F, int6
     case 64: launch_gemm_tf32<64>(ma, mb, S, kchunks, L, Lp, out); break;
     case 96: launch_gemm_tf32<96>(ma, mb, S, kchunks, L, Lp, out); break;
     case 128: launch_gemm_tf32<128>(ma, mb, S, kchunks, L, Lp, out); break;
+    default: fail(KRP_EUNSUPPORTED, "unsupported TF32 MMA width %d", N);
+  }
+}
+
+namespace {
+template <int N>
+void launch_mttkrp_tf32(const CUtensorMap& mx, const CUtensorMap& mb, int64_t n1, int64_t T,
+                        int kchunks, const float* wT, int L, float* Y) {
+  const int mblocks = static_cast<int>((n1 + kBM - 1) / kBM);
+  int64_t chunks = std::max<int64_t>(1, current()->num_sms / mblocks);
+  chunks = std::min<int64_t>(chunks, T);
+  const int64_t per = (T + chunks - 1) / chunks;
+  chunks = (T + per - 1) / per;
+  const int grid = static_cast<int>(mblocks * chunks);
+  constexpr int NS = 3;
+  const size_t smem = 1024 + NS * (size_t)(2 * kBM * kBK32 * 4 + 4 * 32 * kBK32 * 4 + N * kBK32 * 4) +
+                      sizeof(BarsT) + 64;
+  set_smem(tc_mttkrp_tf32_kernel<N, NS>, smem);
+  tc_mttkrp_tf32_kernel<N, NS><<<grid, kTf32Threads, smem, stream()>>>(
+      mx, mb, n1, T, kchunks, mblocks, per, wT, L, Y, current()->d_status);
+  check_launch("tc_mttkrp_tf32");
+}
+}  // namespace
+
+bool tc_mttkrp_tf32_supported(int64_t n1, int64_t n2, int64_t T, int L, const void* X) {
+  return n1 % 4 == 0 && n1 < (int64_t(1) << 31) && n2 < (int64_t(1) << 31) &&
+         T < (int64_t(1) << 31) && L >= 1 && L <= 64 && (reinterpret_cast<uintptr_t>(X) & 15) == 0;
+}
+
+size_t tc_mttkrp_tf32_workspace_bytes(int64_t n2, int L) {
+  const int64_t n2p = (n2 + kBK32 - 1) / kBK32 * kBK32;
+  const int64_t Lp = (L + 15) / 16 * 16;
+  return ws_bytes((size_t)n2p * 2 * Lp, 4) + (1 << 12);
+}
+
+void tc_mttkrp_first_tf32(const float* X, int64_t n1, int64_t n2, int64_t T, const float* Om2,
+                          const float* wT, int L, float* Y) {
+  KRP_REQUIRE(tc_mttkrp_tf32_supported(n1, n2, T, L, X), "TF32 MTTKRP: unsupported shape or alignment");
+  const int Lp = round_up(L, 16);
+  const int N = 2 * Lp;
+  const int64_t n2p = round_up(n2, kBK32);
+  float* Bc = current()->ws.take<float>((size_t)n2p * N);
+  const int64_t tot = n2p * N;
+  pack_factor_tf32_kernel<<<(int)std::min<int64_t>((tot + 255) / 256, 4096), 256, 0, stream()>>>(
+      Om2, n2, n2, n2p, L, Lp, N, Bc);
+  check_launch("pack_factor_tf32");
+  const uint64_t xdims[3] = {(uint64_t)n1, (uint64_t)n2, (uint64_t)T};
+  const uint64_t xstr[2] = {(uint64_t)n1 * 4, (uint64_t)n1 * n2 * 4};
+  const uint32_t xbox[3] = {32, kBK32, 1};
+  const CUtensorMap mx = make_map(X, 3, xdims, xstr, xbox, CU_TENSOR_MAP_DATA_TYPE_FLOAT32);
+  const uint64_t bdims[2] = {(uint64_t)n2p, (uint64_t)N};
+  const uint64_t bstr[1] = {(uint64_t)n2p * 4};
+  const uint32_t bbox[2] = {kBK32, (uint32_t)N};
+  const CUtensorMap mb = make_map(Bc, 2, bdims, bstr, bbox, CU_TENSOR_MAP_DATA_TYPE_FLOAT32);
+  const int kchunks = static_cast<int>((n2 + kBK32 - 1) / kBK32);
+  switch (N) {
+    case 32: launch_mttkrp_tf32<32>(mx, mb, n1, T, kchunks, wT, L, Y); break;
+    case 64: launch_mttkrp_tf32<64>(mx, mb, n1, T, kchunks, wT, L, Y); break;
+    case 96: launch_mttkrp_tf32<96>(mx, mb, n1, T, kchunks, wT, L, Y); break;
+    case 128: launch_mttkrp_tf32<128>(mx, mb, n1, T, kchunks, wT, L, Y); break;
     default: fail(KRP_EUNSUPPORTED, "unsupported TF32 MMA width %d", N);
   }
 }

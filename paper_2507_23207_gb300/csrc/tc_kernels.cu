@@ -429,7 +429,7 @@ __global__ void __launch_bounds__(kTf32Threads, 1)
     for (int s = 0; s < NS; ++s) {
       mbar_init(smem_u32(&bars->full[s]), 1);
       mbar_init(smem_u32(&bars->empty[s]), 1);
-      mbar_init(smem_u32(&bars->lofull[s]), 128);
+      mbar_init(smem_u32(&bars->lofull[s]), 4);  // the four converter warps
     }
     for (int a = 0; a < 2; ++a) {
       mbar_init(smem_u32(&bars->tfull[a]), 1);
@@ -570,7 +570,8 @@ __global__ void __launch_bounds__(kTf32Threads, 1)
           dst[ct + 128 * j] = l;
         }
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        mbar_arrive(smem_u32(&bars->lofull[st]));
+        __syncwarp();
+        if (lane == 0) mbar_arrive(smem_u32(&bars->lofull[st]));
       }
     }
   }
@@ -592,14 +593,27 @@ __global__ void __launch_bounds__(kTf32Threads, 1)
 // MMAs take K-major operands only, so four converter warps turn each landed
 // X tile (four TMA boxes of 32 i x 32 i2, rows i2) into K-major rows i of 32
 // i2, once as X (the MMA reads its TF32 part X_h) and once as X_l = X - X_h,
-// both in the 128-byte swizzle of the descriptors, and release them through
-// an mbarrier after a proxy fence.  D_t = X_h [Om2_h | Om2_l] + X_l Om2_h
-// accumulates in TMEM over the i2 chunks of slab t (two buffers of width N =
-// 2 Lp); the epilogue adds the two column halves, weights them by w_t and
-// keeps Y's partial sums in registers, one FP32 atomic add per output at the
-// end.  CTA (mb, z) takes rows mb*128.. and slabs [z t_per_cta, ...).
-// Warps: 0 TMA producer, 1 TMEM + MMA issuer, 2-5 epilogue, 6-9 converters.
-template <int N, int NS>
+// both in the 128-byte swizzle of the descriptors.  D_t = X_h [Om2_h | Om2_l]
+// + X_l Om2_h accumulates in TMEM over the i2 chunks of slab t (two buffers of
+// width N = 2 Lp); the epilogue adds the two column halves, weights them by
+// w_t and keeps Y's partial sums in registers, one FP32 atomic add per output
+// at the end.  CTA (mb, z) takes rows mb*128.. and slabs [z t_per_cta, ...).
+// Two rings: NR raw X tiles (TMA, released by the converters as soon as they
+// hold the values in registers, so that many tiles are in flight from HBM)
+// and NC operand stages (X_h^T, X_l^T written by the converters, the Om2
+// chunk loaded by TMA from converter thread 0; released by the MMA commit).
+// Warps: 0 TMA producer of X, 1 TMEM + MMA issuer, 2-5 epilogue, 6-9
+// converters.
+struct BarsM : Bars {
+  uint64_t rempty[8];  // raw X stage read by the four converter warps
+  uint64_t bfull[8];   // the Om2 chunk of an operand stage has landed
+  uint64_t lofull[8];  // X_h^T, X_l^T of an operand stage are written
+  int r_consumed;      // raw stages converter thread 0 saw land
+  int b_issued;        // Om2 chunk loads issued (converter thread 0)
+  int b_consumed;      // Om2 chunk loads the MMA warp saw land
+};
+
+template <int N, int NR, int NC>
 __global__ void __launch_bounds__(kTf32Threads, 1)
     tc_mttkrp_tf32_kernel(const __grid_constant__ CUtensorMap mapX,
                           const __grid_constant__ CUtensorMap mapB, int64_t n1, int64_t T,
@@ -608,26 +622,33 @@ __global__ void __launch_bounds__(kTf32Threads, 1)
                           int* status) {
   constexpr int Lp = N / 2;
   constexpr uint32_t kBox = 32 * kBK32 * 4;    // 32 (i) x 32 (i2) FP32 = 4 KB
-  constexpr uint32_t kRaw = 4 * kBox;          // the landed X tile (16 KB)
+  constexpr uint32_t kRaw = 4 * kBox;          // one landed X tile (16 KB)
   constexpr uint32_t kA = kBM * kBK32 * 4;     // one K-major operand tile (16 KB)
   constexpr uint32_t kBBytes = N * kBK32 * 4;
-  constexpr uint32_t kStage = 2 * kA + kRaw + kBBytes;  // [X_h | X_l | raw X | B]
+  constexpr uint32_t kOp = 2 * kA + kBBytes;   // [X_h^T | X_l^T | Om2 chunk]
+  static_assert(kOp % 1024 == 0, "operand stages must keep the 1 KB swizzle alignment");
   constexpr uint32_t kTmemCols = (2 * N <= 64) ? 64 : (2 * N <= 128) ? 128 : 256;
   constexpr uint32_t kIdesc = idesc_tf32(kBM, N);
   constexpr uint32_t kIdescLo = idesc_tf32(kBM, Lp);
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-  BarsT* bars = reinterpret_cast<BarsT*>(smem + NS * kStage);
+  uint8_t* ops = smem;
+  uint8_t* raws = smem + NC * kOp;
+  BarsM* bars = reinterpret_cast<BarsM*>(raws + NR * kRaw);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int mb = blockIdx.x % mblocks;
   const int64_t t0 = static_cast<int64_t>(blockIdx.x / mblocks) * t_per_cta;
   const int64_t t1 = min(T, t0 + t_per_cta);
 
   if (threadIdx.x == 0) {
-    for (int s = 0; s < NS; ++s) {
+    for (int s = 0; s < NR; ++s) {
       mbar_init(smem_u32(&bars->full[s]), 1);
-      mbar_init(smem_u32(&bars->empty[s]), 1);
-      mbar_init(smem_u32(&bars->lofull[s]), 128);
+      mbar_init(smem_u32(&bars->rempty[s]), 4);
+    }
+    for (int c = 0; c < NC; ++c) {
+      mbar_init(smem_u32(&bars->empty[c]), 1);
+      mbar_init(smem_u32(&bars->bfull[c]), 1);
+      mbar_init(smem_u32(&bars->lofull[c]), 4);
     }
     for (int a = 0; a < 2; ++a) {
       mbar_init(smem_u32(&bars->tfull[a]), 1);
@@ -637,6 +658,9 @@ __global__ void __launch_bounds__(kTf32Threads, 1)
     bars->abort_flag = 0;
     bars->issued = 0;
     bars->consumed = 0;
+    bars->r_consumed = 0;
+    bars->b_issued = 0;
+    bars->b_consumed = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   }
@@ -653,20 +677,18 @@ __global__ void __launch_bounds__(kTf32Threads, 1)
       int it = 0;
       for (int64_t t = t0; t < t1 && !*abort_flag; ++t) {
         for (int kc = 0; kc < kchunks; ++kc, ++it) {
-          const int st = it % NS;
-          const uint32_t ph = (it / NS) & 1;
-          if (!mbar_wait(smem_u32(&bars->empty[st]), ph ^ 1, abort_flag, lim)) {
+          const int r = it % NR;
+          const uint32_t ph = (it / NR) & 1;
+          if (!mbar_wait(smem_u32(&bars->rempty[r]), ph ^ 1, abort_flag, lim)) {
             raise_timeout(bars, status);
             break;
           }
-          const uint32_t a = smem_u32(smem + st * kStage);
-          const uint32_t fb = smem_u32(&bars->full[st]);
-          mbar_expect_tx(fb, kRaw + kBBytes);
+          const uint32_t a = smem_u32(raws + r * kRaw);
+          const uint32_t fb = smem_u32(&bars->full[r]);
+          mbar_expect_tx(fb, kRaw);
 #pragma unroll
           for (int b = 0; b < 4; ++b)
-            tma_load_3d(a + 2 * kA + b * kBox, &mapX, fb, mb * kBM + 32 * b, kc * kBK32,
-                        static_cast<int>(t));
-          tma_load_2d(a + 2 * kA + kRaw, &mapB, fb, kc * kBK32, 0);
+            tma_load_3d(a + b * kBox, &mapX, fb, mb * kBM + 32 * b, kc * kBK32, static_cast<int>(t));
           bars->issued = it + 1;
         }
       }
@@ -685,18 +707,19 @@ __global__ void __launch_bounds__(kTf32Threads, 1)
         const uint32_t dt = tmem + acc * N;
         bool ok = true;
         for (int kc = 0; kc < kchunks; ++kc, ++it) {
-          const int st = it % NS;
-          const uint32_t ph = (it / NS) & 1;
-          if (!mbar_wait(smem_u32(&bars->full[st]), ph, abort_flag, lim) ||
-              !mbar_wait(smem_u32(&bars->lofull[st]), ph, abort_flag, lim)) {
+          const int c = it % NC;
+          const uint32_t ph = (it / NC) & 1;
+          if (!mbar_wait(smem_u32(&bars->bfull[c]), ph, abort_flag, lim) ||
+              !mbar_wait(smem_u32(&bars->lofull[c]), ph, abort_flag, lim)) {
             raise_timeout(bars, status);
             ok = false;
             break;
           }
+          bars->b_consumed = it + 1;
           tc_fence_after();
-          const uint32_t ah = smem_u32(smem + st * kStage);
+          const uint32_t ah = smem_u32(ops + c * kOp);
           const uint32_t al = ah + kA;
-          const uint32_t b = ah + 2 * kA + kRaw;
+          const uint32_t b = ah + 2 * kA;
 #pragma unroll
           for (int k = 0; k < kBK32 / 8; ++k) {
             mma_tf32(dt, sdesc(ah + 32 * k, 16, 1024), sdesc(b + 32 * k, 16, 1024), kIdesc,
@@ -704,8 +727,7 @@ __global__ void __launch_bounds__(kTf32Threads, 1)
             // X_l times the hi columns of Om2 (the first Lp rows of B)
             mma_tf32(dt, sdesc(al + 32 * k, 16, 1024), sdesc(b + 32 * k, 16, 1024), kIdescLo, 1);
           }
-          mma_commit(smem_u32(&bars->empty[st]));
-          bars->consumed = it + 1;
+          mma_commit(smem_u32(&bars->empty[c]));
         }
         if (!ok) break;
         mma_commit(smem_u32(&bars->tfull[acc]));
@@ -759,40 +781,63 @@ __global__ void __launch_bounds__(kTf32Threads, 1)
     bool ok = true;
     for (int64_t t = t0; t < t1 && ok; ++t) {
       for (int kc = 0; kc < kchunks; ++kc, ++it) {
-        const int st = it % NS;
-        const uint32_t ph = (it / NS) & 1;
-        if (!mbar_wait(smem_u32(&bars->full[st]), ph, abort_flag, lim)) {
+        const int r = it % NR, c = it % NC;
+        const uint32_t rph = (it / NR) & 1, cph = (it / NC) & 1;
+        // the operand stage is free once the MMAs of its previous use are done
+        if (!mbar_wait(smem_u32(&bars->empty[c]), cph ^ 1, abort_flag, lim)) {
           raise_timeout(bars, status);
           ok = false;
           break;
         }
-        uint8_t* sg = smem + st * kStage;
-        const uint8_t* raw = sg + 2 * kA + bx * kBox + ((il & 3) << 2);
+        uint8_t* og = ops + c * kOp;
+        if (ct == 0) {
+          const uint32_t bb = smem_u32(&bars->bfull[c]);
+          mbar_expect_tx(bb, kBBytes);
+          tma_load_2d(smem_u32(og + 2 * kA), &mapB, bb, kc * kBK32, 0);
+          bars->b_issued = it + 1;
+        }
+        if (!mbar_wait(smem_u32(&bars->full[r]), rph, abort_flag, lim)) {
+          raise_timeout(bars, status);
+          ok = false;
+          break;
+        }
+        if (ct == 0) bars->r_consumed = it + 1;
+        const uint8_t* raw = raws + r * kRaw + bx * kBox + ((il & 3) << 2);
         float x[kBK32];
 #pragma unroll
-        for (int r = 0; r < kBK32; ++r)
-          x[r] = *reinterpret_cast<const float*>(raw + r * 128 + ((((il >> 2) ^ (r & 7))) << 4));
-        uint8_t* hrow = sg + ct * 128;
-        uint8_t* lrow = sg + kA + ct * 128;
+        for (int rr = 0; rr < kBK32; ++rr)
+          x[rr] = *reinterpret_cast<const float*>(raw + rr * 128 + ((((il >> 2) ^ (rr & 7))) << 4));
+        __syncwarp();
+        if (lane == 0) mbar_arrive(smem_u32(&bars->rempty[r]));
+        uint8_t* hrow = og + ct * 128;
+        uint8_t* lrow = og + kA + ct * 128;
 #pragma unroll
-        for (int c = 0; c < kBK32 / 4; ++c) {
-          const float4 h = make_float4(x[4 * c], x[4 * c + 1], x[4 * c + 2], x[4 * c + 3]);
+        for (int q4 = 0; q4 < kBK32 / 4; ++q4) {
+          const float4 h = make_float4(x[4 * q4], x[4 * q4 + 1], x[4 * q4 + 2], x[4 * q4 + 3]);
           float4 l;
           l.x = h.x - __uint_as_float(__float_as_uint(h.x) & 0xFFFFE000u);
           l.y = h.y - __uint_as_float(__float_as_uint(h.y) & 0xFFFFE000u);
           l.z = h.z - __uint_as_float(__float_as_uint(h.z) & 0xFFFFE000u);
           l.w = h.w - __uint_as_float(__float_as_uint(h.w) & 0xFFFFE000u);
-          const uint32_t off = (static_cast<uint32_t>(c) ^ sw) << 4;
+          const uint32_t off = (static_cast<uint32_t>(q4) ^ sw) << 4;
           *reinterpret_cast<float4*>(hrow + off) = h;
           *reinterpret_cast<float4*>(lrow + off) = l;
         }
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        mbar_arrive(smem_u32(&bars->lofull[st]));
+        __syncwarp();
+        if (lane == 0) mbar_arrive(smem_u32(&bars->lofull[c]));
       }
     }
   }
   __syncthreads();
-  if (warp == 0 && lane == 0 && bars->abort_flag) drain_loads<NS>(bars);
+  if (warp == 0 && lane == 0 && bars->abort_flag) {
+    // every TMA write into shared memory must land before the CTA exits
+    int dummy = 0;
+    for (int j = bars->r_consumed; j < bars->issued; ++j)
+      mbar_wait(smem_u32(&bars->full[j % NR]), (j / NR) & 1, reinterpret_cast<volatile int*>(&dummy));
+    for (int j = bars->b_consumed; j < bars->b_issued; ++j)
+      mbar_wait(smem_u32(&bars->bfull[j % NC]), (j / NC) & 1, reinterpret_cast<volatile int*>(&dummy));
+  }
   __syncthreads();
   if (warp == 1) {
     tc_fence_after();
@@ -2130,7 +2175,7 @@ void launch_gemm_tf32(const CUtensorMap& ma, const CUtensorMap& mb, int64_t S, i
                       int Lp, float* out) {
   const int64_t tiles = (S + kBM - 1) / kBM;
   const int grid = static_cast<int>(std::min<int64_t>(tiles, current()->num_sms));
-  constexpr int NS = (N <= 64) ? 5 : 4;
+  constexpr int NS = (N <= 96) ? 5 : 4;
   const size_t smem = 1024 + NS * (size_t)(2 * kBM * kBK32 * 4 + N * kBK32 * 4) + sizeof(BarsT) + 64;
   set_smem(tc_gemm_tn_tf32_kernel<N, NS>, smem);
   tc_gemm_tn_tf32_kernel<N, NS><<<grid, kTf32Threads, smem, stream()>>>(ma, mb, S, kchunks, L, Lp,
@@ -2189,11 +2234,12 @@ void launch_mttkrp_tf32(const CUtensorMap& mx, const CUtensorMap& mb, int64_t n1
   const int64_t per = (T + chunks - 1) / chunks;
   chunks = (T + per - 1) / per;
   const int grid = static_cast<int>(mblocks * chunks);
-  constexpr int NS = 3;
-  const size_t smem = 1024 + NS * (size_t)(2 * kBM * kBK32 * 4 + 4 * 32 * kBK32 * 4 + N * kBK32 * 4) +
-                      sizeof(BarsT) + 64;
-  set_smem(tc_mttkrp_tf32_kernel<N, NS>, smem);
-  tc_mttkrp_tf32_kernel<N, NS><<<grid, kTf32Threads, smem, stream()>>>(
+  // 8 raw X tiles in flight (7 for the widest operand stages), 2 operand stages
+  constexpr int NR = (N <= 96) ? 8 : 7, NC = 2;
+  const size_t smem = 1024 + NC * (size_t)(2 * kBM * kBK32 * 4 + N * kBK32 * 4) +
+                      NR * (size_t)(4 * 32 * kBK32 * 4) + sizeof(BarsM) + 64;
+  set_smem(tc_mttkrp_tf32_kernel<N, NR, NC>, smem);
+  tc_mttkrp_tf32_kernel<N, NR, NC><<<grid, kTf32Threads, smem, stream()>>>(
       mx, mb, n1, T, kchunks, mblocks, per, wT, L, Y, current()->d_status);
   check_launch("tc_mttkrp_tf32");
 }

@@ -593,28 +593,32 @@ __global__ void __launch_bounds__(kTf32Threads, 1)
 // MMAs take K-major operands only, so four converter warps turn each landed
 // X tile (four TMA boxes of 32 i x 32 i2, rows i2) into K-major rows i of 32
 // i2, once as X (the MMA reads its TF32 part X_h) and once as X_l = X - X_h,
-// both in the 128-byte swizzle of the descriptors.  D_t = X_h [Om2_h | Om2_l]
-// + X_l Om2_h accumulates in TMEM over the i2 chunks of slab t (two buffers of
-// width N = 2 Lp); the epilogue adds the two column halves, weights them by
-// w_t and keeps Y's partial sums in registers, one FP32 atomic add per output
-// at the end.  CTA (mb, z) takes rows mb*128.. and slabs [z t_per_cta, ...).
+// both in the 128-byte swizzle of the descriptors.  D_t = X_h Om2_h +
+// X_h Om2_l + X_l Om2_h (three MMAs of width Lp into one accumulator; B holds
+// Om2_h in rows 0..Lp-1 and Om2_l in rows Lp..2Lp-1, N = 2 Lp) accumulates in
+// TMEM over the i2 chunks of slab t (two buffers); the epilogue weights it by
+// w_t and keeps Y's partial sums in registers, one FP32 atomic add per
+// output at the end.  CTA (mb, z) takes rows mb*128.. and slabs [z t_per_cta, ...).
 // Two rings: NR raw X tiles (TMA, released by the converters as soon as they
 // hold the values in registers, so that many tiles are in flight from HBM)
 // and NC operand stages (X_h^T, X_l^T written by the converters, the Om2
 // chunk loaded by TMA from converter thread 0; released by the MMA commit).
-// Warps: 0 TMA producer of X, 1 TMEM + MMA issuer, 2-5 epilogue, 6-9
-// converters.
+// Two groups of four converter warps take the even and the odd chunks (so
+// that one group converts while the other waits on its loads), each with its
+// own operand stage.  Warps: 0 TMA producer of X, 1 TMEM + MMA issuer, 2-5
+// epilogue, 6-9 and 10-13 the converter groups.
+constexpr int kMtThreads = 448;
 struct BarsM : Bars {
-  uint64_t rempty[8];  // raw X stage read by the four converter warps
+  uint64_t rempty[8];  // raw X stage read by one group of four converter warps
   uint64_t bfull[8];   // the Om2 chunk of an operand stage has landed
   uint64_t lofull[8];  // X_h^T, X_l^T of an operand stage are written
-  int r_consumed;      // raw stages converter thread 0 saw land
-  int b_issued;        // Om2 chunk loads issued (converter thread 0)
+  int r_consumed[2];   // chunks (of group g's parity) group g's thread 0 saw land
+  int b_issued[2];     // Om2 chunk loads group g's thread 0 issued
   int b_consumed;      // Om2 chunk loads the MMA warp saw land
 };
 
 template <int N, int NR, int NC>
-__global__ void __launch_bounds__(kTf32Threads, 1)
+__global__ void __launch_bounds__(kMtThreads, 1)
     tc_mttkrp_tf32_kernel(const __grid_constant__ CUtensorMap mapX,
                           const __grid_constant__ CUtensorMap mapB, int64_t n1, int64_t T,
                           int kchunks, int mblocks, int64_t t_per_cta,
@@ -627,9 +631,8 @@ __global__ void __launch_bounds__(kTf32Threads, 1)
   constexpr uint32_t kBBytes = N * kBK32 * 4;
   constexpr uint32_t kOp = 2 * kA + kBBytes;   // [X_h^T | X_l^T | Om2 chunk]
   static_assert(kOp % 1024 == 0, "operand stages must keep the 1 KB swizzle alignment");
-  constexpr uint32_t kTmemCols = (2 * N <= 64) ? 64 : (2 * N <= 128) ? 128 : 256;
-  constexpr uint32_t kIdesc = idesc_tf32(kBM, N);
-  constexpr uint32_t kIdescLo = idesc_tf32(kBM, Lp);
+  constexpr uint32_t kTmemCols = (2 * Lp <= 32) ? 32 : (2 * Lp <= 64) ? 64 : 128;
+  constexpr uint32_t kIdesc = idesc_tf32(kBM, Lp);
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   uint8_t* ops = smem;
@@ -658,8 +661,8 @@ __global__ void __launch_bounds__(kTf32Threads, 1)
     bars->abort_flag = 0;
     bars->issued = 0;
     bars->consumed = 0;
-    bars->r_consumed = 0;
-    bars->b_issued = 0;
+    bars->r_consumed[0] = bars->r_consumed[1] = 0;
+    bars->b_issued[0] = bars->b_issued[1] = 0;
     bars->b_consumed = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -704,7 +707,7 @@ __global__ void __launch_bounds__(kTf32Threads, 1)
           break;
         }
         tc_fence_after();
-        const uint32_t dt = tmem + acc * N;
+        const uint32_t dt = tmem + acc * Lp;
         bool ok = true;
         for (int kc = 0; kc < kchunks; ++kc, ++it) {
           const int c = it % NC;
@@ -720,12 +723,13 @@ __global__ void __launch_bounds__(kTf32Threads, 1)
           const uint32_t ah = smem_u32(ops + c * kOp);
           const uint32_t al = ah + kA;
           const uint32_t b = ah + 2 * kA;
+          const uint32_t bl = b + Lp * 128;  // Om2_l rows (whole 1 KB swizzle atoms)
 #pragma unroll
           for (int k = 0; k < kBK32 / 8; ++k) {
             mma_tf32(dt, sdesc(ah + 32 * k, 16, 1024), sdesc(b + 32 * k, 16, 1024), kIdesc,
                      (kc | k) != 0);
-            // X_l times the hi columns of Om2 (the first Lp rows of B)
-            mma_tf32(dt, sdesc(al + 32 * k, 16, 1024), sdesc(b + 32 * k, 16, 1024), kIdescLo, 1);
+            mma_tf32(dt, sdesc(ah + 32 * k, 16, 1024), sdesc(bl + 32 * k, 16, 1024), kIdesc, 1);
+            mma_tf32(dt, sdesc(al + 32 * k, 16, 1024), sdesc(b + 32 * k, 16, 1024), kIdesc, 1);
           }
           mma_commit(smem_u32(&bars->empty[c]));
         }
@@ -752,15 +756,14 @@ __global__ void __launch_bounds__(kTf32Threads, 1)
         break;
       }
       tc_fence_after();
-      const uint32_t base = tmem + (static_cast<uint32_t>(q * 32) << 16) + acc * N;
+      const uint32_t base = tmem + (static_cast<uint32_t>(q * 32) << 16) + acc * Lp;
       const float* wt = wT + t * Lp;
 #pragma unroll
       for (int c0 = 0; c0 < Lp; c0 += 16) {
-        float v[16], u[16];
+        float v[16];
         tmem_ld16(base + c0, v);
-        tmem_ld16(base + Lp + c0, u);
 #pragma unroll
-        for (int j = 0; j < 16; ++j) accum[c0 + j] = fmaf(__ldg(wt + c0 + j), v[j] + u[j], accum[c0 + j]);
+        for (int j = 0; j < 16; ++j) accum[c0 + j] = fmaf(__ldg(wt + c0 + j), v[j], accum[c0 + j]);
       }
       tc_fence_before();
       __syncwarp();
@@ -772,15 +775,18 @@ __global__ void __launch_bounds__(kTf32Threads, 1)
         if (k < L) atomicAdd(Y + i + n1 * k, accum[k]);
     }
   } else {
-    // converters: thread ct owns row i = ct of the K-major tiles; it reads its
+    // converters: group g takes the chunks it with it % 2 == g (operand
+    // stage g); thread ct owns row i = ct of the K-major tiles and reads its
     // 32 values of i2 from box ct / 32 (a warp reads one 128-byte row per load)
-    const int ct = threadIdx.x - 6 * 32;  // 0..127
+    const int g = (warp - 6) >> 2;
+    const int ct = (threadIdx.x - 6 * 32) & 127;
     const int bx = ct >> 5, il = ct & 31;
     const uint32_t sw = static_cast<uint32_t>(ct & 7);
     int it = 0;
     bool ok = true;
     for (int64_t t = t0; t < t1 && ok; ++t) {
       for (int kc = 0; kc < kchunks; ++kc, ++it) {
+        if ((it & 1) != g) continue;
         const int r = it % NR, c = it % NC;
         const uint32_t rph = (it / NR) & 1, cph = (it / NC) & 1;
         // the operand stage is free once the MMAs of its previous use are done
@@ -794,14 +800,14 @@ __global__ void __launch_bounds__(kTf32Threads, 1)
           const uint32_t bb = smem_u32(&bars->bfull[c]);
           mbar_expect_tx(bb, kBBytes);
           tma_load_2d(smem_u32(og + 2 * kA), &mapB, bb, kc * kBK32, 0);
-          bars->b_issued = it + 1;
+          bars->b_issued[g] = it + 1;
         }
         if (!mbar_wait(smem_u32(&bars->full[r]), rph, abort_flag, lim)) {
           raise_timeout(bars, status);
           ok = false;
           break;
         }
-        if (ct == 0) bars->r_consumed = it + 1;
+        if (ct == 0) bars->r_consumed[g] = it + 1;
         const uint8_t* raw = raws + r * kRaw + bx * kBox + ((il & 3) << 2);
         float x[kBK32];
 #pragma unroll
@@ -831,12 +837,18 @@ __global__ void __launch_bounds__(kTf32Threads, 1)
   }
   __syncthreads();
   if (warp == 0 && lane == 0 && bars->abort_flag) {
-    // every TMA write into shared memory must land before the CTA exits
+    // every TMA write into shared memory must land before the CTA exits:
+    // the X tiles issued but not seen by their group, the Om2 chunks issued
+    // but not seen by the MMA warp (neither stage can have been reused)
     int dummy = 0;
-    for (int j = bars->r_consumed; j < bars->issued; ++j)
-      mbar_wait(smem_u32(&bars->full[j % NR]), (j / NR) & 1, reinterpret_cast<volatile int*>(&dummy));
-    for (int j = bars->b_consumed; j < bars->b_issued; ++j)
-      mbar_wait(smem_u32(&bars->bfull[j % NC]), (j / NC) & 1, reinterpret_cast<volatile int*>(&dummy));
+    const int rc[2] = {bars->r_consumed[0], bars->r_consumed[1]};
+    const int bi[2] = {bars->b_issued[0], bars->b_issued[1]};
+    for (int j = min(rc[0], rc[1]); j < bars->issued; ++j)
+      if (j >= rc[j & 1])
+        mbar_wait(smem_u32(&bars->full[j % NR]), (j / NR) & 1, reinterpret_cast<volatile int*>(&dummy));
+    for (int j = bars->b_consumed; j < max(bi[0], bi[1]); ++j)
+      if (j < bi[j & 1])
+        mbar_wait(smem_u32(&bars->bfull[j % NC]), (j / NC) & 1, reinterpret_cast<volatile int*>(&dummy));
   }
   __syncthreads();
   if (warp == 1) {
@@ -2234,12 +2246,13 @@ void launch_mttkrp_tf32(const CUtensorMap& mx, const CUtensorMap& mb, int64_t n1
   const int64_t per = (T + chunks - 1) / chunks;
   chunks = (T + per - 1) / per;
   const int grid = static_cast<int>(mblocks * chunks);
-  // 8 raw X tiles in flight (7 for the widest operand stages), 2 operand stages
+  // 8 raw X tiles in flight (7 for the widest operand stages), one operand
+  // stage per converter group
   constexpr int NR = (N <= 96) ? 8 : 7, NC = 2;
   const size_t smem = 1024 + NC * (size_t)(2 * kBM * kBK32 * 4 + N * kBK32 * 4) +
                       NR * (size_t)(4 * 32 * kBK32 * 4) + sizeof(BarsM) + 64;
   set_smem(tc_mttkrp_tf32_kernel<N, NR, NC>, smem);
-  tc_mttkrp_tf32_kernel<N, NR, NC><<<grid, kTf32Threads, smem, stream()>>>(
+  tc_mttkrp_tf32_kernel<N, NR, NC><<<grid, kMtThreads, smem, stream()>>>(
       mx, mb, n1, T, kchunks, mblocks, per, wT, L, Y, current()->d_status);
   check_launch("tc_mttkrp_tf32");
 }

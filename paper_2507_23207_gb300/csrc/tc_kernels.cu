@@ -593,12 +593,11 @@ __global__ void __launch_bounds__(kTf32Threads, 1)
 // MMAs take K-major operands only, so four converter warps turn each landed
 // X tile (four TMA boxes of 32 i x 32 i2, rows i2) into K-major rows i of 32
 // i2, once as X (the MMA reads its TF32 part X_h) and once as X_l = X - X_h,
-// both in the 128-byte swizzle of the descriptors.  D_t = X_h Om2_h +
-// X_h Om2_l + X_l Om2_h (three MMAs of width Lp into one accumulator; B holds
-// Om2_h in rows 0..Lp-1 and Om2_l in rows Lp..2Lp-1, N = 2 Lp) accumulates in
-// TMEM over the i2 chunks of slab t (two buffers); the epilogue weights it by
-// w_t and keeps Y's partial sums in registers, one FP32 atomic add per
-// output at the end.  CTA (mb, z) takes rows mb*128.. and slabs [z t_per_cta, ...).
+// both in the 128-byte swizzle of the descriptors.  D_t = X_h [Om2_h | Om2_l]
+// + X_l Om2_h accumulates in TMEM over the i2 chunks of slab t (two buffers of
+// width N = 2 Lp; one MMA of width N reads the X_h tile once); the epilogue
+// adds the two column halves, weights them by w_t and keeps Y's partial sums
+// in registers, one FP32 atomic add per output at the end.  CTA (mb, z) takes rows mb*128.. and slabs [z t_per_cta, ...).
 // Two rings: NR raw X tiles (TMA, released by the converters as soon as they
 // hold the values in registers, so that many tiles are in flight from HBM)
 // and NC operand stages (X_h^T, X_l^T written by the converters, the Om2
@@ -631,8 +630,9 @@ __global__ void __launch_bounds__(kMtThreads, 1)
   constexpr uint32_t kBBytes = N * kBK32 * 4;
   constexpr uint32_t kOp = 2 * kA + kBBytes;   // [X_h^T | X_l^T | Om2 chunk]
   static_assert(kOp % 1024 == 0, "operand stages must keep the 1 KB swizzle alignment");
-  constexpr uint32_t kTmemCols = (2 * Lp <= 32) ? 32 : (2 * Lp <= 64) ? 64 : 128;
-  constexpr uint32_t kIdesc = idesc_tf32(kBM, Lp);
+  constexpr uint32_t kTmemCols = (2 * N <= 64) ? 64 : (2 * N <= 128) ? 128 : 256;
+  constexpr uint32_t kIdesc = idesc_tf32(kBM, N);
+  constexpr uint32_t kIdescLo = idesc_tf32(kBM, Lp);
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   uint8_t* ops = smem;
@@ -707,7 +707,7 @@ __global__ void __launch_bounds__(kMtThreads, 1)
           break;
         }
         tc_fence_after();
-        const uint32_t dt = tmem + acc * Lp;
+        const uint32_t dt = tmem + acc * N;
         bool ok = true;
         for (int kc = 0; kc < kchunks; ++kc, ++it) {
           const int c = it % NC;
@@ -723,13 +723,12 @@ __global__ void __launch_bounds__(kMtThreads, 1)
           const uint32_t ah = smem_u32(ops + c * kOp);
           const uint32_t al = ah + kA;
           const uint32_t b = ah + 2 * kA;
-          const uint32_t bl = b + Lp * 128;  // Om2_l rows (whole 1 KB swizzle atoms)
 #pragma unroll
           for (int k = 0; k < kBK32 / 8; ++k) {
             mma_tf32(dt, sdesc(ah + 32 * k, 16, 1024), sdesc(b + 32 * k, 16, 1024), kIdesc,
                      (kc | k) != 0);
-            mma_tf32(dt, sdesc(ah + 32 * k, 16, 1024), sdesc(bl + 32 * k, 16, 1024), kIdesc, 1);
-            mma_tf32(dt, sdesc(al + 32 * k, 16, 1024), sdesc(b + 32 * k, 16, 1024), kIdesc, 1);
+            // X_l times the hi columns of Om2 (the first Lp rows of B)
+            mma_tf32(dt, sdesc(al + 32 * k, 16, 1024), sdesc(b + 32 * k, 16, 1024), kIdescLo, 1);
           }
           mma_commit(smem_u32(&bars->empty[c]));
         }
@@ -756,14 +755,15 @@ __global__ void __launch_bounds__(kMtThreads, 1)
         break;
       }
       tc_fence_after();
-      const uint32_t base = tmem + (static_cast<uint32_t>(q * 32) << 16) + acc * Lp;
+      const uint32_t base = tmem + (static_cast<uint32_t>(q * 32) << 16) + acc * N;
       const float* wt = wT + t * Lp;
 #pragma unroll
       for (int c0 = 0; c0 < Lp; c0 += 16) {
-        float v[16];
+        float v[16], u[16];
         tmem_ld16(base + c0, v);
+        tmem_ld16(base + Lp + c0, u);
 #pragma unroll
-        for (int j = 0; j < 16; ++j) accum[c0 + j] = fmaf(__ldg(wt + c0 + j), v[j], accum[c0 + j]);
+        for (int j = 0; j < 16; ++j) accum[c0 + j] = fmaf(__ldg(wt + c0 + j), v[j] + u[j], accum[c0 + j]);
       }
       tc_fence_before();
       __syncwarp();

@@ -650,9 +650,16 @@ def nystrom_run(ctx, dev, stream, reps, warm):
 
 
 # DRAM traffic (read + write bytes) per launch at 1024^3, from ncu captures at
-# 512^3 scaled by the bytes each part moves (X x8, the small outputs x2 or x4).
-# None where no capture of the current kernel exists.
-TRAFFIC_1024 = {}
+# 512^3 (dram__bytes_read.sum + dram__bytes_write.sum) scaled by the bytes
+# each part moves: X x8; the TTM's output (S x l) x4; the residual's H hi/lo
+# rows (S x 64) x4; the per-CTA atomic adds of the MTTKRP and the residual
+# (one row block of Y_1, two sums per CTA) x1.  A kernel changed since its
+# capture has no entry (null in the line).
+TRAFFIC_1024 = {
+    "tc_gemm_tn_tf32": 537.192192e6 * 8 + 43.580416e6 * 4,
+    "tc_mttkrp_tf32": 537.426176e6 * 8 + 3.841792e6,
+    "tc_residual_tf32": 537.2e6 * 8 + (604.1536e6 - 537.2e6) * 4 + 3.219456e6,
+}
 
 
 def _kernel_work(name, spec):

@@ -38,9 +38,13 @@
  *     returns a non-zero krp_status, launches nothing and records a message
  *     readable with krp_last_error.  No entry point aborts or throws.
  *   Threads.  A context may be used by one host thread at a time.
- *   Precision.  KRP_F32 inputs use FP32 CUDA-core arithmetic (the plain form);
- *     KRP_BF16 inputs run the contractions over X on tcgen05 tensor cores with
- *     FP32 accumulation.  QR, truncation and residual are FP64.
+ *   Precision.  KRP_F32 inputs keep FP32-level error: the passes over X run
+ *     on tcgen05 tensor cores as three TF32 products of exact hi/lo splits
+ *     (X F ~ X_h F_h + X_h F_l + X_l F_h) where n_1 % 4 == 0, X is 16-byte
+ *     aligned and the widths fit (l <= 64; c_1 <= 32 for the residual), and
+ *     on FP32 CUDA cores otherwise; KRP_BF16 inputs run the contractions over
+ *     X on tcgen05 with BF16 operands and FP32 accumulation.  QR, truncation
+ *     and the residual's sums are FP64.
  */
 #ifndef KRP_H_
 #define KRP_H_

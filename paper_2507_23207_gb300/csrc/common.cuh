@@ -125,7 +125,8 @@ struct Radix {
   const float* V[KRP_MAXD];  // FP32 factors, column-major, ld = radix
 };
 
-// FP32 CUDA-core kernels (f32_kernels.cu)
+// FP32 CUDA-core kernels (f32_kernels.cu; mttkrp_first_f32 hands shapes the
+// tensor cores take to the TF32 MTTKRP of tc_kernels.cu)
 // out[s + ldo*k] (=|+=) sum_i A[i + lda*s] * F[i + ldf*k], s<S, k<L, i<K
 void gemm_tn_f32(const float* A, int64_t lda, int64_t S, int K, const float* F,
                  int64_t ldf, int L, float* out, int64_t ldo, bool accumulate);

@@ -98,7 +98,8 @@ void hankel_sketch_only(const void* blocks, krp_dtype bt, int m, int n, int s,
                         const void* psi2, int ell_l, float* Y, float* Z);
 
 // Contractions over the big tensor, dispatched on its element type:
-// FP32 -> CUDA-core kernels, BF16 -> tcgen05 tensor-core kernels.
+// FP32 -> tcgen05 as three TF32 products where the shape allows (else FP32
+// CUDA-core kernels), BF16 -> tcgen05 tensor-core kernels.
 //   out[s + S*k] = sum_{i < n1} X[i + n1*s] F[i + n1*k],  S = N / n1
 // F is given in FP32 (Ff) and, for BF16 X, as a bf16 hi/lo pair (Fhi, Flo;
 // Flo may be null).

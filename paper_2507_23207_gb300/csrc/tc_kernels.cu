@@ -1,6 +1,11 @@
-// BF16 tensor-core contractions over the big tensor on sm_103a: tcgen05.mma
-// (kind::f16, BF16 operands, FP32 accumulators in TMEM) fed by TMA
-// (cp.async.bulk.tensor, 128-byte swizzle) through an mbarrier pipeline.
+// Tensor-core contractions over the big tensor on sm_103a: tcgen05.mma
+// (kind::f16 with BF16 operands; kind::tf32 for FP32 data as three TF32
+// products of exact hi/lo splits; FP32 accumulators in TMEM) fed by TMA
+// (cp.async.bulk.tensor, 128-byte swizzle) through mbarrier pipelines.
+//
+//   tc_gemm_tn_tf32, tc_mttkrp_first_tf32, tc_residual_tf32: the same three
+//       contractions for FP32 X (the MTTKRP's converter warps transpose each
+//       X tile into K-major rows, since these MMAs take K-major operands)
 //
 //   tc_gemm_tn_bf16:       out[s, k] = sum_i X[i, s] F[i, k]
 //       (TTM of the fastest mode, Sec. 2.1; A = X is K-major: i contiguous)

@@ -64,6 +64,7 @@ void ensure_workspace(Ctx* c, size_t bytes) {
   if (c->ws.cap >= bytes) return;
   if (c->ws.base) {
     KRP_CUDA_CHECK(cudaStreamSynchronize(c->stream));
+    if (c->side_stream) KRP_CUDA_CHECK(cudaStreamSynchronize(c->side_stream));
     KRP_CUDA_CHECK(cudaFree(c->ws.base));
     c->ws.base = nullptr;
     c->ws.cap = 0;
@@ -184,6 +185,15 @@ krp_status krp_destroy(krp_ctx ctx) {
     ctx->c.copy_events.clear();
     if (ctx->c.copy_stream) cudaStreamDestroy(ctx->c.copy_stream);
     ctx->c.copy_stream = nullptr;
+    for (cudaEvent_t& e : ctx->c.side_events) {
+      if (e) cudaEventDestroy(e);
+      e = nullptr;
+    }
+    if (ctx->c.side_stream) {
+      cudaStreamSynchronize(ctx->c.side_stream);
+      cudaStreamDestroy(ctx->c.side_stream);
+    }
+    ctx->c.side_stream = nullptr;
     if (ctx->c.batch_plan) ctx->c.batch_plan_free(ctx->c.batch_plan);
     ctx->c.batch_plan = nullptr;
     if (ctx->c.hankel_plan) ctx->c.hankel_plan_free(ctx->c.hankel_plan);

@@ -78,6 +78,11 @@ struct Ctx {
   // host-to-device copies overlapped with the sketch (created on first use)
   cudaStream_t copy_stream = nullptr;
   std::vector<cudaEvent_t> copy_events;
+  // FP64 QR beside the FP32 form's TF32 TTMs (created on first use); the
+  // TF32 TTM leaves tc_reserve_sms SMs free while it is set
+  cudaStream_t side_stream = nullptr;
+  cudaEvent_t side_events[4] = {};
+  int tc_reserve_sms = 0;
   // tree splits picked by timing, per (dims, l, dtype)
   std::map<std::vector<int64_t>, int> tree_split_cache;
   // launch trace (krp_trace_begin/end): an event after every launch

@@ -1,6 +1,8 @@
 // Internal: pipelines built from the kernels (not part of the C ABI).
 #pragma once
 
+#include <functional>
+
 #include "common.cuh"
 
 namespace krp {
@@ -29,11 +31,18 @@ void sketch_one_mode(const SketchArgs& a, int n, float* Y);
 // and the merged modes 2..tree_split+1 in one pass (1 <= tree_split <= d-1);
 // -1 picks it by timing each candidate on the first call for a shape
 // (cached in the context).  The FP32 form ignores it.
-void sketch_all_modes(const SketchArgs& a, float* const* Y, int tree_split = -1);
+// after_first: called (if set) once Y[0] is enqueued and before the rest of
+// the FP32 form's tree, so that work on Y[0] can start beside it
+void sketch_all_modes(const SketchArgs& a, float* const* Y, int tree_split = -1,
+                      const std::function<void()>& after_first = {});
 
 size_t multi_ttm_workspace_bytes(int d, const int64_t* dims, const int* cols, krp_dtype xt);
+// q0_ready / qrest_ready (optional): events after which Q[0] / Q[1..d-1]
+// are written (by work on another stream); the context's stream waits on
+// each before it first reads that factor
 void multi_ttm(const void* X, krp_dtype xt, int d, const int64_t* dims, const double* const* Q,
-               const int* cols, float* G);
+               const int* cols, float* G, cudaEvent_t q0_ready = nullptr,
+               cudaEvent_t qrest_ready = nullptr);
 
 size_t core_truncate_workspace_bytes(int d, const int* ell, const int* ranks);
 void core_truncate(int d, const int64_t* dims, const int* ell, const int* ranks, const float* G,

@@ -231,6 +231,8 @@ static const __nv_bfloat16* lo_plane(const void* X, krp_dtype xt, int64_t N) {
 }
 static bool bf16_family(krp_dtype t) { return t == KRP_BF16 || t == KRP_BF16X2; }
 static int round_up16(int v) { return (v + 15) / 16 * 16; }
+// SMs the FP32 form's TF32 TTMs leave to the FP64 QR on the second stream
+constexpr int kQrSideSms = 8;
 
 void big_gemm_tn(const void* X, krp_dtype xt, int64_t n1, int64_t S, const float* Ff,
                  const __nv_bfloat16* Fhi, const __nv_bfloat16* Flo, int L, float* out) {
@@ -423,7 +425,8 @@ static bool tree_split_ok(const SketchArgs& a, int s) {
   return n2 < (int64_t(1) << 31) && a.N / (a.dims[0] * n2) < (int64_t(1) << 31);
 }
 
-void sketch_all_modes(const SketchArgs& a, float* const* Y, int tree_split) {
+void sketch_all_modes(const SketchArgs& a, float* const* Y, int tree_split,
+                      const std::function<void()>& after_first) {
   for (int j = 0; j < a.d; ++j) KRP_REQUIRE(a.omega[j], "omega[%d] is NULL", j);
   const int64_t n1 = a.dims[0], S = a.N / n1;
   const float* f32v[KRP_MAXD];
@@ -477,6 +480,7 @@ void sketch_all_modes(const SketchArgs& a, float* const* Y, int tree_split) {
   }
   f32_factor_views(a, f32v);
   big_mttkrp_first(a.X, a.xt, n1, a.d - 1, a.dims + 1, a.omega + 1, a.ell, Y[0]);
+  if (after_first) after_first();
   float* B = current()->ws.take<float>((size_t)S * a.ell);
   big_gemm_tn(a.X, a.xt, n1, S, f32v[0], static_cast<const __nv_bfloat16*>(a.omega[0]), nullptr,
               a.ell, B);
@@ -563,15 +567,19 @@ size_t multi_ttm_workspace_bytes(int d, const int64_t* dims, const int* cols, kr
 }
 
 void multi_ttm(const void* X, krp_dtype xt, int d, const int64_t* dims, const double* const* Q,
-               const int* cols, float* G) {
+               const int* cols, float* G, cudaEvent_t q0_ready, cudaEvent_t qrest_ready) {
   Ctx* c = current();
   const int64_t N = checked_numel(d, dims);
   const int64_t n1 = dims[0];
   float* Qf[KRP_MAXD];
   __nv_bfloat16 *Qh = nullptr, *Ql = nullptr;
+  if (q0_ready) KRP_CUDA_CHECK(cudaStreamWaitEvent(c->stream, q0_ready, 0));
+  // the other factors are read after the first TTM when they come from
+  // another stream (qrest_ready), else converted here
+  const int jcast = qrest_ready ? 1 : d;
   for (int j = 0; j < d; ++j) {
     Qf[j] = c->ws.take<float>((size_t)dims[j] * cols[j]);
-    cast_f64_to_f32(Q[j], Qf[j], dims[j] * cols[j]);
+    if (j < jcast) cast_f64_to_f32(Q[j], Qf[j], dims[j] * cols[j]);
   }
   if (bf16_family(xt)) {
     Qh = c->ws.take<__nv_bfloat16>((size_t)n1 * cols[0]);
@@ -604,6 +612,11 @@ void multi_ttm(const void* X, krp_dtype xt, int d, const int64_t* dims, const do
   } else {
     big_gemm_tn(X, xt, n1, N / n1, Qf[0], Qh, Ql, cols[0], cur);
     size = (N / n1) * cols[0];
+  }
+  if (qrest_ready) {
+    KRP_REQUIRE(j0 == 1, "factor events need the first TTM alone before the rest");
+    KRP_CUDA_CHECK(cudaStreamWaitEvent(c->stream, qrest_ready, 0));
+    for (int j = 1; j < d; ++j) cast_f64_to_f32(Q[j], Qf[j], dims[j] * cols[j]);
   }
   for (int j = j0; j < d; ++j) {
     float* nxt = (j == d - 1) ? G : buf[j & 1];
@@ -859,14 +872,51 @@ void tucker_pipeline(bool sequential, const void* X, krp_dtype xt, int d, const 
       }
     }
     tm.mark();  // 1
+    // FP32 form (two passes over X in the sketch): the FP64 QR of mode 1 runs
+    // on a second stream beside the tree's B-part TTM, the QRs of modes 2..d
+    // beside the core's first TTM (which needs Q_1 only); those TF32 TTMs
+    // leave kQrSideSms SMs to it.  Off under the launch trace, which times
+    // the launches of one stream.
+    const bool qr_side = memo && !overlap && xt == KRP_F32 && d >= 2 && !c->trace_on;
+    cudaEvent_t* sev = c->side_events;
+    auto side_qr = [&](int i0, int cnt, cudaEvent_t start, cudaEvent_t done) {
+      KRP_CUDA_CHECK(cudaEventRecord(start, c->stream));
+      KRP_CUDA_CHECK(cudaStreamWaitEvent(c->side_stream, start, 0));
+      struct Swap {
+        Ctx* c;
+        cudaStream_t s;
+        ~Swap() { c->stream = s; }
+      } swap{c, c->stream};
+      c->stream = c->side_stream;
+      run_qr(i0, cnt);
+      KRP_CUDA_CHECK(cudaEventRecord(done, c->side_stream));
+    };
+    if (qr_side) {
+      if (!c->side_stream)
+        KRP_CUDA_CHECK(cudaStreamCreateWithFlags(&c->side_stream, cudaStreamNonBlocking));
+      for (cudaEvent_t& e : c->side_events)
+        if (!e) KRP_CUDA_CHECK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    }
     if (memo) {
       SketchArgs a{};
       a.X = Xd; a.xt = xt; a.d = d; a.omt = ft; a.ell = ellmax; a.N = N;
       for (int j = 0; j < d; ++j) { a.dims[j] = dims[j]; a.omega[j] = fac[0][j]; }
-      if (overlap)
+      if (overlap) {
         sketch_host_overlapped(a, X, Y);
-      else
+      } else if (qr_side) {
+        struct Reserve {
+          Ctx* c;
+          ~Reserve() { c->tc_reserve_sms = 0; }
+        } reserve{c};
+        c->tc_reserve_sms = kQrSideSms;
+        sketch_all_modes(a, Y, -1, [&] { side_qr(0, 1, sev[0], sev[1]); });
+        side_qr(1, d - 1, sev[2], sev[3]);
+        tm.mark();  // 2
+        tm.mark();  // 3 (the QR runs beside the sketch and the core)
+        multi_ttm(Xd, xt, d, dims, Q, ell, G, sev[1], sev[3]);
+      } else {
         sketch_all_modes(a, Y);
+      }
     } else {
       for (int i = 0; i < d; ++i) {
         SketchArgs a{};
@@ -880,10 +930,12 @@ void tucker_pipeline(bool sequential, const void* X, krp_dtype xt, int d, const 
         ws.off = mark;
       }
     }
-    tm.mark();  // 2
-    run_qr(0, d);
-    tm.mark();  // 3
-    multi_ttm(Xd, xt, d, dims, Q, ell, G);
+    if (!qr_side) {
+      tm.mark();  // 2
+      run_qr(0, d);
+      tm.mark();  // 3
+      multi_ttm(Xd, xt, d, dims, Q, ell, G);
+    }
     tm.mark();  // 4
   } else {
     // Alg. 8: G <- X; for i: sketch G_(i), QR, G <- G x_i Q_i^T  (rotated layout)

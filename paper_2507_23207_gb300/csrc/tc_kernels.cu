@@ -2191,7 +2191,9 @@ template <int N>
 void launch_gemm_tf32(const CUtensorMap& ma, const CUtensorMap& mb, int64_t S, int kchunks, int L,
                       int Lp, float* out) {
   const int64_t tiles = (S + kBM - 1) / kBM;
-  const int grid = static_cast<int>(std::min<int64_t>(tiles, current()->num_sms));
+  // SMs left to work on another stream (the FP64 QR beside the TTM)
+  const int sms = std::max(1, current()->num_sms - current()->tc_reserve_sms);
+  const int grid = static_cast<int>(std::min<int64_t>(tiles, sms));
   constexpr int NS = (N <= 96) ? 5 : 4;
   const size_t smem = 1024 + NS * (size_t)(2 * kBM * kBK32 * 4 + N * kBK32 * 4) + sizeof(BarsT) + 64;
   set_smem(tc_gemm_tn_tf32_kernel<N, NS>, smem);

@@ -704,7 +704,8 @@ def trace_roofline(spec, f32, peaks, args):
     per launch / its average launch time; the other candidates are reported
     beside it."""
     tr = f32.get("trace") or []
-    step_ms = sum(t for _, t in tr) / max(1, args.steps)
+    # the timed step (launches on the second stream overlap the first's)
+    step_ms = f32.get("ms") or sum(t for _, t in tr) / max(1, args.steps)
     tot = {}
     for name, t in tr:
         if _kernel_work(name, spec):

@@ -237,12 +237,13 @@ krp_status krp_qr_noalloc(const float* Y, int64_t m, int l, double* Q,
                           double* R, void* cuda_stream);
 
 /* Launch trace (diagnostics): between krp_trace_begin and krp_trace_end the
- * context records a CUDA event on its stream after every kernel it launches
- * (not inside captured graphs).  krp_trace_end synchronises the stream and
- * writes a JSON list [["launch name", ms], ...] into json (cap bytes): the
- * time between consecutive events, i.e. each launch's duration on the stream
- * including any copy or memset enqueued just before it.  KRP_EINVAL if the
- * buffer is too small. */
+ * context records a CUDA event after every kernel it launches, on the stream
+ * of the launch (its own stream, or the second stream that runs the FP32
+ * form's QR beside the TTMs; not inside captured graphs).  krp_trace_end
+ * synchronises and writes a JSON list [["launch name", ms], ...] into json
+ * (cap bytes): the time from the previous event on the same stream, i.e.
+ * each launch's duration on its stream including any copy or memset
+ * enqueued just before it.  KRP_EINVAL if the buffer is too small. */
 krp_status krp_trace_begin(krp_ctx ctx);
 krp_status krp_trace_end(krp_ctx ctx, char* json, size_t cap);
 

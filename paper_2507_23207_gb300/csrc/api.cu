@@ -53,8 +53,17 @@ void check_launch(const char* name) {
     if (cs == cudaStreamCaptureStatusNone) {
       cudaEvent_t ev = trace_event(c);
       KRP_CUDA_CHECK(cudaEventRecord(ev, c->stream));
-      c->trace.push_back({name, ev});
+      c->trace.push_back({name, ev, c->stream});
     }
+  }
+}
+
+void trace_marker() {
+  Ctx* c = g_current;
+  if (c && c->trace_on) {
+    cudaEvent_t ev = trace_event(c);
+    KRP_CUDA_CHECK(cudaEventRecord(ev, c->stream));
+    c->trace.push_back({nullptr, ev, c->stream});
   }
 }
 
@@ -412,7 +421,7 @@ krp_status krp_trace_begin(krp_ctx ctx) {
     c->trace.clear();
     cudaEvent_t ev = trace_event(c);
     KRP_CUDA_CHECK(cudaEventRecord(ev, c->stream));
-    c->trace.push_back({nullptr, ev});
+    c->trace.push_back({nullptr, ev, c->stream});
     c->trace_on = true;
   });
 }
@@ -423,12 +432,20 @@ krp_status krp_trace_end(krp_ctx ctx, char* json, size_t cap) {
     c->trace_on = false;
     KRP_REQUIRE(json && cap > 2, "json buffer is NULL or too small");
     KRP_CUDA_CHECK(cudaStreamSynchronize(c->stream));
+    if (c->side_stream) KRP_CUDA_CHECK(cudaStreamSynchronize(c->side_stream));
+    // each launch: the time since the previous event on its own stream
     std::string out = "[";
+    bool first = true;
     for (size_t i = 1; i < c->trace.size(); ++i) {
+      if (!c->trace[i].name) continue;
+      size_t p = i;
+      while (p > 0 && c->trace[p - 1].st != c->trace[i].st) --p;
+      if (p == 0) continue;  // no earlier event on this stream
       float ms = 0.f;
-      KRP_CUDA_CHECK(cudaEventElapsedTime(&ms, c->trace[i - 1].second, c->trace[i].second));
+      KRP_CUDA_CHECK(cudaEventElapsedTime(&ms, c->trace[p - 1].ev, c->trace[i].ev));
       char item[160];
-      snprintf(item, sizeof(item), "%s[\"%s\", %.6f]", i > 1 ? ", " : "", c->trace[i].first, ms);
+      snprintf(item, sizeof(item), "%s[\"%s\", %.6f]", first ? "" : ", ", c->trace[i].name, ms);
+      first = false;
       out += item;
     }
     out += "]";

@@ -85,12 +85,22 @@ struct Ctx {
   int tc_reserve_sms = 0;
   // tree splits picked by timing, per (dims, l, dtype)
   std::map<std::vector<int64_t>, int> tree_split_cache;
-  // launch trace (krp_trace_begin/end): an event after every launch
+  // launch trace (krp_trace_begin/end): an event after every launch, on the
+  // stream of the launch (name null: a marker, e.g. where a second stream
+  // starts after waiting on the first)
+  struct TraceRec {
+    const char* name;
+    cudaEvent_t ev;
+    cudaStream_t st;
+  };
   bool trace_on = false;
-  std::vector<std::pair<const char*, cudaEvent_t>> trace;
+  std::vector<TraceRec> trace;
   std::vector<cudaEvent_t> trace_pool;
 };
 
+// launch trace: an unnamed event on the current stream (where a second
+// stream starts after waiting on the first)
+void trace_marker();
 Ctx* current();           // context of the API call in progress (thread-local)
 cudaStream_t stream();    // its stream
 void ensure_workspace(Ctx* c, size_t bytes);

@@ -232,7 +232,7 @@ static const __nv_bfloat16* lo_plane(const void* X, krp_dtype xt, int64_t N) {
 static bool bf16_family(krp_dtype t) { return t == KRP_BF16 || t == KRP_BF16X2; }
 static int round_up16(int v) { return (v + 15) / 16 * 16; }
 // SMs the FP32 form's TF32 TTMs leave to the FP64 QR on the second stream
-constexpr int kQrSideSms = 8;
+constexpr int kQrSideSms = 16;
 
 void big_gemm_tn(const void* X, krp_dtype xt, int64_t n1, int64_t S, const float* Ff,
                  const __nv_bfloat16* Fhi, const __nv_bfloat16* Flo, int L, float* out) {
@@ -875,9 +875,8 @@ void tucker_pipeline(bool sequential, const void* X, krp_dtype xt, int d, const 
     // FP32 form (two passes over X in the sketch): the FP64 QR of mode 1 runs
     // on a second stream beside the tree's B-part TTM, the QRs of modes 2..d
     // beside the core's first TTM (which needs Q_1 only); those TF32 TTMs
-    // leave kQrSideSms SMs to it.  Off under the launch trace, which times
-    // the launches of one stream.
-    const bool qr_side = memo && !overlap && xt == KRP_F32 && d >= 2 && !c->trace_on;
+    // leave kQrSideSms SMs to it.
+    const bool qr_side = memo && !overlap && xt == KRP_F32 && d >= 2;
     cudaEvent_t* sev = c->side_events;
     auto side_qr = [&](int i0, int cnt, cudaEvent_t start, cudaEvent_t done) {
       KRP_CUDA_CHECK(cudaEventRecord(start, c->stream));
@@ -888,6 +887,7 @@ void tucker_pipeline(bool sequential, const void* X, krp_dtype xt, int d, const 
         ~Swap() { c->stream = s; }
       } swap{c, c->stream};
       c->stream = c->side_stream;
+      trace_marker();
       run_qr(i0, cnt);
       KRP_CUDA_CHECK(cudaEventRecord(done, c->side_stream));
     };

@@ -232,7 +232,7 @@ static const __nv_bfloat16* lo_plane(const void* X, krp_dtype xt, int64_t N) {
 static bool bf16_family(krp_dtype t) { return t == KRP_BF16 || t == KRP_BF16X2; }
 static int round_up16(int v) { return (v + 15) / 16 * 16; }
 // SMs the FP32 form's TF32 TTMs leave to the FP64 QR on the second stream
-constexpr int kQrSideSms = 16;
+constexpr int kQrSideSms = 8;
 
 void big_gemm_tn(const void* X, krp_dtype xt, int64_t n1, int64_t S, const float* Ff,
                  const __nv_bfloat16* Fhi, const __nv_bfloat16* Flo, int L, float* out) {

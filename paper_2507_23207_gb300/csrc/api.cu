@@ -69,11 +69,14 @@ void trace_marker() {
 
 void ensure_workspace(Ctx* c, size_t bytes) {
   bytes = (bytes + (size_t(1) << 20)) & ~((size_t(1) << 20) - 1);
+  // the second stream's work of an earlier call (joined into the context's
+  // stream on success; possibly still running after an error) must not see
+  // its workspace handed out again
+  if (c->side_stream) KRP_CUDA_CHECK(cudaStreamSynchronize(c->side_stream));
   c->ws.off = 0;
   if (c->ws.cap >= bytes) return;
   if (c->ws.base) {
     KRP_CUDA_CHECK(cudaStreamSynchronize(c->stream));
-    if (c->side_stream) KRP_CUDA_CHECK(cudaStreamSynchronize(c->side_stream));
     KRP_CUDA_CHECK(cudaFree(c->ws.base));
     c->ws.base = nullptr;
     c->ws.cap = 0;

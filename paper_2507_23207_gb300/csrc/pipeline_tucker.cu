@@ -749,14 +749,13 @@ void tucker_pipeline(bool sequential, const void* X, krp_dtype xt, int d, const 
   const bool memo = (flags & KRP_MEMO) && !sequential;
   const bool trunc = flags & KRP_TRUNCATE;
   const bool resid = flags & KRP_RESIDUAL;
-  int ell[KRP_MAXD], oc[KRP_MAXD];
+  int ell[KRP_MAXD];
   int ellmax = 0;
   for (int i = 0; i < d; ++i) {
     KRP_REQUIRE(ranks[i] >= 1, "ranks[%d] must be >= 1", i);
     ell[i] = ranks[i] + oversample;
     KRP_REQUIRE(ell[i] <= dims[i], "l_%d = %d exceeds n_%d = %lld", i, ell[i], i, (long long)dims[i]);
     KRP_REQUIRE(ell[i] <= (trunc ? 64 : 256), "l_%d = %d too large", i, ell[i]);
-    oc[i] = trunc ? ranks[i] : ell[i];
     ellmax = std::max(ellmax, ell[i]);
     KRP_REQUIRE(out->factors[i], "out->factors[%d] is NULL", i);
   }

@@ -554,7 +554,7 @@ __global__ void __launch_bounds__(256)
     __syncthreads();
     for (int q = tid; q < KC * TM; q += 256) {
       const int kk = q / TM, r = q % TM;
-      const int64_t i = i0 + r, s = s0 + r;
+      const int64_t i = i0 + r;
       Qs[kk][r] = (kc + kk < l && i < n1) ? Q1[i + n1 * (kc + kk)] : 0.f;
     }
     for (int q = tid; q < KC * TM; q += 256) {
